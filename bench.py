@@ -1,0 +1,358 @@
+"""Benchmark of the B300 drone physics step (one JSON line on stdout).
+
+Default workload (the headline configuration): 16384 worlds x 1 drone,
+first-principles model, attitude interface, RK4 at dt = 1/500 s, 1000 steps
+fused as launches of K = 100.  One benchmark "step" is that whole rollout
+(10 launches).  The metric is drone-steps per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+build) on a bounded sample of the same workload on the host cores.
+Under torchrun (N > 1) every rank runs an independent shard of worlds (no
+collective on the data path; "weak" scaling), and rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "drone-steps/s (fwd, fused RK4, first-principles + attitude controller)"
+UNIT = "drone-steps/s"
+# FP32 arithmetic of one RK4 drone-step of the first-principles model under the
+# attitude interface (FMA = 2 flop), counted term by term from the kernel's
+# formulation: controller 93 + 4 derivatives x 78 + RK4 combination 221 +
+# quaternion renormalisation 11 = 637 (command decode, amortised over 50-step
+# holds, adds ~1.2).
+FLOP_PER_DRONE_STEP = {("fp", "rk4", "attitude"): 637.0, ("fp", "euler", "attitude"): 216.0}
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if s[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# --------------------------------------------------------------------------- helpers
+
+
+def _src_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2606_01478_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(f"{kernel}:{workload}")
+    if not rec or rec.get("src_hash") != _src_hash():
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def _max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- reference arm
+
+
+def oracle_sample(wl, n_drones: int, n_steps: int) -> tuple[float, int]:
+    """Time the FP64 oracle on the first n_drones drones for n_steps steps.
+    Returns (seconds, drone-steps)."""
+    from oracle import physics as ph
+    t = time.perf_counter()
+    ph.rollout_workload(wl, steps=n_steps, drones=np.arange(n_drones))
+    return time.perf_counter() - t, n_drones * n_steps
+
+
+def cpu_baseline(wl, budget_s: float = 12.0) -> dict:
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    workload: all worlds, as many steps as fit about budget_s seconds."""
+    dt1, _ = oracle_sample(wl, wl.M, 2)
+    steps = int(max(4, min(wl.steps, budget_s / max(dt1 / 2, 1e-6))))
+    secs, units = oracle_sample(wl, wl.M, steps)
+    return {"value": units / secs, "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"{wl.M} drones x {steps} of {wl.steps} steps (FP64 torch CPU oracle)"}
+
+
+def run_reference(args, wl):
+    dist, rank, ws = _dist()
+    if rank != 0:
+        return 0
+    n_steps = 20
+    for _ in range(args.warmup):
+        oracle_sample(wl, wl.M, n_steps)
+    secs, units = 0.0, 0
+    for _ in range(args.steps):
+        s, u = oracle_sample(wl, wl.M, n_steps)
+        secs += s
+        units += u
+    value = units / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(wl, args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{wl.M} drones x {n_steps} of {wl.steps} steps per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(wl, args):
+    return {"workload": wl.name, "worlds": wl.M, "drones_per_world": wl.N,
+            "model": "first-principles", "integrator": "rk4", "control": "attitude",
+            "dt": wl.dt, "steps_per_rollout": wl.steps, "K_fused": wl.K,
+            "parallelism": f"replicas x{args.gpus} (independent worlds)",
+            "l2": "flushed (256 MiB write) before every timed iteration"}
+
+
+# --------------------------------------------------------------------------- B300 arm
+
+
+def run_b300(args, wl):
+    from paper_2606_01478_b300 import Sim
+    dist, rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    sim = Sim(wl.M, wl.N, 0, wl.integrator, wl.dt, ctrl=wl.ctrl, max_cmd_blocks=wl.cmd.shape[0],
+              device=dev)
+    sim.set_params(wl.params, wl.param_set_of_world)
+    if args.tpb:
+        sim.set_block_size(args.tpb)
+    x0_dev = torch.tensor(wl.x0, dtype=torch.float32, device=dev).contiguous()
+    cmd_dev = torch.tensor(wl.cmd, dtype=torch.float32, device=dev).contiguous()
+    x0_host = torch.tensor(wl.x0, dtype=torch.float32).pin_memory()
+    cmd_host = torch.tensor(wl.cmd, dtype=torch.float32).pin_memory()
+    out_host = torch.empty_like(x0_host).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    n_launch = (wl.steps + wl.K - 1) // wl.K
+
+    def one_rollout(events):
+        for j in range(n_launch):
+            k = min(wl.K, wl.steps - j * wl.K)
+            if events is not None:
+                events[j][0].record(stream)
+            sim.step(k)
+            if events is not None:
+                events[j][1].record(stream)
+
+    def reset():
+        sim.set_state(x0_dev)
+        sim.set_commands(cmd_dev, wl.hold)
+
+    for _ in range(args.warmup):
+        reset()
+        one_rollout(None)
+    torch.cuda.synchronize()
+    assert sim.status() == 0, "non-finite state during warm-up"
+
+    # device-resident timing (inputs already in HBM)
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_launch)]
+          for _ in range(args.steps)]
+    launches0 = sim.launches
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    _barrier(dist)
+    torch.cuda.synchronize()
+    per_iter_ms = []
+    for it in range(args.steps):
+        reset()
+        flush.fill_(it & 0xFF)
+        one_rollout(ev[it])
+        torch.cuda.synchronize()
+        per_iter_ms.append(ev[it][0][0].elapsed_time(ev[it][-1][1]))
+    torch.cuda.synchronize()
+    _barrier(dist)
+    clocks = sampler.stop()
+    # the set_state launch of each reset is not part of the timed region
+    gpu_launches = sim.launches - launches0 - args.steps * 1
+    launch_ms = [e[0].elapsed_time(e[1]) for it in range(args.steps) for e in ev[it]]
+    total_ms = _max_over_ranks(dist, sum(per_iter_ms))
+    units = wl.M * wl.steps * args.steps * ws
+    value = units / (total_ms / 1e3)
+
+    # end to end through the C-ABI with host buffers
+    e2e_ms = []
+    for it in range(args.steps):
+        flush.fill_(it & 0xFF)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        sim.set_state(x0_host)
+        sim.set_commands(cmd_host, wl.hold)
+        one_rollout(None)
+        sim.get_state(out=out_host)
+        t1.record(stream)
+        t1.synchronize()
+        e2e_ms.append(t0.elapsed_time(t1))
+    e2e_total = _max_over_ranks(dist, sum(e2e_ms))
+    assert sim.status() == 0
+    h2d = x0_host.numel() * 4 + cmd_host.numel() * 4
+    d2h = out_host.numel() * 4
+
+    if rank != 0:
+        return 0
+    pk, pk_kind = peaks()
+    clk_max = pk.get("sm_max_mhz", 2032.0)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clk_max * 1e6 / 1e12
+    flop = FLOP_PER_DRONE_STEP[("fp", "rk4", "attitude")]
+    avg_launch_s = statistics.mean(launch_ms) / 1e3
+    achieved = flop * wl.M * wl.K / avg_launch_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak,
+            "traffic": _profiled_traffic("step_kernel", wl.name),
+            "kernel": "step_kernel<first-principles, RK4, attitude>",
+            "flop_per_drone_step": flop,
+            "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                          f"{clk_max:.0f} MHz (max SM clock, {pk_kind} peaks file)"}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / (fp32_peak * clocks["sm_mhz"] / clk_max)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config(wl, args),
+        "e2e": {"value": units / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": gpu_launches,
+        "launch_ms": {"mean": statistics.mean(launch_ms), "min": min(launch_ms),
+                      "max": max(launch_ms), "count": len(launch_ms)},
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--tpb", type=int, default=0, help="threads per block (0 = library default)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    wl = W.config1(seed=1001 + 7919 * rank)
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_b300(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,176 @@
+/*
+ * crazyflow.h -- C-ABI of the B300 batched drone physics step.
+ *
+ * The library advances an M_worlds x N_drones batch of quadrotors through the
+ * simulation step of Crazyflow (arXiv 2606.01478, Materials and Methods):
+ * controller -> rotor dynamics -> rotor forces/torques -> rigid-body (or
+ * abstracted) derivative -> Euler or RK4 integrator, with K steps fused into
+ * one kernel launch (the paper fuses its step pipeline and scans it over
+ * steps: Architecture section).
+ *
+ * Conventions shared by every call
+ *   - Units: SI, rotor speeds in RPM.  World z up, gravity along -z.  Body x
+ *     forward, y left, z up.  Quaternions scalar-last [x, y, z, w] (First
+ *     Principles Modeling, after Eqs. 1-4).
+ *   - State row (SIM_STATE_DIM = 20 floats per drone):
+ *       first-principles: p(3) q(4) v(3) omega_body(3) Omega(4) I(3)
+ *         (the paper's x = [p, q, v, omega, Omega], text after Eq. 6, plus the
+ *          position-controller integrator I)
+ *       abstracted: p(3) Psi(3: roll, pitch, yaw) v(3) Psidot(3) f_sigma(1),
+ *         slots 13..19 unused (Abstracted Physics Modeling, state after Eq. 10)
+ *   - Command row (SIM_CMD_DIM = 4 floats per drone), by control interface:
+ *       SIM_CTRL_ROTOR_SPEED: Omega_cmd (RPM) per rotor
+ *       SIM_CTRL_ATTITUDE:    a in [-1,1]^4 = (roll, pitch, yaw, thrust),
+ *                             angles a*max_angle, thrust m g (1 + thrust_scale a4)
+ *       SIM_CTRL_POSITION:    (x, y, z, yaw) setpoint
+ *     (the paper's control interfaces: text after Eq. 6)
+ *   - Drone i of world w has global index w*N + i (uniform batches) or
+ *     offset[w] + i with offset the exclusive prefix sum of n_per_world.
+ *
+ * Memory ownership
+ *   The caller owns ALL device memory.  sim_workspace_bytes() reports the size
+ *   of one device workspace; sim_bind() hands it to the handle, which keeps the
+ *   pointer (not a copy) until sim_destroy() or the next sim_bind().  Inside it
+ *   live the state (5 float4 planes of length Ntot: plane j holds state slots
+ *   4j..4j+3 of every drone), the parameter sets, the command blocks, a staging
+ *   area for host transfers and a 4-byte device status word.  The library
+ *   itself allocates only the host-side handle (malloc) and never calls
+ *   cudaMalloc/cudaFree.
+ *
+ * Streams and errors
+ *   Every call that touches the device is asynchronous on the given stream
+ *   (a cudaStream_t passed as void*; NULL = legacy default stream) and
+ *   launches nothing when it returns an error.  Argument and call-order errors
+ *   return SIM_EINVAL / SIM_ESTATE immediately; a failed CUDA launch or copy
+ *   returns SIM_ECUDA.  sim_last_error() gives a message for the last failure
+ *   on that handle.  Conditions detected on the device (a non-finite state)
+ *   set bits in the device status word, read by sim_status().  No call traps,
+ *   asserts on the device or aborts the process.
+ */
+#ifndef CRAZYFLOW_B300_H
+#define CRAZYFLOW_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define SIM_OK 0
+#define SIM_EINVAL (-1)  /* bad argument (size, enum, NULL, unsupported combination) */
+#define SIM_ENOMEM (-2)  /* host allocation of the handle failed / workspace too small */
+#define SIM_ECUDA (-3)   /* a CUDA call failed; see sim_last_error */
+#define SIM_ESTATE (-4)  /* call order: e.g. sim_step before sim_bind / sim_set_params */
+
+/* device status word bits (sim_status) */
+#define SIM_FLAG_NONFINITE 1u /* some drone's state became NaN/Inf after a launch */
+
+/* physics models (First Principles Modeling, Eqs. 1-6; Abstracted Physics Modeling, Eqs. 7-10) */
+#define SIM_FIRST_PRINCIPLES 0
+#define SIM_ABSTRACTED 1
+
+/* integrators: explicit Euler, classic RK4 (controller output held over the stages) */
+#define SIM_EULER 0
+#define SIM_RK4 1
+
+/* control interfaces (text after Eq. 6); the abstracted model takes attitude commands only */
+#define SIM_CTRL_ROTOR_SPEED 0
+#define SIM_CTRL_ATTITUDE 1
+#define SIM_CTRL_POSITION 2
+
+#define SIM_STATE_DIM 20
+#define SIM_CMD_DIM 4
+#define SIM_NPARAMS 48
+
+/* Per-platform parameter vector (float[SIM_NPARAMS]); indices below.  kf and km
+ * are per RPM^2; the rotor model is Eq. 6 with coefficients (cv_up, cd_up) for
+ * spin-up and (cv_down, cd_down) for spin-down; C_a is the diagonal of the
+ * body-frame linear drag matrix (text after Eq. 5); gains are those of the
+ * geometric attitude/position controller; c1..c3 (roll, pitch, yaw), c_tau and
+ * c_f are the abstracted-model coefficients of Eqs. 8-10. */
+enum sim_param_index {
+  SIM_P_MASS = 0, SIM_P_JX, SIM_P_JY, SIM_P_JZ, SIM_P_ARM, SIM_P_KF, SIM_P_KM,
+  SIM_P_CV_UP, SIM_P_CD_UP, SIM_P_CV_DOWN, SIM_P_CD_DOWN, SIM_P_OMEGA_MAX,
+  SIM_P_CA_X, SIM_P_CA_Y, SIM_P_CA_Z,
+  SIM_P_KR_X, SIM_P_KR_Y, SIM_P_KR_Z, SIM_P_KW_X, SIM_P_KW_Y, SIM_P_KW_Z,
+  SIM_P_KP_X, SIM_P_KP_Y, SIM_P_KP_Z, SIM_P_KD_X, SIM_P_KD_Y, SIM_P_KD_Z,
+  SIM_P_KI_X, SIM_P_KI_Y, SIM_P_KI_Z,
+  SIM_P_MAX_ANGLE, SIM_P_THRUST_SCALE, SIM_P_G,
+  SIM_P_C1_R, SIM_P_C1_P, SIM_P_C1_Y, SIM_P_C2_R, SIM_P_C2_P, SIM_P_C2_Y,
+  SIM_P_C3_R, SIM_P_C3_P, SIM_P_C3_Y, SIM_P_C_TAU, SIM_P_C_F,
+  SIM_P_COUNT /* = 44 used entries; the vector is padded to SIM_NPARAMS */
+};
+
+typedef struct sim_s* sim_h;
+
+/* Create a handle for a uniform batch of M worlds x N drones, one model, one
+ * integrator, step dt (s).  Control interface defaults to SIM_CTRL_ATTITUDE.
+ * Returns SIM_EINVAL for M, N < 1, M*N > 2^31-1, unknown enums, dt <= 0. */
+int sim_create(sim_h* out, int64_t M, int64_t N, int model, int integrator, float dt);
+
+/* Create a handle for uneven / mixed batches: world w holds n_per_world[w]
+ * drones of model model_per_world[w] (both host arrays of length M, read
+ * during the call only).  Drones are laid out world after world. */
+int sim_create_batched(sim_h* out, int64_t M, const int64_t* n_per_world,
+                       const int32_t* model_per_world, int integrator, float dt);
+
+/* Select the control interface (SIM_CTRL_*).  SIM_EINVAL if the batch holds
+ * abstracted-model drones and ctrl is not SIM_CTRL_ATTITUDE. */
+int sim_set_control(sim_h h, int ctrl);
+
+/* Bytes of device workspace needed when up to max_cmd_blocks command blocks
+ * will be set (see sim_set_commands).  256-byte alignment required. */
+int sim_workspace_bytes(sim_h h, int64_t max_cmd_blocks, size_t* bytes);
+
+/* Give the handle its device workspace (caller-owned, >= the reported size,
+ * 256-byte aligned).  Clears nothing; sim_set_state / sim_set_params /
+ * sim_set_commands fill it.  Resets the status word (async on stream). */
+int sim_bind(sim_h h, void* workspace, size_t bytes, int64_t max_cmd_blocks, void* stream);
+
+/* Parameter sets: params is a host array [n_sets][SIM_NPARAMS] (floats in the
+ * order of enum sim_param_index), set_of_world a host array [M] of indices into
+ * it (NULL: every world uses set 0).  Both are read during the call only;
+ * derived constants are computed on the host in double precision and copied
+ * to the workspace with cudaMemcpyAsync on stream.  1 <= n_sets <= M. */
+int sim_set_params(sim_h h, const float* params, int64_t n_sets, const int32_t* set_of_world,
+                   void* stream);
+
+/* Load / read the state as rows [Ntot][SIM_STATE_DIM].  x may be host memory
+ * (pinned or pageable; copied through the workspace staging area) or device
+ * memory (read/written directly).  Asynchronous on stream; for pageable host
+ * memory CUDA makes the copy synchronous with respect to the host. */
+int sim_set_state(sim_h h, const float* x, void* stream);
+int sim_get_state(sim_h h, float* x, void* stream);
+
+/* Commands: cmd is [n_blocks][Ntot][SIM_CMD_DIM] (host or device memory,
+ * copied into the workspace).  Step s after this call (s = 0, 1, ...) uses
+ * block min(s / hold, n_blocks - 1).  1 <= n_blocks <= max_cmd_blocks, hold >= 1. */
+int sim_set_commands(sim_h h, const float* cmd, int64_t n_blocks, int hold, void* stream);
+
+/* Advance every drone by K steps in ONE kernel launch (state kept in
+ * registers across the K steps).  1 <= K <= 100000. */
+int sim_step(sim_h h, int K, void* stream);
+
+/* Advance n_steps steps as ceil(n_steps / K) launches of at most K steps. */
+int sim_run(sim_h h, int64_t n_steps, int K, void* stream);
+
+/* Threads per block used by sim_step (default 128; 32..256, multiple of 32). */
+int sim_set_block_size(sim_h h, int threads_per_block);
+
+/* Synchronise stream, read and clear the device status word (SIM_FLAG_*). */
+int sim_status(sim_h h, uint32_t* flags, void* stream);
+
+int64_t sim_num_drones(sim_h h);     /* Ntot, or -1 for a NULL handle */
+int64_t sim_step_count(sim_h h);     /* steps taken since the last sim_set_commands */
+const char* sim_last_error(sim_h h); /* message of the last failure ("" if none) */
+void sim_destroy(sim_h h);           /* frees the host handle; the workspace stays the caller's */
+
+/* Number of kernel launches issued on this handle since creation (all calls). */
+int64_t sim_launch_count(sim_h h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRAZYFLOW_B300_H */

@@ -1,0 +1,83 @@
+"""ctypes loader of libcrazyflow_b300.so (the C-ABI in include/crazyflow.h).
+
+The loader fails loudly: there is no fallback of any kind.  ``load()`` raises
+if the shared library has not been built (``python -m
+paper_2606_01478_b300.build``) or lacks a symbol the header declares.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_float, c_int, c_int64, c_size_t, c_uint32, c_void_p
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcrazyflow_b300.so")
+
+SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ESTATE = 0, -1, -2, -3, -4
+SIM_FLAG_NONFINITE = 1
+FIRST_PRINCIPLES, ABSTRACTED = 0, 1
+EULER, RK4 = 0, 1
+CTRL_ROTOR_SPEED, CTRL_ATTITUDE, CTRL_POSITION = 0, 1, 2
+STATE_DIM, CMD_DIM, NPARAMS = 20, 4, 48
+
+# Order of enum sim_param_index in include/crazyflow.h (checked by a CPU test).
+PARAM_ORDER = (
+    "mass", "Jx", "Jy", "Jz", "arm", "kf", "km",
+    "cv_up", "cd_up", "cv_down", "cd_down", "omega_max",
+    "Ca_x", "Ca_y", "Ca_z",
+    "KR_x", "KR_y", "KR_z", "Kw_x", "Kw_y", "Kw_z",
+    "Kp_x", "Kp_y", "Kp_z", "Kd_x", "Kd_y", "Kd_z", "Ki_x", "Ki_y", "Ki_z",
+    "max_angle", "thrust_scale", "g",
+    "c1_r", "c1_p", "c1_y", "c2_r", "c2_p", "c2_y", "c3_r", "c3_p", "c3_y",
+    "c_tau", "c_f",
+)
+
+_SIGS = {
+    "sim_create": (c_int, [POINTER(c_void_p), c_int64, c_int64, c_int, c_int, c_float]),
+    "sim_create_batched": (c_int, [POINTER(c_void_p), c_int64, POINTER(c_int64), POINTER(ctypes.c_int32),
+                                   c_int, c_float]),
+    "sim_set_control": (c_int, [c_void_p, c_int]),
+    "sim_workspace_bytes": (c_int, [c_void_p, c_int64, POINTER(c_size_t)]),
+    "sim_bind": (c_int, [c_void_p, c_void_p, c_size_t, c_int64, c_void_p]),
+    "sim_set_params": (c_int, [c_void_p, POINTER(c_float), c_int64, POINTER(ctypes.c_int32), c_void_p]),
+    "sim_set_state": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "sim_get_state": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "sim_set_commands": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_void_p]),
+    "sim_step": (c_int, [c_void_p, c_int, c_void_p]),
+    "sim_run": (c_int, [c_void_p, c_int64, c_int, c_void_p]),
+    "sim_set_block_size": (c_int, [c_void_p, c_int]),
+    "sim_status": (c_int, [c_void_p, POINTER(c_uint32), c_void_p]),
+    "sim_num_drones": (c_int64, [c_void_p]),
+    "sim_step_count": (c_int64, [c_void_p]),
+    "sim_launch_count": (c_int64, [c_void_p]),
+    "sim_last_error": (c_char_p, [c_void_p]),
+    "sim_destroy": (None, [c_void_p]),
+}
+
+_lib = None
+
+
+class SimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def load():
+    """Load the library (once) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2606_01478_b300.build` (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)  # AttributeError if the symbol is missing
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_symbols() -> tuple:
+    return tuple(_SIGS)

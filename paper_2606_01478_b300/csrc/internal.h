@@ -1,0 +1,18 @@
+// Host-side declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace cf {
+
+// Forward step launch (step.cu).  per_set: parameters per world from a.params.
+cudaError_t launch_step(const StepArgs& a, const DevParams& P, int model, int integrator, int ctrl,
+                        bool general_motor, bool per_set, int tpb, cudaStream_t st);
+
+// Row-major [n][20] floats <-> 5 float4 planes [5][n] (layout.cu).
+cudaError_t launch_rows_to_planes(const float4* rows, float4* planes, int n, cudaStream_t st);
+cudaError_t launch_planes_to_rows(const float4* planes, float4* rows, int n, cudaStream_t st);
+
+}  // namespace cf

@@ -1,0 +1,230 @@
+// Device functions of one drone step (one drone per thread, state in registers).
+//
+// State slots (SIM_STATE_DIM = 20):
+//   first-principles: 0-2 p, 3-6 q (x,y,z,w), 7-9 v, 10-12 omega (body),
+//                     13-16 Omega (RPM), 17-19 position-controller integrator
+//   abstracted:       0-2 p, 3-5 Psi, 6-8 v, 9-11 Psidot, 12 f_sigma
+#pragma once
+
+#include "common.cuh"
+
+namespace cf {
+
+enum : int { MOTOR_LAG = 0, MOTOR_GENERAL = 1 };
+
+// Rotation matrix (body -> world) of a scalar-last quaternion, quadratic form
+// R = (w^2 - |v|^2) I + 2 v v^T + 2 w [v]x applied to q as stored.
+__device__ __forceinline__ void quat_rot(float qx, float qy, float qz, float qw, float R[9]) {
+  const float xx = qx * qx, yy = qy * qy, zz = qz * qz, ww = qw * qw;
+  const float xy = qx * qy, xz = qx * qz, yz = qy * qz;
+  const float wx = qw * qx, wy = qw * qy, wz = qw * qz;
+  R[0] = (ww + xx) - (yy + zz);
+  R[1] = 2.f * (xy - wz);
+  R[2] = 2.f * (xz + wy);
+  R[3] = 2.f * (xy + wz);
+  R[4] = (ww + yy) - (xx + zz);
+  R[5] = 2.f * (yz - wx);
+  R[6] = 2.f * (xz - wy);
+  R[7] = 2.f * (yz + wx);
+  R[8] = (ww + zz) - (xx + yy);
+}
+
+// R = Rz(yaw) Ry(pitch) Rx(roll) from sines/cosines.
+__device__ __forceinline__ void euler_rot(float sr, float cr, float sp, float cp, float sy, float cy,
+                                          float R[9]) {
+  R[0] = cy * cp;
+  R[1] = cy * sp * sr - sy * cr;
+  R[2] = cy * sp * cr + sy * sr;
+  R[3] = sy * cp;
+  R[4] = sy * sp * sr + cy * cr;
+  R[5] = sy * sp * cr - cy * sr;
+  R[6] = -sp;
+  R[7] = cp * sr;
+  R[8] = cp * cr;
+}
+
+// Eq. 6 rotor dynamics.  LAG: cv_up = cv_down, cd = 0 (first-order lag).
+// GENERAL: W' = (Wc - W) (c_v + c_d (Wc + W)) with (c_v, c_d) picked by Wc >= W,
+// which equals c_v (Wc - W) + c_d (Wc^2 - W^2).
+template <int MOTOR>
+__device__ __forceinline__ float motor_rate(float W, float Wc, const DevParams& P) {
+  const float e = Wc - W;
+  if constexpr (MOTOR == MOTOR_LAG) {
+    return P.cv_up * e;
+  } else {
+    const bool up = Wc >= W;
+    const float cv = up ? P.cv_up : P.cv_down;
+    const float cd = up ? P.cd_up : P.cd_down;
+    return e * fmaf(cd, Wc + W, cv);
+  }
+}
+
+// First-principles derivative (Eqs. 1-4 with the rotor wrench and Eq. 6) of
+// x[0..16] for held rotor commands Wc.  Rotor i at (sx_i a, sy_i a) with
+// sx = (+,-,-,+), sy = (-,-,+,+), yaw sign s = (-,+,-,+).
+template <int MOTOR>
+__device__ __forceinline__ void deriv_fp(const float* x, const float Wc[4], const DevParams& P,
+                                         bool drag, float* d) {
+  const float qx = x[3], qy = x[4], qz = x[5], qw = x[6];
+  const float wx = x[10], wy = x[11], wz = x[12];
+  const float s0 = x[13] * x[13], s1 = x[14] * x[14], s2 = x[15] * x[15], s3 = x[16] * x[16];
+  const float T = P.kf * ((s0 + s1) + (s2 + s3));
+  const float tx = P.kfa * ((s2 + s3) - (s0 + s1));
+  const float ty = P.kfa * ((s1 + s2) - (s0 + s3));
+  const float tz = P.km * ((s1 + s3) - (s0 + s2));
+  // thrust along the third column of R(q)
+  const float Tm = T * P.inv_m;
+  const float r02 = 2.f * fmaf(qx, qz, qw * qy);
+  const float r12 = 2.f * fmaf(qy, qz, -qw * qx);
+  const float r22 = (qw * qw + qz * qz) - (qx * qx + qy * qy);
+  float ax = Tm * r02, ay = Tm * r12, az = fmaf(Tm, r22, -P.g);
+  if (drag) {
+    float R[9];
+    quat_rot(qx, qy, qz, qw, R);
+    const float vx = x[7], vy = x[8], vz = x[9];
+    const float bx = P.Ca_x * P.inv_m * (R[0] * vx + R[3] * vy + R[6] * vz);
+    const float by = P.Ca_y * P.inv_m * (R[1] * vx + R[4] * vy + R[7] * vz);
+    const float bz = P.Ca_z * P.inv_m * (R[2] * vx + R[5] * vy + R[8] * vz);
+    ax += R[0] * bx + R[1] * by + R[2] * bz;
+    ay += R[3] * bx + R[4] * by + R[5] * bz;
+    az += R[6] * bx + R[7] * by + R[8] * bz;
+  }
+  d[0] = x[7];
+  d[1] = x[8];
+  d[2] = x[9];
+  // q' = 1/2 q (x) [w, 0]
+  d[3] = 0.5f * (fmaf(qw, wx, qy * wz) - qz * wy);
+  d[4] = 0.5f * (fmaf(qw, wy, qz * wx) - qx * wz);
+  d[5] = 0.5f * (fmaf(qw, wz, qx * wy) - qy * wx);
+  d[6] = -0.5f * (fmaf(qx, wx, qy * wy) + qz * wz);
+  d[7] = ax;
+  d[8] = ay;
+  d[9] = az;
+  // w' = J^-1 tau - J^-1 (w x J w)
+  d[10] = fmaf(tx, P.inv_Jx, P.cJx * wy * wz);
+  d[11] = fmaf(ty, P.inv_Jy, P.cJy * wz * wx);
+  d[12] = fmaf(tz, P.inv_Jz, P.cJz * wx * wy);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) d[13 + r] = motor_rate<MOTOR>(x[13 + r], Wc[r], P);
+}
+
+// Abstracted derivative (Eqs. 7-10) of x[0..12] for u = (Psi_cmd, f_cmd).
+__device__ __forceinline__ void deriv_abs(const float* x, const float u[4], const DevParams& P,
+                                          bool drag, float* d) {
+  float sr, cr, sp, cp, sy, cy;
+  __sincosf(x[3], &sr, &cr);
+  __sincosf(x[4], &sp, &cp);
+  __sincosf(x[5], &sy, &cy);
+  // third column of Rz Ry Rx
+  const float r02 = fmaf(cy * sp, cr, sy * sr);
+  const float r12 = fmaf(sy * sp, cr, -cy * sr);
+  const float r22 = cp * cr;
+  const float fm = P.cf_inv_m * x[12];
+  float ax = fm * r02, ay = fm * r12, az = fmaf(fm, r22, -P.g);
+  if (drag) {
+    float R[9];
+    euler_rot(sr, cr, sp, cp, sy, cy, R);
+    const float vx = x[6], vy = x[7], vz = x[8];
+    const float bx = P.Ca_x * P.inv_m * (R[0] * vx + R[3] * vy + R[6] * vz);
+    const float by = P.Ca_y * P.inv_m * (R[1] * vx + R[4] * vy + R[7] * vz);
+    const float bz = P.Ca_z * P.inv_m * (R[2] * vx + R[5] * vy + R[8] * vz);
+    ax += R[0] * bx + R[1] * by + R[2] * bz;
+    ay += R[3] * bx + R[4] * by + R[5] * bz;
+    az += R[6] * bx + R[7] * by + R[8] * bz;
+  }
+  d[0] = x[6];
+  d[1] = x[7];
+  d[2] = x[8];
+  d[3] = x[9];
+  d[4] = x[10];
+  d[5] = x[11];
+  d[6] = ax;
+  d[7] = ay;
+  d[8] = az;
+  d[9] = fmaf(P.c1_r, x[3], fmaf(P.c2_r, x[9], P.c3_r * u[0]));
+  d[10] = fmaf(P.c1_p, x[4], fmaf(P.c2_p, x[10], P.c3_p * u[1]));
+  d[11] = fmaf(P.c1_y, x[5], fmaf(P.c2_y, x[11], P.c3_y * u[2]));
+  d[12] = P.c_tau * (u[3] - x[12]);
+}
+
+// ---------------------------------------------------------------- controller
+
+// Attitude action a -> desired rotation Rd and collective thrust Td.
+__device__ __forceinline__ void attitude_command(float4 a, const DevParams& P, float Rd[9],
+                                                 float& Td) {
+  const float ar = clampf(a.x, -1.f, 1.f) * P.max_angle;
+  const float ap = clampf(a.y, -1.f, 1.f) * P.max_angle;
+  const float ay = clampf(a.z, -1.f, 1.f) * P.max_angle;
+  float sr, cr, sp, cp, sy, cy;
+  __sincosf(ar, &sr, &cr);
+  __sincosf(ap, &sp, &cp);
+  __sincosf(ay, &sy, &cy);
+  euler_rot(sr, cr, sp, cp, sy, cy, Rd);
+  Td = fmaf(P.ts_mg, clampf(a.w, -1.f, 1.f), P.mg);
+}
+
+// Abstracted-model input (Psi_cmd, f_cmd) from an attitude action.
+__device__ __forceinline__ void abstracted_command(float4 a, const DevParams& P, float u[4]) {
+  u[0] = clampf(a.x, -1.f, 1.f) * P.max_angle;
+  u[1] = clampf(a.y, -1.f, 1.f) * P.max_angle;
+  u[2] = clampf(a.z, -1.f, 1.f) * P.max_angle;
+  u[3] = fmaf(P.ts_mg, clampf(a.w, -1.f, 1.f), P.mg);
+}
+
+// Geometric attitude PD, tau = -K_R J e_R - K_w J w with
+// e_R = 1/2 vee(Rd^T R - R^T Rd); only the off-diagonal entries of Rd^T R are formed.
+__device__ __forceinline__ void attitude_torque(const float R[9], const float Rd[9], float wx,
+                                                float wy, float wz, const DevParams& P,
+                                                float& tx, float& ty, float& tz) {
+#define CF_M(i, j) fmaf(Rd[i], R[j], fmaf(Rd[3 + i], R[3 + j], Rd[6 + i] * R[6 + j]))
+  const float ex = CF_M(2, 1) - CF_M(1, 2);
+  const float ey = CF_M(0, 2) - CF_M(2, 0);
+  const float ez = CF_M(1, 0) - CF_M(0, 1);
+#undef CF_M
+  tx = -fmaf(P.KRJh_x, ex, P.KwJ_x * wx);
+  ty = -fmaf(P.KRJh_y, ey, P.KwJ_y * wy);
+  tz = -fmaf(P.KRJh_z, ez, P.KwJ_z * wz);
+}
+
+// X-configuration mixer: per-rotor thrusts from (T, tau), clipped to
+// [0, fmax], converted to rotor-speed commands.
+__device__ __forceinline__ void mixer(float T, float tx, float ty, float tz, const DevParams& P,
+                                      float Wc[4]) {
+  const float A = 0.25f * T, X = tx * P.mix_a, Y = ty * P.mix_a, Z = tz * P.mix_k;
+  float f[4];
+  f[0] = (A - X) - (Y + Z);
+  f[1] = (A - X) + (Y + Z);
+  f[2] = (A + X) + (Y - Z);
+  f[3] = (A + X) - (Y - Z);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) Wc[r] = sqrt_approx(clampf(f[r], 0.f, P.fmax) * P.inv_kf);
+}
+
+// Position PID (geometric): setpoint sp = (x, y, z, yaw) with (sin, cos) of
+// yaw precomputed; returns Rd, Td and the integrator increment e_p.
+__device__ __forceinline__ void position_command(const float* x, const float R[9], float4 sp,
+                                                 float syaw, float cyaw, const DevParams& P,
+                                                 float Rd[9], float& Td, float ep[3]) {
+  ep[0] = sp.x - x[0];
+  ep[1] = sp.y - x[1];
+  ep[2] = sp.z - x[2];
+  const float adx = fmaf(P.Kp_x, ep[0], fmaf(P.Ki_x, x[17], -P.Kd_x * x[7]));
+  const float ady = fmaf(P.Kp_y, ep[1], fmaf(P.Ki_y, x[18], -P.Kd_y * x[8]));
+  const float adz = fmaf(P.Kp_z, ep[2], fmaf(P.Ki_z, x[19], -P.Kd_z * x[9])) + P.g;
+  Td = P.mass * fmaf(adx, R[2], fmaf(ady, R[5], adz * R[8]));
+  const float inz = rsqrt_approx(fmaf(adx, adx, fmaf(ady, ady, adz * adz)));
+  const float zx = adx * inz, zy = ady * inz, zz = adz * inz;
+  // y_d = z_d x (cos yaw, sin yaw, 0), normalised
+  float yx = -zz * syaw, yy = zz * cyaw, yz = fmaf(zx, syaw, -zy * cyaw);
+  const float iny = rsqrt_approx(fmaf(yx, yx, fmaf(yy, yy, yz * yz)));
+  yx *= iny;
+  yy *= iny;
+  yz *= iny;
+  // x_d = y_d x z_d
+  const float xx = fmaf(yy, zz, -yz * zy), xy = fmaf(yz, zx, -yx * zz), xz = fmaf(yx, zy, -yy * zx);
+  Rd[0] = xx; Rd[1] = yx; Rd[2] = zx;
+  Rd[3] = xy; Rd[4] = yy; Rd[5] = zy;
+  Rd[6] = xz; Rd[7] = yz; Rd[8] = zz;
+}
+
+}  // namespace cf

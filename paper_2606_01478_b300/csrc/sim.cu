@@ -1,0 +1,447 @@
+// C-ABI of the B300 drone step: handle management, argument validation,
+// workspace layout, host<->device transfers and kernel dispatch.
+// Declarations and contracts: include/crazyflow.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using cf::DevParams;
+
+struct sim_s {
+  int64_t M = 0, N = 0, ntot = 0;
+  bool batched = false;
+  int model = SIM_FIRST_PRINCIPLES;  // uniform batches
+  int integrator = SIM_EULER;
+  int ctrl = SIM_CTRL_ATTITUDE;
+  float dt = 0.f;
+  int tpb = 128;
+  std::vector<int64_t> n_per_world, offset;
+  std::vector<int32_t> model_of_world;
+  // workspace (caller-owned device memory)
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int64_t max_blocks = 0;
+  float4* planes = nullptr;
+  DevParams* params_dev = nullptr;
+  int32_t* set_of_world_dev = nullptr;
+  float4* cmd = nullptr;
+  float4* staging = nullptr;
+  uint32_t* status = nullptr;
+  // host copies
+  std::vector<DevParams> params_host;
+  DevParams p0;  // the single set of a uniform batch, passed by value
+  std::vector<int32_t> set_of_world_host;
+  bool params_ok = false, per_set = false, general_motor = false, state_ok = false;
+  int64_t n_blocks = 0;
+  int hold = 1;
+  int64_t t = 0;
+  int64_t launches = 0;
+  char err[512] = {0};
+};
+
+namespace {
+
+int fail(sim_h h, int code, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->err, sizeof(h->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+int cuda_fail(sim_h h, cudaError_t e, const char* what) {
+  return fail(h, SIM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t planes, params, set_of_world, cmd, staging, status, total;
+};
+
+Layout layout_of(const sim_s* h, int64_t max_blocks) {
+  Layout L;
+  size_t off = 0;
+  L.planes = off;
+  off = align256(off + (size_t)h->ntot * 5 * sizeof(float4));
+  L.params = off;
+  off = align256(off + (size_t)h->M * sizeof(DevParams));
+  L.set_of_world = off;
+  off = align256(off + (size_t)h->M * sizeof(int32_t));
+  L.cmd = off;
+  off = align256(off + (size_t)max_blocks * h->ntot * sizeof(float4));
+  L.staging = off;
+  off = align256(off + (size_t)h->ntot * SIM_STATE_DIM * sizeof(float));
+  L.status = off;
+  off = align256(off + sizeof(uint32_t));
+  L.total = off;
+  return L;
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool valid_enums(int model, int integrator) {
+  return (model == SIM_FIRST_PRINCIPLES || model == SIM_ABSTRACTED) &&
+         (integrator == SIM_EULER || integrator == SIM_RK4);
+}
+
+// Host derivation of the kernel constants from one user parameter vector.
+int derive_params(const float* p, DevParams* d, char* why, size_t why_n) {
+  for (int k = 0; k < SIM_P_COUNT; ++k) {
+    if (!isfinite(p[k])) {
+      snprintf(why, why_n, "parameter %d is not finite", k);
+      return SIM_EINVAL;
+    }
+  }
+  const int pos[] = {SIM_P_MASS, SIM_P_JX, SIM_P_JY, SIM_P_JZ, SIM_P_ARM, SIM_P_KF, SIM_P_KM,
+                     SIM_P_OMEGA_MAX};
+  for (int k : pos) {
+    if (!(p[k] > 0.f)) {
+      snprintf(why, why_n, "parameter %d must be > 0", k);
+      return SIM_EINVAL;
+    }
+  }
+  const double m = p[SIM_P_MASS], g = p[SIM_P_G];
+  const double Jx = p[SIM_P_JX], Jy = p[SIM_P_JY], Jz = p[SIM_P_JZ];
+  const double a = p[SIM_P_ARM] / sqrt(2.0);
+  const double kf = p[SIM_P_KF], km = p[SIM_P_KM], wmax = p[SIM_P_OMEGA_MAX];
+  memset(d, 0, sizeof(*d));
+  d->inv_m = (float)(1.0 / m);
+  d->g = (float)g;
+  d->mass = (float)m;
+  d->inv_Jx = (float)(1.0 / Jx);
+  d->inv_Jy = (float)(1.0 / Jy);
+  d->inv_Jz = (float)(1.0 / Jz);
+  d->cJx = (float)((Jy - Jz) / Jx);
+  d->cJy = (float)((Jz - Jx) / Jy);
+  d->cJz = (float)((Jx - Jy) / Jz);
+  d->kf = (float)kf;
+  d->kfa = (float)(kf * a);
+  d->km = (float)km;
+  d->cv_up = p[SIM_P_CV_UP];
+  d->cd_up = p[SIM_P_CD_UP];
+  d->cv_down = p[SIM_P_CV_DOWN];
+  d->cd_down = p[SIM_P_CD_DOWN];
+  d->Ca_x = p[SIM_P_CA_X];
+  d->Ca_y = p[SIM_P_CA_Y];
+  d->Ca_z = p[SIM_P_CA_Z];
+  d->KRJh_x = (float)(0.5 * p[SIM_P_KR_X] * Jx);
+  d->KRJh_y = (float)(0.5 * p[SIM_P_KR_Y] * Jy);
+  d->KRJh_z = (float)(0.5 * p[SIM_P_KR_Z] * Jz);
+  d->KwJ_x = (float)(p[SIM_P_KW_X] * Jx);
+  d->KwJ_y = (float)(p[SIM_P_KW_Y] * Jy);
+  d->KwJ_z = (float)(p[SIM_P_KW_Z] * Jz);
+  d->Kp_x = p[SIM_P_KP_X];
+  d->Kp_y = p[SIM_P_KP_Y];
+  d->Kp_z = p[SIM_P_KP_Z];
+  d->Kd_x = p[SIM_P_KD_X];
+  d->Kd_y = p[SIM_P_KD_Y];
+  d->Kd_z = p[SIM_P_KD_Z];
+  d->Ki_x = p[SIM_P_KI_X];
+  d->Ki_y = p[SIM_P_KI_Y];
+  d->Ki_z = p[SIM_P_KI_Z];
+  d->max_angle = p[SIM_P_MAX_ANGLE];
+  d->mg = (float)(m * g);
+  d->ts_mg = (float)(p[SIM_P_THRUST_SCALE] * m * g);
+  d->mix_a = (float)(1.0 / (4.0 * a));
+  d->mix_k = (float)(kf / (4.0 * km));
+  d->inv_kf = (float)(1.0 / kf);
+  d->fmax = (float)(kf * wmax * wmax);
+  d->omega_max = (float)wmax;
+  d->c1_r = p[SIM_P_C1_R];
+  d->c1_p = p[SIM_P_C1_P];
+  d->c1_y = p[SIM_P_C1_Y];
+  d->c2_r = p[SIM_P_C2_R];
+  d->c2_p = p[SIM_P_C2_P];
+  d->c2_y = p[SIM_P_C2_Y];
+  d->c3_r = p[SIM_P_C3_R];
+  d->c3_p = p[SIM_P_C3_P];
+  d->c3_y = p[SIM_P_C3_Y];
+  d->c_tau = p[SIM_P_C_TAU];
+  d->cf_inv_m = (float)(p[SIM_P_C_F] / m);
+  int flags = 0;
+  if (p[SIM_P_CA_X] != 0.f || p[SIM_P_CA_Y] != 0.f || p[SIM_P_CA_Z] != 0.f) flags |= cf::PF_DRAG;
+  if (p[SIM_P_CV_UP] != p[SIM_P_CV_DOWN] || p[SIM_P_CD_UP] != 0.f || p[SIM_P_CD_DOWN] != 0.f)
+    flags |= cf::PF_GENERAL_MOTOR;
+  d->flags = flags;
+  return SIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sim_create(sim_h* out, int64_t M, int64_t N, int model, int integrator, float dt) {
+  if (!out) return SIM_EINVAL;
+  *out = nullptr;
+  if (M < 1 || N < 1 || M * N > 0x7fffffffLL || !valid_enums(model, integrator) || !(dt > 0.f) ||
+      !isfinite(dt))
+    return SIM_EINVAL;
+  sim_s* h = new (std::nothrow) sim_s();
+  if (!h) return SIM_ENOMEM;
+  h->M = M;
+  h->N = N;
+  h->ntot = M * N;
+  h->model = model;
+  h->integrator = integrator;
+  h->dt = dt;
+  *out = h;
+  return SIM_OK;
+}
+
+int sim_create_batched(sim_h* out, int64_t M, const int64_t* n_per_world,
+                       const int32_t* model_per_world, int integrator, float dt) {
+  if (!out) return SIM_EINVAL;
+  *out = nullptr;
+  if (M < 1 || !n_per_world || !model_per_world || !valid_enums(SIM_FIRST_PRINCIPLES, integrator) ||
+      !(dt > 0.f) || !isfinite(dt))
+    return SIM_EINVAL;
+  int64_t tot = 0;
+  for (int64_t w = 0; w < M; ++w) {
+    if (n_per_world[w] < 1 || !valid_enums(model_per_world[w], integrator)) return SIM_EINVAL;
+    tot += n_per_world[w];
+    if (tot > 0x7fffffffLL) return SIM_EINVAL;
+  }
+  sim_s* h = new (std::nothrow) sim_s();
+  if (!h) return SIM_ENOMEM;
+  h->M = M;
+  h->N = 0;
+  h->ntot = tot;
+  h->batched = true;
+  h->integrator = integrator;
+  h->dt = dt;
+  h->n_per_world.assign(n_per_world, n_per_world + M);
+  h->model_of_world.assign(model_per_world, model_per_world + M);
+  h->offset.resize(M + 1);
+  h->offset[0] = 0;
+  for (int64_t w = 0; w < M; ++w) h->offset[w + 1] = h->offset[w] + n_per_world[w];
+  *out = h;
+  return SIM_OK;
+}
+
+int sim_set_control(sim_h h, int ctrl) {
+  if (!h) return SIM_EINVAL;
+  if (ctrl != SIM_CTRL_ROTOR_SPEED && ctrl != SIM_CTRL_ATTITUDE && ctrl != SIM_CTRL_POSITION)
+    return fail(h, SIM_EINVAL, "unknown control interface %d", ctrl);
+  bool any_abs = h->batched ? false : h->model == SIM_ABSTRACTED;
+  for (int32_t m : h->model_of_world) any_abs |= (m == SIM_ABSTRACTED);
+  if (any_abs && ctrl != SIM_CTRL_ATTITUDE)
+    return fail(h, SIM_EINVAL, "the abstracted model takes attitude commands only");
+  h->ctrl = ctrl;
+  return SIM_OK;
+}
+
+int sim_workspace_bytes(sim_h h, int64_t max_cmd_blocks, size_t* bytes) {
+  if (!h || !bytes || max_cmd_blocks < 1) return h ? fail(h, SIM_EINVAL, "bad arguments") : SIM_EINVAL;
+  *bytes = layout_of(h, max_cmd_blocks).total;
+  return SIM_OK;
+}
+
+int sim_bind(sim_h h, void* workspace, size_t bytes, int64_t max_cmd_blocks, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!workspace || max_cmd_blocks < 1 || ((uintptr_t)workspace & 255))
+    return fail(h, SIM_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  const Layout L = layout_of(h, max_cmd_blocks);
+  if (bytes < L.total)
+    return fail(h, SIM_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", bytes,
+                L.total);
+  char* ws = (char*)workspace;
+  h->ws = ws;
+  h->ws_bytes = bytes;
+  h->max_blocks = max_cmd_blocks;
+  h->planes = (float4*)(ws + L.planes);
+  h->params_dev = (DevParams*)(ws + L.params);
+  h->set_of_world_dev = (int32_t*)(ws + L.set_of_world);
+  h->cmd = (float4*)(ws + L.cmd);
+  h->staging = (float4*)(ws + L.staging);
+  h->status = (uint32_t*)(ws + L.status);
+  h->params_ok = h->state_ok = false;
+  h->n_blocks = 0;
+  h->t = 0;
+  cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(uint32_t), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "clearing the status word");
+  return SIM_OK;
+}
+
+int sim_set_params(sim_h h, const float* params, int64_t n_sets, const int32_t* set_of_world,
+                   void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!h->ws) return fail(h, SIM_ESTATE, "sim_bind must come first");
+  if (!params || n_sets < 1 || n_sets > h->M)
+    return fail(h, SIM_EINVAL, "need 1 <= n_sets <= M and a parameter array");
+  std::vector<DevParams> dp((size_t)n_sets);
+  char why[128];
+  for (int64_t s = 0; s < n_sets; ++s) {
+    if (derive_params(params + s * SIM_NPARAMS, &dp[(size_t)s], why, sizeof(why)) != SIM_OK)
+      return fail(h, SIM_EINVAL, "parameter set %lld: %s", (long long)s, why);
+  }
+  std::vector<int32_t> sow((size_t)h->M, 0);
+  bool uniform = true;
+  if (set_of_world) {
+    for (int64_t w = 0; w < h->M; ++w) {
+      if (set_of_world[w] < 0 || set_of_world[w] >= n_sets)
+        return fail(h, SIM_EINVAL, "set_of_world[%lld] = %d out of range", (long long)w,
+                    set_of_world[w]);
+      sow[(size_t)w] = set_of_world[w];
+      uniform &= (set_of_world[w] == set_of_world[0]);
+    }
+  }
+  int flags = 0;
+  for (const DevParams& d : dp) flags |= d.flags;
+  h->params_host = dp;
+  h->set_of_world_host = sow;
+  h->per_set = !uniform;
+  h->general_motor = (flags & cf::PF_GENERAL_MOTOR) != 0;
+  // every set carries the union of the flags so one kernel variant serves all
+  for (DevParams& d : h->params_host) d.flags = flags;
+  h->p0 = h->params_host[(size_t)sow[0]];
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(h->params_dev, h->params_host.data(),
+                                  h->params_host.size() * sizeof(DevParams),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->set_of_world_dev, h->set_of_world_host.data(),
+                        h->set_of_world_host.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "uploading parameters");
+  h->params_ok = true;
+  return SIM_OK;
+}
+
+int sim_set_state(sim_h h, const float* x, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!h->ws) return fail(h, SIM_ESTATE, "sim_bind must come first");
+  if (!x || ((uintptr_t)x & 15)) return fail(h, SIM_EINVAL, "state pointer must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  const float4* rows = (const float4*)x;
+  cudaError_t e;
+  if (!is_device_pointer(x)) {
+    e = cudaMemcpyAsync(h->staging, x, (size_t)h->ntot * SIM_STATE_DIM * sizeof(float),
+                        cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copying the state to the device");
+    rows = h->staging;
+  }
+  e = cf::launch_rows_to_planes(rows, h->planes, (int)h->ntot, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "rows_to_planes launch");
+  h->launches++;
+  h->state_ok = true;
+  return SIM_OK;
+}
+
+int sim_get_state(sim_h h, float* x, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!h->ws || !h->state_ok) return fail(h, SIM_ESTATE, "no state has been set");
+  if (!x || ((uintptr_t)x & 15)) return fail(h, SIM_EINVAL, "state pointer must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dev = is_device_pointer(x);
+  float4* rows = dev ? (float4*)x : h->staging;
+  cudaError_t e = cf::launch_planes_to_rows(h->planes, rows, (int)h->ntot, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "planes_to_rows launch");
+  h->launches++;
+  if (!dev) {
+    e = cudaMemcpyAsync(x, h->staging, (size_t)h->ntot * SIM_STATE_DIM * sizeof(float),
+                        cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copying the state to the host");
+  }
+  return SIM_OK;
+}
+
+int sim_set_commands(sim_h h, const float* cmd, int64_t n_blocks, int hold, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!h->ws) return fail(h, SIM_ESTATE, "sim_bind must come first");
+  if (!cmd || n_blocks < 1 || n_blocks > h->max_blocks || hold < 1 ||
+      n_blocks * (int64_t)hold > 0x7fffffffLL)
+    return fail(h, SIM_EINVAL, "need a command array, 1 <= n_blocks <= %lld, hold >= 1",
+                (long long)h->max_blocks);
+  cudaError_t e = cudaMemcpyAsync(h->cmd, cmd, (size_t)n_blocks * h->ntot * sizeof(float4),
+                                  cudaMemcpyDefault, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "copying commands");
+  h->n_blocks = n_blocks;
+  h->hold = hold;
+  h->t = 0;
+  return SIM_OK;
+}
+
+int sim_set_block_size(sim_h h, int tpb) {
+  if (!h) return SIM_EINVAL;
+  if (tpb < 32 || tpb > 256 || (tpb & 31)) return fail(h, SIM_EINVAL, "bad block size %d", tpb);
+  h->tpb = tpb;
+  return SIM_OK;
+}
+
+int sim_step(sim_h h, int K, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (K < 1 || K > 100000) return fail(h, SIM_EINVAL, "K = %d outside [1, 100000]", K);
+  if (!h->ws || !h->params_ok || !h->state_ok || h->n_blocks < 1)
+    return fail(h, SIM_ESTATE, "bind, parameters, state and commands must be set before stepping");
+  if (h->batched) return fail(h, SIM_EINVAL, "uneven batches step through sim_step_batched");
+  cf::StepArgs a;
+  a.planes = h->planes;
+  a.cmd = h->cmd;
+  a.params = h->params_dev;
+  a.set_of_world = h->set_of_world_dev;
+  a.status = h->status;
+  a.n = (int)h->ntot;
+  a.N = (int)h->N;
+  a.n_blocks = (int)h->n_blocks;
+  a.hold = h->hold;
+  const int64_t tmax = (h->n_blocks - 1) * (int64_t)h->hold;
+  a.t0 = (int)(h->t < tmax ? h->t : tmax);
+  a.K = K;
+  a.dt = h->dt;
+  cudaError_t e = cf::launch_step(a, h->p0, h->model, h->integrator, h->ctrl,
+                                  h->general_motor, h->per_set, h->tpb, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+  h->launches++;
+  h->t += K;
+  return SIM_OK;
+}
+
+int sim_run(sim_h h, int64_t n_steps, int K, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (n_steps < 0 || K < 1) return fail(h, SIM_EINVAL, "need n_steps >= 0 and K >= 1");
+  while (n_steps > 0) {
+    const int k = (int)(n_steps < K ? n_steps : K);
+    const int r = sim_step(h, k, stream);
+    if (r != SIM_OK) return r;
+    n_steps -= k;
+  }
+  return SIM_OK;
+}
+
+int sim_status(sim_h h, uint32_t* flags, void* stream) {
+  if (!h || !flags) return h ? fail(h, SIM_EINVAL, "flags is NULL") : SIM_EINVAL;
+  if (!h->ws) return fail(h, SIM_ESTATE, "sim_bind must come first");
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t v = 0;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(&v, h->status, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "reading the status word");
+  *flags = v;
+  return SIM_OK;
+}
+
+int64_t sim_num_drones(sim_h h) { return h ? h->ntot : -1; }
+int64_t sim_step_count(sim_h h) { return h ? h->t : -1; }
+int64_t sim_launch_count(sim_h h) { return h ? h->launches : -1; }
+const char* sim_last_error(sim_h h) { return h ? h->err : "NULL handle"; }
+void sim_destroy(sim_h h) { delete h; }
+
+}  // extern "C"

@@ -1,0 +1,214 @@
+// Fused K-step forward kernel: one drone per thread, the 20-float state held in
+// registers for all K steps, one coalesced float4-plane read and write per
+// launch (the paper's fused step pipeline scanned over steps, Architecture
+// section).
+#include "internal.h"
+#include "physics.cuh"
+
+namespace cf {
+
+// Controller state held between command-block changes.
+struct CtrlHold {
+  float Rd[9];
+  float Td;
+  float Wc[4];       // rotor-speed interface: clipped commands
+  float4 sp;         // position interface: setpoint
+  float syaw, cyaw;  // position interface: yaw sine/cosine
+  float u[4];        // abstracted model input
+};
+
+template <int MODEL, int CTRL>
+__device__ __forceinline__ void decode_command(float4 c, const DevParams& P, CtrlHold& h) {
+  if constexpr (MODEL == SIM_ABSTRACTED) {
+    abstracted_command(c, P, h.u);
+  } else if constexpr (CTRL == SIM_CTRL_ATTITUDE) {
+    attitude_command(c, P, h.Rd, h.Td);
+  } else if constexpr (CTRL == SIM_CTRL_POSITION) {
+    h.sp = c;
+    __sincosf(c.w, &h.syaw, &h.cyaw);
+  } else {
+    h.Wc[0] = clampf(c.x, 0.f, P.omega_max);
+    h.Wc[1] = clampf(c.y, 0.f, P.omega_max);
+    h.Wc[2] = clampf(c.z, 0.f, P.omega_max);
+    h.Wc[3] = clampf(c.w, 0.f, P.omega_max);
+  }
+}
+
+template <int MODEL, int INTEG, int CTRL, int MOTOR>
+__device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevParams& P, bool drag,
+                                         float dt) {
+  constexpr int D = (MODEL == SIM_FIRST_PRINCIPLES) ? 17 : 13;
+  float Wc[4];
+  float ep[3] = {0.f, 0.f, 0.f};
+  if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
+    if constexpr (CTRL == SIM_CTRL_ROTOR_SPEED) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) Wc[r] = h.Wc[r];
+    } else {
+      float R[9];
+      quat_rot(s[3], s[4], s[5], s[6], R);
+      float tx, ty, tz;
+      if constexpr (CTRL == SIM_CTRL_POSITION) {
+        float Rd[9], Td;
+        position_command(s, R, h.sp, h.syaw, h.cyaw, P, Rd, Td, ep);
+        attitude_torque(R, Rd, s[10], s[11], s[12], P, tx, ty, tz);
+        mixer(Td, tx, ty, tz, P, Wc);
+      } else {
+        attitude_torque(R, h.Rd, s[10], s[11], s[12], P, tx, ty, tz);
+        mixer(h.Td, tx, ty, tz, P, Wc);
+      }
+    }
+  }
+  auto deriv = [&](const float* x, float* d) {
+    if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
+      deriv_fp<MOTOR>(x, Wc, P, drag, d);
+    } else {
+      deriv_abs(x, h.u, P, drag, d);
+    }
+  };
+  if constexpr (INTEG == SIM_EULER) {
+    float d[D];
+    deriv(s, d);
+#pragma unroll
+    for (int j = 0; j < D; ++j) s[j] = fmaf(dt, d[j], s[j]);
+  } else {
+    float k[D], acc[D], xs[D];
+    const float h2 = 0.5f * dt, h6 = dt * (1.f / 6.f);
+    deriv(s, k);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      acc[j] = k[j];
+      xs[j] = fmaf(h2, k[j], s[j]);
+    }
+    deriv(xs, k);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      acc[j] = fmaf(2.f, k[j], acc[j]);
+      xs[j] = fmaf(h2, k[j], s[j]);
+    }
+    deriv(xs, k);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      acc[j] = fmaf(2.f, k[j], acc[j]);
+      xs[j] = fmaf(dt, k[j], s[j]);
+    }
+    deriv(xs, k);
+#pragma unroll
+    for (int j = 0; j < D; ++j) s[j] = fmaf(h6, acc[j] + k[j], s[j]);
+  }
+  if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
+    const float in = rsqrt_approx(fmaf(s[3], s[3], fmaf(s[4], s[4], fmaf(s[5], s[5], s[6] * s[6]))));
+    s[3] *= in;
+    s[4] *= in;
+    s[5] *= in;
+    s[6] *= in;
+    if constexpr (CTRL == SIM_CTRL_POSITION) {
+      s[17] = fmaf(dt, ep[0], s[17]);
+      s[18] = fmaf(dt, ep[1], s[18]);
+      s[19] = fmaf(dt, ep[2], s[19]);
+    }
+  }
+}
+
+template <int MODEL, int INTEG, int CTRL, int MOTOR>
+__device__ __forceinline__ void run_drone(const StepArgs& a, int i, const DevParams& P) {
+  constexpr int NPL = (MODEL == SIM_FIRST_PRINCIPLES) ? 5 : 4;
+  const int n = a.n;
+  float s[20];
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    const float4 v = a.planes[(size_t)j * n + i];
+    s[4 * j + 0] = v.x;
+    s[4 * j + 1] = v.y;
+    s[4 * j + 2] = v.z;
+    s[4 * j + 3] = v.w;
+  }
+  const bool drag = (P.flags & PF_DRAG) != 0;
+  const int last = a.n_blocks - 1;
+  int blk = min(a.t0 / a.hold, last);
+  int left = (a.t0 / a.hold >= last) ? 0x7fffffff : a.hold - a.t0 % a.hold;
+  CtrlHold h;
+  decode_command<MODEL, CTRL>(a.cmd[(size_t)blk * n + i], P, h);
+  float4 next = a.cmd[(size_t)min(blk + 1, last) * n + i];
+  for (int k = 0; k < a.K; ++k) {
+    if (left == 0) {
+      ++blk;
+      decode_command<MODEL, CTRL>(next, P, h);
+      left = (blk >= last) ? 0x7fffffff : a.hold;
+      next = a.cmd[(size_t)min(blk + 1, last) * n + i];
+    }
+    --left;
+    one_step<MODEL, INTEG, CTRL, MOTOR>(s, h, P, drag, a.dt);
+  }
+  float chk = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4 * NPL; ++j) chk += s[j];
+  if (!isfinite(chk)) atomicOr(a.status, SIM_FLAG_NONFINITE);
+#pragma unroll
+  for (int j = 0; j < NPL; ++j)
+    a.planes[(size_t)j * n + i] = make_float4(s[4 * j], s[4 * j + 1], s[4 * j + 2], s[4 * j + 3]);
+}
+
+template <int MODEL, int INTEG, int CTRL, int MOTOR, bool PERSET>
+__global__ void __launch_bounds__(256) step_kernel(StepArgs a, DevParams P0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  if constexpr (PERSET) {
+    const DevParams P = a.params[a.set_of_world[i / a.N]];
+    run_drone<MODEL, INTEG, CTRL, MOTOR>(a, i, P);
+  } else {
+    run_drone<MODEL, INTEG, CTRL, MOTOR>(a, i, P0);
+  }
+}
+
+template <int MODEL, int INTEG, int CTRL, int MOTOR, bool PERSET>
+static cudaError_t launch_t(const StepArgs& a, const DevParams& P, int tpb, cudaStream_t st) {
+  const int grid = (a.n + tpb - 1) / tpb;
+  step_kernel<MODEL, INTEG, CTRL, MOTOR, PERSET><<<grid, tpb, 0, st>>>(a, P);
+  return cudaGetLastError();
+}
+
+template <int MODEL, int INTEG, int CTRL>
+static cudaError_t launch_m(const StepArgs& a, const DevParams& P, bool gm, bool perset, int tpb,
+                            cudaStream_t st) {
+  if (gm) {
+    return perset ? launch_t<MODEL, INTEG, CTRL, MOTOR_GENERAL, true>(a, P, tpb, st)
+                  : launch_t<MODEL, INTEG, CTRL, MOTOR_GENERAL, false>(a, P, tpb, st);
+  }
+  return perset ? launch_t<MODEL, INTEG, CTRL, MOTOR_LAG, true>(a, P, tpb, st)
+                : launch_t<MODEL, INTEG, CTRL, MOTOR_LAG, false>(a, P, tpb, st);
+}
+
+template <int MODEL, int INTEG>
+static cudaError_t launch_c(const StepArgs& a, const DevParams& P, int ctrl, bool gm, bool perset,
+                            int tpb, cudaStream_t st) {
+  if constexpr (MODEL == SIM_ABSTRACTED) {
+    // the abstracted model has no rotors: motor kind is irrelevant
+    return perset ? launch_t<MODEL, INTEG, SIM_CTRL_ATTITUDE, MOTOR_LAG, true>(a, P, tpb, st)
+                  : launch_t<MODEL, INTEG, SIM_CTRL_ATTITUDE, MOTOR_LAG, false>(a, P, tpb, st);
+  } else {
+    switch (ctrl) {
+      case SIM_CTRL_ROTOR_SPEED:
+        return launch_m<MODEL, INTEG, SIM_CTRL_ROTOR_SPEED>(a, P, gm, perset, tpb, st);
+      case SIM_CTRL_POSITION:
+        return launch_m<MODEL, INTEG, SIM_CTRL_POSITION>(a, P, gm, perset, tpb, st);
+      default:
+        return launch_m<MODEL, INTEG, SIM_CTRL_ATTITUDE>(a, P, gm, perset, tpb, st);
+    }
+  }
+}
+
+cudaError_t launch_step(const StepArgs& a, const DevParams& P, int model, int integrator, int ctrl,
+                        bool general_motor, bool per_set, int tpb, cudaStream_t st) {
+  if (model == SIM_FIRST_PRINCIPLES) {
+    return integrator == SIM_RK4
+               ? launch_c<SIM_FIRST_PRINCIPLES, SIM_RK4>(a, P, ctrl, general_motor, per_set, tpb, st)
+               : launch_c<SIM_FIRST_PRINCIPLES, SIM_EULER>(a, P, ctrl, general_motor, per_set, tpb,
+                                                           st);
+  }
+  return integrator == SIM_RK4
+             ? launch_c<SIM_ABSTRACTED, SIM_RK4>(a, P, ctrl, general_motor, per_set, tpb, st)
+             : launch_c<SIM_ABSTRACTED, SIM_EULER>(a, P, ctrl, general_motor, per_set, tpb, st);
+}
+
+}  // namespace cf

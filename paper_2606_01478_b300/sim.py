@@ -1,0 +1,146 @@
+"""Thin Python binding of the C-ABI: argument marshalling only.
+
+PyTorch supplies device memory (one uint8 workspace tensor per handle) and the
+stream; every step of the simulation runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def pack_params(params) -> np.ndarray:
+    """dict or list of dicts (names of ``PARAM_ORDER``) -> float32 [n_sets, 48]."""
+    if isinstance(params, dict):
+        params = [params]
+    out = np.zeros((len(params), L.NPARAMS), dtype=np.float32)
+    for s, p in enumerate(params):
+        for k, name in enumerate(L.PARAM_ORDER):
+            out[s, k] = p[name]
+    return out
+
+
+class Sim:
+    """One batch of drones bound to a device workspace.
+
+    Sim(M, N, model, integrator, dt) for uniform batches, or
+    Sim.batched(n_per_world, model_per_world, integrator, dt)."""
+
+    def __init__(self, M=None, N=None, model=L.FIRST_PRINCIPLES, integrator=L.EULER, dt=1 / 500,
+                 ctrl=L.CTRL_ATTITUDE, max_cmd_blocks=1, device="cuda", _handle=None):
+        self.lib = L.load()
+        self.device = torch.device(device)
+        h = ctypes.c_void_p()
+        if _handle is None:
+            self._check_create(self.lib.sim_create(ctypes.byref(h), int(M), int(N), int(model),
+                                                   int(integrator), float(dt)))
+        else:
+            h = _handle
+        self.h = h
+        self.ntot = int(self.lib.sim_num_drones(h))
+        self._check(self.lib.sim_set_control(h, int(ctrl)))
+        self.max_cmd_blocks = int(max_cmd_blocks)
+        nbytes = ctypes.c_size_t()
+        self._check(self.lib.sim_workspace_bytes(h, self.max_cmd_blocks, ctypes.byref(nbytes)))
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        self._check(self.lib.sim_bind(h, ctypes.c_void_p(self.workspace.data_ptr()), nbytes.value,
+                                      self.max_cmd_blocks, _stream_ptr(None)))
+
+    @classmethod
+    def batched(cls, n_per_world, model_per_world, integrator=L.EULER, dt=1 / 500,
+                ctrl=L.CTRL_ATTITUDE, max_cmd_blocks=1, device="cuda"):
+        lib = L.load()
+        n = np.ascontiguousarray(n_per_world, dtype=np.int64)
+        m = np.ascontiguousarray(model_per_world, dtype=np.int32)
+        if n.shape != m.shape:
+            raise ValueError("n_per_world and model_per_world differ in length")
+        h = ctypes.c_void_p()
+        r = lib.sim_create_batched(ctypes.byref(h), len(n),
+                                   n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                   m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   int(integrator), float(dt))
+        if r != L.SIM_OK:
+            raise L.SimError(r, "sim_create_batched rejected its arguments")
+        return cls(ctrl=ctrl, max_cmd_blocks=max_cmd_blocks, device=device, _handle=h)
+
+    # ------------------------------------------------------------------ helpers
+    def _check_create(self, r):
+        if r != L.SIM_OK:
+            raise L.SimError(r, "sim_create rejected its arguments")
+
+    def _check(self, r):
+        if r != L.SIM_OK:
+            raise L.SimError(r, self.lib.sim_last_error(self.h).decode())
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            self.lib.sim_destroy(h)
+            self.h = None
+
+    # ------------------------------------------------------------------ API
+    def set_params(self, params, set_of_world=None, stream=None):
+        arr = pack_params(params)
+        sow = None
+        if set_of_world is not None:
+            sow = np.ascontiguousarray(set_of_world, dtype=np.int32)
+        self._check(self.lib.sim_set_params(
+            self.h, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), arr.shape[0],
+            None if sow is None else sow.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+            _stream_ptr(stream)))
+        self._keep = (arr, sow)
+
+    def set_state(self, x: torch.Tensor, stream=None):
+        if x.dtype != torch.float32 or not x.is_contiguous() or tuple(x.shape) != (self.ntot, L.STATE_DIM):
+            raise ValueError(f"state must be contiguous float32 [{self.ntot}, {L.STATE_DIM}]")
+        self._check(self.lib.sim_set_state(self.h, ctypes.c_void_p(x.data_ptr()), _stream_ptr(stream)))
+        self._state_src = x
+
+    def get_state(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.ntot, L.STATE_DIM, dtype=torch.float32, device=self.device)
+        if out.dtype != torch.float32 or not out.is_contiguous() or tuple(out.shape) != (self.ntot, L.STATE_DIM):
+            raise ValueError("bad output tensor")
+        self._check(self.lib.sim_get_state(self.h, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def set_commands(self, cmd: torch.Tensor, hold: int, stream=None):
+        if cmd.dim() == 2:
+            cmd = cmd[None]
+        if cmd.dtype != torch.float32 or not cmd.is_contiguous() or cmd.shape[1:] != (self.ntot, L.CMD_DIM):
+            raise ValueError(f"commands must be contiguous float32 [n_blocks, {self.ntot}, 4]")
+        self._check(self.lib.sim_set_commands(self.h, ctypes.c_void_p(cmd.data_ptr()), cmd.shape[0],
+                                              int(hold), _stream_ptr(stream)))
+        self._cmd_src = cmd
+
+    def set_block_size(self, tpb: int):
+        self._check(self.lib.sim_set_block_size(self.h, int(tpb)))
+
+    def step(self, K: int = 1, stream=None):
+        self._check(self.lib.sim_step(self.h, int(K), _stream_ptr(stream)))
+
+    def run(self, n_steps: int, K: int, stream=None):
+        self._check(self.lib.sim_run(self.h, int(n_steps), int(K), _stream_ptr(stream)))
+
+    def status(self, stream=None) -> int:
+        v = ctypes.c_uint32()
+        self._check(self.lib.sim_status(self.h, ctypes.byref(v), _stream_ptr(stream)))
+        return v.value
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.sim_launch_count(self.h))
+
+    @property
+    def steps_taken(self) -> int:
+        return int(self.lib.sim_step_count(self.h))

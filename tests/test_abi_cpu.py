@@ -1,0 +1,114 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+include/*.h declares, and validates arguments on the host (no call here
+reaches a CUDA API)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import workloads as W
+from paper_2606_01478_b300 import _lib as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(hdr).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if not n.startswith(("defined",))))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return L.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert len(declared) >= 18
+    for name in declared:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert set(L.declared_symbols()) <= set(declared)
+
+
+def test_param_order_matches_header():
+    src = open(os.path.join(ROOT, "include", "crazyflow.h")).read()
+    body = src[src.index("enum sim_param_index"):]
+    body = body[body.index("{") + 1:body.index("SIM_P_COUNT")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = [t.strip().split("=")[0].strip() for t in body.split(",") if t.strip()]
+    assert len(names) == len(L.PARAM_ORDER) == 44
+    for hname, pname in zip(names, L.PARAM_ORDER):
+        assert hname == "SIM_P_" + pname.upper()
+    assert tuple(W.PARAM_NAMES) == L.PARAM_ORDER
+
+
+def _create(lib, M, N, model=0, integ=0, dt=0.002):
+    h = ctypes.c_void_p()
+    r = lib.sim_create(ctypes.byref(h), M, N, model, integ, dt)
+    return r, h
+
+
+def test_create_validates_arguments(lib):
+    for args in [(0, 1), (1, 0), (-3, 2), (1 << 20, 1 << 12)]:
+        r, h = _create(lib, *args)
+        assert r == L.SIM_EINVAL and not h.value
+    assert _create(lib, 4, 4, model=7)[0] == L.SIM_EINVAL
+    assert _create(lib, 4, 4, integ=2)[0] == L.SIM_EINVAL
+    assert _create(lib, 4, 4, dt=0.0)[0] == L.SIM_EINVAL
+    assert _create(lib, 4, 4, dt=float("nan"))[0] == L.SIM_EINVAL
+    r, h = _create(lib, 3, 5)
+    assert r == L.SIM_OK and lib.sim_num_drones(h) == 15
+    lib.sim_destroy(h)
+
+
+def test_create_batched_validates(lib):
+    h = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 3)(4, 0, 2)
+    m = (ctypes.c_int32 * 3)(0, 1, 0)
+    assert lib.sim_create_batched(ctypes.byref(h), 3, n, m, 0, 0.002) == L.SIM_EINVAL
+    n = (ctypes.c_int64 * 3)(4, 7, 2)
+    m = (ctypes.c_int32 * 3)(0, 5, 0)
+    assert lib.sim_create_batched(ctypes.byref(h), 3, n, m, 0, 0.002) == L.SIM_EINVAL
+    m = (ctypes.c_int32 * 3)(0, 1, 0)
+    assert lib.sim_create_batched(ctypes.byref(h), 3, n, m, 1, 0.002) == L.SIM_OK
+    assert lib.sim_num_drones(h) == 13
+    # abstracted drones accept attitude commands only
+    assert lib.sim_set_control(h, L.CTRL_POSITION) == L.SIM_EINVAL
+    assert b"attitude" in lib.sim_last_error(h)
+    assert lib.sim_set_control(h, L.CTRL_ATTITUDE) == L.SIM_OK
+    lib.sim_destroy(h)
+
+
+def test_workspace_size_and_call_order(lib):
+    r, h = _create(lib, 10, 3)
+    nb = ctypes.c_size_t()
+    assert lib.sim_workspace_bytes(h, 4, ctypes.byref(nb)) == L.SIM_OK
+    # planes + 4 command blocks + staging dominate: 30*(80 + 64 + 80) bytes
+    assert nb.value >= 30 * (80 + 4 * 16 + 80)
+    assert nb.value % 256 == 0
+    assert lib.sim_workspace_bytes(h, 0, ctypes.byref(nb)) == L.SIM_EINVAL
+    # nothing may run before a workspace is bound
+    assert lib.sim_step(h, 1, None) == L.SIM_ESTATE
+    assert lib.sim_set_commands(h, ctypes.c_void_p(16), 1, 1, None) == L.SIM_ESTATE
+    assert lib.sim_step(h, 0, None) == L.SIM_EINVAL
+    assert lib.sim_set_block_size(h, 48) == L.SIM_EINVAL
+    assert lib.sim_set_block_size(h, 512) == L.SIM_EINVAL
+    assert lib.sim_set_block_size(h, 64) == L.SIM_OK
+    assert lib.sim_set_control(h, 9) == L.SIM_EINVAL
+    # a misaligned workspace is refused before any CUDA call
+    assert lib.sim_bind(h, ctypes.c_void_p(0x1000 + 8), 1 << 20, 1, None) == L.SIM_EINVAL
+    assert lib.sim_bind(h, ctypes.c_void_p(0x1000), 16, 1, None) == L.SIM_ENOMEM
+    lib.sim_destroy(h)
+
+
+def test_null_handle_is_rejected(lib):
+    assert lib.sim_step(None, 1, None) == L.SIM_EINVAL
+    assert lib.sim_num_drones(None) == -1
+    assert lib.sim_last_error(None) == b"NULL handle"
+    lib.sim_destroy(None)

@@ -1,0 +1,205 @@
+"""GPU parity of the fused forward step against the FP64 oracle (through the
+C-ABI), plus properties that hold at any size (fused K == repeated K = 1,
+determinism, layout round trip, non-finite detection)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import physics as ph
+from paper_2606_01478_b300 import Sim
+from paper_2606_01478_b300 import _lib as L
+
+from gpu_util import assert_parity, make_sim
+
+pytestmark = pytest.mark.gpu
+
+
+def _models_of(wl, drones=None):
+    n = wl.M * wl.N
+    idx = np.arange(n) if drones is None else np.asarray(drones)
+    return np.asarray(wl.model_of_world)[idx // wl.N]
+
+
+def _run_gpu(wl, steps=None, K=None, tpb=None):
+    sim = make_sim(wl, tpb=tpb)
+    sim.run(wl.steps if steps is None else steps, K or wl.K)
+    out = sim.get_state().cpu().numpy()
+    assert sim.status() == 0
+    return out, sim
+
+
+def test_config0_position_error_below_1e4_m():
+    """1 world x 1 drone, position PID, Euler at 500 Hz, 1000 steps in ONE
+    launch: |p_GPU - p_FP64| <= 1e-4 m (the stated bar)."""
+    wl = W.config0()
+    gpu, sim = _run_gpu(wl)
+    assert sim.launches >= 1
+    ref = ph.rollout_workload(wl).numpy()
+    errs = assert_parity(gpu, ref, _models_of(wl))
+    assert np.abs(gpu[0, 0:3] - ref[0, 0:3]).max() <= 1e-4, errs
+
+
+@pytest.mark.parametrize("tpb", [32, 128, 256])
+def test_config1_small_rk4_attitude(tpb):
+    """Config-1 recipe at 1000 drones (ragged tail for every block size),
+    RK4, 250 steps as launches of K = 100 (command blocks of 50 change inside
+    and across launches)."""
+    wl = W.config1(M=1000, steps=250, K=100)
+    gpu, _ = _run_gpu(wl, tpb=tpb)
+    ref = ph.rollout_workload(wl).numpy()
+    assert_parity(gpu, ref, _models_of(wl))
+
+
+@pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
+@pytest.mark.parametrize("ctrl", [ph.CTRL_ROTOR_SPEED, ph.CTRL_ATTITUDE, ph.CTRL_POSITION])
+def test_first_principles_all_controls(integrator, ctrl):
+    wl = W.config1(M=333, steps=120, K=37)
+    wl.integrator, wl.ctrl = integrator, ctrl
+    rng = np.random.default_rng(5)
+    if ctrl == ph.CTRL_ROTOR_SPEED:
+        wl.cmd = rng.uniform(9000, 19000, wl.cmd.shape)
+    elif ctrl == ph.CTRL_POSITION:
+        wl.cmd = np.concatenate([rng.uniform(-1, 1, wl.cmd.shape[:2] + (2,)),
+                                 rng.uniform(0.5, 1.5, wl.cmd.shape[:2] + (1,)),
+                                 rng.uniform(-0.5, 0.5, wl.cmd.shape[:2] + (1,))], -1)
+        wl.x0[:, 17:20] = rng.uniform(-0.05, 0.05, (wl.M, 3))
+    gpu, _ = _run_gpu(wl)
+    ref = ph.rollout_workload(wl).numpy()
+    assert_parity(gpu, ref, _models_of(wl))
+
+
+@pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
+def test_general_motor_and_drag(integrator):
+    """Asymmetric rotor coefficients with quadratic terms (Eq. 6 general form)
+    and non-zero body drag, per-world parameter sets."""
+    wl = W.config1(M=300, steps=100, K=50)
+    wl.integrator = integrator
+    rng = np.random.default_rng(8)
+    base = W.crazyflie_params(cv_up=40.0, cd_up=1e-3, cv_down=20.0, cd_down=5e-4,
+                              Ca_x=-0.01, Ca_y=-0.012, Ca_z=-0.02)
+    wl.params = [dict(base, mass=base["mass"] * s) for s in rng.uniform(0.95, 1.05, 5)]
+    wl.param_set_of_world = rng.integers(0, 5, wl.M).astype(np.int32)
+    gpu, _ = _run_gpu(wl)
+    ref = ph.rollout_workload(wl).numpy()
+    assert_parity(gpu, ref, _models_of(wl))
+
+
+@pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
+def test_abstracted_model_per_world_coefficients(integrator):
+    wl = W.config2(M=6, N=100, steps=150, K=64)
+    keep = wl.model_of_world == 1
+    # an all-abstracted uniform batch: take the odd worlds of the config-2 recipe
+    worlds = np.nonzero(keep)[0]
+    drones = (worlds[:, None] * wl.N + np.arange(wl.N)[None, :]).ravel()
+    wl.x0 = wl.x0[drones]
+    wl.cmd = wl.cmd[:, drones]
+    wl.params = [wl.params[w] for w in worlds]
+    wl.M = len(worlds)
+    wl.param_set_of_world = np.arange(wl.M, dtype=np.int32)
+    wl.model_of_world = np.ones(wl.M, np.int32)
+    wl.integrator = integrator
+    gpu, _ = _run_gpu(wl)
+    ref = ph.rollout_workload(wl).numpy()
+    assert_parity(gpu, ref, _models_of(wl))
+
+
+def test_config1_full_size_sampled():
+    """Config 1 at full size (16384 worlds, RK4, 1000 steps as 10 launches of
+    K = 100, the launch configuration the benchmark times); the oracle checks
+    a sample of 48 drones (exact, since drones do not interact)."""
+    wl = W.config1()
+    gpu, _ = _run_gpu(wl)
+    sample = np.random.default_rng(0).choice(wl.M, 48, replace=False)
+    ref = ph.rollout_workload(wl, drones=sample).numpy()
+    assert_parity(gpu[sample], ref, _models_of(wl, sample))
+
+
+def test_hover_fixed_point_on_gpu():
+    wl = W.config1(M=256, steps=1000, K=250)
+    P = wl.params[0]
+    wl.x0[:] = 0
+    wl.x0[:, 0:3] = np.random.default_rng(1).uniform(-1, 1, (256, 3))
+    wl.x0[:, 6] = 1.0
+    wl.x0[:, 13:17] = W.hover_rpm(P)
+    wl.cmd[:] = 0
+    gpu, _ = _run_gpu(wl)
+    x0 = wl.x0.astype(np.float32)
+    assert np.abs(gpu[:, 0:3] - x0[:, 0:3]).max() < 1e-5
+    assert np.abs(gpu[:, 7:13]).max() < 1e-5
+
+
+def test_fused_K_equals_single_steps():
+    """One launch of K steps and K launches of one step run the same float
+    operations: the states agree bit for bit."""
+    wl = W.config1(M=500, steps=60, K=60)
+    a, _ = _run_gpu(wl, K=60)
+    b, _ = _run_gpu(wl, K=1)
+    c, _ = _run_gpu(wl, K=7)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_deterministic_and_resumable():
+    wl = W.config1(M=700, steps=100, K=100)
+    a, _ = _run_gpu(wl)
+    b, _ = _run_gpu(wl)
+    assert np.array_equal(a, b)
+    # stop after 50 steps, read the state back, reload it into a fresh handle
+    sim = make_sim(wl)
+    sim.run(50, 50)
+    mid = sim.get_state()
+    sim2 = make_sim(wl)
+    sim2.set_state(mid)
+    sim2.set_commands(torch.tensor(wl.cmd[1:], dtype=torch.float32, device="cuda").contiguous(), 50)
+    sim2.run(50, 50)
+    assert np.array_equal(sim2.get_state().cpu().numpy(), a)
+
+
+def test_state_roundtrip_host_and_device():
+    wl = W.config1(M=1234, steps=1)
+    sim = make_sim(wl)
+    x = torch.tensor(wl.x0, dtype=torch.float32)
+    assert torch.equal(sim.get_state().cpu(), x)
+    host_out = torch.empty_like(x).pin_memory()
+    sim.get_state(out=host_out)
+    torch.cuda.synchronize()
+    assert torch.equal(host_out, x)
+    y = (x + 1.0).pin_memory()
+    sim.set_state(y)
+    torch.cuda.synchronize()
+    assert torch.equal(sim.get_state().cpu(), y)
+
+
+def test_nonfinite_state_sets_status_flag():
+    wl = W.config1(M=100, steps=5, K=5)
+    wl.x0[17, 7] = np.nan
+    sim = make_sim(wl)
+    sim.run(5, 5)
+    assert sim.status() & L.SIM_FLAG_NONFINITE
+    assert sim.status() == 0  # reading clears the word
+    wl2 = W.config1(M=100, steps=5, K=5)
+    sim2 = make_sim(wl2)
+    sim2.run(5, 5)
+    assert sim2.status() == 0
+
+
+def test_call_order_and_argument_errors():
+    sim = Sim(4, 4, ph.FIRST_PRINCIPLES, ph.EULER, 0.002)
+    with pytest.raises(L.SimError) as e:
+        sim.step(1)
+    assert e.value.code == L.SIM_ESTATE
+    sim.set_params(W.crazyflie_params())
+    with pytest.raises(L.SimError) as e:
+        sim.set_params(W.crazyflie_params(mass=-1.0))
+    assert e.value.code == L.SIM_EINVAL
+    with pytest.raises(L.SimError):
+        sim.set_params([W.crazyflie_params()] * 2, set_of_world=np.array([0, 1, 2, 0]))
+    x = torch.zeros(16, 20, dtype=torch.float32, device="cuda")
+    sim.set_state(x)
+    c = torch.zeros(2, 16, 4, device="cuda")
+    with pytest.raises(L.SimError) as e:
+        sim.set_commands(c, 10)  # only 1 block fits the workspace
+    assert e.value.code == L.SIM_EINVAL
+    sim.set_commands(c[:1].contiguous(), 10)
+    sim.step(3)
+    assert sim.steps_taken == 3
