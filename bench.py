@@ -267,6 +267,9 @@ def run_b300(args, wl):
     for it in range(args.steps):
         reset()
         flush.fill_(it & 0xFF)
+        # keep the device busy while the host enqueues the rollout, so the
+        # events time device execution and not host launch latency
+        torch.cuda._sleep(1_000_000)
         one_rollout(ev[it])
         torch.cuda.synchronize()
         per_iter_ms.append(ev[it][0][0].elapsed_time(ev[it][-1][1]))
