@@ -39,7 +39,11 @@ UNIT = "drone-steps/s"
 # formulation: controller 93 + 4 derivatives x 78 + RK4 combination 221 +
 # quaternion renormalisation 11 = 637 (command decode, amortised over 50-step
 # holds, adds ~1.2).
-FLOP_PER_DRONE_STEP = {("fp", "rk4", "attitude"): 637.0, ("fp", "euler", "attitude"): 216.0}
+FLOP_PER_DRONE_STEP = {("fp", "rk4", "attitude"): 637.0, ("fp", "euler", "attitude"): 216.0,
+                       ("abs", "euler", "attitude"): 58.0}
+# Algorithmic HBM bytes of one single-step launch per drone: state in + out
+# (first-principles 5 float4 planes, abstracted 4) + one float4 command.
+BYTES_PER_DRONE_STEP = {"fp": 80 + 80 + 16, "abs": 64 + 64 + 16}
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 
@@ -225,14 +229,21 @@ def run_b300(args, wl):
     sim = Sim(wl.M, wl.N, 0, wl.integrator, wl.dt, ctrl=wl.ctrl, max_cmd_blocks=wl.cmd.shape[0],
               device=dev)
     sim.set_params(wl.params, wl.param_set_of_world)
-    if args.tpb:
-        sim.set_block_size(args.tpb)
     x0_dev = torch.tensor(wl.x0, dtype=torch.float32, device=dev).contiguous()
     cmd_dev = torch.tensor(wl.cmd, dtype=torch.float32, device=dev).contiguous()
     x0_host = torch.tensor(wl.x0, dtype=torch.float32).pin_memory()
     cmd_host = torch.tensor(wl.cmd, dtype=torch.float32).pin_memory()
     out_host = torch.empty_like(x0_host).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    sim.set_state(x0_dev)
+    sim.set_commands(cmd_dev, wl.hold)
+    if args.tpb:
+        sim.set_block_size(args.tpb)
+        tuned = {"tpb": args.tpb, "K": wl.K, "source": "--tpb"}
+    else:
+        from paper_2606_01478_b300 import autotune
+        tuned = autotune.tune_step(sim, wl.steps, tag="config1", Ks=(wl.K,), reps=2)
+        tuned = {k: v for k, v in tuned.items() if k != "table"}
     n_launch = (wl.steps + wl.K - 1) // wl.K
 
     def one_rollout(events):
@@ -333,10 +344,77 @@ def run_b300(args, wl):
         "roofline": roof,
         "clocks": clocks,
     }
+    line["config"]["tpb"] = tuned["tpb"]
+    line["autotune"] = tuned
+    if not args.no_extra:
+        line["extra"] = {"config2": measure_config2(dev)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_config2(dev, reps: int = 3) -> dict:
+    """Config 2 (1000 worlds x 4000 drones, 50/50 first-principles / abstracted,
+    Euler, 200 steps) in both modes: one fused launch of K = 200 (FP32-issue
+    bound) and 200 launches of K = 1 (HBM bound)."""
+    from paper_2606_01478_b300 import Sim
+    from paper_2606_01478_b300 import autotune
+    wl = W.config2()
+    n = wl.M * wl.N
+    sim = Sim.batched(np.full(wl.M, wl.N), wl.model_of_world, wl.integrator, wl.dt, ctrl=wl.ctrl,
+                      max_cmd_blocks=wl.cmd.shape[0], device=dev)
+    sim.set_params(wl.params, wl.param_set_of_world)
+    x0 = torch.tensor(wl.x0, dtype=torch.float32, device=dev)
+    cmd = torch.tensor(wl.cmd, dtype=torch.float32, device=dev)
+    del wl.x0, wl.cmd
+    sim.set_state(x0)
+    sim.set_commands(cmd, wl.hold)
+    tuned = autotune.tune_step(sim, wl.steps, tag="config2", Ks=(1, 200), reps=1)
+    stream = torch.cuda.current_stream(dev)
+    n_fp = n // 2
+    n_abs = n - n_fp
+    out = {}
+    for K in (wl.steps, 1):
+        times = []
+        for r in range(reps + 1):
+            sim.set_state(x0)
+            sim.set_commands(cmd, wl.hold)
+            torch.cuda._sleep(1_000_000)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.run(wl.steps, K)
+            e1.record(stream)
+            e1.synchronize()
+            if r:
+                times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        units = n * wl.steps
+        rec = {"value": units / (ms / 1e3), "unit": UNIT, "ms": ms, "K": K,
+               "launches": (wl.steps + K - 1) // K, "tpb": tuned["tpb"]}
+        if K == 1:
+            byt = n_fp * BYTES_PER_DRONE_STEP["fp"] + n_abs * BYTES_PER_DRONE_STEP["abs"]
+            pk, kind = peaks()
+            achieved = byt * wl.steps / (ms / 1e3) / 1e9
+            rec["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                               "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                               "traffic": None, "bytes_per_launch": byt,
+                               "peak_basis": f"{kind} HBM copy bandwidth"}
+        else:
+            flop = (n_fp * FLOP_PER_DRONE_STEP[("fp", "euler", "attitude")]
+                    + n_abs * FLOP_PER_DRONE_STEP[("abs", "euler", "attitude")])
+            pk, kind = peaks()
+            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+            achieved = flop * wl.steps / (ms / 1e3) / 1e12
+            rec["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak,
+                               "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                               "note": "abstracted drones also issue 6 MUFU sin/cos per step"}
+        out[f"fused_K{K}" if K > 1 else "single_step_K1"] = rec
+    assert sim.status() == 0
+    out["workload"] = "c2_1000x4000_mixed_euler_attitude_200"
+    out["autotune"] = {k: v for k, v in tuned.items() if k != "table"}
+    return out
 
 
 def main(argv=None):
@@ -347,6 +425,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--tpb", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the config-2 measurements")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -164,6 +164,9 @@ int sim_status(sim_h h, uint32_t* flags, void* stream);
 
 int64_t sim_num_drones(sim_h h);     /* Ntot, or -1 for a NULL handle */
 int64_t sim_step_count(sim_h h);     /* steps taken since the last sim_set_commands */
+/* Set that step counter (it selects the command block of the next launch), e.g.
+ * to undo the advance made while capturing launches into a CUDA graph. */
+int sim_set_step_count(sim_h h, int64_t t);
 const char* sim_last_error(sim_h h); /* message of the last failure ("" if none) */
 void sim_destroy(sim_h h);           /* frees the host handle; the workspace stays the caller's */
 

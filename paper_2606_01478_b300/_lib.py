@@ -48,6 +48,7 @@ _SIGS = {
     "sim_status": (c_int, [c_void_p, POINTER(c_uint32), c_void_p]),
     "sim_num_drones": (c_int64, [c_void_p]),
     "sim_step_count": (c_int64, [c_void_p]),
+    "sim_set_step_count": (c_int, [c_void_p, c_int64]),
     "sim_launch_count": (c_int64, [c_void_p]),
     "sim_last_error": (c_char_p, [c_void_p]),
     "sim_destroy": (None, [c_void_p]),

@@ -11,6 +11,11 @@ namespace cf {
 cudaError_t launch_step(const StepArgs& a, const DevParams& P, int model, int integrator, int ctrl,
                         bool general_motor, bool per_set, int tpb, cudaStream_t st);
 
+// Uneven / mixed batches (step.cu): tiles [n_tiles] of (first drone, count <= 32,
+// world, model), one warp per tile, persistent grid.
+cudaError_t launch_step_batched(const StepArgs& a, const int4* tiles, int n_tiles, int integrator,
+                                int ctrl, bool general_motor, int tpb, cudaStream_t st);
+
 // Row-major [n][20] floats <-> 5 float4 planes [5][n] (layout.cu).
 cudaError_t launch_rows_to_planes(const float4* rows, float4* planes, int n, cudaStream_t st);
 cudaError_t launch_planes_to_rows(const float4* planes, float4* rows, int n, cudaStream_t st);

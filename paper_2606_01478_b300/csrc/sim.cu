@@ -24,6 +24,7 @@ struct sim_s {
   int tpb = 128;
   std::vector<int64_t> n_per_world, offset;
   std::vector<int32_t> model_of_world;
+  std::vector<int4> tiles;  // uneven batches: (first drone, count <= 32, world, model)
   // workspace (caller-owned device memory)
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -34,6 +35,7 @@ struct sim_s {
   float4* cmd = nullptr;
   float4* staging = nullptr;
   uint32_t* status = nullptr;
+  int4* tiles_dev = nullptr;
   // host copies
   std::vector<DevParams> params_host;
   DevParams p0;  // the single set of a uniform batch, passed by value
@@ -65,7 +67,7 @@ int cuda_fail(sim_h h, cudaError_t e, const char* what) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t planes, params, set_of_world, cmd, staging, status, total;
+  size_t planes, params, set_of_world, cmd, staging, status, tiles, total;
 };
 
 Layout layout_of(const sim_s* h, int64_t max_blocks) {
@@ -83,6 +85,8 @@ Layout layout_of(const sim_s* h, int64_t max_blocks) {
   off = align256(off + (size_t)h->ntot * SIM_STATE_DIM * sizeof(float));
   L.status = off;
   off = align256(off + sizeof(uint32_t));
+  L.tiles = off;
+  off = align256(off + h->tiles.size() * sizeof(int4));
   L.total = off;
   return L;
 }
@@ -231,6 +235,12 @@ int sim_create_batched(sim_h* out, int64_t M, const int64_t* n_per_world,
   h->offset.resize(M + 1);
   h->offset[0] = 0;
   for (int64_t w = 0; w < M; ++w) h->offset[w + 1] = h->offset[w] + n_per_world[w];
+  for (int64_t w = 0; w < M; ++w) {
+    for (int64_t s = 0; s < n_per_world[w]; s += 32) {
+      const int64_t c = n_per_world[w] - s < 32 ? n_per_world[w] - s : 32;
+      h->tiles.push_back(make_int4((int)(h->offset[w] + s), (int)c, (int)w, model_per_world[w]));
+    }
+  }
   *out = h;
   return SIM_OK;
 }
@@ -271,11 +281,15 @@ int sim_bind(sim_h h, void* workspace, size_t bytes, int64_t max_cmd_blocks, voi
   h->cmd = (float4*)(ws + L.cmd);
   h->staging = (float4*)(ws + L.staging);
   h->status = (uint32_t*)(ws + L.status);
+  h->tiles_dev = (int4*)(ws + L.tiles);
   h->params_ok = h->state_ok = false;
   h->n_blocks = 0;
   h->t = 0;
   cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(uint32_t), (cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "clearing the status word");
+  if (e == cudaSuccess && !h->tiles.empty())
+    e = cudaMemcpyAsync(h->tiles_dev, h->tiles.data(), h->tiles.size() * sizeof(int4),
+                        cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "initialising the workspace");
   return SIM_OK;
 }
 
@@ -389,7 +403,6 @@ int sim_step(sim_h h, int K, void* stream) {
   if (K < 1 || K > 100000) return fail(h, SIM_EINVAL, "K = %d outside [1, 100000]", K);
   if (!h->ws || !h->params_ok || !h->state_ok || h->n_blocks < 1)
     return fail(h, SIM_ESTATE, "bind, parameters, state and commands must be set before stepping");
-  if (h->batched) return fail(h, SIM_EINVAL, "uneven batches step through sim_step_batched");
   cf::StepArgs a;
   a.planes = h->planes;
   a.cmd = h->cmd;
@@ -404,8 +417,12 @@ int sim_step(sim_h h, int K, void* stream) {
   a.t0 = (int)(h->t < tmax ? h->t : tmax);
   a.K = K;
   a.dt = h->dt;
-  cudaError_t e = cf::launch_step(a, h->p0, h->model, h->integrator, h->ctrl,
-                                  h->general_motor, h->per_set, h->tpb, (cudaStream_t)stream);
+  cudaError_t e =
+      h->batched
+          ? cf::launch_step_batched(a, h->tiles_dev, (int)h->tiles.size(), h->integrator, h->ctrl,
+                                    h->general_motor, h->tpb, (cudaStream_t)stream)
+          : cf::launch_step(a, h->p0, h->model, h->integrator, h->ctrl, h->general_motor,
+                            h->per_set, h->tpb, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
   h->launches++;
   h->t += K;
@@ -440,6 +457,12 @@ int sim_status(sim_h h, uint32_t* flags, void* stream) {
 
 int64_t sim_num_drones(sim_h h) { return h ? h->ntot : -1; }
 int64_t sim_step_count(sim_h h) { return h ? h->t : -1; }
+int sim_set_step_count(sim_h h, int64_t t) {
+  if (!h) return SIM_EINVAL;
+  if (t < 0) return fail(h, SIM_EINVAL, "negative step count");
+  h->t = t;
+  return SIM_OK;
+}
 int64_t sim_launch_count(sim_h h) { return h ? h->launches : -1; }
 const char* sim_last_error(sim_h h) { return h ? h->err : "NULL handle"; }
 void sim_destroy(sim_h h) { delete h; }

@@ -161,6 +161,70 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a, DevParams P0) {
   }
 }
 
+// Uneven / mixed batches: warp w of the persistent grid takes tiles w, w + W,
+// w + 2W, ... (W = warps in the grid).  A tile is up to 32 consecutive drones of
+// one world (x = first drone, y = count, z = world, w = model), so the branch
+// on the model is uniform across the warp and parameters are a broadcast load.
+template <int INTEG, int CTRL, int MOTOR>
+__global__ void __launch_bounds__(256) step_batched_kernel(StepArgs a, const int4* __restrict__ tiles,
+                                                           int n_tiles) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = warp; t < n_tiles; t += nwarps) {
+    const int4 d = tiles[t];
+    if (lane < d.y) {
+      const DevParams P = a.params[a.set_of_world[d.z]];
+      if (d.w == SIM_FIRST_PRINCIPLES) {
+        run_drone<SIM_FIRST_PRINCIPLES, INTEG, CTRL, MOTOR>(a, d.x + lane, P);
+      } else {
+        run_drone<SIM_ABSTRACTED, INTEG, SIM_CTRL_ATTITUDE, MOTOR_LAG>(a, d.x + lane, P);
+      }
+    }
+  }
+}
+
+template <int INTEG, int CTRL, int MOTOR>
+static cudaError_t launch_b(const StepArgs& a, const int4* tiles, int n_tiles, int tpb,
+                            cudaStream_t st) {
+  // occupancy per (device, block size), queried once per kernel variant
+  static int cached[16][9] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int slot = tpb / 32;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = (dev < 16 && slot <= 8) ? cached[dev][slot] : 0;
+  if (per_sm == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_batched_kernel<INTEG, CTRL, MOTOR>,
+                                                  tpb, 0);
+    if (per_sm < 1) per_sm = 1;
+    if (dev < 16 && slot <= 8) cached[dev][slot] = per_sm;
+  }
+  const int warps_per_block = tpb / 32;
+  int grid = sms * per_sm;
+  const int need = (n_tiles + warps_per_block - 1) / warps_per_block;
+  if (grid > need) grid = need;
+  step_batched_kernel<INTEG, CTRL, MOTOR><<<grid, tpb, 0, st>>>(a, tiles, n_tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_batched(const StepArgs& a, const int4* tiles, int n_tiles, int integrator,
+                                int ctrl, bool general_motor, int tpb, cudaStream_t st) {
+#define CF_B(I, C)                                                              \
+  return general_motor ? launch_b<I, C, MOTOR_GENERAL>(a, tiles, n_tiles, tpb, st) \
+                       : launch_b<I, C, MOTOR_LAG>(a, tiles, n_tiles, tpb, st)
+  if (integrator == SIM_RK4) {
+    if (ctrl == SIM_CTRL_ROTOR_SPEED) CF_B(SIM_RK4, SIM_CTRL_ROTOR_SPEED);
+    if (ctrl == SIM_CTRL_POSITION) CF_B(SIM_RK4, SIM_CTRL_POSITION);
+    CF_B(SIM_RK4, SIM_CTRL_ATTITUDE);
+  }
+  if (ctrl == SIM_CTRL_ROTOR_SPEED) CF_B(SIM_EULER, SIM_CTRL_ROTOR_SPEED);
+  if (ctrl == SIM_CTRL_POSITION) CF_B(SIM_EULER, SIM_CTRL_POSITION);
+  CF_B(SIM_EULER, SIM_CTRL_ATTITUDE);
+#undef CF_B
+}
+
 template <int MODEL, int INTEG, int CTRL, int MOTOR, bool PERSET>
 static cudaError_t launch_t(const StepArgs& a, const DevParams& P, int tpb, cudaStream_t st) {
   const int grid = (a.n + tpb - 1) / tpb;

@@ -122,6 +122,7 @@ class Sim:
         self._check(self.lib.sim_set_commands(self.h, ctypes.c_void_p(cmd.data_ptr()), cmd.shape[0],
                                               int(hold), _stream_ptr(stream)))
         self._cmd_src = cmd
+        self._hold = int(hold)
 
     def set_block_size(self, tpb: int):
         self._check(self.lib.sim_set_block_size(self.h, int(tpb)))
@@ -131,6 +132,24 @@ class Sim:
 
     def run(self, n_steps: int, K: int, stream=None):
         self._check(self.lib.sim_run(self.h, int(n_steps), int(K), _stream_ptr(stream)))
+
+    def capture_run(self, n_steps: int, K: int) -> torch.cuda.CUDAGraph:
+        """Capture `n_steps` steps (launches of at most K) into a CUDA graph.
+
+        The step counter that selects command blocks is baked into the captured
+        launches: each replay re-runs steps t .. t + n_steps - 1 counted from
+        the command schedule's state at capture time (normally right after
+        set_commands), on whatever state the workspace holds."""
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        t0 = self.steps_taken
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.run(n_steps, K, stream=s)
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        self._check(self.lib.sim_set_step_count(self.h, t0))
+        return g
 
     def status(self, stream=None) -> int:
         v = ctypes.c_uint32()

@@ -1,0 +1,99 @@
+"""Pins of the policy-rollout oracle: float64 central finite differences of the
+loss (so the autograd gradient is checked against an independent numerical
+derivative), the zero-policy hover case and MLP structure."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import physics as ph
+from oracle import policy as po
+
+F64 = torch.float64
+
+
+def _small(M=6, H=30, seed=3):
+    return W.config3(seed=seed, M=M, H=H, C=10)
+
+
+def _loss(rw, x0, weights):
+    Wt = po.weights_tensors(weights)
+    L, _, _ = po.rollout_loss(torch.tensor(x0), Wt, rw.p_ref, rw.params, rw.dt, rw.H, rw.w_act)
+    return float(L)
+
+
+def test_gradient_matches_central_differences_weights():
+    rw = _small()
+    L, _, dW, _ = po.rollout_grad(rw.x0, rw.weights, rw.p_ref, rw.params, rw.dt, rw.H, rw.w_act)
+    flat = po.pack(rw.weights)
+    g = po.pack(dW)
+    rng = np.random.default_rng(0)
+    h = 1e-5
+    # individual coordinates of every tensor + random directions over all
+    idx = [0, 5, 12, 832 + 3, 896 + 100, 896 + 4095, 4992 + 7, 5056 + 200, 5312, 5315]
+    for i in idx:
+        e = np.zeros_like(flat)
+        e[i] = h
+        fd = (_loss(rw, rw.x0, po.unpack(flat + e)) - _loss(rw, rw.x0, po.unpack(flat - e))) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-9, (i, fd, g[i])
+    for _ in range(3):
+        d = rng.normal(size=flat.shape)
+        d /= np.linalg.norm(d)
+        fd = (_loss(rw, rw.x0, po.unpack(flat + h * d)) - _loss(rw, rw.x0, po.unpack(flat - h * d))) / (2 * h)
+        assert abs(fd - g @ d) <= 1e-6 * max(1.0, abs(g @ d))
+
+
+def test_gradient_matches_central_differences_initial_state():
+    rw = _small(M=4, H=25)
+    _, _, _, dx0 = po.rollout_grad(rw.x0, rw.weights, rw.p_ref, rw.params, rw.dt, rw.H, rw.w_act)
+    h = 1e-6
+    for (w, j) in [(0, 0), (1, 2), (2, 4), (3, 6), (0, 8), (1, 11), (2, 12), (3, 15)]:
+        xp, xm = rw.x0.copy(), rw.x0.copy()
+        scale = 1e4 if j >= 13 else 1.0  # rotor speeds are O(1e4) RPM
+        xp[w, j] += h * scale
+        xm[w, j] -= h * scale
+        fd = (_loss(rw, xp, rw.weights) - _loss(rw, xm, rw.weights)) / (2 * h * scale)
+        assert abs(fd - dx0[w, j]) <= 1e-6 * max(1.0, abs(dx0[w, j])) + 1e-10, (w, j, fd, dx0[w, j])
+    assert np.all(dx0[:, 17:20] == 0)
+
+
+def test_zero_policy_at_hover_has_closed_form_loss():
+    """All-zero weights give a = tanh(0) = 0: hover command, so a drone at hover
+    stays put; the loss is H |offset|^2 for a reference displaced by a constant
+    offset (and exactly 0 without offset), and the action term vanishes."""
+    rw = _small(M=3, H=40)
+    zero = {k: np.zeros(po.SIZES[k]) for k in po.NAMES}
+    x0 = np.zeros((3, 20))
+    x0[:, 0:3] = [[0.0, 0.0, 1.0], [0.3, -0.2, 1.5], [-1.0, 2.0, 0.5]]
+    x0[:, 6] = 1.0
+    x0[:, 13:17] = W.hover_rpm(rw.params)
+    ref = np.broadcast_to(x0[None, :, 0:3], (rw.H + 1, 3, 3)).copy()
+    Wt = po.weights_tensors(zero)
+    L0, _, xf = po.rollout_loss(torch.tensor(x0), Wt, ref, rw.params, rw.dt, rw.H, rw.w_act)
+    assert float(L0) < 1e-20
+    assert np.abs(xf.numpy()[:, 0:13] - x0[:, 0:13]).max() < 1e-12
+    off = np.array([0.1, -0.2, 0.05])
+    L1, per, _ = po.rollout_loss(torch.tensor(x0), Wt, ref + off, rw.params, rw.dt, rw.H, rw.w_act)
+    np.testing.assert_allclose(per.numpy(), rw.H * (off ** 2).sum(), rtol=1e-12)
+
+
+def test_mlp_odd_symmetry_and_linear_limit():
+    rng = np.random.default_rng(4)
+    Wd = {k: rng.normal(0, 0.3, po.SIZES[k]) for k in po.NAMES}
+    for k in ("b1", "b2", "b3"):
+        Wd[k][:] = 0
+    Wt = po.weights_tensors(Wd)
+    obs = torch.tensor(rng.normal(size=(7, 13)))
+    assert torch.allclose(po.mlp(-obs, Wt), -po.mlp(obs, Wt), atol=0)
+    # tiny inputs: tanh is the identity to first order, so the MLP is the matrix product
+    eps = 1e-7
+    lin = obs @ (Wt["W3"] @ Wt["W2"] @ Wt["W1"]).T
+    assert torch.allclose(po.mlp(eps * obs, Wt) / eps, lin, rtol=1e-9, atol=1e-12)
+
+
+def test_policy_weights_are_bf16_values():
+    w = W.policy_weights(7)
+    for k in po.NAMES:
+        a = np.asarray(w[k], dtype=np.float32)
+        assert np.all((a.view(np.uint32) & 0xFFFF) == 0)
+        assert np.array_equal(a.astype(np.float64), w[k])

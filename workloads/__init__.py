@@ -343,3 +343,73 @@ def config4(seed: int = 1004, M: int = 512, S: int = 256, H: int = 50, n_max: in
     key = int(rng.integers(0, 2**63))
     return SamplingWorkload(f"c4_{M}w_uneven_S{S}_H{H}_rk4", M, n_w, S, H, 1.0 / 500, 0.2, key, P,
                             x0, goals, obs, 1000.0)
+
+
+@dataclass
+class BatchedWorkload:
+    """Uneven / mixed batch: world w holds n_per_world[w] drones of model
+    model_of_world[w]; drones are laid out world after world."""
+    name: str
+    n_per_world: np.ndarray     # [M] int64
+    model_of_world: np.ndarray  # [M] int32
+    integrator: int
+    ctrl: int
+    dt: float
+    steps: int
+    K: int
+    hold: int
+    params: list                # one parameter set per world
+    x0: np.ndarray              # [sum N, 20]
+    cmd: np.ndarray             # [n_blocks, sum N, 4]
+
+    @property
+    def M(self):
+        return len(self.n_per_world)
+
+    @property
+    def ntot(self):
+        return int(self.n_per_world.sum())
+
+    def world_of_drone(self):
+        return np.repeat(np.arange(self.M), self.n_per_world)
+
+
+def batched_workload(seed: int, n_per_world, model_of_world, integrator: int = 0,
+                     steps: int = 200, K: int = 200, hold: int = 50,
+                     jitter: float = 0.1) -> BatchedWorkload:
+    """Uneven/mixed batch with the config-2 recipe: first-principles worlds use
+    the Crazyflie set, abstracted worlds scale each abstracted coefficient by
+    U(1 - jitter, 1 + jitter); initial states and attitude commands as in
+    config 2 (commands per drone, held `hold` steps)."""
+    rng = np.random.default_rng(seed)
+    n_w = np.asarray(n_per_world, dtype=np.int64)
+    mw = np.asarray(model_of_world, dtype=np.int32)
+    base = crazyflie_params()
+    params = []
+    for m in mw:
+        q = dict(base)
+        if m == 1:
+            for k in ("c1_r", "c1_p", "c1_y", "c2_r", "c2_p", "c2_y", "c3_r", "c3_p", "c3_y",
+                      "c_tau", "c_f"):
+                q[k] = base[k] * rng.uniform(1 - jitter, 1 + jitter)
+        params.append(q)
+    n = int(n_w.sum())
+    pos = np.array([0.0, 0.0, 1.0]) + rng.uniform(-1, 1, (n, 3))
+    rpy = rng.uniform(-np.deg2rad(30), np.deg2rad(30), (n, 3))
+    vel = rng.uniform(-1, 1, (n, 3))
+    w = rng.uniform(-2, 2, (n, 3))
+    x0 = fp_state(pos, rpy, vel, w, np.full((n, 4), hover_rpm(base)))
+    is_abs = mw[np.repeat(np.arange(len(n_w)), n_w)] == 1
+    if is_abs.any():
+        x0[is_abs] = abs_state(pos[is_abs], rpy[is_abs], vel[is_abs],
+                               np.zeros((is_abs.sum(), 3)),
+                               np.full(is_abs.sum(), base["mass"] * base["g"]))
+    cmd = _attitude_commands(rng, (steps + hold - 1) // hold, n)
+    return BatchedWorkload(f"batched_{len(n_w)}w_{n}d", n_w, mw, integrator, 1, 1.0 / 500, steps,
+                           K, hold, params, x0, cmd)
+
+
+def log_uniform_counts(seed: int, M: int, n_max: int) -> np.ndarray:
+    """N_w = clamp(round(exp(U(0, ln n_max))), 1, n_max) (the sampling workload's recipe)."""
+    rng = np.random.default_rng(seed)
+    return np.clip(np.round(np.exp(rng.uniform(0.0, math.log(n_max), M))), 1, n_max).astype(np.int64)
