@@ -170,6 +170,46 @@ int sim_set_step_count(sim_h h, int64_t t);
 const char* sim_last_error(sim_h h); /* message of the last failure ("" if none) */
 void sim_destroy(sim_h h);           /* frees the host handle; the workspace stays the caller's */
 
+/* ---------------------------------------------------------------------------
+ * Differentiable policy rollout (backpropagation through time; Materials and
+ * Methods, Backpropagation Through Time).  For every drone of the handle,
+ * independently:
+ *   obs_k = [p_k - r_k, q_k, v_k, omega_k]                         (13)
+ *   a_k   = tanh(W3 tanh(W2 tanh(W1 obs_k + b1) + b2) + b3)        (4, attitude action)
+ *   x_{k+1} = one Euler step of the first-principles model under the attitude
+ *             interface with command a_k, k = 0 .. H-1
+ *   L = (1/Ntot) sum_drones sum_k |p_{k+1} - r_{k+1}|^2 + w_act |a_k|^2
+ * Requires a handle created with SIM_FIRST_PRINCIPLES and SIM_EULER, one
+ * parameter set with a first-order-lag rotor model (cv_up = cv_down, cd = 0)
+ * and zero drag.  The policy MLP runs on tensor cores with bf16 weights and
+ * fp32 accumulation.
+ *
+ * Device buffers (all caller-owned, 16-byte aligned):
+ *   x0    [Ntot][SIM_STATE_DIM] float   initial states (slots 17..19 ignored)
+ *   w     [SIM_POLICY_NPARAMS] bf16 bit patterns, packed row-major
+ *         W1[64][13] b1[64] W2[64][64] b2[64] W3[4][64] b3[4]
+ *   p_ref [H+1][Ntot][3] float          reference positions r_k
+ *   ws    rollout workspace of sim_rollout_workspace_bytes(h, H, C) bytes:
+ *         checkpoints every C steps, segment states, per-drone losses, dW partials
+ *   loss  [1] float; dL [1] float (upstream gradient, read on the device);
+ *   dW    [SIM_POLICY_NPARAMS] float = dL * dL/dw (in the packed order of w)
+ *   dx0   [Ntot][SIM_STATE_DIM] float = dL * dL/dx0 (slots 17..19 = 0)
+ * sim_rollout_fwd writes the loss and the checkpoints; sim_rollout_bwd must
+ * follow it with the same x0, w, p_ref, H, C, w_act and workspace.  Gradients
+ * are deterministic (fixed-order reductions).  1 <= C <= H.
+ */
+#define SIM_POLICY_NPARAMS 5316
+int sim_rollout_workspace_bytes(sim_h h, int H, int C, size_t* bytes);
+int sim_rollout_fwd(sim_h h, const float* x0, const uint16_t* w, const float* p_ref, int H, int C,
+                    float w_act, void* ws, size_t ws_bytes, float* loss, void* stream);
+int sim_rollout_bwd(sim_h h, const float* x0, const uint16_t* w, const float* p_ref, int H, int C,
+                    float w_act, void* ws, size_t ws_bytes, const float* dL, float* dW, float* dx0,
+                    void* stream);
+/* Forward and backward in one call with dL = 1 (dL_one: device scalar holding 1.0f). */
+int sim_rollout_grad(sim_h h, const float* x0, const uint16_t* w, const float* p_ref, int H, int C,
+                     float w_act, void* ws, size_t ws_bytes, float* loss, const float* dL_one,
+                     float* dW, float* dx0, void* stream);
+
 /* Number of kernel launches issued on this handle since creation (all calls). */
 int64_t sim_launch_count(sim_h h);
 

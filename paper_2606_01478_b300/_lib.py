@@ -18,6 +18,7 @@ FIRST_PRINCIPLES, ABSTRACTED = 0, 1
 EULER, RK4 = 0, 1
 CTRL_ROTOR_SPEED, CTRL_ATTITUDE, CTRL_POSITION = 0, 1, 2
 STATE_DIM, CMD_DIM, NPARAMS = 20, 4, 48
+POLICY_NPARAMS = 5316
 
 # Order of enum sim_param_index in include/crazyflow.h (checked by a CPU test).
 PARAM_ORDER = (
@@ -50,6 +51,14 @@ _SIGS = {
     "sim_step_count": (c_int64, [c_void_p]),
     "sim_set_step_count": (c_int, [c_void_p, c_int64]),
     "sim_launch_count": (c_int64, [c_void_p]),
+    "sim_rollout_workspace_bytes": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),
+    "sim_rollout_fwd": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_float,
+                                c_void_p, c_size_t, c_void_p, c_void_p]),
+    "sim_rollout_bwd": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_float,
+                                c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sim_rollout_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_float,
+                                 c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_void_p,
+                                 c_void_p]),
     "sim_last_error": (c_char_p, [c_void_p]),
     "sim_destroy": (None, [c_void_p]),
 }

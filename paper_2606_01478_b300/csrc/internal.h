@@ -16,6 +16,18 @@ cudaError_t launch_step(const StepArgs& a, const DevParams& P, int model, int in
 cudaError_t launch_step_batched(const StepArgs& a, const int4* tiles, int n_tiles, int integrator,
                                 int ctrl, bool general_motor, int tpb, cudaStream_t st);
 
+// Differentiable policy rollout (rollout.cu).  Workspace: checkpoints
+// [ceil(H/C)][n][20], segment states [C][n][20], per-drone loss [n], per-CTA dW
+// partials; all fp32.
+constexpr int POLICY_NPARAMS = 5316;
+size_t rollout_workspace_bytes(int n, int H, int C);
+cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
+                               int C, float dt, float w_act, const DevParams& P, void* ws,
+                               float* loss, bool store_ckpt, cudaStream_t st);
+cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
+                               int C, float dt, float w_act, const DevParams& P, void* ws,
+                               const float* dL, float* dW, float* dx0, cudaStream_t st);
+
 // Row-major [n][20] floats <-> 5 float4 planes [5][n] (layout.cu).
 cudaError_t launch_rows_to_planes(const float4* rows, float4* planes, int n, cudaStream_t st);
 cudaError_t launch_planes_to_rows(const float4* planes, float4* rows, int n, cudaStream_t st);

@@ -1,0 +1,942 @@
+// Differentiable policy rollout (backpropagation through time).
+//
+// The paper trains policies with exact analytic gradients through the unrolled
+// dynamics and the onboard controller stack (Materials and Methods,
+// Backpropagation Through Time).  Here, per drone:
+//   obs_k = [p_k - r_k, q_k, v_k, w_k];  a_k = MLP(obs_k)  (13 -> 64 -> 64 -> 4, tanh)
+//   x_{k+1} = Euler step of the first-principles model under the attitude
+//             interface with action a_k (controller, mixer, motor lag, Eqs. 1-6)
+//   L = (1/M) sum_w sum_k |p_{k+1} - r_{k+1}|^2 + w_act |a_k|^2
+// Forward kernel: rollout + loss, checkpoints of x every C steps.
+// Backward kernel: per segment, recompute the C states from the checkpoint,
+// then sweep them in reverse with the hand-written adjoint of the step and of
+// the MLP; accumulate dL/dW per CTA; dL/dx0 per drone.
+//
+// Layout: one CTA = 4 warps = 64 drones; warp v owns drones 16v..16v+15 of the
+// CTA (one m16 MMA tile; lane l handles drone l & 15 of the tile for the
+// per-drone dynamics, lanes 16..31 duplicate lanes 0..15).  The MLP runs on
+// tensor cores with mma.sync m16n8k16 (bf16 inputs, fp32 accumulate).  Weights
+// are bf16 values; activations and adjoints enter the MMAs as hi + lo bf16
+// pairs (2 MMAs, ~2^-16 relative), dW products as hi*hi + hi*lo + lo*hi.
+// The accumulator fragment of one layer is the A fragment of the next, so
+// activations stay in registers between layers.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+#include "physics.cuh"
+
+namespace cf {
+namespace ro {
+
+constexpr int OFF_W1 = 0, OFF_B1 = 832, OFF_W2 = 896, OFF_B2 = 4992, OFF_W3 = 5056,
+              OFF_B3 = 5312, NPOL = 5316, NPOL_PAD = 5376;
+constexpr int TPB = 128, DPC = 64;  // threads and drones per CTA
+constexpr int S16 = 24, S64 = 72;   // padded smem row strides (bf16 elements)
+
+struct __align__(16) Smem {
+  __nv_bfloat16 W1[64 * S16];  // [i][c]  (c < 13 used)
+  __nv_bfloat16 W2[64 * S64];  // [j][i]
+  __nv_bfloat16 W3[16 * S64];  // [o][j]  (o < 4 used)
+  __nv_bfloat16 obs[2][DPC * S16];  // hi, lo; column 13 = 1 (bias column)
+  __nv_bfloat16 h1[2][DPC * S64];   // column 64 = 1
+  __nv_bfloat16 h2[2][DPC * S64];   // column 64 = 1
+  __nv_bfloat16 dz1[2][DPC * S64];
+  __nv_bfloat16 dz2[2][DPC * S64];
+  __nv_bfloat16 dz3[2][DPC * S16];
+  float b1[64], b2[64], b3[8];
+  float act[DPC][4];
+  float dobs[DPC][16];
+};
+
+struct RolloutArgs {
+  const float* x0;        // [n][20]
+  const uint16_t* w;      // [NPOL] bf16 bits, packed W1 b1 W2 b2 W3 b3
+  const float* p_ref;     // [H + 1][n][3]
+  float* ckpt;            // [n_ckpt][n][20]
+  float* seg;             // [C][n][20]
+  float* loss_w;          // [n] per-drone loss
+  float* part;            // [n_cta][NPOL_PAD] dW partials
+  float* dx0;             // [n][20]
+  const float* dL;        // device scalar: upstream gradient of the loss
+  int n, H, C;
+  float dt, w_act, inv_n;
+  int store_ckpt;
+};
+
+// ------------------------------------------------------------------ MMA helpers
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t r[2], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t r[2], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(smem_addr(p)));
+}
+
+// D += A (16x16, row) * B (16x8, col); bf16 inputs, fp32 accumulators.
+__device__ __forceinline__ void mma(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// x ~= hi + lo with hi = bf16(x), lo = bf16(x - hi); two values per 32-bit word.
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 f = __bfloat1622float2(h);
+  __nv_bfloat162 l = __floats2bfloat162_rn(a - f.x, b - f.y);
+  hi = *reinterpret_cast<uint32_t*>(&h);
+  lo = *reinterpret_cast<uint32_t*>(&l);
+}
+
+__device__ __forceinline__ float2 unpack2(uint32_t hi, uint32_t lo) {
+  const float2 h = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&hi));
+  const float2 l = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&lo));
+  return make_float2(h.x + l.x, h.y + l.y);
+}
+
+// A fragments (hi, lo) of k-tile kk from accumulator fragments c[8][4]
+// (n-tiles 2kk, 2kk+1 form the 16 columns of k-tile kk).
+__device__ __forceinline__ void c_to_a(const float c[8][4], int kk, uint32_t ah[4], uint32_t al[4]) {
+  split2(c[2 * kk][0], c[2 * kk][1], ah[0], al[0]);
+  split2(c[2 * kk][2], c[2 * kk][3], ah[1], al[1]);
+  split2(c[2 * kk + 1][0], c[2 * kk + 1][1], ah[2], al[2]);
+  split2(c[2 * kk + 1][2], c[2 * kk + 1][3], ah[3], al[3]);
+}
+
+// Store accumulator fragments c[8][4] (rows r0 + g, r0 + g + 8; 64 columns) as
+// hi/lo bf16 into a [*][S64] tile pair.
+__device__ __forceinline__ void store_c64(__nv_bfloat16 (*t)[DPC * S64], int r0, int lane,
+                                          const float c[8][4]) {
+  const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    uint32_t h, l;
+    const int col = 8 * n + 2 * tq;
+    split2(c[n][0], c[n][1], h, l);
+    *reinterpret_cast<uint32_t*>(&t[0][(r0 + g) * S64 + col]) = h;
+    *reinterpret_cast<uint32_t*>(&t[1][(r0 + g) * S64 + col]) = l;
+    split2(c[n][2], c[n][3], h, l);
+    *reinterpret_cast<uint32_t*>(&t[0][(r0 + g + 8) * S64 + col]) = h;
+    *reinterpret_cast<uint32_t*>(&t[1][(r0 + g + 8) * S64 + col]) = l;
+  }
+}
+
+// Reload accumulator-fragment values (hi + lo) from a [*][S64] tile pair.
+__device__ __forceinline__ void load_c64(__nv_bfloat16 (*t)[DPC * S64], int r0, int lane,
+                                         float c[8][4]) {
+  const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const int col = 8 * n + 2 * tq;
+    float2 a = unpack2(*reinterpret_cast<uint32_t*>(&t[0][(r0 + g) * S64 + col]),
+                       *reinterpret_cast<uint32_t*>(&t[1][(r0 + g) * S64 + col]));
+    float2 b = unpack2(*reinterpret_cast<uint32_t*>(&t[0][(r0 + g + 8) * S64 + col]),
+                       *reinterpret_cast<uint32_t*>(&t[1][(r0 + g + 8) * S64 + col]));
+    c[n][0] = a.x;
+    c[n][1] = a.y;
+    c[n][2] = b.x;
+    c[n][3] = b.y;
+  }
+}
+
+// ------------------------------------------------------------------ MLP
+
+__device__ void load_weights(Smem& s, const uint16_t* __restrict__ w) {
+  const __nv_bfloat16* wb = reinterpret_cast<const __nv_bfloat16*>(w);
+  const __nv_bfloat16 z = __float2bfloat16(0.f);
+  for (int e = threadIdx.x; e < 64 * S16; e += TPB) {
+    const int i = e / S16, c = e % S16;
+    s.W1[e] = c < 13 ? wb[OFF_W1 + i * 13 + c] : z;
+  }
+  for (int e = threadIdx.x; e < 64 * S64; e += TPB) {
+    const int j = e / S64, i = e % S64;
+    s.W2[e] = i < 64 ? wb[OFF_W2 + j * 64 + i] : z;
+  }
+  for (int e = threadIdx.x; e < 16 * S64; e += TPB) {
+    const int o = e / S64, j = e % S64;
+    s.W3[e] = (o < 4 && j < 64) ? wb[OFF_W3 + o * 64 + j] : z;
+  }
+  for (int e = threadIdx.x; e < 64; e += TPB) {
+    s.b1[e] = __bfloat162float(wb[OFF_B1 + e]);
+    s.b2[e] = __bfloat162float(wb[OFF_B2 + e]);
+  }
+  if (threadIdx.x < 8) s.b3[threadIdx.x] = threadIdx.x < 4 ? __bfloat162float(wb[OFF_B3 + threadIdx.x]) : 0.f;
+  // constant columns of the activation tiles: 1 in the bias column, 0 padding
+  const __nv_bfloat16 one = __float2bfloat16(1.f);
+  for (int r = threadIdx.x; r < DPC; r += TPB) {
+    for (int c = 64; c < S64; ++c) {
+      s.h1[0][r * S64 + c] = c == 64 ? one : z;
+      s.h1[1][r * S64 + c] = z;
+      s.h2[0][r * S64 + c] = c == 64 ? one : z;
+      s.h2[1][r * S64 + c] = z;
+      s.dz1[0][r * S64 + c] = z;
+      s.dz1[1][r * S64 + c] = z;
+      s.dz2[0][r * S64 + c] = z;
+      s.dz2[1][r * S64 + c] = z;
+    }
+    for (int c = 0; c < S16; ++c) {
+      s.obs[0][r * S16 + c] = z;
+      s.obs[1][r * S16 + c] = z;
+      s.dz3[0][r * S16 + c] = z;
+      s.dz3[1][r * S16 + c] = z;
+    }
+  }
+}
+
+// Write one drone's observation row (hi, lo; bias column 13 = 1).
+__device__ __forceinline__ void put_obs(Smem& s, int row, const float* x, const float r[3]) {
+  float o[16];
+  o[0] = x[0] - r[0];
+  o[1] = x[1] - r[1];
+  o[2] = x[2] - r[2];
+#pragma unroll
+  for (int j = 3; j < 13; ++j) o[j] = x[j];
+  o[13] = 1.f;
+  o[14] = 0.f;
+  o[15] = 0.f;
+#pragma unroll
+  for (int j = 0; j < 16; j += 2) {
+    uint32_t h, l;
+    split2(o[j], o[j + 1], h, l);
+    *reinterpret_cast<uint32_t*>(&s.obs[0][row * S16 + j]) = h;
+    *reinterpret_cast<uint32_t*>(&s.obs[1][row * S16 + j]) = l;
+  }
+}
+
+// MLP forward for the warp's 16 drones (rows r0..r0+15).  Returns h1, h2
+// (fp32 accumulator fragments, after tanh) and writes the actions to s.act.
+__device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[8][4]) {
+  const int g = lane >> 2, tq = lane & 3;
+  const int arow = r0 + (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
+  uint32_t oh[4], ol[4];
+  ldsm_x4(oh, &s.obs[0][arow * S16 + acol]);
+  ldsm_x4(ol, &s.obs[1][arow * S16 + acol]);
+  // layer 1: z1[d][i] = sum_c obs[d][c] W1[i][c] + b1[i]
+  const int brow = (lane & 7) + (lane >> 4) * 8, bcol = ((lane >> 3) & 1) * 8;
+#pragma unroll
+  for (int n = 0; n < 8; n += 2) {
+    uint32_t b[4];
+    ldsm_x4(b, &s.W1[(8 * n + brow) * S16 + bcol]);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float b0 = s.b1[8 * (n + u) + 2 * tq], b1v = s.b1[8 * (n + u) + 2 * tq + 1];
+      float* c = h1[n + u];
+      c[0] = b0;
+      c[1] = b1v;
+      c[2] = b0;
+      c[3] = b1v;
+      mma(c, oh, b[2 * u], b[2 * u + 1]);
+      mma(c, ol, b[2 * u], b[2 * u + 1]);
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < 8; ++n)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) h1[n][e] = tanhf(h1[n][e]);
+  // layer 2: z2[d][j] = sum_i h1[d][i] W2[j][i] + b2[j]
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const float b0 = s.b2[8 * n + 2 * tq], b1v = s.b2[8 * n + 2 * tq + 1];
+    h2[n][0] = b0;
+    h2[n][1] = b1v;
+    h2[n][2] = b0;
+    h2[n][3] = b1v;
+  }
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    uint32_t ah[4], al[4];
+    c_to_a(h1, kk, ah, al);
+#pragma unroll
+    for (int n = 0; n < 8; n += 2) {
+      uint32_t b[4];
+      ldsm_x4(b, &s.W2[(8 * n + brow) * S64 + 16 * kk + bcol]);
+      mma(h2[n], ah, b[0], b[1]);
+      mma(h2[n], al, b[0], b[1]);
+      mma(h2[n + 1], ah, b[2], b[3]);
+      mma(h2[n + 1], al, b[2], b[3]);
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < 8; ++n)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) h2[n][e] = tanhf(h2[n][e]);
+  // layer 3: z3[d][o] = sum_j h2[d][j] W3[o][j] + b3[o]
+  float z3[4];
+  z3[0] = s.b3[2 * tq];
+  z3[1] = s.b3[2 * tq + 1];
+  z3[2] = z3[0];
+  z3[3] = z3[1];
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    uint32_t ah[4], al[4];
+    c_to_a(h2, kk, ah, al);
+    uint32_t b[2];
+    ldsm_x2(b, &s.W3[(lane & 7) * S64 + 16 * kk + bcol]);
+    mma(z3, ah, b[0], b[1]);
+    mma(z3, al, b[0], b[1]);
+  }
+  if (tq < 2) {
+    s.act[r0 + g][2 * tq] = tanhf(z3[0]);
+    s.act[r0 + g][2 * tq + 1] = tanhf(z3[1]);
+    s.act[r0 + g + 8][2 * tq] = tanhf(z3[2]);
+    s.act[r0 + g + 8][2 * tq + 1] = tanhf(z3[3]);
+  }
+}
+
+// MLP backward for the warp's 16 drones, given dz3 rows in s.dz3 and the
+// forward activations in s.h1 / s.h2 (hi + lo).  Writes dz1, dz2 tiles and the
+// observation adjoint into s.dobs.
+__device__ void mlp_backward(Smem& s, int r0, int lane) {
+  const int g = lane >> 2, tq = lane & 3;
+  const int arow = r0 + (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
+  // transposed B fragments: storage [k][n]
+  const int trow = (lane & 7) + ((lane >> 3) & 1) * 8, tcol = (lane >> 4) * 8;
+  float d[8][4];
+  // dh2[d][j] = sum_o dz3[d][o] W3[o][j]
+  {
+    uint32_t ah[4], al[4];
+    ldsm_x4(ah, &s.dz3[0][arow * S16 + acol]);
+    ldsm_x4(al, &s.dz3[1][arow * S16 + acol]);
+#pragma unroll
+    for (int n = 0; n < 8; n += 2) {
+      uint32_t b[4];
+      ldsm_x4_t(b, &s.W3[trow * S64 + 8 * n + tcol]);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        d[n + u][0] = d[n + u][1] = d[n + u][2] = d[n + u][3] = 0.f;
+        mma(d[n + u], ah, b[2 * u], b[2 * u + 1]);
+        mma(d[n + u], al, b[2 * u], b[2 * u + 1]);
+      }
+    }
+  }
+  // dz2 = dh2 (1 - h2^2)
+  {
+    float h[8][4];
+    load_c64(s.h2, r0, lane, h);
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d[n][e] *= fmaf(-h[n][e], h[n][e], 1.f);
+  }
+  store_c64(s.dz2, r0, lane, d);
+  // dh1[d][i] = sum_j dz2[d][j] W2[j][i]
+  float e1[8][4];
+#pragma unroll
+  for (int n = 0; n < 8; ++n) e1[n][0] = e1[n][1] = e1[n][2] = e1[n][3] = 0.f;
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    uint32_t ah[4], al[4];
+    c_to_a(d, kk, ah, al);
+#pragma unroll
+    for (int n = 0; n < 8; n += 2) {
+      uint32_t b[4];
+      ldsm_x4_t(b, &s.W2[(16 * kk + trow) * S64 + 8 * n + tcol]);
+      mma(e1[n], ah, b[0], b[1]);
+      mma(e1[n], al, b[0], b[1]);
+      mma(e1[n + 1], ah, b[2], b[3]);
+      mma(e1[n + 1], al, b[2], b[3]);
+    }
+  }
+  // dz1 = dh1 (1 - h1^2)
+  {
+    float h[8][4];
+    load_c64(s.h1, r0, lane, h);
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) e1[n][e] *= fmaf(-h[n][e], h[n][e], 1.f);
+  }
+  store_c64(s.dz1, r0, lane, e1);
+  // dobs[d][c] = sum_i dz1[d][i] W1[i][c]
+  float o[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    uint32_t ah[4], al[4];
+    c_to_a(e1, kk, ah, al);
+    uint32_t b[4];
+    ldsm_x4_t(b, &s.W1[(16 * kk + trow) * S16 + tcol]);
+    mma(o[0], ah, b[0], b[1]);
+    mma(o[0], al, b[0], b[1]);
+    mma(o[1], ah, b[2], b[3]);
+    mma(o[1], al, b[2], b[3]);
+  }
+#pragma unroll
+  for (int n = 0; n < 2; ++n) {
+    s.dobs[r0 + g][8 * n + 2 * tq] = o[n][0];
+    s.dobs[r0 + g][8 * n + 2 * tq + 1] = o[n][1];
+    s.dobs[r0 + g + 8][8 * n + 2 * tq] = o[n][2];
+    s.dobs[r0 + g + 8][8 * n + 2 * tq + 1] = o[n][3];
+  }
+}
+
+// dW accumulation over the CTA's 64 drones for this step (warp v's slice):
+//   dW2 rows j in [16v, 16v+16) x columns 0..64 (64 = bias b2)
+//   dW1 rows i in [16v, 16v+16) x columns 0..15 (13 = bias b1)
+//   dW3 rows o in [0, 16) x columns j in [16v, 16v+16) (+ column 64 = b3 on warp 3)
+struct DwAcc {
+  float w2[9][4];
+  float w1[2][4];
+  float w3[3][4];
+};
+
+__device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc) {
+  // A = dz^T: A(row m, col d) = dz[d][m], storage [d][m] -> transposed load
+  const int arow = (lane & 7) + (lane >> 4) * 8, acol = ((lane >> 3) & 1) * 8;
+  // B(k = d, n) = act[d][n], storage [d][n] -> transposed load
+  const int brow = (lane & 7) + ((lane >> 3) & 1) * 8, bcol = (lane >> 4) * 8;
+#pragma unroll
+  for (int kd = 0; kd < 4; ++kd) {
+    const int d0 = 16 * kd;
+    uint32_t ah[4], al[4];
+    // dW2
+    ldsm_x4_t(ah, &s.dz2[0][(d0 + arow) * S64 + 16 * v + acol]);
+    ldsm_x4_t(al, &s.dz2[1][(d0 + arow) * S64 + 16 * v + acol]);
+#pragma unroll
+    for (int n = 0; n < 8; n += 2) {
+      uint32_t bh[4], bl[4];
+      ldsm_x4_t(bh, &s.h1[0][(d0 + brow) * S64 + 8 * n + bcol]);
+      ldsm_x4_t(bl, &s.h1[1][(d0 + brow) * S64 + 8 * n + bcol]);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        mma(acc.w2[n + u], ah, bh[2 * u], bh[2 * u + 1]);
+        mma(acc.w2[n + u], ah, bl[2 * u], bl[2 * u + 1]);
+        mma(acc.w2[n + u], al, bh[2 * u], bh[2 * u + 1]);
+      }
+    }
+    {
+      uint32_t bh[2];
+      ldsm_x2_t(bh, &s.h1[0][(d0 + brow) * S64 + 64]);
+      mma(acc.w2[8], ah, bh[0], bh[1]);
+      mma(acc.w2[8], al, bh[0], bh[1]);  // the bias column is exact (lo = 0)
+    }
+    // dW1
+    ldsm_x4_t(ah, &s.dz1[0][(d0 + arow) * S64 + 16 * v + acol]);
+    ldsm_x4_t(al, &s.dz1[1][(d0 + arow) * S64 + 16 * v + acol]);
+    {
+      uint32_t bh[4], bl[4];
+      ldsm_x4_t(bh, &s.obs[0][(d0 + brow) * S16 + bcol]);
+      ldsm_x4_t(bl, &s.obs[1][(d0 + brow) * S16 + bcol]);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        mma(acc.w1[u], ah, bh[2 * u], bh[2 * u + 1]);
+        mma(acc.w1[u], ah, bl[2 * u], bl[2 * u + 1]);
+        mma(acc.w1[u], al, bh[2 * u], bh[2 * u + 1]);
+      }
+    }
+    // dW3
+    ldsm_x4_t(ah, &s.dz3[0][(d0 + arow) * S16 + acol]);
+    ldsm_x4_t(al, &s.dz3[1][(d0 + arow) * S16 + acol]);
+    {
+      uint32_t bh[4], bl[4];
+      ldsm_x4_t(bh, &s.h2[0][(d0 + brow) * S64 + 16 * v + bcol]);
+      ldsm_x4_t(bl, &s.h2[1][(d0 + brow) * S64 + 16 * v + bcol]);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        mma(acc.w3[u], ah, bh[2 * u], bh[2 * u + 1]);
+        mma(acc.w3[u], ah, bl[2 * u], bl[2 * u + 1]);
+        mma(acc.w3[u], al, bh[2 * u], bh[2 * u + 1]);
+      }
+      if (v == 3) {
+        uint32_t b1[2];
+        ldsm_x2_t(b1, &s.h2[0][(d0 + brow) * S64 + 64]);
+        mma(acc.w3[2], ah, b1[0], b1[1]);
+        mma(acc.w3[2], al, b1[0], b1[1]);
+      }
+    }
+  }
+}
+
+__device__ void store_dw(const DwAcc& acc, int v, int lane, float* __restrict__ part) {
+  const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int rr = g + (e >= 2 ? 8 : 0), cc = 2 * tq + (e & 1);
+    // dW2 / db2
+#pragma unroll
+    for (int n = 0; n < 9; ++n) {
+      const int j = 16 * v + rr, i = 8 * n + cc;
+      if (i < 64) part[OFF_W2 + j * 64 + i] = acc.w2[n][e];
+      else if (i == 64) part[OFF_B2 + j] = acc.w2[n][e];
+    }
+    // dW1 / db1
+#pragma unroll
+    for (int n = 0; n < 2; ++n) {
+      const int i = 16 * v + rr, c = 8 * n + cc;
+      if (c < 13) part[OFF_W1 + i * 13 + c] = acc.w1[n][e];
+      else if (c == 13) part[OFF_B1 + i] = acc.w1[n][e];
+    }
+    // dW3 / db3
+#pragma unroll
+    for (int n = 0; n < 3; ++n) {
+      if (n == 2 && v != 3) continue;
+      const int o = rr, j = (n < 2) ? 16 * v + 8 * n + cc : 64 + cc;
+      if (o >= 4) continue;
+      if (j < 64) part[OFF_W3 + o * 64 + j] = acc.w3[n][e];
+      else if (j == 64) part[OFF_B3 + o] = acc.w3[n][e];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ dynamics
+
+// Euler step of the first-principles model under the attitude interface
+// (first-order-lag rotors, no drag), a = the policy action.
+__device__ __forceinline__ void policy_step(float* x, const float a[4], const DevParams& P, float dt) {
+  float Rd[9], Td, R[9], tx, ty, tz, Wc[4], d[17];
+  attitude_command(make_float4(a[0], a[1], a[2], a[3]), P, Rd, Td);
+  quat_rot(x[3], x[4], x[5], x[6], R);
+  attitude_torque(R, Rd, x[10], x[11], x[12], P, tx, ty, tz);
+  mixer(Td, tx, ty, tz, P, Wc);
+  deriv_fp<MOTOR_LAG>(x, Wc, P, false, d);
+#pragma unroll
+  for (int j = 0; j < 17; ++j) x[j] = fmaf(dt, d[j], x[j]);
+  const float in = rsqrt_approx(fmaf(x[3], x[3], fmaf(x[4], x[4], fmaf(x[5], x[5], x[6] * x[6]))));
+  x[3] *= in;
+  x[4] *= in;
+  x[5] *= in;
+  x[6] *= in;
+}
+
+// Adjoint of policy_step.  In: x (pre-step state), a, lam = dL/dx_{k+1}.
+// Out: lam = dL/dx_k through the step (the observation path is added by the
+// caller), ga = dL/da through the controller.
+__device__ void policy_step_adjoint(const float* x, const float a[4], float* lam, float ga[4],
+                                    const DevParams& P, float dt) {
+  // ---------------- forward recomputation
+  const float ac0 = clampf(a[0], -1.f, 1.f), ac1 = clampf(a[1], -1.f, 1.f);
+  const float ac2 = clampf(a[2], -1.f, 1.f), ac3 = clampf(a[3], -1.f, 1.f);
+  float sr, cr, sp, cp, sy, cy;
+  __sincosf(ac0 * P.max_angle, &sr, &cr);
+  __sincosf(ac1 * P.max_angle, &sp, &cp);
+  __sincosf(ac2 * P.max_angle, &sy, &cy);
+  float Rd[9];
+  euler_rot(sr, cr, sp, cp, sy, cy, Rd);
+  const float Td = fmaf(P.ts_mg, ac3, P.mg);
+  const float qx = x[3], qy = x[4], qz = x[5], qw = x[6];
+  const float wx = x[10], wy = x[11], wz = x[12];
+  float R[9];
+  quat_rot(qx, qy, qz, qw, R);
+  float tx, ty, tz;
+  attitude_torque(R, Rd, wx, wy, wz, P, tx, ty, tz);
+  const float A = 0.25f * Td, X = tx * P.mix_a, Y = ty * P.mix_a, Z = tz * P.mix_k;
+  float f[4], Wc[4];
+  f[0] = (A - X) - (Y + Z);
+  f[1] = (A - X) + (Y + Z);
+  f[2] = (A + X) + (Y - Z);
+  f[3] = (A + X) - (Y - Z);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) Wc[r] = sqrt_approx(clampf(f[r], 0.f, P.fmax) * P.inv_kf);
+  float d[17];
+  deriv_fp<MOTOR_LAG>(x, Wc, P, false, d);
+  float qt[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) qt[j] = fmaf(dt, d[3 + j], x[3 + j]);
+  const float in = rsqrt_approx(fmaf(qt[0], qt[0], fmaf(qt[1], qt[1], fmaf(qt[2], qt[2], qt[3] * qt[3]))));
+  // ---------------- reverse: normalisation q' = qt / |qt|
+  {
+    const float q0 = qt[0] * in, q1 = qt[1] * in, q2 = qt[2] * in, q3 = qt[3] * in;
+    const float dot = fmaf(q0, lam[3], fmaf(q1, lam[4], fmaf(q2, lam[5], q3 * lam[6])));
+    lam[3] = (lam[3] - q0 * dot) * in;
+    lam[4] = (lam[4] - q1 * dot) * in;
+    lam[5] = (lam[5] - q2 * dot) * in;
+    lam[6] = (lam[6] - q3 * dot) * in;
+  }
+  // x_tilde = x + dt * xdot: mu = dt * lam (adjoint of xdot); lam stays (identity)
+  float mu[17];
+#pragma unroll
+  for (int j = 0; j < 17; ++j) mu[j] = dt * lam[j];
+  // p' = v
+  lam[7] += mu[0];
+  lam[8] += mu[1];
+  lam[9] += mu[2];
+  // q' = 1/2 q (x) [w, 0]
+  lam[3] += 0.5f * (-wz * mu[4] + wy * mu[5] - wx * mu[6]);
+  lam[4] += 0.5f * (wz * mu[3] - wx * mu[5] - wy * mu[6]);
+  lam[5] += 0.5f * (-wy * mu[3] + wx * mu[4] - wz * mu[6]);
+  lam[6] += 0.5f * (wx * mu[3] + wy * mu[4] + wz * mu[5]);
+  float gwx = 0.5f * (qw * mu[3] + qz * mu[4] - qy * mu[5] - qx * mu[6]);
+  float gwy = 0.5f * (-qz * mu[3] + qw * mu[4] + qx * mu[5] - qy * mu[6]);
+  float gwz = 0.5f * (qy * mu[3] - qx * mu[4] + qw * mu[5] - qz * mu[6]);
+  // v' = (T/m) R e_z - g e_z
+  const float s0 = x[13] * x[13], s1 = x[14] * x[14], s2 = x[15] * x[15], s3 = x[16] * x[16];
+  const float T = P.kf * ((s0 + s1) + (s2 + s3));
+  const float Tm = T * P.inv_m;
+  const float r02 = 2.f * fmaf(qx, qz, qw * qy);
+  const float r12 = 2.f * fmaf(qy, qz, -qw * qx);
+  const float r22 = (qw * qw + qz * qz) - (qx * qx + qy * qy);
+  const float gT = P.inv_m * fmaf(mu[7], r02, fmaf(mu[8], r12, mu[9] * r22));
+  {
+    const float g02 = Tm * mu[7], g12 = Tm * mu[8], g22 = Tm * mu[9];
+    lam[3] += 2.f * (qz * g02 - qw * g12 - qx * g22);
+    lam[4] += 2.f * (qw * g02 + qz * g12 - qy * g22);
+    lam[5] += 2.f * (qx * g02 + qy * g12 + qz * g22);
+    lam[6] += 2.f * (qy * g02 - qx * g12 + qw * g22);
+  }
+  // w' = tau_rotor / J + (cJx wy wz, cJy wz wx, cJz wx wy)
+  const float gtx = mu[10] * P.inv_Jx, gty = mu[11] * P.inv_Jy, gtz = mu[12] * P.inv_Jz;
+  gwx += P.cJy * wz * mu[11] + P.cJz * wy * mu[12];
+  gwy += P.cJx * wz * mu[10] + P.cJz * wx * mu[12];
+  gwz += P.cJx * wy * mu[10] + P.cJy * wx * mu[11];
+  // rotor wrench of s_i = W_i^2
+  const float gs0 = P.kf * gT - P.kfa * gtx - P.kfa * gty - P.km * gtz;
+  const float gs1 = P.kf * gT - P.kfa * gtx + P.kfa * gty + P.km * gtz;
+  const float gs2 = P.kf * gT + P.kfa * gtx + P.kfa * gty - P.km * gtz;
+  const float gs3 = P.kf * gT + P.kfa * gtx - P.kfa * gty + P.km * gtz;
+  lam[13] += 2.f * x[13] * gs0 - P.cv_up * mu[13];
+  lam[14] += 2.f * x[14] * gs1 - P.cv_up * mu[14];
+  lam[15] += 2.f * x[15] * gs2 - P.cv_up * mu[15];
+  lam[16] += 2.f * x[16] * gs3 - P.cv_up * mu[16];
+  // ---------------- controller: W_cmd -> mixer -> torque -> attitude error
+  float gf[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const float gWc = P.cv_up * mu[13 + r];
+    const bool pass = f[r] >= 0.f && f[r] <= P.fmax && Wc[r] > 0.f;
+    gf[r] = pass ? gWc * P.inv_kf * 0.5f / Wc[r] : 0.f;
+  }
+  const float gA = (gf[0] + gf[1]) + (gf[2] + gf[3]);
+  const float gX = (gf[2] + gf[3]) - (gf[0] + gf[1]);
+  const float gY = (gf[1] + gf[2]) - (gf[0] + gf[3]);
+  const float gZ = (gf[1] + gf[3]) - (gf[0] + gf[2]);
+  const float gTd = 0.25f * gA;
+  const float gtcx = P.mix_a * gX, gtcy = P.mix_a * gY, gtcz = P.mix_k * gZ;
+  // tau = -KRJh e - KwJ w  (e = 2 e_R)
+  const float gex = -P.KRJh_x * gtcx, gey = -P.KRJh_y * gtcy, gez = -P.KRJh_z * gtcz;
+  gwx -= P.KwJ_x * gtcx;
+  gwy -= P.KwJ_y * gtcy;
+  gwz -= P.KwJ_z * gtcz;
+  lam[10] += gwx;
+  lam[11] += gwy;
+  lam[12] += gwz;
+  // e = vee(M - M^T), M = Rd^T R:  gR = Rd G, gRd = R G^T with
+  // G = [[0, -gez, gey], [gez, 0, -gex], [-gey, gex, 0]]
+  float gR[9], gRd[9];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float d0 = Rd[3 * k], d1 = Rd[3 * k + 1], d2 = Rd[3 * k + 2];
+    gR[3 * k + 0] = d1 * gez - d2 * gey;
+    gR[3 * k + 1] = d2 * gex - d0 * gez;
+    gR[3 * k + 2] = d0 * gey - d1 * gex;
+    const float e0 = R[3 * k], e1 = R[3 * k + 1], e2 = R[3 * k + 2];
+    gRd[3 * k + 0] = e2 * gey - e1 * gez;
+    gRd[3 * k + 1] = e0 * gez - e2 * gex;
+    gRd[3 * k + 2] = e1 * gex - e0 * gey;
+  }
+  // R(q) quadratic form
+  lam[3] += 2.f * (qx * (gR[0] - gR[4] - gR[8]) + qy * (gR[1] + gR[3]) + qz * (gR[2] + gR[6]) +
+                   qw * (gR[7] - gR[5]));
+  lam[4] += 2.f * (qy * (gR[4] - gR[0] - gR[8]) + qx * (gR[1] + gR[3]) + qw * (gR[2] - gR[6]) +
+                   qz * (gR[5] + gR[7]));
+  lam[5] += 2.f * (qz * (gR[8] - gR[0] - gR[4]) + qw * (gR[3] - gR[1]) + qx * (gR[2] + gR[6]) +
+                   qy * (gR[5] + gR[7]));
+  lam[6] += 2.f * (qw * (gR[0] + gR[4] + gR[8]) + qz * (gR[3] - gR[1]) + qy * (gR[2] - gR[6]) +
+                   qx * (gR[7] - gR[5]));
+  // Rd = Rz(y) Ry(p) Rx(r)
+  const float gphi = gRd[1] * Rd[2] - gRd[2] * Rd[1] + gRd[4] * Rd[5] - gRd[5] * Rd[4] +
+                     gRd[7] * Rd[8] - gRd[8] * Rd[7];
+  const float gth = -gRd[0] * cy * sp + gRd[1] * cy * cp * sr + gRd[2] * cy * cp * cr -
+                    gRd[3] * sy * sp + gRd[4] * sy * cp * sr + gRd[5] * sy * cp * cr -
+                    gRd[6] * cp - gRd[7] * sp * sr - gRd[8] * sp * cr;
+  const float gpsi = -gRd[0] * Rd[3] - gRd[1] * Rd[4] - gRd[2] * Rd[5] + gRd[3] * Rd[0] +
+                     gRd[4] * Rd[1] + gRd[5] * Rd[2];
+  // clip(a, -1, 1) passes the gradient inside [-1, 1] (inclusive)
+  ga[0] = (a[0] >= -1.f && a[0] <= 1.f) ? gphi * P.max_angle : 0.f;
+  ga[1] = (a[1] >= -1.f && a[1] <= 1.f) ? gth * P.max_angle : 0.f;
+  ga[2] = (a[2] >= -1.f && a[2] <= 1.f) ? gpsi * P.max_angle : 0.f;
+  ga[3] = (a[3] >= -1.f && a[3] <= 1.f) ? gTd * P.ts_mg : 0.f;
+}
+
+__device__ __forceinline__ void load_row(const float* __restrict__ base, int i, float* x) {
+  const float4* p = reinterpret_cast<const float4*>(base + (size_t)i * 20);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float4 v = p[j];
+    x[4 * j] = v.x;
+    x[4 * j + 1] = v.y;
+    x[4 * j + 2] = v.z;
+    x[4 * j + 3] = v.w;
+  }
+  x[16] = base[(size_t)i * 20 + 16];
+}
+
+__device__ __forceinline__ void store_row(float* __restrict__ base, int i, const float* x) {
+  float4* p = reinterpret_cast<float4*>(base + (size_t)i * 20);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) p[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+  p[4] = make_float4(x[16], 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ void ref_at(const float* __restrict__ p_ref, int k, int n, int i,
+                                      float r[3]) {
+  const float* q = p_ref + ((size_t)k * n + i) * 3;
+  r[0] = q[0];
+  r[1] = q[1];
+  r[2] = q[2];
+}
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  load_weights(s, a.w);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
+  const int r0 = 16 * v, row = r0 + (lane & 15);
+  const int i = blockIdx.x * DPC + row;
+  const bool valid = i < a.n;
+  const int ii = valid ? i : a.n - 1;  // out-of-range rows shadow the last drone
+  float x[17];
+  load_row(a.x0, ii, x);
+  float loss = 0.f;
+  for (int k = 0; k < a.H; ++k) {
+    if (a.store_ckpt && (k % a.C) == 0 && valid && lane < 16) store_row(a.ckpt + (size_t)(k / a.C) * a.n * 20, i, x);
+    float r[3];
+    ref_at(a.p_ref, k, a.n, ii, r);
+    if (lane < 16) put_obs(s, row, x, r);
+    __syncwarp();
+    float h1[8][4], h2[8][4];
+    mlp_forward(s, r0, lane, h1, h2);
+    __syncwarp();
+    float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
+    __syncwarp();
+    policy_step(x, act, P, a.dt);
+    ref_at(a.p_ref, k + 1, a.n, ii, r);
+    const float ex = x[0] - r[0], ey = x[1] - r[1], ez = x[2] - r[2];
+    loss += fmaf(ex, ex, fmaf(ey, ey, ez * ez)) +
+            a.w_act * fmaf(act[0], act[0], fmaf(act[1], act[1], fmaf(act[2], act[2], act[3] * act[3])));
+  }
+  if (valid && lane < 16) a.loss_w[i] = loss;
+}
+
+__global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  load_weights(s, a.w);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
+  const int r0 = 16 * v, row = r0 + (lane & 15);
+  const int i = blockIdx.x * DPC + row;
+  const bool valid = i < a.n;
+  const int ii = valid ? i : a.n - 1;
+  const float seed = valid ? (*a.dL) * a.inv_n : 0.f;  // padded rows contribute nothing
+  DwAcc acc;
+#pragma unroll
+  for (int n = 0; n < 9; ++n) acc.w2[n][0] = acc.w2[n][1] = acc.w2[n][2] = acc.w2[n][3] = 0.f;
+#pragma unroll
+  for (int n = 0; n < 2; ++n) acc.w1[n][0] = acc.w1[n][1] = acc.w1[n][2] = acc.w1[n][3] = 0.f;
+#pragma unroll
+  for (int n = 0; n < 3; ++n) acc.w3[n][0] = acc.w3[n][1] = acc.w3[n][2] = acc.w3[n][3] = 0.f;
+  float lam[17];
+#pragma unroll
+  for (int j = 0; j < 17; ++j) lam[j] = 0.f;
+  const int nseg = (a.H + a.C - 1) / a.C;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int k0 = sg * a.C, k1 = min(a.H, k0 + a.C);
+    float x[17];
+    load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
+    // recompute the segment's states
+    for (int k = k0; k < k1; ++k) {
+      if (valid && lane < 16) store_row(a.seg + (size_t)(k - k0) * a.n * 20, i, x);
+      float r[3];
+      ref_at(a.p_ref, k, a.n, ii, r);
+      if (lane < 16) put_obs(s, row, x, r);
+      __syncwarp();
+      float h1[8][4], h2[8][4];
+      mlp_forward(s, r0, lane, h1, h2);
+      __syncwarp();
+      float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
+      __syncwarp();
+      policy_step(x, act, P, a.dt);
+    }
+    // reverse sweep
+    for (int k = k1 - 1; k >= k0; --k) {
+      __syncwarp();
+      // padded rows never read rows written by other warps: they replay the
+      // checkpoint row (finite data; their seed and dz rows are zero)
+      if (valid) load_row(a.seg + (size_t)(k - k0) * a.n * 20, i, x);
+      else load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
+      float r[3];
+      ref_at(a.p_ref, k, a.n, ii, r);
+      if (lane < 16) put_obs(s, row, x, r);
+      __syncwarp();
+      {
+        float h1[8][4], h2[8][4];
+        mlp_forward(s, r0, lane, h1, h2);
+        store_c64(s.h1, r0, lane, h1);
+        store_c64(s.h2, r0, lane, h2);
+      }
+      __syncwarp();
+      const float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
+      // loss term at step k + 1 (position after this step)
+      {
+        float xn[17];
+#pragma unroll
+        for (int j = 0; j < 17; ++j) xn[j] = x[j];
+        policy_step(xn, act, P, a.dt);
+        float rn[3];
+        ref_at(a.p_ref, k + 1, a.n, ii, rn);
+        lam[0] += 2.f * seed * (xn[0] - rn[0]);
+        lam[1] += 2.f * seed * (xn[1] - rn[1]);
+        lam[2] += 2.f * seed * (xn[2] - rn[2]);
+      }
+      float ga[4];
+      policy_step_adjoint(x, act, lam, ga, P, a.dt);
+#pragma unroll
+      for (int o = 0; o < 4; ++o) ga[o] = fmaf(2.f * seed * a.w_act, act[o], ga[o]);
+      // dz3 = ga (1 - a^2); rows of padded drones are zero
+      if (lane < 16) {
+        float dz[16];
+#pragma unroll
+        for (int o = 0; o < 16; ++o) dz[o] = 0.f;
+#pragma unroll
+        for (int o = 0; o < 4; ++o) dz[o] = valid ? ga[o] * fmaf(-act[o], act[o], 1.f) : 0.f;
+#pragma unroll
+        for (int o = 0; o < 16; o += 2) {
+          uint32_t h, l;
+          split2(dz[o], dz[o + 1], h, l);
+          *reinterpret_cast<uint32_t*>(&s.dz3[0][row * S16 + o]) = h;
+          *reinterpret_cast<uint32_t*>(&s.dz3[1][row * S16 + o]) = l;
+        }
+      }
+      __syncwarp();
+      mlp_backward(s, r0, lane);
+      __syncwarp();
+      // observation adjoint: obs = [p - r, q, v, w]
+#pragma unroll
+      for (int j = 0; j < 13; ++j) lam[j] += s.dobs[row][j];
+      __syncthreads();  // every warp's tiles for this step are in shared memory
+      accumulate_dw(s, v, lane, acc);
+      __syncthreads();  // before the next step overwrites the tiles
+    }
+  }
+  if (valid && lane < 16) {
+    float4* p = reinterpret_cast<float4*>(a.dx0 + (size_t)i * 20);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) p[j] = make_float4(lam[4 * j], lam[4 * j + 1], lam[4 * j + 2], lam[4 * j + 3]);
+    p[4] = make_float4(lam[16], 0.f, 0.f, 0.f);
+  }
+  store_dw(acc, v, lane, a.part + (size_t)blockIdx.x * NPOL_PAD);
+}
+
+// Deterministic reductions: dW[p] = sum over CTAs (fixed order, fp64);
+// loss = sum over drones / n (one block, fixed-order tree).
+__global__ void reduce_dw_kernel(const float* __restrict__ part, int n_cta, float* __restrict__ dW) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= NPOL) return;
+  double acc = 0.0;
+  for (int c = 0; c < n_cta; ++c) acc += (double)part[(size_t)c * NPOL_PAD + p];
+  dW[p] = (float)acc;
+}
+
+__global__ void reduce_loss_kernel(const float* __restrict__ loss_w, int n, float* __restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) acc += (double)loss_w[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = (float)(red[0] / n);
+}
+
+}  // namespace ro
+
+size_t rollout_workspace_bytes(int n, int H, int C) {
+  const int n_ck = (H + C - 1) / C;
+  const int n_cta = (n + ro::DPC - 1) / ro::DPC;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  return al((size_t)n_ck * n * 20 * 4) + al((size_t)C * n * 20 * 4) + al((size_t)n * 4) +
+         al((size_t)n_cta * ro::NPOL_PAD * 4);
+}
+
+static void carve(void* ws, int n, int H, int C, ro::RolloutArgs& a) {
+  const int n_ck = (H + C - 1) / C;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  char* p = (char*)ws;
+  a.ckpt = (float*)p;
+  p += al((size_t)n_ck * n * 20 * 4);
+  a.seg = (float*)p;
+  p += al((size_t)C * n * 20 * 4);
+  a.loss_w = (float*)p;
+  p += al((size_t)n * 4);
+  a.part = (float*)p;
+}
+
+cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
+                               int C, float dt, float w_act, const DevParams& P, void* ws,
+                               float* loss, bool store_ckpt, cudaStream_t st) {
+  ro::RolloutArgs a{};
+  carve(ws, n, H, C, a);
+  a.x0 = x0;
+  a.w = w;
+  a.p_ref = p_ref;
+  a.n = n;
+  a.H = H;
+  a.C = C;
+  a.dt = dt;
+  a.w_act = w_act;
+  a.store_ckpt = store_ckpt ? 1 : 0;
+  const int smem = (int)sizeof(ro::Smem);
+  cudaError_t e = cudaFuncSetAttribute(ro::rollout_fwd_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (n + ro::DPC - 1) / ro::DPC;
+  ro::rollout_fwd_kernel<<<grid, ro::TPB, smem, st>>>(a, P);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ro::reduce_loss_kernel<<<1, 256, 0, st>>>(a.loss_w, n, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
+                               int C, float dt, float w_act, const DevParams& P, void* ws,
+                               const float* dL, float* dW, float* dx0, cudaStream_t st) {
+  ro::RolloutArgs a{};
+  carve(ws, n, H, C, a);
+  a.x0 = x0;
+  a.w = w;
+  a.p_ref = p_ref;
+  a.dx0 = dx0;
+  a.n = n;
+  a.H = H;
+  a.C = C;
+  a.dt = dt;
+  a.w_act = w_act;
+  a.dL = dL;
+  a.inv_n = 1.f / (float)n;
+  const int smem = (int)sizeof(ro::Smem);
+  cudaError_t e = cudaFuncSetAttribute(ro::rollout_bwd_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (n + ro::DPC - 1) / ro::DPC;
+  ro::rollout_bwd_kernel<<<grid, ro::TPB, smem, st>>>(a, P);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ro::reduce_dw_kernel<<<(ro::NPOL + 255) / 256, 256, 0, st>>>(a.part, grid, dW);
+  return cudaGetLastError();
+}
+
+}  // namespace cf

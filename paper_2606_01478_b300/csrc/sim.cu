@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <initializer_list>
 #include <new>
 #include <vector>
 
@@ -453,6 +454,64 @@ int sim_status(sim_h h, uint32_t* flags, void* stream) {
   if (e != cudaSuccess) return cuda_fail(h, e, "reading the status word");
   *flags = v;
   return SIM_OK;
+}
+
+// ---------------------------------------------------------------- rollout (BPTT)
+
+static int rollout_check(sim_h h, int H, int C, const void* ws, size_t ws_bytes,
+                         std::initializer_list<const void*> dev_ptrs) {
+  if (h->batched || h->model != SIM_FIRST_PRINCIPLES || h->integrator != SIM_EULER)
+    return fail(h, SIM_EINVAL, "policy rollouts need a uniform first-principles Euler handle");
+  if (!h->params_ok) return fail(h, SIM_ESTATE, "sim_set_params must come first");
+  if (h->per_set || (h->p0.flags & (cf::PF_DRAG | cf::PF_GENERAL_MOTOR)))
+    return fail(h, SIM_EINVAL, "policy rollouts need one parameter set, lag rotors and no drag");
+  if (H < 1 || C < 1 || C > H) return fail(h, SIM_EINVAL, "need 1 <= C <= H");
+  if (!ws || ((uintptr_t)ws & 255)) return fail(h, SIM_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < cf::rollout_workspace_bytes((int)h->ntot, H, C))
+    return fail(h, SIM_ENOMEM, "rollout workspace too small");
+  for (const void* p : dev_ptrs)
+    if (!p || ((uintptr_t)p & 15)) return fail(h, SIM_EINVAL, "device buffers must be 16-byte aligned");
+  return SIM_OK;
+}
+
+int sim_rollout_workspace_bytes(sim_h h, int H, int C, size_t* bytes) {
+  if (!h || !bytes) return SIM_EINVAL;
+  if (H < 1 || C < 1 || C > H) return fail(h, SIM_EINVAL, "need 1 <= C <= H");
+  *bytes = cf::rollout_workspace_bytes((int)h->ntot, H, C);
+  return SIM_OK;
+}
+
+int sim_rollout_fwd(sim_h h, const float* x0, const uint16_t* w, const float* p_ref, int H, int C,
+                    float w_act, void* ws, size_t ws_bytes, float* loss, void* stream) {
+  if (!h) return SIM_EINVAL;
+  int r = rollout_check(h, H, C, ws, ws_bytes, {x0, w, p_ref, loss});
+  if (r != SIM_OK) return r;
+  cudaError_t e = cf::launch_rollout_fwd(x0, w, p_ref, (int)h->ntot, H, C, h->dt, w_act, h->p0, ws,
+                                         loss, true, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "rollout forward launch");
+  h->launches += 2;
+  return SIM_OK;
+}
+
+int sim_rollout_bwd(sim_h h, const float* x0, const uint16_t* w, const float* p_ref, int H, int C,
+                    float w_act, void* ws, size_t ws_bytes, const float* dL, float* dW, float* dx0,
+                    void* stream) {
+  if (!h) return SIM_EINVAL;
+  int r = rollout_check(h, H, C, ws, ws_bytes, {x0, w, p_ref, dL, dW, dx0});
+  if (r != SIM_OK) return r;
+  cudaError_t e = cf::launch_rollout_bwd(x0, w, p_ref, (int)h->ntot, H, C, h->dt, w_act, h->p0, ws,
+                                         dL, dW, dx0, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "rollout backward launch");
+  h->launches += 2;
+  return SIM_OK;
+}
+
+int sim_rollout_grad(sim_h h, const float* x0, const uint16_t* w, const float* p_ref, int H, int C,
+                     float w_act, void* ws, size_t ws_bytes, float* loss, const float* dL_one,
+                     float* dW, float* dx0, void* stream) {
+  int r = sim_rollout_fwd(h, x0, w, p_ref, H, C, w_act, ws, ws_bytes, loss, stream);
+  if (r != SIM_OK) return r;
+  return sim_rollout_bwd(h, x0, w, p_ref, H, C, w_act, ws, ws_bytes, dL_one, dW, dx0, stream);
 }
 
 int64_t sim_num_drones(sim_h h) { return h ? h->ntot : -1; }

@@ -1,0 +1,140 @@
+"""GPU parity of the differentiable policy rollout (forward loss, dL/dW and
+dL/dx0 from the hand-written adjoint kernels) against the FP64 oracle, whose
+autograd gradient is itself pinned by central finite differences.  Bar:
+relative error <= 1e-3 (norm-wise, per parameter tensor and per state group)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import policy as po
+from paper_2606_01478_b300 import EULER, FIRST_PRINCIPLES, Sim
+from paper_2606_01478_b300.rollout import PolicyRollout, rollout_loss
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-3
+GROUPS = {"p": slice(0, 3), "q": slice(3, 7), "v": slice(7, 10), "w": slice(10, 13),
+          "W": slice(13, 17)}
+
+
+def _gpu_inputs(rw):
+    sim = Sim(rw.M, 1, FIRST_PRINCIPLES, EULER, rw.dt)
+    sim.set_params(rw.params)
+    runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act)
+    x0 = torch.tensor(rw.x0, dtype=torch.float32, device="cuda")
+    w = torch.tensor(po.pack(rw.weights), dtype=torch.float32, device="cuda")
+    p_ref = torch.tensor(rw.p_ref, dtype=torch.float32, device="cuda").contiguous()
+    return sim, runner, x0, w, p_ref
+
+
+def _as_oracle_inputs(rw):
+    """The FP32-rounded inputs the GPU sees, held exactly in float64."""
+    x0 = rw.x0.astype(np.float32).astype(np.float64)
+    p_ref = rw.p_ref.astype(np.float32).astype(np.float64)
+    return x0, p_ref
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-30))
+
+
+def _check(rw, loss, dW, dx0, drones=None):
+    x0, p_ref = _as_oracle_inputs(rw)
+    sel = np.arange(rw.M) if drones is None else np.asarray(drones)
+    L_ref, per, dW_ref, dx_ref = po.rollout_grad(x0[sel], rw.weights, p_ref[:, sel], rw.params,
+                                                 rw.dt, rw.H, rw.w_act)
+    dx_ref = dx_ref * len(sel) / rw.M  # the GPU loss is the mean over all M drones
+    errs = {}
+    if drones is None:
+        errs["loss"] = abs(loss - L_ref) / abs(L_ref)
+        for k in po.NAMES:
+            errs[k] = _rel(po.unpack(dW)[k], dW_ref[k])
+    for gname, s in GROUPS.items():
+        errs["dx0_" + gname] = _rel(dx0[sel][:, s], dx_ref[:, s])
+    bad = {k: v for k, v in errs.items() if not v <= TOL}
+    assert not bad, f"relative errors above {TOL}: {bad}; all: {errs}"
+    return errs
+
+
+def test_rollout_gradient_small_ragged():
+    """200 drones (ragged last CTA of 8), H = 30, C = 7 (last segment short)."""
+    rw = W.config3(seed=31, M=200, H=30, C=7)
+    sim, runner, x0, w, p_ref = _gpu_inputs(rw)
+    loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
+    assert torch.isfinite(dW).all() and torch.isfinite(dx0).all()
+    _check(rw, loss.item(), dW.cpu().numpy(), dx0.cpu().numpy().astype(np.float64))
+    assert torch.all(dx0[:, 17:20] == 0)
+
+
+@pytest.mark.parametrize("C", [25, 250, 1])
+def test_rollout_gradient_config3_horizon(C):
+    """Config-3 horizon (H = 250 Euler steps at 500 Hz) at 256 drones, with
+    checkpoint intervals 25 (the configured), 250 (one segment) and 1."""
+    rw = W.config3(seed=32, M=256, H=250, C=C)
+    sim, runner, x0, w, p_ref = _gpu_inputs(rw)
+    loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
+    _check(rw, loss.item(), dW.cpu().numpy(), dx0.cpu().numpy().astype(np.float64))
+
+
+def test_rollout_full_config3_sampled_and_linearity():
+    """Full config 3 (8192 drones, H = 250, C = 25): dL/dx0 of 16 sampled
+    drones against the oracle (exact per drone), and dW consistent with the
+    drone-count-weighted gradients of two disjoint halves."""
+    rw = W.config3()
+    sim, runner, x0, w, p_ref = _gpu_inputs(rw)
+    wb = w.to(torch.bfloat16)
+    loss, dW, dx0 = runner.grad(x0, wb, p_ref)
+    sample = np.random.default_rng(9).choice(rw.M, 16, replace=False)
+    _check(rw, loss.item(), dW.cpu().numpy(), dx0.cpu().numpy().astype(np.float64), drones=sample)
+    halves = []
+    for lo, hi in ((0, 4096), (4096, 8192)):
+        s2 = Sim(hi - lo, 1, FIRST_PRINCIPLES, EULER, rw.dt)
+        s2.set_params(rw.params)
+        r2 = PolicyRollout(s2, rw.H, rw.C, rw.w_act)
+        l2, g2, _ = r2.grad(x0[lo:hi].contiguous(), wb, p_ref[:, lo:hi].contiguous())
+        halves.append((l2.item(), g2))
+    comb = 0.5 * (halves[0][1] + halves[1][1])
+    assert _rel(dW.cpu().numpy(), comb.cpu().numpy()) < 1e-5
+    assert abs(loss.item() - 0.5 * (halves[0][0] + halves[1][0])) < 1e-5 * abs(loss.item())
+
+
+def test_rollout_deterministic():
+    rw = W.config3(seed=33, M=300, H=40, C=10)
+    sim, runner, x0, w, p_ref = _gpu_inputs(rw)
+    wb = w.to(torch.bfloat16)
+    a = runner.grad(x0, wb, p_ref)
+    b = runner.grad(x0, wb, p_ref)
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
+
+
+def test_autograd_function_matches_direct_call():
+    rw = W.config3(seed=34, M=128, H=20, C=5)
+    sim, runner, x0, w, p_ref = _gpu_inputs(rw)
+    loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
+    xr = x0.clone().requires_grad_(True)
+    wr = w.clone().requires_grad_(True)
+    L = rollout_loss(xr, wr, runner, p_ref)
+    (3.0 * L).backward()
+    assert torch.allclose(L.detach(), loss[0])
+    # the upstream gradient scales the adjoint seed inside the kernel, so fp32
+    # rounding differs from scaling the unit-seed result afterwards
+    assert _rel(wr.grad.cpu().numpy(), 3.0 * dW.cpu().numpy()) < 1e-5
+    assert _rel(xr.grad.cpu().numpy(), 3.0 * dx0.cpu().numpy()) < 1e-5
+
+
+def test_zero_policy_hover_loss():
+    """Zero weights: a = 0 (hover command); drones at hover on a stationary
+    reference displaced by a constant offset give loss H |offset|^2."""
+    rw = W.config3(seed=35, M=64, H=50, C=10)
+    rw.weights = {k: np.zeros(po.SIZES[k]) for k in po.NAMES}
+    rw.x0[:, 7:13] = 0
+    rw.x0[:, 3:7] = [0, 0, 0, 1]
+    off = np.array([0.05, -0.1, 0.2], dtype=np.float32)
+    rw.p_ref = np.broadcast_to(rw.x0[None, :, 0:3].astype(np.float32) + off,
+                               (rw.H + 1, rw.M, 3)).copy()
+    sim, runner, x0, w, p_ref = _gpu_inputs(rw)
+    loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
+    expect = rw.H * float((off.astype(np.float64) ** 2).sum())
+    assert abs(loss.item() - expect) <= 1e-5 * expect
