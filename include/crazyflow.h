@@ -210,6 +210,27 @@ int sim_rollout_grad(sim_h h, const float* x0, const uint16_t* w, const float* p
                      float w_act, void* ws, size_t ws_bytes, float* loss, const float* dL_one,
                      float* dW, float* dx0, void* stream);
 
+/* sim_rollout_grad without a workspace argument.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory when
+ * they need a gradient -- a control loop with a hard deadline (cudaMalloc can
+ * synchronise the device and take milliseconds) or a plugin whose host
+ * framework owns every device allocation.  It allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library call): the scratch lives in a fixed 8 MiB
+ * device array inside the library, which every GPU that loads the library holds
+ * until the process exits (sim_rollout_noalloc_max_bytes reports the size).
+ * Batches whose rollout workspace (sim_rollout_workspace_bytes) exceeds it are
+ * rejected with SIM_EINVAL and a message, before anything is launched.
+ * The caller still passes inputs and outputs (as for sim_rollout_grad; dL is
+ * fixed to 1).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  All calls share the one array and nothing in it needs
+ * to start at zero (every byte a call reads, the same call wrote first), but
+ * calls that overlap on the GPU -- on different streams or threads -- race on it
+ * and must be serialised by the caller. */
+int sim_rollout_grad_noalloc(sim_h h, const float* x0, const uint16_t* w, const float* p_ref, int H,
+                             int C, float w_act, float* loss, float* dW, float* dx0, void* stream);
+int sim_rollout_noalloc_max_bytes(size_t* bytes);
+
 /* Number of kernel launches issued on this handle since creation (all calls). */
 int64_t sim_launch_count(sim_h h);
 

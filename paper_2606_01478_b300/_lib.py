@@ -56,6 +56,9 @@ _SIGS = {
                                 c_void_p, c_size_t, c_void_p, c_void_p]),
     "sim_rollout_bwd": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_float,
                                 c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sim_rollout_grad_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int,
+                                         c_float, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sim_rollout_noalloc_max_bytes": (c_int, [POINTER(c_size_t)]),
     "sim_rollout_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_float,
                                  c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_void_p,
                                  c_void_p]),

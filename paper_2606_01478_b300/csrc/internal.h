@@ -28,6 +28,10 @@ cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* 
                                int C, float dt, float w_act, const DevParams& P, void* ws,
                                const float* dL, float* dW, float* dx0, cudaStream_t st);
 
+// Record a message as the handle's last error (sim.cu); used by entry points
+// defined in other translation units.
+void note_error(sim_h h, const char* fmt, ...);
+
 // Row-major [n][20] floats <-> 5 float4 planes [5][n] (layout.cu).
 cudaError_t launch_rows_to_planes(const float4* rows, float4* planes, int n, cudaStream_t st);
 cudaError_t launch_planes_to_rows(const float4* planes, float4* rows, int n, cudaStream_t st);

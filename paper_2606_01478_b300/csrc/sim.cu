@@ -190,6 +190,16 @@ int derive_params(const float* p, DevParams* d, char* why, size_t why_n) {
 
 }  // namespace
 
+namespace cf {
+void note_error(sim_h h, const char* fmt, ...) {
+  if (!h) return;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(h->err, sizeof(h->err), fmt, ap);
+  va_end(ap);
+}
+}  // namespace cf
+
 extern "C" {
 
 int sim_create(sim_h* out, int64_t M, int64_t N, int model, int integrator, float dt) {
