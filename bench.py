@@ -347,7 +347,8 @@ def run_b300(args, wl):
     line["config"]["tpb"] = tuned["tpb"]
     line["autotune"] = tuned
     if not args.no_extra:
-        line["extra"] = {"config2": measure_config2(dev)}
+        line["extra"] = {"config2": measure_config2(dev), "config3": measure_config3(dev),
+                         "config4": measure_config4(dev)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)
@@ -415,6 +416,121 @@ def measure_config2(dev, reps: int = 3) -> dict:
     out["workload"] = "c2_1000x4000_mixed_euler_attitude_200"
     out["autotune"] = {k: v for k, v in tuned.items() if k != "table"}
     return out
+
+
+def _time_ms(fn, reps: int, dev) -> float:
+    """Median device time of fn() over reps runs (one untimed warm-up)."""
+    stream = torch.cuda.current_stream(dev)
+    times = []
+    for r in range(reps + 1):
+        torch.cuda._sleep(1_000_000)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        if r:
+            times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
+# MLP FLOPs of one policy evaluation (13 -> 64 -> 64 -> 4): 2 x 5184 multiply-adds.
+MLP_FLOP = 2.0 * (13 * 64 + 64 * 64 + 64 * 4)
+
+
+def measure_config3(dev, reps: int = 3) -> dict:
+    """Config 3 (8192 drones, policy MLP in the loop, Euler at 500 Hz, H = 250,
+    checkpoints every C = 25): forward rollout, forward + adjoint (BPTT), and
+    plain forward stepping of the same drones without the policy."""
+    from paper_2606_01478_b300 import EULER, FIRST_PRINCIPLES, Sim
+    from paper_2606_01478_b300.rollout import PolicyRollout, pack_policy
+    rw = W.config3()
+    sim = Sim(rw.M, 1, FIRST_PRINCIPLES, EULER, rw.dt, device=dev)
+    sim.set_params(rw.params)
+    runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act)
+    x0 = torch.tensor(rw.x0, dtype=torch.float32, device=dev)
+    wb = torch.tensor(pack_policy(rw.weights), dtype=torch.float32, device=dev).to(torch.bfloat16)
+    p_ref = torch.tensor(rw.p_ref, dtype=torch.float32, device=dev).contiguous()
+    loss = torch.empty(1, device=dev)
+    ms_fwd = _time_ms(lambda: runner.forward(x0, wb, p_ref, loss=loss), reps, dev)
+    ms_grad = _time_ms(lambda: runner.grad(x0, wb, p_ref), reps, dev)
+    # plain forward stepping of the same drones (attitude interface, hover commands)
+    sim.set_state(x0)
+    sim.set_commands(torch.zeros(1, rw.M, 4, device=dev), rw.H)
+    ms_plain = _time_ms(lambda: sim.run(rw.H, rw.H), reps, dev)
+    units = rw.M * rw.H
+    pk, kind = peaks()
+    bf16 = pk.get("bf16_tflops", 1800.0)
+    # algorithmic tensor work of forward + backward: policy forward, input-adjoint
+    # and weight-gradient contractions, 3 x 2 x 5184 flop per drone-step
+    grad_flop = 3 * MLP_FLOP * units
+    return {
+        "workload": rw.name,
+        "fwd": {"value": units / (ms_fwd / 1e3), "unit": UNIT, "ms": ms_fwd},
+        "fwd_adjoint": {"value": units / (ms_grad / 1e3), "unit": UNIT, "ms": ms_grad,
+                        "gradients_per_s": rw.M / (ms_grad / 1e3)},
+        "plain_forward_stepping": {"value": units / (ms_plain / 1e3), "unit": UNIT, "ms": ms_plain},
+        "adjoint_over_plain": ms_grad / ms_plain,
+        "roofline_fwd_adjoint": {"bound": "tensor", "achieved": grad_flop / (ms_grad / 1e3) / 1e12,
+                                 "peak": bf16, "unit": "TFLOP/s",
+                                 "frac": grad_flop / (ms_grad / 1e3) / 1e12 / bf16,
+                                 "traffic": None,
+                                 "note": "latency bound: 250 dependent steps, 128 CTAs of 64 drones; "
+                                         "mma.sync bf16 with hi/lo split (2-3 MMAs per product)"},
+    }
+
+
+# FP32 work of one sampled RK4 step: the step (637), the per-step attitude
+# decode (25), noise scaling and Box-Muller (15), goal distance (10) and 32
+# obstacle tests (8 each) -- Philox integer work and MUFU calls not counted.
+SAMPLE_FLOP_PER_STEP_32OBS = 637.0 + 25.0 + 15.0 + 10.0 + 8.0 * 32
+
+
+def measure_config4(dev, reps: int = 3) -> dict:
+    """Config 4 (512 worlds, log-uniform drone counts, 256 samples, 50 RK4
+    steps): one persistent sampling launch per outer iteration, replayed from a
+    CUDA graph with a fresh device seed each time; block size autotuned."""
+    from paper_2606_01478_b300 import RK4, Sim
+    wl = W.config4()
+    n = len(wl.x0)
+    sim = Sim.batched(wl.n_per_world, np.zeros(wl.M, np.int32), RK4, wl.dt, device=dev)
+    sim.set_params(wl.params)
+    sim.set_state(torch.tensor(wl.x0, dtype=torch.float32, device=dev))
+    goals = torch.tensor(wl.goals, dtype=torch.float32, device=dev)
+    seed = torch.tensor([wl.seed], dtype=torch.int64, device=dev)
+    cost = torch.empty(n, wl.S, device=dev)
+    best = None
+    for tpb in (64, 128, 256):
+        sim.set_block_size(tpb)
+        ms = _time_ms(lambda: sim.sample_rollouts(wl.S, wl.H, seed, wl.sigma, goals, wl.obstacles,
+                                                  wl.w_obs, cost=cost), 1, dev)
+        if best is None or ms < best[1]:
+            best = (tpb, ms)
+    sim.set_block_size(best[0])
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream(dev)
+    st.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            sim.sample_rollouts(wl.S, wl.H, seed, wl.sigma, goals, wl.obstacles, wl.w_obs,
+                                cost=cost, stream=st)
+    torch.cuda.current_stream(dev).wait_stream(st)
+
+    def replay():
+        seed.add_(1)
+        g.replay()
+    ms = _time_ms(replay, reps, dev)
+    units = n * wl.S * wl.H
+    pk, _ = peaks()
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    achieved = SAMPLE_FLOP_PER_STEP_32OBS * units / (ms / 1e3) / 1e12
+    return {"workload": wl.name, "drones": n, "samples_per_drone": wl.S, "horizon": wl.H,
+            "value": units / (ms / 1e3), "unit": UNIT, "ms_per_outer_iteration": ms,
+            "rollouts_per_s": n * wl.S / (ms / 1e3), "tpb": best[0],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "flop_per_sample_step": SAMPLE_FLOP_PER_STEP_32OBS}}
 
 
 def main(argv=None):

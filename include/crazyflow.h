@@ -171,6 +171,40 @@ const char* sim_last_error(sim_h h); /* message of the last failure ("" if none)
 void sim_destroy(sim_h h);           /* frees the host handle; the workspace stays the caller's */
 
 /* ---------------------------------------------------------------------------
+ * Batched sampling rollouts: the forward model of the paper's MPPI / iCEM
+ * sampling controller (Materials and Methods, Model Predictive Path Integral;
+ * Results, Control in Cluttered Environments).  Every drone of the handle
+ * expands S sampled command sequences over H steps, starting from its current
+ * state (the state is read, not modified).  For drone d of world w, sample s,
+ * step k = 0 .. H-1:
+ *   xi  = 4 standard normals: Philox4x32-10 (Salmon et al., SC'11) with counter
+ *         (id mod 2^32, id / 2^32, k, 0), key (seed mod 2^32, seed / 2^32),
+ *         id = d*S + s; u = ((word >> 9) + 0.5) 2^-23; Box-Muller on word pairs
+ *         (0,1) and (2,3)
+ *   a   = clip(nominal[w][k] + sigma xi, -1, 1)   (attitude interface)
+ *   x   <- one step of the handle's integrator (first-principles model)
+ *   cost[d][s] += |p - goal[w]| + w_obs sum_o max(0, r_o - |p - c_o|)
+ * Requires every drone to be first-principles and the attitude interface.
+ *   seed      device uint64 (read by the kernel: a captured graph replays with
+ *             whatever the device word holds)
+ *   nominal   device [M][H][4] float, or NULL for zero (hover)
+ *   goals     device [M][3] float
+ *   obstacles HOST [n_obs][4] float (centre xyz, radius >= 0), read during the
+ *             call and passed by value; 0 <= n_obs <= SIM_MAX_OBSTACLES
+ *   cost      device [Ntot][S] float (output)
+ * One persistent kernel launch; no scratch memory. */
+#define SIM_MAX_OBSTACLES 64
+/* The sampling noise on its own: for ids first_id .. first_id + n - 1 at step
+ * `step`, writes the four Philox4x32-10 words (device uint32 [n][4], or NULL)
+ * and the four normals (device float [n][4], or NULL) exactly as the sampling
+ * kernel draws them.  seed: device uint64.  Needs no handle. */
+int sim_philox_normals(const uint64_t* seed, uint64_t first_id, int64_t n, int step, uint32_t* words,
+                       float* normals, void* stream);
+int sim_sample_rollouts(sim_h h, int S, int H, const uint64_t* seed, float sigma,
+                        const float* nominal, const float* goals, const float* obstacles,
+                        int n_obs, float w_obs, float* cost, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Differentiable policy rollout (backpropagation through time; Materials and
  * Methods, Backpropagation Through Time).  For every drone of the handle,
  * independently:

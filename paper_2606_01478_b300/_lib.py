@@ -19,6 +19,7 @@ EULER, RK4 = 0, 1
 CTRL_ROTOR_SPEED, CTRL_ATTITUDE, CTRL_POSITION = 0, 1, 2
 STATE_DIM, CMD_DIM, NPARAMS = 20, 4, 48
 POLICY_NPARAMS = 5316
+MAX_OBSTACLES = 64
 
 # Order of enum sim_param_index in include/crazyflow.h (checked by a CPU test).
 PARAM_ORDER = (
@@ -51,6 +52,10 @@ _SIGS = {
     "sim_step_count": (c_int64, [c_void_p]),
     "sim_set_step_count": (c_int, [c_void_p, c_int64]),
     "sim_launch_count": (c_int64, [c_void_p]),
+    "sim_sample_rollouts": (c_int, [c_void_p, c_int, c_int, c_void_p, c_float, c_void_p, c_void_p,
+                                    POINTER(c_float), c_int, c_float, c_void_p, c_void_p]),
+    "sim_philox_normals": (c_int, [c_void_p, ctypes.c_uint64, c_int64, c_int, c_void_p, c_void_p,
+                                   c_void_p]),
     "sim_rollout_workspace_bytes": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),
     "sim_rollout_fwd": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_float,
                                 c_void_p, c_size_t, c_void_p, c_void_p]),

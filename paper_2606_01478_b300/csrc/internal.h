@@ -28,6 +28,17 @@ cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* 
                                int C, float dt, float w_act, const DevParams& P, void* ws,
                                const float* dL, float* dW, float* dx0, cudaStream_t st);
 
+// Batched sampling rollouts (sample.cu).
+cudaError_t launch_sample(const float4* planes, int n, const int* offsets, int M, int N,
+                          const float* goals, const float* nominal, const unsigned long long* seed,
+                          const DevParams* params, const int32_t* set_of_world, const DevParams& P0,
+                          bool per_set, bool general_motor, int integrator, const float* obstacles,
+                          int n_obs, float w_obs, float sigma, float dt, int S, int H, float* cost,
+                          int tpb, cudaStream_t st);
+
+cudaError_t launch_philox(const unsigned long long* seed, unsigned long long first_id, long long n,
+                          int step, uint32_t* words, float* normals, cudaStream_t st);
+
 // Record a message as the handle's last error (sim.cu); used by entry points
 // defined in other translation units.
 void note_error(sim_h h, const char* fmt, ...);

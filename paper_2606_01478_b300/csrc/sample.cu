@@ -1,0 +1,242 @@
+// Batched sampling rollouts: the forward model of the paper's MPPI / iCEM
+// controller (Results, Control in Cluttered Environments; Materials and
+// Methods, Model Predictive Path Integral), which evaluates many sampled
+// command sequences per control step with the full simulation.
+//
+// One rollout (drone d, sample s) per thread of a persistent grid.  Per step k:
+//   xi = 4 normals: Philox4x32-10 (Salmon et al., SC'11) on counter
+//        (id_lo, id_hi, k, 0), key = 64-bit seed, id = d * S + s; Box-Muller on
+//        the top 23 bits of each word
+//   a  = clip(nominal[w][k] + sigma xi, -1, 1)  (attitude interface)
+//   one first-principles step (Euler or RK4) from the drone's current state
+//   cost += |p - g_w| + w_obs sum_o max(0, r_o - |p - c_o|)
+// The S samples of a drone are consecutive threads, so the drone's state,
+// goal and parameters are broadcast loads; the obstacles live in kernel
+// parameter space (constant bank).
+#include "internal.h"
+#include "stepcore.cuh"
+
+namespace cf {
+namespace sp {
+
+struct Scene {
+  float4 obs[SIM_MAX_OBSTACLES];  // centre xyz, radius
+  float r2[SIM_MAX_OBSTACLES];    // radius^2
+  int n_obs;
+  float w_obs, sigma, dt;
+  int S, H;
+};
+
+struct Args {
+  const float4* planes;  // [5][n] drone states (read only)
+  const int* offsets;    // [M + 1] first drone of each world (uneven batches) or null
+  const float* goals;    // [M][3]
+  const float* nominal;  // [M][H][4] or null (zero)
+  const unsigned long long* seed;
+  const DevParams* params;
+  const int32_t* set_of_world;
+  float* cost;  // [n][S]
+  long long total;
+  int n, M, N;
+};
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// Two standard normals from two words: u = ((w >> 9) + 0.5) 2^-23 (exact),
+// r = sqrt(-2 ln u1), angle 2 pi u2 (evaluated as 2 pi u2 - pi, in [-pi, pi)).
+__device__ __forceinline__ float2 box_muller(uint32_t w1, uint32_t w2) {
+  const float u1 = ((float)(w1 >> 9) + 0.5f) * 1.1920928955078125e-07f;
+  const float u2 = ((float)(w2 >> 9) + 0.5f) * 1.1920928955078125e-07f;
+  const float r = sqrtf(-2.f * logf(u1));
+  float s, c;
+  __sincosf(fmaf(6.28318530717958648f, u2, -3.14159265358979324f), &s, &c);
+  return make_float2(-r * c, -r * s);
+}
+
+template <int INTEG, int MOTOR>
+__device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const DevParams& P,
+                                         long long r, int d, int w, uint32_t k0, uint32_t k1) {
+  float s[20];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const float4 v = a.planes[(size_t)j * a.n + d];
+    s[4 * j] = v.x;
+    s[4 * j + 1] = v.y;
+    s[4 * j + 2] = v.z;
+    s[4 * j + 3] = v.w;
+  }
+  const float gx = a.goals[3 * w], gy = a.goals[3 * w + 1], gz = a.goals[3 * w + 2];
+  const bool drag = (P.flags & PF_DRAG) != 0;
+  const uint32_t id_lo = (uint32_t)r, id_hi = (uint32_t)((unsigned long long)r >> 32);
+  const float4* nom = a.nominal ? reinterpret_cast<const float4*>(a.nominal) + (size_t)w * sc.H : nullptr;
+  float cost = 0.f;
+  for (int k = 0; k < sc.H; ++k) {
+    uint32_t c[4] = {id_lo, id_hi, (uint32_t)k, 0u};
+    philox4x32_10(c, k0, k1);
+    const float2 z01 = box_muller(c[0], c[1]);
+    const float2 z23 = box_muller(c[2], c[3]);
+    float4 act = make_float4(sc.sigma * z01.x, sc.sigma * z01.y, sc.sigma * z23.x, sc.sigma * z23.y);
+    if (nom) {
+      const float4 m = nom[k];
+      act.x += m.x;
+      act.y += m.y;
+      act.z += m.z;
+      act.w += m.w;
+    }
+    CtrlHold h;
+    decode_command<SIM_FIRST_PRINCIPLES, SIM_CTRL_ATTITUDE>(act, P, h);
+    one_step<SIM_FIRST_PRINCIPLES, INTEG, SIM_CTRL_ATTITUDE, MOTOR>(s, h, P, drag, sc.dt);
+    const float ex = s[0] - gx, ey = s[1] - gy, ez = s[2] - gz;
+    float pen = 0.f;
+    for (int o = 0; o < sc.n_obs; ++o) {
+      const float4 ob = sc.obs[o];
+      const float dx = s[0] - ob.x, dy = s[1] - ob.y, dz = s[2] - ob.z;
+      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (d2 < sc.r2[o]) pen += ob.w - sqrt_approx(d2);
+    }
+    cost += sqrt_approx(fmaf(ex, ex, fmaf(ey, ey, ez * ez))) + sc.w_obs * pen;
+  }
+  return cost;
+}
+
+template <int INTEG, int MOTOR, bool PERSET>
+__global__ void __launch_bounds__(256) sample_kernel(Args a, Scene sc, DevParams P0) {
+  const unsigned long long seed = *a.seed;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < a.total; r += stride) {
+    const int d = (int)(r / sc.S);
+    int w;
+    if (a.offsets) {  // largest w with offsets[w] <= d
+      int lo = 0, hi = a.M - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.offsets[mid] <= d) lo = mid;
+        else hi = mid - 1;
+      }
+      w = lo;
+    } else {
+      w = d / a.N;
+    }
+    float cost;
+    if constexpr (PERSET) {
+      const DevParams P = a.params[a.set_of_world[w]];
+      cost = rollout<INTEG, MOTOR>(a, sc, P, r, d, w, k0, k1);
+    } else {
+      cost = rollout<INTEG, MOTOR>(a, sc, P0, r, d, w, k0, k1);
+    }
+    a.cost[r] = cost;
+  }
+}
+
+template <int INTEG, int MOTOR, bool PERSET>
+static cudaError_t launch_t(const Args& a, const Scene& sc, const DevParams& P, int tpb,
+                            cudaStream_t st) {
+  static int cached[16][9] = {};
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int slot = tpb / 32;
+  int per_sm = (dev < 16 && slot <= 8) ? cached[dev][slot] : 0;
+  if (per_sm == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_kernel<INTEG, MOTOR, PERSET>, tpb, 0);
+    if (per_sm < 1) per_sm = 1;
+    if (dev < 16 && slot <= 8) cached[dev][slot] = per_sm;
+  }
+  long long grid = (long long)sms * per_sm;
+  const long long need = (a.total + tpb - 1) / tpb;
+  if (grid > need) grid = need;
+  sample_kernel<INTEG, MOTOR, PERSET><<<(unsigned)grid, tpb, 0, st>>>(a, sc, P);
+  return cudaGetLastError();
+}
+
+__global__ void philox_kernel(const unsigned long long* seed, unsigned long long first_id, long long n,
+                              int step, uint32_t* words, float* normals) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long s = *seed, id = first_id + (unsigned long long)i;
+  uint32_t c[4] = {(uint32_t)id, (uint32_t)(id >> 32), (uint32_t)step, 0u};
+  philox4x32_10(c, (uint32_t)s, (uint32_t)(s >> 32));
+  if (words) {
+    words[4 * i] = c[0];
+    words[4 * i + 1] = c[1];
+    words[4 * i + 2] = c[2];
+    words[4 * i + 3] = c[3];
+  }
+  if (normals) {
+    const float2 a = box_muller(c[0], c[1]), b = box_muller(c[2], c[3]);
+    normals[4 * i] = a.x;
+    normals[4 * i + 1] = a.y;
+    normals[4 * i + 2] = b.x;
+    normals[4 * i + 3] = b.y;
+  }
+}
+
+}  // namespace sp
+
+cudaError_t launch_philox(const unsigned long long* seed, unsigned long long first_id, long long n,
+                          int step, uint32_t* words, float* normals, cudaStream_t st) {
+  const int tpb = 256;
+  sp::philox_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(seed, first_id, n, step, words,
+                                                                     normals);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const float4* planes, int n, const int* offsets, int M, int N,
+                          const float* goals, const float* nominal, const unsigned long long* seed,
+                          const DevParams* params, const int32_t* set_of_world, const DevParams& P0,
+                          bool per_set, bool general_motor, int integrator, const float* obstacles,
+                          int n_obs, float w_obs, float sigma, float dt, int S, int H, float* cost,
+                          int tpb, cudaStream_t st) {
+  sp::Args a;
+  a.planes = planes;
+  a.offsets = offsets;
+  a.goals = goals;
+  a.nominal = nominal;
+  a.seed = seed;
+  a.params = params;
+  a.set_of_world = set_of_world;
+  a.cost = cost;
+  a.total = (long long)n * S;
+  a.n = n;
+  a.M = M;
+  a.N = N;
+  sp::Scene sc;
+  for (int o = 0; o < SIM_MAX_OBSTACLES; ++o) {
+    sc.obs[o] = o < n_obs ? make_float4(obstacles[4 * o], obstacles[4 * o + 1], obstacles[4 * o + 2],
+                                        obstacles[4 * o + 3])
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+    sc.r2[o] = o < n_obs ? obstacles[4 * o + 3] * obstacles[4 * o + 3] : 0.f;
+  }
+  sc.n_obs = n_obs;
+  sc.w_obs = w_obs;
+  sc.sigma = sigma;
+  sc.dt = dt;
+  sc.S = S;
+  sc.H = H;
+#define CF_S(I, MO)                                                       \
+  return per_set ? sp::launch_t<I, MO, true>(a, sc, P0, tpb, st)           \
+                 : sp::launch_t<I, MO, false>(a, sc, P0, tpb, st)
+  if (integrator == SIM_RK4) {
+    if (general_motor) CF_S(SIM_RK4, MOTOR_GENERAL);
+    CF_S(SIM_RK4, MOTOR_LAG);
+  }
+  if (general_motor) CF_S(SIM_EULER, MOTOR_GENERAL);
+  CF_S(SIM_EULER, MOTOR_LAG);
+#undef CF_S
+}
+
+}  // namespace cf

@@ -26,6 +26,7 @@ struct sim_s {
   std::vector<int64_t> n_per_world, offset;
   std::vector<int32_t> model_of_world;
   std::vector<int4> tiles;  // uneven batches: (first drone, count <= 32, world, model)
+  std::vector<int32_t> offsets32;  // uneven batches: first drone of each world, [M + 1]
   // workspace (caller-owned device memory)
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -37,6 +38,7 @@ struct sim_s {
   float4* staging = nullptr;
   uint32_t* status = nullptr;
   int4* tiles_dev = nullptr;
+  int32_t* offsets_dev = nullptr;
   // host copies
   std::vector<DevParams> params_host;
   DevParams p0;  // the single set of a uniform batch, passed by value
@@ -68,7 +70,7 @@ int cuda_fail(sim_h h, cudaError_t e, const char* what) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t planes, params, set_of_world, cmd, staging, status, tiles, total;
+  size_t planes, params, set_of_world, cmd, staging, status, tiles, offsets, total;
 };
 
 Layout layout_of(const sim_s* h, int64_t max_blocks) {
@@ -88,6 +90,8 @@ Layout layout_of(const sim_s* h, int64_t max_blocks) {
   off = align256(off + sizeof(uint32_t));
   L.tiles = off;
   off = align256(off + h->tiles.size() * sizeof(int4));
+  L.offsets = off;
+  off = align256(off + h->offsets32.size() * sizeof(int32_t));
   L.total = off;
   return L;
 }
@@ -252,6 +256,7 @@ int sim_create_batched(sim_h* out, int64_t M, const int64_t* n_per_world,
       h->tiles.push_back(make_int4((int)(h->offset[w] + s), (int)c, (int)w, model_per_world[w]));
     }
   }
+  h->offsets32.assign(h->offset.begin(), h->offset.end());
   *out = h;
   return SIM_OK;
 }
@@ -293,12 +298,16 @@ int sim_bind(sim_h h, void* workspace, size_t bytes, int64_t max_cmd_blocks, voi
   h->staging = (float4*)(ws + L.staging);
   h->status = (uint32_t*)(ws + L.status);
   h->tiles_dev = (int4*)(ws + L.tiles);
+  h->offsets_dev = (int32_t*)(ws + L.offsets);
   h->params_ok = h->state_ok = false;
   h->n_blocks = 0;
   h->t = 0;
   cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(uint32_t), (cudaStream_t)stream);
   if (e == cudaSuccess && !h->tiles.empty())
     e = cudaMemcpyAsync(h->tiles_dev, h->tiles.data(), h->tiles.size() * sizeof(int4),
+                        cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  if (e == cudaSuccess && !h->offsets32.empty())
+    e = cudaMemcpyAsync(h->offsets_dev, h->offsets32.data(), h->offsets32.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "initialising the workspace");
   return SIM_OK;
@@ -464,6 +473,51 @@ int sim_status(sim_h h, uint32_t* flags, void* stream) {
   if (e != cudaSuccess) return cuda_fail(h, e, "reading the status word");
   *flags = v;
   return SIM_OK;
+}
+
+// ---------------------------------------------------------------- sampling rollouts
+
+int sim_sample_rollouts(sim_h h, int S, int H, const uint64_t* seed, float sigma,
+                        const float* nominal, const float* goals, const float* obstacles,
+                        int n_obs, float w_obs, float* cost, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!h->ws || !h->params_ok || !h->state_ok)
+    return fail(h, SIM_ESTATE, "bind, parameters and state must be set before sampling");
+  bool all_fp = h->batched ? true : h->model == SIM_FIRST_PRINCIPLES;
+  for (int32_t m : h->model_of_world) all_fp &= (m == SIM_FIRST_PRINCIPLES);
+  if (!all_fp) return fail(h, SIM_EINVAL, "sampling rollouts need first-principles drones");
+  if (h->ctrl != SIM_CTRL_ATTITUDE)
+    return fail(h, SIM_EINVAL, "sampling rollouts use the attitude interface");
+  if (S < 1 || H < 1 || n_obs < 0 || n_obs > SIM_MAX_OBSTACLES || !(sigma >= 0.f) ||
+      !isfinite(sigma) || !isfinite(w_obs))
+    return fail(h, SIM_EINVAL, "need S, H >= 1, 0 <= n_obs <= %d, finite sigma >= 0",
+                SIM_MAX_OBSTACLES);
+  if ((double)h->ntot * S > 4.0e18) return fail(h, SIM_EINVAL, "too many rollouts");
+  if (!seed || ((uintptr_t)seed & 7) || !goals || ((uintptr_t)goals & 3) || !cost ||
+      ((uintptr_t)cost & 3) || (nominal && ((uintptr_t)nominal & 15)) || (n_obs > 0 && !obstacles))
+    return fail(h, SIM_EINVAL, "bad or misaligned buffer");
+  for (int o = 0; o < n_obs; ++o) {
+    for (int j = 0; j < 4; ++j)
+      if (!isfinite(obstacles[4 * o + j])) return fail(h, SIM_EINVAL, "obstacle %d not finite", o);
+    if (obstacles[4 * o + 3] < 0.f) return fail(h, SIM_EINVAL, "obstacle %d has a negative radius", o);
+  }
+  cudaError_t e = cf::launch_sample(
+      h->planes, (int)h->ntot, h->batched ? h->offsets_dev : nullptr, (int)h->M, (int)h->N, goals,
+      nominal, (const unsigned long long*)seed, h->params_dev, h->set_of_world_dev, h->p0,
+      h->per_set || h->batched, h->general_motor, h->integrator, obstacles, n_obs, w_obs, sigma,
+      h->dt, S, H, cost, h->tpb, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sampling launch");
+  h->launches++;
+  return SIM_OK;
+}
+
+int sim_philox_normals(const uint64_t* seed, uint64_t first_id, int64_t n, int step, uint32_t* words,
+                       float* normals, void* stream) {
+  if (!seed || ((uintptr_t)seed & 7) || n < 0 || step < 0 || (!words && !normals)) return SIM_EINVAL;
+  if (n == 0) return SIM_OK;
+  cudaError_t e = cf::launch_philox((const unsigned long long*)seed, first_id, n, step, words, normals,
+                                    (cudaStream_t)stream);
+  return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
 }
 
 // ---------------------------------------------------------------- rollout (BPTT)

@@ -18,6 +18,23 @@ from . import _lib as L
 from .sim import _stream_ptr
 
 
+POLICY_ORDER = (("W1", (64, 13)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)),
+                ("W3", (4, 64)), ("b3", (4,)))
+
+
+def pack_policy(weights: dict):
+    """Flatten {W1, b1, W2, b2, W3, b3} (row-major) into the packed vector of
+    SIM_POLICY_NPARAMS = 5316 values the rollout entry points take."""
+    import numpy as np
+    parts = []
+    for name, shape in POLICY_ORDER:
+        a = np.asarray(weights[name], dtype=np.float64)
+        if a.shape != shape:
+            raise ValueError(f"{name} must have shape {shape}")
+        parts.append(a.ravel())
+    return np.concatenate(parts)
+
+
 def _p(t: torch.Tensor) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr())
 

@@ -151,6 +151,28 @@ class Sim:
         self._check(self.lib.sim_set_step_count(self.h, t0))
         return g
 
+    def sample_rollouts(self, S: int, H: int, seed: torch.Tensor, sigma: float, goals: torch.Tensor,
+                        obstacles, w_obs: float, nominal: torch.Tensor | None = None,
+                        cost: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Costs [Ntot, S] of S sampled command sequences per drone over H steps
+        (see sim_sample_rollouts).  seed: int64 device tensor of one element
+        (its bits are the 64-bit Philox key); obstacles: [n_obs, 4] host array."""
+        if seed.dtype != torch.int64 or seed.numel() != 1 or not seed.is_cuda:
+            raise ValueError("seed must be a one-element int64 CUDA tensor")
+        if goals.dtype != torch.float32 or not goals.is_contiguous() or goals.dim() != 2 or goals.shape[1] != 3:
+            raise ValueError("goals must be contiguous float32 [M, 3]")
+        obs = np.ascontiguousarray(np.asarray(obstacles, dtype=np.float32).reshape(-1, 4))
+        if cost is None:
+            cost = torch.empty(self.ntot, int(S), dtype=torch.float32, device=self.device)
+        if nominal is not None and (nominal.dtype != torch.float32 or not nominal.is_contiguous()):
+            raise ValueError("nominal must be contiguous float32 [M, H, 4]")
+        self._check(self.lib.sim_sample_rollouts(
+            self.h, int(S), int(H), ctypes.c_void_p(seed.data_ptr()), float(sigma),
+            None if nominal is None else ctypes.c_void_p(nominal.data_ptr()),
+            ctypes.c_void_p(goals.data_ptr()), obs.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+            obs.shape[0], float(w_obs), ctypes.c_void_p(cost.data_ptr()), _stream_ptr(stream)))
+        return cost
+
     def status(self, stream=None) -> int:
         v = ctypes.c_uint32()
         self._check(self.lib.sim_status(self.h, ctypes.byref(v), _stream_ptr(stream)))
