@@ -541,10 +541,19 @@ def main(argv=None):
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--tpb", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the config-2 measurements")
+    ap.add_argument("--no-extra", action="store_true", help="skip the config-2/3/4 measurements")
+    ap.add_argument("--only", choices=["c2", "c3", "c4"], default=None,
+                    help="run one extra workload alone and print its record (for profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.only:
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        fn = {"c2": measure_config2, "c3": measure_config3, "c4": measure_config4}[args.only]
+        print(json.dumps({"only": args.only, "record": fn(dev, reps=args.steps)}), flush=True)
+        return 0
     rank = int(os.environ.get("RANK", "0"))
     wl = W.config1(seed=1001 + 7919 * rank)
     if args.impl == "reference":
