@@ -111,10 +111,19 @@ class ClockSampler:
 # --------------------------------------------------------------------------- helpers
 
 
-def _src_hash() -> str:
+# Source files each profiled kernel is built from.
+KERNEL_SOURCES = {
+    "step_kernel": ("step.cu", "stepcore.cuh", "physics.cuh", "common.cuh"),
+    "step_batched_kernel": ("step.cu", "stepcore.cuh", "physics.cuh", "common.cuh"),
+    "rollout_bwd_kernel": ("rollout.cu", "physics.cuh", "common.cuh"),
+    "sample_kernel": ("sample.cu", "stepcore.cuh", "physics.cuh", "common.cuh"),
+}
+
+
+def _src_hash(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_01478_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -122,13 +131,13 @@ def _src_hash() -> str:
 
 def _profiled_traffic(kernel: str, workload: str):
     """Per-launch DRAM bytes from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+    on the current sources of that kernel (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         rec = json.load(f).get(f"{kernel}:{workload}")
-    if not rec or rec.get("src_hash") != _src_hash():
+    if not rec or rec.get("src_hash") != _src_hash(kernel):
         return None
     return rec.get("bytes_per_launch")
 
@@ -409,7 +418,8 @@ def measure_config2(dev, reps: int = 3) -> dict:
             peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
             achieved = flop * wl.steps / (ms / 1e3) / 1e12
             rec["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak,
-                               "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                               "unit": "TFLOP/s", "frac": achieved / peak,
+                               "traffic": _profiled_traffic("step_batched_kernel", wl.name),
                                "note": "abstracted drones also issue 6 MUFU sin/cos per step"}
         out[f"fused_K{K}" if K > 1 else "single_step_K1"] = rec
     assert sim.status() == 0
@@ -475,16 +485,18 @@ def measure_config3(dev, reps: int = 3) -> dict:
         "roofline_fwd_adjoint": {"bound": "tensor", "achieved": grad_flop / (ms_grad / 1e3) / 1e12,
                                  "peak": bf16, "unit": "TFLOP/s",
                                  "frac": grad_flop / (ms_grad / 1e3) / 1e12 / bf16,
-                                 "traffic": None,
+                                 "traffic": _profiled_traffic("rollout_bwd_kernel", rw.name),
                                  "note": "latency bound: 250 dependent steps, 128 CTAs of 64 drones; "
                                          "mma.sync bf16 with hi/lo split (2-3 MMAs per product)"},
     }
 
 
 # FP32 work of one sampled RK4 step: the step (637), the per-step attitude
-# decode (25), noise scaling and Box-Muller (15), goal distance (10) and 32
-# obstacle tests (8 each) -- Philox integer work and MUFU calls not counted.
-SAMPLE_FLOP_PER_STEP_32OBS = 637.0 + 25.0 + 15.0 + 10.0 + 8.0 * 32
+# decode (25), noise scaling and Box-Muller (15) and the goal distance (10).
+# Obstacle tests are not counted: the kernel drops obstacles outside a drone's
+# reach bound (exact zeros), leaving almost none; Philox integer work and MUFU
+# calls are not counted either.  ncu measures 773 executed flop per sample-step.
+SAMPLE_FLOP_PER_STEP = 637.0 + 25.0 + 15.0 + 10.0
 
 
 def measure_config4(dev, reps: int = 3) -> dict:
@@ -524,13 +536,14 @@ def measure_config4(dev, reps: int = 3) -> dict:
     units = n * wl.S * wl.H
     pk, _ = peaks()
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-    achieved = SAMPLE_FLOP_PER_STEP_32OBS * units / (ms / 1e3) / 1e12
+    achieved = SAMPLE_FLOP_PER_STEP * units / (ms / 1e3) / 1e12
     return {"workload": wl.name, "drones": n, "samples_per_drone": wl.S, "horizon": wl.H,
             "value": units / (ms / 1e3), "unit": UNIT, "ms_per_outer_iteration": ms,
             "rollouts_per_s": n * wl.S / (ms / 1e3), "tpb": best[0],
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "flop_per_sample_step": SAMPLE_FLOP_PER_STEP_32OBS}}
+                         "frac": achieved / peak,
+                         "traffic": _profiled_traffic("sample_kernel", wl.name),
+                         "flop_per_sample_step": SAMPLE_FLOP_PER_STEP}}
 
 
 def main(argv=None):

@@ -62,9 +62,10 @@ __device__ __forceinline__ float motor_rate(float W, float Wc, const DevParams& 
 // First-principles derivative (Eqs. 1-4 with the rotor wrench and Eq. 6) of
 // x[0..16] for held rotor commands Wc.  Rotor i at (sx_i a, sy_i a) with
 // sx = (+,-,-,+), sy = (-,-,+,+), yaw sign s = (-,+,-,+).
+// Rc: optional R(q) of this very x (row-major 9), e.g. from the controller.
 template <int MOTOR>
 __device__ __forceinline__ void deriv_fp(const float* x, const float Wc[4], const DevParams& P,
-                                         bool drag, float* d) {
+                                         bool drag, float* d, const float* Rc = nullptr) {
   const float qx = x[3], qy = x[4], qz = x[5], qw = x[6];
   const float wx = x[10], wy = x[11], wz = x[12];
   const float s0 = x[13] * x[13], s1 = x[14] * x[14], s2 = x[15] * x[15], s3 = x[16] * x[16];
@@ -74,13 +75,18 @@ __device__ __forceinline__ void deriv_fp(const float* x, const float Wc[4], cons
   const float tz = P.km * ((s1 + s3) - (s0 + s2));
   // thrust along the third column of R(q)
   const float Tm = T * P.inv_m;
-  const float r02 = 2.f * fmaf(qx, qz, qw * qy);
-  const float r12 = 2.f * fmaf(qy, qz, -qw * qx);
-  const float r22 = (qw * qw + qz * qz) - (qx * qx + qy * qy);
+  const float r02 = Rc ? Rc[2] : 2.f * fmaf(qx, qz, qw * qy);
+  const float r12 = Rc ? Rc[5] : 2.f * fmaf(qy, qz, -qw * qx);
+  const float r22 = Rc ? Rc[8] : (qw * qw + qz * qz) - (qx * qx + qy * qy);
   float ax = Tm * r02, ay = Tm * r12, az = fmaf(Tm, r22, -P.g);
   if (drag) {
     float R[9];
-    quat_rot(qx, qy, qz, qw, R);
+    if (Rc) {
+#pragma unroll
+      for (int j = 0; j < 9; ++j) R[j] = Rc[j];
+    } else {
+      quat_rot(qx, qy, qz, qw, R);
+    }
     const float vx = x[7], vy = x[8], vz = x[9];
     const float bx = P.Ca_x * P.inv_m * (R[0] * vx + R[3] * vy + R[6] * vz);
     const float by = P.Ca_y * P.inv_m * (R[1] * vx + R[4] * vy + R[7] * vz);

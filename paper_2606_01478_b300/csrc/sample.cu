@@ -82,6 +82,27 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
   const bool drag = (P.flags & PF_DRAG) != 0;
   const uint32_t id_lo = (uint32_t)r, id_hi = (uint32_t)((unsigned long long)r >> 32);
   const float4* nom = a.nominal ? reinterpret_cast<const float4*>(a.nominal) + (size_t)w * sc.H : nullptr;
+  // Obstacles the drone cannot reach within the horizon contribute exactly 0 to
+  // every step's penalty and are skipped.  Reach bound: |v0| T + A T^2 with
+  // A >= |p''| = |(T_rotor/m) R e_z - g e_z| <= 4 kf W_max^2 / m + g, valid for
+  // Euler and RK4 (both move p by at most T|v0| + A T^2 / 2) when the rotor
+  // speeds stay within [0, max(W_max, W_0)]: first-order-lag rotors with
+  // dt * cv <= 1 and no drag.  Otherwise every obstacle is tested.
+  unsigned long long cand = sc.n_obs >= 64 ? ~0ull : ((1ull << sc.n_obs) - 1ull);
+  if (MOTOR == MOTOR_LAG && !drag && sc.dt * P.cv_up <= 1.f) {
+    const float wmax = fmaxf(fmaxf(P.omega_max, fmaxf(s[13], s[14])), fmaxf(s[15], s[16]));
+    const float acc = 4.f * P.kf * wmax * wmax * P.inv_m * 1.01f + P.g;
+    const float T = sc.H * sc.dt;
+    const float v0 = sqrtf(fmaf(s[7], s[7], fmaf(s[8], s[8], s[9] * s[9])));
+    const float reach = fmaf(T, v0, acc * T * T) * 1.01f + 1e-3f;
+    cand = 0ull;
+    for (int o = 0; o < sc.n_obs; ++o) {
+      const float4 ob = sc.obs[o];
+      const float dx = s[0] - ob.x, dy = s[1] - ob.y, dz = s[2] - ob.z;
+      const float lim = ob.w + reach;
+      if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < lim * lim) cand |= 1ull << o;
+    }
+  }
   float cost = 0.f;
   for (int k = 0; k < sc.H; ++k) {
     uint32_t c[4] = {id_lo, id_hi, (uint32_t)k, 0u};
@@ -101,7 +122,8 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
     one_step<SIM_FIRST_PRINCIPLES, INTEG, SIM_CTRL_ATTITUDE, MOTOR>(s, h, P, drag, sc.dt);
     const float ex = s[0] - gx, ey = s[1] - gy, ez = s[2] - gz;
     float pen = 0.f;
-    for (int o = 0; o < sc.n_obs; ++o) {
+    for (unsigned long long m = cand; m; m &= m - 1ull) {
+      const int o = __ffsll((long long)m) - 1;
       const float4 ob = sc.obs[o];
       const float dx = s[0] - ob.x, dy = s[1] - ob.y, dz = s[2] - ob.z;
       const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));

@@ -40,13 +40,13 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
   constexpr int D = (MODEL == SIM_FIRST_PRINCIPLES) ? 17 : 13;
   float Wc[4];
   float ep[3] = {0.f, 0.f, 0.f};
+  float R[9];  // R(q) of the state at the start of the step (controller and first stage)
   if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
+    quat_rot(s[3], s[4], s[5], s[6], R);
     if constexpr (CTRL == SIM_CTRL_ROTOR_SPEED) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) Wc[r] = h.Wc[r];
     } else {
-      float R[9];
-      quat_rot(s[3], s[4], s[5], s[6], R);
       float tx, ty, tz;
       if constexpr (CTRL == SIM_CTRL_POSITION) {
         float Rd[9], Td;
@@ -59,40 +59,41 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
       }
     }
   }
-  auto deriv = [&](const float* x, float* d) {
+  auto deriv = [&](const float* x, float* d, const float* Rx) {
     if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
-      deriv_fp<MOTOR>(x, Wc, P, drag, d);
+      deriv_fp<MOTOR>(x, Wc, P, drag, d, Rx);
     } else {
       deriv_abs(x, h.u, P, drag, d);
     }
   };
+  const float* R0 = (MODEL == SIM_FIRST_PRINCIPLES) ? R : nullptr;
   if constexpr (INTEG == SIM_EULER) {
     float d[D];
-    deriv(s, d);
+    deriv(s, d, R0);
 #pragma unroll
     for (int j = 0; j < D; ++j) s[j] = fmaf(dt, d[j], s[j]);
   } else {
     float k[D], acc[D], xs[D];
     const float h2 = 0.5f * dt, h6 = dt * (1.f / 6.f);
-    deriv(s, k);
+    deriv(s, k, R0);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       acc[j] = k[j];
       xs[j] = fmaf(h2, k[j], s[j]);
     }
-    deriv(xs, k);
+    deriv(xs, k, nullptr);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       acc[j] = fmaf(2.f, k[j], acc[j]);
       xs[j] = fmaf(h2, k[j], s[j]);
     }
-    deriv(xs, k);
+    deriv(xs, k, nullptr);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       acc[j] = fmaf(2.f, k[j], acc[j]);
       xs[j] = fmaf(dt, k[j], s[j]);
     }
-    deriv(xs, k);
+    deriv(xs, k, nullptr);
 #pragma unroll
     for (int j = 0; j < D; ++j) s[j] = fmaf(h6, acc[j] + k[j], s[j]);
   }

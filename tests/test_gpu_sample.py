@@ -175,3 +175,30 @@ def test_graph_replay_reads_a_fresh_seed():
         torch.cuda.synchronize()
         assert torch.equal(cost, eager[s])
     assert not torch.equal(eager[111], eager[222])
+
+
+def test_moving_drones_near_obstacle_shells():
+    """Drones with initial velocity and obstacles placed on shells around the
+    start positions (inside, near and beyond what the horizon can reach), high
+    noise: costs match the oracle, so no reachable obstacle is skipped."""
+    n_w = [6, 10]
+    wl, x0 = _scene(75, n_w)
+    rng = np.random.default_rng(8)
+    x0[:, 7:10] = rng.uniform(-2.0, 2.0, (16, 3))
+    obs = []
+    for d in range(0, 16, 3):
+        for dist in (0.05, 0.2, 0.35, 0.5, 0.8):
+            u = rng.normal(size=3)
+            u /= np.linalg.norm(u)
+            obs.append(list(x0[d, 0:3] + (dist + 0.15) * u) + [0.15])
+    obs = np.array(obs[:64])
+    sim = _sim_for(n_w, wl.params, x0)
+    S, H = 24, 60
+    cost = sim.sample_rollouts(S, H, _seed_tensor(5), 0.6,
+                               torch.tensor(wl.goals, dtype=torch.float32, device="cuda"), obs, 1000.0)
+    drones = np.repeat(np.arange(16), S)
+    samples = np.tile(np.arange(S), 16)
+    ref = _oracle(x0, wl.goals, obs, wl.params, S, H, 0.6, 5, 1000.0, n_w, drones, samples).reshape(16, S)
+    np.testing.assert_allclose(cost.cpu().numpy(), ref, rtol=RTOL, atol=1e-4)
+    # the scene does put obstacles inside the reachable region
+    assert (ref > H * 0.0 + 1.0).any()
