@@ -23,19 +23,24 @@ __device__ __forceinline__ void run_drone(const StepArgs& a, int i, const DevPar
   const bool drag = (P.flags & PF_DRAG) != 0;
   const int last = a.n_blocks - 1;
   int blk = min(a.t0 / a.hold, last);
+  // steps left in the current command block (the last block lasts forever)
   int left = (a.t0 / a.hold >= last) ? 0x7fffffff : a.hold - a.t0 % a.hold;
   CtrlHold h;
   decode_command<MODEL, CTRL>(a.cmd[(size_t)blk * n + i], P, h);
   float4 next = a.cmd[(size_t)min(blk + 1, last) * n + i];
-  for (int k = 0; k < a.K; ++k) {
+  // outer loop over command-block segments, inner loop over the steps of one
+  // segment (no per-step block bookkeeping in the hot loop)
+  for (int k = 0; k < a.K;) {
     if (left == 0) {
       ++blk;
       decode_command<MODEL, CTRL>(next, P, h);
       left = (blk >= last) ? 0x7fffffff : a.hold;
       next = a.cmd[(size_t)min(blk + 1, last) * n + i];
     }
-    --left;
-    one_step<MODEL, INTEG, CTRL, MOTOR>(s, h, P, drag, a.dt);
+    const int seg = min(left, a.K - k);
+    for (int j = 0; j < seg; ++j) one_step<MODEL, INTEG, CTRL, MOTOR>(s, h, P, drag, a.dt);
+    k += seg;
+    left -= seg;
   }
   float chk = 0.f;
 #pragma unroll

@@ -59,9 +59,11 @@ def test_log_uniform_swarms_first_principles():
     assert_parity(gpu[sample], ref, np.zeros(400, np.int64))
 
 
-def test_batched_matches_uniform_path_bitwise():
-    """A batched handle over equal worlds of one model runs the same float
-    operations as the uniform handle: identical states."""
+def test_batched_matches_uniform_path():
+    """A batched handle over equal worlds of one model computes the same
+    formulas as the uniform handle.  The two are separate kernels (per-world
+    parameters in registers vs constant-bank operands), so the compiler may
+    fuse multiply-adds differently: agreement to float32 rounding, not bits."""
     wl = W.config1(M=777, steps=90, K=45)
     a = make_sim(wl)
     a.run(90, 45)
@@ -72,7 +74,7 @@ def test_batched_matches_uniform_path_bitwise():
     b.set_state(torch.tensor(wl.x0, dtype=torch.float32, device="cuda"))
     b.set_commands(torch.tensor(wl.cmd, dtype=torch.float32, device="cuda"), wl.hold)
     b.run(90, 45)
-    assert np.array_equal(b.get_state().cpu().numpy(), sa)
+    np.testing.assert_allclose(b.get_state().cpu().numpy(), sa, rtol=2e-6, atol=2e-6)
 
 
 def test_config2_full_size_sampled():
