@@ -81,6 +81,46 @@ def normals(seed: int, sample_ids: np.ndarray, step: int) -> np.ndarray:
     return np.stack([z0, z1, z2, z3], axis=-1)
 
 
+def cost_of_actions(x0_rows, goal_rows, obstacles, params: dict, actions, dt: float, w_obs: float,
+                    integrator: int = ph.RK4):
+    """Cost of fixed action sequences: x0_rows [n, 20], goal_rows [n, 3],
+    actions [n, H, 4] (already clipped)."""
+    x = torch.tensor(np.asarray(x0_rows), dtype=F64)
+    g = torch.tensor(np.asarray(goal_rows), dtype=F64)
+    obs = torch.tensor(np.asarray(obstacles), dtype=F64).reshape(-1, 4)
+    a_all = torch.tensor(np.asarray(actions), dtype=F64)
+    n = x.shape[0]
+    P = ph.param_batch([params], [0] * n)
+    cost = torch.zeros(n, dtype=F64)
+    for k in range(a_all.shape[1]):
+        x = ph.step(x, a_all[:, k], P, dt, integrator, ph.CTRL_ATTITUDE, ph.FIRST_PRINCIPLES)
+        p = x[:, 0:3]
+        cost = cost + torch.linalg.vector_norm(p - g, dim=-1)
+        d = torch.linalg.vector_norm(p[:, None, :] - obs[None, :, 0:3], dim=-1)
+        cost = cost + w_obs * torch.clamp(obs[None, :, 3] - d, min=0.0).sum(-1)
+    return cost.numpy()
+
+
+def sampled_actions(seed: int, ids, H: int, nominal_rows, sigma: float, rho: float = 0.0):
+    """Actions [n, H, 4] of the samples with the given ids: clip(nominal + sigma
+    eps, -1, 1) with eps_0 = xi_0, eps_k = rho eps_{k-1} + sqrt(1 - rho^2) xi_k
+    (AR(1) temporal correlation; rho = 0 is white noise).  nominal_rows
+    [n, H, 4] or None."""
+    ids = np.asarray(ids, dtype=np.uint64)
+    n = len(ids)
+    out = np.zeros((n, H, 4))
+    eps = np.zeros((n, 4))
+    c = np.sqrt(1.0 - rho * rho)
+    for k in range(H):
+        xi = normals(seed, ids, k)
+        eps = xi if k == 0 else rho * eps + c * xi
+        a = sigma * eps
+        if nominal_rows is not None:
+            a = a + np.asarray(nominal_rows)[:, k]
+        out[:, k] = np.clip(a, -1.0, 1.0)
+    return out
+
+
 def rollout_cost(x0, goals, obstacles, params: dict, S: int, H: int, dt: float, sigma: float,
                  seed: int, w_obs: float, drones, samples, world_of_drone, nominal=None):
     """Costs of the (drone, sample) pairs listed in `drones`, `samples` (equal
@@ -88,22 +128,9 @@ def rollout_cost(x0, goals, obstacles, params: dict, S: int, H: int, dt: float, 
     [Ntot]; nominal [M, H, 4] or None (zeros)."""
     drones = np.asarray(drones, dtype=np.int64)
     samples = np.asarray(samples, dtype=np.int64)
-    n = len(drones)
     ids = drones.astype(np.uint64) * np.uint64(S) + samples.astype(np.uint64)
-    x = torch.tensor(np.asarray(x0)[drones], dtype=F64)
     world = np.asarray(world_of_drone)[drones]
-    g = torch.tensor(np.asarray(goals)[world], dtype=F64)
-    obs = torch.tensor(np.asarray(obstacles), dtype=F64)
-    P = ph.param_batch([params], [0] * n)
-    cost = torch.zeros(n, dtype=F64)
-    for k in range(H):
-        a = torch.tensor(sigma * normals(seed, ids, k), dtype=F64)
-        if nominal is not None:
-            a = a + torch.tensor(np.asarray(nominal)[world, k], dtype=F64)
-        a = a.clamp(-1.0, 1.0)
-        x = ph.step(x, a, P, dt, ph.RK4, ph.CTRL_ATTITUDE, ph.FIRST_PRINCIPLES)
-        p = x[:, 0:3]
-        cost = cost + torch.linalg.vector_norm(p - g, dim=-1)
-        d = torch.linalg.vector_norm(p[:, None, :] - obs[None, :, 0:3], dim=-1)
-        cost = cost + w_obs * torch.clamp(obs[None, :, 3] - d, min=0.0).sum(-1)
-    return cost.numpy()
+    nom = None if nominal is None else np.asarray(nominal)[world]
+    acts = sampled_actions(seed, ids, H, nom, sigma)
+    return cost_of_actions(np.asarray(x0)[drones], np.asarray(goals)[world], obstacles, params,
+                           acts, dt, w_obs)
