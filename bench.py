@@ -274,9 +274,7 @@ def run_b300(args, wl):
     torch.cuda.synchronize()
     assert sim.status() == 0, "non-finite state during warm-up"
 
-    # device-resident timing (inputs already in HBM)
-    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_launch)]
-          for _ in range(args.steps)]
+    # device-resident timing (inputs already in HBM): two events per rollout
     launches0 = sim.launches
     sampler = ClockSampler(local)
     sampler.start()
@@ -290,15 +288,28 @@ def run_b300(args, wl):
         # keep the device busy while the host enqueues the rollout, so the
         # events time device execution and not host launch latency
         torch.cuda._sleep(1_000_000)
-        one_rollout(ev[it])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_rollout(None)
+        e1.record(stream)
         torch.cuda.synchronize()
-        per_iter_ms.append(ev[it][0][0].elapsed_time(ev[it][-1][1]))
+        per_iter_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     _barrier(dist)
     clocks = sampler.stop()
     # the set_state launch of each reset is not part of the timed region
     gpu_launches = sim.launches - launches0 - args.steps * 1
-    launch_ms = [e[0].elapsed_time(e[1]) for it in range(args.steps) for e in ev[it]]
+    # per-launch durations of the step kernel (for the roofline), in a separate pass
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_launch)]
+    launch_ms = []
+    for it in range(args.steps):
+        reset()
+        flush.fill_(it & 0xFF)
+        torch.cuda._sleep(1_000_000)
+        one_rollout(ev)
+        torch.cuda.synchronize()
+        launch_ms += [e[0].elapsed_time(e[1]) for e in ev]
     total_ms = _max_over_ranks(dist, sum(per_iter_ms))
     units = wl.M * wl.steps * args.steps * ws
     value = units / (total_ms / 1e3)
@@ -357,7 +368,7 @@ def run_b300(args, wl):
     line["autotune"] = tuned
     if not args.no_extra:
         line["extra"] = {"config2": measure_config2(dev), "config3": measure_config3(dev),
-                         "config4": measure_config4(dev)}
+                         "config4": measure_config4(dev), "mppi": measure_mppi(dev)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)
@@ -546,6 +557,34 @@ def measure_config4(dev, reps: int = 3) -> dict:
                          "flop_per_sample_step": SAMPLE_FLOP_PER_STEP}}
 
 
+def measure_mppi(dev, reps: int = 3) -> dict:
+    """MPPI / iCEM control at the paper's scale: 64 drones x 8000 samples
+    (512k trajectories per iteration), 5 controllers, 25-step horizon at 50 Hz,
+    RK4; one iteration = sampling launch + update launch."""
+    from paper_2606_01478_b300 import RK4, Sim
+    wl = W.mppi_workload()
+    n = len(wl.x0)
+    c = wl.cfg
+    sim = Sim.batched(wl.n_per_world, np.zeros(n, np.int32), RK4, wl.dt, device=dev)
+    sim.set_params(wl.params)
+    sim.set_state(torch.tensor(wl.x0, dtype=torch.float32, device=dev))
+    goals = torch.tensor(wl.goals, dtype=torch.float32, device=dev)
+    seed = torch.tensor([wl.seed], dtype=torch.int64, device=dev)
+    mean = torch.zeros(n, c["n_ctrl"], c["H"], 4, device=dev)
+    plan = torch.empty(n, c["H"], 4, device=dev)
+    cost = torch.empty(n, c["S"], device=dev)
+    best = torch.empty(n, device=dev)
+
+    def it():
+        seed.add_(1)
+        sim.mppi_iteration(c, seed, goals, wl.obstacles, mean, plan=plan, cost=cost, best_cost=best)
+    ms = _time_ms(it, reps, dev)
+    units = n * c["S"] * c["H"]
+    return {"workload": wl.name, "ms_per_iteration": ms, "iterations_per_s": 1e3 / ms,
+            "value": units / (ms / 1e3), "unit": UNIT, "trajectories_per_iteration": n * c["S"],
+            "paper_context": "500k samples x 25 steps at 50 Hz = 6.25e8 steps/s on an unnamed GPU"}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -555,7 +594,7 @@ def main(argv=None):
     ap.add_argument("--tpb", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the config-2/3/4 measurements")
-    ap.add_argument("--only", choices=["c2", "c3", "c4"], default=None,
+    ap.add_argument("--only", choices=["c2", "c3", "c4", "mppi"], default=None,
                     help="run one extra workload alone and print its record (for profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
@@ -564,7 +603,8 @@ def main(argv=None):
         local = int(os.environ.get("LOCAL_RANK", "0"))
         torch.cuda.set_device(local)
         dev = torch.device("cuda", local)
-        fn = {"c2": measure_config2, "c3": measure_config3, "c4": measure_config4}[args.only]
+        fn = {"c2": measure_config2, "c3": measure_config3, "c4": measure_config4,
+              "mppi": measure_mppi}[args.only]
         print(json.dumps({"only": args.only, "record": fn(dev, reps=args.steps)}), flush=True)
         return 0
     rank = int(os.environ.get("RANK", "0"))

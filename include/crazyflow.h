@@ -205,6 +205,42 @@ int sim_sample_rollouts(sim_h h, int S, int H, const uint64_t* seed, float sigma
                         int n_obs, float w_obs, float* cost, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * One MPPI / iCEM control iteration (Materials and Methods, Model Predictive
+ * Path Integral: parallel controllers, top-fraction elites, temporally
+ * correlated noise, warm start from the previous mean, exponential weighting
+ * of the elites, best controller applied).  For every drone d of the handle:
+ *   sample s (0 <= s < S) belongs to controller c = s / (S / n_ctrl); its
+ *   actions are clip(mean[d][c][k] + sigma eps_k, -1, 1) with the noise of
+ *   sim_sample_rollouts made AR(1): eps_0 = xi_0,
+ *   eps_k = rho eps_{k-1} + sqrt(1 - rho^2) xi_k
+ *   cost[d][s] as in sim_sample_rollouts (goal of the drone's world, obstacles)
+ *   elites of controller c: its n_e = clamp(ceil(elite_frac S/n_ctrl - 1e-4), 1, 32)
+ *   lowest costs (ties: lower sample index; NaN costs never selected)
+ *   mean'[d][c] = sum_e w_e a_e / sum_e w_e,  w_e = exp(-(J_e - J_min,c) / lambda)
+ *   plan[d] = mean'[d][c*], c* = argmin_c J_min,c (ties: lower c);
+ *   best_cost[d] = J_min,c*
+ *   mean[d][c][k] <- mean'[d][c][k+1] (warm start; the last step repeated)
+ * Buffers (device): mean [Ntot][n_ctrl][H][4] float (in/out, 16-byte aligned),
+ * plan [Ntot][H][4] float, cost [Ntot][S] float (written), best_cost [Ntot]
+ * float; goals, obstacles and seed as for sim_sample_rollouts.
+ * Constraints: S % n_ctrl == 0, 1 <= n_ctrl <= 32, 0 <= rho < 1, lambda > 0,
+ * 0 < elite_frac <= 1.  Two launches (sampling, update); no scratch memory. */
+typedef struct {
+  int S;            /* samples per drone, all controllers */
+  int H;            /* horizon (steps of the handle's dt and integrator) */
+  int n_ctrl;       /* parallel controllers per drone */
+  float sigma;      /* noise scale */
+  float rho;        /* AR(1) temporal correlation of the noise */
+  float elite_frac; /* elite fraction of each controller's samples */
+  float lambda;     /* temperature of the exponential weights */
+  float w_obs;      /* obstacle penalty weight */
+} sim_mppi_config;
+
+int sim_mppi_iteration(sim_h h, const sim_mppi_config* cfg, const uint64_t* seed,
+                       const float* goals, const float* obstacles, int n_obs, float* mean,
+                       float* plan, float* cost, float* best_cost, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Differentiable policy rollout (backpropagation through time; Materials and
  * Methods, Backpropagation Through Time).  For every drone of the handle,
  * independently:

@@ -12,7 +12,7 @@ every drone d, with n_ctrl controllers of S_c = S / n_ctrl samples each:
     sample s belongs to controller c = s // S_c; its actions are
         clip(mean[d, c, k] + sigma eps_{s,k}, -1, 1),  eps AR(1) with rho
         (Philox noise of sample id d * S + s, see oracle.sampling)
-    elites E_c: the n_e = clamp(ceil(elite_frac S_c), 1, 32) smallest costs
+    elites E_c: the n_e = clamp(ceil(elite_frac S_c - 1e-4), 1, 32) smallest costs
         (ties: lower sample index first)
     w_e = exp(-(J_e - J_min,c) / lam),  mean'[d, c] = sum_e w_e a_e / sum_e w_e
     c* = argmin_c J_min,c (ties: lower c);  plan[d] = mean'[d, c*]
@@ -37,7 +37,9 @@ MAX_ELITES = 32
 
 
 def n_elites(S_c: int, elite_frac: float) -> int:
-    return int(min(MAX_ELITES, max(1, math.ceil(elite_frac * S_c))))
+    """clamp(ceil(elite_frac S_c - 1e-4), 1, 32): the 1e-4 guard makes a
+    fraction given in float32 (0.1 -> 0.100000001) count as intended."""
+    return int(min(MAX_ELITES, max(1, math.ceil(elite_frac * S_c - 1e-4))))
 
 
 def select_elites(costs_c: np.ndarray, n_e: int) -> np.ndarray:

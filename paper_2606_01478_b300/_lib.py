@@ -33,6 +33,12 @@ PARAM_ORDER = (
     "c_tau", "c_f",
 )
 
+class MppiConfig(ctypes.Structure):
+    """sim_mppi_config (include/crazyflow.h)."""
+    _fields_ = [("S", c_int), ("H", c_int), ("n_ctrl", c_int), ("sigma", c_float), ("rho", c_float),
+                ("elite_frac", c_float), ("lambda_", c_float), ("w_obs", c_float)]
+
+
 _SIGS = {
     "sim_create": (c_int, [POINTER(c_void_p), c_int64, c_int64, c_int, c_int, c_float]),
     "sim_create_batched": (c_int, [POINTER(c_void_p), c_int64, POINTER(c_int64), POINTER(ctypes.c_int32),
@@ -54,6 +60,9 @@ _SIGS = {
     "sim_launch_count": (c_int64, [c_void_p]),
     "sim_sample_rollouts": (c_int, [c_void_p, c_int, c_int, c_void_p, c_float, c_void_p, c_void_p,
                                     POINTER(c_float), c_int, c_float, c_void_p, c_void_p]),
+    "sim_mppi_iteration": (c_int, [c_void_p, POINTER(MppiConfig), c_void_p, c_void_p,
+                                   POINTER(c_float), c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   c_void_p]),
     "sim_philox_normals": (c_int, [c_void_p, ctypes.c_uint64, c_int64, c_int, c_void_p, c_void_p,
                                    c_void_p]),
     "sim_rollout_workspace_bytes": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),

@@ -34,7 +34,10 @@ cudaError_t launch_sample(const float4* planes, int n, const int* offsets, int M
                           const DevParams* params, const int32_t* set_of_world, const DevParams& P0,
                           bool per_set, bool general_motor, int integrator, const float* obstacles,
                           int n_obs, float w_obs, float sigma, float dt, int S, int H, float* cost,
-                          int tpb, cudaStream_t st);
+                          int tpb, cudaStream_t st, int n_ctrl = 0, float rho = 0.f);
+cudaError_t launch_mppi_update(const float* cost, float* mean, float* plan, float* best_cost,
+                               const unsigned long long* seed, int n, int S, int H, int C, int n_e,
+                               float sigma, float rho, float lambda, cudaStream_t st);
 
 cudaError_t launch_philox(const unsigned long long* seed, unsigned long long first_id, long long n,
                           int step, uint32_t* words, float* normals, cudaStream_t st);

@@ -38,6 +38,10 @@ struct Args {
   float* cost;  // [n][S]
   long long total;
   int n, M, N;
+  // MPPI mode (n_ctrl > 0): nominal is [n][n_ctrl][H][4], sample s uses
+  // controller s / S_c; noise eps_k = rho eps_{k-1} + rho_c xi_k (rho_c = sqrt(1 - rho^2))
+  int n_ctrl, S_c;
+  float rho, rho_c;
 };
 
 __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
@@ -68,7 +72,8 @@ __device__ __forceinline__ float2 box_muller(uint32_t w1, uint32_t w2) {
 
 template <int INTEG, int MOTOR>
 __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const DevParams& P,
-                                         long long r, int d, int w, uint32_t k0, uint32_t k1) {
+                                         long long r, int d, int smp, int w, uint32_t k0,
+                                         uint32_t k1) {
   float s[20];
 #pragma unroll
   for (int j = 0; j < 5; ++j) {
@@ -81,7 +86,11 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
   const float gx = a.goals[3 * w], gy = a.goals[3 * w + 1], gz = a.goals[3 * w + 2];
   const bool drag = (P.flags & PF_DRAG) != 0;
   const uint32_t id_lo = (uint32_t)r, id_hi = (uint32_t)((unsigned long long)r >> 32);
-  const float4* nom = a.nominal ? reinterpret_cast<const float4*>(a.nominal) + (size_t)w * sc.H : nullptr;
+  const float4* nom = nullptr;
+  if (a.nominal) {
+    const size_t row = a.n_ctrl > 0 ? (size_t)d * a.n_ctrl + smp / a.S_c : (size_t)w;
+    nom = reinterpret_cast<const float4*>(a.nominal) + row * sc.H;
+  }
   // Obstacles the drone cannot reach within the horizon contribute exactly 0 to
   // every step's penalty and are skipped.  Reach bound: |v0| T + A T^2 with
   // A >= |p''| = |(T_rotor/m) R e_z - g e_z| <= 4 kf W_max^2 / m + g, valid for
@@ -104,12 +113,20 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
     }
   }
   float cost = 0.f;
+  float4 eps = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int k = 0; k < sc.H; ++k) {
     uint32_t c[4] = {id_lo, id_hi, (uint32_t)k, 0u};
     philox4x32_10(c, k0, k1);
     const float2 z01 = box_muller(c[0], c[1]);
     const float2 z23 = box_muller(c[2], c[3]);
-    float4 act = make_float4(sc.sigma * z01.x, sc.sigma * z01.y, sc.sigma * z23.x, sc.sigma * z23.y);
+    // AR(1) temporal correlation: eps_0 = xi_0, eps_k = rho eps_{k-1} + rho_c xi_k
+    // (rho = 0, rho_c = 1: white noise, eps = xi exactly)
+    const float cx = k == 0 ? 1.f : a.rho_c;
+    eps.x = fmaf(a.rho, eps.x, cx * z01.x);
+    eps.y = fmaf(a.rho, eps.y, cx * z01.y);
+    eps.z = fmaf(a.rho, eps.z, cx * z23.x);
+    eps.w = fmaf(a.rho, eps.w, cx * z23.y);
+    float4 act = make_float4(sc.sigma * eps.x, sc.sigma * eps.y, sc.sigma * eps.z, sc.sigma * eps.w);
     if (nom) {
       const float4 m = nom[k];
       act.x += m.x;
@@ -141,6 +158,7 @@ __global__ void __launch_bounds__(256) sample_kernel(Args a, Scene sc, DevParams
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < a.total; r += stride) {
     const int d = (int)(r / sc.S);
+    const int smp = (int)(r - (long long)d * sc.S);
     int w;
     if (a.offsets) {  // largest w with offsets[w] <= d
       int lo = 0, hi = a.M - 1;
@@ -156,9 +174,9 @@ __global__ void __launch_bounds__(256) sample_kernel(Args a, Scene sc, DevParams
     float cost;
     if constexpr (PERSET) {
       const DevParams P = a.params[a.set_of_world[w]];
-      cost = rollout<INTEG, MOTOR>(a, sc, P, r, d, w, k0, k1);
+      cost = rollout<INTEG, MOTOR>(a, sc, P, r, d, smp, w, k0, k1);
     } else {
-      cost = rollout<INTEG, MOTOR>(a, sc, P0, r, d, w, k0, k1);
+      cost = rollout<INTEG, MOTOR>(a, sc, P0, r, d, smp, w, k0, k1);
     }
     a.cost[r] = cost;
   }
@@ -207,7 +225,134 @@ __global__ void philox_kernel(const unsigned long long* seed, unsigned long long
   }
 }
 
+// MPPI / iCEM update: one block per drone, warp c = controller c.
+struct MppiArgs {
+  const float* cost;  // [n][S]
+  float* mean;        // [n][C][H][4]: in = current means, out = updated means shifted one step
+  float* plan;        // [n][H][4]: updated mean of the best controller
+  float* best_cost;   // [n]
+  const unsigned long long* seed;
+  int n, S, H, C, S_c, n_e;
+  float sigma, rho, rho_c, inv_lam;
+};
+
+__device__ __forceinline__ bool lex_less(float a, int ia, float b, int ib) {
+  return a < b || (a == b && ia < ib);
+}
+
+__global__ void mppi_update_kernel(MppiArgs a) {
+  __shared__ float jmin_s[32];
+  const int d = blockIdx.x;
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* cc = a.cost + (size_t)d * a.S + (size_t)c * a.S_c;
+  // elites: n_e rounds of a warp arg-min over (cost, index) after the previous
+  // elite, ties to the lower index; NaN costs are never selected
+  float prev_c = -INFINITY, el_c = INFINITY;
+  int prev_i = -1, el_i = 0x7fffffff;
+  for (int e = 0; e < a.n_e; ++e) {
+    float bc = INFINITY;
+    int bi = 0x7fffffff;
+    for (int s = lane; s < a.S_c; s += 32) {
+      const float v = cc[s];
+      if (v == v && lex_less(prev_c, prev_i, v, s) && lex_less(v, s, bc, bi)) {
+        bc = v;
+        bi = s;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (lex_less(oc, oi, bc, bi)) {
+        bc = oc;
+        bi = oi;
+      }
+    }
+    if (lane == e) {
+      el_c = bc;
+      el_i = bi;
+    }
+    prev_c = bc;
+    prev_i = bi;
+  }
+  const float jmin = __shfl_sync(0xffffffffu, el_c, 0);
+  if (lane == 0) jmin_s[c] = jmin;
+  __syncthreads();
+  int cbest = 0;
+  for (int q = 1; q < a.C; ++q)
+    if (jmin_s[q] < jmin_s[cbest]) cbest = q;
+  if (threadIdx.x == 0) a.best_cost[d] = jmin_s[cbest];
+  const bool mine = lane < a.n_e && el_i != 0x7fffffff;
+  const float wgt = mine ? expf(-(el_c - jmin) * a.inv_lam) : 0.f;
+  float wsum = wgt;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+  const float inv_w = 1.f / wsum;
+  const unsigned long long id =
+      (unsigned long long)d * a.S + (unsigned long long)c * a.S_c + (mine ? (unsigned)el_i : 0u);
+  const unsigned long long sd = *a.seed;
+  float4* mrow = reinterpret_cast<float4*>(a.mean) + ((size_t)d * a.C + c) * a.H;
+  float4* prow = reinterpret_cast<float4*>(a.plan) + (size_t)d * a.H;
+  float4 eps = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 last = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = 0; k < a.H; ++k) {
+    const float4 m = mrow[k];
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (mine) {
+      uint32_t ct[4] = {(uint32_t)id, (uint32_t)(id >> 32), (uint32_t)k, 0u};
+      philox4x32_10(ct, (uint32_t)sd, (uint32_t)(sd >> 32));
+      const float2 z01 = box_muller(ct[0], ct[1]);
+      const float2 z23 = box_muller(ct[2], ct[3]);
+      const float cx = k == 0 ? 1.f : a.rho_c;
+      eps.x = fmaf(a.rho, eps.x, cx * z01.x);
+      eps.y = fmaf(a.rho, eps.y, cx * z01.y);
+      eps.z = fmaf(a.rho, eps.z, cx * z23.x);
+      eps.w = fmaf(a.rho, eps.w, cx * z23.y);
+      v.x = wgt * clampf(fmaf(a.sigma, eps.x, m.x), -1.f, 1.f);
+      v.y = wgt * clampf(fmaf(a.sigma, eps.y, m.y), -1.f, 1.f);
+      v.z = wgt * clampf(fmaf(a.sigma, eps.z, m.z), -1.f, 1.f);
+      v.w = wgt * clampf(fmaf(a.sigma, eps.w, m.w), -1.f, 1.f);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      v.z += __shfl_xor_sync(0xffffffffu, v.z, o);
+      v.w += __shfl_xor_sync(0xffffffffu, v.w, o);
+    }
+    last = make_float4(v.x * inv_w, v.y * inv_w, v.z * inv_w, v.w * inv_w);
+    if (lane == 0) {
+      if (k > 0) mrow[k - 1] = last;  // warm start: shift by one step (row k-1 was read already)
+      if (c == cbest) prow[k] = last;
+    }
+  }
+  if (lane == 0) mrow[a.H - 1] = last;
+}
+
 }  // namespace sp
+
+cudaError_t launch_mppi_update(const float* cost, float* mean, float* plan, float* best_cost,
+                               const unsigned long long* seed, int n, int S, int H, int C, int n_e,
+                               float sigma, float rho, float lambda, cudaStream_t st) {
+  sp::MppiArgs a;
+  a.cost = cost;
+  a.mean = mean;
+  a.plan = plan;
+  a.best_cost = best_cost;
+  a.seed = seed;
+  a.n = n;
+  a.S = S;
+  a.H = H;
+  a.C = C;
+  a.S_c = S / C;
+  a.n_e = n_e;
+  a.sigma = sigma;
+  a.rho = rho;
+  a.rho_c = sqrtf(1.f - rho * rho);
+  a.inv_lam = 1.f / lambda;
+  sp::mppi_update_kernel<<<n, 32 * C, 0, st>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_philox(const unsigned long long* seed, unsigned long long first_id, long long n,
                           int step, uint32_t* words, float* normals, cudaStream_t st) {
@@ -222,7 +367,7 @@ cudaError_t launch_sample(const float4* planes, int n, const int* offsets, int M
                           const DevParams* params, const int32_t* set_of_world, const DevParams& P0,
                           bool per_set, bool general_motor, int integrator, const float* obstacles,
                           int n_obs, float w_obs, float sigma, float dt, int S, int H, float* cost,
-                          int tpb, cudaStream_t st) {
+                          int tpb, cudaStream_t st, int n_ctrl, float rho) {
   sp::Args a;
   a.planes = planes;
   a.offsets = offsets;
@@ -236,6 +381,10 @@ cudaError_t launch_sample(const float4* planes, int n, const int* offsets, int M
   a.n = n;
   a.M = M;
   a.N = N;
+  a.n_ctrl = n_ctrl;
+  a.S_c = n_ctrl > 0 ? S / n_ctrl : S;
+  a.rho = rho;
+  a.rho_c = sqrtf(1.f - rho * rho);
   sp::Scene sc;
   for (int o = 0; o < SIM_MAX_OBSTACLES; ++o) {
     sc.obs[o] = o < n_obs ? make_float4(obstacles[4 * o], obstacles[4 * o + 1], obstacles[4 * o + 2],

@@ -477,9 +477,9 @@ int sim_status(sim_h h, uint32_t* flags, void* stream) {
 
 // ---------------------------------------------------------------- sampling rollouts
 
-int sim_sample_rollouts(sim_h h, int S, int H, const uint64_t* seed, float sigma,
-                        const float* nominal, const float* goals, const float* obstacles,
-                        int n_obs, float w_obs, float* cost, void* stream) {
+static int sample_impl(sim_h h, int S, int H, const uint64_t* seed, float sigma,
+                       const float* nominal, const float* goals, const float* obstacles, int n_obs,
+                       float w_obs, float* cost, void* stream, int n_ctrl, float rho) {
   if (!h) return SIM_EINVAL;
   if (!h->ws || !h->params_ok || !h->state_ok)
     return fail(h, SIM_ESTATE, "bind, parameters and state must be set before sampling");
@@ -505,11 +505,51 @@ int sim_sample_rollouts(sim_h h, int S, int H, const uint64_t* seed, float sigma
       h->planes, (int)h->ntot, h->batched ? h->offsets_dev : nullptr, (int)h->M, (int)h->N, goals,
       nominal, (const unsigned long long*)seed, h->params_dev, h->set_of_world_dev, h->p0,
       h->per_set || h->batched, h->general_motor, h->integrator, obstacles, n_obs, w_obs, sigma,
-      h->dt, S, H, cost, h->tpb, (cudaStream_t)stream);
+      h->dt, S, H, cost, h->tpb, (cudaStream_t)stream, n_ctrl, rho);
   if (e != cudaSuccess) return cuda_fail(h, e, "sampling launch");
   h->launches++;
   return SIM_OK;
 }
+
+int sim_sample_rollouts(sim_h h, int S, int H, const uint64_t* seed, float sigma,
+                        const float* nominal, const float* goals, const float* obstacles,
+                        int n_obs, float w_obs, float* cost, void* stream) {
+  return sample_impl(h, S, H, seed, sigma, nominal, goals, obstacles, n_obs, w_obs, cost, stream, 0,
+                     0.f);
+}
+
+int sim_mppi_iteration(sim_h h, const sim_mppi_config* cfg, const uint64_t* seed,
+                       const float* goals, const float* obstacles, int n_obs, float* mean,
+                       float* plan, float* cost, float* best_cost, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!cfg) return fail(h, SIM_EINVAL, "cfg is NULL");
+  const sim_mppi_config c = *cfg;
+  if (c.S < 1 || c.H < 1 || c.n_ctrl < 1 || c.n_ctrl > 32 || c.S % c.n_ctrl != 0 ||
+      !(c.rho >= 0.f && c.rho < 1.f) || !(c.lambda > 0.f) || !(c.elite_frac > 0.f && c.elite_frac <= 1.f) ||
+      !isfinite(c.lambda))
+    return fail(h, SIM_EINVAL,
+                "MPPI config: need S %% n_ctrl == 0, 1 <= n_ctrl <= 32, 0 <= rho < 1, lambda > 0, "
+                "0 < elite_frac <= 1");
+  if (!mean || ((uintptr_t)mean & 15) || !plan || ((uintptr_t)plan & 15) || !best_cost ||
+      ((uintptr_t)best_cost & 3))
+    return fail(h, SIM_EINVAL, "bad or misaligned MPPI buffer");
+  // sampling with per-(drone, controller) means and AR(1) noise
+  int r = sample_impl(h, c.S, c.H, seed, c.sigma, mean, goals, obstacles, n_obs, c.w_obs, cost,
+                      stream, c.n_ctrl, c.rho);
+  if (r != SIM_OK) return r;
+  const int S_c = c.S / c.n_ctrl;
+  // ceil with a 1e-4 guard so that e.g. 0.1 (0.100000001 in float) of 20 samples is 2
+  int n_e = (int)ceil((double)c.elite_frac * S_c - 1e-4);
+  n_e = n_e < 1 ? 1 : (n_e > 32 ? 32 : n_e);
+  cudaError_t e = cf::launch_mppi_update(cost, mean, plan, best_cost,
+                                         (const unsigned long long*)seed, (int)h->ntot, c.S, c.H,
+                                         c.n_ctrl, n_e, c.sigma, c.rho, c.lambda,
+                                         (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "MPPI update launch");
+  h->launches++;
+  return SIM_OK;
+}
+
 
 int sim_philox_normals(const uint64_t* seed, uint64_t first_id, int64_t n, int step, uint32_t* words,
                        float* normals, void* stream) {

@@ -173,6 +173,34 @@ class Sim:
             obs.shape[0], float(w_obs), ctypes.c_void_p(cost.data_ptr()), _stream_ptr(stream)))
         return cost
 
+    def mppi_iteration(self, cfg: dict, seed: torch.Tensor, goals: torch.Tensor, obstacles,
+                       mean: torch.Tensor, plan: torch.Tensor | None = None,
+                       cost: torch.Tensor | None = None, best_cost: torch.Tensor | None = None,
+                       stream=None):
+        """One MPPI / iCEM iteration (see sim_mppi_iteration).  cfg keys: S, H,
+        n_ctrl, sigma, rho, elite_frac, lam, w_obs.  mean [Ntot, n_ctrl, H, 4] is
+        updated in place (warm-started).  Returns (plan, cost, best_cost)."""
+        c = L.MppiConfig(int(cfg["S"]), int(cfg["H"]), int(cfg["n_ctrl"]), float(cfg["sigma"]),
+                         float(cfg["rho"]), float(cfg["elite_frac"]), float(cfg["lam"]),
+                         float(cfg["w_obs"]))
+        dev = self.device
+        if mean.dtype != torch.float32 or not mean.is_contiguous() or tuple(mean.shape) != (
+                self.ntot, c.n_ctrl, c.H, 4):
+            raise ValueError("mean must be contiguous float32 [Ntot, n_ctrl, H, 4]")
+        if plan is None:
+            plan = torch.empty(self.ntot, c.H, 4, dtype=torch.float32, device=dev)
+        if cost is None:
+            cost = torch.empty(self.ntot, c.S, dtype=torch.float32, device=dev)
+        if best_cost is None:
+            best_cost = torch.empty(self.ntot, dtype=torch.float32, device=dev)
+        obs = np.ascontiguousarray(np.asarray(obstacles, dtype=np.float32).reshape(-1, 4))
+        self._check(self.lib.sim_mppi_iteration(
+            self.h, ctypes.byref(c), ctypes.c_void_p(seed.data_ptr()), ctypes.c_void_p(goals.data_ptr()),
+            obs.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), obs.shape[0],
+            ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(plan.data_ptr()),
+            ctypes.c_void_p(cost.data_ptr()), ctypes.c_void_p(best_cost.data_ptr()), _stream_ptr(stream)))
+        return plan, cost, best_cost
+
     def status(self, stream=None) -> int:
         v = ctypes.c_uint32()
         self._check(self.lib.sim_status(self.h, ctypes.byref(v), _stream_ptr(stream)))

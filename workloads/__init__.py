@@ -413,3 +413,38 @@ def log_uniform_counts(seed: int, M: int, n_max: int) -> np.ndarray:
     """N_w = clamp(round(exp(U(0, ln n_max))), 1, n_max) (the sampling workload's recipe)."""
     rng = np.random.default_rng(seed)
     return np.clip(np.round(np.exp(rng.uniform(0.0, math.log(n_max), M))), 1, n_max).astype(np.int64)
+
+
+@dataclass
+class MppiWorkload:
+    name: str
+    n_per_world: np.ndarray
+    params: dict
+    x0: np.ndarray           # [Ntot, 20]
+    goals: np.ndarray        # [M, 3]
+    obstacles: np.ndarray    # [n_obs, 4]
+    dt: float
+    cfg: dict                # S, H, n_ctrl, sigma, rho, elite_frac, lam, w_obs
+    seed: int
+
+
+def mppi_workload(seed: int = 1005, n_drones: int = 64, S: int = 8000, n_ctrl: int = 5, H: int = 25,
+                  dt: float = 1.0 / 50, n_obs: int = 32) -> MppiWorkload:
+    """MPPI / iCEM control at the paper's scale: 64 drones (one world each)
+    with 8000 samples each (512k sampled trajectories per iteration, as the
+    paper's 500k), 5 parallel controllers, top 1 % elites, a 25-step horizon at
+    50 Hz, RK4; drones at rest in [-1.5,1.5]^2 x [0.5,3.5], goals in the same
+    box, 32 spherical obstacles as in config 4."""
+    rng = np.random.default_rng(seed)
+    P = crazyflie_params()
+    lo, hi = np.array([-1.5, -1.5, 0.5]), np.array([1.5, 1.5, 3.5])
+    pos = rng.uniform(lo, hi, (n_drones, 3))
+    x0 = fp_state(pos, np.zeros((n_drones, 3)), np.zeros((n_drones, 3)), np.zeros((n_drones, 3)),
+                  np.full((n_drones, 4), hover_rpm(P)))
+    goals = rng.uniform(lo, hi, (n_drones, 3))
+    obs = np.zeros((n_obs, 4))
+    obs[:, 0:3] = rng.uniform(np.array([-2.0, -2.0, 0.0]), np.array([2.0, 2.0, 4.0]), (n_obs, 3))
+    obs[:, 3] = rng.uniform(0.1, 0.3, n_obs)
+    cfg = dict(S=S, H=H, n_ctrl=n_ctrl, sigma=0.3, rho=0.7, elite_frac=0.01, lam=0.05, w_obs=1000.0)
+    return MppiWorkload(f"mppi_{n_drones}x{S}_C{n_ctrl}_H{H}_50Hz", np.ones(n_drones, np.int64), P,
+                        x0, goals, obs, dt, cfg, int(rng.integers(0, 2**62)))
