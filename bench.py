@@ -368,7 +368,8 @@ def run_b300(args, wl):
     line["autotune"] = tuned
     if not args.no_extra:
         line["extra"] = {"config2": measure_config2(dev), "config3": measure_config3(dev),
-                         "config4": measure_config4(dev), "mppi": measure_mppi(dev)}
+                         "config4": measure_config4(dev), "mppi": measure_mppi(dev),
+                         "bptt_training": measure_bptt_training(dev)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)
@@ -585,6 +586,47 @@ def measure_mppi(dev, reps: int = 3) -> dict:
             "paper_context": "500k samples x 25 steps at 50 Hz = 6.25e8 steps/s on an unnamed GPU"}
 
 
+def measure_bptt_training(dev, reps: int = 3) -> dict:
+    """The paper's BPTT tracking setup (16 environments, 40 steps per rollout,
+    learning rate 4.6e-2, 100 000 timesteps = 156 iterations): each iteration
+    is the rollout gradient (forward + adjoint kernels) and the Adam kernel;
+    one iteration is captured in a CUDA graph and replayed 156 times."""
+    from paper_2606_01478_b300 import EULER, FIRST_PRINCIPLES, Sim
+    from paper_2606_01478_b300.rollout import PolicyRollout, pack_policy
+    from paper_2606_01478_b300.train import PolicyTrainer
+    M, H, C, iters, lr = 16, 40, 10, 156, 4.6e-2
+    rw = W.config3(M=M, H=H, C=C)
+    sim = Sim(M, 1, FIRST_PRINCIPLES, EULER, rw.dt, device=dev)
+    sim.set_params(rw.params)
+    runner = PolicyRollout(sim, H, C, rw.w_act)
+    w0 = torch.tensor(pack_policy(rw.weights), dtype=torch.float32, device=dev)
+    x0 = torch.tensor(rw.x0, dtype=torch.float32, device=dev)
+    p_ref = torch.tensor(rw.p_ref, dtype=torch.float32, device=dev).contiguous()
+    times, losses = [], None
+    for r in range(reps + 1):
+        trainer = PolicyTrainer(runner, w0, lr)
+        g = trainer.capture(x0, p_ref)
+        hist = torch.empty(iters, device=dev)
+        torch.cuda._sleep(1_000_000)
+        stream = torch.cuda.current_stream(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(iters):
+            g.replay()
+        e1.record(stream)
+        e1.synchronize()
+        if r:
+            times.append(e0.elapsed_time(e1))
+        losses = trainer.loss.item()
+    ms = statistics.median(times)
+    return {"workload": f"bptt_train_{M}envs_H{H}_{iters}iters_lr{lr}", "ms_total": ms,
+            "ms_per_iteration": ms / iters, "iterations": iters,
+            "timesteps": M * H * iters, "final_loss": losses,
+            "paper_context": "1.56 s to train the 10 s Lissajous tracker (100k timesteps) on a CPU, "
+                             "with the paper's reward (this build's loss differs)"}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -594,7 +636,7 @@ def main(argv=None):
     ap.add_argument("--tpb", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the config-2/3/4 measurements")
-    ap.add_argument("--only", choices=["c2", "c3", "c4", "mppi"], default=None,
+    ap.add_argument("--only", choices=["c2", "c3", "c4", "mppi", "bptt"], default=None,
                     help="run one extra workload alone and print its record (for profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
@@ -604,7 +646,7 @@ def main(argv=None):
         torch.cuda.set_device(local)
         dev = torch.device("cuda", local)
         fn = {"c2": measure_config2, "c3": measure_config3, "c4": measure_config4,
-              "mppi": measure_mppi}[args.only]
+              "mppi": measure_mppi, "bptt": measure_bptt_training}[args.only]
         print(json.dumps({"only": args.only, "record": fn(dev, reps=args.steps)}), flush=True)
         return 0
     rank = int(os.environ.get("RANK", "0"))

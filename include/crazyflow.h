@@ -280,6 +280,17 @@ int sim_rollout_grad(sim_h h, const float* x0, const uint16_t* w, const float* p
                      float w_act, void* ws, size_t ws_bytes, float* loss, const float* dL_one,
                      float* dW, float* dx0, void* stream);
 
+/* One Adam step (Kingma & Ba, ICLR 2015) on n parameters, in place -- the
+ * optimiser of the BPTT training loop (Materials and Methods, Backpropagation
+ * Through Time: rollouts and optimisation fused on the device).  With
+ * t = *step + 1 (step: device int32, incremented by the call):
+ *   m <- b1 m + (1-b1) g;  v <- b2 v + (1-b2) g^2;
+ *   w <- w - lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps);  w_bf16 <- bf16_rn(w)
+ * grad, w, m, v: device float [n]; w_bf16: device bf16 bits [n] (the weights the
+ * next rollout reads).  One single-block launch; 1 <= n <= 2^24. */
+int sim_adam_step(const float* grad, float* w, float* m, float* v, uint16_t* w_bf16, int64_t n,
+                  int32_t* step, float lr, float beta1, float beta2, float eps, void* stream);
+
 /* sim_rollout_grad without a workspace argument.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory when
  * they need a gradient -- a control loop with a hard deadline (cudaMalloc can

@@ -63,6 +63,8 @@ _SIGS = {
     "sim_mppi_iteration": (c_int, [c_void_p, POINTER(MppiConfig), c_void_p, c_void_p,
                                    POINTER(c_float), c_int, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p]),
+    "sim_adam_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p,
+                              c_float, c_float, c_float, c_float, c_void_p]),
     "sim_philox_normals": (c_int, [c_void_p, ctypes.c_uint64, c_int64, c_int, c_void_p, c_void_p,
                                    c_void_p]),
     "sim_rollout_workspace_bytes": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),

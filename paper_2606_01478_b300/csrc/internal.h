@@ -42,6 +42,9 @@ cudaError_t launch_mppi_update(const float* cost, float* mean, float* plan, floa
 cudaError_t launch_philox(const unsigned long long* seed, unsigned long long first_id, long long n,
                           int step, uint32_t* words, float* normals, cudaStream_t st);
 
+cudaError_t launch_adam(const float* g, float* w, float* m, float* v, uint16_t* wb, int n, int* step,
+                        float lr, float b1, float b2, float eps, cudaStream_t st);
+
 // Record a message as the handle's last error (sim.cu); used by entry points
 // defined in other translation units.
 void note_error(sim_h h, const char* fmt, ...);

@@ -862,7 +862,39 @@ __global__ void reduce_loss_kernel(const float* __restrict__ loss_w, int n, floa
   if (threadIdx.x == 0) out[0] = (float)(red[0] / n);
 }
 
+// Adam (Kingma & Ba, ICLR 2015) on the fp32 master weights, one block: the
+// step count is read once by every thread (t = step + 1) and written back by
+// thread 0 at the end, so a captured graph replays successive steps.
+__global__ void __launch_bounds__(1024) adam_kernel(const float* __restrict__ g, float* __restrict__ w,
+                                                    float* __restrict__ m, float* __restrict__ v,
+                                                    __nv_bfloat16* __restrict__ wb, int n, int* step,
+                                                    float lr, float b1, float b2, float eps) {
+  __shared__ int t_s;
+  if (threadIdx.x == 0) t_s = *step + 1;
+  __syncthreads();
+  const int t = t_s;
+  const float bc1 = 1.f - powf(b1, (float)t), bc2 = 1.f - powf(b2, (float)t);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float gi = g[i];
+    const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
+    const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    w[i] = wi;
+    wb[i] = __float2bfloat16_rn(wi);
+  }
+  if (threadIdx.x == 0) *step = t;
+}
+
 }  // namespace ro
+
+cudaError_t launch_adam(const float* g, float* w, float* m, float* v, uint16_t* wb, int n, int* step,
+                        float lr, float b1, float b2, float eps, cudaStream_t st) {
+  ro::adam_kernel<<<1, 1024, 0, st>>>(g, w, m, v, reinterpret_cast<__nv_bfloat16*>(wb), n, step, lr,
+                                      b1, b2, eps);
+  return cudaGetLastError();
+}
 
 size_t rollout_workspace_bytes(int n, int H, int C) {
   const int n_ck = (H + C - 1) / C;

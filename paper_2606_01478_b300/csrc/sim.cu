@@ -618,6 +618,18 @@ int sim_rollout_grad(sim_h h, const float* x0, const uint16_t* w, const float* p
   return sim_rollout_bwd(h, x0, w, p_ref, H, C, w_act, ws, ws_bytes, dL_one, dW, dx0, stream);
 }
 
+int sim_adam_step(const float* grad, float* w, float* m, float* v, uint16_t* w_bf16, int64_t n,
+                  int32_t* step, float lr, float beta1, float beta2, float eps, void* stream) {
+  if (!grad || !w || !m || !v || !w_bf16 || !step || n < 1 || n > (1 << 24) ||
+      ((uintptr_t)grad & 3) || ((uintptr_t)w & 3) || ((uintptr_t)m & 3) || ((uintptr_t)v & 3) ||
+      ((uintptr_t)w_bf16 & 1) || ((uintptr_t)step & 3) || !(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) ||
+      !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return SIM_EINVAL;
+  cudaError_t e = cf::launch_adam(grad, w, m, v, w_bf16, (int)n, step, lr, beta1, beta2, eps,
+                                  (cudaStream_t)stream);
+  return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
+}
+
 int64_t sim_num_drones(sim_h h) { return h ? h->ntot : -1; }
 int64_t sim_step_count(sim_h h) { return h ? h->t : -1; }
 int sim_set_step_count(sim_h h, int64_t t) {

@@ -78,13 +78,13 @@ class PolicyRollout:
                                        _stream_ptr(stream)))
         return dW, dx0
 
-    def grad(self, x0, w_bf16, p_ref, stream=None):
+    def grad(self, x0, w_bf16, p_ref, stream=None, loss=None, dW=None, dx0=None):
         """Loss, dL/dw and dL/dx0 in one call (forward + backward kernels)."""
         self._check_inputs(x0, w_bf16, p_ref)
         dev = self.sim.device
-        loss = torch.empty(1, dtype=torch.float32, device=dev)
-        dW = torch.empty(L.POLICY_NPARAMS, dtype=torch.float32, device=dev)
-        dx0 = torch.empty_like(x0)
+        loss = torch.empty(1, dtype=torch.float32, device=dev) if loss is None else loss
+        dW = torch.empty(L.POLICY_NPARAMS, dtype=torch.float32, device=dev) if dW is None else dW
+        dx0 = torch.empty_like(x0) if dx0 is None else dx0
         s = self.sim
         s._check(s.lib.sim_rollout_grad(s.h, _p(x0), _p(w_bf16), _p(p_ref), self.H, self.C,
                                         self.w_act, _p(self.ws), self.ws.numel(), _p(loss),
