@@ -23,6 +23,7 @@
  *       SIM_CTRL_ATTITUDE:    a in [-1,1]^4 = (roll, pitch, yaw, thrust),
  *                             angles a*max_angle, thrust m g (1 + thrust_scale a4)
  *       SIM_CTRL_POSITION:    (x, y, z, yaw) setpoint
+ *       SIM_CTRL_TORQUE:      (collective thrust N, body torque x, y, z N m)
  *     (the paper's control interfaces: text after Eq. 6)
  *   - Drone i of world w has global index w*N + i (uniform batches) or
  *     offset[w] + i with offset the exclusive prefix sum of n_per_world.
@@ -67,9 +68,12 @@ extern "C" {
 /* device status word bits (sim_status) */
 #define SIM_FLAG_NONFINITE 1u /* some drone's state became NaN/Inf after a launch */
 
-/* physics models (First Principles Modeling, Eqs. 1-6; Abstracted Physics Modeling, Eqs. 7-10) */
+/* physics models (First Principles Modeling, Eqs. 1-6; Abstracted Physics Modeling, Eqs. 7-10;
+ * the abstracted variant without thrust dynamics and drag, last sentence of that section:
+ * f_sigma follows f_cmd at once, the drag term is dropped) */
 #define SIM_FIRST_PRINCIPLES 0
 #define SIM_ABSTRACTED 1
+#define SIM_ABSTRACTED_NOTHRUST 2
 
 /* integrators: explicit Euler, classic RK4 (controller output held over the stages) */
 #define SIM_EULER 0
@@ -79,17 +83,21 @@ extern "C" {
 #define SIM_CTRL_ROTOR_SPEED 0
 #define SIM_CTRL_ATTITUDE 1
 #define SIM_CTRL_POSITION 2
+#define SIM_CTRL_TORQUE 3
 
 #define SIM_STATE_DIM 20
 #define SIM_CMD_DIM 4
 #define SIM_NPARAMS 48
 
-/* Per-platform parameter vector (float[SIM_NPARAMS]); indices below.  kf and km
- * are per RPM^2; the rotor model is Eq. 6 with coefficients (cv_up, cd_up) for
- * spin-up and (cv_down, cd_down) for spin-down; C_a is the diagonal of the
- * body-frame linear drag matrix (text after Eq. 5); gains are those of the
- * geometric attitude/position controller; c1..c3 (roll, pitch, yaw), c_tau and
- * c_f are the abstracted-model coefficients of Eqs. 8-10. */
+/* Per-platform parameter vector (float[SIM_NPARAMS]); indices below.  Per-rotor
+ * thrust kf W^2 + kf1 W + kf0 and drag torque km W^2 + km1 W ("second-order
+ * polynomials", text before Eq. 5; W in RPM); the rotor model is Eq. 6 with
+ * coefficients (cv_up, cd_up) for spin-up and (cv_down, cd_down) for spin-down;
+ * J_p (kg m^2) is the rotor + motor inertia of Eq. 5's gyroscopic and reaction
+ * torques; C_a is the diagonal of the body-frame linear drag matrix (text after
+ * Eq. 5); gains are those of the geometric attitude/position controller;
+ * c1..c3 (roll, pitch, yaw), c_tau and c_f are the abstracted-model
+ * coefficients of Eqs. 8-10. */
 enum sim_param_index {
   SIM_P_MASS = 0, SIM_P_JX, SIM_P_JY, SIM_P_JZ, SIM_P_ARM, SIM_P_KF, SIM_P_KM,
   SIM_P_CV_UP, SIM_P_CD_UP, SIM_P_CV_DOWN, SIM_P_CD_DOWN, SIM_P_OMEGA_MAX,
@@ -100,7 +108,8 @@ enum sim_param_index {
   SIM_P_MAX_ANGLE, SIM_P_THRUST_SCALE, SIM_P_G,
   SIM_P_C1_R, SIM_P_C1_P, SIM_P_C1_Y, SIM_P_C2_R, SIM_P_C2_P, SIM_P_C2_Y,
   SIM_P_C3_R, SIM_P_C3_P, SIM_P_C3_Y, SIM_P_C_TAU, SIM_P_C_F,
-  SIM_P_COUNT /* = 44 used entries; the vector is padded to SIM_NPARAMS */
+  SIM_P_JP, SIM_P_KF0, SIM_P_KF1, SIM_P_KM1,
+  SIM_P_COUNT /* = 48 = SIM_NPARAMS */
 };
 
 typedef struct sim_s* sim_h;

@@ -8,7 +8,12 @@ Paper passages followed (Materials and Methods of arXiv 2606.01478):
   * rigid body, Eqs. 1-4 (First Principles Modeling): p' = v,
     q' = 1/2 q (x) [w; 0], m v' = f_sum, J w' = t_sum - w x J w
   * per-rotor thrust and drag counter-torque, "second-order polynomial" in the
-    rotor speed (text before Eq. 5), read as f_i = kf W_i^2, t_i = km W_i^2
+    rotor speed (text before Eq. 5): f_i = kf W_i^2 + kf1 W_i + kf0,
+    t_i = km W_i^2 + km1 W_i (the configs use kf1 = kf0 = km1 = 0)
+  * gyroscopic and reaction torques of the rotors, Eq. 5 (garbled in the
+    paper; read from the rotors' angular momentum h = J_p (2 pi / 60)
+    sum_i sigma_i W_i e_z with spin direction sigma_i = -s_i: tau_gyro = -w x h,
+    tau_react = -dh/dt, whose z row is Eq. 5's third row)
   * X-configuration mixing (text after Eq. 5) with the yaw sign pattern
     (-, +, -, +) of Eq. 5's third row
   * linear body-frame drag f_a = C_a v_B (text after Eq. 5)
@@ -39,9 +44,9 @@ from .rotation import euler_to_rot, quat_mul, quat_to_rot, vee
 
 F64 = torch.float64
 
-FIRST_PRINCIPLES, ABSTRACTED = 0, 1
+FIRST_PRINCIPLES, ABSTRACTED, ABSTRACTED_NOTHRUST = 0, 1, 2
 EULER, RK4 = 0, 1
-CTRL_ROTOR_SPEED, CTRL_ATTITUDE, CTRL_POSITION = 0, 1, 2
+CTRL_ROTOR_SPEED, CTRL_ATTITUDE, CTRL_POSITION, CTRL_TORQUE = 0, 1, 2, 3
 
 # X configuration (body x forward, y left, z up).  Rotor i sits at
 # (sx_i a, sy_i a, 0) with a = arm / sqrt(2); its drag counter-torque about
@@ -49,6 +54,7 @@ CTRL_ROTOR_SPEED, CTRL_ATTITUDE, CTRL_POSITION = 0, 1, 2
 ROTOR_SX = (1.0, -1.0, -1.0, 1.0)
 ROTOR_SY = (-1.0, -1.0, 1.0, 1.0)
 ROTOR_YAW = (-1.0, 1.0, -1.0, 1.0)
+RPM_TO_RAD_S = 2.0 * math.pi / 60.0
 
 
 def param_batch(params: list, set_of_drone) -> dict:
@@ -76,17 +82,30 @@ def rotor_positions(P) -> torch.Tensor:
     return torch.stack([x, y, torch.zeros_like(x)], dim=-1)
 
 
+def rotor_thrust(W: torch.Tensor, P) -> torch.Tensor:
+    """Per-rotor thrust kf W^2 + kf1 W + kf0 [B, 4]."""
+    return P["kf"][:, None] * W * W + P["kf1"][:, None] * W + P["kf0"][:, None]
+
+
 def rotor_wrench(W: torch.Tensor, P) -> tuple[torch.Tensor, torch.Tensor]:
     """Collective thrust T [B] and body torque tau [B, 3] of rotor speeds W [B, 4]
-    (RPM): f_i = kf W_i^2 along body z at r_i, drag counter-torque km W_i^2
-    with sign s_i about body z."""
-    f = P["kf"][:, None] * W * W
+    (RPM): thrust f_i along body z at r_i, drag counter-torque
+    km W_i^2 + km1 W_i with sign s_i about body z."""
+    f = rotor_thrust(W, P)
     F = torch.zeros(W.shape + (3,), dtype=F64)
     F[..., 2] = f
     tau = torch.linalg.cross(rotor_positions(P), F, dim=-1).sum(dim=1)
     yaw = torch.tensor(ROTOR_YAW, dtype=F64)
-    tau[:, 2] = tau[:, 2] + (P["km"][:, None] * W * W * yaw).sum(dim=1)
+    drag = P["km"][:, None] * W * W + P["km1"][:, None] * W
+    tau[:, 2] = tau[:, 2] + (drag * yaw).sum(dim=1)
     return f.sum(dim=1), tau
+
+
+def rotor_momentum(W: torch.Tensor, P) -> torch.Tensor:
+    """z component of the rotors' angular momentum in the body frame [B]:
+    J_p (2 pi / 60) sum_i sigma_i W_i with spin direction sigma_i = -s_i."""
+    yaw = torch.tensor(ROTOR_YAW, dtype=F64)
+    return -P["J_p"] * RPM_TO_RAD_S * (W * yaw).sum(dim=1)
 
 
 def motor_rate(W: torch.Tensor, Wc: torch.Tensor, P) -> torch.Tensor:
@@ -120,10 +139,32 @@ def deriv_fp(x: torch.Tensor, Wc: torch.Tensor, P) -> torch.Tensor:
     v_dot = f_world / P["mass"][:, None] - g
     J = torch.diag_embed(_v3(P, "Jx", "Jy", "Jz"))
     Jw = (J @ w[..., None])[..., 0]
+    W_dot = motor_rate(W, Wc, P)
+    if bool((P["J_p"] != 0).any()):
+        # rotor angular momentum h e_z: gyroscopic -w x h and reaction -dh/dt
+        h = torch.zeros_like(w)
+        h[:, 2] = rotor_momentum(W, P)
+        dh = torch.zeros_like(w)
+        dh[:, 2] = rotor_momentum(W_dot, P)
+        tau = tau - torch.linalg.cross(w, h, dim=-1) - dh
     w_dot = torch.linalg.solve(J, tau - torch.linalg.cross(w, Jw, dim=-1))
     q_dot = 0.5 * quat_mul(q, torch.cat([w, torch.zeros_like(w[:, :1])], dim=-1))
-    W_dot = motor_rate(W, Wc, P)
     return torch.cat([v, q_dot, v_dot, w_dot, W_dot], dim=-1)
+
+
+def deriv_abs_nothrust(x: torch.Tensor, u: torch.Tensor, P) -> torch.Tensor:
+    """Abstracted model without thrust dynamics and drag (last sentence of
+    Abstracted Physics Modeling): m v' = f_g + R(Psi) e_z c_f f_cmd, with the
+    attitude channels of Eq. 10; the f_sum slot does not evolve (the stepper
+    sets it to f_cmd)."""
+    psi, v, psid = x[:, 3:6], x[:, 6:9], x[:, 9:12]
+    R = euler_to_rot(psi)
+    g = torch.zeros_like(v)
+    g[:, 2] = P["g"]
+    v_dot = R[:, :, 2] * (P["c_f"] * u[:, 3] / P["mass"])[:, None] - g
+    psi_dd = (_v3(P, "c1_r", "c1_p", "c1_y") * psi + _v3(P, "c2_r", "c2_p", "c2_y") * psid
+              + _v3(P, "c3_r", "c3_p", "c3_y") * u[:, 0:3])
+    return torch.cat([v, psid, v_dot, psi_dd, torch.zeros_like(x[:, 12:13])], dim=-1)
 
 
 def deriv_abs(x: torch.Tensor, u: torch.Tensor, P) -> torch.Tensor:
@@ -206,13 +247,19 @@ def mixing_matrix(P) -> torch.Tensor:
 
 
 def mixer(Td: torch.Tensor, tau: torch.Tensor, P) -> torch.Tensor:
-    """Per-rotor thrusts f = A^-1 [T_d, tau] clipped to [0, kf W_max^2], then
-    rotor-speed commands W_cmd = sqrt(f / kf)."""
+    """Per-rotor thrusts f = A^-1 [T_d, tau] clipped to [f(0), f(W_max)], then
+    the rotor-speed commands that produce them: the root W >= 0 of
+    kf W^2 + kf1 W + kf0 = f (W = sqrt(f / kf) for a pure quadratic).  The yaw
+    row of A uses the quadratic coefficients' ratio km / kf."""
     wrench = torch.cat([Td[:, None], tau], dim=-1)
     f = torch.linalg.solve(mixing_matrix(P), wrench)
-    fmax = P["kf"] * P["omega_max"] ** 2
-    f = torch.minimum(torch.clamp(f, min=0.0), fmax[:, None])
-    return torch.sqrt(f / P["kf"][:, None])
+    wmax = P["omega_max"]
+    fmin = P["kf0"]
+    fmax = P["kf"] * wmax * wmax + P["kf1"] * wmax + P["kf0"]
+    f = torch.minimum(torch.maximum(f, fmin[:, None]), fmax[:, None])
+    kf, kf1 = P["kf"][:, None], P["kf1"][:, None]
+    disc = torch.clamp(kf1 * kf1 + 4.0 * kf * (f - P["kf0"][:, None]), min=0.0)
+    return (torch.sqrt(disc) - kf1) / (2.0 * kf)
 
 
 def control(x20: torch.Tensor, u: torch.Tensor, P, ctrl: int, dt: float):
@@ -222,6 +269,8 @@ def control(x20: torch.Tensor, u: torch.Tensor, P, ctrl: int, dt: float):
     if ctrl == CTRL_ROTOR_SPEED:
         Wc = torch.minimum(torch.clamp(u, min=0.0), P["omega_max"][:, None])
         return Wc, I
+    if ctrl == CTRL_TORQUE:
+        return mixer(u[:, 0], u[:, 1:4], P), I
     if ctrl == CTRL_ATTITUDE:
         _, Rd, Td = attitude_command(u, P)
         I_new = I
@@ -256,12 +305,16 @@ def step(x20: torch.Tensor, u: torch.Tensor, P, dt: float, integrator: int, ctrl
         x = integrate(lambda s: deriv_fp(s, Wc, P), x20[:, :17], dt, integrator)
         q = x[:, 3:7] / torch.linalg.vector_norm(x[:, 3:7], dim=-1, keepdim=True)
         return torch.cat([x[:, 0:3], q, x[:, 7:17], I_new], dim=-1)
-    if model == ABSTRACTED:
+    if model in (ABSTRACTED, ABSTRACTED_NOTHRUST):
         if ctrl != CTRL_ATTITUDE:
             raise ValueError("the abstracted model takes attitude commands")
         ang, _, Td = attitude_command(u, P)
         ua = torch.cat([ang, Td[:, None]], dim=-1)
-        x = integrate(lambda s: deriv_abs(s, ua, P), x20[:, :13], dt, integrator)
+        if model == ABSTRACTED:
+            x = integrate(lambda s: deriv_abs(s, ua, P), x20[:, :13], dt, integrator)
+        else:
+            x = integrate(lambda s: deriv_abs_nothrust(s, ua, P), x20[:, :13], dt, integrator)
+            x = torch.cat([x[:, :12], Td[:, None]], dim=-1)  # f_sum follows f_cmd at once
         return torch.cat([x, x20[:, 13:20]], dim=-1)
     raise ValueError(model)
 
@@ -276,7 +329,8 @@ def rollout(x0, cmd, hold: int, steps: int, params: list, set_of_drone, model_of
     cmd = torch.as_tensor(cmd, dtype=F64)
     P_all = param_batch(params, set_of_drone)
     models = torch.as_tensor(model_of_drone, dtype=torch.long)
-    groups = [(m, torch.nonzero(models == m)[:, 0]) for m in (FIRST_PRINCIPLES, ABSTRACTED)]
+    groups = [(m, torch.nonzero(models == m)[:, 0])
+              for m in (FIRST_PRINCIPLES, ABSTRACTED, ABSTRACTED_NOTHRUST)]
     groups = [(m, idx) for m, idx in groups if idx.numel() > 0]
     Pg = {m: {k: v[idx] for k, v in P_all.items()} for m, idx in groups}
     trace = []

@@ -14,9 +14,9 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcrazyflo
 
 SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ESTATE = 0, -1, -2, -3, -4
 SIM_FLAG_NONFINITE = 1
-FIRST_PRINCIPLES, ABSTRACTED = 0, 1
+FIRST_PRINCIPLES, ABSTRACTED, ABSTRACTED_NOTHRUST = 0, 1, 2
 EULER, RK4 = 0, 1
-CTRL_ROTOR_SPEED, CTRL_ATTITUDE, CTRL_POSITION = 0, 1, 2
+CTRL_ROTOR_SPEED, CTRL_ATTITUDE, CTRL_POSITION, CTRL_TORQUE = 0, 1, 2, 3
 STATE_DIM, CMD_DIM, NPARAMS = 20, 4, 48
 POLICY_NPARAMS = 5316
 MAX_OBSTACLES = 64
@@ -31,6 +31,7 @@ PARAM_ORDER = (
     "max_angle", "thrust_scale", "g",
     "c1_r", "c1_p", "c1_y", "c2_r", "c2_p", "c2_y", "c3_r", "c3_p", "c3_y",
     "c_tau", "c_f",
+    "J_p", "kf0", "kf1", "km1",
 )
 
 class MppiConfig(ctypes.Structure):

@@ -98,6 +98,7 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
   // speeds stay within [0, max(W_max, W_0)]: first-order-lag rotors with
   // dt * cv <= 1 and no drag.  Otherwise every obstacle is tested.
   unsigned long long cand = sc.n_obs >= 64 ? ~0ull : ((1ull << sc.n_obs) - 1ull);
+  bool sparse = false;  // few candidates: visit the set bits; else test every obstacle
   if (MOTOR == MOTOR_LAG && !drag && sc.dt * P.cv_up <= 1.f) {
     const float wmax = fmaxf(fmaxf(P.omega_max, fmaxf(s[13], s[14])), fmaxf(s[15], s[16]));
     const float acc = 4.f * P.kf * wmax * wmax * P.inv_m * 1.01f + P.g;
@@ -111,7 +112,9 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
       const float lim = ob.w + reach;
       if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < lim * lim) cand |= 1ull << o;
     }
+    sparse = 3 * __popcll(cand) < sc.n_obs;
   }
+  const uint32_t cand_lo = (uint32_t)cand, cand_hi = (uint32_t)(cand >> 32);
   float cost = 0.f;
   float4 eps = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int k = 0; k < sc.H; ++k) {
@@ -139,12 +142,18 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
     one_step<SIM_FIRST_PRINCIPLES, INTEG, SIM_CTRL_ATTITUDE, MOTOR>(s, h, P, drag, sc.dt);
     const float ex = s[0] - gx, ey = s[1] - gy, ez = s[2] - gz;
     float pen = 0.f;
-    for (unsigned long long m = cand; m; m &= m - 1ull) {
-      const int o = __ffsll((long long)m) - 1;
+    auto test = [&](int o) {
       const float4 ob = sc.obs[o];
       const float dx = s[0] - ob.x, dy = s[1] - ob.y, dz = s[2] - ob.z;
       const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       if (d2 < sc.r2[o]) pen += ob.w - sqrt_approx(d2);
+    };
+    if (sparse) {
+      for (uint32_t m = cand_lo; m; m &= m - 1u) test(__ffs(m) - 1);
+      for (uint32_t m = cand_hi; m; m &= m - 1u) test(32 + __ffs(m) - 1);
+    } else {
+      // dense: obstacles outside the reach bound add exactly zero, so testing them is harmless
+      for (int o = 0; o < sc.n_obs; ++o) test(o);
     }
     cost += sqrt_approx(fmaf(ex, ex, fmaf(ey, ey, ez * ez))) + sc.w_obs * pen;
   }

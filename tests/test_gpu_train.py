@@ -36,7 +36,9 @@ def test_adam_kernel_matches_oracle():
     assert r == L.SIM_OK
     torch.cuda.synchronize()
     f = lambda a: np.asarray(a, np.float32).astype(np.float64)
-    w2, m2, v2 = tr.adam(f(w), f(g), f(m), f(v), 5, 1e-2)
+    # the kernel receives float32 hyper-parameters: give the oracle the same values
+    h = lambda x: float(np.float32(x))
+    w2, m2, v2 = tr.adam(f(w), f(g), f(m), f(v), 5, h(1e-2), h(0.9), h(0.999), h(1e-8))
     np.testing.assert_allclose(wt.cpu().numpy(), w2, rtol=1e-5, atol=1e-7)
     # m cancels (0.9 m + 0.1 g with both terms ~1e-2): compare at the terms' fp32 rounding
     np.testing.assert_allclose(mt.cpu().numpy(), m2, rtol=1e-5, atol=3e-8)

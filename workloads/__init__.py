@@ -44,8 +44,9 @@ PARAM_NAMES = (
     "max_angle", "thrust_scale", "g",
     "c1_r", "c1_p", "c1_y", "c2_r", "c2_p", "c2_y", "c3_r", "c3_p", "c3_y",
     "c_tau", "c_f",
+    "J_p", "kf0", "kf1", "km1",
 )
-NPARAMS = 48  # packed length (44 used, padded to 48 floats = 192 B)
+NPARAMS = 48  # packed length
 
 
 def crazyflie_params(**overrides) -> dict:
@@ -58,6 +59,8 @@ def crazyflie_params(**overrides) -> dict:
     Gains and the action scaling are this build's readings (the paper prints none).
     Abstracted-model coefficients: roll/pitch omega_n = 15 rad/s, zeta = 0.7;
     yaw omega_n = 6 rad/s, zeta = 1; c_tau = 1/0.03; c_f = 1.
+    Rotor inertia J_p (kg m^2) and the non-quadratic coefficients of the thrust
+    (kf0 N, kf1 N/RPM) and drag-torque (km1 N m/RPM) curves default to 0.
     """
     m, kf = 0.027, 3.16e-10
     p = dict(
@@ -73,6 +76,7 @@ def crazyflie_params(**overrides) -> dict:
         c2_r=-21.0, c2_p=-21.0, c2_y=-12.0,
         c3_r=225.0, c3_p=225.0, c3_y=36.0,
         c_tau=1.0 / 0.03, c_f=1.0,
+        J_p=0.0, kf0=0.0, kf1=0.0, km1=0.0,
     )
     for k, v in overrides.items():
         if k not in p:
