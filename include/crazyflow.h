@@ -108,7 +108,7 @@ enum sim_param_index {
   SIM_P_MAX_ANGLE, SIM_P_THRUST_SCALE, SIM_P_G,
   SIM_P_C1_R, SIM_P_C1_P, SIM_P_C1_Y, SIM_P_C2_R, SIM_P_C2_P, SIM_P_C2_Y,
   SIM_P_C3_R, SIM_P_C3_P, SIM_P_C3_Y, SIM_P_C_TAU, SIM_P_C_F,
-  SIM_P_JP, SIM_P_KF0, SIM_P_KF1, SIM_P_KM1,
+  SIM_P_J_P, SIM_P_KF0, SIM_P_KF1, SIM_P_KM1,
   SIM_P_COUNT /* = 48 = SIM_NPARAMS */
 };
 

@@ -36,8 +36,12 @@ struct DevParams {
   float mix_a, mix_k, inv_kf, fmax, omega_max;
   // abstracted model, Eqs. 8-10 (per axis roll, pitch, yaw)
   float c1_r, c1_p, c1_y, c2_r, c2_p, c2_y, c3_r, c3_p, c3_y, c_tau, cf_inv_m;
+  // general rotor curves and inertia (used by the general rotor path only):
+  // thrust kf W^2 + kf1 W + kf0, drag torque km W^2 + km1 W; the mixer clips
+  // thrust to [kf0, fmax] and inverts W = (sqrt(kf1^2 + 4 kf (f - kf0)) - kf1) / (2 kf);
+  // rotor angular momentum about z: -Jpc sum_i s_i W_i (Jpc = J_p 2 pi / 60)
+  float kf0, kf1, km1, kf1sq, four_kf, inv_2kf, Jpc;
   int flags;
-  int pad_[3];
 };
 
 enum : int { PF_DRAG = 1, PF_GENERAL_MOTOR = 2 };

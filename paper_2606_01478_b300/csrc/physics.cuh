@@ -69,10 +69,27 @@ __device__ __forceinline__ void deriv_fp(const float* x, const float Wc[4], cons
   const float qx = x[3], qy = x[4], qz = x[5], qw = x[6];
   const float wx = x[10], wy = x[11], wz = x[12];
   const float s0 = x[13] * x[13], s1 = x[14] * x[14], s2 = x[15] * x[15], s3 = x[16] * x[16];
-  const float T = P.kf * ((s0 + s1) + (s2 + s3));
-  const float tx = P.kfa * ((s2 + s3) - (s0 + s1));
-  const float ty = P.kfa * ((s1 + s2) - (s0 + s3));
-  const float tz = P.km * ((s1 + s3) - (s0 + s2));
+  float T, tx, ty, tz;
+  if constexpr (MOTOR == MOTOR_LAG) {
+    T = P.kf * ((s0 + s1) + (s2 + s3));
+    tx = P.kfa * ((s2 + s3) - (s0 + s1));
+    ty = P.kfa * ((s1 + s2) - (s0 + s3));
+    tz = P.km * ((s1 + s3) - (s0 + s2));
+  } else {
+    // polynomial curves: thrust kf W^2 + kf1 W + kf0, drag torque km W^2 + km1 W
+    float f[4], t[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float Wr = x[13 + r];
+      f[r] = fmaf(P.kf, Wr * Wr, fmaf(P.kf1, Wr, P.kf0));
+      t[r] = fmaf(P.km, Wr * Wr, P.km1 * Wr);
+    }
+    const float fa = P.kfa * P.inv_kf;  // the rotor arm a = kfa / kf
+    T = (f[0] + f[1]) + (f[2] + f[3]);
+    tx = fa * ((f[2] + f[3]) - (f[0] + f[1]));
+    ty = fa * ((f[1] + f[2]) - (f[0] + f[3]));
+    tz = (t[1] + t[3]) - (t[0] + t[2]);
+  }
   // thrust along the third column of R(q)
   const float Tm = T * P.inv_m;
   const float r02 = Rc ? Rc[2] : 2.f * fmaf(qx, qz, qw * qy);
@@ -106,12 +123,21 @@ __device__ __forceinline__ void deriv_fp(const float* x, const float Wc[4], cons
   d[7] = ax;
   d[8] = ay;
   d[9] = az;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) d[13 + r] = motor_rate<MOTOR>(x[13 + r], Wc[r], P);
+  if constexpr (MOTOR != MOTOR_LAG) {
+    // rotor angular momentum h e_z, h = -Jpc sum s_i W_i: gyroscopic -w x h and
+    // reaction -dh/dt (Eq. 5)
+    const float h = -P.Jpc * ((x[14] + x[16]) - (x[13] + x[15]));
+    const float dh = -P.Jpc * ((d[14] + d[16]) - (d[13] + d[15]));
+    tx = fmaf(-wy, h, tx);
+    ty = fmaf(wx, h, ty);
+    tz -= dh;
+  }
   // w' = J^-1 tau - J^-1 (w x J w)
   d[10] = fmaf(tx, P.inv_Jx, P.cJx * wy * wz);
   d[11] = fmaf(ty, P.inv_Jy, P.cJy * wz * wx);
   d[12] = fmaf(tz, P.inv_Jz, P.cJz * wx * wy);
-#pragma unroll
-  for (int r = 0; r < 4; ++r) d[13 + r] = motor_rate<MOTOR>(x[13 + r], Wc[r], P);
 }
 
 // Abstracted derivative (Eqs. 7-10) of x[0..12] for u = (Psi_cmd, f_cmd).
@@ -153,6 +179,30 @@ __device__ __forceinline__ void deriv_abs(const float* x, const float u[4], cons
   d[12] = P.c_tau * (u[3] - x[12]);
 }
 
+// Abstracted model without thrust dynamics and drag (last sentence of Abstracted
+// Physics Modeling): thrust c_f f_cmd acts at once; f_sum does not evolve.
+__device__ __forceinline__ void deriv_abs_nothrust(const float* x, const float u[4],
+                                                   const DevParams& P, float* d) {
+  float sr, cr, sp, cp, sy, cy;
+  __sincosf(x[3], &sr, &cr);
+  __sincosf(x[4], &sp, &cp);
+  __sincosf(x[5], &sy, &cy);
+  const float fm = P.cf_inv_m * u[3];
+  d[0] = x[6];
+  d[1] = x[7];
+  d[2] = x[8];
+  d[3] = x[9];
+  d[4] = x[10];
+  d[5] = x[11];
+  d[6] = fm * fmaf(cy * sp, cr, sy * sr);
+  d[7] = fm * fmaf(sy * sp, cr, -cy * sr);
+  d[8] = fmaf(fm, cp * cr, -P.g);
+  d[9] = fmaf(P.c1_r, x[3], fmaf(P.c2_r, x[9], P.c3_r * u[0]));
+  d[10] = fmaf(P.c1_p, x[4], fmaf(P.c2_p, x[10], P.c3_p * u[1]));
+  d[11] = fmaf(P.c1_y, x[5], fmaf(P.c2_y, x[11], P.c3_y * u[2]));
+  d[12] = 0.f;
+}
+
 // ---------------------------------------------------------------- controller
 
 // Attitude action a -> desired rotation Rd and collective thrust Td.
@@ -192,8 +242,10 @@ __device__ __forceinline__ void attitude_torque(const float R[9], const float Rd
   tz = -fmaf(P.KRJh_z, ez, P.KwJ_z * wz);
 }
 
-// X-configuration mixer: per-rotor thrusts from (T, tau), clipped to
-// [0, fmax], converted to rotor-speed commands.
+// X-configuration mixer: per-rotor thrusts from (T, tau), clipped to the
+// thrust curve's range, converted to rotor-speed commands (pure quadratic:
+// sqrt(f / kf); general: the root of kf W^2 + kf1 W + kf0 = f).
+template <int MOTOR = MOTOR_LAG>
 __device__ __forceinline__ void mixer(float T, float tx, float ty, float tz, const DevParams& P,
                                       float Wc[4]) {
   const float A = 0.25f * T, X = tx * P.mix_a, Y = ty * P.mix_a, Z = tz * P.mix_k;
@@ -203,7 +255,15 @@ __device__ __forceinline__ void mixer(float T, float tx, float ty, float tz, con
   f[2] = (A + X) + (Y - Z);
   f[3] = (A + X) - (Y - Z);
 #pragma unroll
-  for (int r = 0; r < 4; ++r) Wc[r] = sqrt_approx(clampf(f[r], 0.f, P.fmax) * P.inv_kf);
+  for (int r = 0; r < 4; ++r) {
+    if constexpr (MOTOR == MOTOR_LAG) {
+      Wc[r] = sqrt_approx(clampf(f[r], 0.f, P.fmax) * P.inv_kf);
+    } else {
+      const float fc = clampf(f[r], P.kf0, P.fmax);
+      const float disc = fmaxf(fmaf(P.four_kf, fc - P.kf0, P.kf1sq), 0.f);
+      Wc[r] = (sqrt_approx(disc) - P.kf1) * P.inv_2kf;
+    }
+  }
 }
 
 // Position PID (geometric): setpoint sp = (x, y, z, yaw) with (sin, cos) of

@@ -1,6 +1,7 @@
 // C-ABI of the B300 drone step: handle management, argument validation,
 // workspace layout, host<->device transfers and kernel dispatch.
 // Declarations and contracts: include/crazyflow.h.
+#define _USE_MATH_DEFINES
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -106,7 +107,8 @@ bool is_device_pointer(const void* p) {
 }
 
 bool valid_enums(int model, int integrator) {
-  return (model == SIM_FIRST_PRINCIPLES || model == SIM_ABSTRACTED) &&
+  return (model == SIM_FIRST_PRINCIPLES || model == SIM_ABSTRACTED ||
+          model == SIM_ABSTRACTED_NOTHRUST) &&
          (integrator == SIM_EULER || integrator == SIM_RK4);
 }
 
@@ -184,9 +186,19 @@ int derive_params(const float* p, DevParams* d, char* why, size_t why_n) {
   d->c3_y = p[SIM_P_C3_Y];
   d->c_tau = p[SIM_P_C_TAU];
   d->cf_inv_m = (float)(p[SIM_P_C_F] / m);
+  const double kf0 = p[SIM_P_KF0], kf1 = p[SIM_P_KF1];
+  d->kf0 = (float)kf0;
+  d->kf1 = (float)kf1;
+  d->km1 = p[SIM_P_KM1];
+  d->kf1sq = (float)(kf1 * kf1);
+  d->four_kf = (float)(4.0 * kf);
+  d->inv_2kf = (float)(1.0 / (2.0 * kf));
+  d->Jpc = (float)(p[SIM_P_J_P] * 2.0 * M_PI / 60.0);
+  d->fmax = (float)(kf * wmax * wmax + kf1 * wmax + kf0);
   int flags = 0;
   if (p[SIM_P_CA_X] != 0.f || p[SIM_P_CA_Y] != 0.f || p[SIM_P_CA_Z] != 0.f) flags |= cf::PF_DRAG;
-  if (p[SIM_P_CV_UP] != p[SIM_P_CV_DOWN] || p[SIM_P_CD_UP] != 0.f || p[SIM_P_CD_DOWN] != 0.f)
+  if (p[SIM_P_CV_UP] != p[SIM_P_CV_DOWN] || p[SIM_P_CD_UP] != 0.f || p[SIM_P_CD_DOWN] != 0.f ||
+      p[SIM_P_J_P] != 0.f || kf0 != 0.0 || kf1 != 0.0 || p[SIM_P_KM1] != 0.f)
     flags |= cf::PF_GENERAL_MOTOR;
   d->flags = flags;
   return SIM_OK;
@@ -263,10 +275,11 @@ int sim_create_batched(sim_h* out, int64_t M, const int64_t* n_per_world,
 
 int sim_set_control(sim_h h, int ctrl) {
   if (!h) return SIM_EINVAL;
-  if (ctrl != SIM_CTRL_ROTOR_SPEED && ctrl != SIM_CTRL_ATTITUDE && ctrl != SIM_CTRL_POSITION)
+  if (ctrl != SIM_CTRL_ROTOR_SPEED && ctrl != SIM_CTRL_ATTITUDE && ctrl != SIM_CTRL_POSITION &&
+      ctrl != SIM_CTRL_TORQUE)
     return fail(h, SIM_EINVAL, "unknown control interface %d", ctrl);
-  bool any_abs = h->batched ? false : h->model == SIM_ABSTRACTED;
-  for (int32_t m : h->model_of_world) any_abs |= (m == SIM_ABSTRACTED);
+  bool any_abs = h->batched ? false : h->model != SIM_FIRST_PRINCIPLES;
+  for (int32_t m : h->model_of_world) any_abs |= (m != SIM_FIRST_PRINCIPLES);
   if (any_abs && ctrl != SIM_CTRL_ATTITUDE)
     return fail(h, SIM_EINVAL, "the abstracted model takes attitude commands only");
   h->ctrl = ctrl;

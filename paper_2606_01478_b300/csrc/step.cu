@@ -79,8 +79,10 @@ __global__ void __launch_bounds__(256) step_batched_kernel(StepArgs a, const int
       const DevParams P = a.params[a.set_of_world[d.z]];
       if (d.w == SIM_FIRST_PRINCIPLES) {
         run_drone<SIM_FIRST_PRINCIPLES, INTEG, CTRL, MOTOR>(a, d.x + lane, P);
-      } else {
+      } else if (d.w == SIM_ABSTRACTED) {
         run_drone<SIM_ABSTRACTED, INTEG, SIM_CTRL_ATTITUDE, MOTOR_LAG>(a, d.x + lane, P);
+      } else {
+        run_drone<SIM_ABSTRACTED_NOTHRUST, INTEG, SIM_CTRL_ATTITUDE, MOTOR_LAG>(a, d.x + lane, P);
       }
     }
   }
@@ -119,10 +121,12 @@ cudaError_t launch_step_batched(const StepArgs& a, const int4* tiles, int n_tile
   if (integrator == SIM_RK4) {
     if (ctrl == SIM_CTRL_ROTOR_SPEED) CF_B(SIM_RK4, SIM_CTRL_ROTOR_SPEED);
     if (ctrl == SIM_CTRL_POSITION) CF_B(SIM_RK4, SIM_CTRL_POSITION);
+    if (ctrl == SIM_CTRL_TORQUE) CF_B(SIM_RK4, SIM_CTRL_TORQUE);
     CF_B(SIM_RK4, SIM_CTRL_ATTITUDE);
   }
   if (ctrl == SIM_CTRL_ROTOR_SPEED) CF_B(SIM_EULER, SIM_CTRL_ROTOR_SPEED);
   if (ctrl == SIM_CTRL_POSITION) CF_B(SIM_EULER, SIM_CTRL_POSITION);
+  if (ctrl == SIM_CTRL_TORQUE) CF_B(SIM_EULER, SIM_CTRL_TORQUE);
   CF_B(SIM_EULER, SIM_CTRL_ATTITUDE);
 #undef CF_B
 }
@@ -148,8 +152,8 @@ static cudaError_t launch_m(const StepArgs& a, const DevParams& P, bool gm, bool
 template <int MODEL, int INTEG>
 static cudaError_t launch_c(const StepArgs& a, const DevParams& P, int ctrl, bool gm, bool perset,
                             int tpb, cudaStream_t st) {
-  if constexpr (MODEL == SIM_ABSTRACTED) {
-    // the abstracted model has no rotors: motor kind is irrelevant
+  if constexpr (MODEL != SIM_FIRST_PRINCIPLES) {
+    // the abstracted models have no rotors: motor kind is irrelevant
     return perset ? launch_t<MODEL, INTEG, SIM_CTRL_ATTITUDE, MOTOR_LAG, true>(a, P, tpb, st)
                   : launch_t<MODEL, INTEG, SIM_CTRL_ATTITUDE, MOTOR_LAG, false>(a, P, tpb, st);
   } else {
@@ -158,6 +162,8 @@ static cudaError_t launch_c(const StepArgs& a, const DevParams& P, int ctrl, boo
         return launch_m<MODEL, INTEG, SIM_CTRL_ROTOR_SPEED>(a, P, gm, perset, tpb, st);
       case SIM_CTRL_POSITION:
         return launch_m<MODEL, INTEG, SIM_CTRL_POSITION>(a, P, gm, perset, tpb, st);
+      case SIM_CTRL_TORQUE:
+        return launch_m<MODEL, INTEG, SIM_CTRL_TORQUE>(a, P, gm, perset, tpb, st);
       default:
         return launch_m<MODEL, INTEG, SIM_CTRL_ATTITUDE>(a, P, gm, perset, tpb, st);
     }
@@ -171,6 +177,13 @@ cudaError_t launch_step(const StepArgs& a, const DevParams& P, int model, int in
                ? launch_c<SIM_FIRST_PRINCIPLES, SIM_RK4>(a, P, ctrl, general_motor, per_set, tpb, st)
                : launch_c<SIM_FIRST_PRINCIPLES, SIM_EULER>(a, P, ctrl, general_motor, per_set, tpb,
                                                            st);
+  }
+  if (model == SIM_ABSTRACTED_NOTHRUST) {
+    return integrator == SIM_RK4
+               ? launch_c<SIM_ABSTRACTED_NOTHRUST, SIM_RK4>(a, P, ctrl, general_motor, per_set, tpb,
+                                                            st)
+               : launch_c<SIM_ABSTRACTED_NOTHRUST, SIM_EULER>(a, P, ctrl, general_motor, per_set,
+                                                              tpb, st);
   }
   return integrator == SIM_RK4
              ? launch_c<SIM_ABSTRACTED, SIM_RK4>(a, P, ctrl, general_motor, per_set, tpb, st)

@@ -19,8 +19,11 @@ struct CtrlHold {
 
 template <int MODEL, int CTRL>
 __device__ __forceinline__ void decode_command(float4 c, const DevParams& P, CtrlHold& h) {
-  if constexpr (MODEL == SIM_ABSTRACTED) {
+  if constexpr (MODEL != SIM_FIRST_PRINCIPLES) {
     abstracted_command(c, P, h.u);
+  } else if constexpr (CTRL == SIM_CTRL_TORQUE) {
+    h.Td = c.x;
+    h.sp = c;  // body torque in (y, z, w)
   } else if constexpr (CTRL == SIM_CTRL_ATTITUDE) {
     attitude_command(c, P, h.Rd, h.Td);
   } else if constexpr (CTRL == SIM_CTRL_POSITION) {
@@ -46,24 +49,28 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
     if constexpr (CTRL == SIM_CTRL_ROTOR_SPEED) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) Wc[r] = h.Wc[r];
+    } else if constexpr (CTRL == SIM_CTRL_TORQUE) {
+      mixer<MOTOR>(h.Td, h.sp.y, h.sp.z, h.sp.w, P, Wc);
     } else {
       float tx, ty, tz;
       if constexpr (CTRL == SIM_CTRL_POSITION) {
         float Rd[9], Td;
         position_command(s, R, h.sp, h.syaw, h.cyaw, P, Rd, Td, ep);
         attitude_torque(R, Rd, s[10], s[11], s[12], P, tx, ty, tz);
-        mixer(Td, tx, ty, tz, P, Wc);
+        mixer<MOTOR>(Td, tx, ty, tz, P, Wc);
       } else {
         attitude_torque(R, h.Rd, s[10], s[11], s[12], P, tx, ty, tz);
-        mixer(h.Td, tx, ty, tz, P, Wc);
+        mixer<MOTOR>(h.Td, tx, ty, tz, P, Wc);
       }
     }
   }
   auto deriv = [&](const float* x, float* d, const float* Rx) {
     if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
       deriv_fp<MOTOR>(x, Wc, P, drag, d, Rx);
-    } else {
+    } else if constexpr (MODEL == SIM_ABSTRACTED) {
       deriv_abs(x, h.u, P, drag, d);
+    } else {
+      deriv_abs_nothrust(x, h.u, P, d);
     }
   };
   const float* R0 = (MODEL == SIM_FIRST_PRINCIPLES) ? R : nullptr;
@@ -97,6 +104,7 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
 #pragma unroll
     for (int j = 0; j < D; ++j) s[j] = fmaf(h6, acc[j] + k[j], s[j]);
   }
+  if constexpr (MODEL == SIM_ABSTRACTED_NOTHRUST) s[12] = h.u[3];  // f_sum follows f_cmd at once
   if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
     const float in = rsqrt_approx(fmaf(s[3], s[3], fmaf(s[4], s[4], fmaf(s[5], s[5], s[6] * s[6]))));
     s[3] *= in;

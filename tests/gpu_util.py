@@ -40,7 +40,7 @@ def make_sim(wl, max_blocks=None, tpb=None, device="cuda"):
 def field_errors(gpu: np.ndarray, ref: np.ndarray, model_of_drone: np.ndarray) -> dict:
     """Max abs error per named field, split by model."""
     out = {}
-    for model, slices in ((0, FP_SLICES), (1, ABS_SLICES)):
+    for model, slices in ((0, FP_SLICES), (1, ABS_SLICES), (2, ABS_SLICES)):
         sel = model_of_drone == model
         if not sel.any():
             continue

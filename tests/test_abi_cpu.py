@@ -42,7 +42,7 @@ def test_param_order_matches_header():
     body = body[body.index("{") + 1:body.index("SIM_P_COUNT")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     names = [t.strip().split("=")[0].strip() for t in body.split(",") if t.strip()]
-    assert len(names) == len(L.PARAM_ORDER) == 44
+    assert len(names) == len(L.PARAM_ORDER) == 48
     for hname, pname in zip(names, L.PARAM_ORDER):
         assert hname == "SIM_P_" + pname.upper()
     assert tuple(W.PARAM_NAMES) == L.PARAM_ORDER
