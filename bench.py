@@ -369,7 +369,7 @@ def run_b300(args, wl):
     if not args.no_extra:
         line["extra"] = {"config2": measure_config2(dev), "config3": measure_config3(dev),
                          "config4": measure_config4(dev), "mppi": measure_mppi(dev),
-                         "bptt_training": measure_bptt_training(dev)}
+                         "bptt_training": measure_bptt_training(dev), "depth": measure_depth(dev)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)
@@ -627,6 +627,33 @@ def measure_bptt_training(dev, reps: int = 3) -> dict:
                              "with the paper's reward (this build's loss differs)"}
 
 
+def measure_depth(dev, reps: int = 3) -> dict:
+    """Depth images at the paper's scale (64 x 64 rays, 1024 environments, one
+    camera per drone): config 4's 32 obstacles as spheres plus 8 boxes and the
+    ground; frames per second of one batched launch."""
+    import math
+    from paper_2606_01478_b300 import RK4, Sim
+    rng = np.random.default_rng(1006)
+    n = 1024
+    wl4 = W.config4(M=8)
+    P = W.crazyflie_params()
+    x = np.zeros((n, 20))
+    x[:, 0:3] = rng.uniform([-1.5, -1.5, 0.5], [1.5, 1.5, 3.5], (n, 3))
+    x[:, 3:7] = W.quat_from_rpy(rng.uniform([-0.3, -0.3, -np.pi], [0.3, 0.3, np.pi], (n, 3)))
+    x[:, 13:17] = W.hover_rpm(P)
+    sim = Sim(n, 1, 0, RK4, 1 / 500, device=dev)
+    sim.set_params(P)
+    sim.set_state(torch.tensor(x, dtype=torch.float32, device=dev))
+    lo = rng.uniform([-3, -3, 0], [2, 2, 1.5], (8, 3))
+    boxes = np.concatenate([lo, lo + rng.uniform(0.3, 1.0, (8, 3))], 1)
+    out = torch.empty(n, 64, 64, device=dev)
+    ms = _time_ms(lambda: sim.render_depth(64, 64, math.radians(90), math.radians(90), 10.0,
+                                           wl4.obstacles, boxes, out=out), reps, dev)
+    return {"workload": "depth_1024x64x64_32spheres_8boxes", "ms_per_batch": ms,
+            "frames_per_s": n / (ms / 1e3), "rays_per_s": n * 64 * 64 / (ms / 1e3),
+            "paper_context": "350k frames/s at 64x64 across 1024 environments (MJX ray casting)"}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -636,7 +663,7 @@ def main(argv=None):
     ap.add_argument("--tpb", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the config-2/3/4 measurements")
-    ap.add_argument("--only", choices=["c2", "c3", "c4", "mppi", "bptt"], default=None,
+    ap.add_argument("--only", choices=["c2", "c3", "c4", "mppi", "bptt", "depth"], default=None,
                     help="run one extra workload alone and print its record (for profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
@@ -646,7 +673,7 @@ def main(argv=None):
         torch.cuda.set_device(local)
         dev = torch.device("cuda", local)
         fn = {"c2": measure_config2, "c3": measure_config3, "c4": measure_config4,
-              "mppi": measure_mppi, "bptt": measure_bptt_training}[args.only]
+              "mppi": measure_mppi, "bptt": measure_bptt_training, "depth": measure_depth}[args.only]
         print(json.dumps({"only": args.only, "record": fn(dev, reps=args.steps)}), flush=True)
         return 0
     rank = int(os.environ.get("RANK", "0"))

@@ -250,6 +250,28 @@ int sim_mppi_iteration(sim_h h, const sim_mppi_config* cfg, const uint64_t* seed
                        float* plan, float* cost, float* best_cost, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched depth images by ray casting (the paper's parallel depth rendering,
+ * Results, Computation Performance; here as CUDA arithmetic, no graphics API).
+ * Every drone of the handle carries a pinhole camera at its centre looking
+ * along body +x; pixel (row i, column j) casts the ray
+ *   normalise(1, -tan(hfov/2) (2 (j + 0.5) / W - 1), -tan(vfov/2) (2 (i + 0.5) / H - 1))
+ * in the body frame, rotated by the drone's current attitude; depth = range to
+ * the first hit among the spheres, the axis-aligned boxes and the ground plane
+ * z = 0, clipped to max_range.  spheres: HOST [n_spheres][4] (centre, radius);
+ * boxes: HOST [n_boxes][6] (min corner, max corner); both read during the call
+ * (passed by value).  depth: device [Ntot][height][width] float.  Requires
+ * first-principles drones (quaternion attitude).  One launch. */
+#define SIM_MAX_SPHERES 64
+#define SIM_MAX_BOXES 32
+typedef struct {
+  int height, width;     /* pixels */
+  float hfov, vfov;      /* full fields of view, radians, in (0, pi) */
+  float max_range;       /* metres */
+} sim_camera;
+int sim_render_depth(sim_h h, const sim_camera* cam, const float* spheres, int n_spheres,
+                     const float* boxes, int n_boxes, float* depth, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Differentiable policy rollout (backpropagation through time; Materials and
  * Methods, Backpropagation Through Time).  For every drone of the handle,
  * independently:

@@ -34,6 +34,12 @@ PARAM_ORDER = (
     "J_p", "kf0", "kf1", "km1",
 )
 
+class Camera(ctypes.Structure):
+    """sim_camera (include/crazyflow.h)."""
+    _fields_ = [("height", c_int), ("width", c_int), ("hfov", c_float), ("vfov", c_float),
+                ("max_range", c_float)]
+
+
 class MppiConfig(ctypes.Structure):
     """sim_mppi_config (include/crazyflow.h)."""
     _fields_ = [("S", c_int), ("H", c_int), ("n_ctrl", c_int), ("sigma", c_float), ("rho", c_float),
@@ -66,6 +72,8 @@ _SIGS = {
                                    c_void_p]),
     "sim_adam_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p,
                               c_float, c_float, c_float, c_float, c_void_p]),
+    "sim_render_depth": (c_int, [c_void_p, POINTER(Camera), POINTER(c_float), c_int, POINTER(c_float),
+                                 c_int, c_void_p, c_void_p]),
     "sim_philox_normals": (c_int, [c_void_p, ctypes.c_uint64, c_int64, c_int, c_void_p, c_void_p,
                                    c_void_p]),
     "sim_rollout_workspace_bytes": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),

@@ -45,6 +45,11 @@ cudaError_t launch_philox(const unsigned long long* seed, unsigned long long fir
 cudaError_t launch_adam(const float* g, float* w, float* m, float* v, uint16_t* wb, int n, int* step,
                         float lr, float b1, float b2, float eps, cudaStream_t st);
 
+// Depth rendering by ray casting (raycast.cu).
+cudaError_t launch_depth(const float4* planes, int n, int H, int W, float hfov, float vfov,
+                         float max_range, const float* spheres, int n_sph, const float* boxes,
+                         int n_box, float* out, cudaStream_t st);
+
 // Record a message as the handle's last error (sim.cu); used by entry points
 // defined in other translation units.
 void note_error(sim_h h, const char* fmt, ...);

@@ -564,6 +564,34 @@ int sim_mppi_iteration(sim_h h, const sim_mppi_config* cfg, const uint64_t* seed
 }
 
 
+int sim_render_depth(sim_h h, const sim_camera* cam, const float* spheres, int n_spheres,
+                     const float* boxes, int n_boxes, float* depth, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!h->ws || !h->state_ok) return fail(h, SIM_ESTATE, "bind and state must be set before rendering");
+  bool all_fp = h->batched ? true : h->model == SIM_FIRST_PRINCIPLES;
+  for (int32_t m : h->model_of_world) all_fp &= (m == SIM_FIRST_PRINCIPLES);
+  if (!all_fp) return fail(h, SIM_EINVAL, "depth rendering needs first-principles drones");
+  if (!cam || cam->height < 1 || cam->width < 1 || (int64_t)cam->height * cam->width > (1 << 24) ||
+      !(cam->hfov > 0.f && cam->hfov < 3.14159f) || !(cam->vfov > 0.f && cam->vfov < 3.14159f) ||
+      !(cam->max_range > 0.f) || !isfinite(cam->max_range))
+    return fail(h, SIM_EINVAL, "bad camera");
+  if (n_spheres < 0 || n_spheres > SIM_MAX_SPHERES || n_boxes < 0 || n_boxes > SIM_MAX_BOXES ||
+      (n_spheres > 0 && !spheres) || (n_boxes > 0 && !boxes))
+    return fail(h, SIM_EINVAL, "at most %d spheres and %d boxes", SIM_MAX_SPHERES, SIM_MAX_BOXES);
+  for (int i = 0; i < 4 * n_spheres; ++i)
+    if (!isfinite(spheres[i])) return fail(h, SIM_EINVAL, "sphere values must be finite");
+  for (int i = 0; i < 6 * n_boxes; ++i)
+    if (!isfinite(boxes[i])) return fail(h, SIM_EINVAL, "box values must be finite");
+  if (!depth || ((uintptr_t)depth & 3)) return fail(h, SIM_EINVAL, "bad depth buffer");
+  if (h->ntot > 65535) return fail(h, SIM_EINVAL, "at most 65535 cameras per call");
+  cudaError_t e = cf::launch_depth(h->planes, (int)h->ntot, cam->height, cam->width, cam->hfov,
+                                   cam->vfov, cam->max_range, spheres, n_spheres, boxes, n_boxes,
+                                   depth, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "depth launch");
+  h->launches++;
+  return SIM_OK;
+}
+
 int sim_philox_normals(const uint64_t* seed, uint64_t first_id, int64_t n, int step, uint32_t* words,
                        float* normals, void* stream) {
   if (!seed || ((uintptr_t)seed & 7) || n < 0 || step < 0 || (!words && !normals)) return SIM_EINVAL;

@@ -201,6 +201,22 @@ class Sim:
             ctypes.c_void_p(cost.data_ptr()), ctypes.c_void_p(best_cost.data_ptr()), _stream_ptr(stream)))
         return plan, cost, best_cost
 
+    def render_depth(self, height: int, width: int, hfov: float, vfov: float, max_range: float,
+                     spheres=(), boxes=(), out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+        """Depth images [Ntot, height, width] from each drone's pinhole camera
+        (see sim_render_depth).  spheres [n, 4], boxes [n, 6]: host arrays."""
+        cam = L.Camera(int(height), int(width), float(hfov), float(vfov), float(max_range))
+        sph = np.ascontiguousarray(np.asarray(spheres, dtype=np.float32).reshape(-1, 4))
+        box = np.ascontiguousarray(np.asarray(boxes, dtype=np.float32).reshape(-1, 6))
+        if out is None:
+            out = torch.empty(self.ntot, int(height), int(width), dtype=torch.float32, device=self.device)
+        self._check(self.lib.sim_render_depth(
+            self.h, ctypes.byref(cam), sph.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), sph.shape[0],
+            box.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), box.shape[0],
+            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
     def status(self, stream=None) -> int:
         v = ctypes.c_uint32()
         self._check(self.lib.sim_status(self.h, ctypes.byref(v), _stream_ptr(stream)))

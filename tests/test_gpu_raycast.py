@@ -1,0 +1,89 @@
+"""GPU depth rendering against the FP64 ray-cast oracle.  Rays that graze a
+silhouette may hit in one precision and miss in the other; those pixels are
+allowed to differ only where the oracle image itself has a depth edge, and
+only for a small fraction of pixels."""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy.spatial.transform import Rotation
+
+import workloads as W
+from oracle import raycast as rc
+from paper_2606_01478_b300 import RK4, Sim
+
+pytestmark = pytest.mark.gpu
+
+
+def _sim_with_poses(pos, quat):
+    n = len(pos)
+    P = W.crazyflie_params()
+    x = np.zeros((n, 20))
+    x[:, 0:3] = pos
+    x[:, 3:7] = quat
+    x[:, 13:17] = W.hover_rpm(P)
+    sim = Sim(n, 1, 0, RK4, 1 / 500)
+    sim.set_params(P)
+    sim.set_state(torch.tensor(x, dtype=torch.float32, device="cuda"))
+    return sim, x
+
+
+def _scene(seed):
+    rng = np.random.default_rng(seed)
+    sph = np.concatenate([rng.uniform([-3, -3, 0], [3, 3, 3], (12, 3)), rng.uniform(0.2, 0.6, (12, 1))], 1)
+    lo = rng.uniform([-3, -3, 0], [2, 2, 1.5], (4, 3))
+    box = np.concatenate([lo, lo + rng.uniform(0.3, 1.2, (4, 3))], 1)
+    return sph, box
+
+
+def _edge_mask(img, rel=0.02):
+    """Pixels whose 3x3 neighbourhood holds a depth jump above rel."""
+    pad = np.pad(img, ((0, 0), (1, 1), (1, 1)), mode="edge")
+    jump = np.zeros(img.shape, bool)
+    for di in (-1, 0, 1):
+        for dj in (-1, 0, 1):
+            nb = pad[:, 1 + di:1 + di + img.shape[1], 1 + dj:1 + dj + img.shape[2]]
+            jump |= np.abs(nb - img) > rel * img
+    return jump
+
+
+def test_random_poses_match_oracle():
+    rng = np.random.default_rng(7)
+    n = 48
+    pos = rng.uniform([-2, -2, 0.5], [2, 2, 2.5], (n, 3))
+    quat = Rotation.from_euler("ZYX", rng.uniform([-np.pi, -0.7, -0.7], [np.pi, 0.7, 0.7], (n, 3))).as_quat()
+    sim, x = _sim_with_poses(pos, quat)
+    sph, box = _scene(3)
+    H, Wd, hf, vf, mr = 37, 53, math.radians(90), math.radians(70), 12.0
+    gpu = sim.render_depth(H, Wd, hf, vf, mr, sph, box).cpu().numpy().astype(np.float64)
+    poses = x[:, 0:7].astype(np.float32).astype(np.float64)
+    ref = rc.render(poses, sph.astype(np.float32).astype(np.float64),
+                    box.astype(np.float32).astype(np.float64), H, Wd, hf, vf, mr)
+    ok = np.abs(gpu - ref) <= 1e-4 * ref + 1e-4
+    bad = ~ok
+    assert bad.mean() < 5e-3, bad.mean()
+    assert np.all(_edge_mask(ref)[bad]), "a mismatch away from any silhouette"
+    assert (ref < mr).mean() > 0.3  # the scene is actually seen
+
+
+def test_downward_cameras_closed_form():
+    n = 1024
+    rng = np.random.default_rng(8)
+    h = rng.uniform(0.5, 4.0, n)
+    pos = np.stack([rng.uniform(-5, 5, n), rng.uniform(-5, 5, n), h], 1)
+    quat = Rotation.from_euler("ZYX", np.stack([rng.uniform(-np.pi, np.pi, n), np.full(n, np.pi / 2),
+                                                 np.zeros(n)], 1)).as_quat()
+    sim, x = _sim_with_poses(pos, quat)
+    img = sim.render_depth(64, 64, math.radians(60), math.radians(60), 100.0).cpu().numpy()
+    d = rc.ray_directions(64, 64, math.radians(60), math.radians(60))
+    expect = x[:, 2].astype(np.float32).astype(np.float64)[:, None, None] / d[None, :, :, 0]
+    np.testing.assert_allclose(img, expect, rtol=2e-5)
+
+
+def test_rejects_bad_cameras():
+    sim, _ = _sim_with_poses(np.zeros((2, 3)) + [0, 0, 1], np.tile([0, 0, 0, 1.0], (2, 1)))
+    with pytest.raises(Exception):
+        sim.render_depth(8, 8, 3.2, 1.0, 10.0)
+    with pytest.raises(Exception):
+        sim.render_depth(8, 8, 1.0, 1.0, 10.0, spheres=np.zeros((65, 4)))
