@@ -280,6 +280,15 @@ int sim_render_depth(sim_h h, const sim_camera* cam, const float* spheres, int n
  *   x_{k+1} = one Euler step of the first-principles model under the attitude
  *             interface with command a_k, k = 0 .. H-1
  *   L = (1/Ntot) sum_drones sum_k |p_{k+1} - r_{k+1}|^2 + w_act |a_k|^2
+ * (the squared objective, default) or, after sim_rollout_set_objective with
+ * SIM_OBJ_TRACKING_REWARD, the paper's tracking reward (Backpropagation Through
+ * Time, reward equation; discount 1) negated as a loss:
+ *   L = (1/Ntot) sum_drones sum_k [ -exp(-2 |p_{k+1} - r_{k+1}|) + w_theta theta_{k+1}
+ *         + sum_i w_act[i] a_k,i^2 + w_dact[i] (a_k,i - a_{k-1},i)^2 ]
+ * with theta the tilt from upright (angle between body z and world z),
+ * a_{-1} = 0 = the hover action of the attitude map, and gradient 0 at the
+ * kinks of |p - r| and theta.  The w_act argument of the calls below is then
+ * unused.
  * Requires a handle created with SIM_FIRST_PRINCIPLES and SIM_EULER, one
  * parameter set with a first-order-lag rotor model (cv_up = cv_down, cd = 0)
  * and zero drag.  The policy MLP runs on tensor cores with bf16 weights and
@@ -292,6 +301,8 @@ int sim_render_depth(sim_h h, const sim_camera* cam, const float* spheres, int n
  *   p_ref [H+1][Ntot][3] float          reference positions r_k
  *   ws    rollout workspace of sim_rollout_workspace_bytes(h, H, C) bytes:
  *         checkpoints every C steps, segment states, per-drone losses, dW partials
+ *         (and the previous actions under the tracking reward: the size depends
+ *         on the objective set on the handle)
  *   loss  [1] float; dL [1] float (upstream gradient, read on the device);
  *   dW    [SIM_POLICY_NPARAMS] float = dL * dL/dw (in the packed order of w)
  *   dx0   [Ntot][SIM_STATE_DIM] float = dL * dL/dx0 (slots 17..19 = 0)
@@ -300,6 +311,21 @@ int sim_render_depth(sim_h h, const sim_camera* cam, const float* spheres, int n
  * are deterministic (fixed-order reductions).  1 <= C <= H.
  */
 #define SIM_POLICY_NPARAMS 5316
+#define SIM_OBJ_SQUARED 0
+#define SIM_OBJ_TRACKING_REWARD 1
+/* Weights of the tracking reward (the paper's BPTT table: w_theta 0.1,
+ * w_act (0.12, 0.12, 0, 0.02), w_dact (1.4, 1.4, 0, 0.8)); action order
+ * roll, pitch, yaw, thrust. */
+typedef struct sim_objective {
+  int kind;            /* SIM_OBJ_SQUARED or SIM_OBJ_TRACKING_REWARD */
+  float w_theta;       /* tilt weight */
+  float w_act[4];      /* action (distance from hover) weights */
+  float w_dact[4];     /* action smoothness weights */
+} sim_objective;
+/* Objective of every later rollout call on the handle (host-side setting; obj
+ * NULL restores SIM_OBJ_SQUARED).  SIM_EINVAL for an unknown kind or a weight
+ * that is negative or not finite. */
+int sim_rollout_set_objective(sim_h h, const sim_objective* obj);
 int sim_rollout_workspace_bytes(sim_h h, int H, int C, size_t* bytes);
 int sim_rollout_fwd(sim_h h, const float* x0, const uint16_t* w, const float* p_ref, int H, int C,
                     float w_act, void* ws, size_t ws_bytes, float* loss, void* stream);

@@ -40,6 +40,14 @@ class Camera(ctypes.Structure):
                 ("max_range", c_float)]
 
 
+class Objective(ctypes.Structure):
+    """sim_objective (include/crazyflow.h)."""
+    _fields_ = [("kind", c_int), ("w_theta", c_float), ("w_act", c_float * 4), ("w_dact", c_float * 4)]
+
+
+OBJ_SQUARED, OBJ_TRACKING_REWARD = 0, 1
+
+
 class MppiConfig(ctypes.Structure):
     """sim_mppi_config (include/crazyflow.h)."""
     _fields_ = [("S", c_int), ("H", c_int), ("n_ctrl", c_int), ("sigma", c_float), ("rho", c_float),
@@ -76,6 +84,7 @@ _SIGS = {
                                  c_int, c_void_p, c_void_p]),
     "sim_philox_normals": (c_int, [c_void_p, ctypes.c_uint64, c_int64, c_int, c_void_p, c_void_p,
                                    c_void_p]),
+    "sim_rollout_set_objective": (c_int, [c_void_p, POINTER(Objective)]),
     "sim_rollout_workspace_bytes": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),
     "sim_rollout_fwd": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_float,
                                 c_void_p, c_size_t, c_void_p, c_void_p]),

@@ -18,15 +18,23 @@ cudaError_t launch_step_batched(const StepArgs& a, const int4* tiles, int n_tile
 
 // Differentiable policy rollout (rollout.cu).  Workspace: checkpoints
 // [ceil(H/C)][n][20], segment states [C][n][20], per-drone loss [n], per-CTA dW
-// partials; all fp32.
+// partials; all fp32; with the tracking reward also the previous action at each
+// checkpoint [ceil(H/C)][n] and segment step [C][n] (float4).
 constexpr int POLICY_NPARAMS = 5316;
-size_t rollout_workspace_bytes(int n, int H, int C);
+// Objective of the policy rollout (SIM_OBJ_*) with the tracking-reward weights.
+struct RolloutObjective {
+  int kind = SIM_OBJ_SQUARED;
+  float w_theta = 0.f, w_act[4] = {0.f, 0.f, 0.f, 0.f}, w_dact[4] = {0.f, 0.f, 0.f, 0.f};
+};
+size_t rollout_workspace_bytes(int n, int H, int C, int objective);
 cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
-                               int C, float dt, float w_act, const DevParams& P, void* ws,
+                               int C, float dt, float w_act, const RolloutObjective& obj,
+                               const DevParams& P, void* ws,
                                float* loss, bool store_ckpt, cudaStream_t st);
 cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
-                               int C, float dt, float w_act, const DevParams& P, void* ws,
-                               const float* dL, float* dW, float* dx0, cudaStream_t st);
+                               int C, float dt, float w_act, const RolloutObjective& obj,
+                               const DevParams& P, void* ws, const float* dL, float* dW, float* dx0,
+                               cudaStream_t st);
 
 // Batched sampling rollouts (sample.cu).
 cudaError_t launch_sample(const float4* planes, int n, const int* offsets, int M, int N,

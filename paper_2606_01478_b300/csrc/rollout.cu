@@ -6,8 +6,13 @@
 //   obs_k = [p_k - r_k, q_k, v_k, w_k];  a_k = MLP(obs_k)  (13 -> 64 -> 64 -> 4, tanh)
 //   x_{k+1} = Euler step of the first-principles model under the attitude
 //             interface with action a_k (controller, mixer, motor lag, Eqs. 1-6)
-//   L = (1/M) sum_w sum_k |p_{k+1} - r_{k+1}|^2 + w_act |a_k|^2
-// Forward kernel: rollout + loss, checkpoints of x every C steps.
+//   L = (1/M) sum_w sum_k |p_{k+1} - r_{k+1}|^2 + w_act |a_k|^2          (squared objective)
+// or the paper's tracking reward (BPTT section, reward equation), as a loss:
+//   L = (1/M) sum_w sum_k -exp(-2 |p_{k+1} - r_{k+1}|) + w_theta theta_{k+1}
+//         + sum_i w_act,i a_k,i^2 + w_dact,i (a_k,i - a_{k-1},i)^2,   a_{-1} = 0,
+//   theta = 2 atan2(|(qx, qy)|, |(qz, qw)|) the tilt from upright.
+// Forward kernel: rollout + loss, checkpoints of x (and, for the reward, of the
+// previous action) every C steps.
 // Backward kernel: per segment, recompute the C states from the checkpoint,
 // then sweep them in reverse with the hand-written adjoint of the step and of
 // the MLP; accumulate dL/dW per CTA; dL/dx0 per drone.
@@ -58,8 +63,11 @@ struct RolloutArgs {
   float* part;            // [n_cta][NPOL_PAD] dW partials
   float* dx0;             // [n][20]
   const float* dL;        // device scalar: upstream gradient of the loss
+  float4* ckpt_a;         // [n_ckpt][n] previous action at each checkpoint (reward objective)
+  float4* seg_a;          // [C][n] previous action of each segment step (reward objective)
   int n, H, C;
   float dt, w_act, inv_n;
+  float w_theta, w_a[4], w_da[4];  // tracking-reward weights
   int store_ckpt;
 };
 
@@ -694,8 +702,67 @@ __device__ __forceinline__ void ref_at(const float* __restrict__ p_ref, int k, i
   r[2] = q[2];
 }
 
+// ------------------------------------------------------------------ objectives
+
+// Loss of one step: x = post-step state, r = reference at that step, act the
+// step's action, ap the previous one.
+template <int OBJ>
+__device__ __forceinline__ float step_loss(const float* x, const float r[3], const float act[4],
+                                           const float ap[4], const RolloutArgs& a) {
+  const float ex = x[0] - r[0], ey = x[1] - r[1], ez = x[2] - r[2];
+  if (OBJ == SIM_OBJ_SQUARED)
+    return fmaf(ex, ex, fmaf(ey, ey, ez * ez)) +
+           a.w_act * fmaf(act[0], act[0], fmaf(act[1], act[1], fmaf(act[2], act[2], act[3] * act[3])));
+  const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+  const float s = sqrtf(fmaf(x[3], x[3], x[4] * x[4])), c = sqrtf(fmaf(x[5], x[5], x[6] * x[6]));
+  float L = fmaf(a.w_theta, 2.f * atan2f(s, c), -expf(-2.f * d));
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const float da = act[o] - ap[o];
+    L = fmaf(a.w_a[o] * act[o], act[o], fmaf(a.w_da[o] * da, da, L));
+  }
+  return L;
+}
+
+// Adds sd * dL_step/dx (position and attitude terms) to lam; xn = post-step state.
+template <int OBJ>
+__device__ __forceinline__ void step_loss_state_adjoint(const float* xn, const float r[3], float sd,
+                                                        const RolloutArgs& a, float* lam) {
+  const float ex = xn[0] - r[0], ey = xn[1] - r[1], ez = xn[2] - r[2];
+  if (OBJ == SIM_OBJ_SQUARED) {
+    lam[0] = fmaf(2.f * sd, ex, lam[0]);
+    lam[1] = fmaf(2.f * sd, ey, lam[1]);
+    lam[2] = fmaf(2.f * sd, ez, lam[2]);
+    return;
+  }
+  // d/dp of -exp(-2 |e|) = 2 exp(-2 |e|) e / |e|  (0 at e = 0)
+  const float d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+  if (d > 0.f) {
+    const float g = 2.f * sd * expf(-2.f * d) / d;
+    lam[0] = fmaf(g, ex, lam[0]);
+    lam[1] = fmaf(g, ey, lam[1]);
+    lam[2] = fmaf(g, ez, lam[2]);
+  }
+  // theta = 2 atan2(s, c): d theta = 2 (c ds - s dc) / (s^2 + c^2),
+  // ds = (qx dqx + qy dqy) / s, dc = (qz dqz + qw dqw) / c  (0 at the kinks)
+  const float s2 = fmaf(xn[3], xn[3], xn[4] * xn[4]), c2 = fmaf(xn[5], xn[5], xn[6] * xn[6]);
+  const float s = sqrtf(s2), c = sqrtf(c2), n2 = s2 + c2;
+  const float gw = 2.f * sd * a.w_theta / n2;
+  if (s > 0.f) {
+    const float g = gw * c / s;
+    lam[3] = fmaf(g, xn[3], lam[3]);
+    lam[4] = fmaf(g, xn[4], lam[4]);
+  }
+  if (c > 0.f) {
+    const float g = -gw * s / c;
+    lam[5] = fmaf(g, xn[5], lam[5]);
+    lam[6] = fmaf(g, xn[6], lam[6]);
+  }
+}
+
 // ------------------------------------------------------------------ kernels
 
+template <int OBJ>
 __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
@@ -709,8 +776,13 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
   float x[17];
   load_row(a.x0, ii, x);
   float loss = 0.f;
+  float ap[4] = {0.f, 0.f, 0.f, 0.f};  // previous action (a_{-1} = hover = 0)
   for (int k = 0; k < a.H; ++k) {
-    if (a.store_ckpt && (k % a.C) == 0 && valid && lane < 16) store_row(a.ckpt + (size_t)(k / a.C) * a.n * 20, i, x);
+    if (a.store_ckpt && (k % a.C) == 0 && valid && lane < 16) {
+      store_row(a.ckpt + (size_t)(k / a.C) * a.n * 20, i, x);
+      if (OBJ == SIM_OBJ_TRACKING_REWARD)
+        a.ckpt_a[(size_t)(k / a.C) * a.n + i] = make_float4(ap[0], ap[1], ap[2], ap[3]);
+    }
     float r[3];
     ref_at(a.p_ref, k, a.n, ii, r);
     if (lane < 16) put_obs(s, row, x, r);
@@ -722,13 +794,14 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
     __syncwarp();
     policy_step(x, act, P, a.dt);
     ref_at(a.p_ref, k + 1, a.n, ii, r);
-    const float ex = x[0] - r[0], ey = x[1] - r[1], ez = x[2] - r[2];
-    loss += fmaf(ex, ex, fmaf(ey, ey, ez * ez)) +
-            a.w_act * fmaf(act[0], act[0], fmaf(act[1], act[1], fmaf(act[2], act[2], act[3] * act[3])));
+    loss += step_loss<OBJ>(x, r, act, ap, a);
+#pragma unroll
+    for (int o = 0; o < 4; ++o) ap[o] = act[o];
   }
   if (valid && lane < 16) a.loss_w[i] = loss;
 }
 
+template <int OBJ>
 __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
@@ -750,14 +823,21 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
   float lam[17];
 #pragma unroll
   for (int j = 0; j < 17; ++j) lam[j] = 0.f;
+  // smoothness adjoint carried from step k + 1 to a_k: -2 sd w_dact (a_{k+1} - a_k)
+  float carry[4] = {0.f, 0.f, 0.f, 0.f};
   const int nseg = (a.H + a.C - 1) / a.C;
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int k0 = sg * a.C, k1 = min(a.H, k0 + a.C);
     float x[17];
     load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
+    float4 ap4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (OBJ == SIM_OBJ_TRACKING_REWARD) ap4 = a.ckpt_a[(size_t)sg * a.n + ii];
     // recompute the segment's states
     for (int k = k0; k < k1; ++k) {
-      if (valid && lane < 16) store_row(a.seg + (size_t)(k - k0) * a.n * 20, i, x);
+      if (valid && lane < 16) {
+        store_row(a.seg + (size_t)(k - k0) * a.n * 20, i, x);
+        if (OBJ == SIM_OBJ_TRACKING_REWARD) a.seg_a[(size_t)(k - k0) * a.n + i] = ap4;
+      }
       float r[3];
       ref_at(a.p_ref, k, a.n, ii, r);
       if (lane < 16) put_obs(s, row, x, r);
@@ -768,6 +848,7 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
       float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
       __syncwarp();
       policy_step(x, act, P, a.dt);
+      ap4 = make_float4(act[0], act[1], act[2], act[3]);
     }
     // reverse sweep
     for (int k = k1 - 1; k >= k0; --k) {
@@ -776,6 +857,14 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
       // checkpoint row (finite data; their seed and dz rows are zero)
       if (valid) load_row(a.seg + (size_t)(k - k0) * a.n * 20, i, x);
       else load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
+      float ap[4] = {0.f, 0.f, 0.f, 0.f};
+      if (OBJ == SIM_OBJ_TRACKING_REWARD) {
+        const float4 t = valid ? a.seg_a[(size_t)(k - k0) * a.n + i] : a.ckpt_a[(size_t)sg * a.n + ii];
+        ap[0] = t.x;
+        ap[1] = t.y;
+        ap[2] = t.z;
+        ap[3] = t.w;
+      }
       float r[3];
       ref_at(a.p_ref, k, a.n, ii, r);
       if (lane < 16) put_obs(s, row, x, r);
@@ -796,14 +885,21 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
         policy_step(xn, act, P, a.dt);
         float rn[3];
         ref_at(a.p_ref, k + 1, a.n, ii, rn);
-        lam[0] += 2.f * seed * (xn[0] - rn[0]);
-        lam[1] += 2.f * seed * (xn[1] - rn[1]);
-        lam[2] += 2.f * seed * (xn[2] - rn[2]);
+        step_loss_state_adjoint<OBJ>(xn, rn, seed, a, lam);
       }
       float ga[4];
       policy_step_adjoint(x, act, lam, ga, P, a.dt);
+      if (OBJ == SIM_OBJ_SQUARED) {
 #pragma unroll
-      for (int o = 0; o < 4; ++o) ga[o] = fmaf(2.f * seed * a.w_act, act[o], ga[o]);
+        for (int o = 0; o < 4; ++o) ga[o] = fmaf(2.f * seed * a.w_act, act[o], ga[o]);
+      } else {
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const float sm = 2.f * seed * a.w_da[o] * (act[o] - ap[o]);
+          ga[o] = fmaf(2.f * seed * a.w_a[o], act[o], ga[o]) + sm + carry[o];
+          carry[o] = -sm;
+        }
+      }
       // dz3 = ga (1 - a^2); rows of padded drones are zero
       if (lane < 16) {
         float dz[16];
@@ -896,16 +992,19 @@ cudaError_t launch_adam(const float* g, float* w, float* m, float* v, uint16_t* 
   return cudaGetLastError();
 }
 
-size_t rollout_workspace_bytes(int n, int H, int C) {
+size_t rollout_workspace_bytes(int n, int H, int C, int objective) {
   const int n_ck = (H + C - 1) / C;
   const int n_cta = (n + ro::DPC - 1) / ro::DPC;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  return al((size_t)n_ck * n * 20 * 4) + al((size_t)C * n * 20 * 4) + al((size_t)n * 4) +
-         al((size_t)n_cta * ro::NPOL_PAD * 4);
+  size_t b = al((size_t)n_ck * n * 20 * 4) + al((size_t)C * n * 20 * 4) + al((size_t)n * 4) +
+             al((size_t)n_cta * ro::NPOL_PAD * 4);
+  if (objective == SIM_OBJ_TRACKING_REWARD) b += al((size_t)n_ck * n * 16) + al((size_t)C * n * 16);
+  return b;
 }
 
-static void carve(void* ws, int n, int H, int C, ro::RolloutArgs& a) {
+static void carve(void* ws, int n, int H, int C, const RolloutObjective& obj, ro::RolloutArgs& a) {
   const int n_ck = (H + C - 1) / C;
+  const int n_cta = (n + ro::DPC - 1) / ro::DPC;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   char* p = (char*)ws;
   a.ckpt = (float*)p;
@@ -915,13 +1014,35 @@ static void carve(void* ws, int n, int H, int C, ro::RolloutArgs& a) {
   a.loss_w = (float*)p;
   p += al((size_t)n * 4);
   a.part = (float*)p;
+  p += al((size_t)n_cta * ro::NPOL_PAD * 4);
+  if (obj.kind == SIM_OBJ_TRACKING_REWARD) {
+    a.ckpt_a = (float4*)p;
+    p += al((size_t)n_ck * n * 16);
+    a.seg_a = (float4*)p;
+  }
+  a.w_theta = obj.w_theta;
+  for (int o = 0; o < 4; ++o) {
+    a.w_a[o] = obj.w_act[o];
+    a.w_da[o] = obj.w_dact[o];
+  }
+}
+
+template <typename K>
+static cudaError_t launch_rollout_kernel(K kernel, int grid, const ro::RolloutArgs& a,
+                                         const DevParams& P, cudaStream_t st) {
+  const int smem = (int)sizeof(ro::Smem);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kernel<<<grid, ro::TPB, smem, st>>>(a, P);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
-                               int C, float dt, float w_act, const DevParams& P, void* ws,
-                               float* loss, bool store_ckpt, cudaStream_t st) {
+                               int C, float dt, float w_act, const RolloutObjective& obj,
+                               const DevParams& P, void* ws, float* loss, bool store_ckpt,
+                               cudaStream_t st) {
   ro::RolloutArgs a{};
-  carve(ws, n, H, C, a);
+  carve(ws, n, H, C, obj, a);
   a.x0 = x0;
   a.w = w;
   a.p_ref = p_ref;
@@ -931,23 +1052,21 @@ cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* 
   a.dt = dt;
   a.w_act = w_act;
   a.store_ckpt = store_ckpt ? 1 : 0;
-  const int smem = (int)sizeof(ro::Smem);
-  cudaError_t e = cudaFuncSetAttribute(ro::rollout_fwd_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
   const int grid = (n + ro::DPC - 1) / ro::DPC;
-  ro::rollout_fwd_kernel<<<grid, ro::TPB, smem, st>>>(a, P);
-  e = cudaGetLastError();
+  cudaError_t e = obj.kind == SIM_OBJ_TRACKING_REWARD
+                      ? launch_rollout_kernel(ro::rollout_fwd_kernel<SIM_OBJ_TRACKING_REWARD>, grid, a, P, st)
+                      : launch_rollout_kernel(ro::rollout_fwd_kernel<SIM_OBJ_SQUARED>, grid, a, P, st);
   if (e != cudaSuccess) return e;
   ro::reduce_loss_kernel<<<1, 256, 0, st>>>(a.loss_w, n, loss);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
-                               int C, float dt, float w_act, const DevParams& P, void* ws,
-                               const float* dL, float* dW, float* dx0, cudaStream_t st) {
+                               int C, float dt, float w_act, const RolloutObjective& obj,
+                               const DevParams& P, void* ws, const float* dL, float* dW, float* dx0,
+                               cudaStream_t st) {
   ro::RolloutArgs a{};
-  carve(ws, n, H, C, a);
+  carve(ws, n, H, C, obj, a);
   a.x0 = x0;
   a.w = w;
   a.p_ref = p_ref;
@@ -959,13 +1078,10 @@ cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* 
   a.w_act = w_act;
   a.dL = dL;
   a.inv_n = 1.f / (float)n;
-  const int smem = (int)sizeof(ro::Smem);
-  cudaError_t e = cudaFuncSetAttribute(ro::rollout_bwd_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
   const int grid = (n + ro::DPC - 1) / ro::DPC;
-  ro::rollout_bwd_kernel<<<grid, ro::TPB, smem, st>>>(a, P);
-  e = cudaGetLastError();
+  cudaError_t e = obj.kind == SIM_OBJ_TRACKING_REWARD
+                      ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_TRACKING_REWARD>, grid, a, P, st)
+                      : launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED>, grid, a, P, st);
   if (e != cudaSuccess) return e;
   ro::reduce_dw_kernel<<<(ro::NPOL + 255) / 256, 256, 0, st>>>(a.part, grid, dW);
   return cudaGetLastError();

@@ -49,6 +49,7 @@ struct sim_s {
   int hold = 1;
   int64_t t = 0;
   int64_t launches = 0;
+  cf::RolloutObjective objective;
   char err[512] = {0};
 };
 
@@ -612,17 +613,39 @@ static int rollout_check(sim_h h, int H, int C, const void* ws, size_t ws_bytes,
     return fail(h, SIM_EINVAL, "policy rollouts need one parameter set, lag rotors and no drag");
   if (H < 1 || C < 1 || C > H) return fail(h, SIM_EINVAL, "need 1 <= C <= H");
   if (!ws || ((uintptr_t)ws & 255)) return fail(h, SIM_EINVAL, "workspace must be 256-byte aligned");
-  if (ws_bytes < cf::rollout_workspace_bytes((int)h->ntot, H, C))
+  if (ws_bytes < cf::rollout_workspace_bytes((int)h->ntot, H, C, h->objective.kind))
     return fail(h, SIM_ENOMEM, "rollout workspace too small");
   for (const void* p : dev_ptrs)
     if (!p || ((uintptr_t)p & 15)) return fail(h, SIM_EINVAL, "device buffers must be 16-byte aligned");
   return SIM_OK;
 }
 
+int sim_rollout_set_objective(sim_h h, const sim_objective* obj) {
+  if (!h) return SIM_EINVAL;
+  cf::RolloutObjective o;
+  if (obj) {
+    if (obj->kind != SIM_OBJ_SQUARED && obj->kind != SIM_OBJ_TRACKING_REWARD)
+      return fail(h, SIM_EINVAL, "unknown objective kind %d", obj->kind);
+    bool ok = isfinite(obj->w_theta) && obj->w_theta >= 0.f;
+    for (int i = 0; i < 4; ++i)
+      ok = ok && isfinite(obj->w_act[i]) && obj->w_act[i] >= 0.f && isfinite(obj->w_dact[i]) &&
+           obj->w_dact[i] >= 0.f;
+    if (!ok) return fail(h, SIM_EINVAL, "objective weights must be finite and non-negative");
+    o.kind = obj->kind;
+    o.w_theta = obj->w_theta;
+    for (int i = 0; i < 4; ++i) {
+      o.w_act[i] = obj->w_act[i];
+      o.w_dact[i] = obj->w_dact[i];
+    }
+  }
+  h->objective = o;
+  return SIM_OK;
+}
+
 int sim_rollout_workspace_bytes(sim_h h, int H, int C, size_t* bytes) {
   if (!h || !bytes) return SIM_EINVAL;
   if (H < 1 || C < 1 || C > H) return fail(h, SIM_EINVAL, "need 1 <= C <= H");
-  *bytes = cf::rollout_workspace_bytes((int)h->ntot, H, C);
+  *bytes = cf::rollout_workspace_bytes((int)h->ntot, H, C, h->objective.kind);
   return SIM_OK;
 }
 
@@ -631,8 +654,8 @@ int sim_rollout_fwd(sim_h h, const float* x0, const uint16_t* w, const float* p_
   if (!h) return SIM_EINVAL;
   int r = rollout_check(h, H, C, ws, ws_bytes, {x0, w, p_ref, loss});
   if (r != SIM_OK) return r;
-  cudaError_t e = cf::launch_rollout_fwd(x0, w, p_ref, (int)h->ntot, H, C, h->dt, w_act, h->p0, ws,
-                                         loss, true, (cudaStream_t)stream);
+  cudaError_t e = cf::launch_rollout_fwd(x0, w, p_ref, (int)h->ntot, H, C, h->dt, w_act, h->objective,
+                                         h->p0, ws, loss, true, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "rollout forward launch");
   h->launches += 2;
   return SIM_OK;
@@ -644,8 +667,8 @@ int sim_rollout_bwd(sim_h h, const float* x0, const uint16_t* w, const float* p_
   if (!h) return SIM_EINVAL;
   int r = rollout_check(h, H, C, ws, ws_bytes, {x0, w, p_ref, dL, dW, dx0});
   if (r != SIM_OK) return r;
-  cudaError_t e = cf::launch_rollout_bwd(x0, w, p_ref, (int)h->ntot, H, C, h->dt, w_act, h->p0, ws,
-                                         dL, dW, dx0, (cudaStream_t)stream);
+  cudaError_t e = cf::launch_rollout_bwd(x0, w, p_ref, (int)h->ntot, H, C, h->dt, w_act, h->objective,
+                                         h->p0, ws, dL, dW, dx0, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "rollout backward launch");
   h->launches += 2;
   return SIM_OK;

@@ -1,6 +1,8 @@
 """Differentiable policy rollout: thin binding of sim_rollout_fwd / _bwd.
 
-``PolicyRollout(sim, H, C, w_act)`` owns the rollout workspace;
+``PolicyRollout(sim, H, C, w_act, reward=None)`` owns the rollout workspace;
+``reward`` selects the paper's tracking reward (weights as in
+``TRACKING_REWARD``) instead of the squared tracking loss;
 ``rollout_loss(x0, w, runner, p_ref)`` is a torch.autograd.Function whose
 forward and backward are the library's CUDA kernels (the upstream gradient
 is read on the device, so backward does not synchronise).  ``w`` holds the
@@ -17,6 +19,10 @@ import torch
 from . import _lib as L
 from .sim import _stream_ptr
 
+
+# the paper's BPTT tracking-reward weights (hyper-parameter table); action
+# order roll, pitch, yaw, thrust
+TRACKING_REWARD = {"w_theta": 0.1, "w_act": (0.12, 0.12, 0.0, 0.02), "w_dact": (1.4, 1.4, 0.0, 0.8)}
 
 POLICY_ORDER = (("W1", (64, 13)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)),
                 ("W3", (4, 64)), ("b3", (4,)))
@@ -40,14 +46,28 @@ def _p(t: torch.Tensor) -> ctypes.c_void_p:
 
 
 class PolicyRollout:
-    def __init__(self, sim, H: int, C: int, w_act: float = 1e-3):
+    def __init__(self, sim, H: int, C: int, w_act: float = 1e-3, reward: dict | None = None):
         self.sim, self.H, self.C, self.w_act = sim, int(H), int(C), float(w_act)
+        self.objective = L.Objective()
+        if reward is not None:
+            self.objective.kind = L.OBJ_TRACKING_REWARD
+            self.objective.w_theta = float(reward["w_theta"])
+            for i in range(4):
+                self.objective.w_act[i] = float(reward["w_act"][i])
+                self.objective.w_dact[i] = float(reward["w_dact"][i])
+        self._apply_objective()
         nb = ctypes.c_size_t()
         sim._check(sim.lib.sim_rollout_workspace_bytes(sim.h, self.H, self.C, ctypes.byref(nb)))
         self.ws = torch.empty(nb.value, dtype=torch.uint8, device=sim.device)
         self.one = torch.ones(1, dtype=torch.float32, device=sim.device)
 
+    def _apply_objective(self):
+        """The objective is a setting of the handle; set it before every call so
+        that runners sharing one handle do not see each other's."""
+        self.sim._check(self.sim.lib.sim_rollout_set_objective(self.sim.h, ctypes.byref(self.objective)))
+
     def _check_inputs(self, x0, w_bf16, p_ref):
+        self._apply_objective()
         n = self.sim.ntot
         if x0.dtype != torch.float32 or tuple(x0.shape) != (n, L.STATE_DIM) or not x0.is_contiguous():
             raise ValueError(f"x0 must be contiguous float32 [{n}, {L.STATE_DIM}]")

@@ -112,3 +112,27 @@ def test_null_handle_is_rejected(lib):
     assert lib.sim_num_drones(None) == -1
     assert lib.sim_last_error(None) == b"NULL handle"
     lib.sim_destroy(None)
+
+
+def test_rollout_objective_validation(lib):
+    r, h = _create(lib, 64, 1)
+    nb0, nb1 = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.sim_rollout_workspace_bytes(h, 40, 10, ctypes.byref(nb0)) == L.SIM_OK
+    obj = L.Objective()
+    obj.kind = 7
+    assert lib.sim_rollout_set_objective(h, ctypes.byref(obj)) == L.SIM_EINVAL
+    obj.kind = L.OBJ_TRACKING_REWARD
+    obj.w_theta = 0.1
+    obj.w_dact[2] = -1.0
+    assert lib.sim_rollout_set_objective(h, ctypes.byref(obj)) == L.SIM_EINVAL
+    obj.w_dact[2] = float("nan")
+    assert lib.sim_rollout_set_objective(h, ctypes.byref(obj)) == L.SIM_EINVAL
+    obj.w_dact[2] = 0.0
+    assert lib.sim_rollout_set_objective(h, ctypes.byref(obj)) == L.SIM_OK
+    # the reward keeps the previous action per checkpoint and segment step
+    assert lib.sim_rollout_workspace_bytes(h, 40, 10, ctypes.byref(nb1)) == L.SIM_OK
+    assert nb1.value >= nb0.value + 64 * 16 * (4 + 10)
+    assert lib.sim_rollout_set_objective(h, None) == L.SIM_OK
+    assert lib.sim_rollout_workspace_bytes(h, 40, 10, ctypes.byref(nb1)) == L.SIM_OK
+    assert nb1.value == nb0.value
+    lib.sim_destroy(h)

@@ -9,7 +9,7 @@ import torch
 import workloads as W
 from oracle import policy as po
 from paper_2606_01478_b300 import EULER, FIRST_PRINCIPLES, Sim
-from paper_2606_01478_b300.rollout import PolicyRollout, rollout_loss
+from paper_2606_01478_b300.rollout import TRACKING_REWARD, PolicyRollout, rollout_loss
 
 pytestmark = pytest.mark.gpu
 
@@ -18,10 +18,14 @@ GROUPS = {"p": slice(0, 3), "q": slice(3, 7), "v": slice(7, 10), "w": slice(10, 
           "W": slice(13, 17)}
 
 
-def _gpu_inputs(rw):
+# tracking-reward weights that exercise every action channel
+REWARD_GENERAL = {"w_theta": 0.23, "w_act": (0.3, 0.05, 0.2, 0.11), "w_dact": (0.7, 1.3, 0.4, 0.9)}
+
+
+def _gpu_inputs(rw, reward=None):
     sim = Sim(rw.M, 1, FIRST_PRINCIPLES, EULER, rw.dt)
     sim.set_params(rw.params)
-    runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act)
+    runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act, reward=reward)
     x0 = torch.tensor(rw.x0, dtype=torch.float32, device="cuda")
     w = torch.tensor(po.pack(rw.weights), dtype=torch.float32, device="cuda")
     p_ref = torch.tensor(rw.p_ref, dtype=torch.float32, device="cuda").contiguous()
@@ -39,11 +43,11 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-30))
 
 
-def _check(rw, loss, dW, dx0, drones=None):
+def _check(rw, loss, dW, dx0, drones=None, reward=None):
     x0, p_ref = _as_oracle_inputs(rw)
     sel = np.arange(rw.M) if drones is None else np.asarray(drones)
     L_ref, per, dW_ref, dx_ref = po.rollout_grad(x0[sel], rw.weights, p_ref[:, sel], rw.params,
-                                                 rw.dt, rw.H, rw.w_act)
+                                                 rw.dt, rw.H, rw.w_act, reward)
     dx_ref = dx_ref * len(sel) / rw.M  # the GPU loss is the mean over all M drones
     errs = {}
     if drones is None:
@@ -138,3 +142,50 @@ def test_zero_policy_hover_loss():
     loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
     expect = rw.H * float((off.astype(np.float64) ** 2).sum())
     assert abs(loss.item() - expect) <= 1e-5 * expect
+
+
+# ---------------------------------------------------------------- tracking reward
+
+
+@pytest.mark.parametrize("reward", [TRACKING_REWARD, REWARD_GENERAL], ids=["paper", "general"])
+def test_reward_gradient_small_ragged(reward):
+    """The paper's tracking reward: 200 drones (ragged last CTA), H = 30, C = 7
+    (the smoothness adjoint crosses segment boundaries)."""
+    rw = W.config3(seed=35, M=200, H=30, C=7)
+    sim, runner, x0, w, p_ref = _gpu_inputs(rw, reward)
+    loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
+    assert torch.isfinite(dW).all() and torch.isfinite(dx0).all()
+    _check(rw, loss.item(), dW.cpu().numpy(), dx0.cpu().numpy().astype(np.float64), reward=reward)
+
+
+@pytest.mark.parametrize("C", [40, 1])
+def test_reward_gradient_training_shape(C):
+    """The paper's BPTT setting (16 environments, 40 steps) and a long horizon
+    (256 drones, H = 250, C = 25)."""
+    rw = W.config3(seed=36, M=16, H=40, C=C)
+    sim, runner, x0, w, p_ref = _gpu_inputs(rw, TRACKING_REWARD)
+    loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
+    _check(rw, loss.item(), dW.cpu().numpy(), dx0.cpu().numpy().astype(np.float64), reward=TRACKING_REWARD)
+    rw = W.config3(seed=37, M=256, H=250, C=25)
+    sim, runner, x0, w, p_ref = _gpu_inputs(rw, TRACKING_REWARD)
+    loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
+    _check(rw, loss.item(), dW.cpu().numpy(), dx0.cpu().numpy().astype(np.float64), reward=TRACKING_REWARD)
+
+
+def test_objectives_share_a_handle():
+    """Two runners with different objectives on one handle: each call applies its
+    own objective (the results equal those of separate handles)."""
+    rw = W.config3(seed=38, M=96, H=24, C=6)
+    sim, sq, x0, w, p_ref = _gpu_inputs(rw)
+    rew = PolicyRollout(sim, rw.H, rw.C, rw.w_act, reward=TRACKING_REWARD)
+    wb = w.to(torch.bfloat16)
+    a1 = [t.clone() for t in sq.grad(x0, wb, p_ref)]
+    b1 = [t.clone() for t in rew.grad(x0, wb, p_ref)]
+    a2 = sq.grad(x0, wb, p_ref)
+    for u, v in zip(a1, a2):
+        assert torch.equal(u, v)
+    _, ref_runner, _, _, _ = _gpu_inputs(rw, TRACKING_REWARD)
+    b2 = ref_runner.grad(x0, wb, p_ref)
+    for u, v in zip(b1, b2):
+        assert torch.equal(u, v)
+    assert not torch.equal(a1[1], b1[1])

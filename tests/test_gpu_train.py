@@ -49,10 +49,10 @@ def test_adam_kernel_matches_oracle():
                              1e-8, None) == L.SIM_EINVAL
 
 
-def _trainer(rw, lr):
+def _trainer(rw, lr, reward=None):
     sim = Sim(rw.M, 1, FIRST_PRINCIPLES, EULER, rw.dt)
     sim.set_params(rw.params)
-    runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act)
+    runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act, reward=reward)
     w0 = torch.tensor(po.pack(rw.weights), dtype=torch.float32, device="cuda")
     x0 = torch.tensor(rw.x0, dtype=torch.float32, device="cuda")
     p_ref = torch.tensor(rw.p_ref, dtype=torch.float32, device="cuda").contiguous()
@@ -75,6 +75,23 @@ def test_training_iterations_match_oracle_loop():
     # the weights' displacement from the start agrees to 1e-3 of its size
     assert np.linalg.norm((w_gpu - w0) - (w_ref - w0)) <= 1e-3 * np.linalg.norm(w_ref - w0)
     assert tr_gpu.step.item() == iters
+
+
+def test_reward_training_iterations_match_oracle_loop():
+    """The paper's setting: 16 environments, 40 steps per rollout, the tracking
+    reward; five iterations against the FP64 oracle loop."""
+    rw = W.config3(seed=62, M=16, H=40, C=40)
+    lr, iters = 3e-3, 5
+    tr_gpu, x0, p_ref = _trainer(rw, lr, po.TRACKING_REWARD)
+    losses = [tr_gpu.iteration(x0, p_ref).item() for _ in range(iters)]
+    ref_losses, w_ref = tr.train(rw.x0.astype(np.float32).astype(np.float64),
+                                 rw.p_ref.astype(np.float32).astype(np.float64), rw.params,
+                                 po.pack(rw.weights), iters, lr, rw.dt, rw.H, rw.w_act,
+                                 reward=po.TRACKING_REWARD)
+    np.testing.assert_allclose(losses, ref_losses, rtol=1e-3)
+    w_gpu = tr_gpu.w.cpu().numpy().astype(np.float64)
+    w0 = po.pack(rw.weights)
+    assert np.linalg.norm((w_gpu - w0) - (w_ref - w0)) <= 1e-3 * np.linalg.norm(w_ref - w0)
 
 
 def test_graph_replay_equals_eager_iterations():
