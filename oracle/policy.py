@@ -9,7 +9,10 @@ module computes, for a batch of M independent drones:
 
     obs_k = [p_k - r_k, q_k, v_k, w_k]                      (13)
     a_k   = tanh(W3 tanh(W2 tanh(W1 obs_k + b1) + b2) + b3) (4, attitude action)
-    x_{k+1} = step(x_k, a_k)   first-principles model, attitude interface, Euler
+    x_{k+1} = step^R(x_k, a_k) first-principles model, attitude interface, Euler;
+                               the action is held for R >= 1 physics steps (R = 10
+                               runs a 50 Hz policy on 500 Hz physics, the paper's
+                               recommended attitude-interface rate)
     L = (1/M) sum_w sum_{k=0}^{H-1} ( |p_{k+1} - r_{k+1}|^2 + w_act |a_k|^2 )
 
 with r_k the reference position table (a figure-8 sampled per drone; an input).
@@ -35,7 +38,8 @@ against the paper.  The tracking reward follows the paper's equation and table
 tests/test_oracle_policy.py by central finite differences of both losses
 (float64), the zero-policy hover case (loss and closed-form offset loss, for
 both objectives), the action and smoothness penalties of a constant policy in
-closed form, the tilt angle against scipy's rotation matrices, and structural
+closed form, the tilt angle against scipy's rotation matrices, a constant
+policy held R steps against R times as many single steps, and structural
 properties of the MLP.
 """
 from __future__ import annotations
@@ -91,10 +95,11 @@ def tracking_reward(x_next, r_next, a, a_prev, reward: dict) -> torch.Tensor:
 
 
 def rollout_loss(x0, W: dict, p_ref, params: dict, dt: float, H: int, w_act: float,
-                 reward: dict | None = None):
+                 reward: dict | None = None, repeat: int = 1):
     """Returns (L, per-drone loss [M], final state [M, 20]).  reward=None: the
     squared tracking loss with action weight w_act; otherwise the paper's
-    tracking reward with the weights in `reward` (w_act is then unused)."""
+    tracking reward with the weights in `reward` (w_act is then unused).  Each
+    of the H policy actions is held for `repeat` physics steps of dt."""
     x = torch.as_tensor(x0, dtype=F64) if not torch.is_tensor(x0) else x0
     r = torch.as_tensor(p_ref, dtype=F64)
     M = x.shape[0]
@@ -103,7 +108,8 @@ def rollout_loss(x0, W: dict, p_ref, params: dict, dt: float, H: int, w_act: flo
     a_prev = torch.zeros(M, 4, dtype=F64)
     for k in range(H):
         a = mlp(observation(x, r[k]), W)
-        x = ph.step(x, a, P, dt, ph.EULER, ph.CTRL_ATTITUDE, ph.FIRST_PRINCIPLES)
+        for _ in range(repeat):
+            x = ph.step(x, a, P, dt, ph.EULER, ph.CTRL_ATTITUDE, ph.FIRST_PRINCIPLES)
         if reward is None:
             per = per + ((x[:, 0:3] - r[k + 1]) ** 2).sum(-1) + w_act * (a * a).sum(-1)
         else:
@@ -113,13 +119,13 @@ def rollout_loss(x0, W: dict, p_ref, params: dict, dt: float, H: int, w_act: flo
 
 
 def rollout_grad(x0, weights: dict, p_ref, params: dict, dt: float, H: int, w_act: float,
-                 reward: dict | None = None):
+                 reward: dict | None = None, repeat: int = 1):
     """Loss and its gradient w.r.t. the weights (dict of float64 arrays) and the
     initial state [M, 20] (the three integrator slots get zero gradient: the
     attitude interface does not use them)."""
     W = weights_tensors(weights, requires_grad=True)
     x0t = torch.tensor(x0, dtype=F64, requires_grad=True)
-    L, per, _ = rollout_loss(x0t, W, p_ref, params, dt, H, w_act, reward)
+    L, per, _ = rollout_loss(x0t, W, p_ref, params, dt, H, w_act, reward, repeat)
     grads = torch.autograd.grad(L, [x0t] + [W[k] for k in NAMES])
     dx0 = grads[0].detach().numpy()
     dW = {k: g.detach().numpy() for k, g in zip(NAMES, grads[1:])}

@@ -42,7 +42,8 @@ def round_bf16(x):
 
 
 def train(x0, p_ref, params: dict, w0_flat, iters: int, lr: float, dt: float, H: int, w_act: float,
-          b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8, reward: dict | None = None):
+          b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8, reward: dict | None = None,
+          repeat: int = 1):
     """`iters` iterations from master weights w0_flat (5316, float64).  Returns
     (losses [iters], final master weights)."""
     w = np.asarray(w0_flat, dtype=np.float64).copy()
@@ -51,7 +52,7 @@ def train(x0, p_ref, params: dict, w0_flat, iters: int, lr: float, dt: float, H:
     losses = []
     for t in range(1, iters + 1):
         wb = po.unpack(round_bf16(w))
-        L, _, dW, _ = po.rollout_grad(x0, wb, p_ref, params, dt, H, w_act, reward)
+        L, _, dW, _ = po.rollout_grad(x0, wb, p_ref, params, dt, H, w_act, reward, repeat)
         losses.append(L)
         w, m, v = adam(w, po.pack(dW), m, v, t, lr, b1, b2, eps)
     return np.array(losses), w

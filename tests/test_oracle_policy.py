@@ -200,3 +200,51 @@ def test_reward_gradient_matches_central_differences(reward):
         xm[w, j] -= hx * scale
         fd = (_rloss(rw, xp, rw.weights, reward) - _rloss(rw, xm, rw.weights, reward)) / (2 * hx * scale)
         assert abs(fd - dx0[w, j]) <= 1e-6 * max(1.0, abs(dx0[w, j])) + 1e-10, (w, j, fd, dx0[w, j])
+
+
+def test_held_constant_policy_equals_single_steps():
+    """A constant policy (W3 = 0) held R = 4 steps for H policy steps drives the
+    same physics as H R single steps: identical final state, and the squared
+    position terms of the held rollout are those of every R-th single step."""
+    rw = _small(M=3, H=48)
+    wts = {k: np.array(v, dtype=np.float64) for k, v in rw.weights.items()}
+    wts["W3"] = np.zeros_like(wts["W3"])
+    wts["b3"] = np.array([0.2, -0.1, 0.3, 0.15])
+    Wt = po.weights_tensors(wts)
+    R, Hp = 4, 12
+    ref_single = rw.p_ref  # [49, M, 3]
+    ref_held = rw.p_ref[::R]  # [13, M, 3]
+    x0 = torch.tensor(rw.x0)
+    _, per1, xf1 = po.rollout_loss(x0, Wt, ref_single, rw.params, rw.dt, Hp * R, 0.0)
+    _, perR, xfR = po.rollout_loss(x0, Wt, ref_held, rw.params, rw.dt, Hp, 0.0, repeat=R)
+    assert torch.equal(xf1, xfR)
+    # position terms at every R-th step, recomputed from a single-step trajectory
+    x = x0.clone()
+    P = ph.param_batch([rw.params], [0] * 3)
+    a = torch.tanh(torch.tensor(wts["b3"]))[None, :].expand(3, 4)
+    expect = torch.zeros(3, dtype=F64)
+    for k in range(Hp * R):
+        x = ph.step(x, a, P, rw.dt, ph.EULER, ph.CTRL_ATTITUDE, ph.FIRST_PRINCIPLES)
+        if (k + 1) % R == 0:
+            expect += ((x[:, 0:3] - torch.tensor(ref_single[k + 1])) ** 2).sum(-1)
+    np.testing.assert_allclose(perR.numpy(), expect.numpy(), rtol=1e-13)
+
+
+def test_held_policy_gradient_matches_central_differences():
+    rw = _tilted(_small(M=3, H=12))
+    R = 3
+    _, _, dW, _ = po.rollout_grad(rw.x0, rw.weights, rw.p_ref, rw.params, rw.dt, rw.H, 0.0,
+                                  po.TRACKING_REWARD, R)
+    flat = po.pack(rw.weights)
+    g = po.pack(dW)
+
+    def f(v):
+        Wt = po.weights_tensors(po.unpack(v))
+        return float(po.rollout_loss(torch.tensor(rw.x0), Wt, rw.p_ref, rw.params, rw.dt, rw.H, 0.0,
+                                     po.TRACKING_REWARD, R)[0])
+    h = 1e-5
+    for i in [7, 832 + 30, 896 + 3000, 5056 + 100, 5314]:
+        e = np.zeros_like(flat)
+        e[i] = h
+        fd = (f(flat + e) - f(flat - e)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-9, (i, fd, g[i])

@@ -264,9 +264,10 @@ class RolloutWorkload:
     dt: float
     params: dict
     x0: np.ndarray          # [M, 20]
-    p_ref: np.ndarray       # [H + 1, M, 3] reference position at t0 + k dt
+    p_ref: np.ndarray       # [H + 1, M, 3] reference position at t0 + k R dt
     weights: dict
     w_act: float
+    repeat: int = 1         # R: physics steps per policy step
 
 
 def figure8(t: np.ndarray, radius: float = 0.5, period: float = 4.0, height: float = 1.0):
@@ -281,14 +282,17 @@ def figure8(t: np.ndarray, radius: float = 0.5, period: float = 4.0, height: flo
     return pos, vel
 
 
-def config3(seed: int = 1003, M: int = 8192, H: int = 250, C: int = 25) -> RolloutWorkload:
+def config3(seed: int = 1003, M: int = 8192, H: int = 250, C: int = 25,
+            repeat: int = 1) -> RolloutWorkload:
     """Differentiable rollout: M worlds x 1 drone, first-principles, attitude
     interface driven by the policy MLP 13 -> 64 -> 64 -> 4 (tanh, bf16
     weights), Euler at 500 Hz over H steps, checkpoint every C steps.  Target:
     figure-8 of radius 0.5 m and period 4 s at z = 1 m, sampled per world at
     t0 + k dt with t0 ~ U[0, 4) s.  Initial state: on the curve at t0 with
     U(+-0.05 m) position noise, the curve's velocity, identity attitude, zero
-    body rates, rotors at hover speed."""
+    body rates, rotors at hover speed.  repeat = R > 1: the policy acts every R
+    physics steps (R = 10: a 50 Hz attitude policy), H counts policy steps and
+    the reference is sampled at t0 + k R dt."""
     rng = np.random.default_rng(seed)
     P = crazyflie_params()
     dt = 1.0 / 500
@@ -298,10 +302,10 @@ def config3(seed: int = 1003, M: int = 8192, H: int = 250, C: int = 25) -> Rollo
     p0, v0 = figure8(t0)
     x0 = fp_state(p0 + noise, np.zeros((M, 3)), v0, np.zeros((M, 3)),
                   np.full((M, 4), hover_rpm(P)))
-    t = t0[None, :] + dt * np.arange(H + 1)[:, None]
+    t = t0[None, :] + repeat * dt * np.arange(H + 1)[:, None]
     p_ref, _ = figure8(t)
-    return RolloutWorkload(f"c3_{M}x1_bptt_euler_H{H}_C{C}", M, H, C, dt, P, x0, p_ref,
-                           weights, 1e-3)
+    name = f"c3_{M}x1_bptt_euler_H{H}_C{C}" + (f"_R{repeat}" if repeat > 1 else "")
+    return RolloutWorkload(name, M, H, C, dt, P, x0, p_ref, weights, 1e-3, repeat)
 
 
 # ---------------------------------------------------------------------------
