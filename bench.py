@@ -589,17 +589,18 @@ def measure_mppi(dev, reps: int = 3) -> dict:
 def measure_bptt_training(dev, reps: int = 3) -> dict:
     """The paper's BPTT tracking setup (16 environments, 40 steps per rollout,
     learning rate 4.6e-2, 100 000 timesteps = 156 iterations, its tracking
-    reward and weights): each iteration is the rollout gradient (forward +
-    adjoint kernels) and the Adam kernel; one iteration is captured in a CUDA
-    graph and replayed 156 times."""
+    reward and weights) with the policy at the recommended 50 Hz of the
+    attitude interface (each action held for 10 physics steps at 500 Hz): each
+    iteration is the rollout gradient (forward + adjoint kernels) and the Adam
+    kernel; one iteration is captured in a CUDA graph and replayed 156 times."""
     from paper_2606_01478_b300 import EULER, FIRST_PRINCIPLES, Sim
     from paper_2606_01478_b300.rollout import TRACKING_REWARD, PolicyRollout, pack_policy
     from paper_2606_01478_b300.train import PolicyTrainer
-    M, H, C, iters, lr = 16, 40, 10, 156, 4.6e-2
-    rw = W.config3(M=M, H=H, C=C)
+    M, H, C, R, iters, lr = 16, 40, 10, 10, 156, 4.6e-2
+    rw = W.config3(M=M, H=H, C=C, repeat=R)
     sim = Sim(M, 1, FIRST_PRINCIPLES, EULER, rw.dt, device=dev)
     sim.set_params(rw.params)
-    runner = PolicyRollout(sim, H, C, rw.w_act, reward=TRACKING_REWARD)
+    runner = PolicyRollout(sim, H, C, rw.w_act, reward=TRACKING_REWARD, action_repeat=R)
     w0 = torch.tensor(pack_policy(rw.weights), dtype=torch.float32, device=dev)
     x0 = torch.tensor(rw.x0, dtype=torch.float32, device=dev)
     p_ref = torch.tensor(rw.p_ref, dtype=torch.float32, device=dev).contiguous()
@@ -622,9 +623,9 @@ def measure_bptt_training(dev, reps: int = 3) -> dict:
             times.append(e0.elapsed_time(e1))
         final_loss = trainer.loss.item()
     ms = statistics.median(times)
-    return {"workload": f"bptt_train_{M}envs_H{H}_{iters}iters_lr{lr}_tracking_reward", "ms_total": ms,
+    return {"workload": f"bptt_train_{M}envs_H{H}_R{R}_{iters}iters_lr{lr}_tracking_reward", "ms_total": ms,
             "ms_per_iteration": ms / iters, "iterations": iters,
-            "timesteps": M * H * iters,
+            "timesteps": M * H * iters, "physics_steps": M * H * R * iters,
             "mean_reward_per_step_first_iteration": -initial_loss / H,
             "mean_reward_per_step_last_iteration": -final_loss / H,
             "paper_context": "1.56 s to train the 10 s Lissajous tracker (100k timesteps) on a CPU"}

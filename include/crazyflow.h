@@ -277,8 +277,10 @@ int sim_render_depth(sim_h h, const sim_camera* cam, const float* spheres, int n
  * independently:
  *   obs_k = [p_k - r_k, q_k, v_k, omega_k]                         (13)
  *   a_k   = tanh(W3 tanh(W2 tanh(W1 obs_k + b1) + b2) + b3)        (4, attitude action)
- *   x_{k+1} = one Euler step of the first-principles model under the attitude
- *             interface with command a_k, k = 0 .. H-1
+ *   x_{k+1} = R Euler steps of the first-principles model under the attitude
+ *             interface with command a_k held, k = 0 .. H-1 (R = 1 unless set
+ *             by sim_rollout_set_action_repeat; R = 10 runs a 50 Hz policy on
+ *             500 Hz physics, the paper's recommended attitude-interface rate)
  *   L = (1/Ntot) sum_drones sum_k |p_{k+1} - r_{k+1}|^2 + w_act |a_k|^2
  * (the squared objective, default) or, after sim_rollout_set_objective with
  * SIM_OBJ_TRACKING_REWARD, the paper's tracking reward (Backpropagation Through
@@ -298,11 +300,12 @@ int sim_render_depth(sim_h h, const sim_camera* cam, const float* spheres, int n
  *   x0    [Ntot][SIM_STATE_DIM] float   initial states (slots 17..19 ignored)
  *   w     [SIM_POLICY_NPARAMS] bf16 bit patterns, packed row-major
  *         W1[64][13] b1[64] W2[64][64] b2[64] W3[4][64] b3[4]
- *   p_ref [H+1][Ntot][3] float          reference positions r_k
+ *   p_ref [H+1][Ntot][3] float          reference positions r_k (at policy steps)
  *   ws    rollout workspace of sim_rollout_workspace_bytes(h, H, C) bytes:
  *         checkpoints every C steps, segment states, per-drone losses, dW partials
  *         (and the previous actions under the tracking reward: the size depends
- *         on the objective set on the handle)
+ *         on the objective and the action repeat set on the handle; segments
+ *         hold C R sub-step states)
  *   loss  [1] float; dL [1] float (upstream gradient, read on the device);
  *   dW    [SIM_POLICY_NPARAMS] float = dL * dL/dw (in the packed order of w)
  *   dx0   [Ntot][SIM_STATE_DIM] float = dL * dL/dx0 (slots 17..19 = 0)
@@ -326,6 +329,12 @@ typedef struct sim_objective {
  * NULL restores SIM_OBJ_SQUARED).  SIM_EINVAL for an unknown kind or a weight
  * that is negative or not finite. */
 int sim_rollout_set_objective(sim_h h, const sim_objective* obj);
+/* Physics steps per policy action (R) of every later rollout call on the
+ * handle (host-side setting; default 1).  H and C count policy steps, p_ref
+ * holds the reference at policy steps, and the loss is evaluated after every
+ * R-th physics step.  SIM_EINVAL unless 1 <= R <= SIM_MAX_ACTION_REPEAT. */
+#define SIM_MAX_ACTION_REPEAT 100
+int sim_rollout_set_action_repeat(sim_h h, int R);
 int sim_rollout_workspace_bytes(sim_h h, int H, int C, size_t* bytes);
 int sim_rollout_fwd(sim_h h, const float* x0, const uint16_t* w, const float* p_ref, int H, int C,
                     float w_act, void* ws, size_t ws_bytes, float* loss, void* stream);

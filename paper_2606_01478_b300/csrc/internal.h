@@ -17,7 +17,7 @@ cudaError_t launch_step_batched(const StepArgs& a, const int4* tiles, int n_tile
                                 int ctrl, bool general_motor, int tpb, cudaStream_t st);
 
 // Differentiable policy rollout (rollout.cu).  Workspace: checkpoints
-// [ceil(H/C)][n][20], segment states [C][n][20], per-drone loss [n], per-CTA dW
+// [ceil(H/C)][n][20], segment sub-step states [C R][n][20], per-drone loss [n], per-CTA dW
 // partials; all fp32; with the tracking reward also the previous action at each
 // checkpoint [ceil(H/C)][n] and segment step [C][n] (float4).
 constexpr int POLICY_NPARAMS = 5316;
@@ -26,13 +26,13 @@ struct RolloutObjective {
   int kind = SIM_OBJ_SQUARED;
   float w_theta = 0.f, w_act[4] = {0.f, 0.f, 0.f, 0.f}, w_dact[4] = {0.f, 0.f, 0.f, 0.f};
 };
-size_t rollout_workspace_bytes(int n, int H, int C, int objective);
+size_t rollout_workspace_bytes(int n, int H, int C, int objective, int R);
 cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
-                               int C, float dt, float w_act, const RolloutObjective& obj,
+                               int C, int R, float dt, float w_act, const RolloutObjective& obj,
                                const DevParams& P, void* ws,
                                float* loss, bool store_ckpt, cudaStream_t st);
 cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
-                               int C, float dt, float w_act, const RolloutObjective& obj,
+                               int C, int R, float dt, float w_act, const RolloutObjective& obj,
                                const DevParams& P, void* ws, const float* dL, float* dW, float* dx0,
                                cudaStream_t st);
 

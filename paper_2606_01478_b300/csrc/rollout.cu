@@ -4,8 +4,9 @@
 // dynamics and the onboard controller stack (Materials and Methods,
 // Backpropagation Through Time).  Here, per drone:
 //   obs_k = [p_k - r_k, q_k, v_k, w_k];  a_k = MLP(obs_k)  (13 -> 64 -> 64 -> 4, tanh)
-//   x_{k+1} = Euler step of the first-principles model under the attitude
-//             interface with action a_k (controller, mixer, motor lag, Eqs. 1-6)
+//   x_{k+1} = R Euler steps of the first-principles model under the attitude
+//             interface with action a_k held (controller, mixer, motor lag,
+//             Eqs. 1-6); R = 1, or 10 for a 50 Hz policy on 500 Hz physics
 //   L = (1/M) sum_w sum_k |p_{k+1} - r_{k+1}|^2 + w_act |a_k|^2          (squared objective)
 // or the paper's tracking reward (BPTT section, reward equation), as a loss:
 //   L = (1/M) sum_w sum_k -exp(-2 |p_{k+1} - r_{k+1}|) + w_theta theta_{k+1}
@@ -13,8 +14,8 @@
 //   theta = 2 atan2(|(qx, qy)|, |(qz, qw)|) the tilt from upright.
 // Forward kernel: rollout + loss, checkpoints of x (and, for the reward, of the
 // previous action) every C steps.
-// Backward kernel: per segment, recompute the C states from the checkpoint,
-// then sweep them in reverse with the hand-written adjoint of the step and of
+// Backward kernel: per segment, recompute the C R sub-step states from the
+// checkpoint, then sweep them in reverse with the hand-written adjoint of the step and of
 // the MLP; accumulate dL/dW per CTA; dL/dx0 per drone.
 //
 // Layout: one CTA = 4 warps = 64 drones; warp v owns drones 16v..16v+15 of the
@@ -58,14 +59,14 @@ struct RolloutArgs {
   const uint16_t* w;      // [NPOL] bf16 bits, packed W1 b1 W2 b2 W3 b3
   const float* p_ref;     // [H + 1][n][3]
   float* ckpt;            // [n_ckpt][n][20]
-  float* seg;             // [C][n][20]
+  float* seg;             // [C R][n][20]
   float* loss_w;          // [n] per-drone loss
   float* part;            // [n_cta][NPOL_PAD] dW partials
   float* dx0;             // [n][20]
   const float* dL;        // device scalar: upstream gradient of the loss
   float4* ckpt_a;         // [n_ckpt][n] previous action at each checkpoint (reward objective)
   float4* seg_a;          // [C][n] previous action of each segment step (reward objective)
-  int n, H, C;
+  int n, H, C, R;
   float dt, w_act, inv_n;
   float w_theta, w_a[4], w_da[4];  // tracking-reward weights
   int store_ckpt;
@@ -792,7 +793,7 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
     __syncwarp();
     float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
     __syncwarp();
-    policy_step(x, act, P, a.dt);
+    for (int j = 0; j < a.R; ++j) policy_step(x, act, P, a.dt);
     ref_at(a.p_ref, k + 1, a.n, ii, r);
     loss += step_loss<OBJ>(x, r, act, ap, a);
 #pragma unroll
@@ -835,7 +836,7 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
     // recompute the segment's states
     for (int k = k0; k < k1; ++k) {
       if (valid && lane < 16) {
-        store_row(a.seg + (size_t)(k - k0) * a.n * 20, i, x);
+        store_row(a.seg + (size_t)(k - k0) * a.R * a.n * 20, i, x);
         if (OBJ == SIM_OBJ_TRACKING_REWARD) a.seg_a[(size_t)(k - k0) * a.n + i] = ap4;
       }
       float r[3];
@@ -847,7 +848,11 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
       __syncwarp();
       float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
       __syncwarp();
-      policy_step(x, act, P, a.dt);
+      for (int j = 0; j < a.R; ++j) {
+        if (j > 0 && valid && lane < 16)
+          store_row(a.seg + ((size_t)(k - k0) * a.R + j) * a.n * 20, i, x);
+        policy_step(x, act, P, a.dt);
+      }
       ap4 = make_float4(act[0], act[1], act[2], act[3]);
     }
     // reverse sweep
@@ -855,7 +860,7 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
       __syncwarp();
       // padded rows never read rows written by other warps: they replay the
       // checkpoint row (finite data; their seed and dz rows are zero)
-      if (valid) load_row(a.seg + (size_t)(k - k0) * a.n * 20, i, x);
+      if (valid) load_row(a.seg + (size_t)(k - k0) * a.R * a.n * 20, i, x);
       else load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
       float ap[4] = {0.f, 0.f, 0.f, 0.f};
       if (OBJ == SIM_OBJ_TRACKING_REWARD) {
@@ -877,18 +882,35 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
       }
       __syncwarp();
       const float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
-      // loss term at step k + 1 (position after this step)
+      // loss term at policy step k + 1 (state after the last sub-step)
       {
         float xn[17];
+        if (a.R > 1 && valid) {
+          load_row(a.seg + ((size_t)(k - k0) * a.R + a.R - 1) * a.n * 20, i, xn);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 17; ++j) xn[j] = x[j];
+          for (int j = 0; j < 17; ++j) xn[j] = x[j];
+        }
         policy_step(xn, act, P, a.dt);
         float rn[3];
         ref_at(a.p_ref, k + 1, a.n, ii, rn);
         step_loss_state_adjoint<OBJ>(xn, rn, seed, a, lam);
       }
-      float ga[4];
-      policy_step_adjoint(x, act, lam, ga, P, a.dt);
+      // back through the R sub-steps; the held action collects every sub-step's adjoint
+      float ga[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int j = a.R - 1; j >= 0; --j) {
+        float xs[17];
+        if (j > 0 && valid) {
+          load_row(a.seg + ((size_t)(k - k0) * a.R + j) * a.n * 20, i, xs);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 17; ++q) xs[q] = x[q];
+        }
+        float gj[4];
+        policy_step_adjoint(xs, act, lam, gj, P, a.dt);
+#pragma unroll
+        for (int o = 0; o < 4; ++o) ga[o] += gj[o];
+      }
       if (OBJ == SIM_OBJ_SQUARED) {
 #pragma unroll
         for (int o = 0; o < 4; ++o) ga[o] = fmaf(2.f * seed * a.w_act, act[o], ga[o]);
@@ -992,17 +1014,18 @@ cudaError_t launch_adam(const float* g, float* w, float* m, float* v, uint16_t* 
   return cudaGetLastError();
 }
 
-size_t rollout_workspace_bytes(int n, int H, int C, int objective) {
+size_t rollout_workspace_bytes(int n, int H, int C, int objective, int R) {
   const int n_ck = (H + C - 1) / C;
   const int n_cta = (n + ro::DPC - 1) / ro::DPC;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  size_t b = al((size_t)n_ck * n * 20 * 4) + al((size_t)C * n * 20 * 4) + al((size_t)n * 4) +
+  size_t b = al((size_t)n_ck * n * 20 * 4) + al((size_t)C * R * n * 20 * 4) + al((size_t)n * 4) +
              al((size_t)n_cta * ro::NPOL_PAD * 4);
   if (objective == SIM_OBJ_TRACKING_REWARD) b += al((size_t)n_ck * n * 16) + al((size_t)C * n * 16);
   return b;
 }
 
-static void carve(void* ws, int n, int H, int C, const RolloutObjective& obj, ro::RolloutArgs& a) {
+static void carve(void* ws, int n, int H, int C, int R, const RolloutObjective& obj,
+                  ro::RolloutArgs& a) {
   const int n_ck = (H + C - 1) / C;
   const int n_cta = (n + ro::DPC - 1) / ro::DPC;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -1010,7 +1033,7 @@ static void carve(void* ws, int n, int H, int C, const RolloutObjective& obj, ro
   a.ckpt = (float*)p;
   p += al((size_t)n_ck * n * 20 * 4);
   a.seg = (float*)p;
-  p += al((size_t)C * n * 20 * 4);
+  p += al((size_t)C * R * n * 20 * 4);
   a.loss_w = (float*)p;
   p += al((size_t)n * 4);
   a.part = (float*)p;
@@ -1020,6 +1043,7 @@ static void carve(void* ws, int n, int H, int C, const RolloutObjective& obj, ro
     p += al((size_t)n_ck * n * 16);
     a.seg_a = (float4*)p;
   }
+  a.R = R;
   a.w_theta = obj.w_theta;
   for (int o = 0; o < 4; ++o) {
     a.w_a[o] = obj.w_act[o];
@@ -1038,11 +1062,11 @@ static cudaError_t launch_rollout_kernel(K kernel, int grid, const ro::RolloutAr
 }
 
 cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
-                               int C, float dt, float w_act, const RolloutObjective& obj,
+                               int C, int R, float dt, float w_act, const RolloutObjective& obj,
                                const DevParams& P, void* ws, float* loss, bool store_ckpt,
                                cudaStream_t st) {
   ro::RolloutArgs a{};
-  carve(ws, n, H, C, obj, a);
+  carve(ws, n, H, C, R, obj, a);
   a.x0 = x0;
   a.w = w;
   a.p_ref = p_ref;
@@ -1062,11 +1086,11 @@ cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* 
 }
 
 cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
-                               int C, float dt, float w_act, const RolloutObjective& obj,
+                               int C, int R, float dt, float w_act, const RolloutObjective& obj,
                                const DevParams& P, void* ws, const float* dL, float* dW, float* dx0,
                                cudaStream_t st) {
   ro::RolloutArgs a{};
-  carve(ws, n, H, C, obj, a);
+  carve(ws, n, H, C, R, obj, a);
   a.x0 = x0;
   a.w = w;
   a.p_ref = p_ref;

@@ -50,6 +50,7 @@ struct sim_s {
   int64_t t = 0;
   int64_t launches = 0;
   cf::RolloutObjective objective;
+  int rollout_repeat = 1;
   char err[512] = {0};
 };
 
@@ -613,7 +614,7 @@ static int rollout_check(sim_h h, int H, int C, const void* ws, size_t ws_bytes,
     return fail(h, SIM_EINVAL, "policy rollouts need one parameter set, lag rotors and no drag");
   if (H < 1 || C < 1 || C > H) return fail(h, SIM_EINVAL, "need 1 <= C <= H");
   if (!ws || ((uintptr_t)ws & 255)) return fail(h, SIM_EINVAL, "workspace must be 256-byte aligned");
-  if (ws_bytes < cf::rollout_workspace_bytes((int)h->ntot, H, C, h->objective.kind))
+  if (ws_bytes < cf::rollout_workspace_bytes((int)h->ntot, H, C, h->objective.kind, h->rollout_repeat))
     return fail(h, SIM_ENOMEM, "rollout workspace too small");
   for (const void* p : dev_ptrs)
     if (!p || ((uintptr_t)p & 15)) return fail(h, SIM_EINVAL, "device buffers must be 16-byte aligned");
@@ -645,7 +646,15 @@ int sim_rollout_set_objective(sim_h h, const sim_objective* obj) {
 int sim_rollout_workspace_bytes(sim_h h, int H, int C, size_t* bytes) {
   if (!h || !bytes) return SIM_EINVAL;
   if (H < 1 || C < 1 || C > H) return fail(h, SIM_EINVAL, "need 1 <= C <= H");
-  *bytes = cf::rollout_workspace_bytes((int)h->ntot, H, C, h->objective.kind);
+  *bytes = cf::rollout_workspace_bytes((int)h->ntot, H, C, h->objective.kind, h->rollout_repeat);
+  return SIM_OK;
+}
+
+int sim_rollout_set_action_repeat(sim_h h, int R) {
+  if (!h) return SIM_EINVAL;
+  if (R < 1 || R > SIM_MAX_ACTION_REPEAT)
+    return fail(h, SIM_EINVAL, "action repeat must lie in [1, %d]", SIM_MAX_ACTION_REPEAT);
+  h->rollout_repeat = R;
   return SIM_OK;
 }
 
@@ -654,7 +663,8 @@ int sim_rollout_fwd(sim_h h, const float* x0, const uint16_t* w, const float* p_
   if (!h) return SIM_EINVAL;
   int r = rollout_check(h, H, C, ws, ws_bytes, {x0, w, p_ref, loss});
   if (r != SIM_OK) return r;
-  cudaError_t e = cf::launch_rollout_fwd(x0, w, p_ref, (int)h->ntot, H, C, h->dt, w_act, h->objective,
+  cudaError_t e = cf::launch_rollout_fwd(x0, w, p_ref, (int)h->ntot, H, C, h->rollout_repeat, h->dt,
+                                         w_act, h->objective,
                                          h->p0, ws, loss, true, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "rollout forward launch");
   h->launches += 2;
@@ -667,7 +677,8 @@ int sim_rollout_bwd(sim_h h, const float* x0, const uint16_t* w, const float* p_
   if (!h) return SIM_EINVAL;
   int r = rollout_check(h, H, C, ws, ws_bytes, {x0, w, p_ref, dL, dW, dx0});
   if (r != SIM_OK) return r;
-  cudaError_t e = cf::launch_rollout_bwd(x0, w, p_ref, (int)h->ntot, H, C, h->dt, w_act, h->objective,
+  cudaError_t e = cf::launch_rollout_bwd(x0, w, p_ref, (int)h->ntot, H, C, h->rollout_repeat, h->dt,
+                                         w_act, h->objective,
                                          h->p0, ws, dL, dW, dx0, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "rollout backward launch");
   h->launches += 2;

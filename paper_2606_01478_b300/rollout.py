@@ -1,6 +1,8 @@
 """Differentiable policy rollout: thin binding of sim_rollout_fwd / _bwd.
 
-``PolicyRollout(sim, H, C, w_act, reward=None)`` owns the rollout workspace;
+``PolicyRollout(sim, H, C, w_act, reward=None, action_repeat=1)`` owns the
+rollout workspace; ``action_repeat`` = R holds each policy action for R physics
+steps (H and C count policy steps);
 ``reward`` selects the paper's tracking reward (weights as in
 ``TRACKING_REWARD``) instead of the squared tracking loss;
 ``rollout_loss(x0, w, runner, p_ref)`` is a torch.autograd.Function whose
@@ -46,8 +48,10 @@ def _p(t: torch.Tensor) -> ctypes.c_void_p:
 
 
 class PolicyRollout:
-    def __init__(self, sim, H: int, C: int, w_act: float = 1e-3, reward: dict | None = None):
+    def __init__(self, sim, H: int, C: int, w_act: float = 1e-3, reward: dict | None = None,
+                 action_repeat: int = 1):
         self.sim, self.H, self.C, self.w_act = sim, int(H), int(C), float(w_act)
+        self.repeat = int(action_repeat)
         self.objective = L.Objective()
         if reward is not None:
             self.objective.kind = L.OBJ_TRACKING_REWARD
@@ -62,9 +66,10 @@ class PolicyRollout:
         self.one = torch.ones(1, dtype=torch.float32, device=sim.device)
 
     def _apply_objective(self):
-        """The objective is a setting of the handle; set it before every call so
-        that runners sharing one handle do not see each other's."""
+        """Objective and action repeat are settings of the handle; set them before
+        every call so that runners sharing one handle do not see each other's."""
         self.sim._check(self.sim.lib.sim_rollout_set_objective(self.sim.h, ctypes.byref(self.objective)))
+        self.sim._check(self.sim.lib.sim_rollout_set_action_repeat(self.sim.h, self.repeat))
 
     def _check_inputs(self, x0, w_bf16, p_ref):
         self._apply_objective()

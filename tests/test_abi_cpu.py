@@ -136,3 +136,16 @@ def test_rollout_objective_validation(lib):
     assert lib.sim_rollout_workspace_bytes(h, 40, 10, ctypes.byref(nb1)) == L.SIM_OK
     assert nb1.value == nb0.value
     lib.sim_destroy(h)
+
+
+def test_rollout_action_repeat_validation(lib):
+    r, h = _create(lib, 32, 1)
+    nb1, nb10 = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.sim_rollout_workspace_bytes(h, 40, 10, ctypes.byref(nb1)) == L.SIM_OK
+    for bad in (0, -2, 101):
+        assert lib.sim_rollout_set_action_repeat(h, bad) == L.SIM_EINVAL
+    assert lib.sim_rollout_set_action_repeat(h, 10) == L.SIM_OK
+    assert lib.sim_rollout_workspace_bytes(h, 40, 10, ctypes.byref(nb10)) == L.SIM_OK
+    # segments keep C R sub-step states of 80 bytes
+    assert nb10.value >= nb1.value + 32 * 80 * 10 * 9
+    lib.sim_destroy(h)

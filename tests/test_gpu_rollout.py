@@ -25,7 +25,7 @@ REWARD_GENERAL = {"w_theta": 0.23, "w_act": (0.3, 0.05, 0.2, 0.11), "w_dact": (0
 def _gpu_inputs(rw, reward=None):
     sim = Sim(rw.M, 1, FIRST_PRINCIPLES, EULER, rw.dt)
     sim.set_params(rw.params)
-    runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act, reward=reward)
+    runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act, reward=reward, action_repeat=rw.repeat)
     x0 = torch.tensor(rw.x0, dtype=torch.float32, device="cuda")
     w = torch.tensor(po.pack(rw.weights), dtype=torch.float32, device="cuda")
     p_ref = torch.tensor(rw.p_ref, dtype=torch.float32, device="cuda").contiguous()
@@ -47,7 +47,7 @@ def _check(rw, loss, dW, dx0, drones=None, reward=None):
     x0, p_ref = _as_oracle_inputs(rw)
     sel = np.arange(rw.M) if drones is None else np.asarray(drones)
     L_ref, per, dW_ref, dx_ref = po.rollout_grad(x0[sel], rw.weights, p_ref[:, sel], rw.params,
-                                                 rw.dt, rw.H, rw.w_act, reward)
+                                                 rw.dt, rw.H, rw.w_act, reward, rw.repeat)
     dx_ref = dx_ref * len(sel) / rw.M  # the GPU loss is the mean over all M drones
     errs = {}
     if drones is None:
@@ -189,3 +189,16 @@ def test_objectives_share_a_handle():
     for u, v in zip(b1, b2):
         assert torch.equal(u, v)
     assert not torch.equal(a1[1], b1[1])
+
+
+@pytest.mark.parametrize("reward", [None, TRACKING_REWARD], ids=["squared", "reward"])
+def test_held_action_gradient(reward):
+    """Policy actions held for R = 10 physics steps (50 Hz policy, 500 Hz
+    physics): 100 drones (ragged), H = 16 policy steps, C = 5 (ragged last
+    segment); and the paper's training shape, 16 environments x 40 steps."""
+    for rw in (W.config3(seed=39, M=100, H=16, C=5, repeat=10),
+               W.config3(seed=40, M=16, H=40, C=10, repeat=10)):
+        sim, runner, x0, w, p_ref = _gpu_inputs(rw, reward)
+        loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
+        assert torch.isfinite(dW).all()
+        _check(rw, loss.item(), dW.cpu().numpy(), dx0.cpu().numpy().astype(np.float64), reward=reward)

@@ -52,7 +52,7 @@ def test_adam_kernel_matches_oracle():
 def _trainer(rw, lr, reward=None):
     sim = Sim(rw.M, 1, FIRST_PRINCIPLES, EULER, rw.dt)
     sim.set_params(rw.params)
-    runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act, reward=reward)
+    runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act, reward=reward, action_repeat=rw.repeat)
     w0 = torch.tensor(po.pack(rw.weights), dtype=torch.float32, device="cuda")
     x0 = torch.tensor(rw.x0, dtype=torch.float32, device="cuda")
     p_ref = torch.tensor(rw.p_ref, dtype=torch.float32, device="cuda").contiguous()
@@ -78,16 +78,17 @@ def test_training_iterations_match_oracle_loop():
 
 
 def test_reward_training_iterations_match_oracle_loop():
-    """The paper's setting: 16 environments, 40 steps per rollout, the tracking
-    reward; five iterations against the FP64 oracle loop."""
-    rw = W.config3(seed=62, M=16, H=40, C=40)
+    """The paper's setting: 16 environments, 40 policy steps per rollout at
+    50 Hz (10 physics steps each), the tracking reward; five iterations against
+    the FP64 oracle loop."""
+    rw = W.config3(seed=62, M=16, H=40, C=40, repeat=10)
     lr, iters = 3e-3, 5
     tr_gpu, x0, p_ref = _trainer(rw, lr, po.TRACKING_REWARD)
     losses = [tr_gpu.iteration(x0, p_ref).item() for _ in range(iters)]
     ref_losses, w_ref = tr.train(rw.x0.astype(np.float32).astype(np.float64),
                                  rw.p_ref.astype(np.float32).astype(np.float64), rw.params,
                                  po.pack(rw.weights), iters, lr, rw.dt, rw.H, rw.w_act,
-                                 reward=po.TRACKING_REWARD)
+                                 reward=po.TRACKING_REWARD, repeat=rw.repeat)
     np.testing.assert_allclose(losses, ref_losses, rtol=1e-3)
     w_gpu = tr_gpu.w.cpu().numpy().astype(np.float64)
     w0 = po.pack(rw.weights)
