@@ -44,6 +44,9 @@ struct DevParams {
   int flags;
 };
 
+// PF_GENERAL_MOTOR selects the general kernel variants (MOTOR_GENERAL): polynomial
+// rotor curves, asymmetric or quadratic rotor dynamics, rotor inertia, or drag
+// (PF_DRAG implies it).  The lag-rotor variants (MOTOR_LAG) have none of these.
 enum : int { PF_DRAG = 1, PF_GENERAL_MOTOR = 2 };
 
 // Arguments of the step kernels (by value).

@@ -96,7 +96,7 @@ __device__ __forceinline__ void deriv_fp(const float* x, const float Wc[4], cons
   const float r12 = Rc ? Rc[5] : 2.f * fmaf(qy, qz, -qw * qx);
   const float r22 = Rc ? Rc[8] : (qw * qw + qz * qz) - (qx * qx + qy * qy);
   float ax = Tm * r02, ay = Tm * r12, az = fmaf(Tm, r22, -P.g);
-  if (drag) {
+  if (MOTOR != MOTOR_LAG && drag) {
     float R[9];
     if (Rc) {
 #pragma unroll
@@ -140,7 +140,9 @@ __device__ __forceinline__ void deriv_fp(const float* x, const float Wc[4], cons
   d[12] = fmaf(tz, P.inv_Jz, P.cJz * wx * wy);
 }
 
-// Abstracted derivative (Eqs. 7-10) of x[0..12] for u = (Psi_cmd, f_cmd).
+// Abstracted derivative (Eqs. 7-10) of x[0..12] for u = (Psi_cmd, f_cmd).  The
+// drag term exists only in the general variant (MOTOR_GENERAL).
+template <int MOTOR>
 __device__ __forceinline__ void deriv_abs(const float* x, const float u[4], const DevParams& P,
                                           bool drag, float* d) {
   float sr, cr, sp, cp, sy, cy;
@@ -153,7 +155,7 @@ __device__ __forceinline__ void deriv_abs(const float* x, const float u[4], cons
   const float r22 = cp * cr;
   const float fm = P.cf_inv_m * x[12];
   float ax = fm * r02, ay = fm * r12, az = fmaf(fm, r22, -P.g);
-  if (drag) {
+  if (MOTOR != MOTOR_LAG && drag) {
     float R[9];
     euler_rot(sr, cr, sp, cp, sy, cy, R);
     const float vx = x[6], vy = x[7], vz = x[8];

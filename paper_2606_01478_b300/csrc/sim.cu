@@ -198,7 +198,10 @@ int derive_params(const float* p, DevParams* d, char* why, size_t why_n) {
   d->Jpc = (float)(p[SIM_P_J_P] * 2.0 * M_PI / 60.0);
   d->fmax = (float)(kf * wmax * wmax + kf1 * wmax + kf0);
   int flags = 0;
-  if (p[SIM_P_CA_X] != 0.f || p[SIM_P_CA_Y] != 0.f || p[SIM_P_CA_Z] != 0.f) flags |= cf::PF_DRAG;
+  // drag also selects the general kernel variants: the lag-rotor variants carry
+  // no drag term (and no branch on it in the hot loop)
+  if (p[SIM_P_CA_X] != 0.f || p[SIM_P_CA_Y] != 0.f || p[SIM_P_CA_Z] != 0.f)
+    flags |= cf::PF_DRAG | cf::PF_GENERAL_MOTOR;
   if (p[SIM_P_CV_UP] != p[SIM_P_CV_DOWN] || p[SIM_P_CD_UP] != 0.f || p[SIM_P_CD_DOWN] != 0.f ||
       p[SIM_P_J_P] != 0.f || kf0 != 0.0 || kf1 != 0.0 || p[SIM_P_KM1] != 0.f)
     flags |= cf::PF_GENERAL_MOTOR;

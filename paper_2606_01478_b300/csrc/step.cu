@@ -80,9 +80,9 @@ __global__ void __launch_bounds__(256) step_batched_kernel(StepArgs a, const int
       if (d.w == SIM_FIRST_PRINCIPLES) {
         run_drone<SIM_FIRST_PRINCIPLES, INTEG, CTRL, MOTOR>(a, d.x + lane, P);
       } else if (d.w == SIM_ABSTRACTED) {
-        run_drone<SIM_ABSTRACTED, INTEG, SIM_CTRL_ATTITUDE, MOTOR_LAG>(a, d.x + lane, P);
+        run_drone<SIM_ABSTRACTED, INTEG, SIM_CTRL_ATTITUDE, MOTOR>(a, d.x + lane, P);
       } else {
-        run_drone<SIM_ABSTRACTED_NOTHRUST, INTEG, SIM_CTRL_ATTITUDE, MOTOR_LAG>(a, d.x + lane, P);
+        run_drone<SIM_ABSTRACTED_NOTHRUST, INTEG, SIM_CTRL_ATTITUDE, MOTOR>(a, d.x + lane, P);
       }
     }
   }
@@ -153,9 +153,8 @@ template <int MODEL, int INTEG>
 static cudaError_t launch_c(const StepArgs& a, const DevParams& P, int ctrl, bool gm, bool perset,
                             int tpb, cudaStream_t st) {
   if constexpr (MODEL != SIM_FIRST_PRINCIPLES) {
-    // the abstracted models have no rotors: motor kind is irrelevant
-    return perset ? launch_t<MODEL, INTEG, SIM_CTRL_ATTITUDE, MOTOR_LAG, true>(a, P, tpb, st)
-                  : launch_t<MODEL, INTEG, SIM_CTRL_ATTITUDE, MOTOR_LAG, false>(a, P, tpb, st);
+    // the abstracted models have no rotors: the general variant only adds drag
+    return launch_m<MODEL, INTEG, SIM_CTRL_ATTITUDE>(a, P, gm, perset, tpb, st);
   } else {
     switch (ctrl) {
       case SIM_CTRL_ROTOR_SPEED:

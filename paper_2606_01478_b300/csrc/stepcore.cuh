@@ -68,7 +68,7 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
     if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
       deriv_fp<MOTOR>(x, Wc, P, drag, d, Rx);
     } else if constexpr (MODEL == SIM_ABSTRACTED) {
-      deriv_abs(x, h.u, P, drag, d);
+      deriv_abs<MOTOR>(x, h.u, P, drag, d);
     } else {
       deriv_abs_nothrust(x, h.u, P, d);
     }

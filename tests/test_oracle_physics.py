@@ -422,7 +422,7 @@ def test_first_principles_drag_is_body_frame():
 
 def test_rk4_fourth_order_convergence():
     """Smooth case (rotor-speed interface, constant commands, equal motor
-    coefficients): the error at t = 0.5 s against a dt/64 reference falls by
+    coefficients): the error at t = 0.1 s against a dt/64 reference falls by
     about 16 per halving of dt."""
     n = 4
     P = _P(n)
@@ -434,7 +434,7 @@ def test_rk4_fourth_order_convergence():
     x[:, 10:13] = torch.tensor(rng.uniform(-3, 3, (n, 3)))
     x[:, 13:17] = torch.tensor(rng.uniform(12000, 17000, (n, 4)))
     u = torch.tensor(rng.uniform(12000, 17000, (n, 4)))
-    T = 0.5
+    T = 0.1
 
     def run(dt):
         xs = x.clone()
