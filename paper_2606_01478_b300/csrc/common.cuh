@@ -41,6 +41,13 @@ struct DevParams {
   // thrust to [kf0, fmax] and inverts W = (sqrt(kf1^2 + 4 kf (f - kf0)) - kf1) / (2 kf);
   // rotor angular momentum about z: -Jpc sum_i s_i W_i (Jpc = J_p 2 pi / 60)
   float kf0, kf1, km1, kf1sq, four_kf, inv_2kf, Jpc;
+  // lag-rotor step form (one_step with MOTOR_LAG): rotor commands enter as
+  // rates u = cv W_cmd, so W' = u - cv W; constants folded so that
+  //   accel = (kf/m) sum W^2 along R e_z,  w' = (kfa/J) (W^2 combination) + ...,
+  //   u_i = sqrt(clip(cA T + (+-X) + (+-Y) + (+-Z), 0, u2max)) with
+  //   X = cRx e_Rx + cwx w_x etc. (attitude PD times mixer times cv^2 / kf) or
+  //   X = cXt tau_x (torque interface)
+  float kfm, kfm2, kfaJx, kfaJy, kmJz, ncv, cA, cRx, cRy, cRz, cwx, cwy, cwz, cXt, cZt, u2max;
   int flags;
 };
 

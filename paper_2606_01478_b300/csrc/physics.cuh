@@ -140,6 +140,48 @@ __device__ __forceinline__ void deriv_fp(const float* x, const float Wc[4], cons
   d[12] = fmaf(tz, P.inv_Jz, P.cJz * wx * wy);
 }
 
+// First-principles derivative in the lag-rotor step form (MOTOR_LAG, no drag):
+// the same Eqs. 1-6 as deriv_fp, with the rotor commands given as rates
+// u_i = cv W_cmd,i (so W_i' = u_i - cv W_i) and the quaternion rate returned
+// doubled, d[3..6] = q (x) [w, 0] = 2 q' (the integrator folds the 1/2 into its
+// coefficients).  Constants kf/m, kfa/J, km/J are folded (DevParams).
+__device__ __forceinline__ void deriv_fp_rate(const float* x, const float u[4], const DevParams& P,
+                                              float* d, const float* Rc = nullptr) {
+  const float qx = x[3], qy = x[4], qz = x[5], qw = x[6];
+  const float wx = x[10], wy = x[11], wz = x[12];
+  const float s0 = x[13] * x[13], s1 = x[14] * x[14], s2 = x[15] * x[15], s3 = x[16] * x[16];
+  const float a01 = s0 + s1, a23 = s2 + s3, S = a01 + a23;
+  const float Tm = P.kfm * S;  // collective thrust / m
+  float ax, ay, az;
+  if (Rc) {
+    ax = Tm * Rc[2];
+    ay = Tm * Rc[5];
+    az = fmaf(Tm, Rc[8], -P.g);
+  } else {
+    // third column of R(q): 2 (xz + wy), 2 (yz - wx), w^2 - x^2 - y^2 + z^2
+    const float Tm2 = P.kfm2 * S;
+    ax = Tm2 * fmaf(qx, qz, qw * qy);
+    ay = Tm2 * fmaf(qy, qz, -qw * qx);
+    az = fmaf(Tm, (qw * qw + qz * qz) - (qx * qx + qy * qy), -P.g);
+  }
+  d[0] = x[7];
+  d[1] = x[8];
+  d[2] = x[9];
+  d[3] = fmaf(qw, wx, qy * wz) - qz * wy;
+  d[4] = fmaf(qw, wy, qz * wx) - qx * wz;
+  d[5] = fmaf(qw, wz, qx * wy) - qy * wx;
+  d[6] = -(fmaf(qx, wx, qy * wy) + qz * wz);
+  d[7] = ax;
+  d[8] = ay;
+  d[9] = az;
+  // w' = J^-1 tau - J^-1 (w x J w), rotor torques as in deriv_fp
+  d[10] = fmaf(P.kfaJx, a23 - a01, P.cJx * wy * wz);
+  d[11] = fmaf(P.kfaJy, (s1 + s2) - (s0 + s3), P.cJy * wz * wx);
+  d[12] = fmaf(P.kmJz, (s1 + s3) - (s0 + s2), P.cJz * wx * wy);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) d[13 + r] = fmaf(P.ncv, x[13 + r], u[r]);
+}
+
 // Abstracted derivative (Eqs. 7-10) of x[0..12] for u = (Psi_cmd, f_cmd).  The
 // drag term exists only in the general variant (MOTOR_GENERAL).
 template <int MOTOR>
@@ -229,16 +271,23 @@ __device__ __forceinline__ void abstracted_command(float4 a, const DevParams& P,
   u[3] = fmaf(P.ts_mg, clampf(a.w, -1.f, 1.f), P.mg);
 }
 
+// 2 e_R = vee(Rd^T R - R^T Rd); only the off-diagonal entries of Rd^T R are formed.
+__device__ __forceinline__ void attitude_error2(const float R[9], const float Rd[9], float& ex,
+                                                float& ey, float& ez) {
+#define CF_M(i, j) fmaf(Rd[i], R[j], fmaf(Rd[3 + i], R[3 + j], Rd[6 + i] * R[6 + j]))
+  ex = CF_M(2, 1) - CF_M(1, 2);
+  ey = CF_M(0, 2) - CF_M(2, 0);
+  ez = CF_M(1, 0) - CF_M(0, 1);
+#undef CF_M
+}
+
 // Geometric attitude PD, tau = -K_R J e_R - K_w J w with
-// e_R = 1/2 vee(Rd^T R - R^T Rd); only the off-diagonal entries of Rd^T R are formed.
+// e_R = 1/2 vee(Rd^T R - R^T Rd).
 __device__ __forceinline__ void attitude_torque(const float R[9], const float Rd[9], float wx,
                                                 float wy, float wz, const DevParams& P,
                                                 float& tx, float& ty, float& tz) {
-#define CF_M(i, j) fmaf(Rd[i], R[j], fmaf(Rd[3 + i], R[3 + j], Rd[6 + i] * R[6 + j]))
-  const float ex = CF_M(2, 1) - CF_M(1, 2);
-  const float ey = CF_M(0, 2) - CF_M(2, 0);
-  const float ez = CF_M(1, 0) - CF_M(0, 1);
-#undef CF_M
+  float ex, ey, ez;
+  attitude_error2(R, Rd, ex, ey, ez);
   tx = -fmaf(P.KRJh_x, ex, P.KwJ_x * wx);
   ty = -fmaf(P.KRJh_y, ey, P.KwJ_y * wy);
   tz = -fmaf(P.KRJh_z, ez, P.KwJ_z * wz);
@@ -266,6 +315,33 @@ __device__ __forceinline__ void mixer(float T, float tx, float ty, float tz, con
       Wc[r] = (sqrt_approx(disc) - P.kf1) * P.inv_2kf;
     }
   }
+}
+
+// Lag-rotor mixer in the step form: rotor command rates u_i = cv W_cmd,i.  X, Y,
+// Z are the mixer's torque terms tau_x mix_a, tau_y mix_a, tau_z mix_k scaled by
+// cv^2 / kf (as is cA = cv^2 / (4 kf)), so u_i^2 = cv^2 f_i / kf with the same
+// X-configuration signs and thrust clip [0, kf W_max^2] as mixer.
+__device__ __forceinline__ void mixer_rate(float T, float X, float Y, float Z, const DevParams& P,
+                                           float u[4]) {
+  const float A = P.cA * T;
+  float f[4];
+  f[0] = (A - X) - (Y + Z);
+  f[1] = (A - X) + (Y + Z);
+  f[2] = (A + X) + (Y - Z);
+  f[3] = (A + X) - (Y - Z);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) u[r] = sqrt_approx(clampf(f[r], 0.f, P.u2max));
+}
+
+// Attitude PD followed by the step-form mixer (lag rotors): the PD gains, mixer
+// factors and cv^2 / kf are folded into cR*, cw* (DevParams).
+__device__ __forceinline__ void attitude_mixer_rate(const float R[9], const float Rd[9], float T,
+                                                    float wx, float wy, float wz,
+                                                    const DevParams& P, float u[4]) {
+  float ex, ey, ez;
+  attitude_error2(R, Rd, ex, ey, ez);
+  mixer_rate(T, -fmaf(P.cRx, ex, P.cwx * wx), -fmaf(P.cRy, ey, P.cwy * wy),
+             -fmaf(P.cRz, ez, P.cwz * wz), P, u);
 }
 
 // Position PID (geometric): setpoint sp = (x, y, z, yaw) with (sin, cos) of

@@ -197,6 +197,27 @@ int derive_params(const float* p, DevParams* d, char* why, size_t why_n) {
   d->inv_2kf = (float)(1.0 / (2.0 * kf));
   d->Jpc = (float)(p[SIM_P_J_P] * 2.0 * M_PI / 60.0);
   d->fmax = (float)(kf * wmax * wmax + kf1 * wmax + kf0);
+  {
+    // lag-rotor step form (see DevParams)
+    const double cv = p[SIM_P_CV_UP], cv2kf = cv * cv / kf;
+    const double mix_a = 1.0 / (4.0 * a), mix_k = kf / (4.0 * km);
+    d->kfm = (float)(kf / m);
+    d->kfm2 = (float)(2.0 * kf / m);
+    d->kfaJx = (float)(kf * a / Jx);
+    d->kfaJy = (float)(kf * a / Jy);
+    d->kmJz = (float)(km / Jz);
+    d->ncv = (float)(-cv);
+    d->cA = (float)(0.25 * cv2kf);
+    d->cRx = (float)(0.5 * p[SIM_P_KR_X] * Jx * mix_a * cv2kf);
+    d->cRy = (float)(0.5 * p[SIM_P_KR_Y] * Jy * mix_a * cv2kf);
+    d->cRz = (float)(0.5 * p[SIM_P_KR_Z] * Jz * mix_k * cv2kf);
+    d->cwx = (float)(p[SIM_P_KW_X] * Jx * mix_a * cv2kf);
+    d->cwy = (float)(p[SIM_P_KW_Y] * Jy * mix_a * cv2kf);
+    d->cwz = (float)(p[SIM_P_KW_Z] * Jz * mix_k * cv2kf);
+    d->cXt = (float)(mix_a * cv2kf);
+    d->cZt = (float)(mix_k * cv2kf);
+    d->u2max = (float)(cv * cv * wmax * wmax);
+  }
   int flags = 0;
   // drag also selects the general kernel variants: the lag-rotor variants carry
   // no drag term (and no branch on it in the hot loop)

@@ -37,35 +37,58 @@ __device__ __forceinline__ void decode_command(float4 c, const DevParams& P, Ctr
   }
 }
 
+// Lag-rotor step form (first-principles model with MOTOR_LAG): rotor commands
+// are carried as rates u = cv W_cmd, the derivative returns 2 q' (deriv_fp_rate)
+// and the integrator takes half coefficients for q.  Under RK4 the rotor
+// speeds, whose ODE W' = u - cv W is linear with u held, take the RK4 update in
+// closed form: W + k1 (1 - P4(-h)) / cv, P4 the degree-4 Taylor polynomial of
+// exp, h = cv dt -- equal to the four-stage combination in exact arithmetic.
+template <int MODEL, int MOTOR>
+constexpr bool lag_step_form() {
+  return MODEL == SIM_FIRST_PRINCIPLES && MOTOR == MOTOR_LAG;
+}
+
 template <int MODEL, int INTEG, int CTRL, int MOTOR>
 __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevParams& P, bool drag,
                                          float dt) {
   constexpr int D = (MODEL == SIM_FIRST_PRINCIPLES) ? 17 : 13;
-  float Wc[4];
+  constexpr bool LSF = lag_step_form<MODEL, MOTOR>();
+  float Wc[4];  // rotor-speed commands (rates cv W_cmd in the lag step form)
   float ep[3] = {0.f, 0.f, 0.f};
   float R[9];  // R(q) of the state at the start of the step (controller and first stage)
   if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
     quat_rot(s[3], s[4], s[5], s[6], R);
     if constexpr (CTRL == SIM_CTRL_ROTOR_SPEED) {
 #pragma unroll
-      for (int r = 0; r < 4; ++r) Wc[r] = h.Wc[r];
+      for (int r = 0; r < 4; ++r) Wc[r] = LSF ? -P.ncv * h.Wc[r] : h.Wc[r];
     } else if constexpr (CTRL == SIM_CTRL_TORQUE) {
-      mixer<MOTOR>(h.Td, h.sp.y, h.sp.z, h.sp.w, P, Wc);
+      if constexpr (LSF) {
+        mixer_rate(h.Td, h.sp.y * P.cXt, h.sp.z * P.cXt, h.sp.w * P.cZt, P, Wc);
+      } else {
+        mixer<MOTOR>(h.Td, h.sp.y, h.sp.z, h.sp.w, P, Wc);
+      }
     } else {
-      float tx, ty, tz;
+      float Rd[9], Td;
       if constexpr (CTRL == SIM_CTRL_POSITION) {
-        float Rd[9], Td;
         position_command(s, R, h.sp, h.syaw, h.cyaw, P, Rd, Td, ep);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 9; ++j) Rd[j] = h.Rd[j];
+        Td = h.Td;
+      }
+      if constexpr (LSF) {
+        attitude_mixer_rate(R, Rd, Td, s[10], s[11], s[12], P, Wc);
+      } else {
+        float tx, ty, tz;
         attitude_torque(R, Rd, s[10], s[11], s[12], P, tx, ty, tz);
         mixer<MOTOR>(Td, tx, ty, tz, P, Wc);
-      } else {
-        attitude_torque(R, h.Rd, s[10], s[11], s[12], P, tx, ty, tz);
-        mixer<MOTOR>(h.Td, tx, ty, tz, P, Wc);
       }
     }
   }
   auto deriv = [&](const float* x, float* d, const float* Rx) {
-    if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
+    if constexpr (LSF) {
+      deriv_fp_rate(x, Wc, P, d, Rx);
+    } else if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
       deriv_fp<MOTOR>(x, Wc, P, drag, d, Rx);
     } else if constexpr (MODEL == SIM_ABSTRACTED) {
       deriv_abs<MOTOR>(x, h.u, P, drag, d);
@@ -74,35 +97,51 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
     }
   };
   const float* R0 = (MODEL == SIM_FIRST_PRINCIPLES) ? R : nullptr;
+  // integrator coefficient c for element j (halved for q in the lag step form)
+  auto co = [&](int j, float c) { return (LSF && j >= 3 && j <= 6) ? 0.5f * c : c; };
   if constexpr (INTEG == SIM_EULER) {
     float d[D];
     deriv(s, d, R0);
 #pragma unroll
-    for (int j = 0; j < D; ++j) s[j] = fmaf(dt, d[j], s[j]);
+    for (int j = 0; j < D; ++j) s[j] = fmaf(co(j, dt), d[j], s[j]);
   } else {
-    float k[D], acc[D], xs[D];
+    float k[D], acc[D], xs[D], k1W[4];
     const float h2 = 0.5f * dt, h6 = dt * (1.f / 6.f);
     deriv(s, k, R0);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       acc[j] = k[j];
-      xs[j] = fmaf(h2, k[j], s[j]);
+      xs[j] = fmaf(co(j, h2), k[j], s[j]);
+    }
+    if constexpr (LSF) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) k1W[r] = k[13 + r];
     }
     deriv(xs, k, nullptr);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       acc[j] = fmaf(2.f, k[j], acc[j]);
-      xs[j] = fmaf(h2, k[j], s[j]);
+      xs[j] = fmaf(co(j, h2), k[j], s[j]);
     }
     deriv(xs, k, nullptr);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       acc[j] = fmaf(2.f, k[j], acc[j]);
-      xs[j] = fmaf(dt, k[j], s[j]);
+      xs[j] = fmaf(co(j, dt), k[j], s[j]);
     }
     deriv(xs, k, nullptr);
+    if constexpr (LSF) {
 #pragma unroll
-    for (int j = 0; j < D; ++j) s[j] = fmaf(h6, acc[j] + k[j], s[j]);
+      for (int j = 0; j < 13; ++j) s[j] = fmaf(co(j, h6), acc[j] + k[j], s[j]);
+      // (1 - P4(-h)) / cv = dt (1 - h/2 + h^2/6 - h^3/24), h = cv dt
+      const float hc = -P.ncv * dt;
+      const float c4 = dt * fmaf(hc, fmaf(hc, fmaf(hc, -1.f / 24.f, 1.f / 6.f), -0.5f), 1.f);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) s[13 + r] = fmaf(c4, k1W[r], s[13 + r]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j) s[j] = fmaf(h6, acc[j] + k[j], s[j]);
+    }
   }
   if constexpr (MODEL == SIM_ABSTRACTED_NOTHRUST) s[12] = h.u[3];  // f_sum follows f_cmd at once
   if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
