@@ -232,6 +232,18 @@ __device__ __forceinline__ void put_obs(Smem& s, int row, const float* x, const 
   }
 }
 
+// tanh from its definition, tanh x = sign(x) (1 - 2 / (exp(2 |x|) + 1)), on the
+// hardware base-2 exponential and reciprocal approximations: absolute error about
+// 2e-7 (the activations then enter the tensor cores as hi + lo bf16 pairs, ~2^-16
+// relative); saturates to +-1 for large |x|.
+__device__ __forceinline__ float tanh_fast(float x) {
+  float e, r;
+  const float y = fabsf(x) * 2.88539008177792681f;  // 2 / ln 2
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e + 1.f));
+  return copysignf(fmaf(-2.f, r, 1.f), x);
+}
+
 // MLP forward for the warp's 16 drones (rows r0..r0+15).  Returns h1, h2
 // (fp32 accumulator fragments, after tanh) and writes the actions to s.act.
 __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[8][4]) {
@@ -261,7 +273,7 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
 #pragma unroll
   for (int n = 0; n < 8; ++n)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) h1[n][e] = tanhf(h1[n][e]);
+    for (int e = 0; e < 4; ++e) h1[n][e] = tanh_fast(h1[n][e]);
   // layer 2: z2[d][j] = sum_i h1[d][i] W2[j][i] + b2[j]
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
@@ -288,7 +300,7 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
 #pragma unroll
   for (int n = 0; n < 8; ++n)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) h2[n][e] = tanhf(h2[n][e]);
+    for (int e = 0; e < 4; ++e) h2[n][e] = tanh_fast(h2[n][e]);
   // layer 3: z3[d][o] = sum_j h2[d][j] W3[o][j] + b3[o]
   float z3[4];
   z3[0] = s.b3[2 * tq];
@@ -305,10 +317,10 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
     mma(z3, al, b[0], b[1]);
   }
   if (tq < 2) {
-    s.act[r0 + g][2 * tq] = tanhf(z3[0]);
-    s.act[r0 + g][2 * tq + 1] = tanhf(z3[1]);
-    s.act[r0 + g + 8][2 * tq] = tanhf(z3[2]);
-    s.act[r0 + g + 8][2 * tq + 1] = tanhf(z3[3]);
+    s.act[r0 + g][2 * tq] = tanh_fast(z3[0]);
+    s.act[r0 + g][2 * tq + 1] = tanh_fast(z3[1]);
+    s.act[r0 + g + 8][2 * tq] = tanh_fast(z3[2]);
+    s.act[r0 + g + 8][2 * tq + 1] = tanh_fast(z3[3]);
   }
 }
 

@@ -8,7 +8,7 @@ import workloads as W
 from oracle import physics as ph
 from paper_2606_01478_b300 import Sim
 
-from gpu_util import assert_parity, make_sim
+from gpu_util import FP_SLICES, TOL_FP, assert_parity, make_sim
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +63,9 @@ def test_batched_matches_uniform_path():
     """A batched handle over equal worlds of one model computes the same
     formulas as the uniform handle.  The two are separate kernels (per-world
     parameters in registers vs constant-bank operands), so the compiler may
-    fuse multiply-adds differently: agreement to float32 rounding, not bits."""
+    fuse multiply-adds differently: agreement to float32 rounding, not bits --
+    per field, 1/100 of the field's parity tolerance against the FP64 oracle
+    plus 1e-6 relative (a few float32 ulp)."""
     wl = W.config1(M=777, steps=90, K=45)
     a = make_sim(wl)
     a.run(90, 45)
@@ -74,7 +76,9 @@ def test_batched_matches_uniform_path():
     b.set_state(torch.tensor(wl.x0, dtype=torch.float32, device="cuda"))
     b.set_commands(torch.tensor(wl.cmd, dtype=torch.float32, device="cuda"), wl.hold)
     b.run(90, 45)
-    np.testing.assert_allclose(b.get_state().cpu().numpy(), sa, rtol=2e-6, atol=2e-6)
+    sb = b.get_state().cpu().numpy()
+    for k, sl in FP_SLICES.items():
+        np.testing.assert_allclose(sb[:, sl], sa[:, sl], rtol=1e-6, atol=1e-2 * TOL_FP[k], err_msg=k)
 
 
 def test_config2_full_size_sampled():
