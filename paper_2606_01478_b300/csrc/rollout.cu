@@ -529,8 +529,15 @@ __device__ __forceinline__ void policy_step(float* x, const float a[4], const De
   attitude_torque(R, Rd, x[10], x[11], x[12], P, tx, ty, tz);
   mixer(Td, tx, ty, tz, P, Wc);
   deriv_fp<MOTOR_LAG>(x, Wc, P, false, d);
+  // element pairs on the packed FP32 instructions (same rounding as fmaf per lane)
+  const float2 dt2 = make_float2(dt, dt);
 #pragma unroll
-  for (int j = 0; j < 17; ++j) x[j] = fmaf(dt, d[j], x[j]);
+  for (int j = 0; j < 16; j += 2) {
+    const float2 r = __ffma2_rn(dt2, make_float2(d[j], d[j + 1]), make_float2(x[j], x[j + 1]));
+    x[j] = r.x;
+    x[j + 1] = r.y;
+  }
+  x[16] = fmaf(dt, d[16], x[16]);
   const float in = rsqrt_approx(fmaf(x[3], x[3], fmaf(x[4], x[4], fmaf(x[5], x[5], x[6] * x[6]))));
   x[3] *= in;
   x[4] *= in;

@@ -99,50 +99,55 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
   const float* R0 = (MODEL == SIM_FIRST_PRINCIPLES) ? R : nullptr;
   // integrator coefficient c for element j (halved for q in the lag step form)
   auto co = [&](int j, float c) { return (LSF && j >= 3 && j <= 6) ? 0.5f * c : c; };
-  if constexpr (LSF) {
-    // Element-wise integrator arithmetic on element pairs (2i, 2i + 1) with the
-    // packed FP32 instructions (two lanes per instruction, each lane rounded as
-    // its scalar counterpart).
-    auto c2 = [&](int j, float c) { return make_float2(co(j, c), co(j + 1, c)); };
-    auto pr = [](const float* a, int j) { return make_float2(a[j], a[j + 1]); };
-    auto put = [](float* a, int j, float2 v) {
-      a[j] = v.x;
-      a[j + 1] = v.y;
-    };
-    if constexpr (INTEG == SIM_EULER) {
-      float d[D];
-      deriv(s, d, R0);
+  // Element-wise integrator arithmetic runs on element pairs (2i, 2i + 1) with the
+  // packed FP32 instructions (two lanes per instruction, each lane rounded as its
+  // scalar counterpart); D is odd, so element D - 1 is scalar.
+  constexpr int DP = D - 1;
+  auto c2 = [&](int j, float c) { return make_float2(co(j, c), co(j + 1, c)); };
+  auto pr = [](const float* a, int j) { return make_float2(a[j], a[j + 1]); };
+  auto put = [](float* a, int j, float2 v) {
+    a[j] = v.x;
+    a[j + 1] = v.y;
+  };
+  if constexpr (INTEG == SIM_EULER) {
+    float d[D];
+    deriv(s, d, R0);
 #pragma unroll
-      for (int j = 0; j < 16; j += 2) put(s, j, __ffma2_rn(c2(j, dt), pr(d, j), pr(s, j)));
-      s[16] = fmaf(dt, d[16], s[16]);
-    } else {
-      float k[D], acc[D], xs[D], k1W[4];
-      const float h2 = 0.5f * dt, h6 = dt * (1.f / 6.f);
-      const float2 two = make_float2(2.f, 2.f);
-      deriv(s, k, R0);
+    for (int j = 0; j < DP; j += 2) put(s, j, __ffma2_rn(c2(j, dt), pr(d, j), pr(s, j)));
+    s[DP] = fmaf(dt, d[DP], s[DP]);
+  } else {
+    // classic RK4; in the lag step form the rotor speeds (13..16) take the
+    // closed-form update and need no stage accumulator
+    constexpr int NA = LSF ? 13 : D;  // elements with an RK4 accumulator
+    float k[D], acc[D], xs[D], k1W[4];
+    const float h2 = 0.5f * dt, h6 = dt * (1.f / 6.f);
+    const float2 two = make_float2(2.f, 2.f);
+    deriv(s, k, R0);
 #pragma unroll
-      for (int j = 0; j < 16; j += 2) {
-        put(acc, j, pr(k, j));
-        put(xs, j, __ffma2_rn(c2(j, h2), pr(k, j), pr(s, j)));
-      }
-      xs[16] = fmaf(h2, k[16], s[16]);
+    for (int j = 0; j < DP; j += 2) {
+      put(acc, j, pr(k, j));
+      put(xs, j, __ffma2_rn(c2(j, h2), pr(k, j), pr(s, j)));
+    }
+    acc[DP] = k[DP];
+    xs[DP] = fmaf(h2, k[DP], s[DP]);
+    if constexpr (LSF) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) k1W[r] = k[13 + r];
-      deriv(xs, k, nullptr);
+    }
 #pragma unroll
-      for (int j = 0; j < 16; j += 2) {
-        if (j < 13) put(acc, j, __ffma2_rn(two, pr(k, j), pr(acc, j)));
-        put(xs, j, __ffma2_rn(c2(j, h2), pr(k, j), pr(s, j)));
-      }
-      xs[16] = fmaf(h2, k[16], s[16]);
+    for (int st = 0; st < 2; ++st) {
       deriv(xs, k, nullptr);
+      const float c = st == 0 ? h2 : dt;
 #pragma unroll
-      for (int j = 0; j < 16; j += 2) {
-        if (j < 13) put(acc, j, __ffma2_rn(two, pr(k, j), pr(acc, j)));
-        put(xs, j, __ffma2_rn(c2(j, dt), pr(k, j), pr(s, j)));
+      for (int j = 0; j < DP; j += 2) {
+        if (j < NA) put(acc, j, __ffma2_rn(two, pr(k, j), pr(acc, j)));
+        put(xs, j, __ffma2_rn(c2(j, c), pr(k, j), pr(s, j)));
       }
-      xs[16] = fmaf(dt, k[16], s[16]);
-      deriv(xs, k, nullptr);
+      if (DP < NA) acc[DP] = fmaf(2.f, k[DP], acc[DP]);
+      xs[DP] = fmaf(c, k[DP], s[DP]);
+    }
+    deriv(xs, k, nullptr);
+    if constexpr (LSF) {
 #pragma unroll
       for (int j = 0; j < 12; j += 2)
         put(s, j, __ffma2_rn(c2(j, h6), __fadd2_rn(pr(acc, j), pr(k, j)), pr(s, j)));
@@ -153,36 +158,12 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
       s[13] = fmaf(c4, k1W[0], s[13]);
       put(s, 14, __ffma2_rn(make_float2(c4, c4), make_float2(k1W[1], k1W[2]), pr(s, 14)));
       s[16] = fmaf(c4, k1W[3], s[16]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < DP; j += 2)
+        put(s, j, __ffma2_rn(c2(j, h6), __fadd2_rn(pr(acc, j), pr(k, j)), pr(s, j)));
+      s[DP] = fmaf(h6, acc[DP] + k[DP], s[DP]);
     }
-  } else if constexpr (INTEG == SIM_EULER) {
-    float d[D];
-    deriv(s, d, R0);
-#pragma unroll
-    for (int j = 0; j < D; ++j) s[j] = fmaf(dt, d[j], s[j]);
-  } else {
-    float k[D], acc[D], xs[D];
-    const float h2 = 0.5f * dt, h6 = dt * (1.f / 6.f);
-    deriv(s, k, R0);
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      acc[j] = k[j];
-      xs[j] = fmaf(h2, k[j], s[j]);
-    }
-    deriv(xs, k, nullptr);
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      acc[j] = fmaf(2.f, k[j], acc[j]);
-      xs[j] = fmaf(h2, k[j], s[j]);
-    }
-    deriv(xs, k, nullptr);
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      acc[j] = fmaf(2.f, k[j], acc[j]);
-      xs[j] = fmaf(dt, k[j], s[j]);
-    }
-    deriv(xs, k, nullptr);
-#pragma unroll
-    for (int j = 0; j < D; ++j) s[j] = fmaf(h6, acc[j] + k[j], s[j]);
   }
   if constexpr (MODEL == SIM_ABSTRACTED_NOTHRUST) s[12] = h.u[3];  // f_sum follows f_cmd at once
   if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
