@@ -52,6 +52,11 @@ struct __align__(16) Smem {
   float b1[64], b2[64], b3[8];
   float act[DPC][4];
   float dobs[DPC][16];
+  // adjoint kernel: double-buffered prefetch of the next step's state row,
+  // reference position and previous action (cp.async)
+  float pre_x[2][DPC][20];
+  float pre_r[2][DPC][4];
+  float4 pre_a[2][DPC];
 };
 
 struct RolloutArgs {
@@ -77,6 +82,17 @@ struct RolloutArgs {
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+// Asynchronous global -> shared copies (sm_80+ cp.async), completed by the
+// issuing thread's cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -714,6 +730,20 @@ __device__ __forceinline__ void store_row(float* __restrict__ base, int i, const
   p[4] = make_float4(x[16], 0.f, 0.f, 0.f);
 }
 
+// Prefetch helpers (one lane per drone): a 20-float row, a reference position.
+__device__ __forceinline__ void prefetch_row(float* dst, const float* __restrict__ base, int i) {
+  const float* q = base + (size_t)i * 20;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) cp_async16(dst + 4 * j, q + 4 * j);
+}
+__device__ __forceinline__ void prefetch_ref(float* dst, const float* __restrict__ p_ref, int k, int n,
+                                             int i) {
+  const float* q = p_ref + ((size_t)k * n + i) * 3;
+  cp_async4(dst, q);
+  cp_async4(dst + 1, q + 1);
+  cp_async4(dst + 2, q + 2);
+}
+
 __device__ __forceinline__ void ref_at(const float* __restrict__ p_ref, int k, int n, int i,
                                       float r[3]) {
   const float* q = p_ref + ((size_t)k * n + i) * 3;
@@ -797,14 +827,17 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
   load_row(a.x0, ii, x);
   float loss = 0.f;
   float ap[4] = {0.f, 0.f, 0.f, 0.f};  // previous action (a_{-1} = hover = 0)
+  float r[3];
+  ref_at(a.p_ref, 0, a.n, ii, r);
   for (int k = 0; k < a.H; ++k) {
+    // the next reference, loaded early: its latency overlaps this step's MLP
+    float rn[3];
+    ref_at(a.p_ref, k + 1, a.n, ii, rn);
     if (a.store_ckpt && (k % a.C) == 0 && valid && lane < 16) {
       store_row(a.ckpt + (size_t)(k / a.C) * a.n * 20, i, x);
       if (OBJ == SIM_OBJ_TRACKING_REWARD)
         a.ckpt_a[(size_t)(k / a.C) * a.n + i] = make_float4(ap[0], ap[1], ap[2], ap[3]);
     }
-    float r[3];
-    ref_at(a.p_ref, k, a.n, ii, r);
     if (lane < 16) put_obs(s, row, x, r);
     __syncwarp();
     float h1[8][4], h2[8][4];
@@ -813,8 +846,9 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
     float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
     __syncwarp();
     for (int j = 0; j < a.R; ++j) policy_step(x, act, P, a.dt);
-    ref_at(a.p_ref, k + 1, a.n, ii, r);
-    loss += step_loss<OBJ>(x, r, act, ap, a);
+    loss += step_loss<OBJ>(x, rn, act, ap, a);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r[c] = rn[c];
 #pragma unroll
     for (int o = 0; o < 4; ++o) ap[o] = act[o];
   }
@@ -852,14 +886,19 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
     load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
     float4 ap4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (OBJ == SIM_OBJ_TRACKING_REWARD) ap4 = a.ckpt_a[(size_t)sg * a.n + ii];
-    // recompute the segment's states
+    // recompute the segment's states (reference positions prefetched a step ahead)
+    if (lane < 16) prefetch_ref(s.pre_r[k0 & 1][row], a.p_ref, k0, a.n, ii);
+    cp_async_commit();
     for (int k = k0; k < k1; ++k) {
       if (valid && lane < 16) {
         store_row(a.seg + (size_t)(k - k0) * a.R * a.n * 20, i, x);
         if (OBJ == SIM_OBJ_TRACKING_REWARD) a.seg_a[(size_t)(k - k0) * a.n + i] = ap4;
       }
-      float r[3];
-      ref_at(a.p_ref, k, a.n, ii, r);
+      cp_async_wait_all();
+      __syncwarp();
+      const float r[3] = {s.pre_r[k & 1][row][0], s.pre_r[k & 1][row][1], s.pre_r[k & 1][row][2]};
+      if (lane < 16) prefetch_ref(s.pre_r[(k + 1) & 1][row], a.p_ref, k + 1, a.n, ii);
+      cp_async_commit();
       if (lane < 16) put_obs(s, row, x, r);
       __syncwarp();
       float h1[8][4], h2[8][4];
@@ -874,23 +913,44 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
       }
       ap4 = make_float4(act[0], act[1], act[2], act[3]);
     }
-    // reverse sweep
+    // the state after policy step k: x_{k1} from the recompute above, then the
+    // state loaded one iteration earlier
+    float xn[17];
+#pragma unroll
+    for (int j = 0; j < 17; ++j) xn[j] = x[j];
+    // reverse sweep.  Step k's state row, reference and previous action are
+    // prefetched during step k + 1.  Padded rows never read rows written by
+    // other warps: they replay the checkpoint row (finite data; their seed and
+    // dz rows are zero).
+    auto prefetch_step = [&](int k) {
+      float* bx = s.pre_x[k & 1][row];
+      if (valid) prefetch_row(bx, a.seg + (size_t)(k - k0) * a.R * a.n * 20, i);
+      else prefetch_row(bx, a.ckpt + (size_t)sg * a.n * 20, ii);
+      prefetch_ref(s.pre_r[k & 1][row], a.p_ref, k, a.n, ii);
+      if (OBJ == SIM_OBJ_TRACKING_REWARD)
+        cp_async16(&s.pre_a[k & 1][row], valid ? &a.seg_a[(size_t)(k - k0) * a.n + i]
+                                               : &a.ckpt_a[(size_t)sg * a.n + ii]);
+    };
+    __threadfence_block();  // this thread's segment rows precede its async copies of them
+    if (lane < 16) prefetch_step(k1 - 1);
+    cp_async_commit();
     for (int k = k1 - 1; k >= k0; --k) {
+      cp_async_wait_all();
       __syncwarp();
-      // padded rows never read rows written by other warps: they replay the
-      // checkpoint row (finite data; their seed and dz rows are zero)
-      if (valid) load_row(a.seg + (size_t)(k - k0) * a.R * a.n * 20, i, x);
-      else load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
+      const int b = k & 1;
+#pragma unroll
+      for (int j = 0; j < 17; ++j) x[j] = s.pre_x[b][row][j];
+      const float r[3] = {s.pre_r[b][row][0], s.pre_r[b][row][1], s.pre_r[b][row][2]};
       float ap[4] = {0.f, 0.f, 0.f, 0.f};
       if (OBJ == SIM_OBJ_TRACKING_REWARD) {
-        const float4 t = valid ? a.seg_a[(size_t)(k - k0) * a.n + i] : a.ckpt_a[(size_t)sg * a.n + ii];
+        const float4 t = s.pre_a[b][row];
         ap[0] = t.x;
         ap[1] = t.y;
         ap[2] = t.z;
         ap[3] = t.w;
       }
-      float r[3];
-      ref_at(a.p_ref, k, a.n, ii, r);
+      if (k > k0 && lane < 16) prefetch_step(k - 1);
+      cp_async_commit();
       if (lane < 16) put_obs(s, row, x, r);
       __syncwarp();
       {
@@ -903,14 +963,6 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
       const float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
       // loss term at policy step k + 1 (state after the last sub-step)
       {
-        float xn[17];
-        if (a.R > 1 && valid) {
-          load_row(a.seg + ((size_t)(k - k0) * a.R + a.R - 1) * a.n * 20, i, xn);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 17; ++j) xn[j] = x[j];
-        }
-        policy_step(xn, act, P, a.dt);
         float rn[3];
         ref_at(a.p_ref, k + 1, a.n, ii, rn);
         step_loss_state_adjoint<OBJ>(xn, rn, seed, a, lam);
@@ -962,6 +1014,8 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
       // observation adjoint: obs = [p - r, q, v, w]
 #pragma unroll
       for (int j = 0; j < 13; ++j) lam[j] += s.dobs[row][j];
+#pragma unroll
+      for (int j = 0; j < 17; ++j) xn[j] = x[j];
       __syncthreads();  // every warp's tiles for this step are in shared memory
       accumulate_dw(s, v, lane, acc);
       __syncthreads();  // before the next step overwrites the tiles
