@@ -421,7 +421,8 @@ def measure_config2(dev, reps: int = 3) -> dict:
             achieved = byt * wl.steps / (ms / 1e3) / 1e9
             rec["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
                                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                               "traffic": None, "bytes_per_launch": byt,
+                               "traffic": _profiled_traffic("step_batched_kernel", wl.name + "_K1"),
+                               "bytes_per_launch": byt,
                                "peak_basis": f"{kind} HBM copy bandwidth"}
         else:
             flop = (n_fp * FLOP_PER_DRONE_STEP[("fp", "euler", "attitude")]
