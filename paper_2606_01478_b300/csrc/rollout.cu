@@ -38,14 +38,19 @@ constexpr int OFF_W1 = 0, OFF_B1 = 832, OFF_W2 = 896, OFF_B2 = 4992, OFF_W3 = 50
               OFF_B3 = 5312, NPOL = 5316, NPOL_PAD = 5376;
 constexpr int TPB = 128, DPC = 64;  // threads and drones per CTA
 constexpr int S16 = 24, S64 = 72;   // padded smem row strides (bf16 elements)
+// One warp's cached activations of one step, in 16-byte chunks: h1 hi, h1 lo,
+// h2 hi, h2 lo (16 rows x S64 bf16 = 144 chunks each), then 16 action rows.
+constexpr int TILE_CHUNKS = 16 * S64 * 2 / 16, CACHE_CHUNKS = 4 * TILE_CHUNKS + 16;
 
 struct __align__(16) Smem {
   __nv_bfloat16 W1[64 * S16];  // [i][c]  (c < 13 used)
   __nv_bfloat16 W2[64 * S64];  // [j][i]
   __nv_bfloat16 W3[16 * S64];  // [o][j]  (o < 4 used)
   __nv_bfloat16 obs[2][DPC * S16];  // hi, lo; column 13 = 1 (bias column)
-  __nv_bfloat16 h1[2][DPC * S64];   // column 64 = 1
-  __nv_bfloat16 h2[2][DPC * S64];   // column 64 = 1
+  // activation tiles [buffer][hi, lo] (column 64 = 1): the adjoint's reverse sweep
+  // reads step k from buffer k & 1 while step k - 1's copy arrives in the other
+  __nv_bfloat16 h1[2][2][DPC * S64];
+  __nv_bfloat16 h2[2][2][DPC * S64];
   __nv_bfloat16 dz1[2][DPC * S64];
   __nv_bfloat16 dz2[2][DPC * S64];
   __nv_bfloat16 dz3[2][DPC * S16];
@@ -57,6 +62,7 @@ struct __align__(16) Smem {
   float pre_x[2][DPC][20];
   float pre_r[2][DPC][4];
   float4 pre_a[2][DPC];
+  float actb[2][DPC][4];  // cached actions of the reverse sweep [buffer]
 };
 
 struct RolloutArgs {
@@ -68,6 +74,7 @@ struct RolloutArgs {
   float* loss_w;          // [n] per-drone loss
   float* part;            // [n_cta][NPOL_PAD] dW partials
   float* dx0;             // [n][20]
+  uint4* hcache;          // [C][n_warps][CACHE_CHUNKS] activation tiles + actions per step
   const float* dL;        // device scalar: upstream gradient of the loss
   float4* ckpt_a;         // [n_ckpt][n] previous action at each checkpoint (reward objective)
   float4* seg_a;          // [C][n] previous action of each segment step (reward objective)
@@ -210,10 +217,12 @@ __device__ void load_weights(Smem& s, const uint16_t* __restrict__ w) {
   const __nv_bfloat16 one = __float2bfloat16(1.f);
   for (int r = threadIdx.x; r < DPC; r += TPB) {
     for (int c = 64; c < S64; ++c) {
-      s.h1[0][r * S64 + c] = c == 64 ? one : z;
-      s.h1[1][r * S64 + c] = z;
-      s.h2[0][r * S64 + c] = c == 64 ? one : z;
-      s.h2[1][r * S64 + c] = z;
+      for (int b = 0; b < 2; ++b) {
+        s.h1[b][0][r * S64 + c] = c == 64 ? one : z;
+        s.h1[b][1][r * S64 + c] = z;
+        s.h2[b][0][r * S64 + c] = c == 64 ? one : z;
+        s.h2[b][1][r * S64 + c] = z;
+      }
       s.dz1[0][r * S64 + c] = z;
       s.dz1[1][r * S64 + c] = z;
       s.dz2[0][r * S64 + c] = z;
@@ -341,9 +350,9 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
 }
 
 // MLP backward for the warp's 16 drones, given dz3 rows in s.dz3 and the
-// forward activations in s.h1 / s.h2 (hi + lo).  Writes dz1, dz2 tiles and the
+// forward activations in buffer b of s.h1 / s.h2 (hi + lo).  Writes dz1, dz2 tiles and the
 // observation adjoint into s.dobs.
-__device__ void mlp_backward(Smem& s, int r0, int lane) {
+__device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
   const int g = lane >> 2, tq = lane & 3;
   const int arow = r0 + (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
   // transposed B fragments: storage [k][n]
@@ -369,7 +378,7 @@ __device__ void mlp_backward(Smem& s, int r0, int lane) {
   // dz2 = dh2 (1 - h2^2)
   {
     float h[8][4];
-    load_c64(s.h2, r0, lane, h);
+    load_c64(s.h2[b], r0, lane, h);
 #pragma unroll
     for (int n = 0; n < 8; ++n)
 #pragma unroll
@@ -397,7 +406,7 @@ __device__ void mlp_backward(Smem& s, int r0, int lane) {
   // dz1 = dh1 (1 - h1^2)
   {
     float h[8][4];
-    load_c64(s.h1, r0, lane, h);
+    load_c64(s.h1[b], r0, lane, h);
 #pragma unroll
     for (int n = 0; n < 8; ++n)
 #pragma unroll
@@ -436,7 +445,7 @@ struct DwAcc {
   float w3[3][4];
 };
 
-__device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc) {
+__device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc, int hb) {
   // A = dz^T: A(row m, col d) = dz[d][m], storage [d][m] -> transposed load
   const int arow = (lane & 7) + (lane >> 4) * 8, acol = ((lane >> 3) & 1) * 8;
   // B(k = d, n) = act[d][n], storage [d][n] -> transposed load
@@ -451,8 +460,8 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc) {
 #pragma unroll
     for (int n = 0; n < 8; n += 2) {
       uint32_t bh[4], bl[4];
-      ldsm_x4_t(bh, &s.h1[0][(d0 + brow) * S64 + 8 * n + bcol]);
-      ldsm_x4_t(bl, &s.h1[1][(d0 + brow) * S64 + 8 * n + bcol]);
+      ldsm_x4_t(bh, &s.h1[hb][0][(d0 + brow) * S64 + 8 * n + bcol]);
+      ldsm_x4_t(bl, &s.h1[hb][1][(d0 + brow) * S64 + 8 * n + bcol]);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         mma(acc.w2[n + u], ah, bh[2 * u], bh[2 * u + 1]);
@@ -462,7 +471,7 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc) {
     }
     {
       uint32_t bh[2];
-      ldsm_x2_t(bh, &s.h1[0][(d0 + brow) * S64 + 64]);
+      ldsm_x2_t(bh, &s.h1[hb][0][(d0 + brow) * S64 + 64]);
       mma(acc.w2[8], ah, bh[0], bh[1]);
       mma(acc.w2[8], al, bh[0], bh[1]);  // the bias column is exact (lo = 0)
     }
@@ -485,8 +494,8 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc) {
     ldsm_x4_t(al, &s.dz3[1][(d0 + arow) * S16 + acol]);
     {
       uint32_t bh[4], bl[4];
-      ldsm_x4_t(bh, &s.h2[0][(d0 + brow) * S64 + 16 * v + bcol]);
-      ldsm_x4_t(bl, &s.h2[1][(d0 + brow) * S64 + 16 * v + bcol]);
+      ldsm_x4_t(bh, &s.h2[hb][0][(d0 + brow) * S64 + 16 * v + bcol]);
+      ldsm_x4_t(bl, &s.h2[hb][1][(d0 + brow) * S64 + 16 * v + bcol]);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         mma(acc.w3[u], ah, bh[2 * u], bh[2 * u + 1]);
@@ -495,7 +504,7 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc) {
       }
       if (v == 3) {
         uint32_t b1[2];
-        ldsm_x2_t(b1, &s.h2[0][(d0 + brow) * S64 + 64]);
+        ldsm_x2_t(b1, &s.h2[hb][0][(d0 + brow) * S64 + 64]);
         mma(acc.w3[2], ah, b1[0], b1[1]);
         mma(acc.w3[2], al, b1[0], b1[1]);
       }
@@ -752,6 +761,19 @@ __device__ __forceinline__ void ref_at(const float* __restrict__ p_ref, int k, i
   r[2] = q[2];
 }
 
+// ------------------------------------------------------------------ activation cache
+
+// Shared-memory address of chunk c of warp rows r0..r0+15 in tile buffer b
+// (c < 4 TILE_CHUNKS: activation tiles, else action rows of act).
+__device__ __forceinline__ void* cache_smem(Smem& s, int b, int r0, int c, float (*act)[4]) {
+  const int q = c / TILE_CHUNKS, w = c - q * TILE_CHUNKS;
+  if (q < 4) {
+    __nv_bfloat16* t = (q < 2 ? s.h1[b][q] : s.h2[b][q - 2]) + r0 * S64;
+    return reinterpret_cast<uint4*>(t) + w;
+  }
+  return act[r0 + w];
+}
+
 // ------------------------------------------------------------------ objectives
 
 // Loss of one step: x = post-step state, r = reference at that step, act the
@@ -901,9 +923,19 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
       cp_async_commit();
       if (lane < 16) put_obs(s, row, x, r);
       __syncwarp();
-      float h1[8][4], h2[8][4];
-      mlp_forward(s, r0, lane, h1, h2);
+      {
+        float h1[8][4], h2[8][4];
+        mlp_forward(s, r0, lane, h1, h2);
+        // keep this step's activations for the reverse sweep (tiles staged in buffer 0)
+        store_c64(s.h1[0], r0, lane, h1);
+        store_c64(s.h2[0], r0, lane, h2);
+      }
       __syncwarp();
+      {
+        uint4* dst = a.hcache + ((size_t)(k - k0) * gridDim.x * 4 + blockIdx.x * 4 + v) * CACHE_CHUNKS;
+        for (int c = lane; c < CACHE_CHUNKS; c += 32)
+          dst[c] = *reinterpret_cast<const uint4*>(cache_smem(s, 0, r0, c, s.act));
+      }
       float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
       __syncwarp();
       for (int j = 0; j < a.R; ++j) {
@@ -931,8 +963,15 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
         cp_async16(&s.pre_a[k & 1][row], valid ? &a.seg_a[(size_t)(k - k0) * a.n + i]
                                                : &a.ckpt_a[(size_t)sg * a.n + ii]);
     };
+    // step k's activation tiles and actions, copied back from the cache into
+    // buffer k & 1 (each lane reads back the chunks it wrote)
+    auto prefetch_tiles = [&](int k) {
+      const uint4* src = a.hcache + ((size_t)(k - k0) * gridDim.x * 4 + blockIdx.x * 4 + v) * CACHE_CHUNKS;
+      for (int c = lane; c < CACHE_CHUNKS; c += 32) cp_async16(cache_smem(s, k & 1, r0, c, s.actb[k & 1]), src + c);
+    };
     __threadfence_block();  // this thread's segment rows precede its async copies of them
     if (lane < 16) prefetch_step(k1 - 1);
+    prefetch_tiles(k1 - 1);
     cp_async_commit();
     for (int k = k1 - 1; k >= k0; --k) {
       cp_async_wait_all();
@@ -949,18 +988,14 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
         ap[2] = t.z;
         ap[3] = t.w;
       }
-      if (k > k0 && lane < 16) prefetch_step(k - 1);
+      if (k > k0) {
+        if (lane < 16) prefetch_step(k - 1);
+        prefetch_tiles(k - 1);
+      }
       cp_async_commit();
       if (lane < 16) put_obs(s, row, x, r);
       __syncwarp();
-      {
-        float h1[8][4], h2[8][4];
-        mlp_forward(s, r0, lane, h1, h2);
-        store_c64(s.h1, r0, lane, h1);
-        store_c64(s.h2, r0, lane, h2);
-      }
-      __syncwarp();
-      const float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
+      const float act[4] = {s.actb[b][row][0], s.actb[b][row][1], s.actb[b][row][2], s.actb[b][row][3]};
       // loss term at policy step k + 1 (state after the last sub-step)
       {
         float rn[3];
@@ -1009,7 +1044,7 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
         }
       }
       __syncwarp();
-      mlp_backward(s, r0, lane);
+      mlp_backward(s, r0, lane, b);
       __syncwarp();
       // observation adjoint: obs = [p - r, q, v, w]
 #pragma unroll
@@ -1017,7 +1052,7 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
 #pragma unroll
       for (int j = 0; j < 17; ++j) xn[j] = x[j];
       __syncthreads();  // every warp's tiles for this step are in shared memory
-      accumulate_dw(s, v, lane, acc);
+      accumulate_dw(s, v, lane, acc, b);
       __syncthreads();  // before the next step overwrites the tiles
     }
   }
@@ -1092,7 +1127,7 @@ size_t rollout_workspace_bytes(int n, int H, int C, int objective, int R) {
   const int n_cta = (n + ro::DPC - 1) / ro::DPC;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   size_t b = al((size_t)n_ck * n * 20 * 4) + al((size_t)C * R * n * 20 * 4) + al((size_t)n * 4) +
-             al((size_t)n_cta * ro::NPOL_PAD * 4);
+             al((size_t)n_cta * ro::NPOL_PAD * 4) + al((size_t)C * n_cta * 4 * ro::CACHE_CHUNKS * 16);
   if (objective == SIM_OBJ_TRACKING_REWARD) b += al((size_t)n_ck * n * 16) + al((size_t)C * n * 16);
   return b;
 }
@@ -1111,6 +1146,8 @@ static void carve(void* ws, int n, int H, int C, int R, const RolloutObjective& 
   p += al((size_t)n * 4);
   a.part = (float*)p;
   p += al((size_t)n_cta * ro::NPOL_PAD * 4);
+  a.hcache = (uint4*)p;
+  p += al((size_t)C * n_cta * 4 * ro::CACHE_CHUNKS * 16);
   if (obj.kind == SIM_OBJ_TRACKING_REWARD) {
     a.ckpt_a = (float4*)p;
     p += al((size_t)n_ck * n * 16);
