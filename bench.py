@@ -322,10 +322,7 @@ def run_b300(args, wl):
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        sim.set_state(x0_host)
-        sim.set_commands(cmd_host, wl.hold)
-        one_rollout(None)
-        sim.get_state(out=out_host)
+        sim.run_host(x0_host, cmd_host, wl.hold, wl.steps, wl.K, out=out_host)
         t1.record(stream)
         t1.synchronize()
         e2e_ms.append(t0.elapsed_time(t1))

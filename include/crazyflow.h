@@ -146,15 +146,19 @@ int sim_bind(sim_h h, void* workspace, size_t bytes, int64_t max_cmd_blocks, voi
 int sim_set_params(sim_h h, const float* params, int64_t n_sets, const int32_t* set_of_world,
                    void* stream);
 
-/* Load / read the state as rows [Ntot][SIM_STATE_DIM].  x may be host memory
- * (pinned or pageable; copied through the workspace staging area) or device
- * memory (read/written directly).  Asynchronous on stream; for pageable host
- * memory CUDA makes the copy synchronous with respect to the host. */
+/* Load / read the state as rows [Ntot][SIM_STATE_DIM].  x may be device
+ * memory or pinned host memory, both read/written in place by the layout
+ * kernel (pinned host rows travel over the host link as that kernel's own loads
+ * and stores), or pageable host memory (copied through the workspace staging
+ * area).  Asynchronous on stream: x must stay valid and unchanged until stream
+ * reaches the end of the call's work (for pageable memory CUDA makes the copy
+ * synchronous with respect to the host). */
 int sim_set_state(sim_h h, const float* x, void* stream);
 int sim_get_state(sim_h h, float* x, void* stream);
 
-/* Commands: cmd is [n_blocks][Ntot][SIM_CMD_DIM] (host or device memory,
- * copied into the workspace).  Step s after this call (s = 0, 1, ...) uses
+/* Commands: cmd is [n_blocks][Ntot][SIM_CMD_DIM] (device or pinned host memory,
+ * copied into the workspace by a kernel; pageable host memory, by the copy
+ * engine).  Asynchronous on stream, as for sim_set_state.  Step s after this call (s = 0, 1, ...) uses
  * block min(s / hold, n_blocks - 1).  1 <= n_blocks <= max_cmd_blocks, hold >= 1. */
 int sim_set_commands(sim_h h, const float* cmd, int64_t n_blocks, int hold, void* stream);
 
@@ -164,6 +168,21 @@ int sim_step(sim_h h, int K, void* stream);
 
 /* Advance n_steps steps as ceil(n_steps / K) launches of at most K steps. */
 int sim_run(sim_h h, int64_t n_steps, int K, void* stream);
+
+/* One rollout from host memory to host memory on `stream`: sim_set_state(x0),
+ * sim_set_commands(cmd, n_blocks, hold), sim_run(n_steps, K) and
+ * sim_get_state(x_out) in one call.  With pinned (or device) buffers no copy
+ * engine is involved: the layout kernels read and write the state rows in place
+ * and a gather kernel moves the commands, SM loads crossing the host link (on
+ * B300 systems measured several times faster host-to-device than the copy
+ * engine).  The paper has no counterpart; it serves callers whose states and
+ * commands live on the host.
+ *   x0, x_out [Ntot][SIM_STATE_DIM] float, cmd [n_blocks][Ntot][4] float:
+ *   16-byte aligned, caller-owned, valid and unchanged until `stream` reaches
+ *   the end of the call's work (x_out is complete then).
+ * Errors as for the four calls it stands for. */
+int sim_run_host(sim_h h, const float* x0, const float* cmd, int64_t n_blocks, int hold,
+                 int64_t n_steps, int K, float* x_out, void* stream);
 
 /* Threads per block used by sim_step (default 128; 32..256, multiple of 32). */
 int sim_set_block_size(sim_h h, int threads_per_block);

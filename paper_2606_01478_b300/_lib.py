@@ -84,6 +84,8 @@ _SIGS = {
                                  c_int, c_void_p, c_void_p]),
     "sim_philox_normals": (c_int, [c_void_p, ctypes.c_uint64, c_int64, c_int, c_void_p, c_void_p,
                                    c_void_p]),
+    "sim_run_host": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int64, c_int, c_void_p,
+                             c_void_p]),
     "sim_rollout_set_objective": (c_int, [c_void_p, POINTER(Objective)]),
     "sim_rollout_set_action_repeat": (c_int, [c_void_p, c_int]),
     "sim_rollout_workspace_bytes": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),

@@ -65,5 +65,7 @@ void note_error(sim_h h, const char* fmt, ...);
 // Row-major [n][20] floats <-> 5 float4 planes [5][n] (layout.cu).
 cudaError_t launch_rows_to_planes(const float4* rows, float4* planes, int n, cudaStream_t st);
 cudaError_t launch_planes_to_rows(const float4* planes, float4* rows, int n, cudaStream_t st);
+// grid-stride 16-byte copy with at most max_blocks blocks of 256 threads
+cudaError_t launch_copy16(const float4* src, float4* dst, int64_t n, int max_blocks, cudaStream_t st);
 
 }  // namespace cf

@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <initializer_list>
 #include <new>
 #include <vector>
@@ -106,6 +107,20 @@ bool is_device_pointer(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Where kernels can reach a caller's buffer: itself for device memory, its device
+// address for pinned host memory (kernels then move the data over the host link
+// themselves), nullptr for pageable host memory (copy-engine transfers).
+const void* kernel_view(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+  return nullptr;
 }
 
 bool valid_enums(int model, int integrator) {
@@ -401,9 +416,9 @@ int sim_set_state(sim_h h, const float* x, void* stream) {
   if (!h->ws) return fail(h, SIM_ESTATE, "sim_bind must come first");
   if (!x || ((uintptr_t)x & 15)) return fail(h, SIM_EINVAL, "state pointer must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
-  const float4* rows = (const float4*)x;
+  const float4* rows = (const float4*)kernel_view(x);  // device or pinned host: read in place
   cudaError_t e;
-  if (!is_device_pointer(x)) {
+  if (!rows) {
     e = cudaMemcpyAsync(h->staging, x, (size_t)h->ntot * SIM_STATE_DIM * sizeof(float),
                         cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "copying the state to the device");
@@ -421,12 +436,12 @@ int sim_get_state(sim_h h, float* x, void* stream) {
   if (!h->ws || !h->state_ok) return fail(h, SIM_ESTATE, "no state has been set");
   if (!x || ((uintptr_t)x & 15)) return fail(h, SIM_EINVAL, "state pointer must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
-  const bool dev = is_device_pointer(x);
-  float4* rows = dev ? (float4*)x : h->staging;
+  float4* view = (float4*)kernel_view(x);  // device or pinned host: written in place
+  float4* rows = view ? view : h->staging;
   cudaError_t e = cf::launch_planes_to_rows(h->planes, rows, (int)h->ntot, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "planes_to_rows launch");
   h->launches++;
-  if (!dev) {
+  if (!view) {
     e = cudaMemcpyAsync(x, h->staging, (size_t)h->ntot * SIM_STATE_DIM * sizeof(float),
                         cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "copying the state to the host");
@@ -441,8 +456,10 @@ int sim_set_commands(sim_h h, const float* cmd, int64_t n_blocks, int hold, void
       n_blocks * (int64_t)hold > 0x7fffffffLL)
     return fail(h, SIM_EINVAL, "need a command array, 1 <= n_blocks <= %lld, hold >= 1",
                 (long long)h->max_blocks);
-  cudaError_t e = cudaMemcpyAsync(h->cmd, cmd, (size_t)n_blocks * h->ntot * sizeof(float4),
-                                  cudaMemcpyDefault, (cudaStream_t)stream);
+  const float4* view = (const float4*)kernel_view(cmd);
+  cudaError_t e = view ? cf::launch_copy16(view, h->cmd, n_blocks * h->ntot, 592, (cudaStream_t)stream)
+                       : cudaMemcpyAsync(h->cmd, cmd, (size_t)n_blocks * h->ntot * sizeof(float4),
+                                         cudaMemcpyDefault, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "copying commands");
   h->n_blocks = n_blocks;
   h->hold = hold;
@@ -498,6 +515,22 @@ int sim_run(sim_h h, int64_t n_steps, int K, void* stream) {
     n_steps -= k;
   }
   return SIM_OK;
+}
+
+int sim_run_host(sim_h h, const float* x0, const float* cmd, int64_t n_blocks, int hold,
+                 int64_t n_steps, int K, float* x_out, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!h->ws || !h->params_ok) return fail(h, SIM_ESTATE, "sim_bind and sim_set_params must come first");
+  if (n_steps < 0 || K < 1 || K > 100000) return fail(h, SIM_EINVAL, "need n_steps >= 0 and 1 <= K <= 100000");
+  // one stream, no copy engine for pinned or device buffers: measured on B300
+  // systems whose host-to-device copy engine is several times slower than SM
+  // loads over the host link, overlapping command copies with the step kernels
+  // (copy engine or a concurrent gather kernel) lost to this sequence
+  int r = sim_set_state(h, x0, stream);
+  if (r == SIM_OK) r = sim_set_commands(h, cmd, n_blocks, hold, stream);
+  if (r == SIM_OK) r = sim_run(h, n_steps, K, stream);
+  if (r == SIM_OK) r = sim_get_state(h, x_out, stream);
+  return r;
 }
 
 int sim_status(sim_h h, uint32_t* flags, void* stream) {

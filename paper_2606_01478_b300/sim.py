@@ -133,6 +133,28 @@ class Sim:
     def run(self, n_steps: int, K: int, stream=None):
         self._check(self.lib.sim_run(self.h, int(n_steps), int(K), _stream_ptr(stream)))
 
+    def run_host(self, x0: torch.Tensor, cmd: torch.Tensor, hold: int, n_steps: int, K: int,
+                 out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """One rollout from (pinned) host tensors to a host tensor, command blocks
+        streamed in behind the first launches (sim_run_host)."""
+        if cmd.dim() == 2:
+            cmd = cmd[None]
+        shape = (self.ntot, L.STATE_DIM)
+        if x0.dtype != torch.float32 or not x0.is_contiguous() or tuple(x0.shape) != shape:
+            raise ValueError(f"x0 must be contiguous float32 {list(shape)}")
+        if cmd.dtype != torch.float32 or not cmd.is_contiguous() or cmd.shape[1:] != (self.ntot, L.CMD_DIM):
+            raise ValueError(f"commands must be contiguous float32 [n_blocks, {self.ntot}, 4]")
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+        if out.dtype != torch.float32 or not out.is_contiguous() or tuple(out.shape) != shape:
+            raise ValueError("bad output tensor")
+        self._check(self.lib.sim_run_host(self.h, ctypes.c_void_p(x0.data_ptr()), ctypes.c_void_p(cmd.data_ptr()),
+                                          cmd.shape[0], int(hold), int(n_steps), int(K),
+                                          ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        self._cmd_src = cmd
+        self._hold = int(hold)
+        return out
+
     def capture_run(self, n_steps: int, K: int) -> torch.cuda.CUDAGraph:
         """Capture `n_steps` steps (launches of at most K) into a CUDA graph.
 

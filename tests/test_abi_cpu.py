@@ -149,3 +149,11 @@ def test_rollout_action_repeat_validation(lib):
     # segments keep C R sub-step states of 80 bytes
     assert nb10.value >= nb1.value + 32 * 80 * 10 * 9
     lib.sim_destroy(h)
+
+
+def test_run_host_validates_before_any_cuda_call(lib):
+    r, h = _create(lib, 8, 2)
+    buf = ctypes.c_void_p(0x1000)
+    assert lib.sim_run_host(h, buf, buf, 1, 1, 10, 5, buf, None) == L.SIM_ESTATE
+    assert b"bind" in lib.sim_last_error(h)
+    lib.sim_destroy(h)

@@ -203,3 +203,35 @@ def test_call_order_and_argument_errors():
     sim.set_commands(c[:1].contiguous(), 10)
     sim.step(3)
     assert sim.steps_taken == 3
+
+
+@pytest.mark.parametrize("where", ["pinned", "pageable", "device"])
+def test_run_host_equals_separate_calls(where):
+    """sim_run_host (state rows read and written in place, commands gathered by a
+    kernel, when the buffers are pinned or on the device) gives the bits of
+    set_state + set_commands + run + get_state from device buffers: 777 drones,
+    RK4, 230 steps as launches of K = 40 (last one short), hold 30, 12 command
+    blocks (more than the 230 steps read)."""
+    wl = W.config1(M=777, steps=230, K=40)
+    cmd = np.random.default_rng(3).uniform(-0.5, 0.5, (12, 777, 4))
+    a = make_sim(wl, max_blocks=12)
+    a.set_commands(torch.tensor(cmd, dtype=torch.float32, device="cuda"), 30)
+    a.run(230, 40)
+    ref = a.get_state().cpu()
+    b = make_sim(wl, max_blocks=12)
+    x0 = torch.tensor(wl.x0, dtype=torch.float32)
+    c = torch.tensor(cmd, dtype=torch.float32)
+    out = None
+    if where == "pinned":
+        x0, c = x0.pin_memory(), c.pin_memory()
+    elif where == "device":
+        x0, c = x0.cuda(), c.cuda()
+        out = torch.empty(777, 20, device="cuda")
+    got = b.run_host(x0, c, 30, 230, 40, out=out)
+    torch.cuda.synchronize()
+    assert torch.equal(got.cpu(), ref)
+    assert b.steps_taken == 230
+    # the handle continues from there like the separate calls
+    a.run(20, 20)
+    b.run(20, 20)
+    assert torch.equal(a.get_state().cpu(), b.get_state().cpu())
