@@ -25,10 +25,7 @@
 // are bf16 values; activations and adjoints enter the MMAs as hi + lo bf16
 // pairs (2 MMAs, ~2^-16 relative), dW products as hi*hi + hi*lo + lo*hi.
 // The accumulator fragment of one layer is the A fragment of the next, so
-// activations stay in registers between layers.  The weight gradients of layers 1
-// and 2, dense contractions over the CTA's 64 drones per step, run on tcgen05.mma
-// with fp32 accumulators in tensor memory, issued by one thread and completed
-// asynchronously while the warps go on with the next step.
+// activations stay in registers between layers.
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -41,39 +38,21 @@ constexpr int OFF_W1 = 0, OFF_B1 = 832, OFF_W2 = 896, OFF_B2 = 4992, OFF_W3 = 50
               OFF_B3 = 5312, NPOL = 5316, NPOL_PAD = 5376;
 constexpr int TPB = 128, DPC = 64;  // threads and drones per CTA
 constexpr int S16 = 24, S64 = 72;   // padded smem row strides (bf16 elements)
-// Weight-gradient operands of the tensor-memory MMAs: K-major tiles (K = the
-// CTA's 64 drones) in the canonical layout without swizzle -- 8-row x 16-byte core
-// matrices stored contiguously, core matrices along K 128 bytes apart, 8-row
-// groups 1024 bytes apart.  A: rows 0..63 dz2^T (j), 64..127 dz1^T (i), so one
-// M = 128 MMA on rows 0..127 gives dW2 in its first 64 rows (the other rows are
-// never read); B: h1 (N = 80: rows i, bias row 64, zero rows) and obs (N = 16).
-constexpr int TC_M = 128, H1_ROWS = 80, OB_ROWS = 16;
-constexpr int A_BYTES = TC_M * DPC * 2, H1_BYTES = H1_ROWS * DPC * 2, OB_BYTES = OB_ROWS * DPC * 2;
-constexpr uint32_t TMEM_COLS = 128, TMEM_DW1 = 96;  // dW2 in columns 0..79, dW1 in 96..111
-// Byte offset of element (row, drone d) in a canonical K-major tile.
-__device__ __forceinline__ int kmaj(int row, int d) {
-  return (row >> 3) * 1024 + (d >> 3) * 128 + (row & 7) * 16 + (d & 7) * 2;
-}
-
-// One warp's cached activations of one step, in 16-byte chunks: h1 hi, h1 lo (its
-// 16 drones of rows 0..63 of the canonical tile: 8 groups x 256 bytes each), h2 hi,
-// h2 lo (16 rows x S64 bf16 = 144 chunks each), then 16 action rows.
-constexpr int H1_CHUNKS = 8 * 16, TILE_CHUNKS = 16 * S64 * 2 / 16,
-              CACHE_CHUNKS = 2 * H1_CHUNKS + 2 * TILE_CHUNKS + 16;
+// One warp's cached activations of one step, in 16-byte chunks: h1 hi, h1 lo,
+// h2 hi, h2 lo (16 rows x S64 bf16 = 144 chunks each), then 16 action rows.
+constexpr int TILE_CHUNKS = 16 * S64 * 2 / 16, CACHE_CHUNKS = 4 * TILE_CHUNKS + 16;
 
 struct __align__(16) Smem {
-  // tcgen05 operand tiles; A[1][1] must be followed by 8 KB of this struct (the
-  // rows 64..127 of the dW1 MMA, computed and never read)
-  unsigned char A[2][2][A_BYTES];    // [step parity][hi, lo]
-  unsigned char H1[3][2][H1_BYTES];  // [buffer][hi, lo]
-  unsigned char OB[2][2][OB_BYTES];  // [step parity][hi, lo]
   __nv_bfloat16 W1[64 * S16];  // [i][c]  (c < 13 used)
   __nv_bfloat16 W2[64 * S64];  // [j][i]
   __nv_bfloat16 W3[16 * S64];  // [o][j]  (o < 4 used)
   __nv_bfloat16 obs[2][DPC * S16];  // hi, lo; column 13 = 1 (bias column)
-  // h2 tiles [buffer][hi, lo] (column 64 = 1): the adjoint's reverse sweep reads
-  // step k from buffer k & 1 while step k - 1's copy arrives in the other
+  // activation tiles [buffer][hi, lo] (column 64 = 1): the adjoint's reverse sweep
+  // reads step k from buffer k & 1 while step k - 1's copy arrives in the other
+  __nv_bfloat16 h1[2][2][DPC * S64];
   __nv_bfloat16 h2[2][2][DPC * S64];
+  __nv_bfloat16 dz1[2][DPC * S64];
+  __nv_bfloat16 dz2[2][DPC * S64];
   __nv_bfloat16 dz3[2][DPC * S16];
   float b1[64], b2[64], b3[8];
   float act[DPC][4];
@@ -84,8 +63,6 @@ struct __align__(16) Smem {
   float pre_r[2][DPC][4];
   float4 pre_a[2][DPC];
   float actb[2][DPC][4];  // cached actions of the reverse sweep [buffer]
-  unsigned long long mbar[2];  // completion of each step parity's tensor-memory MMAs
-  uint32_t tmem_base;
 };
 
 struct RolloutArgs {
@@ -99,7 +76,6 @@ struct RolloutArgs {
   float* dx0;             // [n][20]
   uint4* hcache;          // [C][n_warps][CACHE_CHUNKS] activation tiles + actions per step
   const float* dL;        // device scalar: upstream gradient of the loss
-  uint32_t* status;       // device status word (SIM_FLAG_TIMEOUT on a wait that gave up)
   float4* ckpt_a;         // [n_ckpt][n] previous action at each checkpoint (reward objective)
   float4* seg_a;          // [C][n] previous action of each segment step (reward objective)
   int n, H, C, R;
@@ -170,25 +146,6 @@ __device__ __forceinline__ float2 unpack2(uint32_t hi, uint32_t lo) {
   return make_float2(h.x + l.x, h.y + l.y);
 }
 
-// One drone's observation (13 values and the bias 1) as hi/lo into column `row`
-// of the canonical obs tile pair (rows 14, 15 stay 0).
-__device__ __forceinline__ void put_obs_kmaj(unsigned char* hi, unsigned char* lo, int row, const float* x,
-                                             const float r[3]) {
-  float o[14];
-  o[0] = x[0] - r[0];
-  o[1] = x[1] - r[1];
-  o[2] = x[2] - r[2];
-#pragma unroll
-  for (int j = 3; j < 13; ++j) o[j] = x[j];
-  o[13] = 1.f;
-#pragma unroll
-  for (int c = 0; c < 14; ++c) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(o[c]);
-    *reinterpret_cast<__nv_bfloat16*>(hi + kmaj(c, row)) = h;
-    *reinterpret_cast<__nv_bfloat16*>(lo + kmaj(c, row)) = __float2bfloat16_rn(o[c] - __bfloat162float(h));
-  }
-}
-
 // A fragments (hi, lo) of k-tile kk from accumulator fragments c[8][4]
 // (n-tiles 2kk, 2kk+1 form the 16 columns of k-tile kk).
 __device__ __forceinline__ void c_to_a(const float c[8][4], int kk, uint32_t ah[4], uint32_t al[4]) {
@@ -236,36 +193,6 @@ __device__ __forceinline__ void load_c64(__nv_bfloat16 (*t)[DPC * S64], int r0, 
 
 // ------------------------------------------------------------------ MLP
 
-// Accumulator fragments c[8][4] (drones r0 + g, r0 + g + 8; 64 columns) as hi/lo
-// bf16 into rows row0 + column of a canonical tile pair (one value per store).
-__device__ __forceinline__ void store_kmaj(unsigned char* hi, unsigned char* lo, int row0, int r0,
-                                           int lane, const float c[8][4]) {
-  const int g = lane >> 2, tq = lane & 3;
-#pragma unroll
-  for (int n = 0; n < 8; ++n)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int o = kmaj(row0 + 8 * n + 2 * tq + (e & 1), r0 + g + ((e >> 1) << 3));
-      const __nv_bfloat16 h = __float2bfloat16_rn(c[n][e]);
-      *reinterpret_cast<__nv_bfloat16*>(hi + o) = h;
-      *reinterpret_cast<__nv_bfloat16*>(lo + o) = __float2bfloat16_rn(c[n][e] - __bfloat162float(h));
-    }
-}
-
-// Reload hi + lo values of rows 0..63 of a canonical tile pair as fragments.
-__device__ __forceinline__ void load_kmaj(const unsigned char* hi, const unsigned char* lo, int r0,
-                                          int lane, float c[8][4]) {
-  const int g = lane >> 2, tq = lane & 3;
-#pragma unroll
-  for (int n = 0; n < 8; ++n)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int o = kmaj(8 * n + 2 * tq + (e & 1), r0 + g + ((e >> 1) << 3));
-      c[n][e] = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(hi + o)) +
-                __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(lo + o));
-    }
-}
-
 __device__ void load_weights(Smem& s, const uint16_t* __restrict__ w) {
   const __nv_bfloat16* wb = reinterpret_cast<const __nv_bfloat16*>(w);
   const __nv_bfloat16 z = __float2bfloat16(0.f);
@@ -291,21 +218,16 @@ __device__ void load_weights(Smem& s, const uint16_t* __restrict__ w) {
   for (int r = threadIdx.x; r < DPC; r += TPB) {
     for (int c = 64; c < S64; ++c) {
       for (int b = 0; b < 2; ++b) {
+        s.h1[b][0][r * S64 + c] = c == 64 ? one : z;
+        s.h1[b][1][r * S64 + c] = z;
         s.h2[b][0][r * S64 + c] = c == 64 ? one : z;
         s.h2[b][1][r * S64 + c] = z;
       }
+      s.dz1[0][r * S64 + c] = z;
+      s.dz1[1][r * S64 + c] = z;
+      s.dz2[0][r * S64 + c] = z;
+      s.dz2[1][r * S64 + c] = z;
     }
-    // constant rows of the canonical tiles (drone r = column K): bias rows 1, the rest 0
-    for (int b = 0; b < 3; ++b)
-      for (int row = 64; row < H1_ROWS; ++row) {
-        *reinterpret_cast<__nv_bfloat16*>(&s.H1[b][0][kmaj(row, r)]) = row == 64 ? one : z;
-        *reinterpret_cast<__nv_bfloat16*>(&s.H1[b][1][kmaj(row, r)]) = z;
-      }
-    for (int b = 0; b < 2; ++b)
-      for (int row = 13; row < OB_ROWS; ++row) {
-        *reinterpret_cast<__nv_bfloat16*>(&s.OB[b][0][kmaj(row, r)]) = row == 13 ? one : z;
-        *reinterpret_cast<__nv_bfloat16*>(&s.OB[b][1][kmaj(row, r)]) = z;
-      }
     for (int c = 0; c < S16; ++c) {
       s.obs[0][r * S16 + c] = z;
       s.obs[1][r * S16 + c] = z;
@@ -428,10 +350,9 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
 }
 
 // MLP backward for the warp's 16 drones, given dz3 rows in s.dz3 and the
-// forward activations (h1 in canonical buffer hb, h2 in buffer b).  Writes dz1, dz2 into the
-// tcgen05 A tile of step parity b and the
+// forward activations in buffer b of s.h1 / s.h2 (hi + lo).  Writes dz1, dz2 tiles and the
 // observation adjoint into s.dobs.
-__device__ void mlp_backward(Smem& s, int r0, int lane, int b, int hb) {
+__device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
   const int g = lane >> 2, tq = lane & 3;
   const int arow = r0 + (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
   // transposed B fragments: storage [k][n]
@@ -463,7 +384,7 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b, int hb) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) d[n][e] *= fmaf(-h[n][e], h[n][e], 1.f);
   }
-  store_kmaj(s.A[b][0], s.A[b][1], 0, r0, lane, d);  // dz2^T rows of the A tile
+  store_c64(s.dz2, r0, lane, d);
   // dh1[d][i] = sum_j dz2[d][j] W2[j][i]
   float e1[8][4];
 #pragma unroll
@@ -485,13 +406,13 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b, int hb) {
   // dz1 = dh1 (1 - h1^2)
   {
     float h[8][4];
-    load_kmaj(s.H1[hb][0], s.H1[hb][1], r0, lane, h);
+    load_c64(s.h1[b], r0, lane, h);
 #pragma unroll
     for (int n = 0; n < 8; ++n)
 #pragma unroll
       for (int e = 0; e < 4; ++e) e1[n][e] *= fmaf(-h[n][e], h[n][e], 1.f);
   }
-  store_kmaj(s.A[b][0], s.A[b][1], 64, r0, lane, e1);  // dz1^T rows of the A tile
+  store_c64(s.dz1, r0, lane, e1);
   // dobs[d][c] = sum_i dz1[d][i] W1[i][c]
   float o[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
@@ -518,96 +439,108 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b, int hb) {
 //   dW2 rows j in [16v, 16v+16) x columns 0..64 (64 = bias b2)
 //   dW1 rows i in [16v, 16v+16) x columns 0..15 (13 = bias b1)
 //   dW3 rows o in [0, 16) x columns j in [16v, 16v+16) (+ column 64 = b3 on warp 3)
-// dW3 (4 x 65) accumulation over the CTA's 64 drones on mma.sync: warp v holds
-// columns j in [16v, 16v+16) (+ column 64 = b3 on warp 3).
 struct DwAcc {
+  float w2[9][4];
+  float w1[2][4];
   float w3[3][4];
 };
 
-__device__ void accumulate_dw3(Smem& s, int v, int lane, DwAcc& acc, int hb) {
-  // A = dz3^T: A(row m, col d) = dz3[d][m], storage [d][m] -> transposed load
+__device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc, int hb) {
+  // A = dz^T: A(row m, col d) = dz[d][m], storage [d][m] -> transposed load
   const int arow = (lane & 7) + (lane >> 4) * 8, acol = ((lane >> 3) & 1) * 8;
-  // B(k = d, n) = h2[d][n], storage [d][n] -> transposed load
+  // B(k = d, n) = act[d][n], storage [d][n] -> transposed load
   const int brow = (lane & 7) + ((lane >> 3) & 1) * 8, bcol = (lane >> 4) * 8;
 #pragma unroll
   for (int kd = 0; kd < 4; ++kd) {
     const int d0 = 16 * kd;
     uint32_t ah[4], al[4];
+    // dW2
+    ldsm_x4_t(ah, &s.dz2[0][(d0 + arow) * S64 + 16 * v + acol]);
+    ldsm_x4_t(al, &s.dz2[1][(d0 + arow) * S64 + 16 * v + acol]);
+#pragma unroll
+    for (int n = 0; n < 8; n += 2) {
+      uint32_t bh[4], bl[4];
+      ldsm_x4_t(bh, &s.h1[hb][0][(d0 + brow) * S64 + 8 * n + bcol]);
+      ldsm_x4_t(bl, &s.h1[hb][1][(d0 + brow) * S64 + 8 * n + bcol]);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        mma(acc.w2[n + u], ah, bh[2 * u], bh[2 * u + 1]);
+        mma(acc.w2[n + u], ah, bl[2 * u], bl[2 * u + 1]);
+        mma(acc.w2[n + u], al, bh[2 * u], bh[2 * u + 1]);
+      }
+    }
+    {
+      uint32_t bh[2];
+      ldsm_x2_t(bh, &s.h1[hb][0][(d0 + brow) * S64 + 64]);
+      mma(acc.w2[8], ah, bh[0], bh[1]);
+      mma(acc.w2[8], al, bh[0], bh[1]);  // the bias column is exact (lo = 0)
+    }
+    // dW1
+    ldsm_x4_t(ah, &s.dz1[0][(d0 + arow) * S64 + 16 * v + acol]);
+    ldsm_x4_t(al, &s.dz1[1][(d0 + arow) * S64 + 16 * v + acol]);
+    {
+      uint32_t bh[4], bl[4];
+      ldsm_x4_t(bh, &s.obs[0][(d0 + brow) * S16 + bcol]);
+      ldsm_x4_t(bl, &s.obs[1][(d0 + brow) * S16 + bcol]);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        mma(acc.w1[u], ah, bh[2 * u], bh[2 * u + 1]);
+        mma(acc.w1[u], ah, bl[2 * u], bl[2 * u + 1]);
+        mma(acc.w1[u], al, bh[2 * u], bh[2 * u + 1]);
+      }
+    }
+    // dW3
     ldsm_x4_t(ah, &s.dz3[0][(d0 + arow) * S16 + acol]);
     ldsm_x4_t(al, &s.dz3[1][(d0 + arow) * S16 + acol]);
-    uint32_t bh[4], bl[4];
-    ldsm_x4_t(bh, &s.h2[hb][0][(d0 + brow) * S64 + 16 * v + bcol]);
-    ldsm_x4_t(bl, &s.h2[hb][1][(d0 + brow) * S64 + 16 * v + bcol]);
+    {
+      uint32_t bh[4], bl[4];
+      ldsm_x4_t(bh, &s.h2[hb][0][(d0 + brow) * S64 + 16 * v + bcol]);
+      ldsm_x4_t(bl, &s.h2[hb][1][(d0 + brow) * S64 + 16 * v + bcol]);
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      mma(acc.w3[u], ah, bh[2 * u], bh[2 * u + 1]);
-      mma(acc.w3[u], ah, bl[2 * u], bl[2 * u + 1]);
-      mma(acc.w3[u], al, bh[2 * u], bh[2 * u + 1]);
-    }
-    if (v == 3) {
-      uint32_t b1[2];
-      ldsm_x2_t(b1, &s.h2[hb][0][(d0 + brow) * S64 + 64]);
-      mma(acc.w3[2], ah, b1[0], b1[1]);
-      mma(acc.w3[2], al, b1[0], b1[1]);
+      for (int u = 0; u < 2; ++u) {
+        mma(acc.w3[u], ah, bh[2 * u], bh[2 * u + 1]);
+        mma(acc.w3[u], ah, bl[2 * u], bl[2 * u + 1]);
+        mma(acc.w3[u], al, bh[2 * u], bh[2 * u + 1]);
+      }
+      if (v == 3) {
+        uint32_t b1[2];
+        ldsm_x2_t(b1, &s.h2[hb][0][(d0 + brow) * S64 + 64]);
+        mma(acc.w3[2], ah, b1[0], b1[1]);
+        mma(acc.w3[2], al, b1[0], b1[1]);
+      }
     }
   }
 }
 
-__device__ void store_dw3(const DwAcc& acc, int v, int lane, float* __restrict__ part) {
+__device__ void store_dw(const DwAcc& acc, int v, int lane, float* __restrict__ part) {
   const int g = lane >> 2, tq = lane & 3;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    const int o = g + (e >= 2 ? 8 : 0), cc = 2 * tq + (e & 1);
-    if (o >= 4) continue;
+    const int rr = g + (e >= 2 ? 8 : 0), cc = 2 * tq + (e & 1);
+    // dW2 / db2
+#pragma unroll
+    for (int n = 0; n < 9; ++n) {
+      const int j = 16 * v + rr, i = 8 * n + cc;
+      if (i < 64) part[OFF_W2 + j * 64 + i] = acc.w2[n][e];
+      else if (i == 64) part[OFF_B2 + j] = acc.w2[n][e];
+    }
+    // dW1 / db1
+#pragma unroll
+    for (int n = 0; n < 2; ++n) {
+      const int i = 16 * v + rr, c = 8 * n + cc;
+      if (c < 13) part[OFF_W1 + i * 13 + c] = acc.w1[n][e];
+      else if (c == 13) part[OFF_B1 + i] = acc.w1[n][e];
+    }
+    // dW3 / db3
 #pragma unroll
     for (int n = 0; n < 3; ++n) {
       if (n == 2 && v != 3) continue;
-      const int j = (n < 2) ? 16 * v + 8 * n + cc : 64 + cc;
+      const int o = rr, j = (n < 2) ? 16 * v + 8 * n + cc : 64 + cc;
+      if (o >= 4) continue;
       if (j < 64) part[OFF_W3 + o * 64 + j] = acc.w3[n][e];
       else if (j == 64) part[OFF_B3 + o] = acc.w3[n][e];
     }
   }
-}
-
-// ------------------------------------------------------------------ tensor memory
-
-// Shared-memory descriptor of a canonical K-major tile without swizzle: start
-// address, leading (K-direction core matrix) stride 128 B, stride between 8-row
-// groups 1024 B, descriptor version 1 (bit 46).
-__device__ __forceinline__ uint64_t umma_desc(const void* p) {
-  const uint32_t a = smem_addr(p);
-  return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         (1ull << 46);
-}
-
-// Instruction descriptor of tcgen05.mma kind::f16: fp32 accumulator (bits 4-5),
-// bf16 A and B (bits 7-9, 10-12), both K-major, N / 8 at bit 17, M / 16 at bit 24.
-__host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void umma_commit(unsigned long long* mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-      smem_addr(mbar)));
-}
-
-// Wait (bounded: about a second) for the phase of the given parity; false if it
-// did not complete.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, uint32_t parity) {
-  uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it)
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_addr(mbar)), "r"(parity));
-  return done != 0;
 }
 
 // ------------------------------------------------------------------ dynamics
@@ -832,37 +765,13 @@ __device__ __forceinline__ void ref_at(const float* __restrict__ p_ref, int k, i
 
 // Shared-memory address of chunk c of warp rows r0..r0+15 in tile buffer b
 // (c < 4 TILE_CHUNKS: activation tiles, else action rows of act).
-__device__ __forceinline__ void* cache_smem(Smem& s, int hb, int b2, int r0, int c, float (*act)[4]) {
-  if (c < 2 * H1_CHUNKS) {  // h1: the warp's 16 drone columns, 256 contiguous bytes per 8-row group
-    const int q = c / H1_CHUNKS, w = c - q * H1_CHUNKS;
-    return s.H1[hb][q] + (w >> 4) * 1024 + (r0 >> 3) * 128 + (w & 15) * 16;
+__device__ __forceinline__ void* cache_smem(Smem& s, int b, int r0, int c, float (*act)[4]) {
+  const int q = c / TILE_CHUNKS, w = c - q * TILE_CHUNKS;
+  if (q < 4) {
+    __nv_bfloat16* t = (q < 2 ? s.h1[b][q] : s.h2[b][q - 2]) + r0 * S64;
+    return reinterpret_cast<uint4*>(t) + w;
   }
-  c -= 2 * H1_CHUNKS;
-  if (c < 2 * TILE_CHUNKS) {
-    const int q = c / TILE_CHUNKS, w = c - q * TILE_CHUNKS;
-    return reinterpret_cast<uint4*>(s.h2[b2][q] + r0 * S64) + w;
-  }
-  return act[r0 + c - 2 * TILE_CHUNKS];
-}
-
-// Weight-gradient MMAs of one reverse step (one thread): dW2 += dz2^T h1 and
-// dW1 += dz1^T obs over the CTA's 64 drones as hi*hi + hi*lo + lo*hi, K = 64 in
-// four K = 16 instructions each; completion is signalled on mbar[b].
-__device__ __forceinline__ void issue_dw_mma(Smem& s, uint32_t tmem, int b, int hb, bool first) {
-  constexpr uint32_t ID2 = umma_idesc(TC_M, H1_ROWS), ID1 = umma_idesc(TC_M, OB_ROWS);
-  asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-  for (int p = 0; p < 3; ++p) {
-    const int pa = p == 2 ? 1 : 0, pb = p == 1 ? 1 : 0;
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      const uint32_t acc = (first && p == 0 && kk == 0) ? 0u : 1u;
-      umma(tmem, umma_desc(s.A[b][pa] + 256 * kk), umma_desc(s.H1[hb][pb] + 256 * kk), ID2, acc);
-      umma(tmem + TMEM_DW1, umma_desc(s.A[b][pa] + 8192 + 256 * kk), umma_desc(s.OB[b][pb] + 256 * kk), ID1,
-           acc);
-    }
-  }
-  umma_commit(&s.mbar[b]);
+  return act[r0 + w];
 }
 
 // ------------------------------------------------------------------ objectives
@@ -973,38 +882,18 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   load_weights(s, a.w);
-  const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
-  // tensor memory for the dW1 / dW2 accumulators and the MMA completion barriers
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s.mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s.mbar[1])));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  if (v == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_addr(&s.tmem_base)),
-                 "r"(TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  asm volatile("fence.proxy.async.shared::cta;");  // constant rows of the operand tiles
-  asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = s.tmem_base;
-  int ncommit[2] = {0, 0};  // commits issued per step parity (uniform across the CTA)
-  bool first_mma = true, timed_out = false;
-  // wait for the latest MMAs of both parities (before tiles are reused wholesale)
-  auto drain = [&]() {
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-      if (ncommit[q] > 0 && !mbar_wait(&s.mbar[q], (uint32_t)((ncommit[q] - 1) & 1))) timed_out = true;
-  };
+  const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
   const int r0 = 16 * v, row = r0 + (lane & 15);
   const int i = blockIdx.x * DPC + row;
   const bool valid = i < a.n;
   const int ii = valid ? i : a.n - 1;
   const float seed = valid ? (*a.dL) * a.inv_n : 0.f;  // padded rows contribute nothing
   DwAcc acc;
+#pragma unroll
+  for (int n = 0; n < 9; ++n) acc.w2[n][0] = acc.w2[n][1] = acc.w2[n][2] = acc.w2[n][3] = 0.f;
+#pragma unroll
+  for (int n = 0; n < 2; ++n) acc.w1[n][0] = acc.w1[n][1] = acc.w1[n][2] = acc.w1[n][3] = 0.f;
 #pragma unroll
   for (int n = 0; n < 3; ++n) acc.w3[n][0] = acc.w3[n][1] = acc.w3[n][2] = acc.w3[n][3] = 0.f;
   float lam[17];
@@ -1037,15 +926,15 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
       {
         float h1[8][4], h2[8][4];
         mlp_forward(s, r0, lane, h1, h2);
-        // keep this step's activations for the reverse sweep (staged in buffer 0)
-        store_kmaj(s.H1[0][0], s.H1[0][1], 0, r0, lane, h1);
+        // keep this step's activations for the reverse sweep (tiles staged in buffer 0)
+        store_c64(s.h1[0], r0, lane, h1);
         store_c64(s.h2[0], r0, lane, h2);
       }
       __syncwarp();
       {
         uint4* dst = a.hcache + ((size_t)(k - k0) * gridDim.x * 4 + blockIdx.x * 4 + v) * CACHE_CHUNKS;
         for (int c = lane; c < CACHE_CHUNKS; c += 32)
-          dst[c] = *reinterpret_cast<const uint4*>(cache_smem(s, 0, 0, r0, c, s.act));
+          dst[c] = *reinterpret_cast<const uint4*>(cache_smem(s, 0, r0, c, s.act));
       }
       float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
       __syncwarp();
@@ -1074,13 +963,11 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
         cp_async16(&s.pre_a[k & 1][row], valid ? &a.seg_a[(size_t)(k - k0) * a.n + i]
                                                : &a.ckpt_a[(size_t)sg * a.n + ii]);
     };
-    // step k's activation tiles and actions, copied back from the cache (h1 into
-    // canonical buffer k % 3, h2 and actions into buffer k & 1; each lane reads
-    // back the chunks it wrote)
+    // step k's activation tiles and actions, copied back from the cache into
+    // buffer k & 1 (each lane reads back the chunks it wrote)
     auto prefetch_tiles = [&](int k) {
       const uint4* src = a.hcache + ((size_t)(k - k0) * gridDim.x * 4 + blockIdx.x * 4 + v) * CACHE_CHUNKS;
-      for (int c = lane; c < CACHE_CHUNKS; c += 32)
-        cp_async16(cache_smem(s, k % 3, k & 1, r0, c, s.actb[k & 1]), src + c);
+      for (int c = lane; c < CACHE_CHUNKS; c += 32) cp_async16(cache_smem(s, k & 1, r0, c, s.actb[k & 1]), src + c);
     };
     __threadfence_block();  // this thread's segment rows precede its async copies of them
     if (lane < 16) prefetch_step(k1 - 1);
@@ -1088,9 +975,8 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
     cp_async_commit();
     for (int k = k1 - 1; k >= k0; --k) {
       cp_async_wait_all();
-      asm volatile("fence.proxy.async.shared::cta;");  // copied h1 tile -> tensor cores
       __syncwarp();
-      const int b = k & 1, hb = k % 3;
+      const int b = k & 1;
 #pragma unroll
       for (int j = 0; j < 17; ++j) x[j] = s.pre_x[b][row][j];
       const float r[3] = {s.pre_r[b][row][0], s.pre_r[b][row][1], s.pre_r[b][row][2]};
@@ -1102,15 +988,12 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
         ap[2] = t.z;
         ap[3] = t.w;
       }
-      // the A and obs tiles of parity b and h1 buffer (k - 1) % 3 were last read
-      // by the MMAs of step k + 2
-      if (ncommit[b] > 0 && !mbar_wait(&s.mbar[b], (uint32_t)((ncommit[b] - 1) & 1))) timed_out = true;
       if (k > k0) {
         if (lane < 16) prefetch_step(k - 1);
         prefetch_tiles(k - 1);
       }
       cp_async_commit();
-      if (lane < 16) put_obs_kmaj(s.OB[b][0], s.OB[b][1], row, x, r);
+      if (lane < 16) put_obs(s, row, x, r);
       __syncwarp();
       const float act[4] = {s.actb[b][row][0], s.actb[b][row][1], s.actb[b][row][2], s.actb[b][row][3]};
       // loss term at policy step k + 1 (state after the last sub-step)
@@ -1161,22 +1044,17 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
         }
       }
       __syncwarp();
-      mlp_backward(s, r0, lane, b, hb);
+      mlp_backward(s, r0, lane, b);
       __syncwarp();
       // observation adjoint: obs = [p - r, q, v, w]
 #pragma unroll
       for (int j = 0; j < 13; ++j) lam[j] += s.dobs[row][j];
 #pragma unroll
       for (int j = 0; j < 17; ++j) xn[j] = x[j];
-      asm volatile("fence.proxy.async.shared::cta;");  // A and obs tiles -> tensor cores
       __syncthreads();  // every warp's tiles for this step are in shared memory
-      if (threadIdx.x == 0) issue_dw_mma(s, tmem, b, hb, first_mma);
-      ++ncommit[b];
-      first_mma = false;
-      accumulate_dw3(s, v, lane, acc, b);
+      accumulate_dw(s, v, lane, acc, b);
       __syncthreads();  // before the next step overwrites the tiles
     }
-    drain();  // the next segment's recompute rewrites the staging tiles
   }
   if (valid && lane < 16) {
     float4* p = reinterpret_cast<float4*>(a.dx0 + (size_t)i * 20);
@@ -1184,52 +1062,7 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
     for (int j = 0; j < 4; ++j) p[j] = make_float4(lam[4 * j], lam[4 * j + 1], lam[4 * j + 2], lam[4 * j + 3]);
     p[4] = make_float4(lam[16], 0.f, 0.f, 0.f);
   }
-  float* part = a.part + (size_t)blockIdx.x * NPOL_PAD;
-  store_dw3(acc, v, lane, part);
-  // dW2 (rows j, columns i and the bias column 64) and dW1 (rows i, columns c and
-  // the bias column 13) from tensor memory: warps 0 and 1 own lanes 0..63
-  const bool ok = __syncthreads_and(!timed_out) != 0;
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (ok && v < 2) {
-    const int m = 32 * v + lane;
-    const uint32_t base = tmem + ((uint32_t)(32 * v) << 16);
-#pragma unroll
-    for (int c0 = 0; c0 < 72; c0 += 8) {
-      uint32_t r[8];
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                   : "r"(base + c0));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int col = c0 + e;
-        if (col < 64) part[OFF_W2 + m * 64 + col] = __uint_as_float(r[e]);
-        else if (col == 64) part[OFF_B2 + m] = __uint_as_float(r[e]);
-      }
-    }
-#pragma unroll
-    for (int c0 = 0; c0 < 16; c0 += 8) {
-      uint32_t r[8];
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                   : "r"(base + TMEM_DW1 + c0));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int col = c0 + e;
-        if (col < 13) part[OFF_W1 + m * 13 + col] = __uint_as_float(r[e]);
-        else if (col == 13) part[OFF_B1 + m] = __uint_as_float(r[e]);
-      }
-    }
-  }
-  if (!ok) {
-    if (threadIdx.x == 0 && a.status) atomicOr(a.status, SIM_FLAG_TIMEOUT);
-    drain();  // give MMAs still in flight a second bounded wait before the release
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  if (v == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  store_dw(acc, v, lane, a.part + (size_t)blockIdx.x * NPOL_PAD);
 }
 
 // Deterministic reductions: dW[p] = sum over CTAs (fixed order, fp64);
@@ -1365,10 +1198,9 @@ cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* 
 cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
                                int C, int R, float dt, float w_act, const RolloutObjective& obj,
                                const DevParams& P, void* ws, const float* dL, float* dW, float* dx0,
-                               uint32_t* status, cudaStream_t st) {
+                               cudaStream_t st) {
   ro::RolloutArgs a{};
   carve(ws, n, H, C, R, obj, a);
-  a.status = status;
   a.x0 = x0;
   a.w = w;
   a.p_ref = p_ref;

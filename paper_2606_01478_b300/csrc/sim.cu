@@ -100,6 +100,15 @@ Layout layout_of(const sim_s* h, int64_t max_blocks) {
   return L;
 }
 
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 // Where kernels can reach a caller's buffer: itself for device memory, its device
 // address for pinned host memory (kernels then move the data over the host link
 // themselves), nullptr for pageable host memory (copy-engine transfers).
@@ -727,7 +736,7 @@ int sim_rollout_bwd(sim_h h, const float* x0, const uint16_t* w, const float* p_
   if (r != SIM_OK) return r;
   cudaError_t e = cf::launch_rollout_bwd(x0, w, p_ref, (int)h->ntot, H, C, h->rollout_repeat, h->dt,
                                          w_act, h->objective,
-                                         h->p0, ws, dL, dW, dx0, h->status, (cudaStream_t)stream);
+                                         h->p0, ws, dL, dW, dx0, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "rollout backward launch");
   h->launches += 2;
   return SIM_OK;
