@@ -100,15 +100,6 @@ Layout layout_of(const sim_s* h, int64_t max_blocks) {
   return L;
 }
 
-bool is_device_pointer(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 // Where kernels can reach a caller's buffer: itself for device memory, its device
 // address for pinned host memory (kernels then move the data over the host link
 // themselves), nullptr for pageable host memory (copy-engine transfers).
