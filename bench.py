@@ -189,6 +189,27 @@ def cpu_baseline(wl, budget_s: float = 12.0) -> dict:
             "sample": f"{wl.M} drones x {steps} of {wl.steps} steps (FP64 torch CPU oracle)"}
 
 
+STATE_FIELDS = {"p_m": slice(0, 3), "q": slice(3, 7), "v_m_s": slice(7, 10), "w_rad_s": slice(10, 13),
+                "W_rpm": slice(13, 17)}
+
+
+def error_vs_fp64(wl, gpu_final: np.ndarray, n_drones: int = 256) -> dict:
+    """Final-state error of the GPU rollout against the FP64 oracle on evenly
+    spaced drones (whole rollouts from the float32 inputs the GPU received),
+    max and median absolute error per state field (part of the CPU-baseline leg)."""
+    import dataclasses
+    from oracle import physics as ph
+    idx = np.linspace(0, wl.M * wl.N - 1, n_drones).round().astype(np.int64)
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    wl32 = dataclasses.replace(wl, x0=f32(wl.x0), cmd=f32(wl.cmd))
+    ref = ph.rollout_workload(wl32, drones=idx).numpy()
+    err = np.abs(np.asarray(gpu_final, np.float64)[idx] - ref)
+    return {"drones": int(n_drones), "steps": int(wl.steps),
+            "max_abs": {k: float(err[:, sl].max()) for k, sl in STATE_FIELDS.items()},
+            "median_abs": {k: float(np.median(err[:, sl])) for k, sl in STATE_FIELDS.items()},
+            "reference": "FP64 oracle from the same float32 inputs"}
+
+
 def run_reference(args, wl):
     dist, rank, ws = _dist()
     if rank != 0:
@@ -369,6 +390,7 @@ def run_b300(args, wl):
                          "bptt_training": measure_bptt_training(dev), "depth": measure_depth(dev)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
+        line["error_vs_fp64"] = error_vs_fp64(wl, out_host.numpy())
     print(json.dumps(line), flush=True)
     return 0
 
@@ -475,6 +497,11 @@ def measure_config3(dev, reps: int = 3) -> dict:
     loss = torch.empty(1, device=dev)
     ms_fwd = _time_ms(lambda: runner.forward(x0, wb, p_ref, loss=loss), reps, dev)
     ms_grad = _time_ms(lambda: runner.grad(x0, wb, p_ref), reps, dev)
+    # the plain-bf16 operand mode (precision for speed; its gradient error against
+    # FP64 is measured by the tests)
+    runner16 = PolicyRollout(sim, rw.H, rw.C, rw.w_act, precision="bf16")
+    ms_fwd16 = _time_ms(lambda: runner16.forward(x0, wb, p_ref, loss=loss), reps, dev)
+    ms_grad16 = _time_ms(lambda: runner16.grad(x0, wb, p_ref), reps, dev)
     # plain forward stepping of the same drones (attitude interface, hover commands)
     sim.set_state(x0)
     sim.set_commands(torch.zeros(1, rw.M, 4, device=dev), rw.H)
@@ -490,6 +517,8 @@ def measure_config3(dev, reps: int = 3) -> dict:
         "fwd": {"value": units / (ms_fwd / 1e3), "unit": UNIT, "ms": ms_fwd},
         "fwd_adjoint": {"value": units / (ms_grad / 1e3), "unit": UNIT, "ms": ms_grad,
                         "gradients_per_s": rw.M / (ms_grad / 1e3)},
+        "bf16_operands": {"fwd_ms": ms_fwd16, "fwd_adjoint_ms": ms_grad16,
+                          "fwd_adjoint_value": units / (ms_grad16 / 1e3), "unit": UNIT},
         "plain_forward_stepping": {"value": units / (ms_plain / 1e3), "unit": UNIT, "ms": ms_plain},
         "adjoint_over_plain": ms_grad / ms_plain,
         "roofline_fwd_adjoint": {"bound": "tensor", "achieved": grad_flop / (ms_grad / 1e3) / 1e12,

@@ -348,6 +348,17 @@ typedef struct sim_objective {
  * NULL restores SIM_OBJ_SQUARED).  SIM_EINVAL for an unknown kind or a weight
  * that is negative or not finite. */
 int sim_rollout_set_objective(sim_h h, const sim_objective* obj);
+/* Tensor-core operand precision of the policy MLP in every later rollout call
+ * on the handle (host-side setting).  SIM_MLP_HILO (default): activations and
+ * adjoints enter the MMAs as hi + lo bf16 pairs (~2^-16 relative; weight
+ * gradients as hi*hi + hi*lo + lo*hi), within the 1e-3 gradient bar against
+ * FP64.  SIM_MLP_BF16: plain bf16 operands (~2^-8 relative; half the forward
+ * and input-adjoint MMAs, a third of the weight-gradient ones), the paper's
+ * "BF16 weights, FP32 accumulate" policy taken literally.  Weights are bf16
+ * values in both; accumulation is fp32.  SIM_EINVAL for another mode. */
+#define SIM_MLP_HILO 0
+#define SIM_MLP_BF16 1
+int sim_rollout_set_precision(sim_h h, int mode);
 /* Physics steps per policy action (R) of every later rollout call on the
  * handle (host-side setting; default 1).  H and C count policy steps, p_ref
  * holds the reference at policy steps, and the loss is evaluated after every

@@ -46,6 +46,7 @@ class Objective(ctypes.Structure):
 
 
 OBJ_SQUARED, OBJ_TRACKING_REWARD = 0, 1
+MLP_HILO, MLP_BF16 = 0, 1
 
 
 class MppiConfig(ctypes.Structure):
@@ -88,6 +89,7 @@ _SIGS = {
                              c_void_p]),
     "sim_rollout_set_objective": (c_int, [c_void_p, POINTER(Objective)]),
     "sim_rollout_set_action_repeat": (c_int, [c_void_p, c_int]),
+    "sim_rollout_set_precision": (c_int, [c_void_p, c_int]),
     "sim_rollout_workspace_bytes": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),
     "sim_rollout_fwd": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_float,
                                 c_void_p, c_size_t, c_void_p, c_void_p]),

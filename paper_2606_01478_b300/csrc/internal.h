@@ -24,6 +24,7 @@ constexpr int POLICY_NPARAMS = 5316;
 // Objective of the policy rollout (SIM_OBJ_*) with the tracking-reward weights.
 struct RolloutObjective {
   int kind = SIM_OBJ_SQUARED;
+  bool hilo = true;  // MLP operands as hi + lo bf16 pairs (SIM_MLP_HILO) or plain bf16
   float w_theta = 0.f, w_act[4] = {0.f, 0.f, 0.f, 0.f}, w_dact[4] = {0.f, 0.f, 0.f, 0.f};
 };
 size_t rollout_workspace_bytes(int n, int H, int C, int objective, int R);

@@ -22,8 +22,10 @@
 // CTA (one m16 MMA tile; lane l handles drone l & 15 of the tile for the
 // per-drone dynamics, lanes 16..31 duplicate lanes 0..15).  The MLP runs on
 // tensor cores with mma.sync m16n8k16 (bf16 inputs, fp32 accumulate).  Weights
-// are bf16 values; activations and adjoints enter the MMAs as hi + lo bf16
-// pairs (2 MMAs, ~2^-16 relative), dW products as hi*hi + hi*lo + lo*hi.
+// are bf16 values; by default (LO) activations and adjoints enter the MMAs as
+// hi + lo bf16 pairs (2 MMAs, ~2^-16 relative), dW products as hi*hi + hi*lo +
+// lo*hi; without LO only the hi parts are multiplied (plain bf16 operands,
+// ~2^-8 relative), the precision-for-speed variant.
 // The accumulator fragment of one layer is the A fragment of the next, so
 // activations stay in registers between layers.
 #include <cuda_bf16.h>
@@ -271,6 +273,7 @@ __device__ __forceinline__ float tanh_fast(float x) {
 
 // MLP forward for the warp's 16 drones (rows r0..r0+15).  Returns h1, h2
 // (fp32 accumulator fragments, after tanh) and writes the actions to s.act.
+template <bool LO>
 __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[8][4]) {
   const int g = lane >> 2, tq = lane & 3;
   const int arow = r0 + (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
@@ -292,7 +295,7 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
       c[2] = b0;
       c[3] = b1v;
       mma(c, oh, b[2 * u], b[2 * u + 1]);
-      mma(c, ol, b[2 * u], b[2 * u + 1]);
+      if constexpr (LO) mma(c, ol, b[2 * u], b[2 * u + 1]);
     }
   }
 #pragma unroll
@@ -317,9 +320,9 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
       uint32_t b[4];
       ldsm_x4(b, &s.W2[(8 * n + brow) * S64 + 16 * kk + bcol]);
       mma(h2[n], ah, b[0], b[1]);
-      mma(h2[n], al, b[0], b[1]);
+      if constexpr (LO) mma(h2[n], al, b[0], b[1]);
       mma(h2[n + 1], ah, b[2], b[3]);
-      mma(h2[n + 1], al, b[2], b[3]);
+      if constexpr (LO) mma(h2[n + 1], al, b[2], b[3]);
     }
   }
 #pragma unroll
@@ -339,7 +342,7 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
     uint32_t b[2];
     ldsm_x2(b, &s.W3[(lane & 7) * S64 + 16 * kk + bcol]);
     mma(z3, ah, b[0], b[1]);
-    mma(z3, al, b[0], b[1]);
+    if constexpr (LO) mma(z3, al, b[0], b[1]);
   }
   if (tq < 2) {
     s.act[r0 + g][2 * tq] = tanh_fast(z3[0]);
@@ -352,6 +355,7 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
 // MLP backward for the warp's 16 drones, given dz3 rows in s.dz3 and the
 // forward activations in buffer b of s.h1 / s.h2 (hi + lo).  Writes dz1, dz2 tiles and the
 // observation adjoint into s.dobs.
+template <bool LO>
 __device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
   const int g = lane >> 2, tq = lane & 3;
   const int arow = r0 + (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
@@ -371,7 +375,7 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
       for (int u = 0; u < 2; ++u) {
         d[n + u][0] = d[n + u][1] = d[n + u][2] = d[n + u][3] = 0.f;
         mma(d[n + u], ah, b[2 * u], b[2 * u + 1]);
-        mma(d[n + u], al, b[2 * u], b[2 * u + 1]);
+        if constexpr (LO) mma(d[n + u], al, b[2 * u], b[2 * u + 1]);
       }
     }
   }
@@ -398,9 +402,9 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
       uint32_t b[4];
       ldsm_x4_t(b, &s.W2[(16 * kk + trow) * S64 + 8 * n + tcol]);
       mma(e1[n], ah, b[0], b[1]);
-      mma(e1[n], al, b[0], b[1]);
+      if constexpr (LO) mma(e1[n], al, b[0], b[1]);
       mma(e1[n + 1], ah, b[2], b[3]);
-      mma(e1[n + 1], al, b[2], b[3]);
+      if constexpr (LO) mma(e1[n + 1], al, b[2], b[3]);
     }
   }
   // dz1 = dh1 (1 - h1^2)
@@ -422,9 +426,9 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
     uint32_t b[4];
     ldsm_x4_t(b, &s.W1[(16 * kk + trow) * S16 + tcol]);
     mma(o[0], ah, b[0], b[1]);
-    mma(o[0], al, b[0], b[1]);
+    if constexpr (LO) mma(o[0], al, b[0], b[1]);
     mma(o[1], ah, b[2], b[3]);
-    mma(o[1], al, b[2], b[3]);
+    if constexpr (LO) mma(o[1], al, b[2], b[3]);
   }
 #pragma unroll
   for (int n = 0; n < 2; ++n) {
@@ -445,6 +449,7 @@ struct DwAcc {
   float w3[3][4];
 };
 
+template <bool LO>
 __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc, int hb) {
   // A = dz^T: A(row m, col d) = dz[d][m], storage [d][m] -> transposed load
   const int arow = (lane & 7) + (lane >> 4) * 8, acol = ((lane >> 3) & 1) * 8;
@@ -465,15 +470,15 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc, int hb) {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         mma(acc.w2[n + u], ah, bh[2 * u], bh[2 * u + 1]);
-        mma(acc.w2[n + u], ah, bl[2 * u], bl[2 * u + 1]);
-        mma(acc.w2[n + u], al, bh[2 * u], bh[2 * u + 1]);
+        if constexpr (LO) mma(acc.w2[n + u], ah, bl[2 * u], bl[2 * u + 1]);
+        if constexpr (LO) mma(acc.w2[n + u], al, bh[2 * u], bh[2 * u + 1]);
       }
     }
     {
       uint32_t bh[2];
       ldsm_x2_t(bh, &s.h1[hb][0][(d0 + brow) * S64 + 64]);
       mma(acc.w2[8], ah, bh[0], bh[1]);
-      mma(acc.w2[8], al, bh[0], bh[1]);  // the bias column is exact (lo = 0)
+      if constexpr (LO) mma(acc.w2[8], al, bh[0], bh[1]);  // the bias column is exact (lo = 0)
     }
     // dW1
     ldsm_x4_t(ah, &s.dz1[0][(d0 + arow) * S64 + 16 * v + acol]);
@@ -485,8 +490,8 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc, int hb) {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         mma(acc.w1[u], ah, bh[2 * u], bh[2 * u + 1]);
-        mma(acc.w1[u], ah, bl[2 * u], bl[2 * u + 1]);
-        mma(acc.w1[u], al, bh[2 * u], bh[2 * u + 1]);
+        if constexpr (LO) mma(acc.w1[u], ah, bl[2 * u], bl[2 * u + 1]);
+        if constexpr (LO) mma(acc.w1[u], al, bh[2 * u], bh[2 * u + 1]);
       }
     }
     // dW3
@@ -499,14 +504,14 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc, int hb) {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         mma(acc.w3[u], ah, bh[2 * u], bh[2 * u + 1]);
-        mma(acc.w3[u], ah, bl[2 * u], bl[2 * u + 1]);
-        mma(acc.w3[u], al, bh[2 * u], bh[2 * u + 1]);
+        if constexpr (LO) mma(acc.w3[u], ah, bl[2 * u], bl[2 * u + 1]);
+        if constexpr (LO) mma(acc.w3[u], al, bh[2 * u], bh[2 * u + 1]);
       }
       if (v == 3) {
         uint32_t b1[2];
         ldsm_x2_t(b1, &s.h2[hb][0][(d0 + brow) * S64 + 64]);
         mma(acc.w3[2], ah, b1[0], b1[1]);
-        mma(acc.w3[2], al, b1[0], b1[1]);
+        if constexpr (LO) mma(acc.w3[2], al, b1[0], b1[1]);
       }
     }
   }
@@ -834,7 +839,7 @@ __device__ __forceinline__ void step_loss_state_adjoint(const float* xn, const f
 
 // ------------------------------------------------------------------ kernels
 
-template <int OBJ>
+template <int OBJ, bool LO>
 __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
@@ -863,7 +868,7 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
     if (lane < 16) put_obs(s, row, x, r);
     __syncwarp();
     float h1[8][4], h2[8][4];
-    mlp_forward(s, r0, lane, h1, h2);
+    mlp_forward<LO>(s, r0, lane, h1, h2);
     __syncwarp();
     float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
     __syncwarp();
@@ -877,7 +882,7 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
   if (valid && lane < 16) a.loss_w[i] = loss;
 }
 
-template <int OBJ>
+template <int OBJ, bool LO>
 __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
@@ -925,7 +930,7 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
       __syncwarp();
       {
         float h1[8][4], h2[8][4];
-        mlp_forward(s, r0, lane, h1, h2);
+        mlp_forward<LO>(s, r0, lane, h1, h2);
         // keep this step's activations for the reverse sweep (tiles staged in buffer 0)
         store_c64(s.h1[0], r0, lane, h1);
         store_c64(s.h2[0], r0, lane, h2);
@@ -1044,7 +1049,7 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
         }
       }
       __syncwarp();
-      mlp_backward(s, r0, lane, b);
+      mlp_backward<LO>(s, r0, lane, b);
       __syncwarp();
       // observation adjoint: obs = [p - r, q, v, w]
 #pragma unroll
@@ -1052,7 +1057,7 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
 #pragma unroll
       for (int j = 0; j < 17; ++j) xn[j] = x[j];
       __syncthreads();  // every warp's tiles for this step are in shared memory
-      accumulate_dw(s, v, lane, acc, b);
+      accumulate_dw<LO>(s, v, lane, acc, b);
       __syncthreads();  // before the next step overwrites the tiles
     }
   }
@@ -1188,8 +1193,10 @@ cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* 
   a.store_ckpt = store_ckpt ? 1 : 0;
   const int grid = (n + ro::DPC - 1) / ro::DPC;
   cudaError_t e = obj.kind == SIM_OBJ_TRACKING_REWARD
-                      ? launch_rollout_kernel(ro::rollout_fwd_kernel<SIM_OBJ_TRACKING_REWARD>, grid, a, P, st)
-                      : launch_rollout_kernel(ro::rollout_fwd_kernel<SIM_OBJ_SQUARED>, grid, a, P, st);
+                      ? (obj.hilo ? launch_rollout_kernel(ro::rollout_fwd_kernel<SIM_OBJ_TRACKING_REWARD, true>, grid, a, P, st)
+                                  : launch_rollout_kernel(ro::rollout_fwd_kernel<SIM_OBJ_TRACKING_REWARD, false>, grid, a, P, st))
+                      : (obj.hilo ? launch_rollout_kernel(ro::rollout_fwd_kernel<SIM_OBJ_SQUARED, true>, grid, a, P, st)
+                                  : launch_rollout_kernel(ro::rollout_fwd_kernel<SIM_OBJ_SQUARED, false>, grid, a, P, st));
   if (e != cudaSuccess) return e;
   ro::reduce_loss_kernel<<<1, 256, 0, st>>>(a.loss_w, n, loss);
   return cudaGetLastError();
@@ -1214,8 +1221,10 @@ cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* 
   a.inv_n = 1.f / (float)n;
   const int grid = (n + ro::DPC - 1) / ro::DPC;
   cudaError_t e = obj.kind == SIM_OBJ_TRACKING_REWARD
-                      ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_TRACKING_REWARD>, grid, a, P, st)
-                      : launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED>, grid, a, P, st);
+                      ? (obj.hilo ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_TRACKING_REWARD, true>, grid, a, P, st)
+                                  : launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_TRACKING_REWARD, false>, grid, a, P, st))
+                      : (obj.hilo ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED, true>, grid, a, P, st)
+                                  : launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED, false>, grid, a, P, st));
   if (e != cudaSuccess) return e;
   ro::reduce_dw_kernel<<<(ro::NPOL + 255) / 256, 256, 0, st>>>(a.part, grid, dW);
   return cudaGetLastError();

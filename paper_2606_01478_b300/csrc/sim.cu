@@ -687,7 +687,15 @@ int sim_rollout_set_objective(sim_h h, const sim_objective* obj) {
       o.w_dact[i] = obj->w_dact[i];
     }
   }
+  o.hilo = h->objective.hilo;  // the precision is a separate setting
   h->objective = o;
+  return SIM_OK;
+}
+
+int sim_rollout_set_precision(sim_h h, int mode) {
+  if (!h) return SIM_EINVAL;
+  if (mode != SIM_MLP_HILO && mode != SIM_MLP_BF16) return fail(h, SIM_EINVAL, "unknown MLP precision %d", mode);
+  h->objective.hilo = mode == SIM_MLP_HILO;
   return SIM_OK;
 }
 

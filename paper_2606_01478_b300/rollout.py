@@ -3,7 +3,8 @@
 ``PolicyRollout(sim, H, C, w_act, reward=None, action_repeat=1)`` owns the
 rollout workspace; ``action_repeat`` = R holds each policy action for R physics
 steps (H and C count policy steps);
-``reward`` selects the paper's tracking reward (weights as in
+``precision`` = "hilo" (default) or "bf16" picks the MLP's tensor-core operand
+precision (sim_rollout_set_precision); ``reward`` selects the paper's tracking reward (weights as in
 ``TRACKING_REWARD``) instead of the squared tracking loss;
 ``rollout_loss(x0, w, runner, p_ref)`` is a torch.autograd.Function whose
 forward and backward are the library's CUDA kernels (the upstream gradient
@@ -49,9 +50,12 @@ def _p(t: torch.Tensor) -> ctypes.c_void_p:
 
 class PolicyRollout:
     def __init__(self, sim, H: int, C: int, w_act: float = 1e-3, reward: dict | None = None,
-                 action_repeat: int = 1):
+                 action_repeat: int = 1, precision: str = "hilo"):
         self.sim, self.H, self.C, self.w_act = sim, int(H), int(C), float(w_act)
         self.repeat = int(action_repeat)
+        if precision not in ("hilo", "bf16"):
+            raise ValueError("precision must be 'hilo' or 'bf16'")
+        self.precision = L.MLP_HILO if precision == "hilo" else L.MLP_BF16
         self.objective = L.Objective()
         if reward is not None:
             self.objective.kind = L.OBJ_TRACKING_REWARD
@@ -70,6 +74,7 @@ class PolicyRollout:
         every call so that runners sharing one handle do not see each other's."""
         self.sim._check(self.sim.lib.sim_rollout_set_objective(self.sim.h, ctypes.byref(self.objective)))
         self.sim._check(self.sim.lib.sim_rollout_set_action_repeat(self.sim.h, self.repeat))
+        self.sim._check(self.sim.lib.sim_rollout_set_precision(self.sim.h, self.precision))
 
     def _check_inputs(self, x0, w_bf16, p_ref):
         self._apply_objective()

@@ -157,3 +157,11 @@ def test_run_host_validates_before_any_cuda_call(lib):
     assert lib.sim_run_host(h, buf, buf, 1, 1, 10, 5, buf, None) == L.SIM_ESTATE
     assert b"bind" in lib.sim_last_error(h)
     lib.sim_destroy(h)
+
+
+def test_rollout_precision_validation(lib):
+    r, h = _create(lib, 16, 1)
+    assert lib.sim_rollout_set_precision(h, 2) == L.SIM_EINVAL
+    assert lib.sim_rollout_set_precision(h, L.MLP_BF16) == L.SIM_OK
+    assert lib.sim_rollout_set_precision(h, L.MLP_HILO) == L.SIM_OK
+    lib.sim_destroy(h)

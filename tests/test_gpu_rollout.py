@@ -202,3 +202,30 @@ def test_held_action_gradient(reward):
         loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
         assert torch.isfinite(dW).all()
         _check(rw, loss.item(), dW.cpu().numpy(), dx0.cpu().numpy().astype(np.float64), reward=reward)
+
+
+def test_plain_bf16_operands_mode():
+    """SIM_MLP_BF16 (plain bf16 tensor-core operands) at the config-3 horizon
+    (H = 250, C = 25, 256 drones): gradients against the FP64 oracle within
+    1e-2 norm-wise relative (a regression bound; the measured errors are
+    printed), and measurably less accurate than the default hi + lo split, so
+    the mode really changes the arithmetic."""
+    rw = W.config3(seed=41, M=256, H=250, C=25)
+    x0, p_ref = _as_oracle_inputs(rw)
+    L_ref, _, dW_ref, dx_ref = po.rollout_grad(x0, rw.weights, p_ref, rw.params, rw.dt, rw.H, rw.w_act)
+    errs = {}
+    for prec in ("hilo", "bf16"):
+        sim = Sim(rw.M, 1, FIRST_PRINCIPLES, EULER, rw.dt)
+        sim.set_params(rw.params)
+        runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act, precision=prec)
+        xg = torch.tensor(rw.x0, dtype=torch.float32, device="cuda")
+        w = torch.tensor(po.pack(rw.weights), dtype=torch.float32, device="cuda").to(torch.bfloat16)
+        pg = torch.tensor(rw.p_ref, dtype=torch.float32, device="cuda").contiguous()
+        loss, dW, dx0 = runner.grad(xg, w, pg)
+        g = po.pack(dW_ref)
+        errs[prec] = (abs(loss.item() - L_ref) / abs(L_ref),
+                      _rel(dW.cpu().numpy(), g), _rel(dx0.cpu().numpy(), dx_ref))
+    print("relative errors (loss, dW, dx0):", errs)
+    assert max(errs["hilo"]) <= TOL
+    assert max(errs["bf16"]) <= 1e-2
+    assert errs["bf16"][1] > errs["hilo"][1]
