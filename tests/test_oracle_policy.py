@@ -248,3 +248,25 @@ def test_held_policy_gradient_matches_central_differences():
         e[i] = h
         fd = (f(flat + e) - f(flat - e)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-9, (i, fd, g[i])
+
+
+def test_gradient_central_differences_step_1e4():
+    """Config 3's check as stated: FP64 central differences with h = 1e-4 on
+    weights of every tensor and on initial-state entries (truncation error
+    O(h^2) relative to the smooth loss; bound 1e-5 relative)."""
+    rw = _small(M=8, H=40)
+    L, _, dW, dx0 = po.rollout_grad(rw.x0, rw.weights, rw.p_ref, rw.params, rw.dt, rw.H, rw.w_act)
+    flat = po.pack(rw.weights)
+    g = po.pack(dW)
+    h = 1e-4
+    for i in [1, 832 + 40, 896 + 1234, 4992 + 33, 5056 + 77, 5314]:
+        e = np.zeros_like(flat)
+        e[i] = h
+        fd = (_loss(rw, rw.x0, po.unpack(flat + e)) - _loss(rw, rw.x0, po.unpack(flat - e))) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(g[i])), (i, fd, g[i])
+    for (w, j) in [(0, 1), (3, 5), (5, 9), (7, 11)]:
+        xp, xm = rw.x0.copy(), rw.x0.copy()
+        xp[w, j] += h
+        xm[w, j] -= h
+        fd = (_loss(rw, xp, rw.weights) - _loss(rw, xm, rw.weights)) / (2 * h)
+        assert abs(fd - dx0[w, j]) <= 1e-5 * max(1.0, abs(dx0[w, j])), (w, j, fd, dx0[w, j])
