@@ -67,6 +67,7 @@ extern "C" {
 
 /* device status word bits (sim_status) */
 #define SIM_FLAG_NONFINITE 1u /* some drone's state became NaN/Inf after a launch */
+#define SIM_FLAG_TIMEOUT 2u   /* a bounded in-kernel wait gave up (that call's results are invalid) */
 
 /* physics models (First Principles Modeling, Eqs. 1-6; Abstracted Physics Modeling, Eqs. 7-10;
  * the abstracted variant without thrust dynamics and drag, last sentence of that section:

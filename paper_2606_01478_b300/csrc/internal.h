@@ -35,7 +35,7 @@ cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* 
 cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
                                int C, int R, float dt, float w_act, const RolloutObjective& obj,
                                const DevParams& P, void* ws, const float* dL, float* dW, float* dx0,
-                               cudaStream_t st);
+                               uint32_t* status, cudaStream_t st);
 
 // Batched sampling rollouts (sample.cu).
 cudaError_t launch_sample(const float4* planes, int n, const int* offsets, int M, int N,

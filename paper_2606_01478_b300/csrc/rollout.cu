@@ -53,9 +53,12 @@ struct __align__(16) Smem {
   // reads step k from buffer k & 1 while step k - 1's copy arrives in the other
   __nv_bfloat16 h1[2][2][DPC * S64];
   __nv_bfloat16 h2[2][2][DPC * S64];
-  __nv_bfloat16 dz1[2][DPC * S64];
-  __nv_bfloat16 dz2[2][DPC * S64];
-  __nv_bfloat16 dz3[2][DPC * S16];
+  // adjoint tiles [step parity][hi, lo]: written by the compute warps at step k,
+  // read by the weight-gradient warps while the compute warps run step k - 1
+  __nv_bfloat16 dz1[2][2][DPC * S64];
+  __nv_bfloat16 dz2[2][2][DPC * S64];
+  __nv_bfloat16 dz3[2][2][DPC * S16];
+  __nv_bfloat16 obsr[2][2][DPC * S16];  // the reverse sweep's observation tiles (dW1 operand)
   float b1[64], b2[64], b3[8];
   float act[DPC][4];
   float dobs[DPC][16];
@@ -65,6 +68,9 @@ struct __align__(16) Smem {
   float pre_r[2][DPC][4];
   float4 pre_a[2][DPC];
   float actb[2][DPC][4];  // cached actions of the reverse sweep [buffer]
+  // reverse-sweep hand-off per step parity: full (4 compute-warp arrivals: the
+  // step's tiles are written), empty (4 weight-gradient-warp arrivals: read)
+  unsigned long long full[2], empty[2];
 };
 
 struct RolloutArgs {
@@ -78,6 +84,7 @@ struct RolloutArgs {
   float* dx0;             // [n][20]
   uint4* hcache;          // [C][n_warps][CACHE_CHUNKS] activation tiles + actions per step
   const float* dL;        // device scalar: upstream gradient of the loss
+  uint32_t* status;       // device status word or null (SIM_FLAG_TIMEOUT when a bounded wait gave up)
   float4* ckpt_a;         // [n_ckpt][n] previous action at each checkpoint (reward objective)
   float4* seg_a;          // [C][n] previous action of each segment step (reward objective)
   int n, H, C, R;
@@ -102,6 +109,11 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -198,26 +210,26 @@ __device__ __forceinline__ void load_c64(__nv_bfloat16 (*t)[DPC * S64], int r0, 
 __device__ void load_weights(Smem& s, const uint16_t* __restrict__ w) {
   const __nv_bfloat16* wb = reinterpret_cast<const __nv_bfloat16*>(w);
   const __nv_bfloat16 z = __float2bfloat16(0.f);
-  for (int e = threadIdx.x; e < 64 * S16; e += TPB) {
+  for (int e = threadIdx.x; e < 64 * S16; e += blockDim.x) {
     const int i = e / S16, c = e % S16;
     s.W1[e] = c < 13 ? wb[OFF_W1 + i * 13 + c] : z;
   }
-  for (int e = threadIdx.x; e < 64 * S64; e += TPB) {
+  for (int e = threadIdx.x; e < 64 * S64; e += blockDim.x) {
     const int j = e / S64, i = e % S64;
     s.W2[e] = i < 64 ? wb[OFF_W2 + j * 64 + i] : z;
   }
-  for (int e = threadIdx.x; e < 16 * S64; e += TPB) {
+  for (int e = threadIdx.x; e < 16 * S64; e += blockDim.x) {
     const int o = e / S64, j = e % S64;
     s.W3[e] = (o < 4 && j < 64) ? wb[OFF_W3 + o * 64 + j] : z;
   }
-  for (int e = threadIdx.x; e < 64; e += TPB) {
+  for (int e = threadIdx.x; e < 64; e += blockDim.x) {
     s.b1[e] = __bfloat162float(wb[OFF_B1 + e]);
     s.b2[e] = __bfloat162float(wb[OFF_B2 + e]);
   }
   if (threadIdx.x < 8) s.b3[threadIdx.x] = threadIdx.x < 4 ? __bfloat162float(wb[OFF_B3 + threadIdx.x]) : 0.f;
   // constant columns of the activation tiles: 1 in the bias column, 0 padding
   const __nv_bfloat16 one = __float2bfloat16(1.f);
-  for (int r = threadIdx.x; r < DPC; r += TPB) {
+  for (int r = threadIdx.x; r < DPC; r += blockDim.x) {
     for (int c = 64; c < S64; ++c) {
       for (int b = 0; b < 2; ++b) {
         s.h1[b][0][r * S64 + c] = c == 64 ? one : z;
@@ -225,22 +237,28 @@ __device__ void load_weights(Smem& s, const uint16_t* __restrict__ w) {
         s.h2[b][0][r * S64 + c] = c == 64 ? one : z;
         s.h2[b][1][r * S64 + c] = z;
       }
-      s.dz1[0][r * S64 + c] = z;
-      s.dz1[1][r * S64 + c] = z;
-      s.dz2[0][r * S64 + c] = z;
-      s.dz2[1][r * S64 + c] = z;
+      for (int b = 0; b < 2; ++b) {
+        s.dz1[b][0][r * S64 + c] = z;
+        s.dz1[b][1][r * S64 + c] = z;
+        s.dz2[b][0][r * S64 + c] = z;
+        s.dz2[b][1][r * S64 + c] = z;
+      }
     }
     for (int c = 0; c < S16; ++c) {
       s.obs[0][r * S16 + c] = z;
       s.obs[1][r * S16 + c] = z;
-      s.dz3[0][r * S16 + c] = z;
-      s.dz3[1][r * S16 + c] = z;
+      for (int b = 0; b < 2; ++b) {
+        s.dz3[b][0][r * S16 + c] = z;
+        s.dz3[b][1][r * S16 + c] = z;
+        s.obsr[b][0][r * S16 + c] = z;
+        s.obsr[b][1][r * S16 + c] = z;
+      }
     }
   }
 }
 
 // Write one drone's observation row (hi, lo; bias column 13 = 1).
-__device__ __forceinline__ void put_obs(Smem& s, int row, const float* x, const float r[3]) {
+__device__ __forceinline__ void put_obs(__nv_bfloat16 (*t)[DPC * S16], int row, const float* x, const float r[3]) {
   float o[16];
   o[0] = x[0] - r[0];
   o[1] = x[1] - r[1];
@@ -254,8 +272,8 @@ __device__ __forceinline__ void put_obs(Smem& s, int row, const float* x, const 
   for (int j = 0; j < 16; j += 2) {
     uint32_t h, l;
     split2(o[j], o[j + 1], h, l);
-    *reinterpret_cast<uint32_t*>(&s.obs[0][row * S16 + j]) = h;
-    *reinterpret_cast<uint32_t*>(&s.obs[1][row * S16 + j]) = l;
+    *reinterpret_cast<uint32_t*>(&t[0][row * S16 + j]) = h;
+    *reinterpret_cast<uint32_t*>(&t[1][row * S16 + j]) = l;
   }
 }
 
@@ -365,8 +383,8 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
   // dh2[d][j] = sum_o dz3[d][o] W3[o][j]
   {
     uint32_t ah[4], al[4];
-    ldsm_x4(ah, &s.dz3[0][arow * S16 + acol]);
-    ldsm_x4(al, &s.dz3[1][arow * S16 + acol]);
+    ldsm_x4(ah, &s.dz3[b][0][arow * S16 + acol]);
+    ldsm_x4(al, &s.dz3[b][1][arow * S16 + acol]);
 #pragma unroll
     for (int n = 0; n < 8; n += 2) {
       uint32_t b[4];
@@ -388,7 +406,7 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) d[n][e] *= fmaf(-h[n][e], h[n][e], 1.f);
   }
-  store_c64(s.dz2, r0, lane, d);
+  store_c64(s.dz2[b], r0, lane, d);
   // dh1[d][i] = sum_j dz2[d][j] W2[j][i]
   float e1[8][4];
 #pragma unroll
@@ -416,7 +434,7 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) e1[n][e] *= fmaf(-h[n][e], h[n][e], 1.f);
   }
-  store_c64(s.dz1, r0, lane, e1);
+  store_c64(s.dz1[b], r0, lane, e1);
   // dobs[d][c] = sum_i dz1[d][i] W1[i][c]
   float o[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
@@ -460,8 +478,8 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc, int hb) {
     const int d0 = 16 * kd;
     uint32_t ah[4], al[4];
     // dW2
-    ldsm_x4_t(ah, &s.dz2[0][(d0 + arow) * S64 + 16 * v + acol]);
-    ldsm_x4_t(al, &s.dz2[1][(d0 + arow) * S64 + 16 * v + acol]);
+    ldsm_x4_t(ah, &s.dz2[hb][0][(d0 + arow) * S64 + 16 * v + acol]);
+    ldsm_x4_t(al, &s.dz2[hb][1][(d0 + arow) * S64 + 16 * v + acol]);
 #pragma unroll
     for (int n = 0; n < 8; n += 2) {
       uint32_t bh[4], bl[4];
@@ -481,12 +499,12 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc, int hb) {
       if constexpr (LO) mma(acc.w2[8], al, bh[0], bh[1]);  // the bias column is exact (lo = 0)
     }
     // dW1
-    ldsm_x4_t(ah, &s.dz1[0][(d0 + arow) * S64 + 16 * v + acol]);
-    ldsm_x4_t(al, &s.dz1[1][(d0 + arow) * S64 + 16 * v + acol]);
+    ldsm_x4_t(ah, &s.dz1[hb][0][(d0 + arow) * S64 + 16 * v + acol]);
+    ldsm_x4_t(al, &s.dz1[hb][1][(d0 + arow) * S64 + 16 * v + acol]);
     {
       uint32_t bh[4], bl[4];
-      ldsm_x4_t(bh, &s.obs[0][(d0 + brow) * S16 + bcol]);
-      ldsm_x4_t(bl, &s.obs[1][(d0 + brow) * S16 + bcol]);
+      ldsm_x4_t(bh, &s.obsr[hb][0][(d0 + brow) * S16 + bcol]);
+      ldsm_x4_t(bl, &s.obsr[hb][1][(d0 + brow) * S16 + bcol]);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         mma(acc.w1[u], ah, bh[2 * u], bh[2 * u + 1]);
@@ -495,8 +513,8 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc, int hb) {
       }
     }
     // dW3
-    ldsm_x4_t(ah, &s.dz3[0][(d0 + arow) * S16 + acol]);
-    ldsm_x4_t(al, &s.dz3[1][(d0 + arow) * S16 + acol]);
+    ldsm_x4_t(ah, &s.dz3[hb][0][(d0 + arow) * S16 + acol]);
+    ldsm_x4_t(al, &s.dz3[hb][1][(d0 + arow) * S16 + acol]);
     {
       uint32_t bh[4], bl[4];
       ldsm_x4_t(bh, &s.h2[hb][0][(d0 + brow) * S64 + 16 * v + bcol]);
@@ -865,7 +883,7 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
       if (OBJ == SIM_OBJ_TRACKING_REWARD)
         a.ckpt_a[(size_t)(k / a.C) * a.n + i] = make_float4(ap[0], ap[1], ap[2], ap[3]);
     }
-    if (lane < 16) put_obs(s, row, x, r);
+    if (lane < 16) put_obs(s.obs, row, x, r);
     __syncwarp();
     float h1[8][4], h2[8][4];
     mlp_forward<LO>(s, r0, lane, h1, h2);
@@ -882,33 +900,90 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
   if (valid && lane < 16) a.loss_w[i] = loss;
 }
 
+// mbarrier helpers for the adjoint's warp hand-off (all threads of a role arrive;
+// waits are bounded: about a second, then the caller flags a timeout).
+__device__ __forceinline__ void mbar_init(unsigned long long* m, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* m) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(m)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* m, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 22) && !done; ++it)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(m)), "r"(parity)
+        : "memory");
+  return done != 0;
+}
+
+// The adjoint runs two warp roles per CTA.  Warps 0-3 (compute) own 16 drones each:
+// segment recompute, then per reverse step the loss and step adjoints and the MLP
+// backward, which leave the step's dz, obs and activation tiles in shared memory.
+// Warps 4-7 (weight gradient) accumulate dW over the CTA's 64 drones from those
+// tiles while the compute warps already run the next (earlier) step.  Hand-off per
+// step parity b = k & 1: full[b] (compute threads arrive when the tiles are
+// written), empty[b] (weight-gradient threads arrive when they are read).
 template <int OBJ, bool LO>
-__global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevParams P) {
+__global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, DevParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   load_weights(s, a.w);
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&s.full[b], TPB);
+      mbar_init(&s.empty[b], TPB);
+    }
+  }
   __syncthreads();
-  const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nseg = (a.H + a.C - 1) / a.C;
+  bool timed_out = false;
+  if (warp >= 4) {
+    // ---------------- weight-gradient warps: slice v of dW2 / dW1 / dW3
+    const int v = warp - 4;
+    DwAcc acc;
+#pragma unroll
+    for (int n = 0; n < 9; ++n) acc.w2[n][0] = acc.w2[n][1] = acc.w2[n][2] = acc.w2[n][3] = 0.f;
+#pragma unroll
+    for (int n = 0; n < 2; ++n) acc.w1[n][0] = acc.w1[n][1] = acc.w1[n][2] = acc.w1[n][3] = 0.f;
+#pragma unroll
+    for (int n = 0; n < 3; ++n) acc.w3[n][0] = acc.w3[n][1] = acc.w3[n][2] = acc.w3[n][3] = 0.f;
+    for (int t = 0; t < a.H; ++t) {  // reverse steps k = H - 1 - t in processing order
+      const int b = (a.H - 1 - t) & 1;
+      if (!mbar_wait(&s.full[b], (uint32_t)((t >> 1) & 1))) timed_out = true;
+      accumulate_dw<LO>(s, v, lane, acc, b);
+      mbar_arrive(&s.empty[b]);
+    }
+    store_dw(acc, v, lane, a.part + (size_t)blockIdx.x * NPOL_PAD);
+    if (timed_out && a.status) atomicOr(a.status, SIM_FLAG_TIMEOUT);
+    return;
+  }
+  // ---------------- compute warps
+  const int v = warp;
   const int r0 = 16 * v, row = r0 + (lane & 15);
   const int i = blockIdx.x * DPC + row;
   const bool valid = i < a.n;
   const int ii = valid ? i : a.n - 1;
   const float seed = valid ? (*a.dL) * a.inv_n : 0.f;  // padded rows contribute nothing
-  DwAcc acc;
-#pragma unroll
-  for (int n = 0; n < 9; ++n) acc.w2[n][0] = acc.w2[n][1] = acc.w2[n][2] = acc.w2[n][3] = 0.f;
-#pragma unroll
-  for (int n = 0; n < 2; ++n) acc.w1[n][0] = acc.w1[n][1] = acc.w1[n][2] = acc.w1[n][3] = 0.f;
-#pragma unroll
-  for (int n = 0; n < 3; ++n) acc.w3[n][0] = acc.w3[n][1] = acc.w3[n][2] = acc.w3[n][3] = 0.f;
   float lam[17];
 #pragma unroll
   for (int j = 0; j < 17; ++j) lam[j] = 0.f;
   // smoothness adjoint carried from step k + 1 to a_k: -2 sd w_dact (a_{k+1} - a_k)
   float carry[4] = {0.f, 0.f, 0.f, 0.f};
-  const int nseg = (a.H + a.C - 1) / a.C;
+  int t = 0;  // reverse steps processed so far (the weight-gradient warps count alike)
+  // wait until the weight-gradient warps have read the tiles of processing step u
+  auto wait_read = [&](int u) {
+    if (u >= 0 && !mbar_wait(&s.empty[(a.H - 1 - u) & 1], (uint32_t)((u >> 1) & 1))) timed_out = true;
+  };
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int k0 = sg * a.C, k1 = min(a.H, k0 + a.C);
+    // the recompute rewrites the staging tiles (buffer 0): every earlier step's
+    // tiles must have been read
+    wait_read(t - 1);
+    wait_read(t - 2);
     float x[17];
     load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
     float4 ap4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -926,7 +1001,7 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
       const float r[3] = {s.pre_r[k & 1][row][0], s.pre_r[k & 1][row][1], s.pre_r[k & 1][row][2]};
       if (lane < 16) prefetch_ref(s.pre_r[(k + 1) & 1][row], a.p_ref, k + 1, a.n, ii);
       cp_async_commit();
-      if (lane < 16) put_obs(s, row, x, r);
+      if (lane < 16) put_obs(s.obs, row, x, r);
       __syncwarp();
       {
         float h1[8][4], h2[8][4];
@@ -968,18 +1043,28 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
         cp_async16(&s.pre_a[k & 1][row], valid ? &a.seg_a[(size_t)(k - k0) * a.n + i]
                                                : &a.ckpt_a[(size_t)sg * a.n + ii]);
     };
-    // step k's activation tiles and actions, copied back from the cache into
-    // buffer k & 1 (each lane reads back the chunks it wrote)
-    auto prefetch_tiles = [&](int k) {
-      const uint4* src = a.hcache + ((size_t)(k - k0) * gridDim.x * 4 + blockIdx.x * 4 + v) * CACHE_CHUNKS;
-      for (int c = lane; c < CACHE_CHUNKS; c += 32) cp_async16(cache_smem(s, k & 1, r0, c, s.actb[k & 1]), src + c);
+    // step k's actions (group A, with the rows above) and activation tiles (group
+    // B), copied back from the cache into buffer k & 1 (each lane reads back the
+    // chunks it wrote)
+    const uint4* cache_w = a.hcache + ((size_t)blockIdx.x * 4 + v) * CACHE_CHUNKS;
+    const size_t cache_step = (size_t)gridDim.x * 4 * CACHE_CHUNKS;
+    auto prefetch_act = [&](int k) {
+      const uint4* src = cache_w + (size_t)(k - k0) * cache_step;
+      if (lane < 16) cp_async16(cache_smem(s, k & 1, r0, 4 * TILE_CHUNKS + lane, s.actb[k & 1]), src + 4 * TILE_CHUNKS + lane);
     };
+    auto prefetch_h = [&](int k) {
+      const uint4* src = cache_w + (size_t)(k - k0) * cache_step;
+      for (int c = lane; c < 4 * TILE_CHUNKS; c += 32) cp_async16(cache_smem(s, k & 1, r0, c, s.actb[k & 1]), src + c);
+    };
+    cp_async_wait_all();
     __threadfence_block();  // this thread's segment rows precede its async copies of them
     if (lane < 16) prefetch_step(k1 - 1);
-    prefetch_tiles(k1 - 1);
-    cp_async_commit();
-    for (int k = k1 - 1; k >= k0; --k) {
-      cp_async_wait_all();
+    prefetch_act(k1 - 1);
+    cp_async_commit();  // A
+    prefetch_h(k1 - 1);
+    cp_async_commit();  // B
+    for (int k = k1 - 1; k >= k0; --k, ++t) {
+      cp_async_wait_group<1>();  // this step's rows and actions (A); its tiles (B) may still be in flight
       __syncwarp();
       const int b = k & 1;
 #pragma unroll
@@ -987,18 +1072,20 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
       const float r[3] = {s.pre_r[b][row][0], s.pre_r[b][row][1], s.pre_r[b][row][2]};
       float ap[4] = {0.f, 0.f, 0.f, 0.f};
       if (OBJ == SIM_OBJ_TRACKING_REWARD) {
-        const float4 t = s.pre_a[b][row];
-        ap[0] = t.x;
-        ap[1] = t.y;
-        ap[2] = t.z;
-        ap[3] = t.w;
+        const float4 q = s.pre_a[b][row];
+        ap[0] = q.x;
+        ap[1] = q.y;
+        ap[2] = q.z;
+        ap[3] = q.w;
       }
       if (k > k0) {
         if (lane < 16) prefetch_step(k - 1);
-        prefetch_tiles(k - 1);
+        prefetch_act(k - 1);
       }
-      cp_async_commit();
-      if (lane < 16) put_obs(s, row, x, r);
+      cp_async_commit();  // A of step k - 1
+      // this step's obs and dz tiles (parity b) were last read at processing step
+      // t - 2, whose read was awaited during step t - 1
+      if (lane < 16) put_obs(s.obsr[b], row, x, r);
       __syncwarp();
       const float act[4] = {s.actb[b][row][0], s.actb[b][row][1], s.actb[b][row][2], s.actb[b][row][3]};
       // loss term at policy step k + 1 (state after the last sub-step)
@@ -1044,30 +1131,36 @@ __global__ void __launch_bounds__(TPB) rollout_bwd_kernel(RolloutArgs a, DevPara
         for (int o = 0; o < 16; o += 2) {
           uint32_t h, l;
           split2(dz[o], dz[o + 1], h, l);
-          *reinterpret_cast<uint32_t*>(&s.dz3[0][row * S16 + o]) = h;
-          *reinterpret_cast<uint32_t*>(&s.dz3[1][row * S16 + o]) = l;
+          *reinterpret_cast<uint32_t*>(&s.dz3[b][0][row * S16 + o]) = h;
+          *reinterpret_cast<uint32_t*>(&s.dz3[b][1][row * S16 + o]) = l;
         }
       }
+      cp_async_wait_group<1>();  // this step's activation tiles (B); A of step k - 1 may pend
       __syncwarp();
       mlp_backward<LO>(s, r0, lane, b);
       __syncwarp();
+      mbar_arrive(&s.full[b]);  // this warp's tiles of step k are written
+      // the tiles of step k - 1 go to buffer (k - 1) & 1, which the weight-gradient
+      // warps read for processing step t - 1 (running meanwhile): wait for that read
+      wait_read(t - 1);
+      if (k > k0) prefetch_h(k - 1);
+      cp_async_commit();  // B of step k - 1
       // observation adjoint: obs = [p - r, q, v, w]
 #pragma unroll
       for (int j = 0; j < 13; ++j) lam[j] += s.dobs[row][j];
 #pragma unroll
       for (int j = 0; j < 17; ++j) xn[j] = x[j];
-      __syncthreads();  // every warp's tiles for this step are in shared memory
-      accumulate_dw<LO>(s, v, lane, acc, b);
-      __syncthreads();  // before the next step overwrites the tiles
     }
   }
+  wait_read(t - 1);  // the weight-gradient warps finish before the CTA's memory is released
+  wait_read(t - 2);
   if (valid && lane < 16) {
     float4* p = reinterpret_cast<float4*>(a.dx0 + (size_t)i * 20);
 #pragma unroll
     for (int j = 0; j < 4; ++j) p[j] = make_float4(lam[4 * j], lam[4 * j + 1], lam[4 * j + 2], lam[4 * j + 3]);
     p[4] = make_float4(lam[16], 0.f, 0.f, 0.f);
   }
-  store_dw(acc, v, lane, a.part + (size_t)blockIdx.x * NPOL_PAD);
+  if (timed_out && a.status) atomicOr(a.status, SIM_FLAG_TIMEOUT);
 }
 
 // Deterministic reductions: dW[p] = sum over CTAs (fixed order, fp64);
@@ -1168,11 +1261,11 @@ static void carve(void* ws, int n, int H, int C, int R, const RolloutObjective& 
 
 template <typename K>
 static cudaError_t launch_rollout_kernel(K kernel, int grid, const ro::RolloutArgs& a,
-                                         const DevParams& P, cudaStream_t st) {
+                                         const DevParams& P, cudaStream_t st, int threads = ro::TPB) {
   const int smem = (int)sizeof(ro::Smem);
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kernel<<<grid, ro::TPB, smem, st>>>(a, P);
+  kernel<<<grid, threads, smem, st>>>(a, P);
   return cudaGetLastError();
 }
 
@@ -1205,9 +1298,10 @@ cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* 
 cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
                                int C, int R, float dt, float w_act, const RolloutObjective& obj,
                                const DevParams& P, void* ws, const float* dL, float* dW, float* dx0,
-                               cudaStream_t st) {
+                               uint32_t* status, cudaStream_t st) {
   ro::RolloutArgs a{};
   carve(ws, n, H, C, R, obj, a);
+  a.status = status;
   a.x0 = x0;
   a.w = w;
   a.p_ref = p_ref;
@@ -1221,10 +1315,10 @@ cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* 
   a.inv_n = 1.f / (float)n;
   const int grid = (n + ro::DPC - 1) / ro::DPC;
   cudaError_t e = obj.kind == SIM_OBJ_TRACKING_REWARD
-                      ? (obj.hilo ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_TRACKING_REWARD, true>, grid, a, P, st)
-                                  : launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_TRACKING_REWARD, false>, grid, a, P, st))
-                      : (obj.hilo ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED, true>, grid, a, P, st)
-                                  : launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED, false>, grid, a, P, st));
+                      ? (obj.hilo ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_TRACKING_REWARD, true>, grid, a, P, st, 2 * ro::TPB)
+                                  : launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_TRACKING_REWARD, false>, grid, a, P, st, 2 * ro::TPB))
+                      : (obj.hilo ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED, true>, grid, a, P, st, 2 * ro::TPB)
+                                  : launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED, false>, grid, a, P, st, 2 * ro::TPB));
   if (e != cudaSuccess) return e;
   ro::reduce_dw_kernel<<<(ro::NPOL + 255) / 256, 256, 0, st>>>(a.part, grid, dW);
   return cudaGetLastError();

@@ -735,7 +735,7 @@ int sim_rollout_bwd(sim_h h, const float* x0, const uint16_t* w, const float* p_
   if (r != SIM_OK) return r;
   cudaError_t e = cf::launch_rollout_bwd(x0, w, p_ref, (int)h->ntot, H, C, h->rollout_repeat, h->dt,
                                          w_act, h->objective,
-                                         h->p0, ws, dL, dW, dx0, (cudaStream_t)stream);
+                                         h->p0, ws, dL, dW, dx0, h->status, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "rollout backward launch");
   h->launches += 2;
   return SIM_OK;
