@@ -1057,6 +1057,10 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       for (int c = lane; c < 4 * TILE_CHUNKS; c += 32) cp_async16(cache_smem(s, k & 1, r0, c, s.actb[k & 1]), src + c);
     };
     cp_async_wait_all();
+    __syncwarp();
+    // the reference at policy step k + 1, carried like xn (the recompute's last
+    // prefetch left the one at k1 in buffer k1 & 1)
+    float rn[3] = {s.pre_r[k1 & 1][row][0], s.pre_r[k1 & 1][row][1], s.pre_r[k1 & 1][row][2]};
     __threadfence_block();  // this thread's segment rows precede its async copies of them
     if (lane < 16) prefetch_step(k1 - 1);
     prefetch_act(k1 - 1);
@@ -1089,11 +1093,7 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       __syncwarp();
       const float act[4] = {s.actb[b][row][0], s.actb[b][row][1], s.actb[b][row][2], s.actb[b][row][3]};
       // loss term at policy step k + 1 (state after the last sub-step)
-      {
-        float rn[3];
-        ref_at(a.p_ref, k + 1, a.n, ii, rn);
-        step_loss_state_adjoint<OBJ>(xn, rn, seed, a, lam);
-      }
+      step_loss_state_adjoint<OBJ>(xn, rn, seed, a, lam);
       // back through the R sub-steps; the held action collects every sub-step's adjoint
       float ga[4] = {0.f, 0.f, 0.f, 0.f};
       for (int j = a.R - 1; j >= 0; --j) {
@@ -1150,6 +1150,8 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       for (int j = 0; j < 13; ++j) lam[j] += s.dobs[row][j];
 #pragma unroll
       for (int j = 0; j < 17; ++j) xn[j] = x[j];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) rn[c] = r[c];
     }
   }
   wait_read(t - 1);  // the weight-gradient warps finish before the CTA's memory is released

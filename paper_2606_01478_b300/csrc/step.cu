@@ -2,10 +2,42 @@
 // registers for all K steps, one coalesced float4-plane read and write per
 // launch (the paper's fused step pipeline scanned over steps, Architecture
 // section).
+#include <utility>
+
 #include "internal.h"
 #include "stepcore.cuh"
 
 namespace cf {
+
+// Programmatic dependent launch of the K-chained step kernels.  A step kernel is
+// launched with programmatic stream serialization, so its CTAs may be scheduled
+// while the previous kernel of the stream drains; griddepcontrol.wait then holds
+// every thread until that kernel has completed and its writes are visible, so
+// every global access of the kernel follows it.  Dependents are released only
+// after the wait: at most two grids of the chain are resident at once, and a
+// dependent is scheduled only once every CTA of this grid has started, so none
+// of this grid's CTAs waits for a slot.  Without the launch attribute (or behind
+// a copy or an ordinary kernel) both instructions return at once.
+__device__ __forceinline__ void chain_wait_then_release() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_chained(void (*kernel)(KArgs...), int grid, int tpb, cudaStream_t st,
+                                  Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(tpb);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 template <int MODEL, int INTEG, int CTRL, int MOTOR>
 __device__ __forceinline__ void run_drone(const StepArgs& a, int i, const DevParams& P) {
@@ -53,6 +85,7 @@ __device__ __forceinline__ void run_drone(const StepArgs& a, int i, const DevPar
 
 template <int MODEL, int INTEG, int CTRL, int MOTOR, bool PERSET>
 __global__ void __launch_bounds__(256) step_kernel(StepArgs a, DevParams P0) {
+  chain_wait_then_release();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   if constexpr (PERSET) {
@@ -70,6 +103,7 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a, DevParams P0) {
 template <int INTEG, int CTRL, int MOTOR>
 __global__ void __launch_bounds__(256) step_batched_kernel(StepArgs a, const int4* __restrict__ tiles,
                                                            int n_tiles) {
+  chain_wait_then_release();
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -109,8 +143,7 @@ static cudaError_t launch_b(const StepArgs& a, const int4* tiles, int n_tiles, i
   int grid = sms * per_sm;
   const int need = (n_tiles + warps_per_block - 1) / warps_per_block;
   if (grid > need) grid = need;
-  step_batched_kernel<INTEG, CTRL, MOTOR><<<grid, tpb, 0, st>>>(a, tiles, n_tiles);
-  return cudaGetLastError();
+  return launch_chained(step_batched_kernel<INTEG, CTRL, MOTOR>, grid, tpb, st, a, tiles, n_tiles);
 }
 
 cudaError_t launch_step_batched(const StepArgs& a, const int4* tiles, int n_tiles, int integrator,
@@ -134,8 +167,7 @@ cudaError_t launch_step_batched(const StepArgs& a, const int4* tiles, int n_tile
 template <int MODEL, int INTEG, int CTRL, int MOTOR, bool PERSET>
 static cudaError_t launch_t(const StepArgs& a, const DevParams& P, int tpb, cudaStream_t st) {
   const int grid = (a.n + tpb - 1) / tpb;
-  step_kernel<MODEL, INTEG, CTRL, MOTOR, PERSET><<<grid, tpb, 0, st>>>(a, P);
-  return cudaGetLastError();
+  return launch_chained(step_kernel<MODEL, INTEG, CTRL, MOTOR, PERSET>, grid, tpb, st, a, P);
 }
 
 template <int MODEL, int INTEG, int CTRL>
