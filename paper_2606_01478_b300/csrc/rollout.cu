@@ -69,8 +69,11 @@ struct __align__(16) Smem {
   float4 pre_a[2][DPC];
   float actb[2][DPC][4];  // cached actions of the reverse sweep [buffer]
   // reverse-sweep hand-off per step parity: full (4 compute-warp arrivals: the
-  // step's tiles are written), empty (4 weight-gradient-warp arrivals: read)
+  // step's tiles are written), empty (4 weight-gradient-warp arrivals: read);
+  // ready[v][b]: the bulk copy of compute warp v's cached tiles and actions into
+  // buffer b has landed (transaction-count completion)
   unsigned long long full[2], empty[2];
+  unsigned long long ready[4][2];
 };
 
 struct RolloutArgs {
@@ -109,11 +112,6 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-// wait until at most N of this thread's committed groups are still pending
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 __device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -290,9 +288,10 @@ __device__ __forceinline__ float tanh_fast(float x) {
 }
 
 // MLP forward for the warp's 16 drones (rows r0..r0+15).  Returns h1, h2
-// (fp32 accumulator fragments, after tanh) and writes the actions to s.act.
+// (fp32 accumulator fragments, after tanh) and writes the actions to act.
 template <bool LO>
-__device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[8][4]) {
+__device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[8][4],
+                            float (*act)[4]) {
   const int g = lane >> 2, tq = lane & 3;
   const int arow = r0 + (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
   uint32_t oh[4], ol[4];
@@ -363,10 +362,10 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
     if constexpr (LO) mma(z3, al, b[0], b[1]);
   }
   if (tq < 2) {
-    s.act[r0 + g][2 * tq] = tanh_fast(z3[0]);
-    s.act[r0 + g][2 * tq + 1] = tanh_fast(z3[1]);
-    s.act[r0 + g + 8][2 * tq] = tanh_fast(z3[2]);
-    s.act[r0 + g + 8][2 * tq + 1] = tanh_fast(z3[3]);
+    act[r0 + g][2 * tq] = tanh_fast(z3[0]);
+    act[r0 + g][2 * tq + 1] = tanh_fast(z3[1]);
+    act[r0 + g + 8][2 * tq] = tanh_fast(z3[2]);
+    act[r0 + g + 8][2 * tq + 1] = tanh_fast(z3[3]);
   }
 }
 
@@ -786,15 +785,72 @@ __device__ __forceinline__ void ref_at(const float* __restrict__ p_ref, int k, i
 
 // ------------------------------------------------------------------ activation cache
 
-// Shared-memory address of chunk c of warp rows r0..r0+15 in tile buffer b
-// (c < 4 TILE_CHUNKS: activation tiles, else action rows of act).
-__device__ __forceinline__ void* cache_smem(Smem& s, int b, int r0, int c, float (*act)[4]) {
-  const int q = c / TILE_CHUNKS, w = c - q * TILE_CHUNKS;
-  if (q < 4) {
-    __nv_bfloat16* t = (q < 2 ? s.h1[b][q] : s.h2[b][q - 2]) + r0 * S64;
-    return reinterpret_cast<uint4*>(t) + w;
-  }
-  return act[r0 + w];
+// One warp's cached step is five contiguous runs in shared memory and in the cache
+// entry alike: the warp's 16 rows of h1 hi, h1 lo, h2 hi, h2 lo in tile buffer b
+// (TILE_CHUNKS 16-byte chunks each) and its 16 action rows in actb[b].  They move
+// as bulk copies (cp.async.bulk: one thread, the copy engine of the SM).
+constexpr uint32_t TILE_BYTES = TILE_CHUNKS * 16, ACT_BYTES = 16 * 16;
+constexpr uint32_t CACHE_BYTES = 4 * TILE_BYTES + ACT_BYTES;
+static_assert(CACHE_BYTES == CACHE_CHUNKS * 16, "cache entry = four tiles + action rows");
+static_assert(offsetof(Smem, h1) % 16 == 0 && offsetof(Smem, h2) % 16 == 0 &&
+                  offsetof(Smem, actb) % 16 == 0 && (DPC * S64 * 2) % 16 == 0,
+              "bulk copies start on 16-byte boundaries");
+
+__device__ __forceinline__ void bulk_s2g(void* g, const void* sm, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(g),
+               "r"(smem_addr(sm)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* sm, const void* g, uint32_t bytes,
+                                         unsigned long long* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(sm)),
+      "l"(g), "r"(bytes), "r"(smem_addr(mbar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's bulk groups still read their source
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
+}
+// wait until all of this thread's bulk groups have completed (writes performed)
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// order this thread's shared-memory writes before bulk copies that read them
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// order global-memory accesses of bulk copies with this thread's synchronisation
+// (after the writer's completed bulk stores, before the reader's bulk loads)
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(m)), "r"(bytes)
+               : "memory");
+}
+
+// Copy out warp rows r0..r0+15 of tile buffer b to cache entry g (one bulk group).
+__device__ __forceinline__ void cache_store(Smem& s, int b, int r0, uint4* g) {
+  bulk_s2g(g, s.h1[b][0] + r0 * S64, TILE_BYTES);
+  bulk_s2g(g + TILE_CHUNKS, s.h1[b][1] + r0 * S64, TILE_BYTES);
+  bulk_s2g(g + 2 * TILE_CHUNKS, s.h2[b][0] + r0 * S64, TILE_BYTES);
+  bulk_s2g(g + 3 * TILE_CHUNKS, s.h2[b][1] + r0 * S64, TILE_BYTES);
+  bulk_s2g(g + 4 * TILE_CHUNKS, s.actb[b][r0], ACT_BYTES);
+  bulk_commit();
+}
+
+// Bring cache entry g back into rows r0..r0+15 of buffer b; mbar completes when
+// all CACHE_BYTES have landed.
+__device__ __forceinline__ void cache_load(Smem& s, int b, int r0, const uint4* g,
+                                           unsigned long long* mbar) {
+  mbar_expect_tx(mbar, CACHE_BYTES);
+  bulk_g2s(s.h1[b][0] + r0 * S64, g, TILE_BYTES, mbar);
+  bulk_g2s(s.h1[b][1] + r0 * S64, g + TILE_CHUNKS, TILE_BYTES, mbar);
+  bulk_g2s(s.h2[b][0] + r0 * S64, g + 2 * TILE_CHUNKS, TILE_BYTES, mbar);
+  bulk_g2s(s.h2[b][1] + r0 * S64, g + 3 * TILE_CHUNKS, TILE_BYTES, mbar);
+  bulk_g2s(s.actb[b][r0], g + 4 * TILE_CHUNKS, ACT_BYTES, mbar);
 }
 
 // ------------------------------------------------------------------ objectives
@@ -886,7 +942,7 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
     if (lane < 16) put_obs(s.obs, row, x, r);
     __syncwarp();
     float h1[8][4], h2[8][4];
-    mlp_forward<LO>(s, r0, lane, h1, h2);
+    mlp_forward<LO>(s, r0, lane, h1, h2, s.act);
     __syncwarp();
     float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
     __syncwarp();
@@ -935,12 +991,23 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
     for (int b = 0; b < 2; ++b) {
       mbar_init(&s.full[b], TPB);
       mbar_init(&s.empty[b], TPB);
+      for (int v = 0; v < 4; ++v) mbar_init(&s.ready[v][b], 1);
     }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nseg = (a.H + a.C - 1) / a.C;
   bool timed_out = false;
+  // protocol waits: after this thread's first timeout the rest are skipped (the
+  // results are then void and flagged), so a broken hand-off costs one wait limit
+  auto wait_on = [&](unsigned long long* m, uint32_t par) {
+    if (!timed_out && !mbar_wait(m, par)) timed_out = true;
+  };
+  // cache entry of warp rows 16 v at segment step j: cache_at(v, j)
+  const size_t cache_step = (size_t)gridDim.x * 4 * CACHE_CHUNKS;
+  auto cache_at = [&](int v, int j) {
+    return a.hcache + (size_t)j * cache_step + ((size_t)blockIdx.x * 4 + v) * CACHE_CHUNKS;
+  };
   if (warp >= 4) {
     // ---------------- weight-gradient warps: slice v of dW2 / dW1 / dW3
     const int v = warp - 4;
@@ -951,12 +1018,35 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
     for (int n = 0; n < 2; ++n) acc.w1[n][0] = acc.w1[n][1] = acc.w1[n][2] = acc.w1[n][3] = 0.f;
 #pragma unroll
     for (int n = 0; n < 3; ++n) acc.w3[n][0] = acc.w3[n][1] = acc.w3[n][2] = acc.w3[n][3] = 0.f;
-    for (int t = 0; t < a.H; ++t) {  // reverse steps k = H - 1 - t in processing order
-      const int b = (a.H - 1 - t) & 1;
-      if (!mbar_wait(&s.full[b], (uint32_t)((t >> 1) & 1))) timed_out = true;
-      accumulate_dw<LO>(s, v, lane, acc, b);
-      mbar_arrive(&s.empty[b]);
+    // Reverse steps k = H - 1 - t in processing order t.  After reading buffer
+    // b = k & 1, and once all four warps of this role have, warp v refills it with
+    // step k - 2 of compute warp v's rows (the steps k1 - 1 and k1 - 2 of a segment
+    // are loaded by the compute warp itself, after its recompute).
+    int t = 0;
+    int last0 = -1, last1 = -1;  // processing step of the last load issued into buffer 0, 1
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+      const int k0 = sg * a.C, k1 = min(a.H, k0 + a.C);
+      for (int k = k1 - 1; k >= k0; --k, ++t) {
+        const int b = k & 1;
+        const uint32_t par = (uint32_t)((t >> 1) & 1);
+        wait_on(&s.full[b], par);
+        accumulate_dw<LO>(s, v, lane, acc, b);
+        mbar_arrive(&s.empty[b]);
+        if (k - 2 >= k0) {
+          wait_on(&s.empty[b], par);
+          if (lane == 0) {
+            fence_proxy_async_global();
+            cache_load(s, b, 16 * v, cache_at(v, k - 2 - k0), &s.ready[v][b]);
+          }
+          if (b) last1 = t + 2;
+          else last0 = t + 2;
+        }
+      }
     }
+    // the compute warp consumes every load issued here; wait (bounded) for the
+    // last one into each buffer, so that no copy is in flight when the CTA exits
+    if (last0 >= 0 && !mbar_wait(&s.ready[v][0], (uint32_t)((last0 >> 1) & 1))) timed_out = true;
+    if (last1 >= 0 && !mbar_wait(&s.ready[v][1], (uint32_t)((last1 >> 1) & 1))) timed_out = true;
     store_dw(acc, v, lane, a.part + (size_t)blockIdx.x * NPOL_PAD);
     if (timed_out && a.status) atomicOr(a.status, SIM_FLAG_TIMEOUT);
     return;
@@ -976,12 +1066,12 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
   int t = 0;  // reverse steps processed so far (the weight-gradient warps count alike)
   // wait until the weight-gradient warps have read the tiles of processing step u
   auto wait_read = [&](int u) {
-    if (u >= 0 && !mbar_wait(&s.empty[(a.H - 1 - u) & 1], (uint32_t)((u >> 1) & 1))) timed_out = true;
+    if (u >= 0) wait_on(&s.empty[(a.H - 1 - u) & 1], (uint32_t)((u >> 1) & 1));
   };
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int k0 = sg * a.C, k1 = min(a.H, k0 + a.C);
-    // the recompute rewrites the staging tiles (buffer 0): every earlier step's
-    // tiles must have been read
+    // the recompute stages its tiles in both buffers: every earlier step's tiles
+    // must have been read
     wait_read(t - 1);
     wait_read(t - 2);
     float x[17];
@@ -1002,21 +1092,21 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       if (lane < 16) prefetch_ref(s.pre_r[(k + 1) & 1][row], a.p_ref, k + 1, a.n, ii);
       cp_async_commit();
       if (lane < 16) put_obs(s.obs, row, x, r);
+      // this step's activations and actions, kept for the reverse sweep: staged in
+      // buffer sb, whose copy-out two steps ago must have read it, then copied out
+      const int sb = (k - k0) & 1;
+      if (k - k0 >= 2 && lane == 0) bulk_wait_read<1>();
       __syncwarp();
       {
         float h1[8][4], h2[8][4];
-        mlp_forward<LO>(s, r0, lane, h1, h2);
-        // keep this step's activations for the reverse sweep (tiles staged in buffer 0)
-        store_c64(s.h1[0], r0, lane, h1);
-        store_c64(s.h2[0], r0, lane, h2);
+        mlp_forward<LO>(s, r0, lane, h1, h2, s.actb[sb]);
+        store_c64(s.h1[sb], r0, lane, h1);
+        store_c64(s.h2[sb], r0, lane, h2);
       }
+      fence_proxy_async_smem();
       __syncwarp();
-      {
-        uint4* dst = a.hcache + ((size_t)(k - k0) * gridDim.x * 4 + blockIdx.x * 4 + v) * CACHE_CHUNKS;
-        for (int c = lane; c < CACHE_CHUNKS; c += 32)
-          dst[c] = *reinterpret_cast<const uint4*>(cache_smem(s, 0, r0, c, s.act));
-      }
-      float act[4] = {s.act[row][0], s.act[row][1], s.act[row][2], s.act[row][3]};
+      if (lane == 0) cache_store(s, sb, r0, cache_at(v, k - k0));
+      float act[4] = {s.actb[sb][row][0], s.actb[sb][row][1], s.actb[sb][row][2], s.actb[sb][row][3]};
       __syncwarp();
       for (int j = 0; j < a.R; ++j) {
         if (j > 0 && valid && lane < 16)
@@ -1043,19 +1133,15 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
         cp_async16(&s.pre_a[k & 1][row], valid ? &a.seg_a[(size_t)(k - k0) * a.n + i]
                                                : &a.ckpt_a[(size_t)sg * a.n + ii]);
     };
-    // step k's actions (group A, with the rows above) and activation tiles (group
-    // B), copied back from the cache into buffer k & 1 (each lane reads back the
-    // chunks it wrote)
-    const uint4* cache_w = a.hcache + ((size_t)blockIdx.x * 4 + v) * CACHE_CHUNKS;
-    const size_t cache_step = (size_t)gridDim.x * 4 * CACHE_CHUNKS;
-    auto prefetch_act = [&](int k) {
-      const uint4* src = cache_w + (size_t)(k - k0) * cache_step;
-      if (lane < 16) cp_async16(cache_smem(s, k & 1, r0, 4 * TILE_CHUNKS + lane, s.actb[k & 1]), src + 4 * TILE_CHUNKS + lane);
-    };
-    auto prefetch_h = [&](int k) {
-      const uint4* src = cache_w + (size_t)(k - k0) * cache_step;
-      for (int c = lane; c < 4 * TILE_CHUNKS; c += 32) cp_async16(cache_smem(s, k & 1, r0, c, s.actb[k & 1]), src + c);
-    };
+    // step k's activation tiles and actions come back from the cache into buffer
+    // k & 1 by bulk copies: steps k1 - 1 and k1 - 2 issued here once the copy-out
+    // has completed, the others by the weight-gradient warps
+    if (lane == 0) {
+      bulk_wait_all();
+      fence_proxy_async_global();
+      cache_load(s, (k1 - 1) & 1, r0, cache_at(v, k1 - 1 - k0), &s.ready[v][(k1 - 1) & 1]);
+      if (k1 - 2 >= k0) cache_load(s, (k1 - 2) & 1, r0, cache_at(v, k1 - 2 - k0), &s.ready[v][(k1 - 2) & 1]);
+    }
     cp_async_wait_all();
     __syncwarp();
     // the reference at policy step k + 1, carried like xn (the recompute's last
@@ -1063,14 +1149,14 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
     float rn[3] = {s.pre_r[k1 & 1][row][0], s.pre_r[k1 & 1][row][1], s.pre_r[k1 & 1][row][2]};
     __threadfence_block();  // this thread's segment rows precede its async copies of them
     if (lane < 16) prefetch_step(k1 - 1);
-    prefetch_act(k1 - 1);
-    cp_async_commit();  // A
-    prefetch_h(k1 - 1);
-    cp_async_commit();  // B
+    cp_async_commit();
     for (int k = k1 - 1; k >= k0; --k, ++t) {
-      cp_async_wait_group<1>();  // this step's rows and actions (A); its tiles (B) may still be in flight
-      __syncwarp();
       const int b = k & 1;
+      cp_async_wait_all();  // this step's state row, reference and previous action
+      // this step's tiles and actions; the buffer's previous contents were read
+      // by the weight-gradient warps before the copy was issued
+      wait_on(&s.ready[v][b], (uint32_t)((t >> 1) & 1));
+      __syncwarp();
 #pragma unroll
       for (int j = 0; j < 17; ++j) x[j] = s.pre_x[b][row][j];
       const float r[3] = {s.pre_r[b][row][0], s.pre_r[b][row][1], s.pre_r[b][row][2]};
@@ -1082,13 +1168,8 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
         ap[2] = q.z;
         ap[3] = q.w;
       }
-      if (k > k0) {
-        if (lane < 16) prefetch_step(k - 1);
-        prefetch_act(k - 1);
-      }
-      cp_async_commit();  // A of step k - 1
-      // this step's obs and dz tiles (parity b) were last read at processing step
-      // t - 2, whose read was awaited during step t - 1
+      if (k > k0 && lane < 16) prefetch_step(k - 1);
+      cp_async_commit();
       if (lane < 16) put_obs(s.obsr[b], row, x, r);
       __syncwarp();
       const float act[4] = {s.actb[b][row][0], s.actb[b][row][1], s.actb[b][row][2], s.actb[b][row][3]};
@@ -1135,16 +1216,10 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
           *reinterpret_cast<uint32_t*>(&s.dz3[b][1][row * S16 + o]) = l;
         }
       }
-      cp_async_wait_group<1>();  // this step's activation tiles (B); A of step k - 1 may pend
       __syncwarp();
       mlp_backward<LO>(s, r0, lane, b);
       __syncwarp();
       mbar_arrive(&s.full[b]);  // this warp's tiles of step k are written
-      // the tiles of step k - 1 go to buffer (k - 1) & 1, which the weight-gradient
-      // warps read for processing step t - 1 (running meanwhile): wait for that read
-      wait_read(t - 1);
-      if (k > k0) prefetch_h(k - 1);
-      cp_async_commit();  // B of step k - 1
       // observation adjoint: obs = [p - r, q, v, w]
 #pragma unroll
       for (int j = 0; j < 13; ++j) lam[j] += s.dobs[row][j];
@@ -1156,6 +1231,10 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
   }
   wait_read(t - 1);  // the weight-gradient warps finish before the CTA's memory is released
   wait_read(t - 2);
+  // no bulk load into this warp's rows may be in flight at exit (bounded, even
+  // after a timeout): the last two deliveries, already consumed unless one was skipped
+  for (int u = t - 2; u < t; ++u)
+    if (u >= 0 && !mbar_wait(&s.ready[v][(a.H - 1 - u) & 1], (uint32_t)((u >> 1) & 1))) timed_out = true;
   if (valid && lane < 16) {
     float4* p = reinterpret_cast<float4*>(a.dx0 + (size_t)i * 20);
 #pragma unroll
