@@ -115,6 +115,7 @@ class ClockSampler:
 KERNEL_SOURCES = {
     "step_kernel": ("step.cu", "stepcore.cuh", "physics.cuh", "common.cuh"),
     "step_batched_kernel": ("step.cu", "stepcore.cuh", "physics.cuh", "common.cuh"),
+    "step_batched_single_kernel": ("step.cu", "stepcore.cuh", "physics.cuh", "common.cuh"),
     "rollout_bwd_kernel": ("rollout.cu", "physics.cuh", "common.cuh"),
     "sample_kernel": ("sample.cu", "stepcore.cuh", "physics.cuh", "common.cuh"),
 }
@@ -445,7 +446,7 @@ def measure_config2(dev, reps: int = 3) -> dict:
             achieved = byt * wl.steps / (ms / 1e3) / 1e9
             rec["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
                                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                               "traffic": _profiled_traffic("step_batched_kernel", wl.name + "_K1"),
+                               "traffic": _profiled_traffic("step_batched_single_kernel", wl.name + "_K1"),
                                "bytes_per_launch": byt,
                                "peak_basis": f"{kind} HBM copy bandwidth"}
         else:

@@ -39,7 +39,8 @@ static cudaError_t launch_chained(void (*kernel)(KArgs...), int grid, int tpb, c
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-template <int MODEL, int INTEG, int CTRL, int MOTOR>
+// SINGLE: the launch is known to take one step (a.K == 1).
+template <int MODEL, int INTEG, int CTRL, int MOTOR, bool SINGLE = false>
 __device__ __forceinline__ void run_drone(const StepArgs& a, int i, const DevParams& P) {
   constexpr int NPL = (MODEL == SIM_FIRST_PRINCIPLES) ? 5 : 4;
   const int n = a.n;
@@ -59,20 +60,27 @@ __device__ __forceinline__ void run_drone(const StepArgs& a, int i, const DevPar
   int left = (a.t0 / a.hold >= last) ? 0x7fffffff : a.hold - a.t0 % a.hold;
   CtrlHold h;
   decode_command<MODEL, CTRL>(a.cmd[(size_t)blk * n + i], P, h);
-  float4 next = a.cmd[(size_t)min(blk + 1, last) * n + i];
-  // outer loop over command-block segments, inner loop over the steps of one
-  // segment (no per-step block bookkeeping in the hot loop)
-  for (int k = 0; k < a.K;) {
-    if (left == 0) {
-      ++blk;
-      decode_command<MODEL, CTRL>(next, P, h);
-      left = (blk >= last) ? 0x7fffffff : a.hold;
-      next = a.cmd[(size_t)min(blk + 1, last) * n + i];
+  if (SINGLE || a.K == 1) {
+    // a single step never reaches the next command block: no look-ahead load
+    one_step<MODEL, INTEG, CTRL, MOTOR>(s, h, P, drag, a.dt);
+  } else {
+    // the next block's command, prefetched when this launch reaches it
+    float4 next = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a.K > left) next = a.cmd[(size_t)min(blk + 1, last) * n + i];
+    // outer loop over command-block segments, inner loop over the steps of one
+    // segment (no per-step block bookkeeping in the hot loop)
+    for (int k = 0; k < a.K;) {
+      if (left == 0) {
+        ++blk;
+        decode_command<MODEL, CTRL>(next, P, h);
+        left = (blk >= last) ? 0x7fffffff : a.hold;
+        if (a.K - k > left) next = a.cmd[(size_t)min(blk + 1, last) * n + i];
+      }
+      const int seg = min(left, a.K - k);
+      for (int j = 0; j < seg; ++j) one_step<MODEL, INTEG, CTRL, MOTOR>(s, h, P, drag, a.dt);
+      k += seg;
+      left -= seg;
     }
-    const int seg = min(left, a.K - k);
-    for (int j = 0; j < seg; ++j) one_step<MODEL, INTEG, CTRL, MOTOR>(s, h, P, drag, a.dt);
-    k += seg;
-    left -= seg;
   }
   float chk = 0.f;
 #pragma unroll
@@ -100,10 +108,8 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a, DevParams P0) {
 // w + 2W, ... (W = warps in the grid).  A tile is up to 32 consecutive drones of
 // one world (x = first drone, y = count, z = world, w = model), so the branch
 // on the model is uniform across the warp and parameters are a broadcast load.
-template <int INTEG, int CTRL, int MOTOR>
-__global__ void __launch_bounds__(256) step_batched_kernel(StepArgs a, const int4* __restrict__ tiles,
-                                                           int n_tiles) {
-  chain_wait_then_release();
+template <int INTEG, int CTRL, int MOTOR, bool SINGLE>
+__device__ __forceinline__ void run_tiles(const StepArgs& a, const int4* __restrict__ tiles, int n_tiles) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -112,19 +118,38 @@ __global__ void __launch_bounds__(256) step_batched_kernel(StepArgs a, const int
     if (lane < d.y) {
       const DevParams P = a.params[a.set_of_world[d.z]];
       if (d.w == SIM_FIRST_PRINCIPLES) {
-        run_drone<SIM_FIRST_PRINCIPLES, INTEG, CTRL, MOTOR>(a, d.x + lane, P);
+        run_drone<SIM_FIRST_PRINCIPLES, INTEG, CTRL, MOTOR, SINGLE>(a, d.x + lane, P);
       } else if (d.w == SIM_ABSTRACTED) {
-        run_drone<SIM_ABSTRACTED, INTEG, SIM_CTRL_ATTITUDE, MOTOR>(a, d.x + lane, P);
+        run_drone<SIM_ABSTRACTED, INTEG, SIM_CTRL_ATTITUDE, MOTOR, SINGLE>(a, d.x + lane, P);
       } else {
-        run_drone<SIM_ABSTRACTED_NOTHRUST, INTEG, SIM_CTRL_ATTITUDE, MOTOR>(a, d.x + lane, P);
+        run_drone<SIM_ABSTRACTED_NOTHRUST, INTEG, SIM_CTRL_ATTITUDE, MOTOR, SINGLE>(a, d.x + lane, P);
       }
     }
   }
 }
 
 template <int INTEG, int CTRL, int MOTOR>
+__global__ void __launch_bounds__(256) step_batched_kernel(StepArgs a, const int4* __restrict__ tiles,
+                                                           int n_tiles) {
+  chain_wait_then_release();
+  run_tiles<INTEG, CTRL, MOTOR, false>(a, tiles, n_tiles);
+}
+
+// One step per launch (HBM bound): compiled for three 256-thread CTAs per SM (two
+// under RK4, whose stages need more registers) so that more state loads are in
+// flight.
+template <int INTEG, int CTRL, int MOTOR>
+__global__ void __launch_bounds__(256, INTEG == SIM_EULER ? 3 : 2)
+    step_batched_single_kernel(StepArgs a, const int4* __restrict__ tiles, int n_tiles) {
+  chain_wait_then_release();
+  run_tiles<INTEG, CTRL, MOTOR, true>(a, tiles, n_tiles);
+}
+
+template <int INTEG, int CTRL, int MOTOR, bool SINGLE>
 static cudaError_t launch_b(const StepArgs& a, const int4* tiles, int n_tiles, int tpb,
                             cudaStream_t st) {
+  auto kernel = SINGLE ? step_batched_single_kernel<INTEG, CTRL, MOTOR>
+                       : step_batched_kernel<INTEG, CTRL, MOTOR>;
   // occupancy per (device, block size), queried once per kernel variant
   static int cached[16][9] = {};
   int dev = 0;
@@ -134,8 +159,7 @@ static cudaError_t launch_b(const StepArgs& a, const int4* tiles, int n_tiles, i
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = (dev < 16 && slot <= 8) ? cached[dev][slot] : 0;
   if (per_sm == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_batched_kernel<INTEG, CTRL, MOTOR>,
-                                                  tpb, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, tpb, 0);
     if (per_sm < 1) per_sm = 1;
     if (dev < 16 && slot <= 8) cached[dev][slot] = per_sm;
   }
@@ -143,14 +167,19 @@ static cudaError_t launch_b(const StepArgs& a, const int4* tiles, int n_tiles, i
   int grid = sms * per_sm;
   const int need = (n_tiles + warps_per_block - 1) / warps_per_block;
   if (grid > need) grid = need;
-  return launch_chained(step_batched_kernel<INTEG, CTRL, MOTOR>, grid, tpb, st, a, tiles, n_tiles);
+  return launch_chained(kernel, grid, tpb, st, a, tiles, n_tiles);
 }
 
 cudaError_t launch_step_batched(const StepArgs& a, const int4* tiles, int n_tiles, int integrator,
                                 int ctrl, bool general_motor, int tpb, cudaStream_t st) {
-#define CF_B(I, C)                                                              \
-  return general_motor ? launch_b<I, C, MOTOR_GENERAL>(a, tiles, n_tiles, tpb, st) \
-                       : launch_b<I, C, MOTOR_LAG>(a, tiles, n_tiles, tpb, st)
+#define CF_B(I, C)                                                                          \
+  {                                                                                         \
+    if (a.K == 1)                                                                           \
+      return general_motor ? launch_b<I, C, MOTOR_GENERAL, true>(a, tiles, n_tiles, tpb, st) \
+                           : launch_b<I, C, MOTOR_LAG, true>(a, tiles, n_tiles, tpb, st);    \
+    return general_motor ? launch_b<I, C, MOTOR_GENERAL, false>(a, tiles, n_tiles, tpb, st)  \
+                         : launch_b<I, C, MOTOR_LAG, false>(a, tiles, n_tiles, tpb, st);     \
+  }
   if (integrator == SIM_RK4) {
     if (ctrl == SIM_CTRL_ROTOR_SPEED) CF_B(SIM_RK4, SIM_CTRL_ROTOR_SPEED);
     if (ctrl == SIM_CTRL_POSITION) CF_B(SIM_RK4, SIM_CTRL_POSITION);
