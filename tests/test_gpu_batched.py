@@ -99,10 +99,14 @@ def test_config2_full_size_sampled():
     assert_parity(gpu[sample], ref, models[sample])
 
 
-def test_config2_single_step_launches_match_fused():
-    """K = 1 launches (the HBM-bound single-step mode) and one fused launch give
-    identical states on a mixed batch."""
-    bw = W.batched_workload(13, [100, 250, 3, 77], [0, 1, 1, 0], steps=40, K=40, hold=10)
+@pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
+def test_single_step_launches_match_fused(integrator):
+    """K = 1 launches (the HBM-bound single-step mode, a kernel of its own) and one
+    fused launch give identical states on a mixed batch, both at parity with the
+    oracle."""
+    bw = W.batched_workload(13, [100, 250, 3, 77], [0, 1, 1, 0], integrator=integrator, steps=40,
+                            K=40, hold=10)
     a = _gpu_batched(bw, K=40)
     b = _gpu_batched(bw, K=1)
+    assert_parity(b, _oracle_batched(bw), bw.model_of_world[bw.world_of_drone()])
     assert np.array_equal(a, b)
