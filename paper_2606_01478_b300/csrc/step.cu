@@ -11,15 +11,20 @@ namespace cf {
 
 // Programmatic dependent launch of the K-chained step kernels.  A step kernel is
 // launched with programmatic stream serialization, so its CTAs may be scheduled
-// while the previous kernel of the stream drains; griddepcontrol.wait then holds
-// every thread until that kernel has completed and its writes are visible, so
-// every global access of the kernel follows it.  Dependents are released only
-// after the wait: at most two grids of the chain are resident at once, and a
-// dependent is scheduled only once every CTA of this grid has started, so none
-// of this grid's CTAs waits for a slot.  Without the launch attribute (or behind
-// a copy or an ordinary kernel) both instructions return at once.
-__device__ __forceinline__ void chain_wait_then_release() {
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+// while the previous kernel of the stream drains; chain_wait (griddepcontrol.wait)
+// holds every thread until that kernel has completed and its writes are visible,
+// so it precedes every global access of the kernel.  chain_release
+// (griddepcontrol.launch_dependents) lets the next kernel be scheduled once every
+// CTA of this one has released or exited.  The uniform kernel releases after each
+// thread's work, so that the next grid is placed while this one drains, on SMs
+// that are emptying: released at the start, a grid of small CTAs was placed beside
+// CTAs that still ran, stacked two warps on some sub-partitions and left others
+// idle (up to 2x slower launches, varying from run to run).  The persistent
+// batched kernels fill every SM at their occupancy, so the next grid can only be
+// placed where CTAs exit; they release at the start.  Without the launch attribute
+// (or behind a copy or an ordinary kernel) both return at once.
+__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void chain_release() {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
@@ -93,15 +98,17 @@ __device__ __forceinline__ void run_drone(const StepArgs& a, int i, const DevPar
 
 template <int MODEL, int INTEG, int CTRL, int MOTOR, bool PERSET>
 __global__ void __launch_bounds__(256) step_kernel(StepArgs a, DevParams P0) {
-  chain_wait_then_release();
+  chain_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  if constexpr (PERSET) {
-    const DevParams P = a.params[a.set_of_world[i / a.N]];
-    run_drone<MODEL, INTEG, CTRL, MOTOR>(a, i, P);
-  } else {
-    run_drone<MODEL, INTEG, CTRL, MOTOR>(a, i, P0);
+  if (i < a.n) {
+    if constexpr (PERSET) {
+      const DevParams P = a.params[a.set_of_world[i / a.N]];
+      run_drone<MODEL, INTEG, CTRL, MOTOR>(a, i, P);
+    } else {
+      run_drone<MODEL, INTEG, CTRL, MOTOR>(a, i, P0);
+    }
   }
+  chain_release();
 }
 
 // Uneven / mixed batches: warp w of the persistent grid takes tiles w, w + W,
@@ -131,7 +138,8 @@ __device__ __forceinline__ void run_tiles(const StepArgs& a, const int4* __restr
 template <int INTEG, int CTRL, int MOTOR>
 __global__ void __launch_bounds__(256) step_batched_kernel(StepArgs a, const int4* __restrict__ tiles,
                                                            int n_tiles) {
-  chain_wait_then_release();
+  chain_wait();
+  chain_release();
   run_tiles<INTEG, CTRL, MOTOR, false>(a, tiles, n_tiles);
 }
 
@@ -141,7 +149,8 @@ __global__ void __launch_bounds__(256) step_batched_kernel(StepArgs a, const int
 template <int INTEG, int CTRL, int MOTOR>
 __global__ void __launch_bounds__(256, INTEG == SIM_EULER ? 3 : 2)
     step_batched_single_kernel(StepArgs a, const int4* __restrict__ tiles, int n_tiles) {
-  chain_wait_then_release();
+  chain_wait();
+  chain_release();
   run_tiles<INTEG, CTRL, MOTOR, true>(a, tiles, n_tiles);
 }
 
