@@ -188,6 +188,15 @@ int sim_run_host(sim_h h, const float* x0, const float* cmd, int64_t n_blocks, i
 /* Threads per block used by sim_step (default 128; 32..256, multiple of 32). */
 int sim_set_block_size(sim_h h, int threads_per_block);
 
+/* Failure-detection self-test of the library's bounded in-kernel waits (the
+ * rollout adjoint's warp hand-off uses them): one small kernel waits on a barrier
+ * phase that never completes, gives up after the wait's limit (about a second on
+ * B300) and sets SIM_FLAG_TIMEOUT in the handle's status word, as a real
+ * hand-off failure would.  Nothing faults, traps or hangs, and the context stays
+ * usable.  Read the flag with sim_status.  Errors: SIM_EINVAL (h NULL),
+ * SIM_ESTATE (not bound), SIM_ECUDA (launch). */
+int sim_selftest_wait_timeout(sim_h h, void* stream);
+
 /* Synchronise stream, read and clear the device status word (SIM_FLAG_*). */
 int sim_status(sim_h h, uint32_t* flags, void* stream);
 

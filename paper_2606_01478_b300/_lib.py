@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcrazyflo
 
 SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ESTATE = 0, -1, -2, -3, -4
 SIM_FLAG_NONFINITE = 1
+SIM_FLAG_TIMEOUT = 2
 FIRST_PRINCIPLES, ABSTRACTED, ABSTRACTED_NOTHRUST = 0, 1, 2
 EULER, RK4 = 0, 1
 CTRL_ROTOR_SPEED, CTRL_ATTITUDE, CTRL_POSITION, CTRL_TORQUE = 0, 1, 2, 3
@@ -74,6 +75,7 @@ _SIGS = {
     "sim_step_count": (c_int64, [c_void_p]),
     "sim_set_step_count": (c_int, [c_void_p, c_int64]),
     "sim_launch_count": (c_int64, [c_void_p]),
+    "sim_selftest_wait_timeout": (c_int, [c_void_p, c_void_p]),
     "sim_sample_rollouts": (c_int, [c_void_p, c_int, c_int, c_void_p, c_float, c_void_p, c_void_p,
                                     POINTER(c_float), c_int, c_float, c_void_p, c_void_p]),
     "sim_mppi_iteration": (c_int, [c_void_p, POINTER(MppiConfig), c_void_p, c_void_p,

@@ -32,6 +32,8 @@ cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* 
                                int C, int R, float dt, float w_act, const RolloutObjective& obj,
                                const DevParams& P, void* ws,
                                float* loss, bool store_ckpt, cudaStream_t st);
+// Self-test of the bounded in-kernel waits (rollout.cu): sets SIM_FLAG_TIMEOUT.
+cudaError_t launch_wait_selftest(uint32_t* status, cudaStream_t st);
 cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
                                int C, int R, float dt, float w_act, const RolloutObjective& obj,
                                const DevParams& P, void* ws, const float* dL, float* dW, float* dx0,

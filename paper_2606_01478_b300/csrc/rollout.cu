@@ -956,8 +956,11 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
   if (valid && lane < 16) a.loss_w[i] = loss;
 }
 
-// mbarrier helpers for the adjoint's warp hand-off (all threads of a role arrive;
-// waits are bounded: about a second, then the caller flags a timeout).
+// mbarrier helpers for the adjoint's warp hand-off (all threads of a role arrive).
+// Waits are bounded: 2^18 polls of try_wait, which suspends the thread for up to a
+// hardware time limit while the phase is incomplete -- measured on B300 at ~3.8 us,
+// so a wait gives up after about a second (at least ~6 ms if it never suspends),
+// far above the longest wait of the hand-off (~0.1 ms); the caller flags a timeout.
 __device__ __forceinline__ void mbar_init(unsigned long long* m, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
 }
@@ -966,13 +969,26 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* m) {
 }
 __device__ __forceinline__ bool mbar_wait(unsigned long long* m, uint32_t parity) {
   uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it)
+  for (int it = 0; it < (1 << 18) && !done; ++it)
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(smem_addr(m)), "r"(parity)
         : "memory");
   return done != 0;
+}
+
+// Failure-detection self-test of the bounded waits: one warp arrives once on a
+// barrier that expects two arrivals, so the phase never completes; every thread's
+// wait (the same bounded wait as the adjoint's hand-off) gives up, and the kernel
+// sets SIM_FLAG_TIMEOUT and returns.  Nothing faults, traps or hangs.
+__global__ void wait_selftest_kernel(uint32_t* status) {
+  __shared__ unsigned long long m;
+  if (threadIdx.x == 0) mbar_init(&m, 2);
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_arrive(&m);
+  const bool done = mbar_wait(&m, 0);
+  if (!done && threadIdx.x == 0) atomicOr(status, SIM_FLAG_TIMEOUT);
 }
 
 // The adjoint runs two warp roles per CTA.  Warps 0-3 (compute) own 16 drones each:
@@ -1347,6 +1363,11 @@ static cudaError_t launch_rollout_kernel(K kernel, int grid, const ro::RolloutAr
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   kernel<<<grid, threads, smem, st>>>(a, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(uint32_t* status, cudaStream_t st) {
+  ro::wait_selftest_kernel<<<1, 32, 0, st>>>(status);
   return cudaGetLastError();
 }
 

@@ -524,6 +524,15 @@ int sim_run_host(sim_h h, const float* x0, const float* cmd, int64_t n_blocks, i
   return r;
 }
 
+int sim_selftest_wait_timeout(sim_h h, void* stream) {
+  if (!h) return SIM_EINVAL;
+  if (!h->ws) return fail(h, SIM_ESTATE, "sim_bind must come first");
+  cudaError_t e = cf::launch_wait_selftest(h->status, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "wait self-test launch");
+  h->launches++;
+  return SIM_OK;
+}
+
 int sim_status(sim_h h, uint32_t* flags, void* stream) {
   if (!h || !flags) return h ? fail(h, SIM_EINVAL, "flags is NULL") : SIM_EINVAL;
   if (!h->ws) return fail(h, SIM_ESTATE, "sim_bind must come first");

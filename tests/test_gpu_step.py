@@ -1,6 +1,8 @@
 """GPU parity of the fused forward step against the FP64 oracle (through the
 C-ABI), plus properties that hold at any size (fused K == repeated K = 1,
 determinism, layout round trip, non-finite detection)."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -181,6 +183,28 @@ def test_nonfinite_state_sets_status_flag():
     sim2 = make_sim(wl2)
     sim2.run(5, 5)
     assert sim2.status() == 0
+
+
+def test_bounded_wait_gives_up_and_reports_timeout():
+    """Failure detection without a GPU fault: a barrier phase that nothing completes
+    makes the bounded in-kernel wait (the rollout adjoint's hand-off wait) give up;
+    the kernel returns, SIM_FLAG_TIMEOUT reaches the host, and the context stays
+    usable for a normal step afterwards."""
+    import time
+    wl = W.config1(M=100, steps=5, K=5)
+    sim = make_sim(wl)
+    assert sim.status() == 0
+    stream = torch.cuda.current_stream().cuda_stream
+    t0 = time.perf_counter()
+    assert sim.lib.sim_selftest_wait_timeout(sim.h, ctypes.c_void_p(stream)) == L.SIM_OK
+    flags = sim.status()
+    elapsed = time.perf_counter() - t0
+    assert flags & L.SIM_FLAG_TIMEOUT
+    assert elapsed < 20.0  # the wait limit is about a second
+    sim.run(5, 5)
+    assert sim.status() == 0
+    ref = ph.rollout_workload(wl).numpy()
+    assert_parity(sim.get_state().cpu().numpy(), ref, np.zeros(wl.M, np.int64))
 
 
 def test_call_order_and_argument_errors():
