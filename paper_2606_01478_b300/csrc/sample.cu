@@ -258,14 +258,38 @@ __global__ void mppi_update_kernel(MppiArgs a) {
   // elite, ties to the lower index; NaN costs are never selected
   float prev_c = -INFINITY, el_c = INFINITY;
   int prev_i = -1, el_i = 0x7fffffff;
+  // up to 2048 costs per controller: each lane keeps its 64 in registers for all
+  // rounds (slots past S_c hold NaN, never selected); more: read them every round
+  constexpr int REG = 64;
+  const bool in_regs = a.S_c <= 32 * REG;
+  float cr[REG];
+  if (in_regs) {
+#pragma unroll
+    for (int j = 0; j < REG; ++j) {
+      const int s = lane + 32 * j;
+      cr[j] = s < a.S_c ? cc[s] : __int_as_float(0x7fc00000);
+    }
+  }
   for (int e = 0; e < a.n_e; ++e) {
     float bc = INFINITY;
     int bi = 0x7fffffff;
-    for (int s = lane; s < a.S_c; s += 32) {
-      const float v = cc[s];
-      if (v == v && lex_less(prev_c, prev_i, v, s) && lex_less(v, s, bc, bi)) {
-        bc = v;
-        bi = s;
+    if (in_regs) {
+#pragma unroll
+      for (int j = 0; j < REG; ++j) {
+        const float v = cr[j];
+        const int s = lane + 32 * j;
+        if (v == v && lex_less(prev_c, prev_i, v, s) && lex_less(v, s, bc, bi)) {
+          bc = v;
+          bi = s;
+        }
+      }
+    } else {
+      for (int s = lane; s < a.S_c; s += 32) {
+        const float v = cc[s];
+        if (v == v && lex_less(prev_c, prev_i, v, s) && lex_less(v, s, bc, bi)) {
+          bc = v;
+          bi = s;
+        }
       }
     }
 #pragma unroll
