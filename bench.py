@@ -390,15 +390,54 @@ def run_b300(args, wl):
     }
     line["config"]["tpb"] = tuned["tpb"]
     line["autotune"] = tuned
+    c0_final = None
     if not args.no_extra:
-        line["extra"] = {"config2": measure_config2(dev), "config3": measure_config3(dev),
+        c0, c0_final = measure_config0(dev)
+        line["extra"] = {"config0": c0, "config2": measure_config2(dev), "config3": measure_config3(dev),
                          "config4": measure_config4(dev), "mppi": measure_mppi(dev),
                          "bptt_training": measure_bptt_training(dev), "depth": measure_depth(dev)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
         line["error_vs_fp64"] = error_vs_fp64(wl, out_host.numpy())
+        if c0_final is not None:
+            line["extra"]["config0"]["error_vs_fp64"] = error_vs_fp64(W.config0(), c0_final, n_drones=1)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_config0(dev, reps: int = 5):
+    """Config 0: one drone under the position controller to a hover setpoint, Euler at
+    500 Hz, 1000 steps in one launch -- one thread's chain of 1000 dependent steps, so
+    latency bound.  Returns the record and the final state (its error against the FP64
+    oracle is taken in the CPU leg)."""
+    from paper_2606_01478_b300 import Sim
+    wl = W.config0()
+    sim = Sim(wl.M, wl.N, int(wl.model_of_world[0]), wl.integrator, wl.dt, ctrl=wl.ctrl,
+              max_cmd_blocks=wl.cmd.shape[0], device=dev)
+    sim.set_params(wl.params, wl.param_set_of_world)
+    x0 = torch.tensor(wl.x0, dtype=torch.float32, device=dev)
+    cmd = torch.tensor(wl.cmd, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    times = []
+    for r in range(reps + 1):
+        sim.set_state(x0)
+        sim.set_commands(cmd, wl.hold)
+        torch.cuda._sleep(1_000_000)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.run(wl.steps, wl.steps)
+        e1.record(stream)
+        e1.synchronize()
+        if r:
+            times.append(e0.elapsed_time(e1))
+    final = sim.get_state().cpu().numpy()
+    assert sim.status() == 0
+    ms = statistics.median(times)
+    return {"workload": "c0_1x1_fp_euler_position_1000", "ms_per_rollout": ms,
+            "us_per_step": ms * 1e3 / wl.steps, "value": wl.M * wl.N * wl.steps / (ms / 1e3),
+            "unit": UNIT, "launches": 1,
+            "note": "one drone: one thread's dependent chain, latency bound"}, final
 
 
 def measure_config2(dev, reps: int = 3) -> dict:
