@@ -390,9 +390,10 @@ def run_b300(args, wl):
     }
     line["config"]["tpb"] = tuned["tpb"]
     line["autotune"] = tuned
-    c0_final = None
+    c0_final = c3_sub = None
     if not args.no_extra:
         c0, c0_final = measure_config0(dev)
+        c3_sub = config3_subset_gradients(dev)
         line["extra"] = {"config0": c0, "config2": measure_config2(dev), "config3": measure_config3(dev),
                          "config4": measure_config4(dev), "mppi": measure_mppi(dev),
                          "bptt_training": measure_bptt_training(dev), "depth": measure_depth(dev)}
@@ -401,8 +402,45 @@ def run_b300(args, wl):
         line["error_vs_fp64"] = error_vs_fp64(wl, out_host.numpy())
         if c0_final is not None:
             line["extra"]["config0"]["error_vs_fp64"] = error_vs_fp64(W.config0(), c0_final, n_drones=1)
+        if c3_sub is not None:
+            line["extra"]["config3"]["gradient_error_vs_fp64"] = gradient_error_vs_fp64(*c3_sub)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def config3_subset_gradients(dev, M: int = 64):
+    """Gradients of the config-3 recipe on M worlds (H = 250, C = 25) in both MLP
+    operand modes, kept for the comparison with the FP64 oracle in the CPU leg."""
+    from paper_2606_01478_b300 import EULER, FIRST_PRINCIPLES, Sim
+    from paper_2606_01478_b300.rollout import PolicyRollout, pack_policy
+    rw = W.config3(M=M)
+    out = {}
+    for prec in ("hilo", "bf16"):
+        sim = Sim(rw.M, 1, FIRST_PRINCIPLES, EULER, rw.dt, device=dev)
+        sim.set_params(rw.params)
+        runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act, precision=prec)
+        x0 = torch.tensor(rw.x0, dtype=torch.float32, device=dev)
+        wb = torch.tensor(pack_policy(rw.weights), dtype=torch.float32, device=dev).to(torch.bfloat16)
+        p_ref = torch.tensor(rw.p_ref, dtype=torch.float32, device=dev).contiguous()
+        loss, dW, dx0 = runner.grad(x0, wb, p_ref)
+        out[prec] = (float(loss.item()), dW.cpu().numpy().astype(np.float64),
+                     dx0.cpu().numpy().astype(np.float64))
+    return rw, out
+
+
+def gradient_error_vs_fp64(rw, gpu: dict) -> dict:
+    """Relative errors of the GPU loss and gradients (norm-wise over dW and over
+    dx0) against the FP64 oracle's adjoint, from the float32 inputs the GPU got."""
+    from oracle import policy as po
+    x0 = rw.x0.astype(np.float32).astype(np.float64)
+    p_ref = rw.p_ref.astype(np.float32).astype(np.float64)
+    L, _, dW_ref, dx_ref = po.rollout_grad(x0, rw.weights, p_ref, rw.params, rw.dt, rw.H, rw.w_act)
+    g = po.pack(dW_ref)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+    return {"worlds": int(rw.M), "H": int(rw.H), "C": int(rw.C),
+            **{prec: {"loss": abs(v[0] - L) / abs(L), "dW": rel(v[1], g), "dx0": rel(v[2][:, :17], dx_ref[:, :17])}
+               for prec, v in gpu.items()},
+            "bar": 1e-3, "reference": "FP64 oracle adjoint from the same float32 inputs"}
 
 
 def measure_config0(dev, reps: int = 5):
