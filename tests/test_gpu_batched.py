@@ -85,12 +85,19 @@ def test_config2_full_size_sampled():
     """Config 2 at full size: 1000 worlds x 4000 drones (4M), even worlds
     first-principles, odd worlds abstracted with per-world coefficients,
     Euler, 200 steps in one launch; the oracle checks 64 sampled drones of each
-    model."""
+    model.  The same 200 steps as 200 single-step launches (the HBM-bound mode,
+    a kernel of its own) give the same bits on every drone."""
     wl = W.config2()
     sim = make_sim(wl)
     sim.run(wl.steps, wl.K)
-    gpu = sim.get_state().cpu().numpy()
+    fused = sim.get_state()
+    gpu = fused.cpu().numpy()
     assert sim.status() == 0
+    single = make_sim(wl)
+    single.run(wl.steps, 1)
+    assert single.status() == 0
+    assert torch.equal(single.get_state(), fused)
+    del single
     rng = np.random.default_rng(2)
     models = wl.model_of_world[np.arange(wl.M * wl.N) // wl.N]
     sample = np.concatenate([rng.choice(np.nonzero(models == m)[0], 64, replace=False)
