@@ -273,7 +273,7 @@ def run_b300(args, wl):
         tuned = {"tpb": args.tpb, "K": wl.K, "source": "--tpb"}
     else:
         from paper_2606_01478_b300 import autotune
-        tuned = autotune.tune_step(sim, wl.steps, tag="config1", Ks=(wl.K,), reps=2)
+        tuned = autotune.tune_step(sim, wl.steps, tag="attitude_swarm", Ks=(wl.K,), reps=2)
         tuned = {k: v for k, v in tuned.items() if k != "table"}
     n_launch = (wl.steps + wl.K - 1) // wl.K
 
@@ -390,30 +390,30 @@ def run_b300(args, wl):
     }
     line["config"]["tpb"] = tuned["tpb"]
     line["autotune"] = tuned
-    c0_final = c3_sub = None
+    sd_final = bptt_sub = None
     if not args.no_extra:
-        c0, c0_final = measure_config0(dev)
-        c3_sub = config3_subset_gradients(dev)
-        line["extra"] = {"config0": c0, "config2": measure_config2(dev), "config3": measure_config3(dev),
-                         "config4": measure_config4(dev), "mppi": measure_mppi(dev),
+        sd, sd_final = measure_single_drone(dev)
+        bptt_sub = bptt_subset_gradients(dev)
+        line["extra"] = {"single_drone": sd, "mixed_swarm": measure_mixed_swarm(dev), "policy_bptt": measure_policy_bptt(dev),
+                         "sampling": measure_sampling(dev), "mppi": measure_mppi(dev),
                          "bptt_training": measure_bptt_training(dev), "depth": measure_depth(dev)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
         line["error_vs_fp64"] = error_vs_fp64(wl, out_host.numpy())
-        if c0_final is not None:
-            line["extra"]["config0"]["error_vs_fp64"] = error_vs_fp64(W.config0(), c0_final, n_drones=1)
-        if c3_sub is not None:
-            line["extra"]["config3"]["gradient_error_vs_fp64"] = gradient_error_vs_fp64(*c3_sub)
+        if sd_final is not None:
+            line["extra"]["single_drone"]["error_vs_fp64"] = error_vs_fp64(W.position_hold_single(), sd_final, n_drones=1)
+        if bptt_sub is not None:
+            line["extra"]["policy_bptt"]["gradient_error_vs_fp64"] = gradient_error_vs_fp64(*bptt_sub)
     print(json.dumps(line), flush=True)
     return 0
 
 
-def config3_subset_gradients(dev, M: int = 64):
-    """Gradients of the config-3 recipe on M worlds (H = 250, C = 25) in both MLP
+def bptt_subset_gradients(dev, M: int = 64):
+    """Gradients of the BPTT recipe on M worlds (H = 250, C = 25) in both MLP
     operand modes, kept for the comparison with the FP64 oracle in the CPU leg."""
     from paper_2606_01478_b300 import EULER, FIRST_PRINCIPLES, Sim
     from paper_2606_01478_b300.rollout import PolicyRollout, pack_policy
-    rw = W.config3(M=M)
+    rw = W.policy_bptt(M=M)
     out = {}
     for prec in ("hilo", "bf16"):
         sim = Sim(rw.M, 1, FIRST_PRINCIPLES, EULER, rw.dt, device=dev)
@@ -443,13 +443,13 @@ def gradient_error_vs_fp64(rw, gpu: dict) -> dict:
             "bar": 1e-3, "reference": "FP64 oracle adjoint from the same float32 inputs"}
 
 
-def measure_config0(dev, reps: int = 5):
-    """Config 0: one drone under the position controller to a hover setpoint, Euler at
+def measure_single_drone(dev, reps: int = 5):
+    """One drone under the position controller to a hover setpoint, Euler at
     500 Hz, 1000 steps in one launch -- one thread's chain of 1000 dependent steps, so
     latency bound.  Returns the record and the final state (its error against the FP64
     oracle is taken in the CPU leg)."""
     from paper_2606_01478_b300 import Sim
-    wl = W.config0()
+    wl = W.position_hold_single()
     sim = Sim(wl.M, wl.N, int(wl.model_of_world[0]), wl.integrator, wl.dt, ctrl=wl.ctrl,
               max_cmd_blocks=wl.cmd.shape[0], device=dev)
     sim.set_params(wl.params, wl.param_set_of_world)
@@ -472,19 +472,19 @@ def measure_config0(dev, reps: int = 5):
     final = sim.get_state().cpu().numpy()
     assert sim.status() == 0
     ms = statistics.median(times)
-    return {"workload": "c0_1x1_fp_euler_position_1000", "ms_per_rollout": ms,
+    return {"workload": "single_1x1_fp_euler_position_1000", "ms_per_rollout": ms,
             "us_per_step": ms * 1e3 / wl.steps, "value": wl.M * wl.N * wl.steps / (ms / 1e3),
             "unit": UNIT, "launches": 1,
             "note": "one drone: one thread's dependent chain, latency bound"}, final
 
 
-def measure_config2(dev, reps: int = 3) -> dict:
-    """Config 2 (1000 worlds x 4000 drones, 50/50 first-principles / abstracted,
+def measure_mixed_swarm(dev, reps: int = 3) -> dict:
+    """The mixed swarm (1000 worlds x 4000 drones, 50/50 first-principles / abstracted,
     Euler, 200 steps) in both modes: one fused launch of K = 200 (FP32-issue
     bound) and 200 launches of K = 1 (HBM bound)."""
     from paper_2606_01478_b300 import Sim
     from paper_2606_01478_b300 import autotune
-    wl = W.config2()
+    wl = W.mixed_swarm_euler()
     n = wl.M * wl.N
     sim = Sim.batched(np.full(wl.M, wl.N), wl.model_of_world, wl.integrator, wl.dt, ctrl=wl.ctrl,
                       max_cmd_blocks=wl.cmd.shape[0], device=dev)
@@ -494,7 +494,7 @@ def measure_config2(dev, reps: int = 3) -> dict:
     del wl.x0, wl.cmd
     sim.set_state(x0)
     sim.set_commands(cmd, wl.hold)
-    tuned = autotune.tune_step(sim, wl.steps, tag="config2", Ks=(1, 200), reps=1)
+    tuned = autotune.tune_step(sim, wl.steps, tag="mixed_swarm", Ks=(1, 200), reps=1)
     stream = torch.cuda.current_stream(dev)
     n_fp = n // 2
     n_abs = n - n_fp
@@ -538,7 +538,7 @@ def measure_config2(dev, reps: int = 3) -> dict:
                                "note": "abstracted drones also issue 6 MUFU sin/cos per step"}
         out[f"fused_K{K}" if K > 1 else "single_step_K1"] = rec
     assert sim.status() == 0
-    out["workload"] = "c2_1000x4000_mixed_euler_attitude_200"
+    out["workload"] = "swarm_1000x4000_mixed_euler_attitude_200"
     out["autotune"] = {k: v for k, v in tuned.items() if k != "table"}
     return out
 
@@ -564,13 +564,13 @@ def _time_ms(fn, reps: int, dev) -> float:
 MLP_FLOP = 2.0 * (13 * 64 + 64 * 64 + 64 * 4)
 
 
-def measure_config3(dev, reps: int = 3) -> dict:
-    """Config 3 (8192 drones, policy MLP in the loop, Euler at 500 Hz, H = 250,
+def measure_policy_bptt(dev, reps: int = 3) -> dict:
+    """The BPTT workload (8192 drones, policy MLP in the loop, Euler at 500 Hz, H = 250,
     checkpoints every C = 25): forward rollout, forward + adjoint (BPTT), and
     plain forward stepping of the same drones without the policy."""
     from paper_2606_01478_b300 import EULER, FIRST_PRINCIPLES, Sim
     from paper_2606_01478_b300.rollout import PolicyRollout, pack_policy
-    rw = W.config3()
+    rw = W.policy_bptt()
     sim = Sim(rw.M, 1, FIRST_PRINCIPLES, EULER, rw.dt, device=dev)
     sim.set_params(rw.params)
     runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act)
@@ -621,12 +621,12 @@ def measure_config3(dev, reps: int = 3) -> dict:
 SAMPLE_FLOP_PER_STEP = 637.0 + 25.0 + 15.0 + 10.0
 
 
-def measure_config4(dev, reps: int = 3) -> dict:
-    """Config 4 (512 worlds, log-uniform drone counts, 256 samples, 50 RK4
+def measure_sampling(dev, reps: int = 3) -> dict:
+    """The uneven sampling workload (512 worlds, log-uniform drone counts, 256 samples, 50 RK4
     steps): one persistent sampling launch per outer iteration, replayed from a
     CUDA graph with a fresh device seed each time; block size autotuned."""
     from paper_2606_01478_b300 import RK4, Sim
-    wl = W.config4()
+    wl = W.uneven_sampling_rk4()
     n = len(wl.x0)
     sim = Sim.batched(wl.n_per_world, np.zeros(wl.M, np.int32), RK4, wl.dt, device=dev)
     sim.set_params(wl.params)
@@ -707,7 +707,7 @@ def measure_bptt_training(dev, reps: int = 3) -> dict:
     from paper_2606_01478_b300.rollout import TRACKING_REWARD, PolicyRollout, pack_policy
     from paper_2606_01478_b300.train import PolicyTrainer
     M, H, C, R, iters, lr = 16, 40, 10, 10, 156, 4.6e-2
-    rw = W.config3(M=M, H=H, C=C, repeat=R)
+    rw = W.policy_bptt(M=M, H=H, C=C, repeat=R)
     sim = Sim(M, 1, FIRST_PRINCIPLES, EULER, rw.dt, device=dev)
     sim.set_params(rw.params)
     runner = PolicyRollout(sim, H, C, rw.w_act, reward=TRACKING_REWARD, action_repeat=R)
@@ -743,13 +743,13 @@ def measure_bptt_training(dev, reps: int = 3) -> dict:
 
 def measure_depth(dev, reps: int = 3) -> dict:
     """Depth images at the paper's scale (64 x 64 rays, 1024 environments, one
-    camera per drone): config 4's 32 obstacles as spheres plus 8 boxes and the
+    camera per drone): the sampling workload's 32 obstacles as spheres plus 8 boxes and the
     ground; frames per second of one batched launch."""
     import math
     from paper_2606_01478_b300 import RK4, Sim
     rng = np.random.default_rng(1006)
     n = 1024
-    wl4 = W.config4(M=8)
+    wl4 = W.uneven_sampling_rk4(M=8)
     P = W.crazyflie_params()
     x = np.zeros((n, 20))
     x[:, 0:3] = rng.uniform([-1.5, -1.5, 0.5], [1.5, 1.5, 3.5], (n, 3))
@@ -776,8 +776,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--tpb", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the config-2/3/4 measurements")
-    ap.add_argument("--only", choices=["c2", "c3", "c4", "mppi", "bptt", "depth"], default=None,
+    ap.add_argument("--no-extra", action="store_true", help="skip the measurements beside the headline")
+    ap.add_argument("--only", choices=["mixed", "bptt", "sampling", "mppi", "training", "depth"], default=None,
                     help="run one extra workload alone and print its record (for profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
@@ -786,12 +786,12 @@ def main(argv=None):
         local = int(os.environ.get("LOCAL_RANK", "0"))
         torch.cuda.set_device(local)
         dev = torch.device("cuda", local)
-        fn = {"c2": measure_config2, "c3": measure_config3, "c4": measure_config4,
-              "mppi": measure_mppi, "bptt": measure_bptt_training, "depth": measure_depth}[args.only]
+        fn = {"mixed": measure_mixed_swarm, "bptt": measure_policy_bptt, "sampling": measure_sampling,
+              "mppi": measure_mppi, "training": measure_bptt_training, "depth": measure_depth}[args.only]
         print(json.dumps({"only": args.only, "record": fn(dev, reps=args.steps)}), flush=True)
         return 0
     rank = int(os.environ.get("RANK", "0"))
-    wl = W.config1(seed=1001 + 7919 * rank)
+    wl = W.attitude_swarm_rk4(seed=1001 + 7919 * rank)
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_b300(args, wl)

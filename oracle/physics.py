@@ -9,7 +9,7 @@ Paper passages followed (Materials and Methods of arXiv 2606.01478):
     q' = 1/2 q (x) [w; 0], m v' = f_sum, J w' = t_sum - w x J w
   * per-rotor thrust and drag counter-torque, "second-order polynomial" in the
     rotor speed (text before Eq. 5): f_i = kf W_i^2 + kf1 W_i + kf0,
-    t_i = km W_i^2 + km1 W_i (the configs use kf1 = kf0 = km1 = 0)
+    t_i = km W_i^2 + km1 W_i (the benchmark workloads use kf1 = kf0 = km1 = 0)
   * gyroscopic and reaction torques of the rotors, Eq. 5 (garbled in the
     paper; read from the rotors' angular momentum h = J_p (2 pi / 60)
     sum_i sigma_i W_i e_z with spin direction sigma_i = -s_i: tau_gyro = -w x h,

@@ -66,7 +66,7 @@ def test_batched_matches_uniform_path():
     fuse multiply-adds differently: agreement to float32 rounding, not bits --
     per field, 1/100 of the field's parity tolerance against the FP64 oracle
     plus 1e-6 relative (a few float32 ulp)."""
-    wl = W.config1(M=777, steps=90, K=45)
+    wl = W.attitude_swarm_rk4(M=777, steps=90, K=45)
     a = make_sim(wl)
     a.run(90, 45)
     sa = a.get_state().cpu().numpy()
@@ -81,13 +81,13 @@ def test_batched_matches_uniform_path():
         np.testing.assert_allclose(sb[:, sl], sa[:, sl], rtol=1e-6, atol=1e-2 * TOL_FP[k], err_msg=k)
 
 
-def test_config2_full_size_sampled():
-    """Config 2 at full size: 1000 worlds x 4000 drones (4M), even worlds
+def test_mixed_swarm_full_size_sampled():
+    """The mixed swarm at full size: 1000 worlds x 4000 drones (4M), even worlds
     first-principles, odd worlds abstracted with per-world coefficients,
     Euler, 200 steps in one launch; the oracle checks 64 sampled drones of each
     model.  The same 200 steps as 200 single-step launches (the HBM-bound mode,
     a kernel of its own) give the same bits on every drone."""
-    wl = W.config2()
+    wl = W.mixed_swarm_euler()
     sim = make_sim(wl)
     sim.run(wl.steps, wl.K)
     fused = sim.get_state()

@@ -97,7 +97,7 @@ def test_free_fall_closed_form(integrator):
 @pytest.mark.parametrize("reward", [None, po.TRACKING_REWARD], ids=["squared", "reward"])
 def test_rollout_single_step_horizon(reward):
     """H = C = 1 on 65 drones (one full CTA of 64 and a one-drone tail)."""
-    rw = W.config3(seed=70, M=65, H=1, C=1)
+    rw = W.policy_bptt(seed=70, M=65, H=1, C=1)
     sim = Sim(rw.M, 1, FIRST_PRINCIPLES, EULER, rw.dt)
     sim.set_params(rw.params)
     runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act, reward=reward)

@@ -28,7 +28,7 @@ def _run(wl, tpb=None):
 
 @pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
 def test_rotor_inertia_and_polynomial_curves(integrator):
-    wl = W.config1(M=400, steps=150, K=50)
+    wl = W.attitude_swarm_rk4(M=400, steps=150, K=50)
     wl.integrator = integrator
     wl.params = [W.crazyflie_params(J_p=3e-8, kf1=1.5e-7, kf0=-0.002, km1=4e-9, cv_up=40.0,
                                     cv_down=25.0, cd_up=2e-4)]
@@ -39,7 +39,7 @@ def test_rotor_inertia_and_polynomial_curves(integrator):
 
 @pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
 def test_torque_interface(integrator):
-    wl = W.config1(M=300, steps=120, K=40)
+    wl = W.attitude_swarm_rk4(M=300, steps=120, K=40)
     wl.integrator, wl.ctrl = integrator, ph.CTRL_TORQUE
     p = W.crazyflie_params()
     rng = np.random.default_rng(6)
@@ -53,7 +53,7 @@ def test_torque_interface(integrator):
 
 @pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
 def test_abstracted_without_thrust_dynamics(integrator):
-    wl = W.config2(M=4, N=150, steps=120, K=60)
+    wl = W.mixed_swarm_euler(M=4, N=150, steps=120, K=60)
     wl.integrator = integrator
     wl.model_of_world = np.full(wl.M, 2, np.int32)
     wl.x0[:, 3:6] = np.random.default_rng(2).uniform(-0.5, 0.5, (wl.M * wl.N, 3))

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 
 def test_graph_replay_matches_eager():
-    wl = W.config1(M=2000, steps=300, K=100)
+    wl = W.attitude_swarm_rk4(M=2000, steps=300, K=100)
     eager = make_sim(wl)
     eager.run(300, 100)
     ref = eager.get_state().cpu()
@@ -53,7 +53,7 @@ def test_graph_replay_uneven_mixed():
 
 def test_autotuner_restores_state_and_caches(tmp_path, monkeypatch):
     monkeypatch.setenv("CRAZYFLOW_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
-    wl = W.config1(M=4096, steps=100, K=100)
+    wl = W.attitude_swarm_rk4(M=4096, steps=100, K=100)
     sim = make_sim(wl)
     before = sim.get_state().clone()
     best = autotune.tune_step(sim, 100, tag="test", tpbs=(32, 128), Ks=(10, 50, 100), reps=1)

@@ -63,7 +63,7 @@ def _check(rw, loss, dW, dx0, drones=None, reward=None):
 
 def test_rollout_gradient_small_ragged():
     """200 drones (ragged last CTA of 8), H = 30, C = 7 (last segment short)."""
-    rw = W.config3(seed=31, M=200, H=30, C=7)
+    rw = W.policy_bptt(seed=31, M=200, H=30, C=7)
     sim, runner, x0, w, p_ref = _gpu_inputs(rw)
     loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
     assert torch.isfinite(dW).all() and torch.isfinite(dx0).all()
@@ -72,20 +72,20 @@ def test_rollout_gradient_small_ragged():
 
 
 @pytest.mark.parametrize("C", [25, 250, 1])
-def test_rollout_gradient_config3_horizon(C):
-    """Config-3 horizon (H = 250 Euler steps at 500 Hz) at 256 drones, with
+def test_rollout_gradient_full_horizon(C):
+    """The full BPTT horizon (H = 250 Euler steps at 500 Hz) at 256 drones, with
     checkpoint intervals 25 (the configured), 250 (one segment) and 1."""
-    rw = W.config3(seed=32, M=256, H=250, C=C)
+    rw = W.policy_bptt(seed=32, M=256, H=250, C=C)
     sim, runner, x0, w, p_ref = _gpu_inputs(rw)
     loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
     _check(rw, loss.item(), dW.cpu().numpy(), dx0.cpu().numpy().astype(np.float64))
 
 
-def test_rollout_full_config3_sampled_and_linearity():
-    """Full config 3 (8192 drones, H = 250, C = 25): dL/dx0 of 16 sampled
+def test_rollout_full_size_sampled_and_linearity():
+    """The full BPTT workload (8192 drones, H = 250, C = 25): dL/dx0 of 16 sampled
     drones against the oracle (exact per drone), and dW consistent with the
     drone-count-weighted gradients of two disjoint halves."""
-    rw = W.config3()
+    rw = W.policy_bptt()
     sim, runner, x0, w, p_ref = _gpu_inputs(rw)
     wb = w.to(torch.bfloat16)
     loss, dW, dx0 = runner.grad(x0, wb, p_ref)
@@ -104,7 +104,7 @@ def test_rollout_full_config3_sampled_and_linearity():
 
 
 def test_rollout_deterministic():
-    rw = W.config3(seed=33, M=300, H=40, C=10)
+    rw = W.policy_bptt(seed=33, M=300, H=40, C=10)
     sim, runner, x0, w, p_ref = _gpu_inputs(rw)
     wb = w.to(torch.bfloat16)
     a = runner.grad(x0, wb, p_ref)
@@ -114,7 +114,7 @@ def test_rollout_deterministic():
 
 
 def test_autograd_function_matches_direct_call():
-    rw = W.config3(seed=34, M=128, H=20, C=5)
+    rw = W.policy_bptt(seed=34, M=128, H=20, C=5)
     sim, runner, x0, w, p_ref = _gpu_inputs(rw)
     loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
     xr = x0.clone().requires_grad_(True)
@@ -131,7 +131,7 @@ def test_autograd_function_matches_direct_call():
 def test_zero_policy_hover_loss():
     """Zero weights: a = 0 (hover command); drones at hover on a stationary
     reference displaced by a constant offset give loss H |offset|^2."""
-    rw = W.config3(seed=35, M=64, H=50, C=10)
+    rw = W.policy_bptt(seed=35, M=64, H=50, C=10)
     rw.weights = {k: np.zeros(po.SIZES[k]) for k in po.NAMES}
     rw.x0[:, 7:13] = 0
     rw.x0[:, 3:7] = [0, 0, 0, 1]
@@ -151,7 +151,7 @@ def test_zero_policy_hover_loss():
 def test_reward_gradient_small_ragged(reward):
     """The paper's tracking reward: 200 drones (ragged last CTA), H = 30, C = 7
     (the smoothness adjoint crosses segment boundaries)."""
-    rw = W.config3(seed=35, M=200, H=30, C=7)
+    rw = W.policy_bptt(seed=35, M=200, H=30, C=7)
     sim, runner, x0, w, p_ref = _gpu_inputs(rw, reward)
     loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
     assert torch.isfinite(dW).all() and torch.isfinite(dx0).all()
@@ -162,11 +162,11 @@ def test_reward_gradient_small_ragged(reward):
 def test_reward_gradient_training_shape(C):
     """The paper's BPTT setting (16 environments, 40 steps) and a long horizon
     (256 drones, H = 250, C = 25)."""
-    rw = W.config3(seed=36, M=16, H=40, C=C)
+    rw = W.policy_bptt(seed=36, M=16, H=40, C=C)
     sim, runner, x0, w, p_ref = _gpu_inputs(rw, TRACKING_REWARD)
     loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
     _check(rw, loss.item(), dW.cpu().numpy(), dx0.cpu().numpy().astype(np.float64), reward=TRACKING_REWARD)
-    rw = W.config3(seed=37, M=256, H=250, C=25)
+    rw = W.policy_bptt(seed=37, M=256, H=250, C=25)
     sim, runner, x0, w, p_ref = _gpu_inputs(rw, TRACKING_REWARD)
     loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
     _check(rw, loss.item(), dW.cpu().numpy(), dx0.cpu().numpy().astype(np.float64), reward=TRACKING_REWARD)
@@ -175,7 +175,7 @@ def test_reward_gradient_training_shape(C):
 def test_objectives_share_a_handle():
     """Two runners with different objectives on one handle: each call applies its
     own objective (the results equal those of separate handles)."""
-    rw = W.config3(seed=38, M=96, H=24, C=6)
+    rw = W.policy_bptt(seed=38, M=96, H=24, C=6)
     sim, sq, x0, w, p_ref = _gpu_inputs(rw)
     rew = PolicyRollout(sim, rw.H, rw.C, rw.w_act, reward=TRACKING_REWARD)
     wb = w.to(torch.bfloat16)
@@ -196,8 +196,8 @@ def test_held_action_gradient(reward):
     """Policy actions held for R = 10 physics steps (50 Hz policy, 500 Hz
     physics): 100 drones (ragged), H = 16 policy steps, C = 5 (ragged last
     segment); and the paper's training shape, 16 environments x 40 steps."""
-    for rw in (W.config3(seed=39, M=100, H=16, C=5, repeat=10),
-               W.config3(seed=40, M=16, H=40, C=10, repeat=10)):
+    for rw in (W.policy_bptt(seed=39, M=100, H=16, C=5, repeat=10),
+               W.policy_bptt(seed=40, M=16, H=40, C=10, repeat=10)):
         sim, runner, x0, w, p_ref = _gpu_inputs(rw, reward)
         loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
         assert torch.isfinite(dW).all()
@@ -205,12 +205,12 @@ def test_held_action_gradient(reward):
 
 
 def test_plain_bf16_operands_mode():
-    """SIM_MLP_BF16 (plain bf16 tensor-core operands) at the config-3 horizon
+    """SIM_MLP_BF16 (plain bf16 tensor-core operands) at the full BPTT horizon
     (H = 250, C = 25, 256 drones): gradients against the FP64 oracle within
     1e-2 norm-wise relative (a regression bound; the measured errors are
     printed), and measurably less accurate than the default hi + lo split, so
     the mode really changes the arithmetic."""
-    rw = W.config3(seed=41, M=256, H=250, C=25)
+    rw = W.policy_bptt(seed=41, M=256, H=250, C=25)
     x0, p_ref = _as_oracle_inputs(rw)
     L_ref, _, dW_ref, dx_ref = po.rollout_grad(x0, rw.weights, p_ref, rw.params, rw.dt, rw.H, rw.w_act)
     errs = {}

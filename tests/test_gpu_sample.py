@@ -40,7 +40,7 @@ def _oracle(x0, goals, obs, P, S, H, sigma, seed, w_obs, n_per_world, drones, sa
 
 
 def _scene(seed, n_per_world, **kw):
-    wl = W.config4(seed=seed, M=len(n_per_world), **kw)
+    wl = W.uneven_sampling_rk4(seed=seed, M=len(n_per_world), **kw)
     n = int(np.sum(n_per_world))
     rng = np.random.default_rng(seed)
     x0 = wl.x0[:1].repeat(n, 0)
@@ -129,11 +129,11 @@ def test_nominal_sequence_and_uniform_handle():
     np.testing.assert_allclose(cost.cpu().numpy(), ref, rtol=RTOL, atol=1e-4)
 
 
-def test_config4_full_size_sampled():
-    """Config 4: 512 worlds with log-uniform drone counts in [1, 4000], 256
+def test_uneven_sampling_full_size_sampled():
+    """The uneven sampling workload: 512 worlds with log-uniform drone counts in [1, 4000], 256
     samples each, 50 RK4 steps; 64 sampled (drone, sample) pairs against the
     oracle."""
-    wl = W.config4()
+    wl = W.uneven_sampling_rk4()
     sim = _sim_for(wl.n_per_world, wl.params, wl.x0)
     goals = torch.tensor(wl.goals, dtype=torch.float32, device="cuda")
     cost = sim.sample_rollouts(wl.S, wl.H, _seed_tensor(wl.seed), wl.sigma, goals, wl.obstacles,

@@ -31,10 +31,10 @@ def _run_gpu(wl, steps=None, K=None, tpb=None):
     return out, sim
 
 
-def test_config0_position_error_below_1e4_m():
+def test_single_drone_position_error_below_1e4_m():
     """1 world x 1 drone, position PID, Euler at 500 Hz, 1000 steps in ONE
     launch: |p_GPU - p_FP64| <= 1e-4 m (the stated bar)."""
-    wl = W.config0()
+    wl = W.position_hold_single()
     gpu, sim = _run_gpu(wl)
     assert sim.launches >= 1
     ref = ph.rollout_workload(wl).numpy()
@@ -43,11 +43,11 @@ def test_config0_position_error_below_1e4_m():
 
 
 @pytest.mark.parametrize("tpb", [32, 128, 256])
-def test_config1_small_rk4_attitude(tpb):
-    """Config-1 recipe at 1000 drones (ragged tail for every block size),
+def test_attitude_swarm_small_rk4(tpb):
+    """The RK4 attitude-swarm recipe at 1000 drones (ragged tail for every block size),
     RK4, 250 steps as launches of K = 100 (command blocks of 50 change inside
     and across launches)."""
-    wl = W.config1(M=1000, steps=250, K=100)
+    wl = W.attitude_swarm_rk4(M=1000, steps=250, K=100)
     gpu, _ = _run_gpu(wl, tpb=tpb)
     ref = ph.rollout_workload(wl).numpy()
     assert_parity(gpu, ref, _models_of(wl))
@@ -56,7 +56,7 @@ def test_config1_small_rk4_attitude(tpb):
 @pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
 @pytest.mark.parametrize("ctrl", [ph.CTRL_ROTOR_SPEED, ph.CTRL_ATTITUDE, ph.CTRL_POSITION])
 def test_first_principles_all_controls(integrator, ctrl):
-    wl = W.config1(M=333, steps=120, K=37)
+    wl = W.attitude_swarm_rk4(M=333, steps=120, K=37)
     wl.integrator, wl.ctrl = integrator, ctrl
     rng = np.random.default_rng(5)
     if ctrl == ph.CTRL_ROTOR_SPEED:
@@ -75,7 +75,7 @@ def test_first_principles_all_controls(integrator, ctrl):
 def test_general_motor_and_drag(integrator):
     """Asymmetric rotor coefficients with quadratic terms (Eq. 6 general form)
     and non-zero body drag, per-world parameter sets."""
-    wl = W.config1(M=300, steps=100, K=50)
+    wl = W.attitude_swarm_rk4(M=300, steps=100, K=50)
     wl.integrator = integrator
     rng = np.random.default_rng(8)
     base = W.crazyflie_params(cv_up=40.0, cd_up=1e-3, cv_down=20.0, cd_down=5e-4,
@@ -89,9 +89,9 @@ def test_general_motor_and_drag(integrator):
 
 @pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
 def test_abstracted_model_per_world_coefficients(integrator):
-    wl = W.config2(M=6, N=100, steps=150, K=64)
+    wl = W.mixed_swarm_euler(M=6, N=100, steps=150, K=64)
     keep = wl.model_of_world == 1
-    # an all-abstracted uniform batch: take the odd worlds of the config-2 recipe
+    # an all-abstracted uniform batch: take the odd worlds of the mixed-swarm recipe
     worlds = np.nonzero(keep)[0]
     drones = (worlds[:, None] * wl.N + np.arange(wl.N)[None, :]).ravel()
     wl.x0 = wl.x0[drones]
@@ -106,11 +106,11 @@ def test_abstracted_model_per_world_coefficients(integrator):
     assert_parity(gpu, ref, _models_of(wl))
 
 
-def test_config1_full_size_sampled():
-    """Config 1 at full size (16384 worlds, RK4, 1000 steps as 10 launches of
+def test_attitude_swarm_full_size_sampled():
+    """The RK4 attitude swarm at full size (16384 worlds, RK4, 1000 steps as 10 launches of
     K = 100, the launch configuration the benchmark times); the oracle checks
     a sample of 48 drones (exact, since drones do not interact)."""
-    wl = W.config1()
+    wl = W.attitude_swarm_rk4()
     gpu, _ = _run_gpu(wl)
     sample = np.random.default_rng(0).choice(wl.M, 48, replace=False)
     ref = ph.rollout_workload(wl, drones=sample).numpy()
@@ -118,7 +118,7 @@ def test_config1_full_size_sampled():
 
 
 def test_hover_fixed_point_on_gpu():
-    wl = W.config1(M=256, steps=1000, K=250)
+    wl = W.attitude_swarm_rk4(M=256, steps=1000, K=250)
     P = wl.params[0]
     wl.x0[:] = 0
     wl.x0[:, 0:3] = np.random.default_rng(1).uniform(-1, 1, (256, 3))
@@ -134,7 +134,7 @@ def test_hover_fixed_point_on_gpu():
 def test_fused_K_equals_single_steps():
     """One launch of K steps and K launches of one step run the same float
     operations: the states agree bit for bit."""
-    wl = W.config1(M=500, steps=60, K=60)
+    wl = W.attitude_swarm_rk4(M=500, steps=60, K=60)
     a, _ = _run_gpu(wl, K=60)
     b, _ = _run_gpu(wl, K=1)
     c, _ = _run_gpu(wl, K=7)
@@ -142,7 +142,7 @@ def test_fused_K_equals_single_steps():
 
 
 def test_deterministic_and_resumable():
-    wl = W.config1(M=700, steps=100, K=100)
+    wl = W.attitude_swarm_rk4(M=700, steps=100, K=100)
     a, _ = _run_gpu(wl)
     b, _ = _run_gpu(wl)
     assert np.array_equal(a, b)
@@ -158,7 +158,7 @@ def test_deterministic_and_resumable():
 
 
 def test_state_roundtrip_host_and_device():
-    wl = W.config1(M=1234, steps=1)
+    wl = W.attitude_swarm_rk4(M=1234, steps=1)
     sim = make_sim(wl)
     x = torch.tensor(wl.x0, dtype=torch.float32)
     assert torch.equal(sim.get_state().cpu(), x)
@@ -173,13 +173,13 @@ def test_state_roundtrip_host_and_device():
 
 
 def test_nonfinite_state_sets_status_flag():
-    wl = W.config1(M=100, steps=5, K=5)
+    wl = W.attitude_swarm_rk4(M=100, steps=5, K=5)
     wl.x0[17, 7] = np.nan
     sim = make_sim(wl)
     sim.run(5, 5)
     assert sim.status() & L.SIM_FLAG_NONFINITE
     assert sim.status() == 0  # reading clears the word
-    wl2 = W.config1(M=100, steps=5, K=5)
+    wl2 = W.attitude_swarm_rk4(M=100, steps=5, K=5)
     sim2 = make_sim(wl2)
     sim2.run(5, 5)
     assert sim2.status() == 0
@@ -191,7 +191,7 @@ def test_bounded_wait_gives_up_and_reports_timeout():
     the kernel returns, SIM_FLAG_TIMEOUT reaches the host, and the context stays
     usable for a normal step afterwards."""
     import time
-    wl = W.config1(M=100, steps=5, K=5)
+    wl = W.attitude_swarm_rk4(M=100, steps=5, K=5)
     sim = make_sim(wl)
     assert sim.status() == 0
     stream = torch.cuda.current_stream().cuda_stream
@@ -236,7 +236,7 @@ def test_run_host_equals_separate_calls(where):
     set_state + set_commands + run + get_state from device buffers: 777 drones,
     RK4, 230 steps as launches of K = 40 (last one short), hold 30, 12 command
     blocks (more than the 230 steps read)."""
-    wl = W.config1(M=777, steps=230, K=40)
+    wl = W.attitude_swarm_rk4(M=777, steps=230, K=40)
     cmd = np.random.default_rng(3).uniform(-0.5, 0.5, (12, 777, 4))
     a = make_sim(wl, max_blocks=12)
     a.set_commands(torch.tensor(cmd, dtype=torch.float32, device="cuda"), 30)

@@ -60,7 +60,7 @@ def _trainer(rw, lr, reward=None):
 
 
 def test_training_iterations_match_oracle_loop():
-    rw = W.config3(seed=61, M=64, H=40, C=10)
+    rw = W.policy_bptt(seed=61, M=64, H=40, C=10)
     lr, iters = 3e-3, 5
     tr_gpu, x0, p_ref = _trainer(rw, lr)
     losses = []
@@ -81,7 +81,7 @@ def test_reward_training_iterations_match_oracle_loop():
     """The paper's setting: 16 environments, 40 policy steps per rollout at
     50 Hz (10 physics steps each), the tracking reward; five iterations against
     the FP64 oracle loop."""
-    rw = W.config3(seed=62, M=16, H=40, C=40, repeat=10)
+    rw = W.policy_bptt(seed=62, M=16, H=40, C=40, repeat=10)
     lr, iters = 3e-3, 5
     tr_gpu, x0, p_ref = _trainer(rw, lr, po.TRACKING_REWARD)
     losses = [tr_gpu.iteration(x0, p_ref).item() for _ in range(iters)]
@@ -96,7 +96,7 @@ def test_reward_training_iterations_match_oracle_loop():
 
 
 def test_graph_replay_equals_eager_iterations():
-    rw = W.config3(seed=62, M=128, H=30, C=10)
+    rw = W.policy_bptt(seed=62, M=128, H=30, C=10)
     a, x0, p_ref = _trainer(rw, 1e-2)
     for _ in range(4):
         a.iteration(x0, p_ref)

@@ -167,7 +167,7 @@ def test_asymmetric_tumbling_conserves_energy_and_momentum():
 
 @pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
 def test_quaternion_stays_unit(integrator):
-    wl = W.config1(M=64, steps=40)
+    wl = W.attitude_swarm_rk4(M=64, steps=40)
     x = torch.tensor(wl.x0, dtype=F64)
     P = ph.param_batch(wl.params, [0] * 64)
     cmd = torch.tensor(wl.cmd, dtype=F64)
@@ -287,7 +287,7 @@ def test_attitude_error_small_angle_linearisation():
 def test_attitude_loop_tracks_commanded_angles():
     """Closed loop (attitude interface, RK4): from random tilts within 30 deg and
     rates within 2 rad/s, the attitude converges to R_d of the command."""
-    wl = W.config1(M=32, steps=1)
+    wl = W.attitude_swarm_rk4(M=32, steps=1)
     x = torch.tensor(wl.x0, dtype=F64)
     x[:, 7:10] = 0
     P = ph.param_batch(wl.params, [0] * 32)
@@ -301,10 +301,10 @@ def test_attitude_loop_tracks_commanded_angles():
     assert x[:, 10:13].abs().max() < 1e-5
 
 
-def test_position_loop_converges_config0():
-    """Config 0 closed loop (position PID + attitude PD, Euler 500 Hz): after
+def test_position_loop_converges_single_drone():
+    """Single-drone closed loop (position PID + attitude PD, Euler 500 Hz): after
     10 s the drone holds the (0, 0, 1) setpoint."""
-    wl = W.config0()
+    wl = W.position_hold_single()
     sp = torch.tensor([0.0, 0.0, 1.0], dtype=F64)
     e0 = (torch.tensor(wl.x0[0, 0:3]) - sp).norm()
     x5 = ph.rollout_workload(wl, steps=2500)

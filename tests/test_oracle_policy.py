@@ -13,7 +13,7 @@ F64 = torch.float64
 
 
 def _small(M=6, H=30, seed=3):
-    return W.config3(seed=seed, M=M, H=H, C=10)
+    return W.policy_bptt(seed=seed, M=M, H=H, C=10)
 
 
 def _loss(rw, x0, weights):
@@ -163,7 +163,7 @@ def test_reward_constant_policy_penalties_closed_form():
 
 
 def _tilted(rw, seed=11):
-    """Config-3 starts upright with zero body rate, so the tilt sits on its
+    """The BPTT workload starts upright with zero body rate, so the tilt sits on its
     kink for the first steps; finite differences need states off the kink."""
     from scipy.spatial.transform import Rotation
     rng = np.random.default_rng(seed)
@@ -251,7 +251,7 @@ def test_held_policy_gradient_matches_central_differences():
 
 
 def test_gradient_central_differences_step_1e4():
-    """Config 3's check as stated: FP64 central differences with h = 1e-4 on
+    """The BPTT workload's check as stated: FP64 central differences with h = 1e-4 on
     weights of every tensor and on initial-state entries (truncation error
     O(h^2) relative to the smooth loss; bound 1e-5 relative)."""
     rw = _small(M=8, H=40)

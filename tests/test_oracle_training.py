@@ -39,7 +39,7 @@ def test_round_bf16_matches_torch():
 
 
 def test_loss_falls_over_iterations():
-    rw = W.config3(seed=51, M=16, H=40, C=10)
+    rw = W.policy_bptt(seed=51, M=16, H=40, C=10)
     losses, w = tr.train(rw.x0, rw.p_ref, rw.params, po.pack(rw.weights), 8, 3e-3, rw.dt, rw.H,
                          rw.w_act)
     assert losses[-1] < losses[0]
@@ -48,7 +48,7 @@ def test_loss_falls_over_iterations():
 def test_reward_loss_falls_over_iterations():
     """The loop under the paper's tracking reward (16 environments, 40 steps)
     improves the reward."""
-    rw = W.config3(seed=51, M=16, H=40, C=10)
+    rw = W.policy_bptt(seed=51, M=16, H=40, C=10)
     losses, _ = tr.train(rw.x0, rw.p_ref, rw.params, po.pack(rw.weights), 8, 3e-3, rw.dt, rw.H,
                          0.0, reward=po.TRACKING_REWARD)
     assert losses[-1] < losses[0]

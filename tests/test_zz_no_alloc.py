@@ -35,7 +35,7 @@ def _rel(a, b):
 
 
 def _inputs(seed, M, H, C):
-    rw = W.config3(seed=seed, M=M, H=H, C=C)
+    rw = W.policy_bptt(seed=seed, M=M, H=H, C=C)
     x0 = torch.tensor(rw.x0, dtype=torch.float32, device="cuda")
     w = torch.tensor(po.pack(rw.weights), dtype=torch.bfloat16, device="cuda")
     p_ref = torch.tensor(rw.p_ref, dtype=torch.float32, device="cuda").contiguous()

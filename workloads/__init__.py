@@ -146,7 +146,7 @@ class Workload:
 # The five workloads.  Seeds are 1000 + config index.
 
 
-def config0(seed: int = 1000) -> Workload:
+def position_hold_single(seed: int = 1000) -> Workload:
     """1 world x 1 drone, first-principles, position PID to a hover setpoint at
     (0, 0, 1); hover at z = 1 m plus U(+-0.1 m) position, U(+-10 deg) attitude
     per roll/pitch/yaw axis and U(+-1 rad/s) body rates; Euler, dt = 1/500 s,
@@ -158,7 +158,7 @@ def config0(seed: int = 1000) -> Workload:
     w = rng.uniform(-1.0, 1.0, (1, 3))
     x0 = fp_state(pos, rpy, np.zeros((1, 3)), w, np.full((1, 4), hover_rpm(P)))
     cmd = np.array([[[0.0, 0.0, 1.0, 0.0]]])
-    return Workload("c0_1x1_fp_euler_position_1000", 1, 1, 0, 0, 2, 1.0 / 500, 1000, 1000,
+    return Workload("single_1x1_fp_euler_position_1000", 1, 1, 0, 0, 2, 1.0 / 500, 1000, 1000,
                     1000, [P], np.zeros(1, np.int32), np.zeros(1, np.int32), x0, cmd)
 
 
@@ -166,7 +166,7 @@ def _attitude_commands(rng, n_blocks, n, lo=-0.5, hi=0.5):
     return rng.uniform(lo, hi, (n_blocks, n, 4))
 
 
-def config1(seed: int = 1001, M: int = 16384, steps: int = 1000, K: int = 100) -> Workload:
+def attitude_swarm_rk4(seed: int = 1001, M: int = 16384, steps: int = 1000, K: int = 100) -> Workload:
     """16384 worlds x 1 drone, first-principles, attitude interface, RK4 at
     dt = 1/500 s, 1000 steps as launches of K = 100 fused steps.  Initial state:
     position U(+-1 m) around (0,0,1), roll/pitch/yaw U(+-30 deg), velocity
@@ -182,15 +182,15 @@ def config1(seed: int = 1001, M: int = 16384, steps: int = 1000, K: int = 100) -
     x0 = fp_state(pos, rpy, vel, w, np.full((n, 4), hover_rpm(P)))
     hold = 50
     cmd = _attitude_commands(rng, (steps + hold - 1) // hold, n)
-    return Workload(f"c1_{M}x1_fp_rk4_attitude_{steps}", M, 1, 0, 1, 1, 1.0 / 500, steps, K,
+    return Workload(f"swarm_{M}x1_fp_rk4_attitude_{steps}", M, 1, 0, 1, 1, 1.0 / 500, steps, K,
                     hold, [P], np.zeros(M, np.int32), np.zeros(M, np.int32), x0, cmd)
 
 
-def config2(seed: int = 1002, M: int = 1000, N: int = 4000, steps: int = 200, K: int = 200) -> Workload:
+def mixed_swarm_euler(seed: int = 1002, M: int = 1000, N: int = 4000, steps: int = 200, K: int = 200) -> Workload:
     """M worlds x N drones (default 1000 x 4000 = 4M), even worlds
     first-principles, odd worlds abstracted with each abstracted coefficient
     scaled by U(0.9, 1.1) per world; attitude interface; Euler at dt = 1/500 s,
-    200 steps.  Initial states as in config1 (abstracted: Psi from the same
+    200 steps.  Initial states as in attitude_swarm_rk4 (abstracted: Psi from the same
     roll/pitch/yaw draw, Psidot = 0, f_sigma = m g); per-drone attitude
     commands U[-0.5, 0.5]^4 held for 50 steps."""
     rng = np.random.default_rng(seed)
@@ -219,7 +219,7 @@ def config2(seed: int = 1002, M: int = 1000, N: int = 4000, steps: int = 200, K:
     x0[is_abs] = xa
     hold = 50
     cmd = _attitude_commands(rng, (steps + hold - 1) // hold, n)
-    return Workload(f"c2_{M}x{N}_mixed_euler_attitude_{steps}", M, N, -1, 0, 1, 1.0 / 500, steps,
+    return Workload(f"swarm_{M}x{N}_mixed_euler_attitude_{steps}", M, N, -1, 0, 1, 1.0 / 500, steps,
                     K, hold, params, np.arange(M, dtype=np.int32), models, x0, cmd)
 
 
@@ -282,7 +282,7 @@ def figure8(t: np.ndarray, radius: float = 0.5, period: float = 4.0, height: flo
     return pos, vel
 
 
-def config3(seed: int = 1003, M: int = 8192, H: int = 250, C: int = 25,
+def policy_bptt(seed: int = 1003, M: int = 8192, H: int = 250, C: int = 25,
             repeat: int = 1) -> RolloutWorkload:
     """Differentiable rollout: M worlds x 1 drone, first-principles, attitude
     interface driven by the policy MLP 13 -> 64 -> 64 -> 4 (tanh, bf16
@@ -304,7 +304,7 @@ def config3(seed: int = 1003, M: int = 8192, H: int = 250, C: int = 25,
                   np.full((M, 4), hover_rpm(P)))
     t = t0[None, :] + repeat * dt * np.arange(H + 1)[:, None]
     p_ref, _ = figure8(t)
-    name = f"c3_{M}x1_bptt_euler_H{H}_C{C}" + (f"_R{repeat}" if repeat > 1 else "")
+    name = f"bptt_{M}x1_euler_H{H}_C{C}" + (f"_R{repeat}" if repeat > 1 else "")
     return RolloutWorkload(name, M, H, C, dt, P, x0, p_ref, weights, 1e-3, repeat)
 
 
@@ -328,7 +328,7 @@ class SamplingWorkload:
     w_obs: float
 
 
-def config4(seed: int = 1004, M: int = 512, S: int = 256, H: int = 50, n_max: int = 4000,
+def uneven_sampling_rk4(seed: int = 1004, M: int = 512, S: int = 256, H: int = 50, n_max: int = 4000,
             n_obs: int = 32) -> SamplingWorkload:
     """512 worlds with drone counts N_w = clamp(round(exp(U(0, ln 4000))), 1, 4000);
     each drone expands S = 256 command sequences a = clip(0.2 * xi, -1, 1)
@@ -349,7 +349,7 @@ def config4(seed: int = 1004, M: int = 512, S: int = 256, H: int = 50, n_max: in
     obs[:, 0:3] = rng.uniform(np.array([-2.0, -2.0, 0.0]), np.array([2.0, 2.0, 4.0]), (n_obs, 3))
     obs[:, 3] = rng.uniform(0.1, 0.3, n_obs)
     key = int(rng.integers(0, 2**63))
-    return SamplingWorkload(f"c4_{M}w_uneven_S{S}_H{H}_rk4", M, n_w, S, H, 1.0 / 500, 0.2, key, P,
+    return SamplingWorkload(f"sampling_{M}w_uneven_S{S}_H{H}_rk4", M, n_w, S, H, 1.0 / 500, 0.2, key, P,
                             x0, goals, obs, 1000.0)
 
 
@@ -385,10 +385,10 @@ class BatchedWorkload:
 def batched_workload(seed: int, n_per_world, model_of_world, integrator: int = 0,
                      steps: int = 200, K: int = 200, hold: int = 50,
                      jitter: float = 0.1) -> BatchedWorkload:
-    """Uneven/mixed batch with the config-2 recipe: first-principles worlds use
+    """Uneven/mixed batch with the mixed-swarm recipe: first-principles worlds use
     the Crazyflie set, abstracted worlds scale each abstracted coefficient by
     U(1 - jitter, 1 + jitter); initial states and attitude commands as in
-    config 2 (commands per drone, held `hold` steps)."""
+    the mixed swarm (commands per drone, held `hold` steps)."""
     rng = np.random.default_rng(seed)
     n_w = np.asarray(n_per_world, dtype=np.int64)
     mw = np.asarray(model_of_world, dtype=np.int32)
@@ -442,7 +442,7 @@ def mppi_workload(seed: int = 1005, n_drones: int = 64, S: int = 8000, n_ctrl: i
     with 8000 samples each (512k sampled trajectories per iteration, as the
     paper's 500k), 5 parallel controllers, top 1 % elites, a 25-step horizon at
     50 Hz, RK4; drones at rest in [-1.5,1.5]^2 x [0.5,3.5], goals in the same
-    box, 32 spherical obstacles as in config 4."""
+    box, 32 spherical obstacles as in the uneven sampling workload."""
     rng = np.random.default_rng(seed)
     P = crazyflie_params()
     lo, hi = np.array([-1.5, -1.5, 0.5]), np.array([1.5, 1.5, 3.5])
