@@ -21,7 +21,7 @@ Modules
     sampling   Philox4x32-10, Box-Muller, sampled rollout cost
 
 Parity status per function is listed in each module header.  Functions whose
-definitions are this build's readings (the controller gains and structure,
+definitions are readings of the paper adopted here (the controller gains and structure,
 the action mapping, the policy, the sampling cost) follow no printed equation
 of the paper: they are "parity unpinned" against the paper and pinned only by
 invariants (hover fixed point, small-angle linearisation, closed-loop

@@ -19,8 +19,8 @@ every drone d, with n_ctrl controllers of S_c = S / n_ctrl samples each:
     warm start: mean[d, c, k] <- mean'[d, c, k + 1] (last step repeated)
 
 Parity status: the iCEM/MPPI structure follows the paper's description; the
-noise correlation model (AR(1)), the elite cap and the parameter values are this
-build's reading (the paper defers them to its supplementary code).  Pinned in
+noise correlation model (AR(1)), the elite cap and the parameter values are the
+reading adopted here (the paper defers them to its supplementary code).  Pinned in
 tests/test_oracle_mppi.py by: a single elite reproducing the best sample's
 sequence exactly, the infinite-temperature limit (plain elite mean), the warm
 start shift, AR(1) noise statistics, and cost decrease over iterations.

@@ -30,7 +30,7 @@ Parity status:
     abstracted response, RK4 order) in tests/test_oracle_physics.py.
   mixer: pinned by reproducing the requested wrench through rotor_wrench.
   attitude_command, attitude_torque, position_command: parity unpinned against
-    the paper (this build's controller reading); pinned by the hover fixed
+    the paper (the controller reading adopted here); pinned by the hover fixed
     point, the small-angle linearisation of the attitude error and closed-loop
     convergence.
 """
@@ -191,7 +191,7 @@ def deriv_abs(x: torch.Tensor, u: torch.Tensor, P) -> torch.Tensor:
 
 
 # ---------------------------------------------------------------------------
-# Controller (this build's reading of the Mellinger stack; see module header)
+# Controller (the reading of the Mellinger stack adopted here; see module header)
 
 
 def attitude_command(a: torch.Tensor, P) -> tuple[torch.Tensor, torch.Tensor, torch.Tensor]:

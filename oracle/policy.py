@@ -32,7 +32,7 @@ The policy weights are bf16 values held exactly in float64.  The gradient of L
 with respect to all weights and biases and the initial state is that of this
 exact discrete computation, taken with torch.autograd.
 
-Parity status: the squared loss is this build's reading; parity unpinned
+Parity status: the squared loss is the reading adopted here; parity unpinned
 against the paper.  The tracking reward follows the paper's equation and table
 (a_hover, a_{-1} and the tilt definition are readings).  Pinned in
 tests/test_oracle_policy.py by central finite differences of both losses

@@ -4,8 +4,8 @@ TEST INFRASTRUCTURE ONLY (see the package header).
 
 The paper renders depth images in parallel with MJX's ray-cast pipeline
 (Results, Computation Performance: 64x64 rays across 1024 environments;
-Materials and Methods, Visualization and Collision Checking).  This build's
-reading: each drone carries a pinhole depth camera at its centre looking along
+Materials and Methods, Visualization and Collision Checking).  The reading adopted
+here: each drone carries a pinhole depth camera at its centre looking along
 body +x (image columns run from body +y to -y, rows from body +z to -z); pixel
 (row i, column j) of an H x W image casts the ray
     d_body = normalise(1, -tan(hfov/2) (2 (j + 0.5) / W - 1),

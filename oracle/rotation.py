@@ -1,12 +1,14 @@
 """Rotations used by the oracle (float64, batched over the leading dimension).
 
+TEST INFRASTRUCTURE ONLY (see the package header).
+
 Quaternions are scalar-last, q = [x, y, z, w], as the paper fixes for the
 first-principles model (Materials and Methods, First Principles Modeling,
 after Eqs. 1-4).  The product is the Hamilton product.  R(q) maps body-frame
 vectors to the world frame.  Euler angles Psi = (roll, pitch, yaw) of the
 abstracted model (Abstracted Physics Modeling, Eqs. 7-10) use
-R = Rz(yaw) Ry(pitch) Rx(roll) (the paper does not state the convention; this
-is the reading the whole build uses).
+R = Rz(yaw) Ry(pitch) Rx(roll) (the paper does not state the convention; the oracle
+and the CUDA kernels both read it this way).
 
 Pinned by tests/test_oracle_rotation.py against scipy.spatial.transform
 (an independent library implementation of the same conventions).

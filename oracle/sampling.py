@@ -19,7 +19,7 @@ with g_w the goal of the drone's world and (c_o, r_o) spherical obstacles.
 
 Parity status: Philox is pinned bit-exactly by its published known-answer
 vectors (tests/golden/philox4x32_10_kat.txt); the Box-Muller map by exact
-uniform values and moments; the cost (this build's reading: the paper prints
+uniform values and moments; the cost (the reading adopted here: the paper prints
 no cost) by the closed form at hover with zero noise and by a scalar
 brute-force evaluation on a tiny instance.
 """

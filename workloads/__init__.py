@@ -56,7 +56,7 @@ def crazyflie_params(**overrides) -> dict:
     cv_up = cv_down = 1/0.03 and cd_up = cd_down = 0).
 
     omega_max: per-rotor speed limit giving a total thrust-to-weight of 1.9.
-    Gains and the action scaling are this build's readings (the paper prints none).
+    Gains and the action scaling are readings adopted here (the paper prints none).
     Abstracted-model coefficients: roll/pitch omega_n = 15 rad/s, zeta = 0.7;
     yaw omega_n = 6 rad/s, zeta = 1; c_tau = 1/0.03; c_f = 1.
     Rotor inertia J_p (kg m^2) and the non-quadratic coefficients of the thrust
