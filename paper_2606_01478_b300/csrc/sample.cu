@@ -47,8 +47,11 @@ struct Args {
 __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    // one widening multiply gives both halves of each 32 x 32 -> 64-bit product
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c[0];
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
     const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
     c[0] = n0;
     c[1] = lo1;
@@ -62,9 +65,10 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
 // Two standard normals from two words: u = ((w >> 9) + 0.5) 2^-23 (exact),
 // r = sqrt(-2 ln u1), angle 2 pi u2 (evaluated as 2 pi u2 - pi, in [-pi, pi)).
 __device__ __forceinline__ float2 box_muller(uint32_t w1, uint32_t w2) {
-  const float u1 = ((float)(w1 >> 9) + 0.5f) * 1.1920928955078125e-07f;
-  const float u2 = ((float)(w2 >> 9) + 0.5f) * 1.1920928955078125e-07f;
-  const float r = sqrtf(-2.f * logf(u1));
+  // one fused multiply-add: the product and the sum are exact, as in the definition
+  const float u1 = fmaf((float)(w1 >> 9), 1.1920928955078125e-07f, 5.9604644775390625e-08f);
+  const float u2 = fmaf((float)(w2 >> 9), 1.1920928955078125e-07f, 5.9604644775390625e-08f);
+  const float r = sqrt_approx(-2.f * logf(u1));  // within 1 ulp of the rounded root
   float s, c;
   __sincosf(fmaf(6.28318530717958648f, u2, -3.14159265358979324f), &s, &c);
   return make_float2(-r * c, -r * s);
