@@ -460,6 +460,7 @@ def measure_single_drone(dev, reps: int = 5):
     for r in range(reps + 1):
         sim.set_state(x0)
         sim.set_commands(cmd, wl.hold)
+        _flush_l2(dev)
         torch.cuda._sleep(1_000_000)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -504,6 +505,7 @@ def measure_mixed_swarm(dev, reps: int = 3) -> dict:
         for r in range(reps + 1):
             sim.set_state(x0)
             sim.set_commands(cmd, wl.hold)
+            _flush_l2(dev)
             torch.cuda._sleep(1_000_000)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -543,11 +545,25 @@ def measure_mixed_swarm(dev, reps: int = 3) -> dict:
     return out
 
 
+_FLUSH = {}
+
+
+def _flush_l2(dev) -> None:
+    """Write a 256 MiB buffer (twice the 126 MB L2) so the next timed run starts
+    with cold caches."""
+    buf = _FLUSH.get(str(dev))
+    if buf is None:
+        buf = _FLUSH[str(dev)] = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    buf.fill_(len(_FLUSH) & 0xFF)
+
+
 def _time_ms(fn, reps: int, dev) -> float:
-    """Median device time of fn() over reps runs (one untimed warm-up)."""
+    """Median device time of fn() over reps runs (one untimed warm-up), the L2
+    flushed before each run."""
     stream = torch.cuda.current_stream(dev)
     times = []
     for r in range(reps + 1):
+        _flush_l2(dev)
         torch.cuda._sleep(1_000_000)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -720,6 +736,7 @@ def measure_bptt_training(dev, reps: int = 3) -> dict:
     for r in range(reps + 1):
         trainer = PolicyTrainer(runner, w0, lr)
         g = trainer.capture(x0, p_ref)
+        _flush_l2(dev)
         torch.cuda._sleep(1_000_000)
         stream = torch.cuda.current_stream(dev)
         e0 = torch.cuda.Event(enable_timing=True)

@@ -928,12 +928,14 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
   load_row(a.x0, ii, x);
   float loss = 0.f;
   float ap[4] = {0.f, 0.f, 0.f, 0.f};  // previous action (a_{-1} = hover = 0)
-  float r[3];
+  // reference positions at steps k, k + 1 and k + 2: each is loaded two steps
+  // before its first use, so that a cold load's latency overlaps two steps' work
+  float r[3], rn[3];
   ref_at(a.p_ref, 0, a.n, ii, r);
+  ref_at(a.p_ref, 1, a.n, ii, rn);
   for (int k = 0; k < a.H; ++k) {
-    // the next reference, loaded early: its latency overlaps this step's MLP
-    float rn[3];
-    ref_at(a.p_ref, k + 1, a.n, ii, rn);
+    float rnn[3] = {0.f, 0.f, 0.f};
+    if (k + 2 <= a.H) ref_at(a.p_ref, k + 2, a.n, ii, rnn);
     if (a.store_ckpt && (k % a.C) == 0 && valid && lane < 16) {
       store_row(a.ckpt + (size_t)(k / a.C) * a.n * 20, i, x);
       if (OBJ == SIM_OBJ_TRACKING_REWARD)
@@ -949,7 +951,10 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
     for (int j = 0; j < a.R; ++j) policy_step(x, act, P, a.dt);
     loss += step_loss<OBJ>(x, rn, act, ap, a);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) r[c] = rn[c];
+    for (int c = 0; c < 3; ++c) {
+      r[c] = rn[c];
+      rn[c] = rnn[c];
+    }
 #pragma unroll
     for (int o = 0; o < 4; ++o) ap[o] = act[o];
   }
