@@ -179,6 +179,18 @@ def oracle_sample(wl, n_drones: int, n_steps: int) -> tuple[float, int]:
     return time.perf_counter() - t, n_drones * n_steps
 
 
+def _cpu_model() -> str:
+    """The host CPU's model name (Linux), for the record beside the CPU timing."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(wl, budget_s: float = 12.0) -> dict:
     """The oracle as it stands on the host cores, on a bounded sample of the
     workload: all worlds, as many steps as fit about budget_s seconds."""
@@ -186,7 +198,7 @@ def cpu_baseline(wl, budget_s: float = 12.0) -> dict:
     steps = int(max(4, min(wl.steps, budget_s / max(dt1 / 2, 1e-6))))
     secs, units = oracle_sample(wl, wl.M, steps)
     return {"value": units / secs, "unit": UNIT, "cores": torch.get_num_threads(),
-            "kind": "oracle",
+            "cpu": _cpu_model(), "kind": "oracle",
             "sample": f"{wl.M} drones x {steps} of {wl.steps} steps (FP64 torch CPU oracle)"}
 
 
@@ -230,7 +242,7 @@ def run_reference(args, wl):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": _config(wl, args),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(),
-                         "kind": "oracle",
+                         "cpu": _cpu_model(), "kind": "oracle",
                          "sample": f"{wl.M} drones x {n_steps} of {wl.steps} steps per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
