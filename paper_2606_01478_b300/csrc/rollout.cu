@@ -783,6 +783,13 @@ __device__ __forceinline__ void ref_at(const float* __restrict__ p_ref, int k, i
   r[2] = q[2];
 }
 
+__device__ __forceinline__ void ref_at_pinned(const float* __restrict__ p_ref, int k, int n, int i,
+                                             float r[3]) {
+  const float* q = p_ref + ((size_t)k * n + i) * 3;
+  asm volatile("ld.global.nc.f32 %0, [%3];\n\tld.global.nc.f32 %1, [%3+4];\n\tld.global.nc.f32 %2, [%3+8];"
+               : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]) : "l"(q));
+}
+
 // ------------------------------------------------------------------ activation cache
 
 // One warp's cached step is five contiguous runs in shared memory and in the cache
@@ -935,7 +942,7 @@ __global__ void __launch_bounds__(TPB) rollout_fwd_kernel(RolloutArgs a, DevPara
   ref_at(a.p_ref, 1, a.n, ii, rn);
   for (int k = 0; k < a.H; ++k) {
     float rnn[3] = {0.f, 0.f, 0.f};
-    if (k + 2 <= a.H) ref_at(a.p_ref, k + 2, a.n, ii, rnn);
+    if (k + 2 <= a.H) ref_at_pinned(a.p_ref, k + 2, a.n, ii, rnn);
     if (a.store_ckpt && (k % a.C) == 0 && valid && lane < 16) {
       store_row(a.ckpt + (size_t)(k / a.C) * a.n * 20, i, x);
       if (OBJ == SIM_OBJ_TRACKING_REWARD)
@@ -1099,20 +1106,19 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
     load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
     float4 ap4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (OBJ == SIM_OBJ_TRACKING_REWARD) ap4 = a.ckpt_a[(size_t)sg * a.n + ii];
-    // recompute the segment's states (reference positions prefetched a step ahead)
-    if (lane < 16) prefetch_ref(s.pre_r[k0 & 1][row], a.p_ref, k0, a.n, ii);
-    cp_async_commit();
+    // recompute the segment's states; the reference positions of steps k, k + 1
+    // and k + 2 are carried in registers, each loaded two steps before its use
+    float rr[3], rr1[3];
+    ref_at(a.p_ref, k0, a.n, ii, rr);
+    ref_at(a.p_ref, k0 + 1, a.n, ii, rr1);
     for (int k = k0; k < k1; ++k) {
       if (valid && lane < 16) {
         store_row(a.seg + (size_t)(k - k0) * a.R * a.n * 20, i, x);
         if (OBJ == SIM_OBJ_TRACKING_REWARD) a.seg_a[(size_t)(k - k0) * a.n + i] = ap4;
       }
-      cp_async_wait_all();
-      __syncwarp();
-      const float r[3] = {s.pre_r[k & 1][row][0], s.pre_r[k & 1][row][1], s.pre_r[k & 1][row][2]};
-      if (lane < 16) prefetch_ref(s.pre_r[(k + 1) & 1][row], a.p_ref, k + 1, a.n, ii);
-      cp_async_commit();
-      if (lane < 16) put_obs(s.obs, row, x, r);
+      float rr2[3] = {0.f, 0.f, 0.f};
+      if (k + 2 <= a.H) ref_at_pinned(a.p_ref, k + 2, a.n, ii, rr2);
+      if (lane < 16) put_obs(s.obs, row, x, rr);
       // this step's activations and actions, kept for the reverse sweep: staged in
       // buffer sb, whose copy-out two steps ago must have read it, then copied out
       const int sb = (k - k0) & 1;
@@ -1135,6 +1141,11 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
         policy_step(x, act, P, a.dt);
       }
       ap4 = make_float4(act[0], act[1], act[2], act[3]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        rr[c] = rr1[c];
+        rr1[c] = rr2[c];
+      }
     }
     // the state after policy step k: x_{k1} from the recompute above, then the
     // state loaded one iteration earlier
@@ -1163,11 +1174,9 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       cache_load(s, (k1 - 1) & 1, r0, cache_at(v, k1 - 1 - k0), &s.ready[v][(k1 - 1) & 1]);
       if (k1 - 2 >= k0) cache_load(s, (k1 - 2) & 1, r0, cache_at(v, k1 - 2 - k0), &s.ready[v][(k1 - 2) & 1]);
     }
-    cp_async_wait_all();
-    __syncwarp();
-    // the reference at policy step k + 1, carried like xn (the recompute's last
-    // prefetch left the one at k1 in buffer k1 & 1)
-    float rn[3] = {s.pre_r[k1 & 1][row][0], s.pre_r[k1 & 1][row][1], s.pre_r[k1 & 1][row][2]};
+    // the reference at policy step k + 1, carried like xn (the recompute ends with
+    // the one at k1)
+    float rn[3] = {rr[0], rr[1], rr[2]};
     __threadfence_block();  // this thread's segment rows precede its async copies of them
     if (lane < 16) prefetch_step(k1 - 1);
     cp_async_commit();
