@@ -44,30 +44,46 @@ struct Args {
   float rho, rho_c;
 };
 
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+// Round r of Philox4x32-10 xors the key (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85)
+// into the high product halves.  The round keys depend on the seed alone: the
+// sampling kernel builds the ten once per block in shared memory and every draw
+// reads them from there.
+__device__ __forceinline__ uint2 philox_round_key(uint32_t k0, uint32_t k1, uint32_t r) {
+  return make_uint2(k0 + r * 0x9E3779B9u, k1 + r * 0xBB67AE85u);
+}
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], const uint2* keys) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
+    const uint2 k = keys[r];
     // one widening multiply gives both halves of each 32 x 32 -> 64-bit product
-    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c[0];
-    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c[2];
+    unsigned long long p0, p1;
+    asm("mul.wide.u32 %0, %1, 0xD2511F53;" : "=l"(p0) : "r"(c[0]));
+    asm("mul.wide.u32 %0, %1, 0xCD9E8D57;" : "=l"(p1) : "r"(c[2]));
     const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
     const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
-    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k.x, n2 = hi0 ^ c[3] ^ k.y;
     c[0] = n0;
     c[1] = lo1;
     c[2] = n2;
     c[3] = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
   }
+}
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  uint2 keys[10];
+#pragma unroll
+  for (int r = 0; r < 10; ++r) keys[r] = philox_round_key(k0, k1, r);
+  philox4x32_10(c, keys);
 }
 
 // Two standard normals from two words: u = ((w >> 9) + 0.5) 2^-23 (exact),
 // r = sqrt(-2 ln u1), angle 2 pi u2 (evaluated as 2 pi u2 - pi, in [-pi, pi)).
 __device__ __forceinline__ float2 box_muller(uint32_t w1, uint32_t w2) {
-  // one fused multiply-add: the product and the sum are exact, as in the definition
-  const float u1 = fmaf((float)(w1 >> 9), 1.1920928955078125e-07f, 5.9604644775390625e-08f);
-  const float u2 = fmaf((float)(w2 >> 9), 1.1920928955078125e-07f, 5.9604644775390625e-08f);
+  // the float with a zero exponent and mantissa w >> 9 is 1 + (w >> 9) 2^-23;
+  // subtracting 1 - 2^-24 is exact and leaves ((w >> 9) + 0.5) 2^-23
+  const float u1 = __uint_as_float((w1 >> 9) + 0x3F800000u) - 0.99999994039535522f;
+  const float u2 = __uint_as_float((w2 >> 9) + 0x3F800000u) - 0.99999994039535522f;
   const float r = sqrt_approx(-2.f * logf(u1));  // within 1 ulp of the rounded root
   float s, c;
   __sincosf(fmaf(6.28318530717958648f, u2, -3.14159265358979324f), &s, &c);
@@ -76,8 +92,8 @@ __device__ __forceinline__ float2 box_muller(uint32_t w1, uint32_t w2) {
 
 template <int INTEG, int MOTOR>
 __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const DevParams& P,
-                                         long long r, int d, int smp, int w, uint32_t k0,
-                                         uint32_t k1) {
+                                         long long r, int d, int smp, int w,
+                                         const uint2* keys) {
   float s[20];
 #pragma unroll
   for (int j = 0; j < 5; ++j) {
@@ -123,7 +139,7 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
   float4 eps = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int k = 0; k < sc.H; ++k) {
     uint32_t c[4] = {id_lo, id_hi, (uint32_t)k, 0u};
-    philox4x32_10(c, k0, k1);
+    philox4x32_10(c, keys);
     const float2 z01 = box_muller(c[0], c[1]);
     const float2 z23 = box_muller(c[2], c[3]);
     // AR(1) temporal correlation: eps_0 = xi_0, eps_k = rho eps_{k-1} + rho_c xi_k
@@ -167,7 +183,10 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
 template <int INTEG, int MOTOR, bool PERSET>
 __global__ void __launch_bounds__(256) sample_kernel(Args a, Scene sc, DevParams P0) {
   const unsigned long long seed = *a.seed;
-  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  __shared__ uint2 keys[10];
+  for (int r = threadIdx.x; r < 10; r += blockDim.x)
+    keys[r] = philox_round_key((uint32_t)seed, (uint32_t)(seed >> 32), r);
+  __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < a.total; r += stride) {
     const int d = (int)(r / sc.S);
@@ -187,9 +206,9 @@ __global__ void __launch_bounds__(256) sample_kernel(Args a, Scene sc, DevParams
     float cost;
     if constexpr (PERSET) {
       const DevParams P = a.params[a.set_of_world[w]];
-      cost = rollout<INTEG, MOTOR>(a, sc, P, r, d, smp, w, k0, k1);
+      cost = rollout<INTEG, MOTOR>(a, sc, P, r, d, smp, w, keys);
     } else {
-      cost = rollout<INTEG, MOTOR>(a, sc, P0, r, d, smp, w, k0, k1);
+      cost = rollout<INTEG, MOTOR>(a, sc, P0, r, d, smp, w, keys);
     }
     a.cost[r] = cost;
   }
