@@ -122,10 +122,11 @@ def sampled_actions(seed: int, ids, H: int, nominal_rows, sigma: float, rho: flo
 
 
 def rollout_cost(x0, goals, obstacles, params: dict, S: int, H: int, dt: float, sigma: float,
-                 seed: int, w_obs: float, drones, samples, world_of_drone, nominal=None):
+                 seed: int, w_obs: float, drones, samples, world_of_drone, nominal=None,
+                 integrator: int = ph.RK4):
     """Costs of the (drone, sample) pairs listed in `drones`, `samples` (equal
     length).  x0 [Ntot, 20], goals [M, 3], obstacles [O, 4], world_of_drone
-    [Ntot]; nominal [M, H, 4] or None (zeros)."""
+    [Ntot]; nominal [M, H, 4] or None (zeros); integrator ph.RK4 or ph.EULER."""
     drones = np.asarray(drones, dtype=np.int64)
     samples = np.asarray(samples, dtype=np.int64)
     ids = drones.astype(np.uint64) * np.uint64(S) + samples.astype(np.uint64)
@@ -133,4 +134,4 @@ def rollout_cost(x0, goals, obstacles, params: dict, S: int, H: int, dt: float, 
     nom = None if nominal is None else np.asarray(nominal)[world]
     acts = sampled_actions(seed, ids, H, nom, sigma)
     return cost_of_actions(np.asarray(x0)[drones], np.asarray(goals)[world], obstacles, params,
-                           acts, dt, w_obs)
+                           acts, dt, w_obs, integrator)

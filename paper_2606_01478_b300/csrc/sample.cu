@@ -13,6 +13,9 @@
 // The S samples of a drone are consecutive threads, so the drone's state,
 // goal and parameters are broadcast loads; the obstacles live in kernel
 // parameter space (constant bank).
+#include <algorithm>
+#include <cmath>
+
 #include "internal.h"
 #include "stepcore.cuh"
 
@@ -25,6 +28,7 @@ struct Scene {
   int n_obs;
   float w_obs, sigma, dt;
   int S, H;
+  int cull_steps;  // obstacle culling window (steps)
 };
 
 struct Args {
@@ -90,7 +94,7 @@ __device__ __forceinline__ float2 box_muller(uint32_t w1, uint32_t w2) {
   return make_float2(-r * c, -r * s);
 }
 
-template <int INTEG, int MOTOR>
+template <int INTEG, int MOTOR, bool WINDOWED>
 __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const DevParams& P,
                                          long long r, int d, int smp, int w,
                                          const uint2* keys) {
@@ -111,33 +115,49 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
     const size_t row = a.n_ctrl > 0 ? (size_t)d * a.n_ctrl + smp / a.S_c : (size_t)w;
     nom = reinterpret_cast<const float4*>(a.nominal) + row * sc.H;
   }
-  // Obstacles the drone cannot reach within the horizon contribute exactly 0 to
-  // every step's penalty and are skipped.  Reach bound: |v0| T + A T^2 with
+  // Obstacles the drone cannot reach within a window of T = steps x dt contribute
+  // exactly 0 to the penalties of those steps and are skipped.  Reach bound from
+  // the state at the window's start: |v| T + A T^2 with
   // A >= |p''| = |(T_rotor/m) R e_z - g e_z| <= 4 kf W_max^2 / m + g, valid for
-  // Euler and RK4 (both move p by at most T|v0| + A T^2 / 2) when the rotor
-  // speeds stay within [0, max(W_max, W_0)]: first-order-lag rotors with
-  // dt * cv <= 1 and no drag.  Otherwise every obstacle is tested.
-  unsigned long long cand = sc.n_obs >= 64 ? ~0ull : ((1ull << sc.n_obs) - 1ull);
+  // Euler and RK4 (both move p by at most T|v| + A T^2 / 2) when the rotor
+  // speeds stay within [0, max(W_max, W)]: first-order-lag rotors with
+  // dt * cv <= 1 and no drag.  Otherwise every obstacle is tested.  The
+  // candidate set is rebuilt at the start of every window of sc.cull_steps
+  // steps: over a long horizon the bound would cover the whole scene.
+  const unsigned long long all = sc.n_obs >= 64 ? ~0ull : ((1ull << sc.n_obs) - 1ull);
+  uint32_t cand_lo = (uint32_t)all, cand_hi = (uint32_t)(all >> 32);
   bool sparse = false;  // few candidates: visit the set bits; else test every obstacle
-  if (MOTOR == MOTOR_LAG && !drag && sc.dt * P.cv_up <= 1.f) {
+  auto cull = [&](int steps) {
     const float wmax = fmaxf(fmaxf(P.omega_max, fmaxf(s[13], s[14])), fmaxf(s[15], s[16]));
     const float acc = 4.f * P.kf * wmax * wmax * P.inv_m * 1.01f + P.g;
-    const float T = sc.H * sc.dt;
+    const float T = steps * sc.dt;
     const float v0 = sqrtf(fmaf(s[7], s[7], fmaf(s[8], s[8], s[9] * s[9])));
     const float reach = fmaf(T, v0, acc * T * T) * 1.01f + 1e-3f;
-    cand = 0ull;
+    unsigned long long cand = 0ull;
     for (int o = 0; o < sc.n_obs; ++o) {
       const float4 ob = sc.obs[o];
       const float dx = s[0] - ob.x, dy = s[1] - ob.y, dz = s[2] - ob.z;
       const float lim = ob.w + reach;
       if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < lim * lim) cand |= 1ull << o;
     }
+    cand_lo = (uint32_t)cand;
+    cand_hi = (uint32_t)(cand >> 32);
     sparse = 3 * __popcll(cand) < sc.n_obs;
-  }
-  const uint32_t cand_lo = (uint32_t)cand, cand_hi = (uint32_t)(cand >> 32);
+  };
+  const bool cullable = MOTOR == MOTOR_LAG && !drag && sc.dt * P.cv_up <= 1.f;
+  if (cullable) cull(WINDOWED ? min(sc.cull_steps, sc.H) : sc.H);
   float cost = 0.f;
   float4 eps = make_float4(0.f, 0.f, 0.f, 0.f);
+  // WINDOWED: the horizon spans several windows (a kernel of its own, so that a
+  // horizon of one window keeps a loop without culling code)
+  int next_cull = cullable ? sc.cull_steps : sc.H;
   for (int k = 0; k < sc.H; ++k) {
+    if constexpr (WINDOWED) {
+      if (k == next_cull) {
+        cull(min(sc.cull_steps, sc.H - k));
+        next_cull += sc.cull_steps;
+      }
+    }
     uint32_t c[4] = {id_lo, id_hi, (uint32_t)k, 0u};
     philox4x32_10(c, keys);
     const float2 z01 = box_muller(c[0], c[1]);
@@ -149,14 +169,11 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
     eps.y = fmaf(a.rho, eps.y, cx * z01.y);
     eps.z = fmaf(a.rho, eps.z, cx * z23.x);
     eps.w = fmaf(a.rho, eps.w, cx * z23.y);
-    float4 act = make_float4(sc.sigma * eps.x, sc.sigma * eps.y, sc.sigma * eps.z, sc.sigma * eps.w);
-    if (nom) {
-      const float4 m = nom[k];
-      act.x += m.x;
-      act.y += m.y;
-      act.z += m.z;
-      act.w += m.w;
-    }
+    // sigma eps + nominal as one fused multiply-add, as the MPPI update forms it
+    // (no nominal: + 0, the product itself)
+    const float4 m = nom ? nom[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 act = make_float4(fmaf(sc.sigma, eps.x, m.x), fmaf(sc.sigma, eps.y, m.y),
+                                   fmaf(sc.sigma, eps.z, m.z), fmaf(sc.sigma, eps.w, m.w));
     CtrlHold h;
     decode_command<SIM_FIRST_PRINCIPLES, SIM_CTRL_ATTITUDE>(act, P, h);
     one_step<SIM_FIRST_PRINCIPLES, INTEG, SIM_CTRL_ATTITUDE, MOTOR>(s, h, P, drag, sc.dt);
@@ -180,7 +197,7 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
   return cost;
 }
 
-template <int INTEG, int MOTOR, bool PERSET>
+template <int INTEG, int MOTOR, bool PERSET, bool WINDOWED>
 __global__ void __launch_bounds__(256) sample_kernel(Args a, Scene sc, DevParams P0) {
   const unsigned long long seed = *a.seed;
   __shared__ uint2 keys[10];
@@ -206,15 +223,15 @@ __global__ void __launch_bounds__(256) sample_kernel(Args a, Scene sc, DevParams
     float cost;
     if constexpr (PERSET) {
       const DevParams P = a.params[a.set_of_world[w]];
-      cost = rollout<INTEG, MOTOR>(a, sc, P, r, d, smp, w, keys);
+      cost = rollout<INTEG, MOTOR, WINDOWED>(a, sc, P, r, d, smp, w, keys);
     } else {
-      cost = rollout<INTEG, MOTOR>(a, sc, P0, r, d, smp, w, keys);
+      cost = rollout<INTEG, MOTOR, WINDOWED>(a, sc, P0, r, d, smp, w, keys);
     }
     a.cost[r] = cost;
   }
 }
 
-template <int INTEG, int MOTOR, bool PERSET>
+template <int INTEG, int MOTOR, bool PERSET, bool WINDOWED>
 static cudaError_t launch_t(const Args& a, const Scene& sc, const DevParams& P, int tpb,
                             cudaStream_t st) {
   static int cached[16][9] = {};
@@ -224,14 +241,15 @@ static cudaError_t launch_t(const Args& a, const Scene& sc, const DevParams& P, 
   const int slot = tpb / 32;
   int per_sm = (dev < 16 && slot <= 8) ? cached[dev][slot] : 0;
   if (per_sm == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_kernel<INTEG, MOTOR, PERSET>, tpb, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_kernel<INTEG, MOTOR, PERSET, WINDOWED>,
+                                                  tpb, 0);
     if (per_sm < 1) per_sm = 1;
     if (dev < 16 && slot <= 8) cached[dev][slot] = per_sm;
   }
   long long grid = (long long)sms * per_sm;
   const long long need = (a.total + tpb - 1) / tpb;
   if (grid > need) grid = need;
-  sample_kernel<INTEG, MOTOR, PERSET><<<(unsigned)grid, tpb, 0, st>>>(a, sc, P);
+  sample_kernel<INTEG, MOTOR, PERSET, WINDOWED><<<(unsigned)grid, tpb, 0, st>>>(a, sc, P);
   return cudaGetLastError();
 }
 
@@ -454,15 +472,23 @@ cudaError_t launch_sample(const float4* planes, int n, const int* offsets, int M
   sc.dt = dt;
   sc.S = S;
   sc.H = H;
-#define CF_S(I, MO)                                                       \
-  return per_set ? sp::launch_t<I, MO, true>(a, sc, P0, tpb, st)           \
-                 : sp::launch_t<I, MO, false>(a, sc, P0, tpb, st)
+  // culling windows of about 0.1 s: a Crazyflie-class drone (thrust-to-weight
+  // about 2) moves at most ~0.3 m + 0.1 |v| in that time
+  sc.cull_steps = (int)std::min<double>(H, std::max(1.0, std::floor(0.1 / dt + 0.5)));
+  // culling runs only for lag rotors; with those, a horizon of several windows
+  // takes the windowed kernel
+  const bool windowed = sc.cull_steps < H;
+#define CF_S(I, MO, WI)                                                      \
+  return per_set ? sp::launch_t<I, MO, true, WI>(a, sc, P0, tpb, st)          \
+                 : sp::launch_t<I, MO, false, WI>(a, sc, P0, tpb, st)
   if (integrator == SIM_RK4) {
-    if (general_motor) CF_S(SIM_RK4, MOTOR_GENERAL);
-    CF_S(SIM_RK4, MOTOR_LAG);
+    if (general_motor) CF_S(SIM_RK4, MOTOR_GENERAL, false);
+    if (windowed) CF_S(SIM_RK4, MOTOR_LAG, true);
+    CF_S(SIM_RK4, MOTOR_LAG, false);
   }
-  if (general_motor) CF_S(SIM_EULER, MOTOR_GENERAL);
-  CF_S(SIM_EULER, MOTOR_LAG);
+  if (general_motor) CF_S(SIM_EULER, MOTOR_GENERAL, false);
+  if (windowed) CF_S(SIM_EULER, MOTOR_LAG, true);
+  CF_S(SIM_EULER, MOTOR_LAG, false);
 #undef CF_S
 }
 

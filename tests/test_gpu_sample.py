@@ -9,7 +9,7 @@ import torch
 
 import workloads as W
 from oracle import sampling as sa
-from paper_2606_01478_b300 import RK4, Sim
+from paper_2606_01478_b300 import EULER, RK4, Sim
 from paper_2606_01478_b300 import _lib as L
 
 pytestmark = pytest.mark.gpu
@@ -22,21 +22,23 @@ def _seed_tensor(seed):
     return torch.tensor([np.int64(np.uint64(seed).view(np.int64))], device="cuda")
 
 
-def _sim_for(n_per_world, P, x0, integrator=RK4):
+def _sim_for(n_per_world, P, x0, integrator=RK4, dt=1 / 500):
     sim = Sim.batched(np.asarray(n_per_world), np.zeros(len(n_per_world), np.int32), integrator,
-                      1 / 500)
+                      dt)
     sim.set_params(P)
     sim.set_state(torch.tensor(x0, dtype=torch.float32, device="cuda"))
     return sim
 
 
-def _oracle(x0, goals, obs, P, S, H, sigma, seed, w_obs, n_per_world, drones, samples, nominal=None):
+def _oracle(x0, goals, obs, P, S, H, sigma, seed, w_obs, n_per_world, drones, samples, nominal=None,
+            dt=1 / 500, integrator=RK4):
     world = np.repeat(np.arange(len(n_per_world)), n_per_world)
     x0f = np.asarray(x0, np.float32).astype(np.float64)
     return sa.rollout_cost(x0f, np.asarray(goals, np.float32).astype(np.float64),
-                           np.asarray(obs, np.float32).astype(np.float64), P, S, H, 1 / 500, sigma,
+                           np.asarray(obs, np.float32).astype(np.float64), P, S, H, dt, sigma,
                            seed, w_obs, drones, samples, world,
-                           None if nominal is None else np.asarray(nominal, np.float32).astype(np.float64))
+                           None if nominal is None else np.asarray(nominal, np.float32).astype(np.float64),
+                           sa.ph.RK4 if integrator == RK4 else sa.ph.EULER)
 
 
 def _scene(seed, n_per_world, **kw):
@@ -202,3 +204,36 @@ def test_moving_drones_near_obstacle_shells():
     np.testing.assert_allclose(cost.cpu().numpy(), ref, rtol=RTOL, atol=1e-4)
     # the scene does put obstacles inside the reachable region
     assert (ref > H * 0.0 + 1.0).any()
+
+
+@pytest.mark.parametrize("integrator", [RK4, EULER])
+def test_obstacles_along_the_path_over_many_culling_windows(integrator):
+    """A 0.8 s horizon at 100 Hz is eight culling windows of 0.1 s: drones fly at
+    up to 3 m/s and obstacles sit on and beside their straight-line paths at
+    0.05-0.75 s, so most penalties fall in windows after the first.  Costs match
+    the oracle, which tests every obstacle at every step."""
+    n_w = [7, 9]
+    wl, x0 = _scene(76, n_w)
+    rng = np.random.default_rng(9)
+    v = rng.uniform(-3.0, 3.0, (16, 3))
+    x0[:, 7:10] = v
+    obs = []
+    for d in range(16):
+        for t in (0.05, 0.3, 0.55, 0.75):
+            off = rng.normal(size=3) * 0.05
+            obs.append(list(x0[d, 0:3] + v[d] * t + off) + [0.2])
+    obs = np.array(obs[:64])
+    dt, S, H = 1 / 100, 12, 80
+    sim = _sim_for(n_w, wl.params, x0, integrator, dt)
+    goals = torch.tensor(wl.goals, dtype=torch.float32, device="cuda")
+    cost = sim.sample_rollouts(S, H, _seed_tensor(6), 0.3, goals, obs, 1000.0)
+    assert sim.status() == 0
+    drones = np.repeat(np.arange(16), S)
+    samples = np.tile(np.arange(S), 16)
+    ref = _oracle(x0, wl.goals, obs, wl.params, S, H, 0.3, 6, 1000.0, n_w, drones, samples,
+                  dt=dt, integrator=integrator).reshape(16, S)
+    np.testing.assert_allclose(cost.cpu().numpy(), ref, rtol=RTOL, atol=1e-4)
+    # the obstacles matter: without them the costs drop for most drones
+    free = _oracle(x0, wl.goals, obs, wl.params, S, H, 0.3, 6, 0.0, n_w, drones, samples,
+                   dt=dt, integrator=integrator).reshape(16, S)
+    assert ((ref - free) > 1.0).mean() > 0.5
