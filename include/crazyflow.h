@@ -278,6 +278,19 @@ int sim_mppi_iteration(sim_h h, const sim_mppi_config* cfg, const uint64_t* seed
                        const float* goals, const float* obstacles, int n_obs, float* mean,
                        float* plan, float* cost, float* best_cost, void* stream);
 
+/* The elite selection of sim_mppi_iteration on its own (Materials and Methods,
+ * Model Predictive Path Integral: the top fraction of each controller's
+ * samples).  cost: device float [rows][S_c]; for every row, the n_e smallest
+ * (cost, sample index) pairs in lexicographic order, i.e. ties to the lower
+ * index, NaN costs never selected.  idx: device int32 [rows][n_e], the elites'
+ * sample indices in unspecified order, -1 in the slots past the row's number
+ * of non-NaN costs; jmin: device float [rows] (or NULL), the row's smallest
+ * cost (INFINITY if every cost is NaN).  1 <= n_e <= 32, S_c >= 1, 4-byte
+ * aligned buffers.  One launch, no handle.  Returns SIM_EINVAL on bad
+ * arguments (nothing launched), SIM_ECUDA if the launch fails. */
+int sim_mppi_select_elites(const float* cost, int64_t rows, int S_c, int n_e, int32_t* idx,
+                           float* jmin, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Batched depth images by ray casting (the paper's parallel depth rendering,
  * Results, Computation Performance; here as CUDA arithmetic, no graphics API).

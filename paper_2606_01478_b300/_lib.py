@@ -85,6 +85,7 @@ _SIGS = {
                               c_float, c_float, c_float, c_float, c_void_p]),
     "sim_render_depth": (c_int, [c_void_p, POINTER(Camera), POINTER(c_float), c_int, POINTER(c_float),
                                  c_int, c_void_p, c_void_p]),
+    "sim_mppi_select_elites": (c_int, [c_void_p, c_int64, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "sim_philox_normals": (c_int, [c_void_p, ctypes.c_uint64, c_int64, c_int, c_void_p, c_void_p,
                                    c_void_p]),
     "sim_run_host": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int64, c_int, c_void_p,

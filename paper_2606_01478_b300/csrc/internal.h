@@ -50,6 +50,8 @@ cudaError_t launch_mppi_update(const float* cost, float* mean, float* plan, floa
                                const unsigned long long* seed, int n, int S, int H, int C, int n_e,
                                float sigma, float rho, float lambda, cudaStream_t st);
 
+cudaError_t launch_elite_select(const float* cost, long long rows, int S_c, int n_e, int* idx,
+                                float* jmin, cudaStream_t st);
 cudaError_t launch_philox(const unsigned long long* seed, unsigned long long first_id, long long n,
                           int step, uint32_t* words, float* normals, cudaStream_t st);
 

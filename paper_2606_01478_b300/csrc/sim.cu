@@ -651,6 +651,17 @@ int sim_render_depth(sim_h h, const sim_camera* cam, const float* spheres, int n
   return SIM_OK;
 }
 
+int sim_mppi_select_elites(const float* cost, int64_t rows, int S_c, int n_e, int32_t* idx,
+                           float* jmin, void* stream) {
+  if (!cost || !idx || rows < 0 || S_c < 1 || n_e < 1 || n_e > 32 || ((uintptr_t)cost & 3) ||
+      ((uintptr_t)idx & 3) || ((uintptr_t)jmin & 3) || rows > ((int64_t)1 << 34))
+    return SIM_EINVAL;
+  if (rows == 0) return SIM_OK;
+  cudaError_t e = cf::launch_elite_select(cost, (long long)rows, S_c, n_e, (int*)idx, jmin,
+                                          (cudaStream_t)stream);
+  return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
+}
+
 int sim_philox_normals(const uint64_t* seed, uint64_t first_id, int64_t n, int step, uint32_t* words,
                        float* normals, void* stream) {
   if (!seed || ((uintptr_t)seed & 7) || n < 0 || step < 0 || (!words && !normals)) return SIM_EINVAL;
