@@ -285,8 +285,8 @@ int sim_mppi_iteration(sim_h h, const sim_mppi_config* cfg, const uint64_t* seed
  * index, NaN costs never selected.  idx: device int32 [rows][n_e], the elites'
  * sample indices in unspecified order, -1 in the slots past the row's number
  * of non-NaN costs; jmin: device float [rows] (or NULL), the row's smallest
- * cost (INFINITY if every cost is NaN).  1 <= n_e <= 32, S_c >= 1, 4-byte
- * aligned buffers.  One launch, no handle.  Returns SIM_EINVAL on bad
+ * cost (INFINITY if every cost is NaN).  1 <= n_e <= 32, S_c >= 1,
+ * 0 <= rows <= 2^33, 4-byte aligned buffers.  One launch, no handle.  Returns SIM_EINVAL on bad
  * arguments (nothing launched), SIM_ECUDA if the launch fails. */
 int sim_mppi_select_elites(const float* cost, int64_t rows, int S_c, int n_e, int32_t* idx,
                            float* jmin, void* stream);

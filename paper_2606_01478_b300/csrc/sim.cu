@@ -654,7 +654,7 @@ int sim_render_depth(sim_h h, const sim_camera* cam, const float* spheres, int n
 int sim_mppi_select_elites(const float* cost, int64_t rows, int S_c, int n_e, int32_t* idx,
                            float* jmin, void* stream) {
   if (!cost || !idx || rows < 0 || S_c < 1 || n_e < 1 || n_e > 32 || ((uintptr_t)cost & 3) ||
-      ((uintptr_t)idx & 3) || ((uintptr_t)jmin & 3) || rows > ((int64_t)1 << 34))
+      ((uintptr_t)idx & 3) || ((uintptr_t)jmin & 3) || rows > ((int64_t)1 << 33))
     return SIM_EINVAL;
   if (rows == 0) return SIM_OK;
   cudaError_t e = cf::launch_elite_select(cost, (long long)rows, S_c, n_e, (int*)idx, jmin,
