@@ -408,7 +408,8 @@ def run_b300(args, wl):
         bptt_sub = bptt_subset_gradients(dev)
         line["extra"] = {"single_drone": sd, "mixed_swarm": measure_mixed_swarm(dev), "policy_bptt": measure_policy_bptt(dev),
                          "sampling": measure_sampling(dev), "mppi": measure_mppi(dev),
-                         "bptt_training": measure_bptt_training(dev), "depth": measure_depth(dev)}
+                         "bptt_training": measure_bptt_training(dev), "depth": measure_depth(dev),
+                         "swarm_scale": measure_swarm_scale(dev)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
         line["error_vs_fp64"] = error_vs_fp64(wl, out_host.numpy())
@@ -555,6 +556,51 @@ def measure_mixed_swarm(dev, reps: int = 3) -> dict:
     out["workload"] = "swarm_1000x4000_mixed_euler_attitude_200"
     out["autotune"] = {k: v for k, v in tuned.items() if k != "table"}
     return out
+
+
+def measure_swarm_scale(dev, reps: int = 3) -> dict:
+    """The headline's step (first-principles, RK4, attitude interface, lag rotors) on
+    2^20 drones, one fused launch of K = 100 steps.  The 16384 drones of the headline
+    are 512 warps, one per busy SM sub-partition, so its time is one warp's
+    instruction chain; here every sub-partition holds many warps and the kernel runs
+    at its issue rate: the fused step's own fraction of the FP32 peak."""
+    from paper_2606_01478_b300 import CTRL_ATTITUDE, FIRST_PRINCIPLES, RK4, Sim
+    from paper_2606_01478_b300 import autotune
+    wl = W.attitude_swarm_rk4(M=1 << 20, steps=100, K=100)
+    sim = Sim(wl.M, wl.N, FIRST_PRINCIPLES, RK4, wl.dt, ctrl=CTRL_ATTITUDE,
+              max_cmd_blocks=wl.cmd.shape[0], device=dev)
+    sim.set_params(wl.params, wl.param_set_of_world)
+    x0 = torch.tensor(wl.x0, dtype=torch.float32, device=dev)
+    cmd = torch.tensor(wl.cmd, dtype=torch.float32, device=dev)
+    sim.set_state(x0)
+    sim.set_commands(cmd, wl.hold)
+    tuned = autotune.tune_step(sim, wl.steps, tag="swarm_scale", Ks=(wl.K,), reps=1)
+    stream = torch.cuda.current_stream(dev)
+    times = []
+    for r in range(reps + 1):
+        sim.set_state(x0)
+        sim.set_commands(cmd, wl.hold)
+        _flush_l2(dev)
+        torch.cuda._sleep(1_000_000)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.run(wl.steps, wl.K)
+        e1.record(stream)
+        e1.synchronize()
+        if r:
+            times.append(e0.elapsed_time(e1))
+    assert sim.status() == 0
+    ms = statistics.median(times)
+    units = wl.M * wl.steps
+    pk, _ = peaks()
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    achieved = FLOP_PER_DRONE_STEP[("fp", "rk4", "attitude")] * units / (ms / 1e3) / 1e12
+    return {"workload": wl.name, "value": units / (ms / 1e3), "unit": UNIT, "ms": ms, "K": wl.K,
+            "launches": 1, "tpb": tuned["tpb"],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak,
+                         "traffic": _profiled_traffic("step_kernel", wl.name)}}
 
 
 _FLUSH = {}
@@ -806,7 +852,8 @@ def main(argv=None):
     ap.add_argument("--tpb", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the measurements beside the headline")
-    ap.add_argument("--only", choices=["mixed", "bptt", "sampling", "mppi", "training", "depth"], default=None,
+    ap.add_argument("--only", choices=["mixed", "bptt", "sampling", "mppi", "training", "depth", "scale"],
+                    default=None,
                     help="run one extra workload alone and print its record (for profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
@@ -816,7 +863,8 @@ def main(argv=None):
         torch.cuda.set_device(local)
         dev = torch.device("cuda", local)
         fn = {"mixed": measure_mixed_swarm, "bptt": measure_policy_bptt, "sampling": measure_sampling,
-              "mppi": measure_mppi, "training": measure_bptt_training, "depth": measure_depth}[args.only]
+              "mppi": measure_mppi, "training": measure_bptt_training, "depth": measure_depth,
+              "scale": measure_swarm_scale}[args.only]
         print(json.dumps({"only": args.only, "record": fn(dev, reps=args.steps)}), flush=True)
         return 0
     rank = int(os.environ.get("RANK", "0"))
