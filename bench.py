@@ -223,6 +223,45 @@ def error_vs_fp64(wl, gpu_final: np.ndarray, n_drones: int = 256) -> dict:
             "reference": "FP64 oracle from the same float32 inputs"}
 
 
+ABS_FIELDS = {"p_m": slice(0, 3), "psi_rad": slice(3, 6), "v_m_s": slice(6, 9),
+              "psidot_rad_s": slice(9, 12), "f_sigma_N": slice(12, 13)}
+
+
+def mixed_error_vs_fp64(sample, gpu_rows) -> dict:
+    """Final-state error of the mixed swarm's 200 steps against the FP64 oracle on 64
+    sampled drones of each model, from the float32 inputs the GPU received (part of
+    the CPU-baseline leg)."""
+    import dataclasses
+    from oracle import physics as ph
+    wl = W.mixed_swarm_euler()
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    wl32 = dataclasses.replace(wl, x0=f32(wl.x0), cmd=f32(wl.cmd))
+    ref = ph.rollout_workload(wl32, drones=sample).numpy()
+    err = np.abs(np.asarray(gpu_rows, np.float64) - ref)
+    models = wl.model_of_world[np.asarray(sample) // wl.N]
+    out = {"drones_per_model": 64, "steps": int(wl.steps),
+           "reference": "FP64 oracle from the same float32 inputs"}
+    for m, name, fields in ((0, "first_principles", STATE_FIELDS), (1, "abstracted", ABS_FIELDS)):
+        e = err[models == m]
+        out[name] = {"max_abs": {k: float(e[:, sl].max()) for k, sl in fields.items()},
+                     "median_abs": {k: float(np.median(e[:, sl])) for k, sl in fields.items()}}
+    return out
+
+
+def sampling_error_vs_fp64(drones, samples, seed, gpu_cost) -> dict:
+    """Relative error of 64 sampled rollout costs of the uneven sampling workload
+    (the last timed replay, its seed) against the FP64 oracle (CPU-baseline leg)."""
+    from oracle import sampling as sa
+    wl = W.uneven_sampling_rk4()
+    world = np.repeat(np.arange(wl.M), wl.n_per_world)
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    ref = sa.rollout_cost(f32(wl.x0), f32(wl.goals), f32(wl.obstacles), wl.params, wl.S, wl.H, wl.dt,
+                          wl.sigma, seed, wl.w_obs, drones, samples, world)
+    rel = np.abs(np.asarray(gpu_cost, np.float64) - ref) / np.abs(ref)
+    return {"pairs": int(len(drones)), "max_rel": float(rel.max()), "median_rel": float(np.median(rel)),
+            "reference": "FP64 oracle from the same float32 inputs, same Philox seed"}
+
+
 def run_reference(args, wl):
     dist, rank, ws = _dist()
     if rank != 0:
@@ -417,6 +456,13 @@ def run_b300(args, wl):
             line["extra"]["single_drone"]["error_vs_fp64"] = error_vs_fp64(W.position_hold_single(), sd_final, n_drones=1)
         if bptt_sub is not None:
             line["extra"]["policy_bptt"]["gradient_error_vs_fp64"] = gradient_error_vs_fp64(*bptt_sub)
+        if "extra" in line:
+            mx, sp = line["extra"]["mixed_swarm"], line["extra"]["sampling"]
+            mx["error_vs_fp64"] = mixed_error_vs_fp64(*mx["_final_sample"])
+            sp["cost_error_vs_fp64"] = sampling_error_vs_fp64(*sp["_cost_sample"])
+    if "extra" in line:  # GPU results kept for the CPU leg, not part of the record
+        line["extra"]["mixed_swarm"].pop("_final_sample", None)
+        line["extra"]["sampling"].pop("_cost_sample", None)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -553,6 +599,12 @@ def measure_mixed_swarm(dev, reps: int = 3) -> dict:
                                "note": "abstracted drones also issue 6 MUFU sin/cos per step"}
         out[f"fused_K{K}" if K > 1 else "single_step_K1"] = rec
     assert sim.status() == 0
+    # 64 drones of each model, for the FP64 comparison of the CPU leg (the state
+    # after the last run: 200 steps from x0)
+    rng = np.random.default_rng(2)
+    models = wl.model_of_world[np.arange(n) // wl.N]
+    sample = np.concatenate([rng.choice(np.nonzero(models == m)[0], 64, replace=False) for m in (0, 1)])
+    out["_final_sample"] = (sample, sim.get_state()[torch.as_tensor(sample, device=dev)].cpu().numpy())
     out["workload"] = "swarm_1000x4000_mixed_euler_attitude_200"
     out["autotune"] = {k: v for k, v in tuned.items() if k != "table"}
     return out
@@ -729,13 +781,17 @@ def measure_sampling(dev, reps: int = 3) -> dict:
         seed.add_(1)
         g.replay()
     ms = _time_ms(replay, reps, dev)
+    rng = np.random.default_rng(5)
+    drones, samples = rng.integers(0, n, 64), rng.integers(0, wl.S, 64)
+    cost_sample = (drones, samples, int(seed.item()),
+                   cost[torch.as_tensor(drones, device=dev), torch.as_tensor(samples, device=dev)].cpu().numpy())
     units = n * wl.S * wl.H
     pk, _ = peaks()
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     achieved = SAMPLE_FLOP_PER_STEP * units / (ms / 1e3) / 1e12
     return {"workload": wl.name, "drones": n, "samples_per_drone": wl.S, "horizon": wl.H,
             "value": units / (ms / 1e3), "unit": UNIT, "ms_per_outer_iteration": ms,
-            "rollouts_per_s": n * wl.S / (ms / 1e3), "tpb": best[0],
+            "rollouts_per_s": n * wl.S / (ms / 1e3), "tpb": best[0], "_cost_sample": cost_sample,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
                          "traffic": _profiled_traffic("sample_kernel", wl.name),
