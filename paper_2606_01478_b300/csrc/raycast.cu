@@ -35,12 +35,14 @@ struct Scene {
 // margin of 1e-4 (|c| + r) + 1e-5 against rounding in the per-ray tests, so a
 // primitive that a ray's own test could hit is never dropped; the rays then walk
 // the surviving set in index order, and every depth is the one the full loop
-// gives.
+// gives.  The eight warps of a block render one drone: the primitives' centres
+// in its camera frame and their margins are computed once per block.
 constexpr int TILE_R = 4, TILE_C = 8;
 
-__device__ __forceinline__ bool outside_tile(float3 c, float r, float ylo, float yhi, float zlo,
-                                             float zhi, const float ninv[4]) {
-  const float m = r + fmaf(1e-4f, sqrt_approx(fmaf(c.x, c.x, fmaf(c.y, c.y, c.z * c.z))) + r, 1e-5f);
+// c: centre in the camera frame, m: radius plus margin
+__device__ __forceinline__ bool outside_tile(float4 c, float ylo, float yhi, float zlo, float zhi,
+                                             const float ninv[4]) {
+  const float m = c.w;
   return c.x < -m || (ylo * c.x - c.y) * ninv[0] > m || (c.y - yhi * c.x) * ninv[1] > m ||
          (zlo * c.x - c.z) * ninv[2] > m || (c.z - zhi * c.x) * ninv[3] > m;
 }
@@ -48,13 +50,26 @@ __device__ __forceinline__ bool outside_tile(float3 c, float r, float ylo, float
 __global__ void __launch_bounds__(256) depth_kernel(const float4* __restrict__ planes, int n, Scene sc,
                                                     float* __restrict__ out) {
   const unsigned FULL = 0xffffffffu;
-  // the cull reads one primitive per lane: from shared memory (lanes reading
-  // different entries of the constant bank are served one address at a time)
-  __shared__ float4 s_sph[SIM_MAX_SPHERES], s_bsph[SIM_MAX_BOXES];
-  for (int k = threadIdx.x; k < sc.n_sph; k += blockDim.x) s_sph[k] = sc.sph[k];
-  for (int k = threadIdx.x; k < sc.n_box; k += blockDim.x) s_bsph[k] = sc.bsph[k];
-  __syncthreads();
   const int e = blockIdx.y;
+  const float4 a = planes[e], b = planes[(size_t)n + e];
+  const float ox = a.x, oy = a.y, oz = a.z;
+  float R[9];
+  quat_rot(a.w, b.x, b.y, b.z, R);
+  auto to_camera = [&](float4 c) {  // (R^T (centre - o), radius + margin)
+    const float wx = c.x - ox, wy = c.y - oy, wz = c.z - oz;
+    const float x = fmaf(R[0], wx, fmaf(R[3], wy, R[6] * wz));
+    const float y = fmaf(R[1], wx, fmaf(R[4], wy, R[7] * wz));
+    const float z = fmaf(R[2], wx, fmaf(R[5], wy, R[8] * wz));
+    const float m = c.w + fmaf(1e-4f, sqrt_approx(fmaf(x, x, fmaf(y, y, z * z))) + c.w, 1e-5f);
+    return make_float4(x, y, z, m);
+  };
+  // the primitives in this drone's camera frame, once per block, in shared memory
+  // (the cull reads one per lane; lanes reading different entries of the
+  // constant bank are served one address at a time)
+  __shared__ float4 s_sph[SIM_MAX_SPHERES], s_box[SIM_MAX_BOXES];
+  for (int k = threadIdx.x; k < sc.n_sph; k += blockDim.x) s_sph[k] = to_camera(sc.sph[k]);
+  for (int k = threadIdx.x; k < sc.n_box; k += blockDim.x) s_box[k] = to_camera(sc.bsph[k]);
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int tw = (sc.W + TILE_C - 1) / TILE_C, th = (sc.H + TILE_R - 1) / TILE_R;
   const int tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -63,10 +78,6 @@ __global__ void __launch_bounds__(256) depth_kernel(const float4* __restrict__ p
   const int i = ti * TILE_R + lane / TILE_C, j = tj * TILE_C + lane % TILE_C;
   const bool valid = i < sc.H && j < sc.W;
   const int npx = sc.H * sc.W;
-  const float4 a = planes[e], b = planes[(size_t)n + e];
-  const float ox = a.x, oy = a.y, oz = a.z;
-  float R[9];
-  quat_rot(a.w, b.x, b.y, b.z, R);
   auto ray_y = [&](int jj) { return -sc.tan_h * fmaf(2.f / sc.W, jj + 0.5f, -1.f); };
   auto ray_z = [&](int ii) { return -sc.tan_v * fmaf(2.f / sc.H, ii + 0.5f, -1.f); };
   // the tile's bounds (ray_y and ray_z fall with the column and the row)
@@ -75,28 +86,20 @@ __global__ void __launch_bounds__(256) depth_kernel(const float4* __restrict__ p
   const float yhi = ray_y(j0), ylo = ray_y(j1), zhi = ray_z(i0), zlo = ray_z(i1);
   const float ninv[4] = {rsqrtf(fmaf(ylo, ylo, 1.f)), rsqrtf(fmaf(yhi, yhi, 1.f)),
                          rsqrtf(fmaf(zlo, zlo, 1.f)), rsqrtf(fmaf(zhi, zhi, 1.f))};
-  auto to_camera = [&](float x, float y, float z) {  // R^T (p - o)
-    const float wx = x - ox, wy = y - oy, wz = z - oz;
-    return make_float3(fmaf(R[0], wx, fmaf(R[3], wy, R[6] * wz)),
-                       fmaf(R[1], wx, fmaf(R[4], wy, R[7] * wz)),
-                       fmaf(R[2], wx, fmaf(R[5], wy, R[8] * wz)));
-  };
   unsigned keep_s[2], keep_b;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int s = lane + 32 * h;
     bool keep = false;
     if (s < sc.n_sph) {
-      const float4 c = s_sph[s];
-      keep = !outside_tile(to_camera(c.x, c.y, c.z), c.w, ylo, yhi, zlo, zhi, ninv);
+      keep = !outside_tile(s_sph[s], ylo, yhi, zlo, zhi, ninv);
     }
     keep_s[h] = __ballot_sync(FULL, keep);
   }
   {
     bool keep = false;
     if (lane < sc.n_box) {
-      const float4 c = s_bsph[lane];
-      keep = !outside_tile(to_camera(c.x, c.y, c.z), c.w, ylo, yhi, zlo, zhi, ninv);
+      keep = !outside_tile(s_box[lane], ylo, yhi, zlo, zhi, ninv);
     }
     keep_b = __ballot_sync(FULL, keep);
   }
