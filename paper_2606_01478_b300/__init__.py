@@ -7,7 +7,7 @@ missing.  There is no CPU fallback.
 """
 from ._lib import (ABSTRACTED, CTRL_ATTITUDE, CTRL_POSITION, CTRL_ROTOR_SPEED, EULER,
                    FIRST_PRINCIPLES, RK4, SimError, load)
-from .sim import Sim, pack_params
+from .sim import Sim, pack_params, select_elites
 
-__all__ = ["Sim", "SimError", "load", "pack_params", "FIRST_PRINCIPLES", "ABSTRACTED", "EULER",
+__all__ = ["Sim", "SimError", "load", "pack_params", "select_elites", "FIRST_PRINCIPLES", "ABSTRACTED", "EULER",
            "RK4", "CTRL_ROTOR_SPEED", "CTRL_ATTITUDE", "CTRL_POSITION"]

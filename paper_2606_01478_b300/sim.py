@@ -30,6 +30,25 @@ def pack_params(params) -> np.ndarray:
     return out
 
 
+def select_elites(cost: torch.Tensor, n_e: int, stream=None):
+    """The MPPI elite selection on its own (sim_mppi_select_elites): for every row of
+    cost [rows, S_c] (float32, CUDA), the indices of its n_e smallest costs (ties to
+    the lower index, NaN never selected) in unspecified order, -1 past the row's
+    number of non-NaN costs, and the row's smallest cost.  Returns (idx [rows, n_e]
+    int32, jmin [rows] float32)."""
+    if cost.dim() != 2 or cost.dtype != torch.float32 or not cost.is_cuda or not cost.is_contiguous():
+        raise ValueError("cost must be a contiguous float32 CUDA tensor [rows, S_c]")
+    rows, S_c = cost.shape
+    idx = torch.empty(rows, n_e, dtype=torch.int32, device=cost.device)
+    jmin = torch.empty(rows, dtype=torch.float32, device=cost.device)
+    r = L.load().sim_mppi_select_elites(ctypes.c_void_p(cost.data_ptr()), rows, S_c, int(n_e),
+                                        ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(jmin.data_ptr()),
+                                        _stream_ptr(stream))
+    if r != L.SIM_OK:
+        raise L.SimError(f"sim_mppi_select_elites failed ({r}): need 1 <= n_e <= 32 and S_c >= 1")
+    return idx, jmin
+
+
 class Sim:
     """One batch of drones bound to a device workspace.
 

@@ -165,3 +165,12 @@ def test_rollout_precision_validation(lib):
     assert lib.sim_rollout_set_precision(h, L.MLP_BF16) == L.SIM_OK
     assert lib.sim_rollout_set_precision(h, L.MLP_HILO) == L.SIM_OK
     lib.sim_destroy(h)
+
+
+def test_select_elites_refuses_host_tensors():
+    """The elite selection's binding takes CUDA tensors only: a host tensor is an
+    error, never a CPU computation."""
+    import torch
+    from paper_2606_01478_b300 import select_elites
+    with pytest.raises(ValueError):
+        select_elites(torch.zeros(2, 3), 1)

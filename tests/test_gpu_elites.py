@@ -11,19 +11,13 @@ import torch
 
 from oracle import mppi as om
 from paper_2606_01478_b300 import _lib as L
+from paper_2606_01478_b300 import select_elites
 
 pytestmark = pytest.mark.gpu
 
 
 def _select(cost: np.ndarray, n_e: int):
-    rows, S_c = cost.shape
-    c = torch.tensor(cost, dtype=torch.float32, device="cuda")
-    idx = torch.full((rows, n_e), -7, dtype=torch.int32, device="cuda")
-    jmin = torch.empty(rows, dtype=torch.float32, device="cuda")
-    r = L.load().sim_mppi_select_elites(ctypes.c_void_p(c.data_ptr()), rows, S_c, n_e,
-                                        ctypes.c_void_p(idx.data_ptr()),
-                                        ctypes.c_void_p(jmin.data_ptr()), None)
-    assert r == L.SIM_OK
+    idx, jmin = select_elites(torch.tensor(cost, dtype=torch.float32, device="cuda"), n_e)
     return idx.cpu().numpy(), jmin.cpu().numpy()
 
 
