@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE ONLY (see the package header).
 
 The paper's sampling controller (Materials and Methods, Model Predictive Path
-Integral) runs several independent controllers in parallel, keeps the best
-fraction of each controller's trajectories (iCEM), uses temporally correlated
+Integral) runs several independent controllers in parallel, keeps the top 1 %
+of each controller's trajectories as elites (iCEM), uses temporally correlated
 noise, warm-starts from the previous mean, averages the elites with
 exponential (MPPI) weights and applies the best controller's sequence.  For
 every drone d, with n_ctrl controllers of S_c = S / n_ctrl samples each:
@@ -12,34 +12,44 @@ every drone d, with n_ctrl controllers of S_c = S / n_ctrl samples each:
     sample s belongs to controller c = s // S_c; its actions are
         clip(mean[d, c, k] + sigma eps_{s,k}, -1, 1),  eps AR(1) with rho
         (Philox noise of sample id d * S + s, see oracle.sampling)
-    elites E_c: the n_e = clamp(ceil(elite_frac S_c - 1e-4), 1, 32) smallest costs
-        (ties: lower sample index first)
+    elites E_c: the n_e smallest costs of the controller (ties: lower sample
+        index first); the paper's "top 1 %" is n_e = n_elites(S_c, 0.01)
+        = ceil(S_c / 100), e.g. 1000 of the 100 000 samples each of its five
+        controllers draw (500k trajectories in all)
     w_e = exp(-(J_e - J_min,c) / lam),  mean'[d, c] = sum_e w_e a_e / sum_e w_e
     c* = argmin_c J_min,c (ties: lower c);  plan[d] = mean'[d, c*]
     warm start: mean[d, c, k] <- mean'[d, c, k + 1] (last step repeated)
 
 Parity status: the iCEM/MPPI structure follows the paper's description; the
-noise correlation model (AR(1)), the elite cap and the parameter values are the
-reading adopted here (the paper defers them to its supplementary code).  Pinned in
+noise correlation model (AR(1)) and the parameter values are the reading
+adopted here (the paper defers them to its supplementary code).  Pinned in
 tests/test_oracle_mppi.py by: a single elite reproducing the best sample's
-sequence exactly, the infinite-temperature limit (plain elite mean), the warm
-start shift, AR(1) noise statistics, and cost decrease over iterations.
+sequence exactly, finite-temperature weights on hand-picked costs (two and
+three elites whose cost gaps are lam ln 3, lam ln 2 and lam ln 4, so the plan
+must equal (3 a1 + a2) / 4 and (4 a1 + 2 a2 + a3) / 7), the infinite-
+temperature limit (plain elite mean) with brute-force elite sets beyond 32
+elites, the elite counts of the paper's sizes, the warm start shift, AR(1)
+noise statistics, and cost decrease over iterations.
 """
 from __future__ import annotations
 
 import math
+from fractions import Fraction
 
 import numpy as np
 
 from . import sampling as sa
 
-MAX_ELITES = 32
 
-
-def n_elites(S_c: int, elite_frac: float) -> int:
-    """clamp(ceil(elite_frac S_c - 1e-4), 1, 32): the 1e-4 guard makes a
-    fraction given in float32 (0.1 -> 0.100000001) count as intended."""
-    return int(min(MAX_ELITES, max(1, math.ceil(elite_frac * S_c - 1e-4))))
+def n_elites(S_c: int, elite_frac) -> int:
+    """The top fraction of a controller's S_c samples: ceil(elite_frac S_c),
+    at least one.  The fraction is taken as the decimal it is written as (0.01
+    is exactly one hundredth), so the count is exact: 1 % of 100 000 is 1000,
+    1 % of 150 is 2."""
+    f = elite_frac if isinstance(elite_frac, Fraction) else Fraction(str(elite_frac))
+    if not 0 < f <= 1:
+        raise ValueError("elite_frac must lie in (0, 1]")
+    return max(1, math.ceil(f * S_c))
 
 
 def select_elites(costs_c: np.ndarray, n_e: int) -> np.ndarray:
@@ -48,16 +58,18 @@ def select_elites(costs_c: np.ndarray, n_e: int) -> np.ndarray:
 
 
 def update(costs, mean, seed: int, S: int, H: int, n_ctrl: int, sigma: float, rho: float,
-           elite_frac: float, lam: float, drones):
-    """MPPI update of the listed drones.  costs [n, S] (rows for `drones`),
-    mean [n, n_ctrl, H, 4].  Returns (mean_next (warm-started) [n, n_ctrl, H, 4],
-    plan [n, H, 4], best_cost [n])."""
+           n_e: int, lam: float, drones):
+    """MPPI update of the listed drones with n_e elites per controller.  costs
+    [n, S] (rows for `drones`), mean [n, n_ctrl, H, 4].  Returns (mean_next
+    (warm-started) [n, n_ctrl, H, 4], plan [n, H, 4], best_cost [n])."""
     drones = np.asarray(drones, dtype=np.int64)
     costs = np.asarray(costs, dtype=np.float64)
     mean = np.asarray(mean, dtype=np.float64)
     n = len(drones)
     S_c = S // n_ctrl
-    n_e = n_elites(S_c, elite_frac)
+    n_e = int(n_e)
+    if not 1 <= n_e <= S_c:
+        raise ValueError("need 1 <= n_e <= S / n_ctrl")
     new_mean = np.zeros_like(mean)
     plan = np.zeros((n, H, 4))
     best = np.zeros(n)
