@@ -134,8 +134,10 @@ int sim_set_control(sim_h h, int ctrl);
  * will be set (see sim_set_commands).  256-byte alignment required. */
 int sim_workspace_bytes(sim_h h, int64_t max_cmd_blocks, size_t* bytes);
 
-/* Give the handle its device workspace (caller-owned, >= the reported size,
- * 256-byte aligned).  Clears nothing; sim_set_state / sim_set_params /
+/* Give the handle its device workspace (caller-owned device memory, >= the
+ * reported size, 256-byte aligned; SIM_EINVAL for host memory).  The device
+ * that holds it is the handle's device: make it current for every later call
+ * on the handle.  Clears nothing; sim_set_state / sim_set_params /
  * sim_set_commands fill it.  Resets the status word (async on stream). */
 int sim_bind(sim_h h, void* workspace, size_t bytes, int64_t max_cmd_blocks, void* stream);
 
@@ -244,16 +246,18 @@ int sim_sample_rollouts(sim_h h, int S, int H, const uint64_t* seed, float sigma
 
 /* ---------------------------------------------------------------------------
  * One MPPI / iCEM control iteration (Materials and Methods, Model Predictive
- * Path Integral: parallel controllers, top-fraction elites, temporally
- * correlated noise, warm start from the previous mean, exponential weighting
- * of the elites, best controller applied).  For every drone d of the handle:
- *   sample s (0 <= s < S) belongs to controller c = s / (S / n_ctrl); its
- *   actions are clip(mean[d][c][k] + sigma eps_k, -1, 1) with the noise of
+ * Path Integral: parallel controllers, the top fraction of each controller's
+ * trajectories as elites, temporally correlated noise, warm start from the
+ * previous mean, exponential weighting of the elites, best controller applied).
+ * For every drone d of the handle:
+ *   sample s (0 <= s < S) belongs to controller c = s / S_c, S_c = S / n_ctrl;
+ *   its actions are clip(mean[d][c][k] + sigma eps_k, -1, 1) with the noise of
  *   sim_sample_rollouts made AR(1): eps_0 = xi_0,
  *   eps_k = rho eps_{k-1} + sqrt(1 - rho^2) xi_k
  *   cost[d][s] as in sim_sample_rollouts (goal of the drone's world, obstacles)
- *   elites of controller c: its n_e = clamp(ceil(elite_frac S/n_ctrl - 1e-4), 1, 32)
- *   lowest costs (ties: lower sample index; NaN costs never selected)
+ *   elites of controller c: its n_elite lowest costs (ties: lower sample index;
+ *   NaN costs never selected).  The paper keeps the top 1 % of each
+ *   controller's samples: n_elite = ceil(S_c / 100).
  *   mean'[d][c] = sum_e w_e a_e / sum_e w_e,  w_e = exp(-(J_e - J_min,c) / lambda)
  *   plan[d] = mean'[d][c*], c* = argmin_c J_min,c (ties: lower c);
  *   best_cost[d] = J_min,c*
@@ -262,14 +266,24 @@ int sim_sample_rollouts(sim_h h, int S, int H, const uint64_t* seed, float sigma
  * plan [Ntot][H][4] float, cost [Ntot][S] float (written), best_cost [Ntot]
  * float; goals, obstacles and seed as for sim_sample_rollouts.
  * Constraints: S % n_ctrl == 0, 1 <= n_ctrl <= 32, 0 <= rho < 1, lambda > 0,
- * 0 < elite_frac <= 1.  Two launches (sampling, update); no scratch memory. */
+ * 1 <= n_elite <= min(S_c, SIM_MAX_ELITES).  Controllers with more than
+ * SIM_MPPI_WARP_MAX_COSTS samples or more than SIM_MPPI_WARP_MAX_ELITES elites
+ * take the cluster update (one thread block per controller, a drone's
+ * controllers in one thread-block cluster), which needs
+ * n_ctrl <= SIM_MPPI_CLUSTER_MAX_CTRL, H <= SIM_MPPI_CLUSTER_MAX_H and
+ * Ntot n_ctrl < 2^31.  Two launches (sampling, update); no scratch memory. */
+#define SIM_MAX_ELITES 4096
+#define SIM_MPPI_WARP_MAX_COSTS 2048
+#define SIM_MPPI_WARP_MAX_ELITES 32
+#define SIM_MPPI_CLUSTER_MAX_CTRL 8
+#define SIM_MPPI_CLUSTER_MAX_H 1024
 typedef struct {
   int S;            /* samples per drone, all controllers */
   int H;            /* horizon (steps of the handle's dt and integrator) */
   int n_ctrl;       /* parallel controllers per drone */
+  int n_elite;      /* elites per controller */
   float sigma;      /* noise scale */
   float rho;        /* AR(1) temporal correlation of the noise */
-  float elite_frac; /* elite fraction of each controller's samples */
   float lambda;     /* temperature of the exponential weights */
   float w_obs;      /* obstacle penalty weight */
 } sim_mppi_config;
@@ -283,11 +297,12 @@ int sim_mppi_iteration(sim_h h, const sim_mppi_config* cfg, const uint64_t* seed
  * samples).  cost: device float [rows][S_c]; for every row, the n_e smallest
  * (cost, sample index) pairs in lexicographic order, i.e. ties to the lower
  * index, NaN costs never selected.  idx: device int32 [rows][n_e], the elites'
- * sample indices in unspecified order, -1 in the slots past the row's number
- * of non-NaN costs; jmin: device float [rows] (or NULL), the row's smallest
- * cost (INFINITY if every cost is NaN).  1 <= n_e <= 32, S_c >= 1,
- * 0 <= rows <= 2^33, 4-byte aligned buffers.  One launch, no handle.  Returns SIM_EINVAL on bad
- * arguments (nothing launched), SIM_ECUDA if the launch fails. */
+ * sample indices in increasing index order, -1 in the slots past the row's
+ * number of non-NaN costs; jmin: device float [rows] (or NULL), the row's
+ * smallest cost (INFINITY if every cost is NaN).  1 <= n_e <= SIM_MAX_ELITES,
+ * S_c >= 1, 0 <= rows < 2^31, 4-byte aligned buffers.  One launch, no handle.
+ * Returns SIM_EINVAL on bad arguments (nothing launched), SIM_ECUDA if the
+ * launch fails. */
 int sim_mppi_select_elites(const float* cost, int64_t rows, int S_c, int n_e, int32_t* idx,
                            float* jmin, void* stream);
 
@@ -421,9 +436,13 @@ int sim_adam_step(const float* grad, float* w, float* m, float* v, uint16_t* w_b
  * Batches whose rollout workspace (sim_rollout_workspace_bytes) exceeds it are
  * rejected with SIM_EINVAL and a message, before anything is launched.
  * The caller still passes inputs and outputs (as for sim_rollout_grad; dL is
- * fixed to 1).  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before
- * any stream capture.  All calls share the one array and nothing in it needs
+ * fixed to 1), on the device that holds the handle's workspace, which must be
+ * the current device (SIM_EINVAL otherwise).  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress, with that device
+ * current) and keeps it for the life of the process; make that first call
+ * before any stream capture.  A device reset (cudaDeviceReset) invalidates the
+ * kept addresses: do not call this entry point again in a process that reset
+ * a device after its first call there.  All calls share the one array and nothing in it needs
  * to start at zero (every byte a call reads, the same call wrote first), but
  * calls that overlap on the GPU -- on different streams or threads -- race on it
  * and must be serialised by the caller. */

@@ -21,6 +21,7 @@ CTRL_ROTOR_SPEED, CTRL_ATTITUDE, CTRL_POSITION, CTRL_TORQUE = 0, 1, 2, 3
 STATE_DIM, CMD_DIM, NPARAMS = 20, 4, 48
 POLICY_NPARAMS = 5316
 MAX_OBSTACLES = 64
+MAX_ELITES = 4096
 
 # Order of enum sim_param_index in include/crazyflow.h (checked by a CPU test).
 PARAM_ORDER = (
@@ -52,8 +53,8 @@ MLP_HILO, MLP_BF16 = 0, 1
 
 class MppiConfig(ctypes.Structure):
     """sim_mppi_config (include/crazyflow.h)."""
-    _fields_ = [("S", c_int), ("H", c_int), ("n_ctrl", c_int), ("sigma", c_float), ("rho", c_float),
-                ("elite_frac", c_float), ("lambda_", c_float), ("w_obs", c_float)]
+    _fields_ = [("S", c_int), ("H", c_int), ("n_ctrl", c_int), ("n_elite", c_int), ("sigma", c_float),
+                ("rho", c_float), ("lambda_", c_float), ("w_obs", c_float)]
 
 
 _SIGS = {

@@ -50,6 +50,10 @@ cudaError_t launch_mppi_update(const float* cost, float* mean, float* plan, floa
                                const unsigned long long* seed, int n, int S, int H, int C, int n_e,
                                float sigma, float rho, float lambda, cudaStream_t st);
 
+// The MPPI update and the elite selection run one warp per controller when a
+// controller has at most 2048 samples and 32 elites (mppi.cu), else one thread
+// block per controller (the update: a drone's controllers in one cluster).
+bool mppi_uses_warp_path(int S_c, int n_e);
 cudaError_t launch_elite_select(const float* cost, long long rows, int S_c, int n_e, int* idx,
                                 float* jmin, cudaStream_t st);
 cudaError_t launch_philox(const unsigned long long* seed, unsigned long long first_id, long long n,
@@ -66,6 +70,8 @@ cudaError_t launch_depth(const float4* planes, int n, int H, int W, float hfov, 
 // Record a message as the handle's last error (sim.cu); used by entry points
 // defined in other translation units.
 void note_error(sim_h h, const char* fmt, ...);
+// The device that holds the handle's workspace (-1 before sim_bind).
+int handle_device(sim_h h);
 
 // Row-major [n][20] floats <-> 5 float4 planes [5][n] (layout.cu).
 cudaError_t launch_rows_to_planes(const float4* rows, float4* planes, int n, cudaStream_t st);

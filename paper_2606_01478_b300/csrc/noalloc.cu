@@ -69,6 +69,16 @@ extern "C" int sim_rollout_grad_noalloc(sim_h h, const float* x0, const uint16_t
                    need, NOALLOC_SCRATCH_BYTES);
     return SIM_EINVAL;
   }
+  // The array exists once per device and is looked up for the current one:
+  // the handle's buffers must be on that same device.
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != cf::handle_device(h)) {
+    cudaGetLastError();
+    cf::note_error(h, "sim_rollout_grad_noalloc: device %d is current, the handle's workspace is "
+                      "on device %d; make the handle's device current first",
+                   cur, cf::handle_device(h));
+    return SIM_EINVAL;
+  }
   void* scratch = nullptr;
   const float* seed = nullptr;
   cudaError_t e = device_pointers(&scratch, &seed);

@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "noise.cuh"
 #include "stepcore.cuh"
 
 namespace cf {
@@ -48,51 +49,9 @@ struct Args {
   float rho, rho_c;
 };
 
-// Round r of Philox4x32-10 xors the key (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85)
-// into the high product halves.  The round keys depend on the seed alone: the
-// sampling kernel builds the ten once per block in shared memory and every draw
-// reads them from there.
-__device__ __forceinline__ uint2 philox_round_key(uint32_t k0, uint32_t k1, uint32_t r) {
-  return make_uint2(k0 + r * 0x9E3779B9u, k1 + r * 0xBB67AE85u);
-}
-
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], const uint2* keys) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint2 k = keys[r];
-    // one widening multiply gives both halves of each 32 x 32 -> 64-bit product
-    unsigned long long p0, p1;
-    asm("mul.wide.u32 %0, %1, 0xD2511F53;" : "=l"(p0) : "r"(c[0]));
-    asm("mul.wide.u32 %0, %1, 0xCD9E8D57;" : "=l"(p1) : "r"(c[2]));
-    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
-    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
-    const uint32_t n0 = hi1 ^ c[1] ^ k.x, n2 = hi0 ^ c[3] ^ k.y;
-    c[0] = n0;
-    c[1] = lo1;
-    c[2] = n2;
-    c[3] = lo0;
-  }
-}
-
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
-  uint2 keys[10];
-#pragma unroll
-  for (int r = 0; r < 10; ++r) keys[r] = philox_round_key(k0, k1, r);
-  philox4x32_10(c, keys);
-}
-
-// Two standard normals from two words: u = ((w >> 9) + 0.5) 2^-23 (exact),
-// r = sqrt(-2 ln u1), angle 2 pi u2 (evaluated as 2 pi u2 - pi, in [-pi, pi)).
-__device__ __forceinline__ float2 box_muller(uint32_t w1, uint32_t w2) {
-  // the float with a zero exponent and mantissa w >> 9 is 1 + (w >> 9) 2^-23;
-  // subtracting 1 - 2^-24 is exact and leaves ((w >> 9) + 0.5) 2^-23
-  const float u1 = __uint_as_float((w1 >> 9) + 0x3F800000u) - 0.99999994039535522f;
-  const float u2 = __uint_as_float((w2 >> 9) + 0x3F800000u) - 0.99999994039535522f;
-  const float r = sqrt_approx(-2.f * logf(u1));  // within 1 ulp of the rounded root
-  float s, c;
-  __sincosf(fmaf(6.28318530717958648f, u2, -3.14159265358979324f), &s, &c);
-  return make_float2(-r * c, -r * s);
-}
+using noise::box_muller;
+using noise::philox4x32_10;
+using noise::philox_round_key;
 
 template <int INTEG, int MOTOR, bool WINDOWED>
 __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const DevParams& P,
@@ -275,303 +234,7 @@ __global__ void philox_kernel(const unsigned long long* seed, unsigned long long
   }
 }
 
-// MPPI / iCEM update: one block per drone, warp c = controller c.
-struct MppiArgs {
-  const float* cost;  // [n][S]
-  float* mean;        // [n][C][H][4]: in = current means, out = updated means shifted one step
-  float* plan;        // [n][H][4]: updated mean of the best controller
-  float* best_cost;   // [n]
-  const unsigned long long* seed;
-  int n, S, H, C, S_c, n_e;
-  float sigma, rho, rho_c, inv_lam;
-};
-
-__device__ __forceinline__ bool lex_less(float a, int ia, float b, int ib) {
-  return a < b || (a == b && ia < ib);
-}
-
-// Order-preserving map of float costs to unsigned keys (-0 and +0 share a key;
-// NaN maps to ~0u, above every other key, and is never selected).
-__device__ __forceinline__ uint32_t cost_key(float v) {
-  if (v != v) return 0xFFFFFFFFu;
-  const uint32_t b = __float_as_uint(v + 0.f);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float key_cost(uint32_t k) {
-  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
-}
-
-// The elites of one controller, for one warp: the n_e smallest (cost, index)
-// pairs of cc[0..S_c), ties to the lower index, NaN never selected.  On return
-// lanes 0 .. n-1 hold one elite each (el_c, el_i; the others INFINITY and
-// 0x7fffffff), n = min(n_e, number of non-NaN costs), and jmin is the smallest
-// cost (INFINITY if there is none).  Up to 2048 costs (64 per lane, kept in
-// registers as keys): a bisection over the key range finds the threshold T
-// with count(key <= T) >= n, counting with warp reductions and stopping as soon
-// as exactly n keys lie at or below the midpoint; the elites are the keys < T
-// and the lowest-index keys equal to T up to n, compacted into lanes in index
-// order through stage[32] (cost) and stage_i[32] (index) in shared memory.
-// More costs: n rounds of a warp arg-min, reading them from memory each round.
-constexpr int ELITE_REG = 64;
-__device__ __forceinline__ void select_elites(const float* cc, int S_c, int n_e, int lane,
-                                              float* stage, int* stage_i, float& el_c, int& el_i,
-                                              float& jmin) {
-  const unsigned FULL = 0xffffffffu;
-  el_c = INFINITY;
-  el_i = 0x7fffffff;
-  if (S_c <= 32 * ELITE_REG) {
-    uint32_t kr[ELITE_REG];
-    uint32_t kmin = 0xFFFFFFFFu, kmax = 0u;
-    int nv = 0;
-    // every lane loads all its slots (clamped index) before using any: guarded
-    // loads were issued one at a time
-    float cv[ELITE_REG];
-#pragma unroll
-    for (int j = 0; j < ELITE_REG; ++j) cv[j] = cc[min(lane + 32 * j, S_c - 1)];
-#pragma unroll
-    for (int j = 0; j < ELITE_REG; ++j) {
-      const int s = lane + 32 * j;
-      kr[j] = s < S_c ? cost_key(cv[j]) : 0xFFFFFFFFu;
-      if (kr[j] != 0xFFFFFFFFu) {
-        kmin = min(kmin, kr[j]);
-        kmax = max(kmax, kr[j]);
-        ++nv;
-      }
-    }
-    nv = __reduce_add_sync(FULL, nv);
-    kmin = __reduce_min_sync(FULL, kmin);
-    kmax = __reduce_max_sync(FULL, kmax);
-    const int n = min(n_e, nv);
-    jmin = n > 0 ? key_cost(kmin) : INFINITY;
-    if (n == 0) return;
-    auto count_le = [&](uint32_t t) {
-      int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-#pragma unroll
-      for (int j = 0; j < ELITE_REG; j += 4) {
-        c0 += kr[j] <= t;
-        c1 += kr[j + 1] <= t;
-        c2 += kr[j + 2] <= t;
-        c3 += kr[j + 3] <= t;
-      }
-      return __reduce_add_sync(FULL, (c0 + c1) + (c2 + c3));
-    };
-    uint32_t lo = kmin, hi = kmax;  // invariant: count(<= hi) = c_hi >= n
-    int c_hi = nv;
-    while (lo < hi && c_hi != n) {
-      const uint32_t mid = lo + ((hi - lo) >> 1);
-      const int c = count_le(mid);
-      if (c >= n) {
-        hi = mid;
-        c_hi = c;
-      } else {
-        lo = mid + 1;
-      }
-    }
-    const uint32_t T = hi;
-    const unsigned below = (1u << lane) - 1u;
-    int base = 0;
-    auto put = [&](bool take, int j) {
-      const unsigned m = __ballot_sync(FULL, take);
-      if (take) {
-        const int slot = base + __popc(m & below);
-        stage[slot] = key_cost(kr[j]);
-        stage_i[slot] = lane + 32 * j;
-      }
-      base += __popc(m);
-    };
-    if (c_hi == n) {  // the elites are the keys <= T
-#pragma unroll
-      for (int j = 0; j < ELITE_REG; ++j) put(kr[j] <= T, j);
-    } else {  // ties at T: the keys < T, then the lowest-index keys equal to T
-      int quota = n - (T > 0u ? count_le(T - 1u) : 0);
-#pragma unroll
-      for (int j = 0; j < ELITE_REG; ++j) {
-        const unsigned eq = __ballot_sync(FULL, kr[j] == T);
-        put(kr[j] < T || (kr[j] == T && __popc(eq & below) < quota), j);
-        quota -= min(__popc(eq), quota);
-      }
-    }
-    __syncwarp();
-    if (lane < n) {
-      el_c = stage[lane];
-      el_i = stage_i[lane];
-    }
-    __syncwarp();
-    return;
-  }
-  float prev_c = -INFINITY;
-  int prev_i = -1;
-  for (int e = 0; e < n_e; ++e) {
-    float bc = INFINITY;
-    int bi = 0x7fffffff;
-    for (int s = lane; s < S_c; s += 32) {
-      const float v = cc[s];
-      if (v == v && lex_less(prev_c, prev_i, v, s) && lex_less(v, s, bc, bi)) {
-        bc = v;
-        bi = s;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float oc = __shfl_xor_sync(FULL, bc, o);
-      const int oi = __shfl_xor_sync(FULL, bi, o);
-      if (lex_less(oc, oi, bc, bi)) {
-        bc = oc;
-        bi = oi;
-      }
-    }
-    if (lane == e && bi != 0x7fffffff) {
-      el_c = bc;
-      el_i = bi;
-    }
-    prev_c = bc;
-    prev_i = bi;
-  }
-  jmin = __shfl_sync(FULL, el_c, 0);
-}
-
-__global__ void mppi_update_kernel(MppiArgs a) {
-  __shared__ float jmin_s[32];
-  __shared__ float stage[32][32];
-  __shared__ int stage_i[32][32];
-  const int d = blockIdx.x;
-  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const float* cc = a.cost + (size_t)d * a.S + (size_t)c * a.S_c;
-  float el_c, jmin;
-  int el_i;
-  select_elites(cc, a.S_c, a.n_e, lane, stage[c], stage_i[c], el_c, el_i, jmin);
-  if (lane == 0) jmin_s[c] = jmin;
-  __syncthreads();
-  int cbest = 0;
-  for (int q = 1; q < a.C; ++q)
-    if (jmin_s[q] < jmin_s[cbest]) cbest = q;
-  if (threadIdx.x == 0) a.best_cost[d] = jmin_s[cbest];
-  const bool mine = lane < a.n_e && el_i != 0x7fffffff;
-  const float wgt = mine ? expf(-(el_c - jmin) * a.inv_lam) : 0.f;
-  float wsum = wgt;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-  const float inv_w = 1.f / wsum;
-  const unsigned long long id =
-      (unsigned long long)d * a.S + (unsigned long long)c * a.S_c + (mine ? (unsigned)el_i : 0u);
-  const unsigned long long sd = *a.seed;
-  uint2 keys[10];
-#pragma unroll
-  for (int r = 0; r < 10; ++r) keys[r] = philox_round_key((uint32_t)sd, (uint32_t)(sd >> 32), r);
-  float4* mrow = reinterpret_cast<float4*>(a.mean) + ((size_t)d * a.C + c) * a.H;
-  float4* prow = reinterpret_cast<float4*>(a.plan) + (size_t)d * a.H;
-  float4 eps = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 last = make_float4(0.f, 0.f, 0.f, 0.f);
-  // Steps in groups of G: the group's Philox + Box-Muller chains are independent
-  // of each other, and its 4 G sums share one shuffle tree.  The mean rows come
-  // 32 steps at a time, one per lane, each row read before the warm-start shift
-  // overwrites it (row k - 1 is written at step k).
-  constexpr int G = 4;
-  float4 mk = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int k0 = 0; k0 < a.H; k0 += G) {
-    if ((k0 & 31) == 0) mk = k0 + lane < a.H ? mrow[k0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float2 z[G][2];
-#pragma unroll
-    for (int u = 0; u < G; ++u) {
-      z[u][0] = z[u][1] = make_float2(0.f, 0.f);
-      if (mine && k0 + u < a.H) {
-        uint32_t ct[4] = {(uint32_t)id, (uint32_t)(id >> 32), (uint32_t)(k0 + u), 0u};
-        philox4x32_10(ct, keys);
-        z[u][0] = box_muller(ct[0], ct[1]);
-        z[u][1] = box_muller(ct[2], ct[3]);
-      }
-    }
-    float4 v[G];
-#pragma unroll
-    for (int u = 0; u < G; ++u) {
-      const int k = k0 + u;
-      const float4 m = make_float4(__shfl_sync(0xffffffffu, mk.x, k & 31),
-                                   __shfl_sync(0xffffffffu, mk.y, k & 31),
-                                   __shfl_sync(0xffffffffu, mk.z, k & 31),
-                                   __shfl_sync(0xffffffffu, mk.w, k & 31));
-      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (mine && k < a.H) {
-        const float cx = k == 0 ? 1.f : a.rho_c;
-        eps.x = fmaf(a.rho, eps.x, cx * z[u][0].x);
-        eps.y = fmaf(a.rho, eps.y, cx * z[u][0].y);
-        eps.z = fmaf(a.rho, eps.z, cx * z[u][1].x);
-        eps.w = fmaf(a.rho, eps.w, cx * z[u][1].y);
-        v[u].x = wgt * clampf(fmaf(a.sigma, eps.x, m.x), -1.f, 1.f);
-        v[u].y = wgt * clampf(fmaf(a.sigma, eps.y, m.y), -1.f, 1.f);
-        v[u].z = wgt * clampf(fmaf(a.sigma, eps.z, m.z), -1.f, 1.f);
-        v[u].w = wgt * clampf(fmaf(a.sigma, eps.w, m.w), -1.f, 1.f);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-      for (int u = 0; u < G; ++u) {
-        v[u].x += __shfl_xor_sync(0xffffffffu, v[u].x, o);
-        v[u].y += __shfl_xor_sync(0xffffffffu, v[u].y, o);
-        v[u].z += __shfl_xor_sync(0xffffffffu, v[u].z, o);
-        v[u].w += __shfl_xor_sync(0xffffffffu, v[u].w, o);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < G; ++u) {
-      const int k = k0 + u;
-      if (k < a.H) {
-        last = make_float4(v[u].x * inv_w, v[u].y * inv_w, v[u].z * inv_w, v[u].w * inv_w);
-        if (lane == 0) {
-          if (k > 0) mrow[k - 1] = last;  // warm start: shift by one step
-          if (c == cbest) prow[k] = last;
-        }
-      }
-    }
-  }
-  if (lane == 0) mrow[a.H - 1] = last;
-}
-
-// One warp per row of S_c costs: the row's elites (sim_mppi_select_elites).
-__global__ void __launch_bounds__(256) elite_select_kernel(const float* cost, long long rows, int S_c,
-                                                           int n_e, int* idx, float* jmin) {
-  __shared__ float stage[8][32];
-  __shared__ int stage_i[8][32];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long row = (long long)blockIdx.x * 8 + w;
-  if (row >= rows) return;  // the whole warp leaves together
-  float el_c, jm;
-  int el_i;
-  select_elites(cost + row * S_c, S_c, n_e, lane, stage[w], stage_i[w], el_c, el_i, jm);
-  if (lane < n_e) idx[row * n_e + lane] = el_i == 0x7fffffff ? -1 : el_i;
-  if (lane == 0 && jmin) jmin[row] = jm;
-}
-
 }  // namespace sp
-
-cudaError_t launch_mppi_update(const float* cost, float* mean, float* plan, float* best_cost,
-                               const unsigned long long* seed, int n, int S, int H, int C, int n_e,
-                               float sigma, float rho, float lambda, cudaStream_t st) {
-  sp::MppiArgs a;
-  a.cost = cost;
-  a.mean = mean;
-  a.plan = plan;
-  a.best_cost = best_cost;
-  a.seed = seed;
-  a.n = n;
-  a.S = S;
-  a.H = H;
-  a.C = C;
-  a.S_c = S / C;
-  a.n_e = n_e;
-  a.sigma = sigma;
-  a.rho = rho;
-  a.rho_c = sqrtf(1.f - rho * rho);
-  a.inv_lam = 1.f / lambda;
-  sp::mppi_update_kernel<<<n, 32 * C, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_elite_select(const float* cost, long long rows, int S_c, int n_e, int* idx,
-                                float* jmin, cudaStream_t st) {
-  sp::elite_select_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(cost, rows, S_c, n_e, idx, jmin);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_philox(const unsigned long long* seed, unsigned long long first_id, long long n,
                           int step, uint32_t* words, float* normals, cudaStream_t st) {

@@ -29,8 +29,9 @@ struct sim_s {
   std::vector<int32_t> model_of_world;
   std::vector<int4> tiles;  // uneven batches: (first drone, count <= 32, world, model)
   std::vector<int32_t> offsets32;  // uneven batches: first drone of each world, [M + 1]
-  // workspace (caller-owned device memory)
+  // workspace (caller-owned device memory) and the device that holds it
   char* ws = nullptr;
+  int device = -1;
   size_t ws_bytes = 0;
   int64_t max_blocks = 0;
   float4* planes = nullptr;
@@ -246,6 +247,7 @@ void note_error(sim_h h, const char* fmt, ...) {
   vsnprintf(h->err, sizeof(h->err), fmt, ap);
   va_end(ap);
 }
+int handle_device(sim_h h) { return h ? h->device : -1; }
 }  // namespace cf
 
 extern "C" {
@@ -332,7 +334,13 @@ int sim_bind(sim_h h, void* workspace, size_t bytes, int64_t max_cmd_blocks, voi
   if (bytes < L.total)
     return fail(h, SIM_ENOMEM, "workspace of %zu bytes is smaller than the %zu needed", bytes,
                 L.total);
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, workspace) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(h, SIM_EINVAL, "workspace must be device memory");
+  }
   char* ws = (char*)workspace;
+  h->device = pa.device;
   h->ws = ws;
   h->ws_bytes = bytes;
   h->max_blocks = max_cmd_blocks;
@@ -597,11 +605,19 @@ int sim_mppi_iteration(sim_h h, const sim_mppi_config* cfg, const uint64_t* seed
   if (!cfg) return fail(h, SIM_EINVAL, "cfg is NULL");
   const sim_mppi_config c = *cfg;
   if (c.S < 1 || c.H < 1 || c.n_ctrl < 1 || c.n_ctrl > 32 || c.S % c.n_ctrl != 0 ||
-      !(c.rho >= 0.f && c.rho < 1.f) || !(c.lambda > 0.f) || !(c.elite_frac > 0.f && c.elite_frac <= 1.f) ||
-      !isfinite(c.lambda))
+      !(c.rho >= 0.f && c.rho < 1.f) || !(c.lambda > 0.f) || !isfinite(c.lambda) ||
+      c.n_elite < 1 || c.n_elite > SIM_MAX_ELITES || c.n_elite > c.S / c.n_ctrl)
     return fail(h, SIM_EINVAL,
                 "MPPI config: need S %% n_ctrl == 0, 1 <= n_ctrl <= 32, 0 <= rho < 1, lambda > 0, "
-                "0 < elite_frac <= 1");
+                "1 <= n_elite <= min(S / n_ctrl, %d)", SIM_MAX_ELITES);
+  const int S_c = c.S / c.n_ctrl;
+  if (!cf::mppi_uses_warp_path(S_c, c.n_elite) &&
+      (c.n_ctrl > SIM_MPPI_CLUSTER_MAX_CTRL || c.H > SIM_MPPI_CLUSTER_MAX_H ||
+       h->ntot * c.n_ctrl >= ((int64_t)1 << 31)))
+    return fail(h, SIM_EINVAL,
+                "MPPI config: controllers of more than %d samples or %d elites need n_ctrl <= %d, "
+                "H <= %d and Ntot n_ctrl < 2^31", SIM_MPPI_WARP_MAX_COSTS, SIM_MPPI_WARP_MAX_ELITES,
+                SIM_MPPI_CLUSTER_MAX_CTRL, SIM_MPPI_CLUSTER_MAX_H);
   if (!mean || ((uintptr_t)mean & 15) || !plan || ((uintptr_t)plan & 15) || !best_cost ||
       ((uintptr_t)best_cost & 3))
     return fail(h, SIM_EINVAL, "bad or misaligned MPPI buffer");
@@ -609,13 +625,9 @@ int sim_mppi_iteration(sim_h h, const sim_mppi_config* cfg, const uint64_t* seed
   int r = sample_impl(h, c.S, c.H, seed, c.sigma, mean, goals, obstacles, n_obs, c.w_obs, cost,
                       stream, c.n_ctrl, c.rho);
   if (r != SIM_OK) return r;
-  const int S_c = c.S / c.n_ctrl;
-  // ceil with a 1e-4 guard so that e.g. 0.1 (0.100000001 in float) of 20 samples is 2
-  int n_e = (int)ceil((double)c.elite_frac * S_c - 1e-4);
-  n_e = n_e < 1 ? 1 : (n_e > 32 ? 32 : n_e);
   cudaError_t e = cf::launch_mppi_update(cost, mean, plan, best_cost,
                                          (const unsigned long long*)seed, (int)h->ntot, c.S, c.H,
-                                         c.n_ctrl, n_e, c.sigma, c.rho, c.lambda,
+                                         c.n_ctrl, c.n_elite, c.sigma, c.rho, c.lambda,
                                          (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "MPPI update launch");
   h->launches++;
@@ -653,8 +665,9 @@ int sim_render_depth(sim_h h, const sim_camera* cam, const float* spheres, int n
 
 int sim_mppi_select_elites(const float* cost, int64_t rows, int S_c, int n_e, int32_t* idx,
                            float* jmin, void* stream) {
-  if (!cost || !idx || rows < 0 || S_c < 1 || n_e < 1 || n_e > 32 || ((uintptr_t)cost & 3) ||
-      ((uintptr_t)idx & 3) || ((uintptr_t)jmin & 3) || rows > ((int64_t)1 << 33))
+  if (!cost || !idx || rows < 0 || S_c < 1 || n_e < 1 || n_e > SIM_MAX_ELITES ||
+      ((uintptr_t)cost & 3) || ((uintptr_t)idx & 3) || ((uintptr_t)jmin & 3) ||
+      rows >= ((int64_t)1 << 31))
     return SIM_EINVAL;
   if (rows == 0) return SIM_OK;
   cudaError_t e = cf::launch_elite_select(cost, (long long)rows, S_c, n_e, (int*)idx, jmin,

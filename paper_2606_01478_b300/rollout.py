@@ -20,7 +20,7 @@ import ctypes
 import torch
 
 from . import _lib as L
-from .sim import _stream_ptr
+from .sim import _stream_ptr, on_device
 
 
 # the paper's BPTT tracking-reward weights (hyper-parameter table); action
@@ -86,6 +86,7 @@ class PolicyRollout:
         if p_ref.dtype != torch.float32 or tuple(p_ref.shape) != (self.H + 1, n, 3) or not p_ref.is_contiguous():
             raise ValueError(f"p_ref must be contiguous float32 [{self.H + 1}, {n}, 3]")
 
+    @on_device
     def forward(self, x0, w_bf16, p_ref, loss=None, stream=None):
         self._check_inputs(x0, w_bf16, p_ref)
         if loss is None:
@@ -95,6 +96,7 @@ class PolicyRollout:
                                        _p(self.ws), self.ws.numel(), _p(loss), _stream_ptr(stream)))
         return loss
 
+    @on_device
     def backward(self, x0, w_bf16, p_ref, dL, dW=None, dx0=None, stream=None):
         self._check_inputs(x0, w_bf16, p_ref)
         dev = self.sim.device
@@ -108,6 +110,7 @@ class PolicyRollout:
                                        _stream_ptr(stream)))
         return dW, dx0
 
+    @on_device
     def grad(self, x0, w_bf16, p_ref, stream=None, loss=None, dW=None, dx0=None):
         """Loss, dL/dw and dL/dx0 in one call (forward + backward kernels)."""
         self._check_inputs(x0, w_bf16, p_ref)

@@ -13,10 +13,46 @@ import torch
 from . import _lib as L
 
 
-def _stream_ptr(stream) -> ctypes.c_void_p:
+def _stream_ptr(stream, device=None) -> ctypes.c_void_p:
+    """The CUDA stream handle for a call on `device` (default: the current
+    device): the given stream, which must belong to that device, or the
+    device's current stream."""
+    if device is None:
+        device = torch.device("cuda", torch.cuda.current_device())
+    device = torch.device(device)
     if stream is None:
-        stream = torch.cuda.current_stream()
+        stream = torch.cuda.current_stream(device)
+    _check_same_device(stream.device, device, "stream")
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_same_device(got, want, what: str) -> None:
+    """Refuse a stream or tensor on another GPU than the one the call runs on:
+    the library launches on the current device, and a kernel given another
+    device's memory would fault."""
+    got, want = torch.device(got), torch.device(want)
+    if got.type != want.type:
+        raise ValueError(f"{what} is on {got}, the call runs on {want}")
+    gi = got.index if got.index is not None else torch.cuda.current_device()
+    wi = want.index if want.index is not None else torch.cuda.current_device()
+    if gi != wi:
+        raise ValueError(f"{what} is on {got}, the call runs on {want}")
+
+
+def on_device(method):
+    """Run a method of an object with a ``device`` (or ``sim.device``) attribute
+    with that CUDA device current, so that the library's launches and the
+    default stream belong to the device that holds the object's memory."""
+    import functools
+
+    @functools.wraps(method)
+    def wrapped(self, *args, **kwargs):
+        dev = getattr(self, "device", None)
+        if dev is None:
+            dev = self.sim.device
+        with torch.cuda.device(dev):
+            return method(self, *args, **kwargs)
+    return wrapped
 
 
 def pack_params(params) -> np.ndarray:
@@ -33,19 +69,23 @@ def pack_params(params) -> np.ndarray:
 def select_elites(cost: torch.Tensor, n_e: int, stream=None):
     """The MPPI elite selection on its own (sim_mppi_select_elites): for every row of
     cost [rows, S_c] (float32, CUDA), the indices of its n_e smallest costs (ties to
-    the lower index, NaN never selected) in unspecified order, -1 past the row's
-    number of non-NaN costs, and the row's smallest cost.  Returns (idx [rows, n_e]
-    int32, jmin [rows] float32)."""
+    the lower index, NaN never selected) in increasing index order, -1 past the row's
+    number of non-NaN costs, and the row's smallest cost.  Runs on the device that
+    holds `cost` (a given stream must belong to it).  Returns (idx [rows, n_e] int32,
+    jmin [rows] float32)."""
     if cost.dim() != 2 or cost.dtype != torch.float32 or not cost.is_cuda or not cost.is_contiguous():
         raise ValueError("cost must be a contiguous float32 CUDA tensor [rows, S_c]")
     rows, S_c = cost.shape
-    idx = torch.empty(rows, n_e, dtype=torch.int32, device=cost.device)
-    jmin = torch.empty(rows, dtype=torch.float32, device=cost.device)
-    r = L.load().sim_mppi_select_elites(ctypes.c_void_p(cost.data_ptr()), rows, S_c, int(n_e),
-                                        ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(jmin.data_ptr()),
-                                        _stream_ptr(stream))
+    with torch.cuda.device(cost.device):
+        st = _stream_ptr(stream, cost.device)
+        idx = torch.empty(rows, max(int(n_e), 0), dtype=torch.int32, device=cost.device)
+        jmin = torch.empty(rows, dtype=torch.float32, device=cost.device)
+        r = L.load().sim_mppi_select_elites(ctypes.c_void_p(cost.data_ptr()), rows, S_c, int(n_e),
+                                            ctypes.c_void_p(idx.data_ptr()),
+                                            ctypes.c_void_p(jmin.data_ptr()), st)
     if r != L.SIM_OK:
-        raise L.SimError(f"sim_mppi_select_elites failed ({r}): need 1 <= n_e <= 32 and S_c >= 1")
+        raise L.SimError(r, f"sim_mppi_select_elites rejected n_e = {n_e}, S_c = {S_c}, rows = {rows}: "
+                            f"need 1 <= n_e <= {L.MAX_ELITES} and S_c >= 1")
     return idx, jmin
 
 
@@ -59,6 +99,8 @@ class Sim:
                  ctrl=L.CTRL_ATTITUDE, max_cmd_blocks=1, device="cuda", _handle=None):
         self.lib = L.load()
         self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         h = ctypes.c_void_p()
         if _handle is None:
             self._check_create(self.lib.sim_create(ctypes.byref(h), int(M), int(N), int(model),
@@ -72,8 +114,9 @@ class Sim:
         nbytes = ctypes.c_size_t()
         self._check(self.lib.sim_workspace_bytes(h, self.max_cmd_blocks, ctypes.byref(nbytes)))
         self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
-        self._check(self.lib.sim_bind(h, ctypes.c_void_p(self.workspace.data_ptr()), nbytes.value,
-                                      self.max_cmd_blocks, _stream_ptr(None)))
+        with torch.cuda.device(self.device):
+            self._check(self.lib.sim_bind(h, ctypes.c_void_p(self.workspace.data_ptr()), nbytes.value,
+                                          self.max_cmd_blocks, _stream_ptr(None)))
 
     @classmethod
     def batched(cls, n_per_world, model_per_world, integrator=L.EULER, dt=1 / 500,
@@ -108,6 +151,7 @@ class Sim:
             self.h = None
 
     # ------------------------------------------------------------------ API
+    @on_device
     def set_params(self, params, set_of_world=None, stream=None):
         arr = pack_params(params)
         sow = None
@@ -119,12 +163,14 @@ class Sim:
             _stream_ptr(stream)))
         self._keep = (arr, sow)
 
+    @on_device
     def set_state(self, x: torch.Tensor, stream=None):
         if x.dtype != torch.float32 or not x.is_contiguous() or tuple(x.shape) != (self.ntot, L.STATE_DIM):
             raise ValueError(f"state must be contiguous float32 [{self.ntot}, {L.STATE_DIM}]")
         self._check(self.lib.sim_set_state(self.h, ctypes.c_void_p(x.data_ptr()), _stream_ptr(stream)))
         self._state_src = x
 
+    @on_device
     def get_state(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         if out is None:
             out = torch.empty(self.ntot, L.STATE_DIM, dtype=torch.float32, device=self.device)
@@ -133,6 +179,7 @@ class Sim:
         self._check(self.lib.sim_get_state(self.h, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
 
+    @on_device
     def set_commands(self, cmd: torch.Tensor, hold: int, stream=None):
         if cmd.dim() == 2:
             cmd = cmd[None]
@@ -146,12 +193,15 @@ class Sim:
     def set_block_size(self, tpb: int):
         self._check(self.lib.sim_set_block_size(self.h, int(tpb)))
 
+    @on_device
     def step(self, K: int = 1, stream=None):
         self._check(self.lib.sim_step(self.h, int(K), _stream_ptr(stream)))
 
+    @on_device
     def run(self, n_steps: int, K: int, stream=None):
         self._check(self.lib.sim_run(self.h, int(n_steps), int(K), _stream_ptr(stream)))
 
+    @on_device
     def run_host(self, x0: torch.Tensor, cmd: torch.Tensor, hold: int, n_steps: int, K: int,
                  out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """One rollout from (pinned) host tensors to a host tensor, command blocks
@@ -174,6 +224,7 @@ class Sim:
         self._hold = int(hold)
         return out
 
+    @on_device
     def capture_run(self, n_steps: int, K: int) -> torch.cuda.CUDAGraph:
         """Capture `n_steps` steps (launches of at most K) into a CUDA graph.
 
@@ -192,6 +243,7 @@ class Sim:
         self._check(self.lib.sim_set_step_count(self.h, t0))
         return g
 
+    @on_device
     def sample_rollouts(self, S: int, H: int, seed: torch.Tensor, sigma: float, goals: torch.Tensor,
                         obstacles, w_obs: float, nominal: torch.Tensor | None = None,
                         cost: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -214,16 +266,17 @@ class Sim:
             obs.shape[0], float(w_obs), ctypes.c_void_p(cost.data_ptr()), _stream_ptr(stream)))
         return cost
 
+    @on_device
     def mppi_iteration(self, cfg: dict, seed: torch.Tensor, goals: torch.Tensor, obstacles,
                        mean: torch.Tensor, plan: torch.Tensor | None = None,
                        cost: torch.Tensor | None = None, best_cost: torch.Tensor | None = None,
                        stream=None):
         """One MPPI / iCEM iteration (see sim_mppi_iteration).  cfg keys: S, H,
-        n_ctrl, sigma, rho, elite_frac, lam, w_obs.  mean [Ntot, n_ctrl, H, 4] is
-        updated in place (warm-started).  Returns (plan, cost, best_cost)."""
-        c = L.MppiConfig(int(cfg["S"]), int(cfg["H"]), int(cfg["n_ctrl"]), float(cfg["sigma"]),
-                         float(cfg["rho"]), float(cfg["elite_frac"]), float(cfg["lam"]),
-                         float(cfg["w_obs"]))
+        n_ctrl, n_elite (elites per controller), sigma, rho, lam, w_obs.  mean
+        [Ntot, n_ctrl, H, 4] is updated in place (warm-started).  Returns (plan,
+        cost, best_cost)."""
+        c = L.MppiConfig(int(cfg["S"]), int(cfg["H"]), int(cfg["n_ctrl"]), int(cfg["n_elite"]),
+                         float(cfg["sigma"]), float(cfg["rho"]), float(cfg["lam"]), float(cfg["w_obs"]))
         dev = self.device
         if mean.dtype != torch.float32 or not mean.is_contiguous() or tuple(mean.shape) != (
                 self.ntot, c.n_ctrl, c.H, 4):
@@ -242,6 +295,7 @@ class Sim:
             ctypes.c_void_p(cost.data_ptr()), ctypes.c_void_p(best_cost.data_ptr()), _stream_ptr(stream)))
         return plan, cost, best_cost
 
+    @on_device
     def render_depth(self, height: int, width: int, hfov: float, vfov: float, max_range: float,
                      spheres=(), boxes=(), out: torch.Tensor | None = None,
                      stream=None) -> torch.Tensor:
@@ -258,6 +312,7 @@ class Sim:
             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
 
+    @on_device
     def status(self, stream=None) -> int:
         v = ctypes.c_uint32()
         self._check(self.lib.sim_status(self.h, ctypes.byref(v), _stream_ptr(stream)))

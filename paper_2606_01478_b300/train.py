@@ -14,7 +14,7 @@ import torch
 
 from . import _lib as L
 from .rollout import PolicyRollout, _p
-from .sim import _stream_ptr
+from .sim import _stream_ptr, on_device
 
 
 class PolicyTrainer:
@@ -24,6 +24,7 @@ class PolicyTrainer:
         if w0.numel() != L.POLICY_NPARAMS:
             raise ValueError("w0 must hold 5316 values")
         self.runner = runner
+        self.sim = runner.sim
         self.lr, self.b1, self.b2, self.eps = float(lr), float(betas[0]), float(betas[1]), float(eps)
         self.w = w0.detach().to(device=dev, dtype=torch.float32).contiguous().clone()
         self.m = torch.zeros_like(self.w)
@@ -34,6 +35,7 @@ class PolicyTrainer:
         self.dW = torch.zeros(L.POLICY_NPARAMS, dtype=torch.float32, device=dev)
         self.dx0 = None
 
+    @on_device
     def iteration(self, x0: torch.Tensor, p_ref: torch.Tensor, stream=None):
         if self.dx0 is None or self.dx0.shape != x0.shape:
             self.dx0 = torch.empty_like(x0)

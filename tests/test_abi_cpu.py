@@ -174,3 +174,15 @@ def test_select_elites_refuses_host_tensors():
     from paper_2606_01478_b300 import select_elites
     with pytest.raises(ValueError):
         select_elites(torch.zeros(2, 3), 1)
+
+
+def test_calls_refuse_a_stream_or_tensor_of_another_device():
+    """The binding refuses a stream that belongs to another GPU than the one the
+    call runs on (checked on the host, before anything launches)."""
+    import torch
+    from paper_2606_01478_b300.sim import _check_same_device
+    _check_same_device(torch.device("cuda", 1), torch.device("cuda", 1), "stream")
+    with pytest.raises(ValueError):
+        _check_same_device(torch.device("cuda", 1), torch.device("cuda", 0), "stream")
+    with pytest.raises(ValueError):
+        _check_same_device(torch.device("cpu"), torch.device("cuda", 0), "cost")

@@ -113,10 +113,11 @@ def test_rollout_single_step_horizon(reward):
     assert np.linalg.norm(dx0.cpu().numpy() - dx_ref) <= 1e-3 * np.linalg.norm(dx_ref)
 
 
-@pytest.mark.parametrize("elite_frac,n_e", [(1.0, 32), (1e-4, 1)])
-def test_mppi_elite_count_extremes(elite_frac, n_e):
-    """Elite fraction 1 on 100 samples per controller is capped at 32 elites;
-    a tiny fraction keeps one elite, whose plan is that sample's actions."""
+@pytest.mark.parametrize("n_e", [100, 1, 32, 33])
+def test_mppi_elite_count_extremes(n_e):
+    """Every sample of a 100-sample controller an elite (cluster path), a single
+    elite (whose plan is that sample's actions), and elite counts at and just
+    past one warp."""
     rng = np.random.default_rng(9)
     P = W.crazyflie_params()
     n, S, H, C = 4, 200, 8, 2
@@ -126,15 +127,14 @@ def test_mppi_elite_count_extremes(elite_frac, n_e):
     sim = Sim.batched(np.ones(n, np.int64), np.zeros(n, np.int32), RK4, 1 / 50)
     sim.set_params(P)
     sim.set_state(torch.tensor(x0, dtype=torch.float32, device="cuda"))
-    cfg = dict(S=S, H=H, n_ctrl=C, sigma=0.3, rho=0.6, elite_frac=elite_frac, lam=0.3, w_obs=1000.0)
-    assert mp.n_elites(S // C, elite_frac) == n_e
+    cfg = dict(S=S, H=H, n_ctrl=C, sigma=0.3, rho=0.6, n_elite=n_e, lam=0.3, w_obs=1000.0)
     mean0 = _f32(rng.uniform(-0.2, 0.2, (n, C, H, 4)))
     mean = torch.tensor(mean0, dtype=torch.float32, device="cuda")
     seed = torch.tensor([31], dtype=torch.int64, device="cuda")
     plan, cost, best = sim.mppi_iteration(cfg, seed, torch.tensor(goals, dtype=torch.float32, device="cuda"),
                                           np.zeros((0, 4)), mean)
     nxt, plan_ref, best_ref = mp.update(cost.cpu().numpy().astype(np.float64), mean0, 31, S, H, C, 0.3, 0.6,
-                                        elite_frac, 0.3, np.arange(n))
+                                        n_e, 0.3, np.arange(n))
     np.testing.assert_array_equal(best.cpu().numpy().astype(np.float64), best_ref)
     np.testing.assert_allclose(plan.cpu().numpy(), plan_ref, rtol=0, atol=2e-5)
     np.testing.assert_allclose(mean.cpu().numpy(), nxt, rtol=0, atol=2e-5)

@@ -1,8 +1,9 @@
 """GPU parity of the MPPI elite selection (sim_mppi_select_elites, the same
 device code the MPPI update runs) against the oracle's stable argsort: the
 selected sample indices must be identical, on rows with ties, NaN, +-inf,
-+-0, negative costs, fewer valid costs than elites, and rows long enough to
-take the memory path."""
++-0, negative costs and fewer valid costs than elites, on both kernels: one
+warp per row (up to 2048 costs and 32 elites) and one thread block per row
+(beyond that, up to SIM_MAX_ELITES elites)."""
 import ctypes
 
 import numpy as np
@@ -34,19 +35,19 @@ def _check(cost, n_e):
     for r in range(cost.shape[0]):
         el, jm = _expected(cost[r].astype(np.float64), n_e)
         got = idx[r]
-        assert np.array_equal(np.sort(got[:len(el)]), el), (r, np.sort(got[:len(el)]), el)
+        assert np.array_equal(got[:len(el)], el), (r, got[:len(el)], el)  # increasing index order
         assert np.all(got[len(el):] == -1)
         assert (jmin[r] == jm) or (np.isinf(jm) and np.isinf(jmin[r]))
 
 
-@pytest.mark.parametrize("S_c", [1, 5, 31, 32, 33, 100, 1600, 2048])
-@pytest.mark.parametrize("n_e", [1, 16, 32])
+@pytest.mark.parametrize("S_c", [1, 5, 31, 32, 33, 100, 1600, 2048, 2049, 100_000])
+@pytest.mark.parametrize("n_e", [1, 16, 32, 33, 1000, 4096])
 def test_random_rows(S_c, n_e):
     rng = np.random.default_rng(S_c * 100 + n_e)
     _check(rng.uniform(0.0, 1e4, (37, S_c)), n_e)
 
 
-@pytest.mark.parametrize("S_c", [64, 1600, 2048, 2049, 5000])
+@pytest.mark.parametrize("S_c", [64, 1600, 2048, 2049, 5000, 60_000])
 def test_ties_nan_inf_signed_zero(S_c):
     rng = np.random.default_rng(S_c)
     rows = []
@@ -74,7 +75,7 @@ def test_ties_nan_inf_signed_zero(S_c):
     rows.append(np.full(S_c, np.nan))
     # only infinities
     rows.append(np.where(rng.uniform(size=S_c) < 0.5, np.inf, -np.inf))
-    for n_e in (1, 8, 32):
+    for n_e in (1, 8, 32, 33, 500, 4096):
         _check(np.stack(rows), n_e)
 
 
@@ -84,7 +85,16 @@ def test_zero_rows_and_bad_arguments():
     idx = torch.zeros(4, 2, dtype=torch.int32, device="cuda")
     assert lib.sim_mppi_select_elites(ctypes.c_void_p(c.data_ptr()), 0, 8, 2,
                                       ctypes.c_void_p(idx.data_ptr()), None, None) == L.SIM_OK
-    for rows, S_c, n_e in ((-1, 8, 2), (4, 0, 2), (4, 8, 0), (4, 8, 33), ((1 << 33) + 1, 8, 2)):
+    for rows, S_c, n_e in ((-1, 8, 2), (4, 0, 2), (4, 8, 0), (4, 8, L.MAX_ELITES + 1), (1 << 31, 8, 2)):
         assert lib.sim_mppi_select_elites(ctypes.c_void_p(c.data_ptr()), rows, S_c, n_e,
                                           ctypes.c_void_p(idx.data_ptr()), None,
                                           None) == L.SIM_EINVAL
+
+
+def test_binding_reports_rejected_arguments_with_their_code():
+    """A rejected call surfaces as SimError carrying the library's code."""
+    from paper_2606_01478_b300 import SimError
+    c = torch.zeros(3, 10, device="cuda")
+    with pytest.raises(SimError) as ei:
+        select_elites(c, 0)
+    assert ei.value.code == L.SIM_EINVAL

@@ -103,6 +103,16 @@ def test_rollout_full_size_sampled_and_linearity():
     assert abs(loss.item() - 0.5 * (halves[0][0] + halves[1][0])) < 1e-5 * abs(loss.item())
 
 
+def test_rollout_gradient_1024_drones_against_oracle():
+    """dW over 16 CTAs of 64 drones (1024 drones, ragged-free), the full horizon
+    H = 250 with C = 25: the per-CTA partials and their fixed-order reduction
+    against the oracle's FP64 adjoint, with dL/dx0 of every drone."""
+    rw = W.policy_bptt(seed=43, M=1024, H=250, C=25)
+    sim, runner, x0, w, p_ref = _gpu_inputs(rw)
+    loss, dW, dx0 = runner.grad(x0, w.to(torch.bfloat16), p_ref)
+    _check(rw, loss.item(), dW.cpu().numpy(), dx0.cpu().numpy().astype(np.float64))
+
+
 def test_rollout_deterministic():
     rw = W.policy_bptt(seed=33, M=300, H=40, C=10)
     sim, runner, x0, w, p_ref = _gpu_inputs(rw)
@@ -207,9 +217,9 @@ def test_held_action_gradient(reward):
 def test_plain_bf16_operands_mode():
     """SIM_MLP_BF16 (plain bf16 tensor-core operands) at the full BPTT horizon
     (H = 250, C = 25, 256 drones): gradients against the FP64 oracle within
-    1e-2 norm-wise relative (a regression bound; the measured errors are
-    printed), and measurably less accurate than the default hi + lo split, so
-    the mode really changes the arithmetic."""
+    the 1e-3 norm-wise relative bar (the measured errors are printed), and
+    measurably less accurate than the default hi + lo split, so the mode really
+    changes the arithmetic."""
     rw = W.policy_bptt(seed=41, M=256, H=250, C=25)
     x0, p_ref = _as_oracle_inputs(rw)
     L_ref, _, dW_ref, dx_ref = po.rollout_grad(x0, rw.weights, p_ref, rw.params, rw.dt, rw.H, rw.w_act)
@@ -227,5 +237,5 @@ def test_plain_bf16_operands_mode():
                       _rel(dW.cpu().numpy(), g), _rel(dx0.cpu().numpy(), dx_ref))
     print("relative errors (loss, dW, dx0):", errs)
     assert max(errs["hilo"]) <= TOL
-    assert max(errs["bf16"]) <= 1e-2
+    assert max(errs["bf16"]) <= TOL
     assert errs["bf16"][1] > errs["hilo"][1]

@@ -432,7 +432,7 @@ class MppiWorkload:
     goals: np.ndarray        # [M, 3]
     obstacles: np.ndarray    # [n_obs, 4]
     dt: float
-    cfg: dict                # S, H, n_ctrl, sigma, rho, elite_frac, lam, w_obs
+    cfg: dict                # S, H, n_ctrl, sigma, rho, n_elite, lam, w_obs
     seed: int
 
 
@@ -453,6 +453,8 @@ def mppi_workload(seed: int = 1005, n_drones: int = 64, S: int = 8000, n_ctrl: i
     obs = np.zeros((n_obs, 4))
     obs[:, 0:3] = rng.uniform(np.array([-2.0, -2.0, 0.0]), np.array([2.0, 2.0, 4.0]), (n_obs, 3))
     obs[:, 3] = rng.uniform(0.1, 0.3, n_obs)
-    cfg = dict(S=S, H=H, n_ctrl=n_ctrl, sigma=0.3, rho=0.7, elite_frac=0.01, lam=0.05, w_obs=1000.0)
+    # top 1 % of each controller's samples (at least one): ceil(S_c / 100)
+    n_elite = max(1, -(-(S // n_ctrl) // 100))
+    cfg = dict(S=S, H=H, n_ctrl=n_ctrl, sigma=0.3, rho=0.7, n_elite=n_elite, lam=0.05, w_obs=1000.0)
     return MppiWorkload(f"mppi_{n_drones}x{S}_C{n_ctrl}_H{H}_50Hz", np.ones(n_drones, np.int64), P,
                         x0, goals, obs, dt, cfg, int(rng.integers(0, 2**62)))
