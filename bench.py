@@ -1,9 +1,14 @@
 """Benchmark of the B300 drone physics step (one JSON line on stdout).
 
-Default workload (the headline configuration): 16384 worlds x 1 drone,
-first-principles model, attitude interface, RK4 at dt = 1/500 s, 1000 steps
-fused as launches of K = 100.  One benchmark "step" is that whole rollout
-(10 launches).  The metric is drone-steps per second.
+Default workload (the headline configuration, the paper's swarm scale): a
+swarm of 1000 worlds x 4000 drones (4M drones), even worlds first-principles,
+odd worlds the abstracted identified model with per-world coefficients,
+attitude interface, Euler at dt = 1/500 s, 200 steps fused into one launch
+(K from the autotuner).  One benchmark "step" is that whole 200-step rollout.
+The metric is drone-steps per second; the line carries the fused launch's
+FP32 roofline, the single-step (K = 1) launches' HBM roofline, the end-to-end
+rate through the C-ABI with pinned host buffers, the FP64 oracle on the host
+cores and the final-state error against it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
 
@@ -30,17 +35,18 @@ import torch
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+import flopcount  # noqa: E402
 import workloads as W  # noqa: E402
 
-METRIC = "drone-steps/s (fwd, fused RK4, first-principles + attitude controller)"
+METRIC = ("drone-steps/s (fwd, fused Euler, 4M-drone swarm of first-principles and abstracted "
+          "drones, attitude controller)")
 UNIT = "drone-steps/s"
-# FP32 arithmetic of one RK4 drone-step of the first-principles model under the
-# attitude interface (FMA = 2 flop), counted term by term from the kernel's
-# formulation: controller 93 + 4 derivatives x 78 + RK4 combination 221 +
-# quaternion renormalisation 11 = 637 (command decode, amortised over 50-step
-# holds, adds ~1.2).
-FLOP_PER_DRONE_STEP = {("fp", "rk4", "attitude"): 637.0, ("fp", "euler", "attitude"): 216.0,
-                       ("abs", "euler", "attitude"): 58.0}
+# Algorithmic FP32 work per drone-step (flopcount.py: the method's formulas
+# restated on an op-counting scalar; additions, subtractions, multiplications,
+# divisions; the attitude decode amortised over 50-step command holds).
+_FLOPS = flopcount.table()
+FLOP_PER_DRONE_STEP = {(m, i, "attitude"): c["flop"] for (m, i), c in _FLOPS.items()}
+MUFU_PER_DRONE_STEP = {(m, i, "attitude"): c["mufu"] for (m, i), c in _FLOPS.items()}
 # Algorithmic HBM bytes of one single-step launch per drone: state in + out
 # (first-principles 5 float4 planes, abstracted 4) + one float4 command.
 BYTES_PER_DRONE_STEP = {"fp": 80 + 80 + 16, "abs": 64 + 64 + 16}
@@ -191,15 +197,29 @@ def _cpu_model() -> str:
     return "unknown"
 
 
+def world_subset(wl, worlds: int):
+    """The first `worlds` worlds of a uniform-N workload (an exact sub-problem:
+    drones do not interact)."""
+    import dataclasses
+    n = worlds * wl.N
+    return dataclasses.replace(wl, name=f"{wl.name}_first{worlds}worlds", M=worlds,
+                               param_set_of_world=wl.param_set_of_world[:worlds],
+                               model_of_world=wl.model_of_world[:worlds], x0=wl.x0[:n],
+                               cmd=wl.cmd[:, :n])
+
+
 def cpu_baseline(wl, budget_s: float = 12.0) -> dict:
     """The oracle as it stands on the host cores, on a bounded sample of the
-    workload: all worlds, as many steps as fit about budget_s seconds."""
-    dt1, _ = oracle_sample(wl, wl.M, 2)
+    workload (`wl` is already the sample's worlds): all its drones, as many
+    steps as fit about budget_s seconds."""
+    n = wl.M * wl.N
+    dt1, _ = oracle_sample(wl, n, 2)
     steps = int(max(4, min(wl.steps, budget_s / max(dt1 / 2, 1e-6))))
-    secs, units = oracle_sample(wl, wl.M, steps)
+    secs, units = oracle_sample(wl, n, steps)
     return {"value": units / secs, "unit": UNIT, "cores": torch.get_num_threads(),
             "cpu": _cpu_model(), "kind": "oracle",
-            "sample": f"{wl.M} drones x {steps} of {wl.steps} steps (FP64 torch CPU oracle)"}
+            "sample": f"{n} drones ({wl.M} worlds x {wl.N}) x {steps} of {wl.steps} steps "
+                      "(FP64 torch CPU oracle)"}
 
 
 STATE_FIELDS = {"p_m": slice(0, 3), "q": slice(3, 7), "v_m_s": slice(7, 10), "w_rad_s": slice(10, 13),
@@ -227,24 +247,36 @@ ABS_FIELDS = {"p_m": slice(0, 3), "psi_rad": slice(3, 6), "v_m_s": slice(6, 9),
               "psidot_rad_s": slice(9, 12), "f_sigma_N": slice(12, 13)}
 
 
-def mixed_error_vs_fp64(sample, gpu_rows) -> dict:
-    """Final-state error of the mixed swarm's 200 steps against the FP64 oracle on 64
-    sampled drones of each model, from the float32 inputs the GPU received (part of
-    the CPU-baseline leg)."""
-    import dataclasses
+def mixed_sample(wl, per_model: int = 64, seed: int = 2):
+    """Drones drawn from each model of a mixed workload, with their inputs, for
+    the FP64 comparison of the CPU leg."""
+    rng = np.random.default_rng(seed)
+    models = wl.model_of_world[np.arange(wl.M * wl.N) // wl.N]
+    sample = np.concatenate([rng.choice(np.nonzero(models == m)[0], per_model, replace=False)
+                             for m in np.unique(models)])
+    return {"drones": sample, "x0": wl.x0[sample].copy(), "cmd": wl.cmd[:, sample].copy(),
+            "world": sample // wl.N, "wl": wl}
+
+
+def mixed_error_vs_fp64(ms, gpu_rows) -> dict:
+    """Final-state error of a mixed swarm's rollout against the FP64 oracle on
+    the sampled drones of each model, from the float32 inputs the GPU received
+    (part of the CPU-baseline leg)."""
     from oracle import physics as ph
-    wl = W.mixed_swarm_euler()
+    wl = ms["wl"]
     f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
-    wl32 = dataclasses.replace(wl, x0=f32(wl.x0), cmd=f32(wl.cmd))
-    ref = ph.rollout_workload(wl32, drones=sample).numpy()
+    world = ms["world"]
+    models = wl.model_of_world[world]
+    ref = ph.rollout(f32(ms["x0"]), f32(ms["cmd"]), wl.hold, wl.steps, wl.params,
+                     wl.param_set_of_world[world], models, wl.dt, wl.integrator, wl.ctrl).numpy()
     err = np.abs(np.asarray(gpu_rows, np.float64) - ref)
-    models = wl.model_of_world[np.asarray(sample) // wl.N]
-    out = {"drones_per_model": 64, "steps": int(wl.steps),
+    out = {"drones_per_model": int(len(ms["drones"]) // len(np.unique(models))), "steps": int(wl.steps),
            "reference": "FP64 oracle from the same float32 inputs"}
     for m, name, fields in ((0, "first_principles", STATE_FIELDS), (1, "abstracted", ABS_FIELDS)):
         e = err[models == m]
-        out[name] = {"max_abs": {k: float(e[:, sl].max()) for k, sl in fields.items()},
-                     "median_abs": {k: float(np.median(e[:, sl])) for k, sl in fields.items()}}
+        if len(e):
+            out[name] = {"max_abs": {k: float(e[:, sl].max()) for k, sl in fields.items()},
+                         "median_abs": {k: float(np.median(e[:, sl])) for k, sl in fields.items()}}
     return out
 
 
@@ -262,16 +294,21 @@ def sampling_error_vs_fp64(drones, samples, seed, gpu_cost) -> dict:
             "reference": "FP64 oracle from the same float32 inputs, same Philox seed"}
 
 
+CPU_WORLDS = 4  # the oracle's sample of the headline swarm: worlds 0-3 (two of each model)
+
+
 def run_reference(args, wl):
     dist, rank, ws = _dist()
     if rank != 0:
         return 0
-    n_steps = 20
+    sub = world_subset(wl, CPU_WORLDS)
+    n = sub.M * sub.N
+    n_steps = 10
     for _ in range(args.warmup):
-        oracle_sample(wl, wl.M, n_steps)
+        oracle_sample(sub, n, n_steps)
     secs, units = 0.0, 0
     for _ in range(args.steps):
-        s, u = oracle_sample(wl, wl.M, n_steps)
+        s, u = oracle_sample(sub, n, n_steps)
         secs += s
         units += u
     value = units / secs
@@ -279,35 +316,245 @@ def run_reference(args, wl):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": _config(wl, args),
+        "data": "synthetic", "config": _config(wl, args, wl.K),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(),
                          "cpu": _cpu_model(), "kind": "oracle",
-                         "sample": f"{wl.M} drones x {n_steps} of {wl.steps} steps per step"},
+                         "sample": f"{n} drones ({sub.M} worlds x {sub.N}, both models) x {n_steps} "
+                                   f"of {wl.steps} steps per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def _config(wl, args):
+def _config(wl, args, K):
     return {"workload": wl.name, "worlds": wl.M, "drones_per_world": wl.N,
-            "model": "first-principles", "integrator": "rk4", "control": "attitude",
-            "dt": wl.dt, "steps_per_rollout": wl.steps, "K_fused": wl.K,
-            "parallelism": f"replicas x{args.gpus} (independent worlds)",
-            "l2": "flushed (256 MiB write) before every timed iteration"}
+            "model": "mixed: first-principles (even worlds), abstracted (odd worlds, coefficients "
+                     "x U(0.9, 1.1) per world)",
+            "integrator": "euler", "control": "attitude", "dt": wl.dt, "steps_per_rollout": wl.steps,
+            "K_fused": K, "parallelism": f"replicas x{args.gpus} (independent worlds)",
+            "l2": "flushed (256 MiB write) before every timed iteration; the inputs (320 MB of "
+                  "state planes, 256 MB of command blocks) exceed L2"}
+
+
+def _fp32_peak():
+    pk, kind = peaks()
+    clk = pk.get("sm_max_mhz", 2032.0)
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12, clk, kind
 
 
 # --------------------------------------------------------------------------- B300 arm
 
 
 def run_b300(args, wl):
-    from paper_2606_01478_b300 import Sim
+    from paper_2606_01478_b300 import Sim, autotune
     dist, rank, ws = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    n = wl.M * wl.N
+    n_fp = int((wl.model_of_world == 0).sum()) * wl.N
+    n_abs = n - n_fp
 
+    sim = Sim.batched(np.full(wl.M, wl.N), wl.model_of_world, wl.integrator, wl.dt, ctrl=wl.ctrl,
+                      max_cmd_blocks=wl.cmd.shape[0], device=dev)
+    sim.set_params(wl.params, wl.param_set_of_world)
+    x0_host = torch.from_numpy(np.ascontiguousarray(wl.x0, dtype=np.float32)).pin_memory()
+    cmd_host = torch.from_numpy(np.ascontiguousarray(wl.cmd, dtype=np.float32)).pin_memory()
+    out_host = torch.empty_like(x0_host).pin_memory()
+    x0_dev = x0_host.to(dev)
+    cmd_dev = cmd_host.to(dev)
+    # what the CPU leg needs, then drop the float64 arrays (1.2 GB)
+    sub = world_subset(wl, CPU_WORLDS)
+    sub.x0, sub.cmd = sub.x0.copy(), sub.cmd.copy()
+    msample = mixed_sample(wl)
+    wl.x0 = wl.cmd = None
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    sim.set_state(x0_dev)
+    sim.set_commands(cmd_dev, wl.hold)
+    if args.tpb:
+        sim.set_block_size(args.tpb)
+        tuned = {"tpb": args.tpb, "K": wl.K, "source": "--tpb"}
+    else:
+        tuned = autotune.tune_step(sim, wl.steps, Ks=(50, 100, 200), reps=1)
+        tuned = {k: v for k, v in tuned.items() if k != "table"}
+    K = int(tuned["K"])
+    n_launch = (wl.steps + K - 1) // K
+
+    def reset():
+        sim.set_state(x0_dev)
+        sim.set_commands(cmd_dev, wl.hold)
+
+    def timed(fn, it):
+        reset()
+        flush.fill_(it & 0xFF)
+        # keep the device busy while the host enqueues the launches, so the
+        # events time device execution and not host launch latency
+        torch.cuda._sleep(1_000_000)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        reset()
+        sim.run(wl.steps, K)
+    torch.cuda.synchronize()
+    assert sim.status() == 0, "non-finite state during warm-up"
+
+    # device-resident timing (inputs already in HBM): two events per rollout
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    _barrier(dist)
+    torch.cuda.synchronize()
+    per_iter_ms = [timed(lambda: sim.run(wl.steps, K), it) for it in range(args.steps)]
+    torch.cuda.synchronize()
+    _barrier(dist)
+    clocks = sampler.stop()
+    gpu_launches = args.steps * n_launch
+    total_ms = _max_over_ranks(dist, sum(per_iter_ms))
+    units = n * wl.steps * args.steps * ws
+    value = units / (total_ms / 1e3)
+
+    # the same rollout as 200 single-step launches (each reads and writes the
+    # state planes once): the HBM roofline of the step
+    k1_ms = statistics.median([timed(lambda: sim.run(wl.steps, 1), it) for it in range(3)])
+
+    # end to end through the C-ABI with host buffers (pinned): state and command
+    # blocks in, the final state out, inside the timed region
+    e2e_ms = []
+    for it in range(args.steps):
+        flush.fill_(it & 0xFF)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        sim.run_host(x0_host, cmd_host, wl.hold, wl.steps, K, out=out_host)
+        t1.record(stream)
+        t1.synchronize()
+        e2e_ms.append(t0.elapsed_time(t1))
+    e2e_total = _max_over_ranks(dist, sum(e2e_ms))
+    assert sim.status() == 0
+    h2d = x0_host.numel() * 4 + cmd_host.numel() * 4
+    d2h = out_host.numel() * 4
+    final_sample = out_host.numpy()[msample["drones"]].copy()
+    del sim, x0_dev, cmd_dev, flush
+    torch.cuda.empty_cache()
+
+    if rank != 0:
+        return 0
+    fp32_peak, clk_max, pk_kind = _fp32_peak()
+    f_fp = FLOP_PER_DRONE_STEP[("fp", "euler", "attitude")]
+    f_abs = FLOP_PER_DRONE_STEP[("abs", "euler", "attitude")]
+    flop_per_step = n_fp * f_fp + n_abs * f_abs
+    # average launch duration over the timed region (rollout time / launches)
+    avg_launch_s = total_ms / (args.steps * n_launch) / 1e3
+    achieved = flop_per_step * K / avg_launch_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak,
+            "traffic": _profiled_traffic("step_batched_kernel", wl.name),
+            "kernel": "step_batched_kernel<Euler, attitude, lag rotors> (first-principles and "
+                      "abstracted warps in one persistent launch)",
+            "flop_per_drone_step": {"first_principles": f_fp, "abstracted": f_abs},
+            "mufu_per_drone_step": {"first_principles": MUFU_PER_DRONE_STEP[("fp", "euler", "attitude")],
+                                    "abstracted": MUFU_PER_DRONE_STEP[("abs", "euler", "attitude")]},
+            "flop_source": "flopcount.py (the method's formulas on an op-counting scalar)",
+            "launch_ms_timed_region": avg_launch_s * 1e3,
+            "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                          f"{clk_max:.0f} MHz (max SM clock, {pk_kind} peaks file)"}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / (fp32_peak * clocks["sm_mhz"] / clk_max)
+    pk, kind = peaks()
+    byt = n_fp * BYTES_PER_DRONE_STEP["fp"] + n_abs * BYTES_PER_DRONE_STEP["abs"]
+    hbm = byt * wl.steps / (k1_ms / 1e3) / 1e9
+    single = {"value": n * wl.steps / (k1_ms / 1e3), "unit": UNIT, "ms": k1_ms, "K": 1,
+              "launches": wl.steps,
+              "roofline": {"bound": "hbm", "achieved": hbm, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                           "frac": hbm / pk["hbm_gbs"],
+                           "traffic": _profiled_traffic("step_batched_single_kernel", wl.name + "_K1"),
+                           "kernel": "step_batched_single_kernel", "bytes_per_launch": byt,
+                           "peak_basis": f"{kind} HBM copy bandwidth"}}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config(wl, args, K),
+        "e2e": {"value": units / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": gpu_launches,
+        "roofline": roof,
+        "single_step": single,
+        "clocks": clocks,
+    }
+    line["config"]["tpb"] = tuned["tpb"]
+    line["autotune"] = tuned
+    sd_final = bptt_sub = att = None
+    if not args.no_extra:
+        att, att_final = measure_attitude_swarm(dev)
+        sd, sd_final = measure_single_drone(dev)
+        bptt_sub = bptt_subset_gradients(dev)
+        line["extra"] = {"attitude_swarm": att, "single_drone": sd, "policy_bptt": measure_policy_bptt(dev),
+                         "sampling": measure_sampling(dev), "mppi": measure_mppi(dev),
+                         "bptt_training": measure_bptt_training(dev), "depth": measure_depth(dev),
+                         "swarm_scale": measure_swarm_scale(dev)}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sub)
+        line["error_vs_fp64"] = mixed_error_vs_fp64(msample, final_sample)
+        if att is not None:
+            awl = W.attitude_swarm_rk4()
+            att["cpu_baseline"] = cpu_baseline(awl, budget_s=6.0)
+            att["error_vs_fp64"] = error_vs_fp64(awl, att_final)
+        if sd_final is not None:
+            line["extra"]["single_drone"]["error_vs_fp64"] = error_vs_fp64(W.position_hold_single(), sd_final, n_drones=1)
+        if bptt_sub is not None:
+            line["extra"]["policy_bptt"]["gradient_error_vs_fp64"] = gradient_error_vs_fp64(*bptt_sub)
+        if "extra" in line:
+            sp = line["extra"]["sampling"]
+            sp["cost_error_vs_fp64"] = sampling_error_vs_fp64(*sp["_cost_sample"])
+    if "extra" in line:  # GPU results kept for the CPU leg, not part of the record
+        line["extra"]["sampling"].pop("_cost_sample", None)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def measure_mixed(dev, reps: int = 3, worlds: int = 1000) -> dict:
+    """The headline swarm (or its first `worlds` worlds) as fused launches, on
+    its own: used for profiling the step on a smaller case of the same mix."""
+    from paper_2606_01478_b300 import Sim, autotune
+    wl = W.mixed_swarm_euler(M=worlds)
+    sim = Sim.batched(np.full(wl.M, wl.N), wl.model_of_world, wl.integrator, wl.dt, ctrl=wl.ctrl,
+                      max_cmd_blocks=wl.cmd.shape[0], device=dev)
+    sim.set_params(wl.params, wl.param_set_of_world)
+    x0 = torch.tensor(wl.x0, dtype=torch.float32, device=dev)
+    cmd = torch.tensor(wl.cmd, dtype=torch.float32, device=dev)
+    sim.set_state(x0)
+    sim.set_commands(cmd, wl.hold)
+    tuned = autotune.tune_step(sim, wl.steps, Ks=(wl.K,), reps=1)
+
+    def run():
+        sim.set_state(x0)
+        sim.set_commands(cmd, wl.hold)
+        sim.run(wl.steps, wl.K)
+    ms = _time_ms(run, reps, dev)
+    assert sim.status() == 0
+    return {"workload": wl.name, "value": wl.M * wl.N * wl.steps / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "K": wl.K, "tpb": tuned["tpb"]}
+
+
+def measure_attitude_swarm(dev, reps: int = 5):
+    """16384 worlds x 1 drone, first-principles, attitude interface, RK4 at
+    500 Hz, 1000 steps as 10 chained launches of K = 100: drone-steps/s, the
+    fused launch's FP32 roofline, and end to end through the C-ABI with pinned
+    host buffers.  Returns the record and the final state (its error against
+    the FP64 oracle is taken in the CPU leg)."""
+    from paper_2606_01478_b300 import Sim, autotune
+    wl = W.attitude_swarm_rk4()
+    stream = torch.cuda.current_stream(dev)
     sim = Sim(wl.M, wl.N, 0, wl.integrator, wl.dt, ctrl=wl.ctrl, max_cmd_blocks=wl.cmd.shape[0],
               device=dev)
     sim.set_params(wl.params, wl.param_set_of_world)
@@ -316,81 +563,28 @@ def run_b300(args, wl):
     x0_host = torch.tensor(wl.x0, dtype=torch.float32).pin_memory()
     cmd_host = torch.tensor(wl.cmd, dtype=torch.float32).pin_memory()
     out_host = torch.empty_like(x0_host).pin_memory()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     sim.set_state(x0_dev)
     sim.set_commands(cmd_dev, wl.hold)
-    if args.tpb:
-        sim.set_block_size(args.tpb)
-        tuned = {"tpb": args.tpb, "K": wl.K, "source": "--tpb"}
-    else:
-        from paper_2606_01478_b300 import autotune
-        tuned = autotune.tune_step(sim, wl.steps, tag="attitude_swarm", Ks=(wl.K,), reps=2)
-        tuned = {k: v for k, v in tuned.items() if k != "table"}
+    tuned = autotune.tune_step(sim, wl.steps, Ks=(wl.K,), reps=2)
     n_launch = (wl.steps + wl.K - 1) // wl.K
 
-    def one_rollout(events):
-        for j in range(n_launch):
-            k = min(wl.K, wl.steps - j * wl.K)
-            if events is not None:
-                events[j][0].record(stream)
-            sim.step(k)
-            if events is not None:
-                events[j][1].record(stream)
-
-    def reset():
+    def rollout():
         sim.set_state(x0_dev)
         sim.set_commands(cmd_dev, wl.hold)
-
-    for _ in range(args.warmup):
-        reset()
-        one_rollout(None)
-    torch.cuda.synchronize()
-    assert sim.status() == 0, "non-finite state during warm-up"
-
-    # device-resident timing (inputs already in HBM): two events per rollout
-    launches0 = sim.launches
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    _barrier(dist)
-    torch.cuda.synchronize()
-    per_iter_ms = []
-    for it in range(args.steps):
-        reset()
-        flush.fill_(it & 0xFF)
-        # keep the device busy while the host enqueues the rollout, so the
-        # events time device execution and not host launch latency
+        _flush_l2(dev)
         torch.cuda._sleep(1_000_000)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        one_rollout(None)
+        sim.run(wl.steps, wl.K)
         e1.record(stream)
-        torch.cuda.synchronize()
-        per_iter_ms.append(e0.elapsed_time(e1))
-    torch.cuda.synchronize()
-    _barrier(dist)
-    clocks = sampler.stop()
-    # the set_state launch of each reset is not part of the timed region
-    gpu_launches = sim.launches - launches0 - args.steps * 1
-    # per-launch durations of the step kernel (for the roofline), in a separate pass
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_launch)]
-    launch_ms = []
-    for it in range(args.steps):
-        reset()
-        flush.fill_(it & 0xFF)
-        torch.cuda._sleep(1_000_000)
-        one_rollout(ev)
-        torch.cuda.synchronize()
-        launch_ms += [e[0].elapsed_time(e[1]) for e in ev]
-    total_ms = _max_over_ranks(dist, sum(per_iter_ms))
-    units = wl.M * wl.steps * args.steps * ws
-    value = units / (total_ms / 1e3)
-
-    # end to end through the C-ABI with host buffers
-    e2e_ms = []
-    for it in range(args.steps):
-        flush.fill_(it & 0xFF)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+    rollout()
+    ms = statistics.median([rollout() for _ in range(reps)])
+    e2e = []
+    for _ in range(reps):
+        _flush_l2(dev)
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
@@ -398,73 +592,23 @@ def run_b300(args, wl):
         sim.run_host(x0_host, cmd_host, wl.hold, wl.steps, wl.K, out=out_host)
         t1.record(stream)
         t1.synchronize()
-        e2e_ms.append(t0.elapsed_time(t1))
-    e2e_total = _max_over_ranks(dist, sum(e2e_ms))
+        e2e.append(t0.elapsed_time(t1))
     assert sim.status() == 0
-    h2d = x0_host.numel() * 4 + cmd_host.numel() * 4
-    d2h = out_host.numel() * 4
-
-    if rank != 0:
-        return 0
-    pk, pk_kind = peaks()
-    clk_max = pk.get("sm_max_mhz", 2032.0)
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clk_max * 1e6 / 1e12
+    units = wl.M * wl.steps
+    peak, _, _ = _fp32_peak()
     flop = FLOP_PER_DRONE_STEP[("fp", "rk4", "attitude")]
-    # average launch duration over the timed region: the rollout's launches run
-    # back to back on one stream (chained, each scheduled while the previous one
-    # drains), so rollout time / launches; the separate pass above times each
-    # launch between its own events, which serialises the chain
-    avg_launch_s = total_ms / (args.steps * n_launch) / 1e3
-    achieved = flop * wl.M * wl.K / avg_launch_s / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak,
-            "traffic": _profiled_traffic("step_kernel", wl.name),
-            "kernel": "step_kernel<first-principles, RK4, attitude>",
-            "flop_per_drone_step": flop,
-            "launch_ms_timed_region": avg_launch_s * 1e3,
-            "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
-                          f"{clk_max:.0f} MHz (max SM clock, {pk_kind} peaks file)"}
-    if clocks.get("sm_mhz"):
-        roof["frac_at_sampled_clock"] = achieved / (fp32_peak * clocks["sm_mhz"] / clk_max)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": _config(wl, args),
-        "e2e": {"value": units / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": gpu_launches,
-        "launch_ms": {"mean": statistics.mean(launch_ms), "min": min(launch_ms),
-                      "max": max(launch_ms), "count": len(launch_ms)},
-        "roofline": roof,
-        "clocks": clocks,
-    }
-    line["config"]["tpb"] = tuned["tpb"]
-    line["autotune"] = tuned
-    sd_final = bptt_sub = None
-    if not args.no_extra:
-        sd, sd_final = measure_single_drone(dev)
-        bptt_sub = bptt_subset_gradients(dev)
-        line["extra"] = {"single_drone": sd, "mixed_swarm": measure_mixed_swarm(dev), "policy_bptt": measure_policy_bptt(dev),
-                         "sampling": measure_sampling(dev), "mppi": measure_mppi(dev),
-                         "bptt_training": measure_bptt_training(dev), "depth": measure_depth(dev),
-                         "swarm_scale": measure_swarm_scale(dev)}
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl)
-        line["error_vs_fp64"] = error_vs_fp64(wl, out_host.numpy())
-        if sd_final is not None:
-            line["extra"]["single_drone"]["error_vs_fp64"] = error_vs_fp64(W.position_hold_single(), sd_final, n_drones=1)
-        if bptt_sub is not None:
-            line["extra"]["policy_bptt"]["gradient_error_vs_fp64"] = gradient_error_vs_fp64(*bptt_sub)
-        if "extra" in line:
-            mx, sp = line["extra"]["mixed_swarm"], line["extra"]["sampling"]
-            mx["error_vs_fp64"] = mixed_error_vs_fp64(*mx["_final_sample"])
-            sp["cost_error_vs_fp64"] = sampling_error_vs_fp64(*sp["_cost_sample"])
-    if "extra" in line:  # GPU results kept for the CPU leg, not part of the record
-        line["extra"]["mixed_swarm"].pop("_final_sample", None)
-        line["extra"]["sampling"].pop("_cost_sample", None)
-    print(json.dumps(line), flush=True)
-    return 0
+    achieved = flop * units / (ms / 1e3) / 1e12
+    rec = {"workload": wl.name, "value": units / (ms / 1e3), "unit": UNIT, "ms_per_rollout": ms,
+           "K": wl.K, "launches": n_launch, "tpb": tuned["tpb"],
+           "e2e": {"value": units / (statistics.median(e2e) / 1e3), "unit": UNIT,
+                   "h2d_bytes_per_step": (x0_host.numel() + cmd_host.numel()) * 4,
+                   "d2h_bytes_per_step": out_host.numel() * 4},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "flop_per_drone_step": flop,
+                        "traffic": _profiled_traffic("step_kernel", wl.name),
+                        "kernel": "step_kernel<first-principles, RK4, attitude>",
+                        "note": "16384 drones = 512 warps < 592 SM sub-partitions: latency bound"}}
+    return rec, out_host.numpy().copy()
 
 
 def bptt_subset_gradients(dev, M: int = 64):
@@ -538,78 +682,6 @@ def measure_single_drone(dev, reps: int = 5):
             "note": "one drone: one thread's dependent chain, latency bound"}, final
 
 
-def measure_mixed_swarm(dev, reps: int = 3) -> dict:
-    """The mixed swarm (1000 worlds x 4000 drones, 50/50 first-principles / abstracted,
-    Euler, 200 steps) in both modes: one fused launch of K = 200 (FP32-issue
-    bound) and 200 launches of K = 1 (HBM bound)."""
-    from paper_2606_01478_b300 import Sim
-    from paper_2606_01478_b300 import autotune
-    wl = W.mixed_swarm_euler()
-    n = wl.M * wl.N
-    sim = Sim.batched(np.full(wl.M, wl.N), wl.model_of_world, wl.integrator, wl.dt, ctrl=wl.ctrl,
-                      max_cmd_blocks=wl.cmd.shape[0], device=dev)
-    sim.set_params(wl.params, wl.param_set_of_world)
-    x0 = torch.tensor(wl.x0, dtype=torch.float32, device=dev)
-    cmd = torch.tensor(wl.cmd, dtype=torch.float32, device=dev)
-    del wl.x0, wl.cmd
-    sim.set_state(x0)
-    sim.set_commands(cmd, wl.hold)
-    tuned = autotune.tune_step(sim, wl.steps, tag="mixed_swarm", Ks=(1, 200), reps=1)
-    stream = torch.cuda.current_stream(dev)
-    n_fp = n // 2
-    n_abs = n - n_fp
-    out = {}
-    for K in (wl.steps, 1):
-        times = []
-        for r in range(reps + 1):
-            sim.set_state(x0)
-            sim.set_commands(cmd, wl.hold)
-            _flush_l2(dev)
-            torch.cuda._sleep(1_000_000)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sim.run(wl.steps, K)
-            e1.record(stream)
-            e1.synchronize()
-            if r:
-                times.append(e0.elapsed_time(e1))
-        ms = statistics.median(times)
-        units = n * wl.steps
-        rec = {"value": units / (ms / 1e3), "unit": UNIT, "ms": ms, "K": K,
-               "launches": (wl.steps + K - 1) // K, "tpb": tuned["tpb"]}
-        if K == 1:
-            byt = n_fp * BYTES_PER_DRONE_STEP["fp"] + n_abs * BYTES_PER_DRONE_STEP["abs"]
-            pk, kind = peaks()
-            achieved = byt * wl.steps / (ms / 1e3) / 1e9
-            rec["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
-                               "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                               "traffic": _profiled_traffic("step_batched_single_kernel", wl.name + "_K1"),
-                               "bytes_per_launch": byt,
-                               "peak_basis": f"{kind} HBM copy bandwidth"}
-        else:
-            flop = (n_fp * FLOP_PER_DRONE_STEP[("fp", "euler", "attitude")]
-                    + n_abs * FLOP_PER_DRONE_STEP[("abs", "euler", "attitude")])
-            pk, kind = peaks()
-            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-            achieved = flop * wl.steps / (ms / 1e3) / 1e12
-            rec["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak,
-                               "unit": "TFLOP/s", "frac": achieved / peak,
-                               "traffic": _profiled_traffic("step_batched_kernel", wl.name),
-                               "note": "abstracted drones also issue 6 MUFU sin/cos per step"}
-        out[f"fused_K{K}" if K > 1 else "single_step_K1"] = rec
-    assert sim.status() == 0
-    # 64 drones of each model, for the FP64 comparison of the CPU leg (the state
-    # after the last run: 200 steps from x0)
-    rng = np.random.default_rng(2)
-    models = wl.model_of_world[np.arange(n) // wl.N]
-    sample = np.concatenate([rng.choice(np.nonzero(models == m)[0], 64, replace=False) for m in (0, 1)])
-    out["_final_sample"] = (sample, sim.get_state()[torch.as_tensor(sample, device=dev)].cpu().numpy())
-    out["workload"] = "swarm_1000x4000_mixed_euler_attitude_200"
-    out["autotune"] = {k: v for k, v in tuned.items() if k != "table"}
-    return out
-
-
 def measure_swarm_scale(dev, reps: int = 3) -> dict:
     """The headline's step (first-principles, RK4, attitude interface, lag rotors) on
     2^20 drones, one fused launch of K = 100 steps.  The 16384 drones of the headline
@@ -626,7 +698,7 @@ def measure_swarm_scale(dev, reps: int = 3) -> dict:
     cmd = torch.tensor(wl.cmd, dtype=torch.float32, device=dev)
     sim.set_state(x0)
     sim.set_commands(cmd, wl.hold)
-    tuned = autotune.tune_step(sim, wl.steps, tag="swarm_scale", Ks=(wl.K,), reps=1)
+    tuned = autotune.tune_step(sim, wl.steps, Ks=(wl.K,), reps=1)
     stream = torch.cuda.current_stream(dev)
     times = []
     for r in range(reps + 1):
@@ -739,18 +811,18 @@ def measure_policy_bptt(dev, reps: int = 3) -> dict:
     }
 
 
-# FP32 work of one sampled RK4 step: the step (637), the per-step attitude
-# decode (25), noise scaling and Box-Muller (15) and the goal distance (10).
-# Obstacle tests are not counted: the kernel drops obstacles outside a drone's
-# reach bound (exact zeros), leaving almost none; Philox integer work and MUFU
-# calls are not counted either.  ncu measures 773 executed flop per sample-step.
-SAMPLE_FLOP_PER_STEP = 637.0 + 25.0 + 15.0 + 10.0
+# FP32 work of one sampled RK4 step (flopcount.py): the step, the action decode
+# every step, the noise's Box-Muller arithmetic and scaling, and the goal
+# distance.  Obstacle terms of obstacles beyond a drone's reach (exact zeros,
+# which the kernel skips) and Philox's integer rounds are not counted.
+SAMPLE_FLOP_PER_STEP = float(flopcount.sampling_step()["flop"])
 
 
 def measure_sampling(dev, reps: int = 3) -> dict:
     """The uneven sampling workload (512 worlds, log-uniform drone counts, 256 samples, 50 RK4
     steps): one persistent sampling launch per outer iteration, replayed from a
-    CUDA graph with a fresh device seed each time; block size autotuned."""
+    CUDA graph with a fresh device seed each time; block size from the library's
+    autotuner (sim_autotune, SIM_TUNE_SAMPLE)."""
     from paper_2606_01478_b300 import RK4, Sim
     wl = W.uneven_sampling_rk4()
     n = len(wl.x0)
@@ -760,14 +832,9 @@ def measure_sampling(dev, reps: int = 3) -> dict:
     goals = torch.tensor(wl.goals, dtype=torch.float32, device=dev)
     seed = torch.tensor([wl.seed], dtype=torch.int64, device=dev)
     cost = torch.empty(n, wl.S, device=dev)
-    best = None
-    for tpb in (64, 128, 256):
-        sim.set_block_size(tpb)
-        ms = _time_ms(lambda: sim.sample_rollouts(wl.S, wl.H, seed, wl.sigma, goals, wl.obstacles,
-                                                  wl.w_obs, cost=cost), 1, dev)
-        if best is None or ms < best[1]:
-            best = (tpb, ms)
-    sim.set_block_size(best[0])
+    from paper_2606_01478_b300 import autotune
+    tuned = autotune.tune_sample(sim, wl.S, wl.H, seed, wl.sigma, goals, wl.obstacles, wl.w_obs, cost,
+                                 tpbs=(64, 128, 256), reps=1)
     g = torch.cuda.CUDAGraph()
     st = torch.cuda.Stream(dev)
     st.wait_stream(torch.cuda.current_stream(dev))
@@ -791,7 +858,8 @@ def measure_sampling(dev, reps: int = 3) -> dict:
     achieved = SAMPLE_FLOP_PER_STEP * units / (ms / 1e3) / 1e12
     return {"workload": wl.name, "drones": n, "samples_per_drone": wl.S, "horizon": wl.H,
             "value": units / (ms / 1e3), "unit": UNIT, "ms_per_outer_iteration": ms,
-            "rollouts_per_s": n * wl.S / (ms / 1e3), "tpb": best[0], "_cost_sample": cost_sample,
+            "rollouts_per_s": n * wl.S / (ms / 1e3), "tpb": tuned["tpb"],
+            "autotune": {k: v for k, v in tuned.items() if k != "table"}, "_cost_sample": cost_sample,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
                          "traffic": _profiled_traffic("sample_kernel", wl.name),
@@ -920,7 +988,9 @@ def main(argv=None):
     ap.add_argument("--tpb", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the measurements beside the headline")
-    ap.add_argument("--only", choices=["mixed", "bptt", "sampling", "mppi", "training", "depth", "scale"],
+    ap.add_argument("--worlds", type=int, default=1000, help="worlds of --only mixed")
+    ap.add_argument("--only", choices=["mixed", "attitude", "bptt", "sampling", "mppi", "training", "depth",
+                                       "scale"],
                     default=None,
                     help="run one extra workload alone and print its record (for profiling)")
     args = ap.parse_args(argv)
@@ -930,13 +1000,15 @@ def main(argv=None):
         local = int(os.environ.get("LOCAL_RANK", "0"))
         torch.cuda.set_device(local)
         dev = torch.device("cuda", local)
-        fn = {"mixed": measure_mixed_swarm, "bptt": measure_policy_bptt, "sampling": measure_sampling,
+        fn = {"mixed": lambda d, reps: measure_mixed(d, reps, args.worlds),
+              "attitude": lambda d, reps: measure_attitude_swarm(d, reps)[0],
+              "bptt": measure_policy_bptt, "sampling": measure_sampling,
               "mppi": measure_mppi, "training": measure_bptt_training, "depth": measure_depth,
               "scale": measure_swarm_scale}[args.only]
         print(json.dumps({"only": args.only, "record": fn(dev, reps=args.steps)}), flush=True)
         return 0
     rank = int(os.environ.get("RANK", "0"))
-    wl = W.attitude_swarm_rk4(seed=1001 + 7919 * rank)
+    wl = W.mixed_swarm_euler(seed=1002 + 7919 * rank)
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_b300(args, wl)

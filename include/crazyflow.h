@@ -166,7 +166,11 @@ int sim_get_state(sim_h h, float* x, void* stream);
 int sim_set_commands(sim_h h, const float* cmd, int64_t n_blocks, int hold, void* stream);
 
 /* Advance every drone by K steps in ONE kernel launch (state kept in
- * registers across the K steps).  1 <= K <= 100000. */
+ * registers across the K steps).  1 <= K <= 100000.  Consecutive step launches
+ * on a stream are chained as programmatically dependent launches (the next is
+ * scheduled while the previous one drains); with CRAZYFLOW_SERIAL_LAUNCH=1 in
+ * the environment they are plain stream-ordered launches instead (same
+ * kernels, same results), for profilers that do not follow the chained form. */
 int sim_step(sim_h h, int K, void* stream);
 
 /* Advance n_steps steps as ceil(n_steps / K) launches of at most K steps. */
@@ -187,8 +191,74 @@ int sim_run(sim_h h, int64_t n_steps, int K, void* stream);
 int sim_run_host(sim_h h, const float* x0, const float* cmd, int64_t n_blocks, int hold,
                  int64_t n_steps, int K, float* x_out, void* stream);
 
-/* Threads per block used by sim_step (default 128; 32..256, multiple of 32). */
+/* Threads per block of the step and the sampling launches (default 128;
+ * 32..256, multiple of 32). */
 int sim_set_block_size(sim_h h, int threads_per_block);
+
+/* ---------------------------------------------------------------------------
+ * Autotuner of the launch shapes (the batching plan's autotuner: threads per
+ * block and steps per launch of the fused step, threads per block of the
+ * sampling launch).  The library times every candidate on the handle's own
+ * data with CUDA events on `stream` (after one untimed run, the median of
+ * `reps` runs), applies the fastest to the handle (SIM_TUNE_STEP sets the
+ * step launches' block size, SIM_TUNE_SAMPLE the sampling launches'), and
+ * returns it.  The caller passes the chosen K to sim_run / sim_step.
+ * Cache: one JSON line per tuning, {"key", "tpb", "K", "ms"}, appended to
+ * $CRAZYFLOW_AUTOTUNE_CACHE (default ~/.cache/crazyflow_b300/autotune.jsonl);
+ * with use_cache = 1 a matching key (the last one in the file) is returned
+ * without timing.  The key names the GPU (name, compute capability, SM count),
+ * the operation, M, N (or -1 for uneven batches), Ntot, the number of worlds of
+ * each model and a hash of the per-world drone counts and models, the
+ * integrator, the control interface, the rotor model, per-world parameters,
+ * dt, and n_steps (step) or S, H and the obstacle count (sample).
+ * Step trials restore the state planes (saved in the handle's staging region)
+ * and the command schedule around every run and at the end: the handle's
+ * state is the same after the call.  Sampling trials write `cost`.  The call
+ * synchronises `stream`; do not call it during stream capture.  Nothing is
+ * allocated on the device.  Errors: SIM_EINVAL (bad request), SIM_ESTATE
+ * (call order), SIM_ECUDA; on an error the block sizes are left unchanged. */
+#define SIM_TUNE_STEP 0
+#define SIM_TUNE_SAMPLE 1
+#define SIM_TUNE_MAX_CANDIDATES 16
+typedef struct {
+  int op;        /* SIM_TUNE_STEP or SIM_TUNE_SAMPLE */
+  int reps;      /* timed runs per candidate, 1..100 */
+  int use_cache; /* 1: a cached result for the same key is returned without timing */
+  int n_tpb;     /* candidate block sizes (0: 32, 64, 128, 256) */
+  int tpb[SIM_TUNE_MAX_CANDIDATES];
+  int n_K;       /* SIM_TUNE_STEP: candidate steps per launch (0: 1, 5, 10, 25, 50, 100, 200;
+                    candidates above n_steps are dropped) */
+  int K[SIM_TUNE_MAX_CANDIDATES];
+  int64_t n_steps; /* SIM_TUNE_STEP: steps of each timed run (sim_run(n_steps, K)) */
+  /* SIM_TUNE_SAMPLE: the sim_sample_rollouts call to time (arguments as there) */
+  int S, H;
+  const uint64_t* seed;
+  float sigma;
+  const float* nominal;
+  const float* goals;
+  const float* obstacles;
+  int n_obs;
+  float w_obs;
+  float* cost;
+} sim_tune_request;
+
+typedef struct {
+  int tpb;           /* chosen block size (applied to the handle) */
+  int K;             /* SIM_TUNE_STEP: chosen steps per launch; 1 for SIM_TUNE_SAMPLE */
+  float ms;          /* its time (median over reps), or the cached time */
+  int from_cache;    /* 1 when the result came from the cache */
+  int n_trials;      /* candidates timed */
+  int cache_written; /* 1 when the result was appended to the cache file */
+  /* median time of candidate (tpb[i], K[j]) at [i * SIM_TUNE_MAX_CANDIDATES + j]
+     (0 where not timed) */
+  float trial_ms[SIM_TUNE_MAX_CANDIDATES * SIM_TUNE_MAX_CANDIDATES];
+  char key[512];     /* the cache key */
+} sim_tune_result;
+
+int sim_autotune(sim_h h, const sim_tune_request* req, sim_tune_result* out, void* stream);
+/* The cache key sim_autotune would use for this handle and request (no timing,
+ * no device work); SIM_EINVAL if key[n] cannot hold it. */
+int sim_autotune_key(sim_h h, const sim_tune_request* req, char* key, size_t n);
 
 /* Failure-detection self-test of the library's bounded in-kernel waits (the
  * rollout adjoint's warp hand-off uses them): one small kernel waits on a barrier

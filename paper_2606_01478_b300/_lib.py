@@ -57,6 +57,26 @@ class MppiConfig(ctypes.Structure):
                 ("rho", c_float), ("lambda_", c_float), ("w_obs", c_float)]
 
 
+TUNE_STEP, TUNE_SAMPLE = 0, 1
+TUNE_MAX = 16
+
+
+class TuneRequest(ctypes.Structure):
+    """sim_tune_request (include/crazyflow.h)."""
+    _fields_ = [("op", c_int), ("reps", c_int), ("use_cache", c_int), ("n_tpb", c_int),
+                ("tpb", c_int * TUNE_MAX), ("n_K", c_int), ("K", c_int * TUNE_MAX), ("n_steps", c_int64),
+                ("S", c_int), ("H", c_int), ("seed", c_void_p), ("sigma", c_float), ("nominal", c_void_p),
+                ("goals", c_void_p), ("obstacles", c_void_p), ("n_obs", c_int), ("w_obs", c_float),
+                ("cost", c_void_p)]
+
+
+class TuneResult(ctypes.Structure):
+    """sim_tune_result (include/crazyflow.h)."""
+    _fields_ = [("tpb", c_int), ("K", c_int), ("ms", c_float), ("from_cache", c_int), ("n_trials", c_int),
+                ("cache_written", c_int), ("trial_ms", c_float * (TUNE_MAX * TUNE_MAX)),
+                ("key", ctypes.c_char * 512)]
+
+
 _SIGS = {
     "sim_create": (c_int, [POINTER(c_void_p), c_int64, c_int64, c_int, c_int, c_float]),
     "sim_create_batched": (c_int, [POINTER(c_void_p), c_int64, POINTER(c_int64), POINTER(ctypes.c_int32),
@@ -105,6 +125,8 @@ _SIGS = {
     "sim_rollout_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_float,
                                  c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_void_p,
                                  c_void_p]),
+    "sim_autotune": (c_int, [c_void_p, POINTER(TuneRequest), POINTER(TuneResult), c_void_p]),
+    "sim_autotune_key": (c_int, [c_void_p, POINTER(TuneRequest), ctypes.c_char_p, c_size_t]),
     "sim_last_error": (c_char_p, [c_void_p]),
     "sim_destroy": (None, [c_void_p]),
 }

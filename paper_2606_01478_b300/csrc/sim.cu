@@ -13,48 +13,10 @@
 #include <new>
 #include <vector>
 
+#include "handle.h"
 #include "internal.h"
 
 using cf::DevParams;
-
-struct sim_s {
-  int64_t M = 0, N = 0, ntot = 0;
-  bool batched = false;
-  int model = SIM_FIRST_PRINCIPLES;  // uniform batches
-  int integrator = SIM_EULER;
-  int ctrl = SIM_CTRL_ATTITUDE;
-  float dt = 0.f;
-  int tpb = 128;
-  std::vector<int64_t> n_per_world, offset;
-  std::vector<int32_t> model_of_world;
-  std::vector<int4> tiles;  // uneven batches: (first drone, count <= 32, world, model)
-  std::vector<int32_t> offsets32;  // uneven batches: first drone of each world, [M + 1]
-  // workspace (caller-owned device memory) and the device that holds it
-  char* ws = nullptr;
-  int device = -1;
-  size_t ws_bytes = 0;
-  int64_t max_blocks = 0;
-  float4* planes = nullptr;
-  DevParams* params_dev = nullptr;
-  int32_t* set_of_world_dev = nullptr;
-  float4* cmd = nullptr;
-  float4* staging = nullptr;
-  uint32_t* status = nullptr;
-  int4* tiles_dev = nullptr;
-  int32_t* offsets_dev = nullptr;
-  // host copies
-  std::vector<DevParams> params_host;
-  DevParams p0;  // the single set of a uniform batch, passed by value
-  std::vector<int32_t> set_of_world_host;
-  bool params_ok = false, per_set = false, general_motor = false, state_ok = false;
-  int64_t n_blocks = 0;
-  int hold = 1;
-  int64_t t = 0;
-  int64_t launches = 0;
-  cf::RolloutObjective objective;
-  int rollout_repeat = 1;
-  char err[512] = {0};
-};
 
 namespace {
 
@@ -248,6 +210,41 @@ void note_error(sim_h h, const char* fmt, ...) {
   va_end(ap);
 }
 int handle_device(sim_h h) { return h ? h->device : -1; }
+
+int sample_launch(sim_h h, int S, int H, const uint64_t* seed, float sigma,
+                       const float* nominal, const float* goals, const float* obstacles, int n_obs,
+                       float w_obs, float* cost, void* stream, int n_ctrl, float rho) {
+  if (!h) return SIM_EINVAL;
+  if (!h->ws || !h->params_ok || !h->state_ok)
+    return fail(h, SIM_ESTATE, "bind, parameters and state must be set before sampling");
+  bool all_fp = h->batched ? true : h->model == SIM_FIRST_PRINCIPLES;
+  for (int32_t m : h->model_of_world) all_fp &= (m == SIM_FIRST_PRINCIPLES);
+  if (!all_fp) return fail(h, SIM_EINVAL, "sampling rollouts need first-principles drones");
+  if (h->ctrl != SIM_CTRL_ATTITUDE)
+    return fail(h, SIM_EINVAL, "sampling rollouts use the attitude interface");
+  if (S < 1 || H < 1 || n_obs < 0 || n_obs > SIM_MAX_OBSTACLES || !(sigma >= 0.f) ||
+      !isfinite(sigma) || !isfinite(w_obs))
+    return fail(h, SIM_EINVAL, "need S, H >= 1, 0 <= n_obs <= %d, finite sigma >= 0",
+                SIM_MAX_OBSTACLES);
+  if ((double)h->ntot * S > 4.0e18) return fail(h, SIM_EINVAL, "too many rollouts");
+  if (!seed || ((uintptr_t)seed & 7) || !goals || ((uintptr_t)goals & 3) || !cost ||
+      ((uintptr_t)cost & 3) || (nominal && ((uintptr_t)nominal & 15)) || (n_obs > 0 && !obstacles))
+    return fail(h, SIM_EINVAL, "bad or misaligned buffer");
+  for (int o = 0; o < n_obs; ++o) {
+    for (int j = 0; j < 4; ++j)
+      if (!isfinite(obstacles[4 * o + j])) return fail(h, SIM_EINVAL, "obstacle %d not finite", o);
+    if (obstacles[4 * o + 3] < 0.f) return fail(h, SIM_EINVAL, "obstacle %d has a negative radius", o);
+  }
+  cudaError_t e = cf::launch_sample(
+      h->planes, (int)h->ntot, h->batched ? h->offsets_dev : nullptr, (int)h->M, (int)h->N, goals,
+      nominal, (const unsigned long long*)seed, h->params_dev, h->set_of_world_dev, h->p0,
+      h->per_set || h->batched, h->general_motor, h->integrator, obstacles, n_obs, w_obs, sigma,
+      h->dt, S, H, cost, h->tpb_sample, (cudaStream_t)stream, n_ctrl, rho);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sampling launch");
+  h->launches++;
+  return SIM_OK;
+}
+
 }  // namespace cf
 
 extern "C" {
@@ -470,6 +467,7 @@ int sim_set_block_size(sim_h h, int tpb) {
   if (!h) return SIM_EINVAL;
   if (tpb < 32 || tpb > 256 || (tpb & 31)) return fail(h, SIM_EINVAL, "bad block size %d", tpb);
   h->tpb = tpb;
+  h->tpb_sample = tpb;
   return SIM_OK;
 }
 
@@ -557,44 +555,10 @@ int sim_status(sim_h h, uint32_t* flags, void* stream) {
 
 // ---------------------------------------------------------------- sampling rollouts
 
-static int sample_impl(sim_h h, int S, int H, const uint64_t* seed, float sigma,
-                       const float* nominal, const float* goals, const float* obstacles, int n_obs,
-                       float w_obs, float* cost, void* stream, int n_ctrl, float rho) {
-  if (!h) return SIM_EINVAL;
-  if (!h->ws || !h->params_ok || !h->state_ok)
-    return fail(h, SIM_ESTATE, "bind, parameters and state must be set before sampling");
-  bool all_fp = h->batched ? true : h->model == SIM_FIRST_PRINCIPLES;
-  for (int32_t m : h->model_of_world) all_fp &= (m == SIM_FIRST_PRINCIPLES);
-  if (!all_fp) return fail(h, SIM_EINVAL, "sampling rollouts need first-principles drones");
-  if (h->ctrl != SIM_CTRL_ATTITUDE)
-    return fail(h, SIM_EINVAL, "sampling rollouts use the attitude interface");
-  if (S < 1 || H < 1 || n_obs < 0 || n_obs > SIM_MAX_OBSTACLES || !(sigma >= 0.f) ||
-      !isfinite(sigma) || !isfinite(w_obs))
-    return fail(h, SIM_EINVAL, "need S, H >= 1, 0 <= n_obs <= %d, finite sigma >= 0",
-                SIM_MAX_OBSTACLES);
-  if ((double)h->ntot * S > 4.0e18) return fail(h, SIM_EINVAL, "too many rollouts");
-  if (!seed || ((uintptr_t)seed & 7) || !goals || ((uintptr_t)goals & 3) || !cost ||
-      ((uintptr_t)cost & 3) || (nominal && ((uintptr_t)nominal & 15)) || (n_obs > 0 && !obstacles))
-    return fail(h, SIM_EINVAL, "bad or misaligned buffer");
-  for (int o = 0; o < n_obs; ++o) {
-    for (int j = 0; j < 4; ++j)
-      if (!isfinite(obstacles[4 * o + j])) return fail(h, SIM_EINVAL, "obstacle %d not finite", o);
-    if (obstacles[4 * o + 3] < 0.f) return fail(h, SIM_EINVAL, "obstacle %d has a negative radius", o);
-  }
-  cudaError_t e = cf::launch_sample(
-      h->planes, (int)h->ntot, h->batched ? h->offsets_dev : nullptr, (int)h->M, (int)h->N, goals,
-      nominal, (const unsigned long long*)seed, h->params_dev, h->set_of_world_dev, h->p0,
-      h->per_set || h->batched, h->general_motor, h->integrator, obstacles, n_obs, w_obs, sigma,
-      h->dt, S, H, cost, h->tpb, (cudaStream_t)stream, n_ctrl, rho);
-  if (e != cudaSuccess) return cuda_fail(h, e, "sampling launch");
-  h->launches++;
-  return SIM_OK;
-}
-
 int sim_sample_rollouts(sim_h h, int S, int H, const uint64_t* seed, float sigma,
                         const float* nominal, const float* goals, const float* obstacles,
                         int n_obs, float w_obs, float* cost, void* stream) {
-  return sample_impl(h, S, H, seed, sigma, nominal, goals, obstacles, n_obs, w_obs, cost, stream, 0,
+  return cf::sample_launch(h, S, H, seed, sigma, nominal, goals, obstacles, n_obs, w_obs, cost, stream, 0,
                      0.f);
 }
 
@@ -622,7 +586,7 @@ int sim_mppi_iteration(sim_h h, const sim_mppi_config* cfg, const uint64_t* seed
       ((uintptr_t)best_cost & 3))
     return fail(h, SIM_EINVAL, "bad or misaligned MPPI buffer");
   // sampling with per-(drone, controller) means and AR(1) noise
-  int r = sample_impl(h, c.S, c.H, seed, c.sigma, mean, goals, obstacles, n_obs, c.w_obs, cost,
+  int r = cf::sample_launch(h, c.S, c.H, seed, c.sigma, mean, goals, obstacles, n_obs, c.w_obs, cost,
                       stream, c.n_ctrl, c.rho);
   if (r != SIM_OK) return r;
   cudaError_t e = cf::launch_mppi_update(cost, mean, plan, best_cost,

@@ -4,6 +4,8 @@
 // section).
 #include <utility>
 
+#include <cstdlib>
+
 #include "internal.h"
 #include "stepcore.cuh"
 
@@ -28,6 +30,17 @@ __device__ __forceinline__ void chain_release() {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
+// CRAZYFLOW_SERIAL_LAUNCH=1 in the environment (read once per process) drops the
+// attribute: the same kernels run as plain stream-ordered launches, for
+// profilers that do not follow programmatically dependent launches.
+static bool serial_launches() {
+  static const bool serial = [] {
+    const char* e = getenv("CRAZYFLOW_SERIAL_LAUNCH");
+    return e && e[0] == '1';
+  }();
+  return serial;
+}
+
 template <typename... KArgs, typename... Args>
 static cudaError_t launch_chained(void (*kernel)(KArgs...), int grid, int tpb, cudaStream_t st,
                                   Args&&... args) {
@@ -40,7 +53,7 @@ static cudaError_t launch_chained(void (*kernel)(KArgs...), int grid, int tpb, c
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = serial_launches() ? 0 : 1;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 

@@ -186,3 +186,56 @@ def test_calls_refuse_a_stream_or_tensor_of_another_device():
         _check_same_device(torch.device("cuda", 1), torch.device("cuda", 0), "stream")
     with pytest.raises(ValueError):
         _check_same_device(torch.device("cpu"), torch.device("cuda", 0), "cost")
+
+
+
+def test_autotune_keys_name_everything_the_timing_depends_on():
+    """sim_autotune_key (no device work): handles that differ only by integrator,
+    control interface, model mix or shape get different keys; identical handles
+    share one; the key records the operation and the run length."""
+    import ctypes
+    import numpy as np
+    lib = L.load()
+
+    def key(h, op=L.TUNE_STEP, n_steps=100, S=1, H=1):
+        r = L.TuneRequest()
+        r.op, r.n_steps, r.S, r.H, r.reps = op, n_steps, S, H, 1
+        buf = ctypes.create_string_buffer(512)
+        assert lib.sim_autotune_key(h, ctypes.byref(r), buf, 512) == L.SIM_OK
+        return buf.value.decode()
+
+    def uniform(M, N, model, integ, ctrl=L.CTRL_ATTITUDE):
+        h = ctypes.c_void_p()
+        assert lib.sim_create(ctypes.byref(h), M, N, model, integ, 1 / 500) == L.SIM_OK
+        assert lib.sim_set_control(h, ctrl) == L.SIM_OK
+        return h
+
+    def batched(n, models):
+        h = ctypes.c_void_p()
+        n = np.asarray(n, np.int64)
+        m = np.asarray(models, np.int32)
+        assert lib.sim_create_batched(ctypes.byref(h), len(n), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), L.EULER,
+                                      1 / 500) == L.SIM_OK
+        return h
+
+    a = uniform(64, 1, 0, L.EULER)
+    b = uniform(64, 1, 0, L.RK4)
+    c = uniform(64, 1, 0, L.EULER)
+    d = uniform(64, 1, 0, L.EULER, L.CTRL_TORQUE)
+    e = uniform(32, 2, 0, L.EULER)
+    assert key(a) == key(c)
+    assert len({key(a), key(b), key(d), key(e)}) == 4
+    assert "integrator=euler" in key(a) and "integrator=rk4" in key(b) and "ctrl=torque" in key(d)
+    assert key(a, n_steps=100) != key(a, n_steps=200) and "steps=100" in key(a)
+    assert "op=sample" in key(a, op=L.TUNE_SAMPLE, S=256, H=50) and "S=256|H=50" in key(a, op=L.TUNE_SAMPLE, S=256, H=50)
+    f = batched([5, 7], [0, 1])
+    g = batched([5, 7], [1, 0])
+    h = batched([7, 5], [0, 1])
+    assert len({key(f), key(g), key(h)}) == 3
+    r = L.TuneRequest()
+    r.op = 7
+    buf = ctypes.create_string_buffer(512)
+    assert lib.sim_autotune_key(a, ctypes.byref(r), buf, 512) == L.SIM_EINVAL
+    for x in (a, b, c, d, e, f, g, h):
+        lib.sim_destroy(x)

@@ -24,7 +24,7 @@ def test_reference_arm_prints_one_contract_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
-    assert line["config"]["workload"].startswith("swarm_16384x1")
+    assert line["config"]["workload"] == "swarm_1000x4000_mixed_euler_attitude_200"
 
 
 def test_warmup_below_three_is_refused():

@@ -52,11 +52,11 @@ def test_graph_replay_uneven_mixed():
 
 
 def test_autotuner_restores_state_and_caches(tmp_path, monkeypatch):
-    monkeypatch.setenv("CRAZYFLOW_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.setenv("CRAZYFLOW_AUTOTUNE_CACHE", str(tmp_path / "tune.jsonl"))
     wl = W.attitude_swarm_rk4(M=4096, steps=100, K=100)
     sim = make_sim(wl)
     before = sim.get_state().clone()
-    best = autotune.tune_step(sim, 100, tag="test", tpbs=(32, 128), Ks=(10, 50, 100), reps=1)
+    best = autotune.tune_step(sim, 100, tpbs=(32, 128), Ks=(10, 50, 100), reps=1)
     assert best["tpb"] in (32, 128) and best["K"] in (10, 50, 100)
     assert len(best["table"]) == 6 and all(r["ms"] > 0 for r in best["table"])
     assert torch.equal(sim.get_state(), before)
@@ -66,6 +66,79 @@ def test_autotuner_restores_state_and_caches(tmp_path, monkeypatch):
     ref = make_sim(wl)
     ref.run(100, 100)
     assert torch.equal(sim.get_state(), ref.get_state())
-    assert os.path.exists(tmp_path / "tune.json")
-    again = autotune.tune_step(sim, 100, tag="test")
-    assert again["tpb"] == best["tpb"] and again["K"] == best["K"]
+    assert os.path.exists(tmp_path / "tune.jsonl")
+    again = autotune.tune_step(sim, 100)
+    assert again["from_cache"] and again["tpb"] == best["tpb"] and again["K"] == best["K"]
+
+
+def _req(op, tpbs, Ks, reps, use_cache, n_steps):
+    from paper_2606_01478_b300 import _lib as L
+    r = L.TuneRequest()
+    r.op, r.reps, r.use_cache, r.n_steps = op, reps, use_cache, n_steps
+    r.n_tpb, r.n_K = len(tpbs), len(Ks)
+    for i, t in enumerate(tpbs):
+        r.tpb[i] = t
+    for i, k in enumerate(Ks):
+        r.K[i] = k
+    return r
+
+
+def test_sim_autotune_through_the_c_abi(tmp_path, monkeypatch):
+    """sim_autotune called directly: the candidates are timed, the best is
+    applied and appended to the cache file as one JSON line; a cached call
+    returns it without timing; a bad request is refused."""
+    import ctypes
+    import json
+    from paper_2606_01478_b300 import _lib as L
+    path = tmp_path / "c_abi.jsonl"
+    monkeypatch.setenv("CRAZYFLOW_AUTOTUNE_CACHE", str(path))
+    wl = W.attitude_swarm_rk4(M=3000, steps=60, K=20)
+    sim = make_sim(wl)
+    lib = sim.lib
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    res = L.TuneResult()
+    req = _req(L.TUNE_STEP, (64, 256), (20, 60), 1, 1, 60)
+    assert lib.sim_autotune(sim.h, ctypes.byref(req), ctypes.byref(res), st) == L.SIM_OK
+    assert res.n_trials == 4 and not res.from_cache and res.cache_written
+    assert res.tpb in (64, 256) and res.K in (20, 60) and res.ms > 0
+    lines = [json.loads(ln) for ln in path.read_text().splitlines()]
+    assert lines == [{"key": res.key.decode(), "tpb": res.tpb, "K": res.K, "ms": pytest.approx(res.ms, rel=1e-5)}]
+    again = L.TuneResult()
+    assert lib.sim_autotune(sim.h, ctypes.byref(req), ctypes.byref(again), st) == L.SIM_OK
+    assert again.from_cache and again.n_trials == 0 and (again.tpb, again.K) == (res.tpb, res.K)
+    bad = _req(L.TUNE_STEP, (48,), (20,), 1, 0, 60)
+    assert lib.sim_autotune(sim.h, ctypes.byref(bad), ctypes.byref(again), st) == L.SIM_EINVAL
+
+
+def test_handles_differing_only_by_integrator_get_separate_entries(tmp_path, monkeypatch):
+    import json
+    from paper_2606_01478_b300 import EULER, RK4
+    path = tmp_path / "integ.jsonl"
+    monkeypatch.setenv("CRAZYFLOW_AUTOTUNE_CACHE", str(path))
+    keys = []
+    for integ in (EULER, RK4):
+        wl = W.attitude_swarm_rk4(M=2048, steps=40, K=20)
+        wl.integrator = integ
+        sim = make_sim(wl)
+        r = autotune.tune_step(sim, 40, tpbs=(64, 128), Ks=(20, 40), reps=1)
+        assert not r["from_cache"]
+        keys.append(r["key"])
+    assert keys[0] != keys[1]
+    assert [json.loads(ln)["key"] for ln in path.read_text().splitlines()] == keys
+
+
+def test_sampling_block_size_from_the_autotuner(tmp_path, monkeypatch):
+    monkeypatch.setenv("CRAZYFLOW_AUTOTUNE_CACHE", str(tmp_path / "sample.jsonl"))
+    from paper_2606_01478_b300 import RK4
+    wl = W.uneven_sampling_rk4(M=6)
+    sim = Sim.batched(wl.n_per_world, np.zeros(wl.M, np.int32), RK4, wl.dt)
+    sim.set_params(wl.params)
+    sim.set_state(torch.tensor(wl.x0, dtype=torch.float32, device="cuda"))
+    goals = torch.tensor(wl.goals, dtype=torch.float32, device="cuda")
+    seed = torch.tensor([5], dtype=torch.int64, device="cuda")
+    cost = torch.empty(len(wl.x0), 32, device="cuda")
+    r = autotune.tune_sample(sim, 32, 10, seed, 0.2, goals, wl.obstacles, 1000.0, cost, tpbs=(64, 256))
+    assert r["tpb"] in (64, 256) and len(r["table"]) == 2 and "op=sample" in r["key"]
+    ref = sim.sample_rollouts(32, 10, seed, 0.2, goals, wl.obstacles, 1000.0).clone()
+    sim.set_block_size(64 if r["tpb"] == 256 else 256)
+    assert torch.equal(sim.sample_rollouts(32, 10, seed, 0.2, goals, wl.obstacles, 1000.0), ref)
