@@ -11,15 +11,12 @@
 //  * warp path (S_c <= 2048 costs and n_e <= 32 elites per controller): one
 //    block per drone, one warp per controller, the costs in registers as
 //    order-preserving keys and a bisection over the key range;
-//  * cluster path (larger): one 512-thread CTA per (drone, controller), the
-//    controllers of a drone in one thread-block cluster.  The CTA finds the
-//    n_e-th smallest key with at most three 2048-bucket histogram passes over
-//    the costs (the first over [min, max] of the keys, each next one inside the
-//    bucket that holds it), compacts the elites into shared memory in index
-//    order with one counting and one writing pass, and averages them with every
-//    thread regenerating the noise of its elites.  The best controller is found
-//    through distributed shared memory: each CTA publishes its J_min, and after
-//    a cluster barrier every CTA reads its peers'.
+//  * cluster path (larger): one thread-block cluster of up to 8 CTAs per
+//    (drone, controller), each CTA holding a slice of the controller's cost
+//    keys in shared memory; histogram narrowing, compaction and the weighted
+//    mean are split over the cluster's CTAs, which agree through distributed
+//    shared memory (see the section's comment).  sim_mppi_select_elites runs
+//    the same kernels without the mean.
 #include <cooperative_groups.h>
 
 #include <cmath>
@@ -272,199 +269,102 @@ __global__ void __launch_bounds__(256) elite_select_warp_kernel(const float* cos
   if (lane == 0 && jmin) jmin[row] = jm;
 }
 
-// ------------------------------------------------------------------ block path
+// ------------------------------------------------------------------ cluster path
+//
+// One thread-block cluster of P CTAs (P = 1, 2, 4 or 8) per (drone, controller)
+// -- or per row of sim_mppi_select_elites.  CTA p owns the contiguous slice
+// [p L, (p + 1) L) of the controller's S_c samples (L = ceil(S_c / P)) and keeps
+// its cost keys in shared memory when the slice fits.  The CTAs of a cluster
+// agree on every decision by reading each other's shared memory (distributed
+// shared memory) between cluster barriers:
+//  1. range and count of the controller's keys; for the update also every
+//     controller's smallest cost (each CTA reads its share of all the drone's
+//     costs), so each cluster knows the best controller on its own;
+//  2. up to three narrowing passes: every CTA builds a 2048-bucket histogram of
+//     its keys inside [lo, hi]; CTA p adds bucket range p of all the cluster's
+//     histograms (reduce-scatter); every CTA then finds the bucket holding the
+//     n-th smallest key from the P segment totals and that segment's buckets;
+//  3. compaction in index order: CTA offsets from the cluster's counts, warp
+//     offsets within the CTA, lanes by ballot; ties at the threshold go to the
+//     lowest indices across the whole controller;
+//  4. (update) each CTA averages its own elites -- every thread regenerating the
+//     noise of its elites -- into per-step partial sums; after a barrier, CTA p
+//     adds the P partials of its share of the steps in rank order (a fixed
+//     order: repeated runs give identical results) and writes the warm-started
+//     means and, in the best controller's cluster, the plan.
 
-constexpr int BT = 512;        // threads of a block-path CTA
-constexpr int BW = BT / 32;    // its warps
+constexpr int CT = 512;        // threads of a cluster-path CTA
+constexpr int CW = CT / 32;    // its warps
 constexpr int BINS = 2048;     // buckets of one narrowing pass
 constexpr int MAXE = SIM_MAX_ELITES;
-static_assert(BINS == 4 * BT, "each thread scans four buckets");
+constexpr int KCAP = 28672;    // cost keys of a CTA's slice kept in shared memory
+constexpr int MAXC = SIM_MPPI_CLUSTER_MAX_CTRL;
+constexpr int U = 16;          // loads in flight per thread when streaming costs
 
-struct alignas(16) BlockSel {
-  uint32_t hist[BINS];
-  float el_c[MAXE];  // the elites' costs and sample indices, in index order
-  int el_i[MAXE];
-  uint32_t wmin[BW], wmax[BW], wpre[BW];
-  int wcnt[2][BW];
-  uint32_t kmin;
-  int nv, n, bsel, before;
+struct ClusterArgs {
+  const float* cost;  // update: [n][S]; selection: [rows][S_c]
+  int S, S_c, C, n_e, P, L;
+  bool cached;        // the slice's keys are kept in shared memory
+  // update
+  float* mean;
+  float* plan;
+  float* best_cost;
+  const unsigned long long* seed;
+  int H;
+  float sigma, rho, rho_c, inv_lam;
+  // selection
+  int* idx;
+  float* jmin;
 };
-// the input mean rows (float4) follow BlockSel in dynamic shared memory
-static_assert(sizeof(BlockSel) % 16 == 0, "float4 rows after BlockSel must be 16-byte aligned");
 
-// The n = min(n_e, number of non-NaN costs) elites of cc[0..S_c) into
-// sm.el_c / sm.el_i (index order), with sm.n and sm.kmin (the smallest key).
-// Every thread of the block calls it; it ends with a __syncthreads.
-__device__ __forceinline__ void select_elites_block(const float* __restrict__ cc, int S_c, int n_e,
-                                                    BlockSel& sm) {
-  const unsigned FULL = 0xffffffffu;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  // range and count of the non-NaN keys
-  uint32_t kmin = NAN_KEY, kmax = 0u;
-  int nv = 0;
-  for (int s = tid; s < S_c; s += BT) {
-    const uint32_t k = cost_key(cc[s]);
-    if (k != NAN_KEY) {
-      kmin = min(kmin, k);
-      kmax = max(kmax, k);
-      ++nv;
-    }
-  }
-  kmin = __reduce_min_sync(FULL, kmin);
-  kmax = __reduce_max_sync(FULL, kmax);
-  nv = __reduce_add_sync(FULL, nv);
-  if (lane == 0) {
-    sm.wmin[w] = kmin;
-    sm.wmax[w] = kmax;
-    sm.wcnt[0][w] = nv;
-  }
-  __syncthreads();
-  {
-    uint32_t a = NAN_KEY, b = 0u;
-    int c = 0;
-    for (int q = 0; q < BW; ++q) {
-      a = min(a, sm.wmin[q]);
-      b = max(b, sm.wmax[q]);
-      c += sm.wcnt[0][q];
-    }
-    kmin = a;
-    kmax = b;
-    nv = c;
-  }
-  __syncthreads();  // the partials are rewritten below
-  const int n = min(n_e, nv);
-  if (tid == 0) {
-    sm.kmin = kmin;
-    sm.nv = nv;
-    sm.n = n;
-  }
-  if (n == 0) {
-    __syncthreads();
-    return;
-  }
-  // Narrow [lo, hi] down to the n-th smallest key.  below = keys < lo.  Every
-  // thread holds the same lo, hi, below and exact (read from shared memory).
-  uint32_t lo = kmin, hi = kmax, T = kmax;
-  int below = 0;
-  bool exact = nv == n;  // every non-NaN key is an elite
-  while (!exact && lo < hi) {
-    const int sh = max(0, 21 - __clz(hi - lo));  // (hi - lo) >> sh < 2048
-    for (int b = tid; b < BINS; b += BT) sm.hist[b] = 0u;
-    if (tid == 0) {
-      sm.bsel = 0;
-      sm.before = 0;
-    }
-    __syncthreads();
-    for (int s = tid; s < S_c; s += BT) {
-      const uint32_t k = cost_key(cc[s]);
-      if (k >= lo && k <= hi) atomicAdd(&sm.hist[(k - lo) >> sh], 1u);
-    }
-    __syncthreads();
-    // the bucket holding the (n - below)-th smallest key of [lo, hi]: each
-    // thread owns four consecutive buckets; exclusive prefix over the block
-    const uint32_t need = (uint32_t)(n - below);
-    uint32_t h[4], loc = 0u;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      h[j] = sm.hist[4 * tid + j];
-      loc += h[j];
-    }
-    uint32_t incl = loc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t v = __shfl_up_sync(FULL, incl, o);
-      if (lane >= o) incl += v;
-    }
-    if (lane == 31) sm.wpre[w] = incl;
-    __syncthreads();
-    uint32_t run = incl - loc;
-    for (int q = 0; q < w; ++q) run += sm.wpre[q];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (run < need && run + h[j] >= need) {
-        sm.bsel = 4 * tid + j;
-        sm.before = (int)run;
-      }
-      run += h[j];
-    }
-    __syncthreads();
-    const int b = min(max(sm.bsel, 0), BINS - 1);
-    const uint32_t cnt = sm.hist[b];
-    below += sm.before;
-    lo += (uint32_t)b << sh;
-    hi = (uint32_t)min((unsigned long long)hi, (unsigned long long)lo + ((1ull << sh) - 1ull));
-    if (below + (int)cnt == n) {  // exactly n keys at or below this bucket's top
-      exact = true;
-      T = hi;
-    }
-    __syncthreads();  // hist, wpre, bsel are rewritten by the next pass
-  }
-  if (!exact) T = lo;  // lo == hi: the keys < T, then the quota lowest-index keys equal to T
-  const int quota = n - below;
-  // Compaction in index order: warp w owns the contiguous range [s0, s1).
-  const int chunk = ((S_c + BW - 1) / BW + 31) & ~31;
-  const int s0 = min(S_c, w * chunk), s1 = min(S_c, s0 + chunk);
-  int c_lt = 0, c_eq = 0;
-  for (int s = s0 + lane; s < s1; s += 32) {
-    const uint32_t k = cost_key(cc[s]);
-    c_lt += exact ? (k <= T) : (k < T);
-    c_eq += (!exact && k == T);
-  }
-  c_lt = __reduce_add_sync(FULL, c_lt);
-  c_eq = __reduce_add_sync(FULL, c_eq);
-  if (lane == 0) {
-    sm.wcnt[0][w] = c_lt;
-    sm.wcnt[1][w] = c_eq;
-  }
-  __syncthreads();
-  int lt_base = 0, eq_base = 0;
-  for (int q = 0; q < w; ++q) {
-    lt_base += sm.wcnt[0][q];
-    eq_base += sm.wcnt[1][q];
-  }
-  const unsigned bel = (1u << lane) - 1u;
-  for (int s = s0; s < s1; s += 32) {
-    const int i = s + lane;
-    const uint32_t k = i < s1 ? cost_key(cc[i]) : NAN_KEY;  // NaN key: neither below nor at T
-    const bool lt = exact ? k <= T : k < T;
-    const bool eq = !exact && k == T;
-    const unsigned mlt = __ballot_sync(FULL, lt), meq = __ballot_sync(FULL, eq);
-    const int eq_before = eq_base + __popc(meq & bel);
-    if (lt || (eq && eq_before < quota)) {
-      const int slot = lt_base + __popc(mlt & bel) + min(eq_before, quota);
-      if (slot < MAXE) {  // slot < n <= MAXE by construction
-        sm.el_c[slot] = key_cost(k);
-        sm.el_i[slot] = i;
-      }
-    }
-    lt_base += __popc(mlt);
-    eq_base += __popc(meq);
-  }
-  __syncthreads();
+struct alignas(16) ClusterSmem {
+  uint32_t hist[BINS];
+  uint32_t segb[BINS];       // this CTA's bucket range of the cluster-wide histogram
+  float el_c[MAXE];          // this CTA's elites (costs, sample indices), index order
+  int el_i[MAXE];
+  // published to the cluster
+  uint32_t kmin, kmax, seg_total;
+  int nv, cnt_lt, cnt_eq;
+  uint32_t cmin[MAXC];       // smallest key of each controller within this CTA's share
+  float wsum;
+  // block-local
+  uint32_t wred[3][CW];
+  int wcnt[2][CW];
+  uint32_t g_kmin, g_kmax;
+  int g_nv, bsel, before, seg_sel, cta_lt, cta_eq, cbest;
+  float jmin_c, jmin_best;
+};
+// float4 arrays follow ClusterSmem in dynamic shared memory
+static_assert(sizeof(ClusterSmem) % 16 == 0, "float4 arrays after ClusterSmem must be aligned");
+
+template <typename T>
+__device__ __forceinline__ T* peer(cg::cluster_group& cl, T* p, int rank) {
+  return cl.map_shared_rank(p, rank);
 }
 
-// Weighted mean of the elites of one controller, every thread regenerating the
-// noise of elites e = tid + j BT (j < EPT).  Sums per group of G steps: a warp
-// shuffle tree, then the warps' partials added in warp order (fixed order, so
-// repeated runs give identical results).
+// Key of cost i of the CTA's slice (shared memory when cached).
+__device__ __forceinline__ uint32_t slice_key(const ClusterArgs& a, const uint32_t* keys,
+                                              const float* cc, int s0, int i) {
+  return a.cached ? keys[i - s0] : cost_key(cc[i]);
+}
+
+// The MPPI average of this CTA's n_local elites into part[k] (unscaled per-step
+// sums over its elites) and sm.wsum; EPT elites per thread.
 template <int EPT>
-__device__ __forceinline__ void weighted_mean_block(const MppiArgs& a, const BlockSel& sm,
-                                                    const float4* mrow_in, float* mrow_out,
-                                                    float* prow, bool best, int d, int c,
-                                                    float jmin, const uint2* keys,
-                                                    float (*red)[16]) {
+__device__ __forceinline__ void cta_partial_mean(const ClusterArgs& a, ClusterSmem& sm, int n_local,
+                                                 unsigned long long base, float jmin,
+                                                 const float4* mean_in, float4* part,
+                                                 const uint2* keys, float (*red)[16]) {
   const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int n = sm.n;
   float wgt[EPT];
   unsigned long long id[EPT];
   float4 eps[EPT];
   float ws = 0.f;
-  const unsigned long long base = (unsigned long long)d * a.S + (unsigned long long)c * a.S_c;
 #pragma unroll
   for (int j = 0; j < EPT; ++j) {
-    const int e = tid + j * BT;
-    const bool mine = e < n;
+    const int e = tid + j * CT;
+    const bool mine = e < n_local;
     wgt[j] = mine ? expf(-(sm.el_c[e] - jmin) * a.inv_lam) : 0.f;
     id[j] = base + (mine ? (unsigned)sm.el_i[e] : 0u);
     eps[j] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -474,9 +374,11 @@ __device__ __forceinline__ void weighted_mean_block(const MppiArgs& a, const Blo
   for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(FULL, ws, o);
   if (lane == 0) red[w][0] = ws;
   __syncthreads();
-  float wsum = 0.f;
-  for (int q = 0; q < BW; ++q) wsum += red[q][0];
-  const float inv_w = 1.f / wsum;
+  if (tid == 0) {
+    float t = 0.f;
+    for (int q = 0; q < CW; ++q) t += red[q][0];
+    sm.wsum = t;
+  }
   __syncthreads();  // red is rewritten below
   constexpr int G = 4;
   for (int k0 = 0; k0 < a.H; k0 += G) {
@@ -485,7 +387,7 @@ __device__ __forceinline__ void weighted_mean_block(const MppiArgs& a, const Blo
     for (int u = 0; u < G; ++u) v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < EPT; ++j) {
-      if (tid + j * BT >= n) continue;
+      if (tid + j * CT >= n_local) continue;
       float2 z[G][2];
 #pragma unroll
       for (int u = 0; u < G; ++u) {
@@ -507,7 +409,7 @@ __device__ __forceinline__ void weighted_mean_block(const MppiArgs& a, const Blo
           e.y = fmaf(a.rho, e.y, cx * z[u][0].y);
           e.z = fmaf(a.rho, e.z, cx * z[u][1].x);
           e.w = fmaf(a.rho, e.w, cx * z[u][1].y);
-          const float4 m = mrow_in[k];
+          const float4 m = mean_in[k];
           v[u].x += wgt[j] * clampf(fmaf(a.sigma, e.x, m.x), -1.f, 1.f);
           v[u].y += wgt[j] * clampf(fmaf(a.sigma, e.y, m.y), -1.f, 1.f);
           v[u].z += wgt[j] * clampf(fmaf(a.sigma, e.z, m.z), -1.f, 1.f);
@@ -536,83 +438,369 @@ __device__ __forceinline__ void weighted_mean_block(const MppiArgs& a, const Blo
     }
     __syncthreads();
     if (tid < 4 * G) {
-      const int k = k0 + (tid >> 2), ch = tid & 3;
+      const int k = k0 + (tid >> 2);
       if (k < a.H) {
         float t = 0.f;
-        for (int q = 0; q < BW; ++q) t += red[q][tid];
-        const float val = t * inv_w;
-        if (k > 0) mrow_out[4 * (k - 1) + ch] = val;  // warm start: shift by one step
-        if (k == a.H - 1) mrow_out[4 * k + ch] = val;  // the last step repeated
-        if (best) prow[4 * k + ch] = val;
+        for (int q = 0; q < CW; ++q) t += red[q][tid];
+        reinterpret_cast<float*>(part)[4 * k + (tid & 3)] = t;
       }
     }
     __syncthreads();
   }
 }
 
-// One CTA per (drone, controller); the C controllers of a drone form one
-// cluster (cluster rank = controller).  Dynamic shared memory: BlockSel, then
-// the controller's H input mean rows.
-__global__ void __launch_bounds__(BT, 1) mppi_update_cluster_kernel(MppiArgs a) {
+template <bool UPDATE>
+__global__ void __launch_bounds__(CT, 1) elite_cluster_kernel(ClusterArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  BlockSel& sm = *reinterpret_cast<BlockSel*>(smem);
-  float4* mrow_in = reinterpret_cast<float4*>(smem + sizeof(BlockSel));
-  __shared__ float red[BW][16];
-  __shared__ uint2 keys[10];
-  __shared__ float jmin_s;
-  __shared__ int cbest_s;
+  ClusterSmem& sm = *reinterpret_cast<ClusterSmem*>(smem);
+  float4* part = reinterpret_cast<float4*>(smem + sizeof(ClusterSmem));
+  float4* mean_in = part + (UPDATE ? a.H : 0);
+  uint32_t* keys = reinterpret_cast<uint32_t*>(mean_in + (UPDATE ? a.H : 0));
+  __shared__ float red[CW][16];
+  __shared__ uint2 rkeys[10];
+  const unsigned FULL = 0xffffffffu;
   cg::cluster_group cluster = cg::this_cluster();
-  const int c = (int)cluster.block_rank();
-  const int d = blockIdx.x / a.C;
-  const int tid = threadIdx.x;
-  float4* mrow = reinterpret_cast<float4*>(a.mean) + ((size_t)d * a.C + c) * a.H;
-  for (int k = tid; k < a.H; k += BT) mrow_in[k] = mrow[k];
-  if (tid < 10) {
-    const unsigned long long sd = *a.seed;
-    keys[tid] = philox_round_key((uint32_t)sd, (uint32_t)(sd >> 32), tid);
+  const int p = (int)cluster.block_rank();
+  const int P = a.P;
+  const long long grp = blockIdx.x / P;  // (drone, controller) or row
+  const int c = UPDATE ? (int)(grp % a.C) : 0;
+  const long long d = UPDATE ? grp / a.C : grp;
+  const float* rowp = a.cost + d * (long long)a.S;
+  const float* cc = rowp + (size_t)c * a.S_c;
+  const int s0 = min(a.S_c, p * a.L), s1 = min(a.S_c, s0 + a.L);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  float4* mrow = UPDATE ? reinterpret_cast<float4*>(a.mean) + ((size_t)d * a.C + c) * a.H : nullptr;
+  if (UPDATE) {
+    for (int k = tid; k < a.H; k += CT) mean_in[k] = mrow[k];
+    if (tid < 10) {
+      const unsigned long long sd = *a.seed;
+      rkeys[tid] = philox_round_key((uint32_t)sd, (uint32_t)(sd >> 32), tid);
+    }
   }
-  select_elites_block(a.cost + (size_t)d * a.S + (size_t)c * a.S_c, a.S_c, a.n_e, sm);
-  if (tid == 0) jmin_s = sm.n > 0 ? key_cost(sm.kmin) : INFINITY;
-  cluster.sync();  // every controller's J_min is published
-  if (tid == 0) {
-    int cb = 0;
-    float jb = *cluster.map_shared_rank(&jmin_s, 0);
-    for (int q = 1; q < a.C; ++q) {
-      const float jq = *cluster.map_shared_rank(&jmin_s, q);
-      if (jq < jb) {
-        jb = jq;
-        cb = q;
+  // 1. the slice's keys, their range and count; every controller's smallest key
+  uint32_t kmin = NAN_KEY, kmax = 0u;
+  int nv = 0;
+  for (int b = s0 + tid; b < s1; b += U * CT) {
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = b + u * CT;
+      v[u] = i < s1 ? cc[i] : __int_as_float(0x7fffffff);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = b + u * CT;
+      const uint32_t k = cost_key(v[u]);
+      if (i < s1 && a.cached) keys[i - s0] = k;
+      if (k != NAN_KEY) {
+        kmin = min(kmin, k);
+        kmax = max(kmax, k);
+        ++nv;
       }
     }
-    cbest_s = cb;
-    if (c == 0) a.best_cost[d] = jb;
   }
-  cluster.sync();  // the peers' reads are done before any CTA moves on (or exits)
-  const int n = sm.n;
-  const float jmin = jmin_s;
-  const bool best = cbest_s == c;
-  float* mout = reinterpret_cast<float*>(mrow);
-  float* prow = a.plan + (size_t)d * a.H * 4;
-  if (n <= BT)
-    weighted_mean_block<1>(a, sm, mrow_in, mout, prow, best, d, c, jmin, keys, red);
-  else if (n <= 2 * BT)
-    weighted_mean_block<2>(a, sm, mrow_in, mout, prow, best, d, c, jmin, keys, red);
-  else if (n <= 4 * BT)
-    weighted_mean_block<4>(a, sm, mrow_in, mout, prow, best, d, c, jmin, keys, red);
+  uint32_t cm[MAXC];
+#pragma unroll
+  for (int q = 0; q < MAXC; ++q) cm[q] = NAN_KEY;
+  if (UPDATE) {
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+      if (q >= a.C) break;
+      if (q == c) {
+        cm[q] = kmin;
+        continue;
+      }
+      const float* cq = rowp + (size_t)q * a.S_c;
+      uint32_t m = NAN_KEY;
+      for (int b = s0 + tid; b < s1; b += U * CT) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = b + u * CT;
+          v[u] = i < s1 ? cq[i] : __int_as_float(0x7fffffff);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) m = min(m, cost_key(v[u]));
+      }
+      cm[q] = m;
+    }
+  }
+  kmin = __reduce_min_sync(FULL, kmin);
+  kmax = __reduce_max_sync(FULL, kmax);
+  nv = __reduce_add_sync(FULL, nv);
+#pragma unroll
+  for (int q = 0; q < MAXC; ++q) cm[q] = __reduce_min_sync(FULL, cm[q]);
+  __shared__ uint32_t wcm[CW][MAXC];
+  if (lane == 0) {
+    sm.wred[0][w] = kmin;
+    sm.wred[1][w] = kmax;
+    sm.wcnt[0][w] = nv;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) wcm[w][q] = cm[q];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t x = NAN_KEY, y = 0u;
+    int z = 0;
+    for (int q = 0; q < CW; ++q) {
+      x = min(x, sm.wred[0][q]);
+      y = max(y, sm.wred[1][q]);
+      z += sm.wcnt[0][q];
+    }
+    sm.kmin = x;
+    sm.kmax = y;
+    sm.nv = z;
+    for (int q = 0; q < MAXC; ++q) {
+      uint32_t m = NAN_KEY;
+      for (int r = 0; r < CW; ++r) m = min(m, wcm[r][q]);
+      sm.cmin[q] = m;
+    }
+  }
+  cluster.sync();  // every CTA's slice statistics are published
+  if (tid == 0) {
+    uint32_t x = NAN_KEY, y = 0u;
+    int z = 0;
+    uint32_t cmq[MAXC];
+    for (int q = 0; q < MAXC; ++q) cmq[q] = NAN_KEY;
+    for (int r = 0; r < P; ++r) {
+      ClusterSmem* o = peer(cluster, &sm, r);
+      x = min(x, o->kmin);
+      y = max(y, o->kmax);
+      z += o->nv;
+      for (int q = 0; q < MAXC; ++q) cmq[q] = min(cmq[q], o->cmin[q]);
+    }
+    sm.g_kmin = x;
+    sm.g_kmax = y;
+    sm.g_nv = z;
+    sm.jmin_c = z > 0 ? key_cost(x) : INFINITY;
+    if (UPDATE) {  // the best controller: lowest smallest cost, ties to the lower index
+      int cb = 0;
+      float jb = cmq[0] != NAN_KEY ? key_cost(cmq[0]) : INFINITY;
+      for (int q = 1; q < a.C; ++q) {
+        const float jq = cmq[q] != NAN_KEY ? key_cost(cmq[q]) : INFINITY;
+        if (jq < jb) {
+          jb = jq;
+          cb = q;
+        }
+      }
+      sm.cbest = cb;
+      sm.jmin_best = jb;
+    }
+  }
+  __syncthreads();
+  const int gnv = sm.g_nv;
+  const int n = min(a.n_e, gnv);
+  // 2. narrow [lo, hi] down to the n-th smallest key (every CTA holds the same values)
+  uint32_t lo = sm.g_kmin, hi = sm.g_kmax, T = hi;
+  int below = 0;
+  bool exact = gnv == n;  // every non-NaN key is an elite (also n == 0)
+  const int SEG = BINS / P;
+  while (!exact && lo < hi) {
+    const int sh = max(0, 21 - __clz(hi - lo));  // (hi - lo) >> sh < 2048
+    for (int b = tid; b < BINS; b += CT) sm.hist[b] = 0u;
+    __syncthreads();
+    for (int i = s0 + tid; i < s1; i += CT) {
+      const uint32_t k = slice_key(a, keys, cc, s0, i);
+      if (k >= lo && k <= hi) atomicAdd(&sm.hist[(k - lo) >> sh], 1u);
+    }
+    __syncthreads();
+    cluster.sync();  // every CTA's histogram is complete
+    uint32_t ssum = 0u;
+    for (int b = tid; b < SEG; b += CT) {
+      uint32_t t = 0u;
+      for (int r = 0; r < P; ++r) t += peer(cluster, &sm.hist[0], r)[p * SEG + b];
+      sm.segb[b] = t;
+      ssum += t;
+    }
+    ssum = __reduce_add_sync(FULL, ssum);
+    if (lane == 0) sm.wred[2][w] = ssum;
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t t = 0u;
+      for (int q = 0; q < CW; ++q) t += sm.wred[2][q];
+      sm.seg_total = t;
+    }
+    cluster.sync();  // the cluster-wide bucket segments are published
+    const uint32_t need = (uint32_t)(n - below);
+    if (tid == 0) {
+      uint32_t run = 0u;
+      int s = P - 1;
+      for (int r = 0; r < P; ++r) {
+        const uint32_t t = *peer(cluster, &sm.seg_total, r);
+        if (run + t >= need) {
+          s = r;
+          break;
+        }
+        run += t;
+      }
+      sm.seg_sel = s;
+      sm.before = (int)run;
+      sm.bsel = s * SEG;
+    }
+    __syncthreads();
+    {
+      const int s = sm.seg_sel;
+      const uint32_t* sb = peer(cluster, &sm.segb[0], s);
+      const uint32_t need_in = need - (uint32_t)sm.before;
+      // each thread owns four consecutive buckets of the segment
+      uint32_t h[4], loc = 0u;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int b = 4 * tid + j;
+        h[j] = b < SEG ? sb[b] : 0u;
+        loc += h[j];
+      }
+      uint32_t incl = loc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += x;
+      }
+      if (lane == 31) sm.wred[2][w] = incl;
+      __syncthreads();
+      uint32_t run = incl - loc;
+      for (int q = 0; q < w; ++q) run += sm.wred[2][q];
+      const int before0 = sm.before;
+      __syncthreads();  // every thread has read sm.before
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (run < need_in && run + h[j] >= need_in) {
+          sm.bsel = s * SEG + 4 * tid + j;
+          sm.before = before0 + (int)run;
+        }
+        run += h[j];
+      }
+    }
+    __syncthreads();
+    const int b = min(max(sm.bsel, 0), BINS - 1);
+    const uint32_t cnt = peer(cluster, &sm.segb[0], b / SEG)[b % SEG];
+    below += sm.before;
+    lo += (uint32_t)b << sh;
+    hi = (uint32_t)min((unsigned long long)hi, (unsigned long long)lo + ((1ull << sh) - 1ull));
+    if (below + (int)cnt == n) {
+      exact = true;
+      T = hi;
+    }
+    cluster.sync();  // before the next pass rewrites hist, segb and the totals
+  }
+  if (!exact) T = lo;
+  const int quota = n - below;
+  // 3. compaction in index order
+  const int len = s1 - s0;
+  const int chunk = ((len + CW - 1) / CW + 31) & ~31;
+  const int w0 = s0 + min(len, w * chunk), w1 = s0 + min(len, w * chunk + chunk);
+  int c_lt = 0, c_eq = 0;
+  if (n > 0) {
+    for (int i = w0 + lane; i < w1; i += 32) {
+      const uint32_t k = slice_key(a, keys, cc, s0, i);
+      c_lt += exact ? (k <= T) : (k < T);
+      c_eq += (!exact && k == T);
+    }
+  }
+  c_lt = __reduce_add_sync(FULL, c_lt);
+  c_eq = __reduce_add_sync(FULL, c_eq);
+  if (lane == 0) {
+    sm.wcnt[0][w] = c_lt;
+    sm.wcnt[1][w] = c_eq;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int x = 0, y = 0;
+    for (int q = 0; q < CW; ++q) {
+      x += sm.wcnt[0][q];
+      y += sm.wcnt[1][q];
+    }
+    sm.cnt_lt = x;
+    sm.cnt_eq = y;
+  }
+  cluster.sync();  // every CTA's counts are published
+  if (tid == 0) {
+    int x = 0, y = 0;
+    for (int r = 0; r < p; ++r) {
+      ClusterSmem* o = peer(cluster, &sm, r);
+      x += o->cnt_lt;
+      y += o->cnt_eq;
+    }
+    sm.cta_lt = x;
+    sm.cta_eq = y;
+  }
+  __syncthreads();
+  const int cta_lt = sm.cta_lt, cta_eq = sm.cta_eq;
+  int lt_w = 0, eq_w = 0;
+  for (int q = 0; q < w; ++q) {
+    lt_w += sm.wcnt[0][q];
+    eq_w += sm.wcnt[1][q];
+  }
+  const unsigned bel = (1u << lane) - 1u;
+  if (n > 0) {
+    int lt_base = lt_w, eq_base = cta_eq + eq_w;  // lt: within the CTA; eq: controller-wide
+    for (int i0 = w0; i0 < w1; i0 += 32) {
+      const int i = i0 + lane;
+      const uint32_t k = i < w1 ? slice_key(a, keys, cc, s0, i) : NAN_KEY;
+      const bool lt = exact ? k <= T : k < T;
+      const bool eq = !exact && k == T;
+      const unsigned mlt = __ballot_sync(FULL, lt), meq = __ballot_sync(FULL, eq);
+      const int eq_before = eq_base + __popc(meq & bel);
+      if (lt || (eq && eq_before < quota)) {
+        const int taken_eq = min(eq_before, quota);
+        if (UPDATE) {  // local slot: this CTA's elites before this one
+          const int slot = lt_base + __popc(mlt & bel) + taken_eq - min(cta_eq, quota);
+          if (slot < MAXE) {
+            sm.el_c[slot] = key_cost(k);
+            sm.el_i[slot] = i;
+          }
+        } else {  // controller-wide slot
+          const int slot = cta_lt + lt_base + __popc(mlt & bel) + taken_eq;
+          if (slot < a.n_e) a.idx[d * a.n_e + slot] = i;
+        }
+      }
+      lt_base += __popc(mlt);
+      eq_base += __popc(meq);
+    }
+  }
+  if (!UPDATE) {
+    if (p == 0) {
+      for (int e = n + tid; e < a.n_e; e += CT) a.idx[d * a.n_e + e] = -1;
+      if (tid == 0 && a.jmin) a.jmin[d] = sm.jmin_c;
+    }
+    cluster.sync();  // peers' reads of this CTA's shared memory are done
+    return;
+  }
+  __syncthreads();
+  // 4. this CTA's weighted partial sums, then the cluster's reduction in rank order
+  const int n_local = n > 0 ? sm.cnt_lt + (min(cta_eq + sm.cnt_eq, quota) - min(cta_eq, quota)) : 0;
+  const float jmin = sm.jmin_c;
+  const unsigned long long base = (unsigned long long)d * a.S + (unsigned long long)c * a.S_c;
+  if (n_local <= CT)
+    cta_partial_mean<1>(a, sm, n_local, base, jmin, mean_in, part, rkeys, red);
+  else if (n_local <= 2 * CT)
+    cta_partial_mean<2>(a, sm, n_local, base, jmin, mean_in, part, rkeys, red);
+  else if (n_local <= 4 * CT)
+    cta_partial_mean<4>(a, sm, n_local, base, jmin, mean_in, part, rkeys, red);
   else
-    weighted_mean_block<8>(a, sm, mrow_in, mout, prow, best, d, c, jmin, keys, red);
-}
-
-// One CTA per row (sim_mppi_select_elites beyond the warp path's sizes).
-__global__ void __launch_bounds__(BT, 1) elite_select_block_kernel(const float* cost, int S_c,
-                                                                   int n_e, int* idx, float* jmin) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  BlockSel& sm = *reinterpret_cast<BlockSel*>(smem);
-  const long long row = blockIdx.x;
-  select_elites_block(cost + row * S_c, S_c, n_e, sm);
-  const int n = sm.n;
-  for (int e = threadIdx.x; e < n_e; e += BT) idx[row * n_e + e] = e < n ? sm.el_i[e] : -1;
-  if (threadIdx.x == 0 && jmin) jmin[row] = n > 0 ? key_cost(sm.kmin) : INFINITY;
+    cta_partial_mean<8>(a, sm, n_local, base, jmin, mean_in, part, rkeys, red);
+  cluster.sync();  // every CTA's partial sums are published
+  {
+    float wt = 0.f;
+    for (int r = 0; r < P; ++r) wt += *peer(cluster, &sm.wsum, r);
+    const float inv_w = 1.f / wt;
+    const int HS = (a.H + P - 1) / P;
+    const int k0 = min(a.H, p * HS), k1 = min(a.H, k0 + HS);
+    const bool best = sm.cbest == c;
+    float* mout = reinterpret_cast<float*>(mrow);
+    float* prow = a.plan + (size_t)d * a.H * 4;
+    for (int x = 4 * k0 + tid; x < 4 * k1; x += CT) {
+      const int k = x >> 2;
+      float t = 0.f;
+      for (int r = 0; r < P; ++r) t += reinterpret_cast<const float*>(peer(cluster, part, r))[x];
+      const float val = t * inv_w;
+      if (k > 0) mout[x - 4] = val;        // warm start: shift by one step
+      if (k == a.H - 1) mout[x] = val;     // the last step repeated
+      if (best) prow[x] = val;
+    }
+    if (c == 0 && p == 0 && tid == 0) a.best_cost[d] = sm.jmin_best;
+  }
+  cluster.sync();  // peers' reads of this CTA's partial sums are done
 }
 
 }  // namespace mp
@@ -621,46 +809,80 @@ bool mppi_uses_warp_path(int S_c, int n_e) {
   return S_c <= mp::WARP_MAX_COSTS && n_e <= mp::WARP_MAX_ELITES;
 }
 
-cudaError_t launch_mppi_update(const float* cost, float* mean, float* plan, float* best_cost,
-                               const unsigned long long* seed, int n, int S, int H, int C, int n_e,
-                               float sigma, float rho, float lambda, cudaStream_t st) {
-  mp::MppiArgs a;
-  a.cost = cost;
-  a.mean = mean;
-  a.plan = plan;
-  a.best_cost = best_cost;
-  a.seed = seed;
-  a.n = n;
-  a.S = S;
-  a.H = H;
-  a.C = C;
-  a.S_c = S / C;
-  a.n_e = n_e;
-  a.sigma = sigma;
-  a.rho = rho;
-  a.rho_c = sqrtf(1.f - rho * rho);
-  a.inv_lam = 1.f / lambda;
-  if (mppi_uses_warp_path(a.S_c, n_e)) {
-    mp::mppi_update_warp_kernel<<<n, 32 * C, 0, st>>>(a);
-    return cudaGetLastError();
-  }
-  const size_t smem = sizeof(mp::BlockSel) + (size_t)H * sizeof(float4);
-  cudaError_t e = cudaFuncSetAttribute(mp::mppi_update_cluster_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// CTAs per controller on the cluster path: a power of two up to 8 giving
+// slices of at most about 12k costs.
+static int cluster_ctas(int S_c) {
+  int P = 1;
+  while (P < 8 && (S_c + P - 1) / P > 12288) P *= 2;
+  return P;
+}
+
+static cudaError_t launch_cluster(const mp::ClusterArgs& a, bool update, long long groups,
+                                  cudaStream_t st) {
+  const size_t smem = sizeof(mp::ClusterSmem) + (update ? 2 * (size_t)a.H * sizeof(float4) : 0) +
+                      (a.cached ? (size_t)a.L * sizeof(uint32_t) : 0);
+  if (groups * a.P >= (1ll << 31)) return cudaErrorInvalidValue;
+  auto kern = update ? mp::elite_cluster_kernel<true> : mp::elite_cluster_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((long long)n * C), 1, 1);
-  cfg.blockDim = dim3(mp::BT, 1, 1);
+  cfg.gridDim = dim3((unsigned)(groups * a.P), 1, 1);
+  cfg.blockDim = dim3(mp::CT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.x = (unsigned)a.P;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, mp::mppi_update_cluster_kernel, a);
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+cudaError_t launch_mppi_update(const float* cost, float* mean, float* plan, float* best_cost,
+                               const unsigned long long* seed, int n, int S, int H, int C, int n_e,
+                               float sigma, float rho, float lambda, cudaStream_t st) {
+  const int S_c = S / C;
+  if (mppi_uses_warp_path(S_c, n_e)) {
+    mp::MppiArgs a;
+    a.cost = cost;
+    a.mean = mean;
+    a.plan = plan;
+    a.best_cost = best_cost;
+    a.seed = seed;
+    a.n = n;
+    a.S = S;
+    a.H = H;
+    a.C = C;
+    a.S_c = S_c;
+    a.n_e = n_e;
+    a.sigma = sigma;
+    a.rho = rho;
+    a.rho_c = sqrtf(1.f - rho * rho);
+    a.inv_lam = 1.f / lambda;
+    mp::mppi_update_warp_kernel<<<n, 32 * C, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  mp::ClusterArgs a = {};
+  a.cost = cost;
+  a.S = S;
+  a.S_c = S_c;
+  a.C = C;
+  a.n_e = n_e;
+  a.P = cluster_ctas(S_c);
+  a.L = (S_c + a.P - 1) / a.P;
+  a.cached = a.L <= mp::KCAP;
+  a.mean = mean;
+  a.plan = plan;
+  a.best_cost = best_cost;
+  a.seed = seed;
+  a.H = H;
+  a.sigma = sigma;
+  a.rho = rho;
+  a.rho_c = sqrtf(1.f - rho * rho);
+  a.inv_lam = 1.f / lambda;
+  return launch_cluster(a, true, (long long)n * C, st);
 }
 
 cudaError_t launch_elite_select(const float* cost, long long rows, int S_c, int n_e, int* idx,
@@ -670,12 +892,18 @@ cudaError_t launch_elite_select(const float* cost, long long rows, int S_c, int 
                                                                               idx, jmin);
     return cudaGetLastError();
   }
-  const size_t smem = sizeof(mp::BlockSel);
-  cudaError_t e = cudaFuncSetAttribute(mp::elite_select_block_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  mp::elite_select_block_kernel<<<(unsigned)rows, mp::BT, smem, st>>>(cost, S_c, n_e, idx, jmin);
-  return cudaGetLastError();
+  mp::ClusterArgs a = {};
+  a.cost = cost;
+  a.S = S_c;
+  a.S_c = S_c;
+  a.C = 1;
+  a.n_e = n_e;
+  a.P = cluster_ctas(S_c);
+  a.L = (S_c + a.P - 1) / a.P;
+  a.cached = a.L <= mp::KCAP;
+  a.idx = idx;
+  a.jmin = jmin;
+  return launch_cluster(a, false, rows, st);
 }
 
 }  // namespace cf
