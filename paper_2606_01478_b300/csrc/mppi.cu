@@ -284,7 +284,8 @@ __global__ void __launch_bounds__(256) elite_select_warp_kernel(const float* cos
 //     its keys inside [lo, hi]; CTA p adds bucket range p of all the cluster's
 //     histograms (reduce-scatter); every CTA then finds the bucket holding the
 //     n-th smallest key from the P segment totals and that segment's buckets;
-//  3. compaction in index order: CTA offsets from the cluster's counts, warp
+//  3. compaction in index order: CTA offsets from the cluster's counts (the
+//     update needs them only when ties at the threshold are rationed), warp
 //     offsets within the CTA, lanes by ballot; ties at the threshold go to the
 //     lowest indices across the whole controller;
 //  4. (update) each CTA averages its own elites -- every thread regenerating the
@@ -297,9 +298,10 @@ constexpr int CT = 512;        // threads of a cluster-path CTA
 constexpr int CW = CT / 32;    // its warps
 constexpr int BINS = 2048;     // buckets of one narrowing pass
 constexpr int MAXE = SIM_MAX_ELITES;
-constexpr int KCAP = 28672;    // cost keys of a CTA's slice kept in shared memory
+constexpr int KCAP = 24576;    // cost keys of a CTA's slice kept in shared memory
 constexpr int MAXC = SIM_MPPI_CLUSTER_MAX_CTRL;
-constexpr int U = 16;          // loads in flight per thread when streaming costs
+constexpr int U4 = 8;          // float4 loads in flight per thread when streaming costs
+constexpr int XI_F4 = 2048;    // (elite, step) noise buffer of the few-elite mean: 32 KB
 
 struct ClusterArgs {
   const float* cost;  // update: [n][S]; selection: [rows][S_c]
@@ -346,6 +348,117 @@ __device__ __forceinline__ T* peer(cg::cluster_group& cl, T* p, int rank) {
 __device__ __forceinline__ uint32_t slice_key(const ClusterArgs& a, const uint32_t* keys,
                                               const float* cc, int s0, int i) {
   return a.cached ? keys[i - s0] : cost_key(cc[i]);
+}
+
+// f(i, x) for every i in [s0, s1) with x = base[i]: 16-byte vector loads over the
+// aligned interior (U4 of them in flight per thread), scalar loads for the
+// unaligned head and tail.
+template <typename F>
+__device__ __forceinline__ void stream_costs(const float* base, int s0, int s1, F&& f) {
+  const int tid = threadIdx.x;
+  const uintptr_t addr = reinterpret_cast<uintptr_t>(base + s0);
+  const int head = min(s1 - s0, (int)(((16u - (unsigned)(addr & 15u)) & 15u) >> 2));
+  if (tid < head) f(s0 + tid, base[s0 + tid]);
+  const int a0 = s0 + head;
+  const int n4 = (s1 - a0) >> 2;
+  const float4* b4 = reinterpret_cast<const float4*>(base + a0);
+  for (int j = tid; j < n4; j += U4 * CT) {
+    float4 v[U4];
+#pragma unroll
+    for (int u = 0; u < U4; ++u) {
+      const int jj = j + u * CT;
+      v[u] = jj < n4 ? b4[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < U4; ++u) {
+      const int jj = j + u * CT;
+      if (jj < n4) {
+        const int i = a0 + 4 * jj;
+        f(i, v[u].x);
+        f(i + 1, v[u].y);
+        f(i + 2, v[u].z);
+        f(i + 3, v[u].w);
+      }
+    }
+  }
+  const int t0 = a0 + 4 * n4;
+  if (tid < s1 - t0) f(t0 + tid, base[t0 + tid]);
+}
+
+// The weighted mean of a CTA that holds few elites (n_local < CT / 2): every
+// thread draws the noise of (elite, step) pairs of a chunk of steps into
+// shared memory (xi[step][elite]); thread e then runs elite e's AR(1) noise,
+// action and weight in step order; warp w adds the elites' values of steps
+// w, w + CW, ... in a fixed order into part[k].
+__device__ __forceinline__ void cta_partial_mean_few(const ClusterArgs& a, ClusterSmem& sm,
+                                                     int n_local, unsigned long long base,
+                                                     float jmin, const float4* mean_in,
+                                                     float4* part, float4* xi, const uint2* keys,
+                                                     float (*red)[16]) {
+  const unsigned FULL = 0xffffffffu;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const bool mine = tid < n_local;
+  const float wgt = mine ? expf(-(sm.el_c[tid] - jmin) * a.inv_lam) : 0.f;
+  float ws = wgt;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(FULL, ws, o);
+  if (lane == 0) red[w][0] = ws;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int q = 0; q < CW; ++q) t += red[q][0];
+    sm.wsum = t;
+  }
+  float4 eps = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int KS = max(1, min(a.H, XI_F4 / max(n_local, 1)));
+  for (int k0 = 0; k0 < a.H; k0 += KS) {
+    const int kc = min(KS, a.H - k0);
+    for (int q = tid; q < n_local * kc; q += CT) {
+      const int kk = q / n_local, e = q - kk * n_local;
+      const unsigned long long id = base + (unsigned)sm.el_i[e];
+      uint32_t ct[4] = {(uint32_t)id, (uint32_t)(id >> 32), (uint32_t)(k0 + kk), 0u};
+      philox4x32_10(ct, keys);
+      const float2 z01 = box_muller(ct[0], ct[1]), z23 = box_muller(ct[2], ct[3]);
+      xi[q] = make_float4(z01.x, z01.y, z23.x, z23.y);
+    }
+    __syncthreads();
+    if (mine) {
+      for (int kk = 0; kk < kc; ++kk) {
+        const int k = k0 + kk;
+        const float4 z = xi[kk * n_local + tid];
+        const float cx = k == 0 ? 1.f : a.rho_c;
+        eps.x = fmaf(a.rho, eps.x, cx * z.x);
+        eps.y = fmaf(a.rho, eps.y, cx * z.y);
+        eps.z = fmaf(a.rho, eps.z, cx * z.z);
+        eps.w = fmaf(a.rho, eps.w, cx * z.w);
+        const float4 m = mean_in[k];
+        xi[kk * n_local + tid] = make_float4(wgt * clampf(fmaf(a.sigma, eps.x, m.x), -1.f, 1.f),
+                                             wgt * clampf(fmaf(a.sigma, eps.y, m.y), -1.f, 1.f),
+                                             wgt * clampf(fmaf(a.sigma, eps.z, m.z), -1.f, 1.f),
+                                             wgt * clampf(fmaf(a.sigma, eps.w, m.w), -1.f, 1.f));
+      }
+    }
+    __syncthreads();
+    for (int kk = w; kk < kc; kk += CW) {
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int e = lane; e < n_local; e += 32) {
+        const float4 v = xi[kk * n_local + e];
+        t.x += v.x;
+        t.y += v.y;
+        t.z += v.z;
+        t.w += v.w;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        t.x += __shfl_xor_sync(FULL, t.x, o);
+        t.y += __shfl_xor_sync(FULL, t.y, o);
+        t.z += __shfl_xor_sync(FULL, t.z, o);
+        t.w += __shfl_xor_sync(FULL, t.w, o);
+      }
+      if (lane == 0) part[k0 + kk] = t;
+    }
+    __syncthreads();  // xi is rewritten by the next chunk
+  }
 }
 
 // The MPPI average of this CTA's n_local elites into part[k] (unscaled per-step
@@ -455,7 +568,8 @@ __global__ void __launch_bounds__(CT, 1) elite_cluster_kernel(ClusterArgs a) {
   ClusterSmem& sm = *reinterpret_cast<ClusterSmem*>(smem);
   float4* part = reinterpret_cast<float4*>(smem + sizeof(ClusterSmem));
   float4* mean_in = part + (UPDATE ? a.H : 0);
-  uint32_t* keys = reinterpret_cast<uint32_t*>(mean_in + (UPDATE ? a.H : 0));
+  float4* xi = mean_in + (UPDATE ? a.H : 0);  // update: XI_F4 float4, then the keys
+  uint32_t* keys = reinterpret_cast<uint32_t*>(xi + (UPDATE ? XI_F4 : 0));
   __shared__ float red[CW][16];
   __shared__ uint2 rkeys[10];
   const unsigned FULL = 0xffffffffu;
@@ -480,25 +594,15 @@ __global__ void __launch_bounds__(CT, 1) elite_cluster_kernel(ClusterArgs a) {
   // 1. the slice's keys, their range and count; every controller's smallest key
   uint32_t kmin = NAN_KEY, kmax = 0u;
   int nv = 0;
-  for (int b = s0 + tid; b < s1; b += U * CT) {
-    float v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = b + u * CT;
-      v[u] = i < s1 ? cc[i] : __int_as_float(0x7fffffff);
+  stream_costs(cc, s0, s1, [&](int i, float x) {
+    const uint32_t k = cost_key(x);
+    if (a.cached) keys[i - s0] = k;
+    if (k != NAN_KEY) {
+      kmin = min(kmin, k);
+      kmax = max(kmax, k);
+      ++nv;
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = b + u * CT;
-      const uint32_t k = cost_key(v[u]);
-      if (i < s1 && a.cached) keys[i - s0] = k;
-      if (k != NAN_KEY) {
-        kmin = min(kmin, k);
-        kmax = max(kmax, k);
-        ++nv;
-      }
-    }
-  }
+  });
   uint32_t cm[MAXC];
 #pragma unroll
   for (int q = 0; q < MAXC; ++q) cm[q] = NAN_KEY;
@@ -510,18 +614,8 @@ __global__ void __launch_bounds__(CT, 1) elite_cluster_kernel(ClusterArgs a) {
         cm[q] = kmin;
         continue;
       }
-      const float* cq = rowp + (size_t)q * a.S_c;
       uint32_t m = NAN_KEY;
-      for (int b = s0 + tid; b < s1; b += U * CT) {
-        float v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int i = b + u * CT;
-          v[u] = i < s1 ? cq[i] : __int_as_float(0x7fffffff);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) m = min(m, cost_key(v[u]));
-      }
+      stream_costs(rowp + (size_t)q * a.S_c, s0, s1, [&](int, float x) { m = min(m, cost_key(x)); });
       cm[q] = m;
     }
   }
@@ -557,34 +651,43 @@ __global__ void __launch_bounds__(CT, 1) elite_cluster_kernel(ClusterArgs a) {
     }
   }
   cluster.sync();  // every CTA's slice statistics are published
-  if (tid == 0) {
+  if (w == 0) {  // lane r reads CTA r's statistics
     uint32_t x = NAN_KEY, y = 0u;
     int z = 0;
     uint32_t cmq[MAXC];
+#pragma unroll
     for (int q = 0; q < MAXC; ++q) cmq[q] = NAN_KEY;
-    for (int r = 0; r < P; ++r) {
-      ClusterSmem* o = peer(cluster, &sm, r);
-      x = min(x, o->kmin);
-      y = max(y, o->kmax);
-      z += o->nv;
-      for (int q = 0; q < MAXC; ++q) cmq[q] = min(cmq[q], o->cmin[q]);
+    if (lane < P) {
+      const ClusterSmem* o = peer(cluster, &sm, lane);
+      x = o->kmin;
+      y = o->kmax;
+      z = o->nv;
+#pragma unroll
+      for (int q = 0; q < MAXC; ++q) cmq[q] = o->cmin[q];
     }
-    sm.g_kmin = x;
-    sm.g_kmax = y;
-    sm.g_nv = z;
-    sm.jmin_c = z > 0 ? key_cost(x) : INFINITY;
-    if (UPDATE) {  // the best controller: lowest smallest cost, ties to the lower index
-      int cb = 0;
-      float jb = cmq[0] != NAN_KEY ? key_cost(cmq[0]) : INFINITY;
-      for (int q = 1; q < a.C; ++q) {
-        const float jq = cmq[q] != NAN_KEY ? key_cost(cmq[q]) : INFINITY;
-        if (jq < jb) {
-          jb = jq;
-          cb = q;
+    x = __reduce_min_sync(FULL, x);
+    y = __reduce_max_sync(FULL, y);
+    z = __reduce_add_sync(FULL, z);
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) cmq[q] = __reduce_min_sync(FULL, cmq[q]);
+    if (lane == 0) {
+      sm.g_kmin = x;
+      sm.g_kmax = y;
+      sm.g_nv = z;
+      sm.jmin_c = z > 0 ? key_cost(x) : INFINITY;
+      if (UPDATE) {  // the best controller: lowest smallest cost, ties to the lower index
+        int cb = 0;
+        float jb = cmq[0] != NAN_KEY ? key_cost(cmq[0]) : INFINITY;
+        for (int q = 1; q < a.C; ++q) {
+          const float jq = cmq[q] != NAN_KEY ? key_cost(cmq[q]) : INFINITY;
+          if (jq < jb) {
+            jb = jq;
+            cb = q;
+          }
         }
+        sm.cbest = cb;
+        sm.jmin_best = jb;
       }
-      sm.cbest = cb;
-      sm.jmin_best = jb;
     }
   }
   __syncthreads();
@@ -605,6 +708,7 @@ __global__ void __launch_bounds__(CT, 1) elite_cluster_kernel(ClusterArgs a) {
     }
     __syncthreads();
     cluster.sync();  // every CTA's histogram is complete
+    // reduce-scatter: CTA p adds bucket range p of the P histograms
     uint32_t ssum = 0u;
     for (int b = tid; b < SEG; b += CT) {
       uint32_t t = 0u;
@@ -622,20 +726,22 @@ __global__ void __launch_bounds__(CT, 1) elite_cluster_kernel(ClusterArgs a) {
     }
     cluster.sync();  // the cluster-wide bucket segments are published
     const uint32_t need = (uint32_t)(n - below);
-    if (tid == 0) {
-      uint32_t run = 0u;
-      int s = P - 1;
-      for (int r = 0; r < P; ++r) {
-        const uint32_t t = *peer(cluster, &sm.seg_total, r);
-        if (run + t >= need) {
-          s = r;
-          break;
-        }
-        run += t;
+    if (w == 0) {  // lane r reads segment r's total; the first segment reaching need
+      const uint32_t t = lane < P ? *peer(cluster, &sm.seg_total, lane) : 0u;
+      uint32_t incl = t;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += x;
       }
-      sm.seg_sel = s;
-      sm.before = (int)run;
-      sm.bsel = s * SEG;
+      const unsigned hit = __ballot_sync(FULL, lane < P && incl >= need);
+      const int s = hit ? __ffs(hit) - 1 : P - 1;
+      const uint32_t run = __shfl_sync(FULL, incl - t, s);
+      if (lane == 0) {
+        sm.seg_sel = s;
+        sm.before = (int)run;
+        sm.bsel = s * SEG;
+      }
     }
     __syncthreads();
     {
@@ -713,16 +819,27 @@ __global__ void __launch_bounds__(CT, 1) elite_cluster_kernel(ClusterArgs a) {
     sm.cnt_lt = x;
     sm.cnt_eq = y;
   }
-  cluster.sync();  // every CTA's counts are published
-  if (tid == 0) {
+  // Slots need the counts of the CTAs before this one: the selection's global
+  // slots always, the update's local slots only when ties at the threshold are
+  // rationed (every CTA takes the same branch).
+  const bool need_counts = !UPDATE || !exact;
+  if (need_counts) cluster.sync();  // every CTA's counts are published
+  if (need_counts && w == 0) {  // lane r < p reads CTA r's counts
     int x = 0, y = 0;
-    for (int r = 0; r < p; ++r) {
-      ClusterSmem* o = peer(cluster, &sm, r);
-      x += o->cnt_lt;
-      y += o->cnt_eq;
+    if (lane < p) {
+      const ClusterSmem* o = peer(cluster, &sm, lane);
+      x = o->cnt_lt;
+      y = o->cnt_eq;
     }
-    sm.cta_lt = x;
-    sm.cta_eq = y;
+    x = __reduce_add_sync(FULL, x);
+    y = __reduce_add_sync(FULL, y);
+    if (lane == 0) {
+      sm.cta_lt = x;
+      sm.cta_eq = y;
+    }
+  } else if (!need_counts && tid == 0) {
+    sm.cta_lt = 0;  // unused by the update's exact case
+    sm.cta_eq = 0;
   }
   __syncthreads();
   const int cta_lt = sm.cta_lt, cta_eq = sm.cta_eq;
@@ -771,7 +888,9 @@ __global__ void __launch_bounds__(CT, 1) elite_cluster_kernel(ClusterArgs a) {
   const int n_local = n > 0 ? sm.cnt_lt + (min(cta_eq + sm.cnt_eq, quota) - min(cta_eq, quota)) : 0;
   const float jmin = sm.jmin_c;
   const unsigned long long base = (unsigned long long)d * a.S + (unsigned long long)c * a.S_c;
-  if (n_local <= CT)
+  if (2 * n_local < CT)
+    cta_partial_mean_few(a, sm, n_local, base, jmin, mean_in, part, xi, rkeys, red);
+  else if (n_local <= CT)
     cta_partial_mean<1>(a, sm, n_local, base, jmin, mean_in, part, rkeys, red);
   else if (n_local <= 2 * CT)
     cta_partial_mean<2>(a, sm, n_local, base, jmin, mean_in, part, rkeys, red);
@@ -780,10 +899,15 @@ __global__ void __launch_bounds__(CT, 1) elite_cluster_kernel(ClusterArgs a) {
   else
     cta_partial_mean<8>(a, sm, n_local, base, jmin, mean_in, part, rkeys, red);
   cluster.sync();  // every CTA's partial sums are published
-  {
+  if (w == 0) {  // lane r reads CTA r's weight sum; added in rank order
+    const float v = lane < P ? *peer(cluster, &sm.wsum, lane) : 0.f;
     float wt = 0.f;
-    for (int r = 0; r < P; ++r) wt += *peer(cluster, &sm.wsum, r);
-    const float inv_w = 1.f / wt;
+    for (int r = 0; r < P; ++r) wt += __shfl_sync(FULL, v, r);
+    if (lane == 0) red[0][0] = 1.f / wt;
+  }
+  __syncthreads();
+  {
+    const float inv_w = red[0][0];
     const int HS = (a.H + P - 1) / P;
     const int k0 = min(a.H, p * HS), k1 = min(a.H, k0 + HS);
     const bool best = sm.cbest == c;
@@ -819,7 +943,8 @@ static int cluster_ctas(int S_c) {
 
 static cudaError_t launch_cluster(const mp::ClusterArgs& a, bool update, long long groups,
                                   cudaStream_t st) {
-  const size_t smem = sizeof(mp::ClusterSmem) + (update ? 2 * (size_t)a.H * sizeof(float4) : 0) +
+  const size_t smem = sizeof(mp::ClusterSmem) +
+                      (update ? (2 * (size_t)a.H + mp::XI_F4) * sizeof(float4) : 0) +
                       (a.cached ? (size_t)a.L * sizeof(uint32_t) : 0);
   if (groups * a.P >= (1ll << 31)) return cudaErrorInvalidValue;
   auto kern = update ? mp::elite_cluster_kernel<true> : mp::elite_cluster_kernel<false>;
