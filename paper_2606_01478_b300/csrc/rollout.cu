@@ -803,17 +803,32 @@ static_assert(offsetof(Smem, h1) % 16 == 0 && offsetof(Smem, h2) % 16 == 0 &&
                   offsetof(Smem, actb) % 16 == 0 && (DPC * S64 * 2) % 16 == 0,
               "bulk copies start on 16-byte boundaries");
 
-__device__ __forceinline__ void bulk_s2g(void* g, const void* sm, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(g),
-               "r"(smem_addr(sm)), "r"(bytes)
+// L2 priorities of the cache traffic: an entry is written once per segment and
+// read back once in the reverse sweep, so its writes ask L2 to keep it
+// (evict_last) and its read marks it as done (evict_first); a segment's entries
+// then stay in L2 between the two instead of being written back and re-read.
+__device__ __forceinline__ unsigned long long l2_keep() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_done() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void bulk_s2g(void* g, const void* sm, uint32_t bytes,
+                                         unsigned long long pol) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;\n" ::"l"(g),
+               "r"(smem_addr(sm)), "r"(bytes), "l"(pol)
                : "memory");
 }
 __device__ __forceinline__ void bulk_g2s(void* sm, const void* g, uint32_t bytes,
-                                         unsigned long long* mbar) {
+                                         unsigned long long* mbar, unsigned long long pol) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::"r"(
           smem_addr(sm)),
-      "l"(g), "r"(bytes), "r"(smem_addr(mbar))
+      "l"(g), "r"(bytes), "r"(smem_addr(mbar)), "l"(pol)
       : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
@@ -840,11 +855,12 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* m, uint32_t b
 
 // Copy out warp rows r0..r0+15 of tile buffer b to cache entry g (one bulk group).
 __device__ __forceinline__ void cache_store(Smem& s, int b, int r0, uint4* g) {
-  bulk_s2g(g, s.h1[b][0] + r0 * S64, TILE_BYTES);
-  bulk_s2g(g + TILE_CHUNKS, s.h1[b][1] + r0 * S64, TILE_BYTES);
-  bulk_s2g(g + 2 * TILE_CHUNKS, s.h2[b][0] + r0 * S64, TILE_BYTES);
-  bulk_s2g(g + 3 * TILE_CHUNKS, s.h2[b][1] + r0 * S64, TILE_BYTES);
-  bulk_s2g(g + 4 * TILE_CHUNKS, s.actb[b][r0], ACT_BYTES);
+  const unsigned long long pol = l2_keep();
+  bulk_s2g(g, s.h1[b][0] + r0 * S64, TILE_BYTES, pol);
+  bulk_s2g(g + TILE_CHUNKS, s.h1[b][1] + r0 * S64, TILE_BYTES, pol);
+  bulk_s2g(g + 2 * TILE_CHUNKS, s.h2[b][0] + r0 * S64, TILE_BYTES, pol);
+  bulk_s2g(g + 3 * TILE_CHUNKS, s.h2[b][1] + r0 * S64, TILE_BYTES, pol);
+  bulk_s2g(g + 4 * TILE_CHUNKS, s.actb[b][r0], ACT_BYTES, pol);
   bulk_commit();
 }
 
@@ -852,12 +868,23 @@ __device__ __forceinline__ void cache_store(Smem& s, int b, int r0, uint4* g) {
 // all CACHE_BYTES have landed.
 __device__ __forceinline__ void cache_load(Smem& s, int b, int r0, const uint4* g,
                                            unsigned long long* mbar) {
+  const unsigned long long pol = l2_done();
   mbar_expect_tx(mbar, CACHE_BYTES);
-  bulk_g2s(s.h1[b][0] + r0 * S64, g, TILE_BYTES, mbar);
-  bulk_g2s(s.h1[b][1] + r0 * S64, g + TILE_CHUNKS, TILE_BYTES, mbar);
-  bulk_g2s(s.h2[b][0] + r0 * S64, g + 2 * TILE_CHUNKS, TILE_BYTES, mbar);
-  bulk_g2s(s.h2[b][1] + r0 * S64, g + 3 * TILE_CHUNKS, TILE_BYTES, mbar);
-  bulk_g2s(s.actb[b][r0], g + 4 * TILE_CHUNKS, ACT_BYTES, mbar);
+  bulk_g2s(s.h1[b][0] + r0 * S64, g, TILE_BYTES, mbar, pol);
+  bulk_g2s(s.h1[b][1] + r0 * S64, g + TILE_CHUNKS, TILE_BYTES, mbar, pol);
+  bulk_g2s(s.h2[b][0] + r0 * S64, g + 2 * TILE_CHUNKS, TILE_BYTES, mbar, pol);
+  bulk_g2s(s.h2[b][1] + r0 * S64, g + 3 * TILE_CHUNKS, TILE_BYTES, mbar, pol);
+  bulk_g2s(s.actb[b][r0], g + 4 * TILE_CHUNKS, ACT_BYTES, mbar, pol);
+}
+
+// Drop a consumed cache entry from L2 without writing it back: the lanes of the
+// warp invalidate its 128-byte lines (entries start on 128-byte boundaries:
+// the workspace is 256-byte aligned and CACHE_BYTES is a multiple of 128).
+static_assert(CACHE_BYTES % 128 == 0, "cache entries are whole 128-byte lines");
+__device__ __forceinline__ void cache_discard(const uint4* g, int lane) {
+  const char* e = reinterpret_cast<const char*>(g);
+  for (int l = lane; l < (int)(CACHE_BYTES / 128); l += 32)
+    asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(e + 128 * l) : "memory");
 }
 
 // ------------------------------------------------------------------ objectives
@@ -1058,6 +1085,12 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
         const int b = k & 1;
         const uint32_t par = (uint32_t)((t >> 1) & 1);
         wait_on(&s.full[b], par);
+        // step k's cache entry has been copied into shared memory and used: drop
+        // its L2 lines without a write-back; the fence orders the discards before
+        // the bulk stores that reuse the entry in the next segment (issued by the
+        // compute warp after it has waited for this warp's arrivals)
+        cache_discard(cache_at(v, k - k0), lane);
+        fence_proxy_async_global();
         accumulate_dw<LO>(s, v, lane, acc, b);
         mbar_arrive(&s.empty[b]);
         if (k - 2 >= k0) {
