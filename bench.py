@@ -123,7 +123,7 @@ KERNEL_SOURCES = {
     "step_batched_kernel": ("step.cu", "stepcore.cuh", "physics.cuh", "common.cuh"),
     "step_batched_single_kernel": ("step.cu", "stepcore.cuh", "physics.cuh", "common.cuh"),
     "rollout_bwd_kernel": ("rollout.cu", "physics.cuh", "common.cuh"),
-    "sample_kernel": ("sample.cu", "stepcore.cuh", "physics.cuh", "common.cuh"),
+    "sample_kernel": ("sample.cu", "noise.cuh", "stepcore.cuh", "physics.cuh", "common.cuh"),
 }
 
 
@@ -523,8 +523,8 @@ def run_b300(args, wl):
 
 
 def measure_mixed(dev, reps: int = 3, worlds: int = 1000) -> dict:
-    """The headline swarm (or its first `worlds` worlds) as fused launches, on
-    its own: used for profiling the step on a smaller case of the same mix."""
+    """The headline swarm (or its first `worlds` worlds) on its own, as fused
+    launches and as single-step launches: used for profiling."""
     from paper_2606_01478_b300 import Sim, autotune
     wl = W.mixed_swarm_euler(M=worlds)
     sim = Sim.batched(np.full(wl.M, wl.N), wl.model_of_world, wl.integrator, wl.dt, ctrl=wl.ctrl,
@@ -536,14 +536,16 @@ def measure_mixed(dev, reps: int = 3, worlds: int = 1000) -> dict:
     sim.set_commands(cmd, wl.hold)
     tuned = autotune.tune_step(sim, wl.steps, Ks=(wl.K,), reps=1)
 
-    def run():
+    def run(K):
         sim.set_state(x0)
         sim.set_commands(cmd, wl.hold)
-        sim.run(wl.steps, wl.K)
-    ms = _time_ms(run, reps, dev)
+        sim.run(wl.steps, K)
+    ms = _time_ms(lambda: run(wl.K), reps, dev)
+    ms1 = _time_ms(lambda: run(1), reps, dev)
     assert sim.status() == 0
-    return {"workload": wl.name, "value": wl.M * wl.N * wl.steps / (ms / 1e3), "unit": UNIT, "ms": ms,
-            "K": wl.K, "tpb": tuned["tpb"]}
+    units = wl.M * wl.N * wl.steps
+    return {"workload": wl.name, "value": units / (ms / 1e3), "unit": UNIT, "ms": ms, "K": wl.K,
+            "tpb": tuned["tpb"], "single_step": {"value": units / (ms1 / 1e3), "ms": ms1, "K": 1}}
 
 
 def measure_attitude_swarm(dev, reps: int = 5):
@@ -1005,7 +1007,9 @@ def main(argv=None):
               "bptt": measure_policy_bptt, "sampling": measure_sampling,
               "mppi": measure_mppi, "training": measure_bptt_training, "depth": measure_depth,
               "scale": measure_swarm_scale}[args.only]
-        print(json.dumps({"only": args.only, "record": fn(dev, reps=args.steps)}), flush=True)
+        rec = fn(dev, reps=args.steps)
+        rec = {k: v for k, v in rec.items() if not k.startswith("_")}  # GPU data kept for the CPU leg
+        print(json.dumps({"only": args.only, "record": rec}), flush=True)
         return 0
     rank = int(os.environ.get("RANK", "0"))
     wl = W.mixed_swarm_euler(seed=1002 + 7919 * rank)
