@@ -104,9 +104,44 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
     sparse = 3 * __popcll(cand) < sc.n_obs;
   };
   const bool cullable = MOTOR == MOTOR_LAG && !drag && sc.dt * P.cv_up <= 1.f;
-  if (cullable) cull(WINDOWED ? min(sc.cull_steps, sc.H) : sc.H);
+  if (cullable) {
+    // The first window starts from the drone's own state, the same for all its
+    // samples: when the warp's 32 lanes hold samples of one drone, each lane
+    // tests one obstacle and a ballot gathers the set (the same tests as the
+    // per-sample loop, so the same set).
+    const int steps0 = WINDOWED ? min(sc.cull_steps, sc.H) : sc.H;
+    const unsigned FULL = 0xffffffffu;
+    bool coop = false;
+    if (__activemask() == FULL) coop = __all_sync(FULL, d == __shfl_sync(FULL, d, 0));
+    if (coop) {
+      const float wmax = fmaxf(fmaxf(P.omega_max, fmaxf(s[13], s[14])), fmaxf(s[15], s[16]));
+      const float acc = 4.f * P.kf * wmax * wmax * P.inv_m * 1.01f + P.g;
+      const float T = steps0 * sc.dt;
+      const float v0 = sqrtf(fmaf(s[7], s[7], fmaf(s[8], s[8], s[9] * s[9])));
+      const float reach = fmaf(T, v0, acc * T * T) * 1.01f + 1e-3f;
+      const int lane = threadIdx.x & 31;
+      unsigned long long cand = 0ull;
+      for (int base = 0; base < sc.n_obs; base += 32) {
+        const int o = base + lane;
+        bool in = false;
+        if (o < sc.n_obs) {
+          const float4 ob = sc.obs[o];
+          const float dx = s[0] - ob.x, dy = s[1] - ob.y, dz = s[2] - ob.z;
+          const float lim = ob.w + reach;
+          in = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < lim * lim;
+        }
+        cand |= (unsigned long long)__ballot_sync(FULL, in) << base;
+      }
+      cand_lo = (uint32_t)cand;
+      cand_hi = (uint32_t)(cand >> 32);
+      sparse = 3 * __popcll(cand) < sc.n_obs;
+    } else {
+      cull(steps0);
+    }
+  }
   float cost = 0.f;
   float4 eps = make_float4(0.f, 0.f, 0.f, 0.f);
+  const bool ar1 = a.rho != 0.f;
   // WINDOWED: the horizon spans several windows (a kernel of its own, so that a
   // horizon of one window keeps a loop without culling code)
   int next_cull = cullable ? sc.cull_steps : sc.H;
@@ -121,13 +156,17 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
     philox4x32_10(c, keys);
     const float2 z01 = box_muller(c[0], c[1]);
     const float2 z23 = box_muller(c[2], c[3]);
-    // AR(1) temporal correlation: eps_0 = xi_0, eps_k = rho eps_{k-1} + rho_c xi_k
-    // (rho = 0, rho_c = 1: white noise, eps = xi exactly)
-    const float cx = k == 0 ? 1.f : a.rho_c;
-    eps.x = fmaf(a.rho, eps.x, cx * z01.x);
-    eps.y = fmaf(a.rho, eps.y, cx * z01.y);
-    eps.z = fmaf(a.rho, eps.z, cx * z23.x);
-    eps.w = fmaf(a.rho, eps.w, cx * z23.y);
+    // AR(1) temporal correlation: eps_0 = xi_0, eps_k = rho eps_{k-1} + rho_c xi_k;
+    // white noise (rho = 0) takes eps = xi without the arithmetic (a uniform branch)
+    if (ar1) {
+      const float cx = k == 0 ? 1.f : a.rho_c;
+      eps.x = fmaf(a.rho, eps.x, cx * z01.x);
+      eps.y = fmaf(a.rho, eps.y, cx * z01.y);
+      eps.z = fmaf(a.rho, eps.z, cx * z23.x);
+      eps.w = fmaf(a.rho, eps.w, cx * z23.y);
+    } else {
+      eps = make_float4(z01.x, z01.y, z23.x, z23.y);
+    }
     // sigma eps + nominal as one fused multiply-add, as the MPPI update forms it
     // (no nominal: + 0, the product itself)
     const float4 m = nom ? nom[k] : make_float4(0.f, 0.f, 0.f, 0.f);
