@@ -104,40 +104,50 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
     sparse = 3 * __popcll(cand) < sc.n_obs;
   };
   const bool cullable = MOTOR == MOTOR_LAG && !drag && sc.dt * P.cv_up <= 1.f;
-  if (cullable) {
-    // The first window starts from the drone's own state, the same for all its
-    // samples: when the warp's 32 lanes hold samples of one drone, each lane
-    // tests one obstacle and a ballot gathers the set (the same tests as the
-    // per-sample loop, so the same set).
-    const int steps0 = WINDOWED ? min(sc.cull_steps, sc.H) : sc.H;
-    const unsigned FULL = 0xffffffffu;
-    bool coop = false;
-    if (__activemask() == FULL) coop = __all_sync(FULL, d == __shfl_sync(FULL, d, 0));
-    if (coop) {
-      const float wmax = fmaxf(fmaxf(P.omega_max, fmaxf(s[13], s[14])), fmaxf(s[15], s[16]));
-      const float acc = 4.f * P.kf * wmax * wmax * P.inv_m * 1.01f + P.g;
-      const float T = steps0 * sc.dt;
-      const float v0 = sqrtf(fmaf(s[7], s[7], fmaf(s[8], s[8], s[9] * s[9])));
-      const float reach = fmaf(T, v0, acc * T * T) * 1.01f + 1e-3f;
-      const int lane = threadIdx.x & 31;
-      unsigned long long cand = 0ull;
-      for (int base = 0; base < sc.n_obs; base += 32) {
-        const int o = base + lane;
-        bool in = false;
-        if (o < sc.n_obs) {
-          const float4 ob = sc.obs[o];
-          const float dx = s[0] - ob.x, dy = s[1] - ob.y, dz = s[2] - ob.z;
-          const float lim = ob.w + reach;
-          in = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < lim * lim;
-        }
-        cand |= (unsigned long long)__ballot_sync(FULL, in) << base;
+  // When the warp's 32 lanes hold samples of one drone, the warp culls once for
+  // all of them: the union of the lanes' candidate sets is bounded by the
+  // sphere around lane 0's position whose radius is the largest distance of a
+  // lane from it plus that lane's reach; every obstacle outside it lies outside
+  // each lane's own bound (triangle inequality), and testing an obstacle a lane
+  // cannot reach adds exactly zero, so the costs are those of per-sample culling.
+  // Each lane tests one obstacle per pass; a ballot gathers the set.
+  const unsigned FULL = 0xffffffffu;
+  bool coop = false;
+  if (cullable && __activemask() == FULL) coop = __all_sync(FULL, d == __shfl_sync(FULL, d, 0));
+  auto cull_warp = [&](int steps) {
+    const float wmax = fmaxf(fmaxf(P.omega_max, fmaxf(s[13], s[14])), fmaxf(s[15], s[16]));
+    const float acc = 4.f * P.kf * wmax * wmax * P.inv_m * 1.01f + P.g;
+    const float T = steps * sc.dt;
+    const float v0 = sqrtf(fmaf(s[7], s[7], fmaf(s[8], s[8], s[9] * s[9])));
+    const float reach = fmaf(T, v0, acc * T * T) * 1.01f + 1e-3f;
+    const float cx = __shfl_sync(FULL, s[0], 0), cy = __shfl_sync(FULL, s[1], 0),
+                cz = __shfl_sync(FULL, s[2], 0);
+    const float ox = s[0] - cx, oy = s[1] - cy, oz = s[2] - cz;
+    // non-negative floats order like their bit patterns
+    const float rad = __uint_as_float(__reduce_max_sync(
+        FULL, __float_as_uint(sqrtf(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) + reach)));
+    const float R = rad * 1.0001f + 1e-4f;
+    const int lane = threadIdx.x & 31;
+    unsigned long long cand = 0ull;
+    for (int base = 0; base < sc.n_obs; base += 32) {
+      const int o = base + lane;
+      bool in = false;
+      if (o < sc.n_obs) {
+        const float4 ob = sc.obs[o];
+        const float dx = cx - ob.x, dy = cy - ob.y, dz = cz - ob.z;
+        const float lim = ob.w + R;
+        in = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < lim * lim;
       }
-      cand_lo = (uint32_t)cand;
-      cand_hi = (uint32_t)(cand >> 32);
-      sparse = 3 * __popcll(cand) < sc.n_obs;
-    } else {
-      cull(steps0);
+      cand |= (unsigned long long)__ballot_sync(FULL, in) << base;
     }
+    cand_lo = (uint32_t)cand;
+    cand_hi = (uint32_t)(cand >> 32);
+    sparse = 3 * __popcll(cand) < sc.n_obs;
+  };
+  if (cullable) {
+    const int steps0 = WINDOWED ? min(sc.cull_steps, sc.H) : sc.H;
+    if (coop) cull_warp(steps0);
+    else cull(steps0);
   }
   float cost = 0.f;
   float4 eps = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -148,7 +158,8 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
   for (int k = 0; k < sc.H; ++k) {
     if constexpr (WINDOWED) {
       if (k == next_cull) {
-        cull(min(sc.cull_steps, sc.H - k));
+        if (coop) cull_warp(min(sc.cull_steps, sc.H - k));
+        else cull(min(sc.cull_steps, sc.H - k));
         next_cull += sc.cull_steps;
       }
     }
