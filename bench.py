@@ -469,6 +469,14 @@ def run_b300(args, wl):
                           f"{clk_max:.0f} MHz (max SM clock, {pk_kind} peaks file)"}
     if clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (fp32_peak * clocks["sm_mhz"] / clk_max)
+    # the special-function (XU) work charged at the XU rate: one warp instruction
+    # per SM per cycle (32 operations), the peak ncu reports for this pipe
+    mufu = (n_fp * MUFU_PER_DRONE_STEP[("fp", "euler", "attitude")]
+            + n_abs * MUFU_PER_DRONE_STEP[("abs", "euler", "attitude")]) * K
+    xu_peak = SM_COUNT * 32 * clk_max * 1e6 / 1e12
+    roof["xu"] = {"achieved": mufu / avg_launch_s / 1e12, "peak": xu_peak, "unit": "Tops/s",
+                  "frac": mufu / avg_launch_s / 1e12 / xu_peak,
+                  "note": "sqrt, sin, cos per drone-step from flopcount.py; the FMA pipe binds"}
     pk, kind = peaks()
     byt = n_fp * BYTES_PER_DRONE_STEP["fp"] + n_abs * BYTES_PER_DRONE_STEP["abs"]
     hbm = byt * wl.steps / (k1_ms / 1e3) / 1e9
@@ -522,11 +530,11 @@ def run_b300(args, wl):
     return 0
 
 
-def measure_mixed(dev, reps: int = 3, worlds: int = 1000) -> dict:
+def measure_mixed(dev, reps: int = 3, worlds: int = 1000, models_of: str = "mixed") -> dict:
     """The headline swarm (or its first `worlds` worlds) on its own, as fused
     launches and as single-step launches: used for profiling."""
     from paper_2606_01478_b300 import Sim, autotune
-    wl = W.mixed_swarm_euler(M=worlds)
+    wl = W.mixed_swarm_euler(M=worlds, models_of=models_of)
     sim = Sim.batched(np.full(wl.M, wl.N), wl.model_of_world, wl.integrator, wl.dt, ctrl=wl.ctrl,
                       max_cmd_blocks=wl.cmd.shape[0], device=dev)
     sim.set_params(wl.params, wl.param_set_of_world)
@@ -991,6 +999,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the measurements beside the headline")
     ap.add_argument("--worlds", type=int, default=1000, help="worlds of --only mixed")
+    ap.add_argument("--models", default="mixed", choices=["mixed", "fp", "abs"],
+                    help="--only mixed: every world first-principles (fp), abstracted (abs) or alternating")
     ap.add_argument("--only", choices=["mixed", "attitude", "bptt", "sampling", "mppi", "training", "depth",
                                        "scale"],
                     default=None,
@@ -1002,7 +1012,7 @@ def main(argv=None):
         local = int(os.environ.get("LOCAL_RANK", "0"))
         torch.cuda.set_device(local)
         dev = torch.device("cuda", local)
-        fn = {"mixed": lambda d, reps: measure_mixed(d, reps, args.worlds),
+        fn = {"mixed": lambda d, reps: measure_mixed(d, reps, args.worlds, args.models),
               "attitude": lambda d, reps: measure_attitude_swarm(d, reps)[0],
               "bptt": measure_policy_bptt, "sampling": measure_sampling,
               "mppi": measure_mppi, "training": measure_bptt_training, "depth": measure_depth,

@@ -186,25 +186,30 @@ def attitude_swarm_rk4(seed: int = 1001, M: int = 16384, steps: int = 1000, K: i
                     hold, [P], np.zeros(M, np.int32), np.zeros(M, np.int32), x0, cmd)
 
 
-def mixed_swarm_euler(seed: int = 1002, M: int = 1000, N: int = 4000, steps: int = 200, K: int = 200) -> Workload:
+def mixed_swarm_euler(seed: int = 1002, M: int = 1000, N: int = 4000, steps: int = 200, K: int = 200,
+                      models_of: str = "mixed") -> Workload:
     """M worlds x N drones (default 1000 x 4000 = 4M), even worlds
     first-principles, odd worlds abstracted with each abstracted coefficient
     scaled by U(0.9, 1.1) per world; attitude interface; Euler at dt = 1/500 s,
     200 steps.  Initial states as in attitude_swarm_rk4 (abstracted: Psi from the same
     roll/pitch/yaw draw, Psidot = 0, f_sigma = m g); per-drone attitude
-    commands U[-0.5, 0.5]^4 held for 50 steps."""
+    commands U[-0.5, 0.5]^4 held for 50 steps.  models_of = "fp" or "abs"
+    makes every world first-principles or abstracted instead (the same draws)."""
     rng = np.random.default_rng(seed)
     base = crazyflie_params()
     params, models = [], np.zeros(M, np.int32)
     for w in range(M):
-        if w % 2 == 0:
+        first = (w % 2 == 0) if models_of == "mixed" else models_of == "fp"
+        if models_of == "abs" or not first:
+            coeff = {k: rng.uniform(0.9, 1.1) for k in ("c1_r", "c1_p", "c1_y", "c2_r", "c2_p", "c2_y",
+                                                          "c3_r", "c3_p", "c3_y", "c_tau", "c_f")}
+        if first:
             params.append(dict(base))
         else:
             models[w] = 1
             q = dict(base)
-            for k in ("c1_r", "c1_p", "c1_y", "c2_r", "c2_p", "c2_y", "c3_r", "c3_p", "c3_y",
-                      "c_tau", "c_f"):
-                q[k] = base[k] * rng.uniform(0.9, 1.1)
+            for k, f in coeff.items():
+                q[k] = base[k] * f
             params.append(q)
     n = M * N
     pos = np.array([0.0, 0.0, 1.0]) + rng.uniform(-1, 1, (n, 3))
@@ -219,7 +224,8 @@ def mixed_swarm_euler(seed: int = 1002, M: int = 1000, N: int = 4000, steps: int
     x0[is_abs] = xa
     hold = 50
     cmd = _attitude_commands(rng, (steps + hold - 1) // hold, n)
-    return Workload(f"swarm_{M}x{N}_mixed_euler_attitude_{steps}", M, N, -1, 0, 1, 1.0 / 500, steps,
+    kind = {"mixed": "mixed", "fp": "fp", "abs": "abs"}[models_of]
+    return Workload(f"swarm_{M}x{N}_{kind}_euler_attitude_{steps}", M, N, -1, 0, 1, 1.0 / 500, steps,
                     K, hold, params, np.arange(M, dtype=np.int32), models, x0, cmd)
 
 
