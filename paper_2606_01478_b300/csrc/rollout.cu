@@ -287,6 +287,36 @@ __device__ __forceinline__ float tanh_fast(float x) {
   return copysignf(fmaf(-2.f, r, 1.f), x);
 }
 
+// Two tanh values for one reciprocal: with p = exp(2 |a|) + 1 and q = exp(2 |b|) + 1,
+// 1/p = q / (p q) and 1/q = p / (p q) (about 2 ulp apart from the separate
+// reciprocals).  |x| is clamped to 15 first, where tanh already rounds to +-1 in
+// float, so that p q stays finite.
+__device__ __forceinline__ void tanh_pair(float& a, float& b) {
+  float ea, eb, r;
+  const float ya = fminf(fabsf(a), 15.f) * 2.88539008177792681f;
+  const float yb = fminf(fabsf(b), 15.f) * 2.88539008177792681f;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ea) : "f"(ya));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(eb) : "f"(yb));
+  const float p = ea + 1.f, q = eb + 1.f;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p * q));
+  a = copysignf(fmaf(-2.f, r * q, 1.f), a);
+  b = copysignf(fmaf(-2.f, r * p, 1.f), b);
+}
+
+// The MLP's activations: separate reciprocals with hi + lo operands (their
+// latency-bound chain measured slower with the pairing: forward 0.375 ->
+// 0.403 ms), paired with plain bf16 operands (fewer XU operations: forward
+// 0.326 -> 0.311 ms, forward + adjoint 1.421 -> 1.382 ms).
+template <bool LO>
+__device__ __forceinline__ void tanh2(float& a, float& b) {
+  if constexpr (LO) {
+    a = tanh_fast(a);
+    b = tanh_fast(b);
+  } else {
+    tanh_pair(a, b);
+  }
+}
+
 // MLP forward for the warp's 16 drones (rows r0..r0+15).  Returns h1, h2
 // (fp32 accumulator fragments, after tanh) and writes the actions to act.
 template <bool LO>
@@ -318,7 +348,7 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
 #pragma unroll
   for (int n = 0; n < 8; ++n)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) h1[n][e] = tanh_fast(h1[n][e]);
+    for (int e = 0; e < 4; e += 2) tanh2<LO>(h1[n][e], h1[n][e + 1]);
   // layer 2: z2[d][j] = sum_i h1[d][i] W2[j][i] + b2[j]
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
@@ -345,7 +375,7 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
 #pragma unroll
   for (int n = 0; n < 8; ++n)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) h2[n][e] = tanh_fast(h2[n][e]);
+    for (int e = 0; e < 4; e += 2) tanh2<LO>(h2[n][e], h2[n][e + 1]);
   // layer 3: z3[d][o] = sum_j h2[d][j] W3[o][j] + b3[o]
   float z3[4];
   z3[0] = s.b3[2 * tq];
