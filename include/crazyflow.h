@@ -338,10 +338,11 @@ int sim_sample_rollouts(sim_h h, int S, int H, const uint64_t* seed, float sigma
  * Constraints: S % n_ctrl == 0, 1 <= n_ctrl <= 32, 0 <= rho < 1, lambda > 0,
  * 1 <= n_elite <= min(S_c, SIM_MAX_ELITES).  Controllers with more than
  * SIM_MPPI_WARP_MAX_COSTS samples or more than SIM_MPPI_WARP_MAX_ELITES elites
- * take the cluster update (one thread-block cluster of up to 8 blocks per
- * controller, the controller's costs split over its blocks), which needs
+ * take the cluster update (one thread-block cluster of up to 16 blocks per
+ * controller -- 16 where the device places clusters of that size, else 8 --
+ * the controller's costs split over its blocks), which needs
  * n_ctrl <= SIM_MPPI_CLUSTER_MAX_CTRL, H <= SIM_MPPI_CLUSTER_MAX_H and
- * Ntot n_ctrl < 2^28.  Two launches (sampling, update); no scratch memory. */
+ * Ntot n_ctrl < 2^27.  Two launches (sampling, update); no scratch memory. */
 #define SIM_MAX_ELITES 4096
 #define SIM_MPPI_WARP_MAX_COSTS 2048
 #define SIM_MPPI_WARP_MAX_ELITES 32
@@ -370,7 +371,7 @@ int sim_mppi_iteration(sim_h h, const sim_mppi_config* cfg, const uint64_t* seed
  * sample indices in increasing index order, -1 in the slots past the row's
  * number of non-NaN costs; jmin: device float [rows] (or NULL), the row's
  * smallest cost (INFINITY if every cost is NaN).  1 <= n_e <= SIM_MAX_ELITES,
- * S_c >= 1, 0 <= rows < 2^28, 4-byte aligned buffers.  One launch, no handle.
+ * S_c >= 1, 0 <= rows < 2^27, 4-byte aligned buffers.  One launch, no handle.
  * Returns SIM_EINVAL on bad arguments (nothing launched), SIM_ECUDA if the
  * launch fails. */
 int sim_mppi_select_elites(const float* cost, int64_t rows, int S_c, int n_e, int32_t* idx,

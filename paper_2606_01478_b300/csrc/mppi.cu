@@ -11,7 +11,7 @@
 //  * warp path (S_c <= 2048 costs and n_e <= 32 elites per controller): one
 //    block per drone, one warp per controller, the costs in registers as
 //    order-preserving keys and a bisection over the key range;
-//  * cluster path (larger): one thread-block cluster of up to 8 CTAs per
+//  * cluster path (larger): one thread-block cluster of up to 16 CTAs per
 //    (drone, controller), each CTA holding a slice of the controller's cost
 //    keys in shared memory; histogram narrowing, compaction and the weighted
 //    mean are split over the cluster's CTAs, which agree through distributed
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(256) elite_select_warp_kernel(const float* cos
 
 // ------------------------------------------------------------------ cluster path
 //
-// One thread-block cluster of P CTAs (P = 1, 2, 4 or 8) per (drone, controller)
+// One thread-block cluster of P CTAs (P = 1, 2, 4, 8 or 16) per (drone, controller)
 // -- or per row of sim_mppi_select_elites.  CTA p owns the contiguous slice
 // [p L, (p + 1) L) of the controller's S_c samples (L = ceil(S_c / P)) and keeps
 // its cost keys in shared memory when the slice fits.  The CTAs of a cluster
@@ -302,6 +302,7 @@ constexpr int KCAP = 24576;    // cost keys of a CTA's slice kept in shared memo
 constexpr int MAXC = SIM_MPPI_CLUSTER_MAX_CTRL;
 constexpr int U4 = 8;          // float4 loads in flight per thread when streaming costs
 constexpr int XI_F4 = 2048;    // (elite, step) noise buffer of the few-elite mean: 32 KB
+constexpr int MAXP = 16;       // CTAs per cluster at most (the peer-read loops are unrolled to it)
 
 struct ClusterArgs {
   const float* cost;  // update: [n][S]; selection: [rows][S_c]
@@ -607,17 +608,27 @@ __global__ void __launch_bounds__(CT, 1) elite_cluster_kernel(ClusterArgs a) {
 #pragma unroll
   for (int q = 0; q < MAXC; ++q) cm[q] = NAN_KEY;
   if (UPDATE) {
+    // the other controllers' minima over the same slice positions: every
+    // controller's loads of a batch are issued before any is used (one round
+    // trip per batch instead of one per controller)
+    constexpr int UM = 4;
+    for (int b = s0 + tid; b < s1; b += UM * CT) {
+      float v[MAXC][UM];
 #pragma unroll
-    for (int q = 0; q < MAXC; ++q) {
-      if (q >= a.C) break;
-      if (q == c) {
-        cm[q] = kmin;
-        continue;
-      }
-      uint32_t m = NAN_KEY;
-      stream_costs(rowp + (size_t)q * a.S_c, s0, s1, [&](int, float x) { m = min(m, cost_key(x)); });
-      cm[q] = m;
+      for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int u = 0; u < UM; ++u) {
+          const int i = b + u * CT;
+          v[q][u] = (q < a.C && q != c && i < s1) ? rowp[(size_t)q * a.S_c + i] : __int_as_float(0x7fffffff);
+        }
+#pragma unroll
+      for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int u = 0; u < UM; ++u) cm[q] = min(cm[q], cost_key(v[q][u]));
     }
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+      if (q == c) cm[q] = kmin;
   }
   kmin = __reduce_min_sync(FULL, kmin);
   kmax = __reduce_max_sync(FULL, kmax);
@@ -711,8 +722,12 @@ __global__ void __launch_bounds__(CT, 1) elite_cluster_kernel(ClusterArgs a) {
     // reduce-scatter: CTA p adds bucket range p of the P histograms
     uint32_t ssum = 0u;
     for (int b = tid; b < SEG; b += CT) {
+      uint32_t hv[MAXP];  // all peers' loads in flight, then added in rank order
+#pragma unroll
+      for (int r = 0; r < MAXP; ++r) hv[r] = r < P ? peer(cluster, &sm.hist[0], r)[p * SEG + b] : 0u;
       uint32_t t = 0u;
-      for (int r = 0; r < P; ++r) t += peer(cluster, &sm.hist[0], r)[p * SEG + b];
+#pragma unroll
+      for (int r = 0; r < MAXP; ++r) t += hv[r];
       sm.segb[b] = t;
       ssum += t;
     }
@@ -915,8 +930,14 @@ __global__ void __launch_bounds__(CT, 1) elite_cluster_kernel(ClusterArgs a) {
     float* prow = a.plan + (size_t)d * a.H * 4;
     for (int x = 4 * k0 + tid; x < 4 * k1; x += CT) {
       const int k = x >> 2;
+      float pv[MAXP];  // all peers' loads in flight, then added in rank order
+#pragma unroll
+      for (int r = 0; r < MAXP; ++r)
+        pv[r] = r < P ? reinterpret_cast<const float*>(peer(cluster, part, r))[x] : 0.f;
       float t = 0.f;
-      for (int r = 0; r < P; ++r) t += reinterpret_cast<const float*>(peer(cluster, part, r))[x];
+#pragma unroll
+      for (int r = 0; r < MAXP; ++r)
+        if (r < P) t += pv[r];
       const float val = t * inv_w;
       if (k > 0) mout[x - 4] = val;        // warm start: shift by one step
       if (k == a.H - 1) mout[x] = val;     // the last step repeated
@@ -933,23 +954,74 @@ bool mppi_uses_warp_path(int S_c, int n_e) {
   return S_c <= mp::WARP_MAX_COSTS && n_e <= mp::WARP_MAX_ELITES;
 }
 
-// CTAs per controller on the cluster path: a power of two up to 8 giving
-// slices of at most about 12k costs.
-static int cluster_ctas(int S_c) {
+// Whether clusters of 16 CTAs (a non-portable size, opted into per kernel) of
+// this kernel can be placed on the current device with this much shared memory;
+// queried once per device.
+static bool cluster16_ok(void (*kern)(mp::ClusterArgs), size_t smem) {
+  static int known[64][2] = {};  // per device and kernel: 0 unknown, 1 yes, -1 no
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return false;
+  }
+  const int which = kern == mp::elite_cluster_kernel<true> ? 1 : 0;
+  if (known[dev][which]) return known[dev][which] > 0;
+  bool ok = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) == cudaSuccess;
+  if (ok) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16, 1, 1);
+    cfg.blockDim = dim3(mp::CT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    ok = cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0;
+  }
+  cudaGetLastError();
+  known[dev][which] = ok ? 1 : -1;
+  return ok;
+}
+
+// CTAs per controller on the cluster path: a power of two, up to 16 where the
+// device places clusters of 16 (else 8), giving slices of at most about 6k
+// costs (12k at 8 CTAs).
+static int cluster_ctas(int S_c, int max_P) {
   int P = 1;
-  while (P < 8 && (S_c + P - 1) / P > 12288) P *= 2;
+  while (P < max_P && (S_c + P - 1) / P > (max_P > 8 ? 6144 : 12288)) P *= 2;
   return P;
 }
 
-static cudaError_t launch_cluster(const mp::ClusterArgs& a, bool update, long long groups,
+// Shared memory of a cluster-path CTA (the key cache sized for `L` keys).
+static size_t cluster_smem(bool update, int H, bool cached, int L) {
+  return sizeof(mp::ClusterSmem) + (update ? (2 * (size_t)H + mp::XI_F4) * sizeof(float4) : 0) +
+         (cached ? (size_t)L * sizeof(uint32_t) : 0);
+}
+
+// Fills a.P, a.L and a.cached for a controller of S_c costs and launches.
+static cudaError_t launch_cluster(mp::ClusterArgs& a, bool update, long long groups,
                                   cudaStream_t st) {
-  const size_t smem = sizeof(mp::ClusterSmem) +
-                      (update ? (2 * (size_t)a.H + mp::XI_F4) * sizeof(float4) : 0) +
-                      (a.cached ? (size_t)a.L * sizeof(uint32_t) : 0);
-  if (groups * a.P >= (1ll << 31)) return cudaErrorInvalidValue;
   auto kern = update ? mp::elite_cluster_kernel<true> : mp::elite_cluster_kernel<false>;
+  // the largest shared-memory size at 16 CTAs per controller decides the probe
+  const bool big = cluster16_ok(kern, cluster_smem(update, update ? SIM_MPPI_CLUSTER_MAX_H : 0, true,
+                                                   mp::KCAP));
+  a.P = cluster_ctas(a.S_c, big ? 16 : 8);
+  a.L = (a.S_c + a.P - 1) / a.P;
+  a.cached = a.L <= mp::KCAP;
+  const size_t smem = cluster_smem(update, a.H, a.cached, a.L);
+  if (groups * a.P >= (1ll << 31)) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if (a.P > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(groups * a.P), 1, 1);
   cfg.blockDim = dim3(mp::CT, 1, 1);
@@ -995,9 +1067,6 @@ cudaError_t launch_mppi_update(const float* cost, float* mean, float* plan, floa
   a.S_c = S_c;
   a.C = C;
   a.n_e = n_e;
-  a.P = cluster_ctas(S_c);
-  a.L = (S_c + a.P - 1) / a.P;
-  a.cached = a.L <= mp::KCAP;
   a.mean = mean;
   a.plan = plan;
   a.best_cost = best_cost;
@@ -1023,9 +1092,6 @@ cudaError_t launch_elite_select(const float* cost, long long rows, int S_c, int 
   a.S_c = S_c;
   a.C = 1;
   a.n_e = n_e;
-  a.P = cluster_ctas(S_c);
-  a.L = (S_c + a.P - 1) / a.P;
-  a.cached = a.L <= mp::KCAP;
   a.idx = idx;
   a.jmin = jmin;
   return launch_cluster(a, false, rows, st);

@@ -577,10 +577,10 @@ int sim_mppi_iteration(sim_h h, const sim_mppi_config* cfg, const uint64_t* seed
   const int S_c = c.S / c.n_ctrl;
   if (!cf::mppi_uses_warp_path(S_c, c.n_elite) &&
       (c.n_ctrl > SIM_MPPI_CLUSTER_MAX_CTRL || c.H > SIM_MPPI_CLUSTER_MAX_H ||
-       h->ntot * c.n_ctrl >= ((int64_t)1 << 28)))
+       h->ntot * c.n_ctrl >= ((int64_t)1 << 27)))
     return fail(h, SIM_EINVAL,
                 "MPPI config: controllers of more than %d samples or %d elites need n_ctrl <= %d, "
-                "H <= %d and Ntot n_ctrl < 2^28", SIM_MPPI_WARP_MAX_COSTS, SIM_MPPI_WARP_MAX_ELITES,
+                "H <= %d and Ntot n_ctrl < 2^27", SIM_MPPI_WARP_MAX_COSTS, SIM_MPPI_WARP_MAX_ELITES,
                 SIM_MPPI_CLUSTER_MAX_CTRL, SIM_MPPI_CLUSTER_MAX_H);
   if (!mean || ((uintptr_t)mean & 15) || !plan || ((uintptr_t)plan & 15) || !best_cost ||
       ((uintptr_t)best_cost & 3))
@@ -631,7 +631,7 @@ int sim_mppi_select_elites(const float* cost, int64_t rows, int S_c, int n_e, in
                            float* jmin, void* stream) {
   if (!cost || !idx || rows < 0 || S_c < 1 || n_e < 1 || n_e > SIM_MAX_ELITES ||
       ((uintptr_t)cost & 3) || ((uintptr_t)idx & 3) || ((uintptr_t)jmin & 3) ||
-      rows >= ((int64_t)1 << 28))
+      rows >= ((int64_t)1 << 27))
     return SIM_EINVAL;
   if (rows == 0) return SIM_OK;
   cudaError_t e = cf::launch_elite_select(cost, (long long)rows, S_c, n_e, (int*)idx, jmin,

@@ -239,3 +239,36 @@ def test_autotune_keys_name_everything_the_timing_depends_on():
     assert lib.sim_autotune_key(a, ctypes.byref(r), buf, 512) == L.SIM_EINVAL
     for x in (a, b, c, d, e, f, g, h):
         lib.sim_destroy(x)
+
+
+
+def test_autotune_refuses_bad_requests_before_any_device_work():
+    """sim_autotune validates on the host: an unknown op, reps out of range, bad
+    candidate block sizes or too many candidates are SIM_EINVAL; a handle with
+    no bound workspace is SIM_ESTATE; nothing reaches the device."""
+    import ctypes
+    lib = L.load()
+    h = ctypes.c_void_p()
+    assert lib.sim_create(ctypes.byref(h), 8, 1, 0, L.EULER, 1 / 500) == L.SIM_OK
+    res = L.TuneResult()
+
+    def call(**kw):
+        r = L.TuneRequest()
+        r.op, r.reps, r.n_steps = L.TUNE_STEP, 1, 10
+        for k, v in kw.items():
+            setattr(r, k, v)
+        return lib.sim_autotune(h, ctypes.byref(r), ctypes.byref(res), None)
+
+    assert call(op=5) == L.SIM_EINVAL
+    assert call(reps=0) == L.SIM_EINVAL
+    assert call(reps=101) == L.SIM_EINVAL
+    assert call(n_tpb=L.TUNE_MAX + 1) == L.SIM_EINVAL
+    r = L.TuneRequest()
+    r.op, r.reps, r.n_steps, r.n_tpb = L.TUNE_STEP, 1, 10, 1
+    r.tpb[0] = 48  # not a multiple of 32
+    assert lib.sim_autotune(h, ctypes.byref(r), ctypes.byref(res), None) == L.SIM_EINVAL
+    assert call(n_steps=0) == L.SIM_EINVAL
+    assert call() == L.SIM_ESTATE  # not bound: no workspace, state or commands
+    assert b"sim_autotune" in lib.sim_last_error(h)
+    assert lib.sim_autotune(h, None, ctypes.byref(res), None) == L.SIM_EINVAL
+    lib.sim_destroy(h)

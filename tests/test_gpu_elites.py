@@ -85,7 +85,7 @@ def test_zero_rows_and_bad_arguments():
     idx = torch.zeros(4, 2, dtype=torch.int32, device="cuda")
     assert lib.sim_mppi_select_elites(ctypes.c_void_p(c.data_ptr()), 0, 8, 2,
                                       ctypes.c_void_p(idx.data_ptr()), None, None) == L.SIM_OK
-    for rows, S_c, n_e in ((-1, 8, 2), (4, 0, 2), (4, 8, 0), (4, 8, L.MAX_ELITES + 1), (1 << 28, 8, 2)):
+    for rows, S_c, n_e in ((-1, 8, 2), (4, 0, 2), (4, 8, 0), (4, 8, L.MAX_ELITES + 1), (1 << 27, 8, 2)):
         assert lib.sim_mppi_select_elites(ctypes.c_void_p(c.data_ptr()), rows, S_c, n_e,
                                           ctypes.c_void_p(idx.data_ptr()), None,
                                           None) == L.SIM_EINVAL
