@@ -54,7 +54,9 @@ struct DevParams {
 // PF_GENERAL_MOTOR selects the general kernel variants (MOTOR_GENERAL): polynomial
 // rotor curves, asymmetric or quadratic rotor dynamics, rotor inertia, or drag
 // (PF_DRAG implies it).  The lag-rotor variants (MOTOR_LAG) have none of these.
-enum : int { PF_DRAG = 1, PF_GENERAL_MOTOR = 2 };
+// PF_ASYM_XY marks Jx != Jy: without it the yaw rate's gyroscopic term
+// (Jx - Jy) wx wy / Jz is zero, and the lag-rotor variants can leave it out.
+enum : int { PF_DRAG = 1, PF_GENERAL_MOTOR = 2, PF_ASYM_XY = 4 };
 
 // Arguments of the step kernels (by value).
 struct StepArgs {

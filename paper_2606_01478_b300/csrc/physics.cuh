@@ -145,6 +145,9 @@ __device__ __forceinline__ void deriv_fp(const float* x, const float Wc[4], cons
 // u_i = cv W_cmd,i (so W_i' = u_i - cv W_i) and the quaternion rate returned
 // doubled, d[3..6] = q (x) [w, 0] = 2 q' (the integrator folds the 1/2 into its
 // coefficients).  Constants kf/m, kfa/J, km/J are folded (DevParams).
+// SYM_XY: Jx = Jy, where the yaw rate's gyroscopic term (Jx - Jy) wx wy / Jz is
+// zero and is left out.
+template <bool SYM_XY = false>
 __device__ __forceinline__ void deriv_fp_rate(const float* x, const float u[4], const DevParams& P,
                                               float* d, const float* Rc = nullptr) {
   const float qx = x[3], qy = x[4], qz = x[5], qw = x[6];
@@ -177,7 +180,8 @@ __device__ __forceinline__ void deriv_fp_rate(const float* x, const float u[4], 
   // w' = J^-1 tau - J^-1 (w x J w), rotor torques as in deriv_fp
   d[10] = fmaf(P.kfaJx, a23 - a01, P.cJx * wy * wz);
   d[11] = fmaf(P.kfaJy, (s1 + s2) - (s0 + s3), P.cJy * wz * wx);
-  d[12] = fmaf(P.kmJz, (s1 + s3) - (s0 + s2), P.cJz * wx * wy);
+  if constexpr (SYM_XY) d[12] = P.kmJz * ((s1 + s3) - (s0 + s2));
+  else d[12] = fmaf(P.kmJz, (s1 + s3) - (s0 + s2), P.cJz * wx * wy);
 #pragma unroll
   for (int r = 0; r < 4; ++r) d[13 + r] = fmaf(P.ncv, x[13 + r], u[r]);
 }

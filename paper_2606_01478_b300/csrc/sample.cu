@@ -53,7 +53,9 @@ using noise::box_muller;
 using noise::philox4x32_10;
 using noise::philox_round_key;
 
-template <int INTEG, int MOTOR, bool WINDOWED>
+// SYM: Jx = Jy in every parameter set (the lag step form then drops the yaw
+// rate's zero gyroscopic term).
+template <int INTEG, int MOTOR, bool WINDOWED, bool SYM>
 __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const DevParams& P,
                                          long long r, int d, int smp, int w,
                                          const uint2* keys) {
@@ -152,6 +154,7 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
   float cost = 0.f;
   float4 eps = make_float4(0.f, 0.f, 0.f, 0.f);
   const bool ar1 = a.rho != 0.f;
+  noise::PhiloxSteps ph(id_lo, id_hi, keys);
   // WINDOWED: the horizon spans several windows (a kernel of its own, so that a
   // horizon of one window keeps a loop without culling code)
   int next_cull = cullable ? sc.cull_steps : sc.H;
@@ -163,8 +166,8 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
         next_cull += sc.cull_steps;
       }
     }
-    uint32_t c[4] = {id_lo, id_hi, (uint32_t)k, 0u};
-    philox4x32_10(c, keys);
+    uint32_t c[4];
+    ph.next(c, keys);  // the block of counter (id_lo, id_hi, k, 0)
     const float2 z01 = box_muller(c[0], c[1]);
     const float2 z23 = box_muller(c[2], c[3]);
     // AR(1) temporal correlation: eps_0 = xi_0, eps_k = rho eps_{k-1} + rho_c xi_k;
@@ -185,7 +188,7 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
                                    fmaf(sc.sigma, eps.z, m.z), fmaf(sc.sigma, eps.w, m.w));
     CtrlHold h;
     decode_command<SIM_FIRST_PRINCIPLES, SIM_CTRL_ATTITUDE>(act, P, h);
-    one_step<SIM_FIRST_PRINCIPLES, INTEG, SIM_CTRL_ATTITUDE, MOTOR>(s, h, P, drag, sc.dt);
+    one_step<SIM_FIRST_PRINCIPLES, INTEG, SIM_CTRL_ATTITUDE, MOTOR, SYM>(s, h, P, drag, sc.dt);
     const float ex = s[0] - gx, ey = s[1] - gy, ez = s[2] - gz;
     float pen = 0.f;
     auto test = [&](int o) {
@@ -206,7 +209,7 @@ __device__ __forceinline__ float rollout(const Args& a, const Scene& sc, const D
   return cost;
 }
 
-template <int INTEG, int MOTOR, bool PERSET, bool WINDOWED>
+template <int INTEG, int MOTOR, bool PERSET, bool WINDOWED, bool SYM>
 __global__ void __launch_bounds__(256) sample_kernel(Args a, Scene sc, DevParams P0) {
   const unsigned long long seed = *a.seed;
   __shared__ uint2 keys[10];
@@ -232,25 +235,25 @@ __global__ void __launch_bounds__(256) sample_kernel(Args a, Scene sc, DevParams
     float cost;
     if constexpr (PERSET) {
       const DevParams P = a.params[a.set_of_world[w]];
-      cost = rollout<INTEG, MOTOR, WINDOWED>(a, sc, P, r, d, smp, w, keys);
+      cost = rollout<INTEG, MOTOR, WINDOWED, SYM>(a, sc, P, r, d, smp, w, keys);
     } else {
-      cost = rollout<INTEG, MOTOR, WINDOWED>(a, sc, P0, r, d, smp, w, keys);
+      cost = rollout<INTEG, MOTOR, WINDOWED, SYM>(a, sc, P0, r, d, smp, w, keys);
     }
     a.cost[r] = cost;
   }
 }
 
-template <int INTEG, int MOTOR, bool PERSET, bool WINDOWED>
+template <int INTEG, int MOTOR, bool PERSET, bool WINDOWED, bool SYM = false>
 static cudaError_t launch_t(const Args& a, const Scene& sc, const DevParams& P, int tpb,
                             cudaStream_t st) {
-  static int cached[16][9] = {};
+  static int cached[16][9] = {};  // per instantiation
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int slot = tpb / 32;
   int per_sm = (dev < 16 && slot <= 8) ? cached[dev][slot] : 0;
   if (per_sm == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_kernel<INTEG, MOTOR, PERSET, WINDOWED>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_kernel<INTEG, MOTOR, PERSET, WINDOWED, SYM>,
                                                   tpb, 0);
     if (per_sm < 1) per_sm = 1;
     if (dev < 16 && slot <= 8) cached[dev][slot] = per_sm;
@@ -258,7 +261,7 @@ static cudaError_t launch_t(const Args& a, const Scene& sc, const DevParams& P, 
   long long grid = (long long)sms * per_sm;
   const long long need = (a.total + tpb - 1) / tpb;
   if (grid > need) grid = need;
-  sample_kernel<INTEG, MOTOR, PERSET, WINDOWED><<<(unsigned)grid, tpb, 0, st>>>(a, sc, P);
+  sample_kernel<INTEG, MOTOR, PERSET, WINDOWED, SYM><<<(unsigned)grid, tpb, 0, st>>>(a, sc, P);
   return cudaGetLastError();
 }
 
@@ -336,18 +339,27 @@ cudaError_t launch_sample(const float4* planes, int n, const int* offsets, int M
   // culling runs only for lag rotors; with those, a horizon of several windows
   // takes the windowed kernel
   const bool windowed = sc.cull_steps < H;
+  // the lag-rotor variants come in two forms: Jx = Jy in every set (the union of the
+  // sets' flags lacks PF_ASYM_XY) or not
+  const bool sym = (P0.flags & PF_ASYM_XY) == 0;
 #define CF_S(I, MO, WI)                                                      \
   return per_set ? sp::launch_t<I, MO, true, WI>(a, sc, P0, tpb, st)          \
                  : sp::launch_t<I, MO, false, WI>(a, sc, P0, tpb, st)
+#define CF_L(I, WI)                                                                        \
+  return per_set ? (sym ? sp::launch_t<I, MOTOR_LAG, true, WI, true>(a, sc, P0, tpb, st)    \
+                        : sp::launch_t<I, MOTOR_LAG, true, WI, false>(a, sc, P0, tpb, st))  \
+                 : (sym ? sp::launch_t<I, MOTOR_LAG, false, WI, true>(a, sc, P0, tpb, st)   \
+                        : sp::launch_t<I, MOTOR_LAG, false, WI, false>(a, sc, P0, tpb, st))
   if (integrator == SIM_RK4) {
     if (general_motor) CF_S(SIM_RK4, MOTOR_GENERAL, false);
-    if (windowed) CF_S(SIM_RK4, MOTOR_LAG, true);
-    CF_S(SIM_RK4, MOTOR_LAG, false);
+    if (windowed) CF_L(SIM_RK4, true);
+    CF_L(SIM_RK4, false);
   }
   if (general_motor) CF_S(SIM_EULER, MOTOR_GENERAL, false);
-  if (windowed) CF_S(SIM_EULER, MOTOR_LAG, true);
-  CF_S(SIM_EULER, MOTOR_LAG, false);
+  if (windowed) CF_L(SIM_EULER, true);
+  CF_L(SIM_EULER, false);
 #undef CF_S
+#undef CF_L
 }
 
 }  // namespace cf

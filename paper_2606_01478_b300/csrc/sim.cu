@@ -195,6 +195,7 @@ int derive_params(const float* p, DevParams* d, char* why, size_t why_n) {
   if (p[SIM_P_CV_UP] != p[SIM_P_CV_DOWN] || p[SIM_P_CD_UP] != 0.f || p[SIM_P_CD_DOWN] != 0.f ||
       p[SIM_P_J_P] != 0.f || kf0 != 0.0 || kf1 != 0.0 || p[SIM_P_KM1] != 0.f)
     flags |= cf::PF_GENERAL_MOTOR;
+  if (Jx != Jy) flags |= cf::PF_ASYM_XY;
   d->flags = flags;
   return SIM_OK;
 }
@@ -235,10 +236,12 @@ int sample_launch(sim_h h, int S, int H, const uint64_t* seed, float sigma,
       if (!isfinite(obstacles[4 * o + j])) return fail(h, SIM_EINVAL, "obstacle %d not finite", o);
     if (obstacles[4 * o + 3] < 0.f) return fail(h, SIM_EINVAL, "obstacle %d has a negative radius", o);
   }
+  // one parameter set for every world (uniform or batched): the parameters are
+  // kernel arguments (constant bank); otherwise each rollout reads its world's set
   cudaError_t e = cf::launch_sample(
       h->planes, (int)h->ntot, h->batched ? h->offsets_dev : nullptr, (int)h->M, (int)h->N, goals,
       nominal, (const unsigned long long*)seed, h->params_dev, h->set_of_world_dev, h->p0,
-      h->per_set || h->batched, h->general_motor, h->integrator, obstacles, n_obs, w_obs, sigma,
+      h->per_set, h->general_motor, h->integrator, obstacles, n_obs, w_obs, sigma,
       h->dt, S, H, cost, h->tpb_sample, (cudaStream_t)stream, n_ctrl, rho);
   if (e != cudaSuccess) return cuda_fail(h, e, "sampling launch");
   h->launches++;

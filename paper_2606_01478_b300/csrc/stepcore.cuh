@@ -48,7 +48,8 @@ constexpr bool lag_step_form() {
   return MODEL == SIM_FIRST_PRINCIPLES && MOTOR == MOTOR_LAG;
 }
 
-template <int MODEL, int INTEG, int CTRL, int MOTOR>
+// SYM_XY (lag step form only): Jx = Jy, the yaw rate's gyroscopic term left out.
+template <int MODEL, int INTEG, int CTRL, int MOTOR, bool SYM_XY = false>
 __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevParams& P, bool drag,
                                          float dt) {
   constexpr int D = (MODEL == SIM_FIRST_PRINCIPLES) ? 17 : 13;
@@ -87,7 +88,7 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
   }
   auto deriv = [&](const float* x, float* d, const float* Rx) {
     if constexpr (LSF) {
-      deriv_fp_rate(x, Wc, P, d, Rx);
+      deriv_fp_rate<SYM_XY>(x, Wc, P, d, Rx);
     } else if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
       deriv_fp<MOTOR>(x, Wc, P, drag, d, Rx);
     } else if constexpr (MODEL == SIM_ABSTRACTED) {
