@@ -29,8 +29,9 @@ struct DevParams {
   float KwJ_x, KwJ_y, KwJ_z;
   // position PID
   float Kp_x, Kp_y, Kp_z, Kd_x, Kd_y, Kd_z, Ki_x, Ki_y, Ki_z;
-  // action map: angle = a * max_angle, T = m g + (m g thrust_scale) a4
-  float max_angle, mg, ts_mg;
+  // action map: angle = a * max_angle, T = m g + (m g thrust_scale) a4;
+  // half_max_angle = max_angle / 2 (half angles of the desired quaternion)
+  float max_angle, half_max_angle, mg, ts_mg;
   // mixer f_i = T/4 +- tau_x mix_a +- tau_y mix_a +- tau_z mix_k, clip [0, fmax],
   // W_cmd = sqrt(f * inv_kf)
   float mix_a, mix_k, inv_kf, fmax, omega_max;

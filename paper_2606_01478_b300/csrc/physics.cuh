@@ -267,6 +267,47 @@ __device__ __forceinline__ void attitude_command(float4 a, const DevParams& P, f
   Td = fmaf(P.ts_mg, clampf(a.w, -1.f, 1.f), P.mg);
 }
 
+// Attitude action a -> twice the desired unit quaternion qd (scalar last) and the
+// collective thrust Td.  qd is the rotation of Rd = Rz(yaw) Ry(pitch) Rx(roll)
+// (attitude_command), composed from half angles: qd = qz(yaw) (x) qy(pitch) (x)
+// qx(roll).  The factor 2 makes attitude_error2_q's product the vee of the
+// matrix form without another multiply.
+__device__ __forceinline__ void attitude_command_q(float4 a, const DevParams& P, float qd[4],
+                                                   float& Td) {
+  const float hr = clampf(a.x, -1.f, 1.f) * P.half_max_angle;
+  const float hp = clampf(a.y, -1.f, 1.f) * P.half_max_angle;
+  const float hy = clampf(a.z, -1.f, 1.f) * P.half_max_angle;
+  float sr, cr, sp, cp, sy, cy;
+  __sincosf(hr, &sr, &cr);
+  __sincosf(hp, &sp, &cp);
+  __sincosf(hy, &sy, &cy);
+  const float cp2 = cp + cp, sp2 = sp + sp;
+  const float a_ = cp2 * cy, b_ = sp2 * sy, c_ = sp2 * cy, d_ = cp2 * sy;
+  qd[0] = fmaf(sr, a_, -cr * b_);
+  qd[1] = fmaf(cr, c_, sr * d_);
+  qd[2] = fmaf(cr, d_, -sr * c_);
+  qd[3] = fmaf(cr, a_, sr * b_);
+  Td = fmaf(P.ts_mg, clampf(a.w, -1.f, 1.f), P.mg);
+}
+
+// 2 e_R = vee(Rd^T R - R^T Rd) from quaternions: with qe = qd* (x) q,
+// Rd^T R = R(qe) and vee(R(qe) - R(qe)^T) = 4 qe_w qe_v for the quadratic form
+// of R (any norm of q); with qd2 = 2 qd (attitude_command_q) that is
+// (qd2* (x) q)_w (qd2* (x) q)_v.  x = the state (q in slots 3-6).
+__device__ __forceinline__ void attitude_error2_q(const float* x, const float qd2[4], float& ex,
+                                                  float& ey, float& ez) {
+  const float qx = x[3], qy = x[4], qz = x[5], qw = x[6];
+  const float dx = qd2[0], dy = qd2[1], dz = qd2[2], dw = qd2[3];
+  // qd* (x) q = (dw qv - qw dv - dv x qv, dw qw + dv . qv)
+  const float vx = fmaf(dw, qx, fmaf(-qw, dx, fmaf(-dy, qz, dz * qy)));
+  const float vy = fmaf(dw, qy, fmaf(-qw, dy, fmaf(-dz, qx, dx * qz)));
+  const float vz = fmaf(dw, qz, fmaf(-qw, dz, fmaf(-dx, qy, dy * qx)));
+  const float w = fmaf(dw, qw, fmaf(dx, qx, fmaf(dy, qy, dz * qz)));
+  ex = w * vx;
+  ey = w * vy;
+  ez = w * vz;
+}
+
 // Abstracted-model input (Psi_cmd, f_cmd) from an attitude action.
 __device__ __forceinline__ void abstracted_command(float4 a, const DevParams& P, float u[4]) {
   u[0] = clampf(a.x, -1.f, 1.f) * P.max_angle;
@@ -285,16 +326,22 @@ __device__ __forceinline__ void attitude_error2(const float R[9], const float Rd
 #undef CF_M
 }
 
-// Geometric attitude PD, tau = -K_R J e_R - K_w J w with
-// e_R = 1/2 vee(Rd^T R - R^T Rd).
+// Geometric attitude PD, tau = -K_R J e_R - K_w J w, given 2 e_R.
+__device__ __forceinline__ void attitude_torque_e(float ex, float ey, float ez, float wx, float wy,
+                                                  float wz, const DevParams& P, float& tx,
+                                                  float& ty, float& tz) {
+  tx = -fmaf(P.KRJh_x, ex, P.KwJ_x * wx);
+  ty = -fmaf(P.KRJh_y, ey, P.KwJ_y * wy);
+  tz = -fmaf(P.KRJh_z, ez, P.KwJ_z * wz);
+}
+
+// The same with e_R = 1/2 vee(Rd^T R - R^T Rd) from the matrices.
 __device__ __forceinline__ void attitude_torque(const float R[9], const float Rd[9], float wx,
                                                 float wy, float wz, const DevParams& P,
                                                 float& tx, float& ty, float& tz) {
   float ex, ey, ez;
   attitude_error2(R, Rd, ex, ey, ez);
-  tx = -fmaf(P.KRJh_x, ex, P.KwJ_x * wx);
-  ty = -fmaf(P.KRJh_y, ey, P.KwJ_y * wy);
-  tz = -fmaf(P.KRJh_z, ez, P.KwJ_z * wz);
+  attitude_torque_e(ex, ey, ez, wx, wy, wz, P, tx, ty, tz);
 }
 
 // X-configuration mixer: per-rotor thrusts from (T, tau), clipped to the
@@ -337,15 +384,21 @@ __device__ __forceinline__ void mixer_rate(float T, float X, float Y, float Z, c
   for (int r = 0; r < 4; ++r) u[r] = sqrt_approx(clampf(f[r], 0.f, P.u2max));
 }
 
-// Attitude PD followed by the step-form mixer (lag rotors): the PD gains, mixer
-// factors and cv^2 / kf are folded into cR*, cw* (DevParams).
+// Attitude PD followed by the step-form mixer (lag rotors), given 2 e_R: the PD
+// gains, mixer factors and cv^2 / kf are folded into cR*, cw* (DevParams).
+__device__ __forceinline__ void attitude_mixer_rate_e(float ex, float ey, float ez, float T,
+                                                      float wx, float wy, float wz,
+                                                      const DevParams& P, float u[4]) {
+  mixer_rate(T, -fmaf(P.cRx, ex, P.cwx * wx), -fmaf(P.cRy, ey, P.cwy * wy),
+             -fmaf(P.cRz, ez, P.cwz * wz), P, u);
+}
+
 __device__ __forceinline__ void attitude_mixer_rate(const float R[9], const float Rd[9], float T,
                                                     float wx, float wy, float wz,
                                                     const DevParams& P, float u[4]) {
   float ex, ey, ez;
   attitude_error2(R, Rd, ex, ey, ez);
-  mixer_rate(T, -fmaf(P.cRx, ex, P.cwx * wx), -fmaf(P.cRy, ey, P.cwy * wy),
-             -fmaf(P.cRz, ez, P.cwz * wz), P, u);
+  attitude_mixer_rate_e(ex, ey, ez, T, wx, wy, wz, P, u);
 }
 
 // Position PID (geometric): setpoint sp = (x, y, z, yaw) with (sin, cos) of

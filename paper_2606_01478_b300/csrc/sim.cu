@@ -139,6 +139,7 @@ int derive_params(const float* p, DevParams* d, char* why, size_t why_n) {
   d->Ki_y = p[SIM_P_KI_Y];
   d->Ki_z = p[SIM_P_KI_Z];
   d->max_angle = p[SIM_P_MAX_ANGLE];
+  d->half_max_angle = (float)(0.5 * p[SIM_P_MAX_ANGLE]);
   d->mg = (float)(m * g);
   d->ts_mg = (float)(p[SIM_P_THRUST_SCALE] * m * g);
   d->mix_a = (float)(1.0 / (4.0 * a));

@@ -9,7 +9,7 @@ namespace cf {
 
 // Controller state held between command-block changes.
 struct CtrlHold {
-  float Rd[9];
+  float qd[4];       // attitude interface: twice the desired quaternion (attitude_command_q)
   float Td;
   float Wc[4];       // rotor-speed interface: clipped commands
   float4 sp;         // position interface: setpoint
@@ -25,7 +25,7 @@ __device__ __forceinline__ void decode_command(float4 c, const DevParams& P, Ctr
     h.Td = c.x;
     h.sp = c;  // body torque in (y, z, w)
   } else if constexpr (CTRL == SIM_CTRL_ATTITUDE) {
-    attitude_command(c, P, h.Rd, h.Td);
+    attitude_command_q(c, P, h.qd, h.Td);
   } else if constexpr (CTRL == SIM_CTRL_POSITION) {
     h.sp = c;
     __sincosf(c.w, &h.syaw, &h.cyaw);
@@ -56,9 +56,14 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
   constexpr bool LSF = lag_step_form<MODEL, MOTOR>();
   float Wc[4];  // rotor-speed commands (rates cv W_cmd in the lag step form)
   float ep[3] = {0.f, 0.f, 0.f};
-  float R[9];  // R(q) of the state at the start of the step (controller and first stage)
+  // R(q) of the state at the start of the step: the position controller's
+  // matrices; the first derivative stage reads its third column.  The attitude
+  // interface forms its error from quaternions instead and every stage takes the
+  // thrust direction from q.
+  float R[9];
+  constexpr bool NEED_R = MODEL == SIM_FIRST_PRINCIPLES && CTRL == SIM_CTRL_POSITION;
   if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
-    quat_rot(s[3], s[4], s[5], s[6], R);
+    if constexpr (NEED_R) quat_rot(s[3], s[4], s[5], s[6], R);
     if constexpr (CTRL == SIM_CTRL_ROTOR_SPEED) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) Wc[r] = LSF ? -P.ncv * h.Wc[r] : h.Wc[r];
@@ -68,15 +73,19 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
       } else {
         mixer<MOTOR>(h.Td, h.sp.y, h.sp.z, h.sp.w, P, Wc);
       }
+    } else if constexpr (CTRL == SIM_CTRL_ATTITUDE) {
+      float ex, ey, ez;
+      attitude_error2_q(s, h.qd, ex, ey, ez);
+      if constexpr (LSF) {
+        attitude_mixer_rate_e(ex, ey, ez, h.Td, s[10], s[11], s[12], P, Wc);
+      } else {
+        float tx, ty, tz;
+        attitude_torque_e(ex, ey, ez, s[10], s[11], s[12], P, tx, ty, tz);
+        mixer<MOTOR>(h.Td, tx, ty, tz, P, Wc);
+      }
     } else {
       float Rd[9], Td;
-      if constexpr (CTRL == SIM_CTRL_POSITION) {
-        position_command(s, R, h.sp, h.syaw, h.cyaw, P, Rd, Td, ep);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 9; ++j) Rd[j] = h.Rd[j];
-        Td = h.Td;
-      }
+      position_command(s, R, h.sp, h.syaw, h.cyaw, P, Rd, Td, ep);
       if constexpr (LSF) {
         attitude_mixer_rate(R, Rd, Td, s[10], s[11], s[12], P, Wc);
       } else {
@@ -97,7 +106,7 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
       deriv_abs_nothrust(x, h.u, P, d);
     }
   };
-  const float* R0 = (MODEL == SIM_FIRST_PRINCIPLES) ? R : nullptr;
+  const float* R0 = NEED_R ? R : nullptr;
   // integrator coefficient c for element j (halved for q in the lag step form)
   auto co = [&](int j, float c) { return (LSF && j >= 3 && j <= 6) ? 0.5f * c : c; };
   // Element-wise integrator arithmetic runs on element pairs (2i, 2i + 1) with the
