@@ -66,6 +66,9 @@ struct StepArgs {
   const DevParams* params;      // per parameter set (global memory)
   const int32_t* set_of_world;  // [M]
   uint32_t* status;             // device status word
+  // uneven batches, fused launches: [0] the next tile to hand out, [1] warps done;
+  // zero between launches (the grid's last warp resets both)
+  uint32_t* tile_ctr;
   int n;                        // drones
   int N;                        // drones per world (uniform batches)
   int n_blocks, hold, t0, K;

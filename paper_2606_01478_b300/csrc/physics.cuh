@@ -152,8 +152,12 @@ __device__ __forceinline__ void deriv_fp_rate(const float* x, const float u[4], 
                                               float* d, const float* Rc = nullptr) {
   const float qx = x[3], qy = x[4], qz = x[5], qw = x[6];
   const float wx = x[10], wy = x[11], wz = x[12];
-  const float s0 = x[13] * x[13], s1 = x[14] * x[14], s2 = x[15] * x[15], s3 = x[16] * x[16];
-  const float a01 = s0 + s1, a23 = s2 + s3, S = a01 + a23;
+  // squared rotor speeds s_i = W_i^2 in the sums the wrench takes: s0 + s1,
+  // s2 + s3, s1 - s0 and s3 - s2 (two products, four multiply-adds)
+  const float W0 = x[13], W1 = x[14], W2 = x[15], W3 = x[16];
+  const float s0 = W0 * W0, s2 = W2 * W2;
+  const float a01 = fmaf(W1, W1, s0), a23 = fmaf(W3, W3, s2), S = a01 + a23;
+  const float e10 = fmaf(W1, W1, -s0), e32 = fmaf(W3, W3, -s2);
   const float Tm = P.kfm * S;  // collective thrust / m
   float ax, ay, az;
   if (Rc) {
@@ -178,18 +182,22 @@ __device__ __forceinline__ void deriv_fp_rate(const float* x, const float u[4], 
   d[8] = ay;
   d[9] = az;
   // w' = J^-1 tau - J^-1 (w x J w), rotor torques as in deriv_fp
+  // roll (s2 + s3) - (s0 + s1), pitch (s1 + s2) - (s0 + s3) = e10 - e32,
+  // yaw (s1 + s3) - (s0 + s2) = e10 + e32
   d[10] = fmaf(P.kfaJx, a23 - a01, P.cJx * wy * wz);
-  d[11] = fmaf(P.kfaJy, (s1 + s2) - (s0 + s3), P.cJy * wz * wx);
-  if constexpr (SYM_XY) d[12] = P.kmJz * ((s1 + s3) - (s0 + s2));
-  else d[12] = fmaf(P.kmJz, (s1 + s3) - (s0 + s2), P.cJz * wx * wy);
+  d[11] = fmaf(P.kfaJy, e10 - e32, P.cJy * wz * wx);
+  if constexpr (SYM_XY) d[12] = P.kmJz * (e10 + e32);
+  else d[12] = fmaf(P.kmJz, e10 + e32, P.cJz * wx * wy);
 #pragma unroll
   for (int r = 0; r < 4; ++r) d[13 + r] = fmaf(P.ncv, x[13 + r], u[r]);
 }
 
 // Abstracted derivative (Eqs. 7-10) of x[0..12] for u = (Psi_cmd, f_cmd).  The
 // drag term exists only in the general variant (MOTOR_GENERAL).
+// cu = (c3_r Psi_cmd,r, c3_p Psi_cmd,p, c3_y Psi_cmd,y, c_tau f_cmd): the command
+// terms, constant while a command is held (abstracted_command).
 template <int MOTOR>
-__device__ __forceinline__ void deriv_abs(const float* x, const float u[4], const DevParams& P,
+__device__ __forceinline__ void deriv_abs(const float* x, const float cu[4], const DevParams& P,
                                           bool drag, float* d) {
   float sr, cr, sp, cp, sy, cy;
   __sincosf(x[3], &sr, &cr);
@@ -221,21 +229,22 @@ __device__ __forceinline__ void deriv_abs(const float* x, const float u[4], cons
   d[6] = ax;
   d[7] = ay;
   d[8] = az;
-  d[9] = fmaf(P.c1_r, x[3], fmaf(P.c2_r, x[9], P.c3_r * u[0]));
-  d[10] = fmaf(P.c1_p, x[4], fmaf(P.c2_p, x[10], P.c3_p * u[1]));
-  d[11] = fmaf(P.c1_y, x[5], fmaf(P.c2_y, x[11], P.c3_y * u[2]));
-  d[12] = P.c_tau * (u[3] - x[12]);
+  d[9] = fmaf(P.c1_r, x[3], fmaf(P.c2_r, x[9], cu[0]));
+  d[10] = fmaf(P.c1_p, x[4], fmaf(P.c2_p, x[10], cu[1]));
+  d[11] = fmaf(P.c1_y, x[5], fmaf(P.c2_y, x[11], cu[2]));
+  d[12] = fmaf(-P.c_tau, x[12], cu[3]);  // c_tau (f_cmd - f)
 }
 
 // Abstracted model without thrust dynamics and drag (last sentence of Abstracted
 // Physics Modeling): thrust c_f f_cmd acts at once; f_sum does not evolve.
-__device__ __forceinline__ void deriv_abs_nothrust(const float* x, const float u[4],
+// cu as for deriv_abs, with cu[3] = c_f f_cmd / m (the thrust follows its command).
+__device__ __forceinline__ void deriv_abs_nothrust(const float* x, const float cu[4],
                                                    const DevParams& P, float* d) {
   float sr, cr, sp, cp, sy, cy;
   __sincosf(x[3], &sr, &cr);
   __sincosf(x[4], &sp, &cp);
   __sincosf(x[5], &sy, &cy);
-  const float fm = P.cf_inv_m * u[3];
+  const float fm = cu[3];
   d[0] = x[6];
   d[1] = x[7];
   d[2] = x[8];
@@ -245,9 +254,9 @@ __device__ __forceinline__ void deriv_abs_nothrust(const float* x, const float u
   d[6] = fm * fmaf(cy * sp, cr, sy * sr);
   d[7] = fm * fmaf(sy * sp, cr, -cy * sr);
   d[8] = fmaf(fm, cp * cr, -P.g);
-  d[9] = fmaf(P.c1_r, x[3], fmaf(P.c2_r, x[9], P.c3_r * u[0]));
-  d[10] = fmaf(P.c1_p, x[4], fmaf(P.c2_p, x[10], P.c3_p * u[1]));
-  d[11] = fmaf(P.c1_y, x[5], fmaf(P.c2_y, x[11], P.c3_y * u[2]));
+  d[9] = fmaf(P.c1_r, x[3], fmaf(P.c2_r, x[9], cu[0]));
+  d[10] = fmaf(P.c1_p, x[4], fmaf(P.c2_p, x[10], cu[1]));
+  d[11] = fmaf(P.c1_y, x[5], fmaf(P.c2_y, x[11], cu[2]));
   d[12] = 0.f;
 }
 
@@ -308,12 +317,21 @@ __device__ __forceinline__ void attitude_error2_q(const float* x, const float qd
   ez = w * vz;
 }
 
-// Abstracted-model input (Psi_cmd, f_cmd) from an attitude action.
-__device__ __forceinline__ void abstracted_command(float4 a, const DevParams& P, float u[4]) {
+// Abstracted-model input u = (Psi_cmd, f_cmd) from an attitude action, and the
+// derivative's command terms cu (deriv_abs with THRUST_LAG, deriv_abs_nothrust
+// without).
+template <bool THRUST_LAG>
+__device__ __forceinline__ void abstracted_command(float4 a, const DevParams& P, float u[4],
+                                                   float cu[4]) {
   u[0] = clampf(a.x, -1.f, 1.f) * P.max_angle;
   u[1] = clampf(a.y, -1.f, 1.f) * P.max_angle;
   u[2] = clampf(a.z, -1.f, 1.f) * P.max_angle;
   u[3] = fmaf(P.ts_mg, clampf(a.w, -1.f, 1.f), P.mg);
+  // the derivative's command terms (Eqs. 8-10), constant while the command is held
+  cu[0] = P.c3_r * u[0];
+  cu[1] = P.c3_p * u[1];
+  cu[2] = P.c3_y * u[2];
+  cu[3] = THRUST_LAG ? P.c_tau * u[3] : P.cf_inv_m * u[3];
 }
 
 // 2 e_R = vee(Rd^T R - R^T Rd); only the off-diagonal entries of Rd^T R are formed.

@@ -53,8 +53,8 @@ Layout layout_of(const sim_s* h, int64_t max_blocks) {
   off = align256(off + (size_t)max_blocks * h->ntot * sizeof(float4));
   L.staging = off;
   off = align256(off + (size_t)h->ntot * SIM_STATE_DIM * sizeof(float));
-  L.status = off;
-  off = align256(off + sizeof(uint32_t));
+  L.status = off;  // status word, then the two tile counters of the batched kernels
+  off = align256(off + 3 * sizeof(uint32_t));
   L.tiles = off;
   off = align256(off + h->tiles.size() * sizeof(int4));
   L.offsets = off;
@@ -356,7 +356,7 @@ int sim_bind(sim_h h, void* workspace, size_t bytes, int64_t max_cmd_blocks, voi
   h->params_ok = h->state_ok = false;
   h->n_blocks = 0;
   h->t = 0;
-  cudaError_t e = cudaMemsetAsync(h->status, 0, sizeof(uint32_t), (cudaStream_t)stream);
+  cudaError_t e = cudaMemsetAsync(h->status, 0, 3 * sizeof(uint32_t), (cudaStream_t)stream);
   if (e == cudaSuccess && !h->tiles.empty())
     e = cudaMemcpyAsync(h->tiles_dev, h->tiles.data(), h->tiles.size() * sizeof(int4),
                         cudaMemcpyHostToDevice, (cudaStream_t)stream);
@@ -486,6 +486,7 @@ int sim_step(sim_h h, int K, void* stream) {
   a.params = h->params_dev;
   a.set_of_world = h->set_of_world_dev;
   a.status = h->status;
+  a.tile_ctr = h->status + 1;
   a.n = (int)h->ntot;
   a.N = (int)h->N;
   a.n_blocks = (int)h->n_blocks;

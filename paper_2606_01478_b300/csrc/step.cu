@@ -129,21 +129,47 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a, DevParams P0) {
 // one world (x = first drone, y = count, z = world, w = model), so the branch
 // on the model is uniform across the warp and parameters are a broadcast load.
 template <int INTEG, int CTRL, int MOTOR, bool SINGLE>
+__device__ __forceinline__ void run_tile(const StepArgs& a, const int4& d, int lane) {
+  if (lane < d.y) {
+    const DevParams P = a.params[a.set_of_world[d.z]];
+    if (d.w == SIM_FIRST_PRINCIPLES) {
+      run_drone<SIM_FIRST_PRINCIPLES, INTEG, CTRL, MOTOR, SINGLE>(a, d.x + lane, P);
+    } else if (d.w == SIM_ABSTRACTED) {
+      run_drone<SIM_ABSTRACTED, INTEG, SIM_CTRL_ATTITUDE, MOTOR, SINGLE>(a, d.x + lane, P);
+    } else {
+      run_drone<SIM_ABSTRACTED_NOTHRUST, INTEG, SIM_CTRL_ATTITUDE, MOTOR, SINGLE>(a, d.x + lane, P);
+    }
+  }
+}
+
+// Tiles of 32 drones, one per warp at a time.  Single-step launches take them in a
+// fixed stride (a launch is ~0.1 ms; a shared counter would serialise 10^5 atomics).
+// Fused launches take the next tile from a device counter, the next index
+// requested before the current tile's steps and read after them: tiles of the two models differ about
+// threefold in cost, so a fixed stride leaves the warps that drew more
+// first-principles tiles running alone at the end.  Which warp steps a tile does
+// not change its result.  The grid's last warp resets the counters for the next
+// launch (a chained launch waits for this grid's completion before its first access).
+template <int INTEG, int CTRL, int MOTOR, bool SINGLE>
 __device__ __forceinline__ void run_tiles(const StepArgs& a, const int4* __restrict__ tiles, int n_tiles) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int t = warp; t < n_tiles; t += nwarps) {
-    const int4 d = tiles[t];
-    if (lane < d.y) {
-      const DevParams P = a.params[a.set_of_world[d.z]];
-      if (d.w == SIM_FIRST_PRINCIPLES) {
-        run_drone<SIM_FIRST_PRINCIPLES, INTEG, CTRL, MOTOR, SINGLE>(a, d.x + lane, P);
-      } else if (d.w == SIM_ABSTRACTED) {
-        run_drone<SIM_ABSTRACTED, INTEG, SIM_CTRL_ATTITUDE, MOTOR, SINGLE>(a, d.x + lane, P);
-      } else {
-        run_drone<SIM_ABSTRACTED_NOTHRUST, INTEG, SIM_CTRL_ATTITUDE, MOTOR, SINGLE>(a, d.x + lane, P);
-      }
+  if constexpr (SINGLE) {
+    for (int t = warp; t < n_tiles; t += nwarps) run_tile<INTEG, CTRL, MOTOR, SINGLE>(a, tiles[t], lane);
+  } else {
+    const unsigned FULL = 0xffffffffu;
+    unsigned raw = lane == 0 ? atomicAdd(&a.tile_ctr[0], 1u) : 0u;
+    int cur = (int)__shfl_sync(FULL, raw, 0);
+    while (cur < n_tiles) {
+      // lane 0 asks for the next tile; its index is read after this tile's steps
+      raw = lane == 0 ? atomicAdd(&a.tile_ctr[0], 1u) : 0u;
+      run_tile<INTEG, CTRL, MOTOR, SINGLE>(a, tiles[cur], lane);
+      cur = (int)__shfl_sync(FULL, raw, 0);
+    }
+    if (lane == 0 && atomicAdd(&a.tile_ctr[1], 1u) == (unsigned)nwarps - 1u) {
+      a.tile_ctr[0] = 0u;
+      a.tile_ctr[1] = 0u;
     }
   }
 }
@@ -156,11 +182,11 @@ __global__ void __launch_bounds__(256) step_batched_kernel(StepArgs a, const int
   run_tiles<INTEG, CTRL, MOTOR, false>(a, tiles, n_tiles);
 }
 
-// One step per launch (HBM bound): compiled for three 256-thread CTAs per SM (two
-// under RK4, whose stages need more registers) so that more state loads are in
-// flight.
+// One step per launch (HBM bound): compiled for four 256-thread CTAs per SM with
+// lag rotors under Euler (three with the general rotor model, two under RK4, whose
+// registers would spill beyond that) so that more state loads are in flight.
 template <int INTEG, int CTRL, int MOTOR>
-__global__ void __launch_bounds__(256, INTEG == SIM_EULER ? 3 : 2)
+__global__ void __launch_bounds__(256, INTEG == SIM_EULER ? (MOTOR == MOTOR_LAG ? 4 : 3) : 2)
     step_batched_single_kernel(StepArgs a, const int4* __restrict__ tiles, int n_tiles) {
   chain_wait();
   chain_release();

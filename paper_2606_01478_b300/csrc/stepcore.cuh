@@ -15,12 +15,13 @@ struct CtrlHold {
   float4 sp;         // position interface: setpoint
   float syaw, cyaw;  // position interface: yaw sine/cosine
   float u[4];        // abstracted model input
+  float cu[4];       // abstracted model: its command terms (abstracted_command)
 };
 
 template <int MODEL, int CTRL>
 __device__ __forceinline__ void decode_command(float4 c, const DevParams& P, CtrlHold& h) {
   if constexpr (MODEL != SIM_FIRST_PRINCIPLES) {
-    abstracted_command(c, P, h.u);
+    abstracted_command<MODEL == SIM_ABSTRACTED>(c, P, h.u, h.cu);
   } else if constexpr (CTRL == SIM_CTRL_TORQUE) {
     h.Td = c.x;
     h.sp = c;  // body torque in (y, z, w)
@@ -101,9 +102,9 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
     } else if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
       deriv_fp<MOTOR>(x, Wc, P, drag, d, Rx);
     } else if constexpr (MODEL == SIM_ABSTRACTED) {
-      deriv_abs<MOTOR>(x, h.u, P, drag, d);
+      deriv_abs<MOTOR>(x, h.cu, P, drag, d);
     } else {
-      deriv_abs_nothrust(x, h.u, P, d);
+      deriv_abs_nothrust(x, h.cu, P, d);
     }
   };
   const float* R0 = NEED_R ? R : nullptr;
