@@ -40,9 +40,10 @@ constexpr int OFF_W1 = 0, OFF_B1 = 832, OFF_W2 = 896, OFF_B2 = 4992, OFF_W3 = 50
               OFF_B3 = 5312, NPOL = 5316, NPOL_PAD = 5376;
 constexpr int TPB = 128, DPC = 64;  // threads and drones per CTA
 constexpr int S16 = 24, S64 = 72;   // padded smem row strides (bf16 elements)
-// One warp's cached activations of one step, in 16-byte chunks: h1 hi, h1 lo,
-// h2 hi, h2 lo (16 rows x S64 bf16 = 144 chunks each), then 16 action rows.
-constexpr int TILE_CHUNKS = 16 * S64 * 2 / 16, CACHE_CHUNKS = 4 * TILE_CHUNKS + 16;
+// One warp's cached activations of one step, in 16-byte chunks: h2 hi, h2 lo
+// (16 rows x S64 bf16 = 144 chunks each), then 16 action rows.  h1 is not kept:
+// the reverse sweep recomputes it from the state (one layer).
+constexpr int TILE_CHUNKS = 16 * S64 * 2 / 16, CACHE_CHUNKS = 2 * TILE_CHUNKS + 16;
 
 struct __align__(16) Smem {
   __nv_bfloat16 W1[64 * S16];  // [i][c]  (c < 13 used)
@@ -167,39 +168,53 @@ __device__ __forceinline__ void c_to_a(const float c[8][4], int kk, uint32_t ah[
   split2(c[2 * kk + 1][2], c[2 * kk + 1][3], ah[3], al[3]);
 }
 
+// Fragment rows and columns of an x4 matrix move (ldmatrix / stmatrix): lanes 8j..8j+7
+// address the rows of 8x8 matrix j = (rows 0-7 | 8-15) x (columns +0 | +8) of a
+// 16 x 16 block, the order of an A fragment (c_to_a) of one k-tile.
+__device__ __forceinline__ int frag_row(int lane) { return (lane & 7) + ((lane >> 3) & 1) * 8; }
+__device__ __forceinline__ int frag_col(int lane) { return (lane >> 4) * 8; }
+
+__device__ __forceinline__ void stsm_x4(void* p, const uint32_t r[4]) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1,%2,%3,%4};" ::"r"(smem_addr(p)),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3])
+               : "memory");
+}
+
 // Store accumulator fragments c[8][4] (rows r0 + g, r0 + g + 8; 64 columns) as
-// hi/lo bf16 into a [*][S64] tile pair.
+// hi/lo bf16 into a [*][S64] tile pair: per k-tile, the A fragments' hi and lo
+// words go out by one matrix store each (rows of 144 bytes keep the eight rows of
+// each 8x8 matrix on distinct banks).
 __device__ __forceinline__ void store_c64(__nv_bfloat16 (*t)[DPC * S64], int r0, int lane,
                                           const float c[8][4]) {
-  const int g = lane >> 2, tq = lane & 3;
+  const int at = (r0 + frag_row(lane)) * S64 + frag_col(lane);
 #pragma unroll
-  for (int n = 0; n < 8; ++n) {
-    uint32_t h, l;
-    const int col = 8 * n + 2 * tq;
-    split2(c[n][0], c[n][1], h, l);
-    *reinterpret_cast<uint32_t*>(&t[0][(r0 + g) * S64 + col]) = h;
-    *reinterpret_cast<uint32_t*>(&t[1][(r0 + g) * S64 + col]) = l;
-    split2(c[n][2], c[n][3], h, l);
-    *reinterpret_cast<uint32_t*>(&t[0][(r0 + g + 8) * S64 + col]) = h;
-    *reinterpret_cast<uint32_t*>(&t[1][(r0 + g + 8) * S64 + col]) = l;
+  for (int kk = 0; kk < 4; ++kk) {
+    uint32_t h[4], l[4];
+    c_to_a(c, kk, h, l);
+    stsm_x4(&t[0][at + 16 * kk], h);
+    stsm_x4(&t[1][at + 16 * kk], l);
   }
 }
 
 // Reload accumulator-fragment values (hi + lo) from a [*][S64] tile pair.
 __device__ __forceinline__ void load_c64(__nv_bfloat16 (*t)[DPC * S64], int r0, int lane,
                                          float c[8][4]) {
-  const int g = lane >> 2, tq = lane & 3;
+  const int at = (r0 + frag_row(lane)) * S64 + frag_col(lane);
 #pragma unroll
-  for (int n = 0; n < 8; ++n) {
-    const int col = 8 * n + 2 * tq;
-    float2 a = unpack2(*reinterpret_cast<uint32_t*>(&t[0][(r0 + g) * S64 + col]),
-                       *reinterpret_cast<uint32_t*>(&t[1][(r0 + g) * S64 + col]));
-    float2 b = unpack2(*reinterpret_cast<uint32_t*>(&t[0][(r0 + g + 8) * S64 + col]),
-                       *reinterpret_cast<uint32_t*>(&t[1][(r0 + g + 8) * S64 + col]));
-    c[n][0] = a.x;
-    c[n][1] = a.y;
-    c[n][2] = b.x;
-    c[n][3] = b.y;
+  for (int kk = 0; kk < 4; ++kk) {
+    uint32_t h[4], l[4];
+    ldsm_x4(h, &t[0][at + 16 * kk]);
+    ldsm_x4(l, &t[1][at + 16 * kk]);
+    const float2 a0 = unpack2(h[0], l[0]), a1 = unpack2(h[1], l[1]);
+    const float2 a2 = unpack2(h[2], l[2]), a3 = unpack2(h[3], l[3]);
+    c[2 * kk][0] = a0.x;
+    c[2 * kk][1] = a0.y;
+    c[2 * kk][2] = a1.x;
+    c[2 * kk][3] = a1.y;
+    c[2 * kk + 1][0] = a2.x;
+    c[2 * kk + 1][1] = a2.y;
+    c[2 * kk + 1][2] = a3.x;
+    c[2 * kk + 1][3] = a3.y;
   }
 }
 
@@ -317,17 +332,16 @@ __device__ __forceinline__ void tanh2(float& a, float& b) {
   }
 }
 
-// MLP forward for the warp's 16 drones (rows r0..r0+15).  Returns h1, h2
-// (fp32 accumulator fragments, after tanh) and writes the actions to act.
+// Layer 1 of the MLP for the warp's 16 drones (rows r0..r0+15) from the obs tile
+// pair: h1 (fp32 accumulator fragments, after tanh).
 template <bool LO>
-__device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[8][4],
-                            float (*act)[4]) {
-  const int g = lane >> 2, tq = lane & 3;
+__device__ __forceinline__ void mlp_layer1(Smem& s, int r0, int lane, float h1[8][4]) {
+  const int tq = lane & 3;
   const int arow = r0 + (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
   uint32_t oh[4], ol[4];
   ldsm_x4(oh, &s.obs[0][arow * S16 + acol]);
   ldsm_x4(ol, &s.obs[1][arow * S16 + acol]);
-  // layer 1: z1[d][i] = sum_c obs[d][c] W1[i][c] + b1[i]
+  // z1[d][i] = sum_c obs[d][c] W1[i][c] + b1[i]
   const int brow = (lane & 7) + (lane >> 4) * 8, bcol = ((lane >> 3) & 1) * 8;
 #pragma unroll
   for (int n = 0; n < 8; n += 2) {
@@ -349,6 +363,16 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
   for (int n = 0; n < 8; ++n)
 #pragma unroll
     for (int e = 0; e < 4; e += 2) tanh2<LO>(h1[n][e], h1[n][e + 1]);
+}
+
+// MLP forward for the warp's 16 drones (rows r0..r0+15).  Returns h1, h2
+// (fp32 accumulator fragments, after tanh) and writes the actions to act.
+template <bool LO>
+__device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[8][4],
+                            float (*act)[4]) {
+  const int g = lane >> 2, tq = lane & 3;
+  const int bcol = ((lane >> 3) & 1) * 8, brow = (lane & 7) + (lane >> 4) * 8;
+  mlp_layer1<LO>(s, r0, lane, h1);
   // layer 2: z2[d][j] = sum_i h1[d][i] W2[j][i] + b2[j]
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
@@ -822,13 +846,13 @@ __device__ __forceinline__ void ref_at_pinned(const float* __restrict__ p_ref, i
 
 // ------------------------------------------------------------------ activation cache
 
-// One warp's cached step is five contiguous runs in shared memory and in the cache
-// entry alike: the warp's 16 rows of h1 hi, h1 lo, h2 hi, h2 lo in tile buffer b
-// (TILE_CHUNKS 16-byte chunks each) and its 16 action rows in actb[b].  They move
-// as bulk copies (cp.async.bulk: one thread, the copy engine of the SM).
+// One warp's cached step is three contiguous runs in shared memory and in the cache
+// entry alike: the warp's 16 rows of h2 hi, h2 lo in tile buffer b (TILE_CHUNKS
+// 16-byte chunks each) and its 16 action rows in actb[b].  They move as bulk
+// copies (cp.async.bulk: one thread, the copy engine of the SM).
 constexpr uint32_t TILE_BYTES = TILE_CHUNKS * 16, ACT_BYTES = 16 * 16;
-constexpr uint32_t CACHE_BYTES = 4 * TILE_BYTES + ACT_BYTES;
-static_assert(CACHE_BYTES == CACHE_CHUNKS * 16, "cache entry = four tiles + action rows");
+constexpr uint32_t CACHE_BYTES = 2 * TILE_BYTES + ACT_BYTES;
+static_assert(CACHE_BYTES == CACHE_CHUNKS * 16, "cache entry = two tiles + action rows");
 static_assert(offsetof(Smem, h1) % 16 == 0 && offsetof(Smem, h2) % 16 == 0 &&
                   offsetof(Smem, actb) % 16 == 0 && (DPC * S64 * 2) % 16 == 0,
               "bulk copies start on 16-byte boundaries");
@@ -878,33 +902,30 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;\n" ::: "memory");
 }
+// raise the transaction count of the barrier's current phase (no arrival)
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* m, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(m)), "r"(bytes)
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(m)), "r"(bytes)
                : "memory");
 }
 
 // Copy out warp rows r0..r0+15 of tile buffer b to cache entry g (one bulk group).
 __device__ __forceinline__ void cache_store(Smem& s, int b, int r0, uint4* g) {
   const unsigned long long pol = l2_keep();
-  bulk_s2g(g, s.h1[b][0] + r0 * S64, TILE_BYTES, pol);
-  bulk_s2g(g + TILE_CHUNKS, s.h1[b][1] + r0 * S64, TILE_BYTES, pol);
-  bulk_s2g(g + 2 * TILE_CHUNKS, s.h2[b][0] + r0 * S64, TILE_BYTES, pol);
-  bulk_s2g(g + 3 * TILE_CHUNKS, s.h2[b][1] + r0 * S64, TILE_BYTES, pol);
-  bulk_s2g(g + 4 * TILE_CHUNKS, s.actb[b][r0], ACT_BYTES, pol);
+  bulk_s2g(g, s.h2[b][0] + r0 * S64, TILE_BYTES, pol);
+  bulk_s2g(g + TILE_CHUNKS, s.h2[b][1] + r0 * S64, TILE_BYTES, pol);
+  bulk_s2g(g + 2 * TILE_CHUNKS, s.actb[b][r0], ACT_BYTES, pol);
   bulk_commit();
 }
 
-// Bring cache entry g back into rows r0..r0+15 of buffer b; mbar completes when
-// all CACHE_BYTES have landed.
+// Bring cache entry g back into rows r0..r0+15 of buffer b; the barrier's phase
+// waits for all CACHE_BYTES (besides its arrivals).
 __device__ __forceinline__ void cache_load(Smem& s, int b, int r0, const uint4* g,
                                            unsigned long long* mbar) {
   const unsigned long long pol = l2_done();
   mbar_expect_tx(mbar, CACHE_BYTES);
-  bulk_g2s(s.h1[b][0] + r0 * S64, g, TILE_BYTES, mbar, pol);
-  bulk_g2s(s.h1[b][1] + r0 * S64, g + TILE_CHUNKS, TILE_BYTES, mbar, pol);
-  bulk_g2s(s.h2[b][0] + r0 * S64, g + 2 * TILE_CHUNKS, TILE_BYTES, mbar, pol);
-  bulk_g2s(s.h2[b][1] + r0 * S64, g + 3 * TILE_CHUNKS, TILE_BYTES, mbar, pol);
-  bulk_g2s(s.actb[b][r0], g + 4 * TILE_CHUNKS, ACT_BYTES, mbar, pol);
+  bulk_g2s(s.h2[b][0] + r0 * S64, g, TILE_BYTES, mbar, pol);
+  bulk_g2s(s.h2[b][1] + r0 * S64, g + TILE_CHUNKS, TILE_BYTES, mbar, pol);
+  bulk_g2s(s.actb[b][r0], g + 2 * TILE_CHUNKS, ACT_BYTES, mbar, pol);
 }
 
 // Drop a consumed cache entry from L2 without writing it back: the lanes of the
@@ -1064,9 +1085,15 @@ __global__ void wait_selftest_kernel(uint32_t* status) {
 // segment recompute, then per reverse step the loss and step adjoints and the MLP
 // backward, which leave the step's dz, obs and activation tiles in shared memory.
 // Warps 4-7 (weight gradient) accumulate dW over the CTA's 64 drones from those
-// tiles while the compute warps already run the next (earlier) step.  Hand-off per
+// tiles while the compute warps already run the next (earlier) step, and then
+// prepare step k - 2 for compute warp v's drones in the freed buffer: h2 and the
+// actions come back from the segment's cache (bulk copies), h1 is recomputed from
+// the segment state (one layer), so the cache holds half of each step.  The
+// segment's last two steps stay in shared memory from the recompute.  Hand-off per
 // step parity b = k & 1: full[b] (compute threads arrive when the tiles are
-// written), empty[b] (weight-gradient threads arrive when they are read).
+// written), empty[b] (weight-gradient threads arrive when they are read),
+// ready[v][b] (the 32 lanes of the warp that prepared buffer b for warp v's rows
+// arrive, and the copied bytes land).
 template <int OBJ, bool LO>
 __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, DevParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1076,7 +1103,7 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
     for (int b = 0; b < 2; ++b) {
       mbar_init(&s.full[b], TPB);
       mbar_init(&s.empty[b], TPB);
-      for (int v = 0; v < 4; ++v) mbar_init(&s.ready[v][b], 1);
+      for (int v = 0; v < 4; ++v) mbar_init(&s.ready[v][b], 32);
     }
   }
   __syncthreads();
@@ -1093,9 +1120,15 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
   auto cache_at = [&](int v, int j) {
     return a.hcache + (size_t)j * cache_step + ((size_t)blockIdx.x * 4 + v) * CACHE_CHUNKS;
   };
+  // drones of warp v (either role): rows 16 v + (lane & 15) of the CTA's 64;
+  // out-of-range rows shadow the last drone (finite data; their seed and dz are zero)
+  const int v = warp & 3;
+  const int r0 = 16 * v, row = r0 + (lane & 15);
+  const int i = blockIdx.x * DPC + row;
+  const bool valid = i < a.n;
+  const int ii = valid ? i : a.n - 1;
   if (warp >= 4) {
     // ---------------- weight-gradient warps: slice v of dW2 / dW1 / dW3
-    const int v = warp - 4;
     DwAcc acc;
 #pragma unroll
     for (int n = 0; n < 9; ++n) acc.w2[n][0] = acc.w2[n][1] = acc.w2[n][2] = acc.w2[n][3] = 0.f;
@@ -1104,9 +1137,9 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
 #pragma unroll
     for (int n = 0; n < 3; ++n) acc.w3[n][0] = acc.w3[n][1] = acc.w3[n][2] = acc.w3[n][3] = 0.f;
     // Reverse steps k = H - 1 - t in processing order t.  After reading buffer
-    // b = k & 1, and once all four warps of this role have, warp v refills it with
+    // b = k & 1, and once all four warps of this role have, warp v prepares it with
     // step k - 2 of compute warp v's rows (the steps k1 - 1 and k1 - 2 of a segment
-    // are loaded by the compute warp itself, after its recompute).
+    // are left there by the compute warp's recompute).
     int t = 0;
     int last0 = -1, last1 = -1;  // processing step of the last load issued into buffer 0, 1
     for (int sg = nseg - 1; sg >= 0; --sg) {
@@ -1115,20 +1148,39 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
         const int b = k & 1;
         const uint32_t par = (uint32_t)((t >> 1) & 1);
         wait_on(&s.full[b], par);
-        // step k's cache entry has been copied into shared memory and used: drop
-        // its L2 lines without a write-back; the fence orders the discards before
-        // the bulk stores that reuse the entry in the next segment (issued by the
-        // compute warp after it has waited for this warp's arrivals)
-        cache_discard(cache_at(v, k - k0), lane);
-        fence_proxy_async_global();
+        if (k < k1 - 2) {
+          // step k's cache entry has been copied into shared memory and used: drop
+          // its L2 lines without a write-back; the fence orders the discards before
+          // the bulk stores that reuse the entry in the next segment (issued by the
+          // compute warp after it has waited for this warp's arrivals)
+          cache_discard(cache_at(v, k - k0), lane);
+          fence_proxy_async_global();
+        }
+        // step k - 2's state (its first sub-step state, or the checkpoint for rows
+        // without a drone) and reference, loaded during the dW work.  The segment
+        // rows were stored in the compute warps' recompute, before their arrivals on
+        // full[b] (release), which this warp has just waited for (acquire).
+        float x[17], r[3];
+        const bool ahead = k - 2 >= k0;
+        if (ahead) {
+          if (valid) load_row(a.seg + (size_t)(k - 2 - k0) * a.R * a.n * 20, i, x);
+          else load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
+          ref_at(a.p_ref, k - 2, a.n, ii, r);
+        }
         accumulate_dw<LO>(s, v, lane, acc, b);
         mbar_arrive(&s.empty[b]);
-        if (k - 2 >= k0) {
+        if (ahead) {
           wait_on(&s.empty[b], par);
           if (lane == 0) {
             fence_proxy_async_global();
-            cache_load(s, b, 16 * v, cache_at(v, k - 2 - k0), &s.ready[v][b]);
+            cache_load(s, b, r0, cache_at(v, k - 2 - k0), &s.ready[v][b]);
           }
+          if (lane < 16) put_obs(s.obs, row, x, r);
+          __syncwarp();
+          float h1[8][4];
+          mlp_layer1<LO>(s, r0, lane, h1);
+          store_c64(s.h1[b], r0, lane, h1);
+          mbar_arrive(&s.ready[v][b]);  // with the copied bytes, completes the phase
           if (b) last1 = t + 2;
           else last0 = t + 2;
         }
@@ -1143,11 +1195,6 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
     return;
   }
   // ---------------- compute warps
-  const int v = warp;
-  const int r0 = 16 * v, row = r0 + (lane & 15);
-  const int i = blockIdx.x * DPC + row;
-  const bool valid = i < a.n;
-  const int ii = valid ? i : a.n - 1;
   const float seed = valid ? (*a.dL) * a.inv_n : 0.f;  // padded rows contribute nothing
   float lam[17];
 #pragma unroll
@@ -1182,21 +1229,27 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       float rr2[3] = {0.f, 0.f, 0.f};
       if (k + 2 <= a.H) ref_at_pinned(a.p_ref, k + 2, a.n, ii, rr2);
       if (lane < 16) put_obs(s.obs, row, x, rr);
-      // this step's activations and actions, kept for the reverse sweep: staged in
-      // buffer sb, whose copy-out two steps ago must have read it, then copied out
-      const int sb = (k - k0) & 1;
-      if (k - k0 >= 2 && lane == 0) bulk_wait_read<1>();
+      // this step's h2 and actions, kept for the reverse sweep: staged in buffer
+      // b = k & 1, whose copy-out two steps ago must have read it, then copied out.
+      // The segment's last two steps stay in their buffers, with h1, for the first
+      // two reverse steps (the copy-out before them must have read everything).
+      const int b = k & 1;
+      const bool last2 = k >= k1 - 2;
+      if (k - k0 >= 2 && lane == 0) {
+        if (last2) bulk_wait_read<0>();
+        else bulk_wait_read<1>();
+      }
       __syncwarp();
       {
         float h1[8][4], h2[8][4];
-        mlp_forward<LO>(s, r0, lane, h1, h2, s.actb[sb]);
-        store_c64(s.h1[sb], r0, lane, h1);
-        store_c64(s.h2[sb], r0, lane, h2);
+        mlp_forward<LO>(s, r0, lane, h1, h2, s.actb[b]);
+        store_c64(s.h2[b], r0, lane, h2);
+        if (last2) store_c64(s.h1[b], r0, lane, h1);
       }
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) cache_store(s, sb, r0, cache_at(v, k - k0));
-      float act[4] = {s.actb[sb][row][0], s.actb[sb][row][1], s.actb[sb][row][2], s.actb[sb][row][3]};
+      if (lane == 0 && !last2) cache_store(s, b, r0, cache_at(v, k - k0));
+      float act[4] = {s.actb[b][row][0], s.actb[b][row][1], s.actb[b][row][2], s.actb[b][row][3]};
       __syncwarp();
       for (int j = 0; j < a.R; ++j) {
         if (j > 0 && valid && lane < 16)
@@ -1228,15 +1281,15 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
         cp_async16(&s.pre_a[k & 1][row], valid ? &a.seg_a[(size_t)(k - k0) * a.n + i]
                                                : &a.ckpt_a[(size_t)sg * a.n + ii]);
     };
-    // step k's activation tiles and actions come back from the cache into buffer
-    // k & 1 by bulk copies: steps k1 - 1 and k1 - 2 issued here once the copy-out
-    // has completed, the others by the weight-gradient warps
+    // the segment's cache entries are complete before the weight-gradient warps
+    // copy them back (they wait for this warp's arrivals on full[] first); steps
+    // k1 - 1 and k1 - 2 are in their buffers already
     if (lane == 0) {
       bulk_wait_all();
       fence_proxy_async_global();
-      cache_load(s, (k1 - 1) & 1, r0, cache_at(v, k1 - 1 - k0), &s.ready[v][(k1 - 1) & 1]);
-      if (k1 - 2 >= k0) cache_load(s, (k1 - 2) & 1, r0, cache_at(v, k1 - 2 - k0), &s.ready[v][(k1 - 2) & 1]);
     }
+    mbar_arrive(&s.ready[v][(k1 - 1) & 1]);
+    if (k1 - 2 >= k0) mbar_arrive(&s.ready[v][(k1 - 2) & 1]);
     // the reference at policy step k + 1, carried like xn (the recompute ends with
     // the one at k1)
     float rn[3] = {rr[0], rr[1], rr[2]};
