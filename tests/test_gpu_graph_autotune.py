@@ -51,6 +51,41 @@ def test_graph_replay_uneven_mixed():
     assert torch.equal(a.get_state(), b.get_state())
 
 
+def test_fused_uneven_launches_repeat_with_any_grid():
+    """Fused launches of an uneven batch take their tiles from a device counter that each
+    grid's last warp resets: chained launches at several block sizes and a graph replayed
+    several times all give the eager state, bit for bit."""
+    bw = W.batched_workload(22, [3, 130, 64, 1000, 7, 45, 300], [1, 0, 1, 0, 1, 0, 1], steps=100,
+                            K=25, hold=20)
+    x0 = torch.tensor(bw.x0, dtype=torch.float32, device="cuda")
+    cmd = torch.tensor(bw.cmd, dtype=torch.float32, device="cuda")
+
+    def build(tpb=None):
+        s = Sim.batched(bw.n_per_world, bw.model_of_world, bw.integrator, bw.dt,
+                        max_cmd_blocks=bw.cmd.shape[0])
+        s.set_params(bw.params, np.arange(bw.M))
+        if tpb:
+            s.set_block_size(tpb)
+        s.set_state(x0)
+        s.set_commands(cmd, bw.hold)
+        return s
+    ref = build()
+    ref.run(100, 25)
+    expect = ref.get_state().clone()
+    for tpb in (32, 96, 256):
+        s = build(tpb)
+        s.run(100, 25)
+        assert torch.equal(s.get_state(), expect), tpb
+        assert s.status() == 0
+    b = build()
+    g = b.capture_run(100, 25)
+    for _ in range(3):
+        b.set_state(x0)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(b.get_state(), expect)
+
+
 def test_autotuner_restores_state_and_caches(tmp_path, monkeypatch):
     monkeypatch.setenv("CRAZYFLOW_AUTOTUNE_CACHE", str(tmp_path / "tune.jsonl"))
     wl = W.attitude_swarm_rk4(M=4096, steps=100, K=100)
