@@ -290,16 +290,16 @@ __device__ __forceinline__ void put_obs(__nv_bfloat16 (*t)[DPC * S16], int row, 
   }
 }
 
-// tanh from its definition, tanh x = sign(x) (1 - 2 / (exp(2 |x|) + 1)), on the
-// hardware base-2 exponential and reciprocal approximations: absolute error about
-// 2e-7 (the activations then enter the tensor cores as hi + lo bf16 pairs, ~2^-16
-// relative); saturates to +-1 for large |x|.
+// tanh from its definition, tanh x = 1 - 2 / (exp(2 x) + 1), on the hardware
+// base-2 exponential and reciprocal approximations: absolute error about 2e-7 for
+// either sign (the activations then enter the tensor cores as hi + lo bf16 pairs,
+// ~2^-16 relative); saturates to +1 (the exponential overflows to infinity, the
+// reciprocal to 0) and to -1 (the exponential underflows to 0).
 __device__ __forceinline__ float tanh_fast(float x) {
   float e, r;
-  const float y = fabsf(x) * 2.88539008177792681f;  // 2 / ln 2
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x * 2.88539008177792681f));  // 2 / ln 2
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e + 1.f));
-  return copysignf(fmaf(-2.f, r, 1.f), x);
+  return fmaf(-2.f, r, 1.f);
 }
 
 // Two tanh values for one reciprocal: with p = exp(2 |a|) + 1 and q = exp(2 |b|) + 1,
