@@ -623,11 +623,13 @@ __device__ void store_dw(const DwAcc& acc, int v, int lane, float* __restrict__ 
 
 // Euler step of the first-principles model under the attitude interface
 // (first-order-lag rotors, no drag), a = the policy action.
+// The attitude error is taken from quaternions (attitude_command_q, attitude_error2_q:
+// the same e_R as the matrix form) and the thrust direction from q.
 __device__ __forceinline__ void policy_step(float* x, const float a[4], const DevParams& P, float dt) {
-  float Rd[9], Td, R[9], tx, ty, tz, Wc[4], d[17];
-  attitude_command(make_float4(a[0], a[1], a[2], a[3]), P, Rd, Td);
-  quat_rot(x[3], x[4], x[5], x[6], R);
-  attitude_torque(R, Rd, x[10], x[11], x[12], P, tx, ty, tz);
+  float qd[4], Td, ex, ey, ez, tx, ty, tz, Wc[4], d[17];
+  attitude_command_q(make_float4(a[0], a[1], a[2], a[3]), P, qd, Td);
+  attitude_error2_q(x, qd, ex, ey, ez);
+  attitude_torque_e(ex, ey, ez, x[10], x[11], x[12], P, tx, ty, tz);
   mixer(Td, tx, ty, tz, P, Wc);
   deriv_fp<MOTOR_LAG>(x, Wc, P, false, d);
   // element pairs on the packed FP32 instructions (same rounding as fmaf per lane)
@@ -651,22 +653,29 @@ __device__ __forceinline__ void policy_step(float* x, const float a[4], const De
 // caller), ga = dL/da through the controller.
 __device__ void policy_step_adjoint(const float* x, const float a[4], float* lam, float ga[4],
                                     const DevParams& P, float dt) {
-  // ---------------- forward recomputation
+  // ---------------- forward recomputation (as policy_step, with the intermediates
+  // of the quaternion attitude error kept)
   const float ac0 = clampf(a[0], -1.f, 1.f), ac1 = clampf(a[1], -1.f, 1.f);
   const float ac2 = clampf(a[2], -1.f, 1.f), ac3 = clampf(a[3], -1.f, 1.f);
-  float sr, cr, sp, cp, sy, cy;
-  __sincosf(ac0 * P.max_angle, &sr, &cr);
-  __sincosf(ac1 * P.max_angle, &sp, &cp);
-  __sincosf(ac2 * P.max_angle, &sy, &cy);
-  float Rd[9];
-  euler_rot(sr, cr, sp, cp, sy, cy, Rd);
+  float sr, cr, sp, cp, sy, cy;  // of the half angles
+  __sincosf(ac0 * P.half_max_angle, &sr, &cr);
+  __sincosf(ac1 * P.half_max_angle, &sp, &cp);
+  __sincosf(ac2 * P.half_max_angle, &sy, &cy);
+  const float cp2 = cp + cp, sp2 = sp + sp;
+  const float ka = cp2 * cy, kb = sp2 * sy, kc = sp2 * cy, kd = cp2 * sy;
+  // twice the desired quaternion (attitude_command_q)
+  const float dx = fmaf(sr, ka, -cr * kb), dy = fmaf(cr, kc, sr * kd);
+  const float dz = fmaf(cr, kd, -sr * kc), dw = fmaf(cr, ka, sr * kb);
   const float Td = fmaf(P.ts_mg, ac3, P.mg);
   const float qx = x[3], qy = x[4], qz = x[5], qw = x[6];
   const float wx = x[10], wy = x[11], wz = x[12];
-  float R[9];
-  quat_rot(qx, qy, qz, qw, R);
+  // (v, w) = qd2* (x) q, 2 e_R = w v (attitude_error2_q)
+  const float vx = fmaf(dw, qx, fmaf(-qw, dx, fmaf(-dy, qz, dz * qy)));
+  const float vy = fmaf(dw, qy, fmaf(-qw, dy, fmaf(-dz, qx, dx * qz)));
+  const float vz = fmaf(dw, qz, fmaf(-qw, dz, fmaf(-dx, qy, dy * qx)));
+  const float we = fmaf(dw, qw, fmaf(dx, qx, fmaf(dy, qy, dz * qz)));
   float tx, ty, tz;
-  attitude_torque(R, Rd, wx, wy, wz, P, tx, ty, tz);
+  attitude_torque_e(we * vx, we * vy, we * vz, wx, wy, wz, P, tx, ty, tz);
   const float A = 0.25f * Td, X = tx * P.mix_a, Y = ty * P.mix_a, Z = tz * P.mix_k;
   float f[4], Wc[4];
   f[0] = (A - X) - (Y + Z);
@@ -757,41 +766,32 @@ __device__ void policy_step_adjoint(const float* x, const float a[4], float* lam
   lam[10] += gwx;
   lam[11] += gwy;
   lam[12] += gwz;
-  // e = vee(M - M^T), M = Rd^T R:  gR = Rd G, gRd = R G^T with
-  // G = [[0, -gez, gey], [gez, 0, -gex], [-gey, gex, 0]]
-  float gR[9], gRd[9];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const float d0 = Rd[3 * k], d1 = Rd[3 * k + 1], d2 = Rd[3 * k + 2];
-    gR[3 * k + 0] = d1 * gez - d2 * gey;
-    gR[3 * k + 1] = d2 * gex - d0 * gez;
-    gR[3 * k + 2] = d0 * gey - d1 * gex;
-    const float e0 = R[3 * k], e1 = R[3 * k + 1], e2 = R[3 * k + 2];
-    gRd[3 * k + 0] = e2 * gey - e1 * gez;
-    gRd[3 * k + 1] = e0 * gez - e2 * gex;
-    gRd[3 * k + 2] = e1 * gex - e0 * gey;
-  }
-  // R(q) quadratic form
-  lam[3] += 2.f * (qx * (gR[0] - gR[4] - gR[8]) + qy * (gR[1] + gR[3]) + qz * (gR[2] + gR[6]) +
-                   qw * (gR[7] - gR[5]));
-  lam[4] += 2.f * (qy * (gR[4] - gR[0] - gR[8]) + qx * (gR[1] + gR[3]) + qw * (gR[2] - gR[6]) +
-                   qz * (gR[5] + gR[7]));
-  lam[5] += 2.f * (qz * (gR[8] - gR[0] - gR[4]) + qw * (gR[3] - gR[1]) + qx * (gR[2] + gR[6]) +
-                   qy * (gR[5] + gR[7]));
-  lam[6] += 2.f * (qw * (gR[0] + gR[4] + gR[8]) + qz * (gR[3] - gR[1]) + qy * (gR[2] - gR[6]) +
-                   qx * (gR[7] - gR[5]));
-  // Rd = Rz(y) Ry(p) Rx(r)
-  const float gphi = gRd[1] * Rd[2] - gRd[2] * Rd[1] + gRd[4] * Rd[5] - gRd[5] * Rd[4] +
-                     gRd[7] * Rd[8] - gRd[8] * Rd[7];
-  const float gth = -gRd[0] * cy * sp + gRd[1] * cy * cp * sr + gRd[2] * cy * cp * cr -
-                    gRd[3] * sy * sp + gRd[4] * sy * cp * sr + gRd[5] * sy * cp * cr -
-                    gRd[6] * cp - gRd[7] * sp * sr - gRd[8] * sp * cr;
-  const float gpsi = -gRd[0] * Rd[3] - gRd[1] * Rd[4] - gRd[2] * Rd[5] + gRd[3] * Rd[0] +
-                     gRd[4] * Rd[1] + gRd[5] * Rd[2];
+  // 2 e_R = w v with (v, w) = qd2* (x) q: gw = ge . v, gv = w ge
+  const float gw_ = fmaf(gex, vx, fmaf(gey, vy, gez * vz));
+  const float gvx = gex * we, gvy = gey * we, gvz = gez * we;
+  // through q (v and w are bilinear in qd2 and q)
+  lam[3] += fmaf(gvx, dw, fmaf(-gvy, dz, fmaf(gvz, dy, gw_ * dx)));
+  lam[4] += fmaf(gvx, dz, fmaf(gvy, dw, fmaf(-gvz, dx, gw_ * dy)));
+  lam[5] += fmaf(-gvx, dy, fmaf(gvy, dx, fmaf(gvz, dw, gw_ * dz)));
+  lam[6] += fmaf(-gvx, dx, fmaf(-gvy, dy, fmaf(-gvz, dz, gw_ * dw)));
+  // through qd2
+  const float gdx = fmaf(-gvx, qw, fmaf(gvy, qz, fmaf(-gvz, qy, gw_ * qx)));
+  const float gdy = fmaf(-gvx, qz, fmaf(-gvy, qw, fmaf(gvz, qx, gw_ * qy)));
+  const float gdz = fmaf(gvx, qy, fmaf(-gvy, qx, fmaf(-gvz, qw, gw_ * qz)));
+  const float gdw = fmaf(gvx, qx, fmaf(gvy, qy, fmaf(gvz, qz, gw_ * qw)));
+  // qd2 = 2 qz(yaw) (x) qy(pitch) (x) qx(roll) of the half angles hr, hp, hy:
+  // d qd2 / d hr = (dw, dz, -dy, -dx); with ka = 2 cp cy, kb = 2 sp sy, kc = 2 sp cy,
+  // kd = 2 cp sy, d/d hp maps (ka, kb, kc, kd) to (-kc, kd, ka, -kb) and d/d hy to
+  // (-kd, kc, -kb, ka)
+  const float gphi = fmaf(gdx, dw, fmaf(gdy, dz, fmaf(-gdz, dy, -gdw * dx)));
+  const float gth = fmaf(-gdx, fmaf(sr, kc, cr * kd), fmaf(gdy, fmaf(cr, ka, -sr * kb),
+                    fmaf(-gdz, fmaf(cr, kb, sr * ka), gdw * fmaf(sr, kd, -cr * kc))));
+  const float gpsi = fmaf(-gdx, fmaf(sr, kd, cr * kc), fmaf(gdy, fmaf(sr, ka, -cr * kb),
+                     fmaf(gdz, fmaf(cr, ka, sr * kb), gdw * fmaf(sr, kc, -cr * kd))));
   // clip(a, -1, 1) passes the gradient inside [-1, 1] (inclusive)
-  ga[0] = (a[0] >= -1.f && a[0] <= 1.f) ? gphi * P.max_angle : 0.f;
-  ga[1] = (a[1] >= -1.f && a[1] <= 1.f) ? gth * P.max_angle : 0.f;
-  ga[2] = (a[2] >= -1.f && a[2] <= 1.f) ? gpsi * P.max_angle : 0.f;
+  ga[0] = (a[0] >= -1.f && a[0] <= 1.f) ? gphi * P.half_max_angle : 0.f;
+  ga[1] = (a[1] >= -1.f && a[1] <= 1.f) ? gth * P.half_max_angle : 0.f;
+  ga[2] = (a[2] >= -1.f && a[2] <= 1.f) ? gpsi * P.half_max_angle : 0.f;
   ga[3] = (a[3] >= -1.f && a[3] <= 1.f) ? gTd * P.ts_mg : 0.f;
 }
 
