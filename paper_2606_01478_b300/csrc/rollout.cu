@@ -332,15 +332,16 @@ __device__ __forceinline__ void tanh2(float& a, float& b) {
   }
 }
 
-// Layer 1 of the MLP for the warp's 16 drones (rows r0..r0+15) from the obs tile
-// pair: h1 (fp32 accumulator fragments, after tanh).
+// Layer 1 of the MLP for the warp's 16 drones (rows r0..r0+15) from an obs tile
+// pair (hi, lo): h1 (fp32 accumulator fragments, after tanh).
 template <bool LO>
-__device__ __forceinline__ void mlp_layer1(Smem& s, int r0, int lane, float h1[8][4]) {
+__device__ __forceinline__ void mlp_layer1(Smem& s, const __nv_bfloat16 (*obs)[DPC * S16], int r0,
+                                           int lane, float h1[8][4]) {
   const int tq = lane & 3;
   const int arow = r0 + (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
   uint32_t oh[4], ol[4];
-  ldsm_x4(oh, &s.obs[0][arow * S16 + acol]);
-  ldsm_x4(ol, &s.obs[1][arow * S16 + acol]);
+  ldsm_x4(oh, &obs[0][arow * S16 + acol]);
+  ldsm_x4(ol, &obs[1][arow * S16 + acol]);
   // z1[d][i] = sum_c obs[d][c] W1[i][c] + b1[i]
   const int brow = (lane & 7) + (lane >> 4) * 8, bcol = ((lane >> 3) & 1) * 8;
 #pragma unroll
@@ -372,7 +373,7 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
                             float (*act)[4]) {
   const int g = lane >> 2, tq = lane & 3;
   const int bcol = ((lane >> 3) & 1) * 8, brow = (lane & 7) + (lane >> 4) * 8;
-  mlp_layer1<LO>(s, r0, lane, h1);
+  mlp_layer1<LO>(s, s.obs, r0, lane, h1);
   // layer 2: z2[d][j] = sum_i h1[d][i] W2[j][i] + b2[j]
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
@@ -1175,10 +1176,11 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
             fence_proxy_async_global();
             cache_load(s, b, r0, cache_at(v, k - 2 - k0), &s.ready[v][b]);
           }
-          if (lane < 16) put_obs(s.obs, row, x, r);
+          // step k - 2's observation rows, the dW1 operand of that step as well
+          if (lane < 16) put_obs(s.obsr[b], row, x, r);
           __syncwarp();
           float h1[8][4];
-          mlp_layer1<LO>(s, r0, lane, h1);
+          mlp_layer1<LO>(s, s.obsr[b], r0, lane, h1);
           store_c64(s.h1[b], r0, lane, h1);
           mbar_arrive(&s.ready[v][b]);  // with the copied bytes, completes the phase
           if (b) last1 = t + 2;
@@ -1246,6 +1248,7 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
         store_c64(s.h2[b], r0, lane, h2);
         if (last2) store_c64(s.h1[b], r0, lane, h1);
       }
+      if (last2 && lane < 16) put_obs(s.obsr[b], row, x, rr);
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0 && !last2) cache_store(s, b, r0, cache_at(v, k - k0));
@@ -1316,8 +1319,8 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       }
       if (k > k0 && lane < 16) prefetch_step(k - 1);
       cp_async_commit();
-      if (lane < 16) put_obs(s.obsr[b], row, x, r);
-      __syncwarp();
+      // this step's observation rows (the dW1 operand) are in obsr[b] already: written
+      // with its activations by the weight-gradient warp, or by the recompute
       const float act[4] = {s.actb[b][row][0], s.actb[b][row][1], s.actb[b][row][2], s.actb[b][row][3]};
       // loss term at policy step k + 1 (state after the last sub-step)
       step_loss_state_adjoint<OBJ>(xn, rn, seed, a, lam);
