@@ -51,7 +51,7 @@ struct __align__(16) Smem {
   __nv_bfloat16 W3[16 * S64];  // [o][j]  (o < 4 used)
   __nv_bfloat16 obs[2][DPC * S16];  // hi, lo; column 13 = 1 (bias column)
   // activation tiles [buffer][hi, lo] (column 64 = 1): the adjoint's reverse sweep
-  // reads step k from buffer k & 1 while step k - 1's copy arrives in the other
+  // reads step k from buffer k & 1 while step k - 1 is prepared in the other
   __nv_bfloat16 h1[2][2][DPC * S64];
   __nv_bfloat16 h2[2][2][DPC * S64];
   // adjoint tiles [step parity][hi, lo]: written by the compute warps at step k,
@@ -68,11 +68,12 @@ struct __align__(16) Smem {
   float pre_x[2][DPC][20];
   float pre_r[2][DPC][4];
   float4 pre_a[2][DPC];
-  float actb[2][DPC][4];  // cached actions of the reverse sweep [buffer]
+  float actb[2][DPC][4];  // actions of the reverse sweep [buffer]
   // reverse-sweep hand-off per step parity: full (4 compute-warp arrivals: the
   // step's tiles are written), empty (4 weight-gradient-warp arrivals: read);
-  // ready[v][b]: the bulk copy of compute warp v's cached tiles and actions into
-  // buffer b has landed (transaction-count completion)
+  // ready[v][b]: buffer b holds step k's activations, actions and observation rows
+  // for warp v's rows (32 arrivals of the warp that prepared it, and the bytes of the
+  // bulk copy of its cached h2 and actions where there was one)
   unsigned long long full[2], empty[2];
   unsigned long long ready[4][2];
 };
