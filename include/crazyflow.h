@@ -209,8 +209,10 @@ int sim_set_block_size(sim_h h, int threads_per_block);
  * without timing.  The key names the GPU (name, compute capability, SM count),
  * the operation, M, N (or -1 for uneven batches), Ntot, the number of worlds of
  * each model and a hash of the per-world drone counts and models, the
- * integrator, the control interface, the rotor model, per-world parameters,
- * dt, and n_steps (step) or S, H and the obstacle count (sample).
+ * integrator, the control interface, the rotor model (general, lag, or lag with
+ * Jx = Jy in every parameter set: each has kernel variants of its own),
+ * per-world parameters, dt, and n_steps (step) or S, H and the obstacle count
+ * (sample).
  * Step trials restore the state planes (saved in the handle's staging region)
  * and the command schedule around every run and at the end: the handle's
  * state is the same after the call.  Sampling trials write `cost`.  The call

@@ -96,7 +96,10 @@ std::string make_key(const sim_s* h, const sim_tune_request* r) {
                    (long long)h->M, h->batched ? -1ll : (long long)h->N, (long long)h->ntot,
                    n_model[0], n_model[1], n_model[2], (unsigned long long)mix,
                    name_of_integrator(h->integrator), name_of_ctrl(h->ctrl),
-                   h->general_motor ? "general" : "lag", h->per_set ? 1 : 0, (double)h->dt);
+                   h->general_motor ? "general"
+                   : (h->p0.flags & cf::PF_ASYM_XY) ? "lag"
+                                                    : "lag_jxy",  // the Jx = Jy kernel variants
+                   h->per_set ? 1 : 0, (double)h->dt);
   if (r->op == SIM_TUNE_STEP)
     snprintf(buf + k, sizeof(buf) - k, "|steps=%lld", (long long)r->n_steps);
   else

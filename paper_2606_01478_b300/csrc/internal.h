@@ -12,9 +12,10 @@ cudaError_t launch_step(const StepArgs& a, const DevParams& P, int model, int in
                         bool general_motor, bool per_set, int tpb, cudaStream_t st);
 
 // Uneven / mixed batches (step.cu): tiles [n_tiles] of (first drone, count <= 32,
-// world, model), one warp per tile, persistent grid.
+// world, model), one warp per tile, persistent grid.  sym: Jx = Jy in every
+// parameter set.
 cudaError_t launch_step_batched(const StepArgs& a, const int4* tiles, int n_tiles, int integrator,
-                                int ctrl, bool general_motor, int tpb, cudaStream_t st);
+                                int ctrl, bool general_motor, bool sym, int tpb, cudaStream_t st);
 
 // Differentiable policy rollout (rollout.cu).  Workspace: checkpoints
 // [ceil(H/C)][n][20], segment sub-step states [C R][n][20], per-drone loss [n], per-CTA dW

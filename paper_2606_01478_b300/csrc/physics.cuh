@@ -146,7 +146,7 @@ __device__ __forceinline__ void deriv_fp(const float* x, const float Wc[4], cons
 // doubled, d[3..6] = q (x) [w, 0] = 2 q' (the integrator folds the 1/2 into its
 // coefficients).  Constants kf/m, kfa/J, km/J are folded (DevParams).
 // SYM_XY: Jx = Jy, where the yaw rate's gyroscopic term (Jx - Jy) wx wy / Jz is
-// zero and is left out.
+// zero and is left out, and the roll and pitch terms share their factor.
 template <bool SYM_XY = false>
 __device__ __forceinline__ void deriv_fp_rate(const float* x, const float u[4], const DevParams& P,
                                               float* d, const float* Rc = nullptr) {
@@ -184,10 +184,17 @@ __device__ __forceinline__ void deriv_fp_rate(const float* x, const float u[4], 
   // w' = J^-1 tau - J^-1 (w x J w), rotor torques as in deriv_fp
   // roll (s2 + s3) - (s0 + s1), pitch (s1 + s2) - (s0 + s3) = e10 - e32,
   // yaw (s1 + s3) - (s0 + s2) = e10 + e32
-  d[10] = fmaf(P.kfaJx, a23 - a01, P.cJx * wy * wz);
-  d[11] = fmaf(P.kfaJy, e10 - e32, P.cJy * wz * wx);
-  if constexpr (SYM_XY) d[12] = P.kmJz * (e10 + e32);
-  else d[12] = fmaf(P.kmJz, e10 + e32, P.cJz * wx * wy);
+  if constexpr (SYM_XY) {
+    // Jx = Jy: cJy = -cJx exactly (the same quotient negated), cJz = 0
+    const float t = P.cJx * wz;
+    d[10] = fmaf(P.kfaJx, a23 - a01, t * wy);
+    d[11] = fmaf(P.kfaJy, e10 - e32, -t * wx);
+    d[12] = P.kmJz * (e10 + e32);
+  } else {
+    d[10] = fmaf(P.kfaJx, a23 - a01, P.cJx * wy * wz);
+    d[11] = fmaf(P.kfaJy, e10 - e32, P.cJy * wz * wx);
+    d[12] = fmaf(P.kmJz, e10 + e32, P.cJz * wx * wy);
+  }
 #pragma unroll
   for (int r = 0; r < 4; ++r) d[13 + r] = fmaf(P.ncv, x[13 + r], u[r]);
 }

@@ -498,7 +498,8 @@ int sim_step(sim_h h, int K, void* stream) {
   cudaError_t e =
       h->batched
           ? cf::launch_step_batched(a, h->tiles_dev, (int)h->tiles.size(), h->integrator, h->ctrl,
-                                    h->general_motor, h->tpb, (cudaStream_t)stream)
+                                    h->general_motor, (h->p0.flags & cf::PF_ASYM_XY) == 0, h->tpb,
+                                    (cudaStream_t)stream)
           : cf::launch_step(a, h->p0, h->model, h->integrator, h->ctrl, h->general_motor,
                             h->per_set, h->tpb, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "step launch");

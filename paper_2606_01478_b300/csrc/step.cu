@@ -57,8 +57,9 @@ static cudaError_t launch_chained(void (*kernel)(KArgs...), int grid, int tpb, c
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-// SINGLE: the launch is known to take one step (a.K == 1).
-template <int MODEL, int INTEG, int CTRL, int MOTOR, bool SINGLE = false>
+// SINGLE: the launch is known to take one step (a.K == 1).  SYM: Jx = Jy in every
+// parameter set (first-principles lag-rotor steps drop the zero gyroscopic term).
+template <int MODEL, int INTEG, int CTRL, int MOTOR, bool SINGLE = false, bool SYM = false>
 __device__ __forceinline__ void run_drone(const StepArgs& a, int i, const DevParams& P) {
   constexpr int NPL = (MODEL == SIM_FIRST_PRINCIPLES) ? 5 : 4;
   const int n = a.n;
@@ -80,7 +81,7 @@ __device__ __forceinline__ void run_drone(const StepArgs& a, int i, const DevPar
   decode_command<MODEL, CTRL>(a.cmd[(size_t)blk * n + i], P, h);
   if (SINGLE || a.K == 1) {
     // a single step never reaches the next command block: no look-ahead load
-    one_step<MODEL, INTEG, CTRL, MOTOR>(s, h, P, drag, a.dt);
+    one_step<MODEL, INTEG, CTRL, MOTOR, SYM>(s, h, P, drag, a.dt);
   } else {
     // the next block's command, prefetched when this launch reaches it
     float4 next = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -95,7 +96,7 @@ __device__ __forceinline__ void run_drone(const StepArgs& a, int i, const DevPar
         if (a.K - k > left) next = a.cmd[(size_t)min(blk + 1, last) * n + i];
       }
       const int seg = min(left, a.K - k);
-      for (int j = 0; j < seg; ++j) one_step<MODEL, INTEG, CTRL, MOTOR>(s, h, P, drag, a.dt);
+      for (int j = 0; j < seg; ++j) one_step<MODEL, INTEG, CTRL, MOTOR, SYM>(s, h, P, drag, a.dt);
       k += seg;
       left -= seg;
     }
@@ -109,16 +110,16 @@ __device__ __forceinline__ void run_drone(const StepArgs& a, int i, const DevPar
     a.planes[(size_t)j * n + i] = make_float4(s[4 * j], s[4 * j + 1], s[4 * j + 2], s[4 * j + 3]);
 }
 
-template <int MODEL, int INTEG, int CTRL, int MOTOR, bool PERSET>
+template <int MODEL, int INTEG, int CTRL, int MOTOR, bool PERSET, bool SYM = false>
 __global__ void __launch_bounds__(256) step_kernel(StepArgs a, DevParams P0) {
   chain_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < a.n) {
     if constexpr (PERSET) {
       const DevParams P = a.params[a.set_of_world[i / a.N]];
-      run_drone<MODEL, INTEG, CTRL, MOTOR>(a, i, P);
+      run_drone<MODEL, INTEG, CTRL, MOTOR, false, SYM>(a, i, P);
     } else {
-      run_drone<MODEL, INTEG, CTRL, MOTOR>(a, i, P0);
+      run_drone<MODEL, INTEG, CTRL, MOTOR, false, SYM>(a, i, P0);
     }
   }
   chain_release();
@@ -128,12 +129,12 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a, DevParams P0) {
 // w + 2W, ... (W = warps in the grid).  A tile is up to 32 consecutive drones of
 // one world (x = first drone, y = count, z = world, w = model), so the branch
 // on the model is uniform across the warp and parameters are a broadcast load.
-template <int INTEG, int CTRL, int MOTOR, bool SINGLE>
+template <int INTEG, int CTRL, int MOTOR, bool SINGLE, bool SYM>
 __device__ __forceinline__ void run_tile(const StepArgs& a, const int4& d, int lane) {
   if (lane < d.y) {
     const DevParams P = a.params[a.set_of_world[d.z]];
     if (d.w == SIM_FIRST_PRINCIPLES) {
-      run_drone<SIM_FIRST_PRINCIPLES, INTEG, CTRL, MOTOR, SINGLE>(a, d.x + lane, P);
+      run_drone<SIM_FIRST_PRINCIPLES, INTEG, CTRL, MOTOR, SINGLE, SYM>(a, d.x + lane, P);
     } else if (d.w == SIM_ABSTRACTED) {
       run_drone<SIM_ABSTRACTED, INTEG, SIM_CTRL_ATTITUDE, MOTOR, SINGLE>(a, d.x + lane, P);
     } else {
@@ -150,13 +151,13 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, const int4& d, int l
 // first-principles tiles running alone at the end.  Which warp steps a tile does
 // not change its result.  The grid's last warp resets the counters for the next
 // launch (a chained launch waits for this grid's completion before its first access).
-template <int INTEG, int CTRL, int MOTOR, bool SINGLE>
+template <int INTEG, int CTRL, int MOTOR, bool SINGLE, bool SYM>
 __device__ __forceinline__ void run_tiles(const StepArgs& a, const int4* __restrict__ tiles, int n_tiles) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   if constexpr (SINGLE) {
-    for (int t = warp; t < n_tiles; t += nwarps) run_tile<INTEG, CTRL, MOTOR, SINGLE>(a, tiles[t], lane);
+    for (int t = warp; t < n_tiles; t += nwarps) run_tile<INTEG, CTRL, MOTOR, SINGLE, SYM>(a, tiles[t], lane);
   } else {
     const unsigned FULL = 0xffffffffu;
     unsigned raw = lane == 0 ? atomicAdd(&a.tile_ctr[0], 1u) : 0u;
@@ -164,7 +165,7 @@ __device__ __forceinline__ void run_tiles(const StepArgs& a, const int4* __restr
     while (cur < n_tiles) {
       // lane 0 asks for the next tile; its index is read after this tile's steps
       raw = lane == 0 ? atomicAdd(&a.tile_ctr[0], 1u) : 0u;
-      run_tile<INTEG, CTRL, MOTOR, SINGLE>(a, tiles[cur], lane);
+      run_tile<INTEG, CTRL, MOTOR, SINGLE, SYM>(a, tiles[cur], lane);
       cur = (int)__shfl_sync(FULL, raw, 0);
     }
     if (lane == 0 && atomicAdd(&a.tile_ctr[1], 1u) == (unsigned)nwarps - 1u) {
@@ -174,30 +175,30 @@ __device__ __forceinline__ void run_tiles(const StepArgs& a, const int4* __restr
   }
 }
 
-template <int INTEG, int CTRL, int MOTOR>
+template <int INTEG, int CTRL, int MOTOR, bool SYM>
 __global__ void __launch_bounds__(256) step_batched_kernel(StepArgs a, const int4* __restrict__ tiles,
                                                            int n_tiles) {
   chain_wait();
   chain_release();
-  run_tiles<INTEG, CTRL, MOTOR, false>(a, tiles, n_tiles);
+  run_tiles<INTEG, CTRL, MOTOR, false, SYM>(a, tiles, n_tiles);
 }
 
 // One step per launch (HBM bound): compiled for four 256-thread CTAs per SM with
 // lag rotors under Euler (three with the general rotor model, two under RK4, whose
 // registers would spill beyond that) so that more state loads are in flight.
-template <int INTEG, int CTRL, int MOTOR>
+template <int INTEG, int CTRL, int MOTOR, bool SYM>
 __global__ void __launch_bounds__(256, INTEG == SIM_EULER ? (MOTOR == MOTOR_LAG ? 4 : 3) : 2)
     step_batched_single_kernel(StepArgs a, const int4* __restrict__ tiles, int n_tiles) {
   chain_wait();
   chain_release();
-  run_tiles<INTEG, CTRL, MOTOR, true>(a, tiles, n_tiles);
+  run_tiles<INTEG, CTRL, MOTOR, true, SYM>(a, tiles, n_tiles);
 }
 
-template <int INTEG, int CTRL, int MOTOR, bool SINGLE>
+template <int INTEG, int CTRL, int MOTOR, bool SINGLE, bool SYM = false>
 static cudaError_t launch_b(const StepArgs& a, const int4* tiles, int n_tiles, int tpb,
                             cudaStream_t st) {
-  auto kernel = SINGLE ? step_batched_single_kernel<INTEG, CTRL, MOTOR>
-                       : step_batched_kernel<INTEG, CTRL, MOTOR>;
+  auto kernel = SINGLE ? step_batched_single_kernel<INTEG, CTRL, MOTOR, SYM>
+                       : step_batched_kernel<INTEG, CTRL, MOTOR, SYM>;
   // occupancy per (device, block size), queried once per kernel variant
   static int cached[16][9] = {};
   int dev = 0;
@@ -219,14 +220,17 @@ static cudaError_t launch_b(const StepArgs& a, const int4* tiles, int n_tiles, i
 }
 
 cudaError_t launch_step_batched(const StepArgs& a, const int4* tiles, int n_tiles, int integrator,
-                                int ctrl, bool general_motor, int tpb, cudaStream_t st) {
+                                int ctrl, bool general_motor, bool sym, int tpb, cudaStream_t st) {
+#define CF_L(I, C, S)                                                                       \
+  (sym ? launch_b<I, C, MOTOR_LAG, S, true>(a, tiles, n_tiles, tpb, st)                      \
+       : launch_b<I, C, MOTOR_LAG, S, false>(a, tiles, n_tiles, tpb, st))
 #define CF_B(I, C)                                                                          \
   {                                                                                         \
     if (a.K == 1)                                                                           \
       return general_motor ? launch_b<I, C, MOTOR_GENERAL, true>(a, tiles, n_tiles, tpb, st) \
-                           : launch_b<I, C, MOTOR_LAG, true>(a, tiles, n_tiles, tpb, st);    \
+                           : CF_L(I, C, true);                                              \
     return general_motor ? launch_b<I, C, MOTOR_GENERAL, false>(a, tiles, n_tiles, tpb, st)  \
-                         : launch_b<I, C, MOTOR_LAG, false>(a, tiles, n_tiles, tpb, st);     \
+                         : CF_L(I, C, false);                                               \
   }
   if (integrator == SIM_RK4) {
     if (ctrl == SIM_CTRL_ROTOR_SPEED) CF_B(SIM_RK4, SIM_CTRL_ROTOR_SPEED);
@@ -239,12 +243,13 @@ cudaError_t launch_step_batched(const StepArgs& a, const int4* tiles, int n_tile
   if (ctrl == SIM_CTRL_TORQUE) CF_B(SIM_EULER, SIM_CTRL_TORQUE);
   CF_B(SIM_EULER, SIM_CTRL_ATTITUDE);
 #undef CF_B
+#undef CF_L
 }
 
-template <int MODEL, int INTEG, int CTRL, int MOTOR, bool PERSET>
+template <int MODEL, int INTEG, int CTRL, int MOTOR, bool PERSET, bool SYM = false>
 static cudaError_t launch_t(const StepArgs& a, const DevParams& P, int tpb, cudaStream_t st) {
   const int grid = (a.n + tpb - 1) / tpb;
-  return launch_chained(step_kernel<MODEL, INTEG, CTRL, MOTOR, PERSET>, grid, tpb, st, a, P);
+  return launch_chained(step_kernel<MODEL, INTEG, CTRL, MOTOR, PERSET, SYM>, grid, tpb, st, a, P);
 }
 
 template <int MODEL, int INTEG, int CTRL>
@@ -253,6 +258,13 @@ static cudaError_t launch_m(const StepArgs& a, const DevParams& P, bool gm, bool
   if (gm) {
     return perset ? launch_t<MODEL, INTEG, CTRL, MOTOR_GENERAL, true>(a, P, tpb, st)
                   : launch_t<MODEL, INTEG, CTRL, MOTOR_GENERAL, false>(a, P, tpb, st);
+  }
+  // first-principles lag-rotor steps come in two forms: Jx = Jy in every set (the
+  // union of the sets' flags lacks PF_ASYM_XY) or not
+  if constexpr (MODEL == SIM_FIRST_PRINCIPLES) {
+    if ((P.flags & PF_ASYM_XY) == 0)
+      return perset ? launch_t<MODEL, INTEG, CTRL, MOTOR_LAG, true, true>(a, P, tpb, st)
+                    : launch_t<MODEL, INTEG, CTRL, MOTOR_LAG, false, true>(a, P, tpb, st);
   }
   return perset ? launch_t<MODEL, INTEG, CTRL, MOTOR_LAG, true>(a, P, tpb, st)
                 : launch_t<MODEL, INTEG, CTRL, MOTOR_LAG, false>(a, P, tpb, st);
