@@ -72,6 +72,36 @@ def test_first_principles_all_controls(integrator, ctrl):
 
 
 @pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
+@pytest.mark.parametrize("batched", [False, True], ids=["uniform", "batched"])
+def test_asymmetric_inertia_lag_rotors(integrator, batched):
+    """Jx != Jy on the lag rotor model: the kernels keep the yaw rate's gyroscopic
+    term (their Jx = Jy variants leave it out); body rates up to 8 rad/s make the
+    term count.  Batched: two parameter sets, only one of them asymmetric, which
+    must select the asymmetric variant for every world."""
+    wl = W.attitude_swarm_rk4(M=300, steps=150, K=50)
+    wl.integrator = integrator
+    rng = np.random.default_rng(9)
+    wl.x0[:, 10:13] = rng.uniform(-8.0, 8.0, (wl.M, 3))
+    asym = W.crazyflie_params(Jx=1.2e-5, Jy=1.8e-5)
+    if batched:
+        wl.params = [W.crazyflie_params(), asym]
+        wl.param_set_of_world = (np.arange(wl.M) % 2).astype(np.int32)
+        sim = Sim.batched(np.ones(wl.M, np.int64), np.zeros(wl.M, np.int32), integrator, wl.dt,
+                          ctrl=wl.ctrl, max_cmd_blocks=wl.cmd.shape[0])
+        sim.set_params(wl.params, wl.param_set_of_world)
+        sim.set_state(torch.tensor(wl.x0, dtype=torch.float32, device="cuda"))
+        sim.set_commands(torch.tensor(wl.cmd, dtype=torch.float32, device="cuda"), wl.hold)
+        sim.run(wl.steps, wl.K)
+        gpu = sim.get_state().cpu().numpy()
+        assert sim.status() == 0
+    else:
+        wl.params = [asym]
+        gpu, _ = _run_gpu(wl)
+    ref = ph.rollout_workload(wl).numpy()
+    assert_parity(gpu, ref, _models_of(wl))
+
+
+@pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
 def test_general_motor_and_drag(integrator):
     """Asymmetric rotor coefficients with quadratic terms (Eq. 6 general form)
     and non-zero body drag, per-world parameter sets."""
