@@ -432,10 +432,12 @@ int sim_render_depth(sim_h h, const sim_camera* cam, const float* spheres, int n
  *         W1[64][13] b1[64] W2[64][64] b2[64] W3[4][64] b3[4]
  *   p_ref [H+1][Ntot][3] float          reference positions r_k (at policy steps)
  *   ws    rollout workspace of sim_rollout_workspace_bytes(h, H, C) bytes:
- *         checkpoints every C steps, segment states, per-drone losses, dW partials
- *         (and the previous actions under the tracking reward: the size depends
- *         on the objective and the action repeat set on the handle; segments
- *         hold C R sub-step states)
+ *         checkpoints every C steps, per-drone losses, dW partials and two
+ *         segment buffers (the recomputed states and activation cache of the
+ *         segment being swept and of the one recomputed beside it), and the
+ *         previous actions under the tracking reward: the size depends on the
+ *         objective and the action repeat set on the handle; a segment buffer
+ *         holds C R + 1 sub-step states
  *   loss  [1] float; dL [1] float (upstream gradient, read on the device);
  *   dW    [SIM_POLICY_NPARAMS] float = dL * dL/dw (in the packed order of w)
  *   dx0   [Ntot][SIM_STATE_DIM] float = dL * dL/dx0 (slots 17..19 = 0)

@@ -40,16 +40,12 @@ constexpr int OFF_W1 = 0, OFF_B1 = 832, OFF_W2 = 896, OFF_B2 = 4992, OFF_W3 = 50
               OFF_B3 = 5312, NPOL = 5316, NPOL_PAD = 5376;
 constexpr int TPB = 128, DPC = 64;  // threads and drones per CTA
 constexpr int S16 = 24, S64 = 72;   // padded smem row strides (bf16 elements)
-// One warp's cached activations of one step, in 16-byte chunks: h2 hi, h2 lo
-// (16 rows x S64 bf16 = 144 chunks each), then 16 action rows.  h1 is not kept:
-// the reverse sweep recomputes it from the state (one layer).
-constexpr int TILE_CHUNKS = 16 * S64 * 2 / 16, CACHE_CHUNKS = 2 * TILE_CHUNKS + 16;
 
 struct __align__(16) Smem {
   __nv_bfloat16 W1[64 * S16];  // [i][c]  (c < 13 used)
   __nv_bfloat16 W2[64 * S64];  // [j][i]
   __nv_bfloat16 W3[16 * S64];  // [o][j]  (o < 4 used)
-  __nv_bfloat16 obs[2][DPC * S16];  // hi, lo; column 13 = 1 (bias column)
+  __nv_bfloat16 obs[2][DPC * S16];  // hi, lo; column 13 = 1 (bias column); the adjoint's recompute
   // activation tiles [buffer][hi, lo] (column 64 = 1): the adjoint's reverse sweep
   // reads step k from buffer k & 1 while step k - 1 is prepared in the other
   __nv_bfloat16 h1[2][2][DPC * S64];
@@ -61,37 +57,44 @@ struct __align__(16) Smem {
   __nv_bfloat16 dz3[2][2][DPC * S16];
   __nv_bfloat16 obsr[2][2][DPC * S16];  // the reverse sweep's observation tiles (dW1 operand)
   float b1[64], b2[64], b3[8];
-  float act[DPC][4];
+  float act[DPC][4];  // the actions of the forward rollout and of the adjoint's recompute
+  // the adjoint's recompute: one h2 tile per warp, hi then lo, staged for the bulk
+  // stores into the activation cache (column 64 = 1, the bias column of the tiles)
+  __nv_bfloat16 stage[4][16 * S64];
   float dobs[DPC][16];
-  // adjoint kernel: double-buffered prefetch of the next step's state row,
-  // reference position and previous action (cp.async)
+  // adjoint kernel: double-buffered prefetch of the next step's state row, its
+  // step record (StepRecord: five float4) and previous action (cp.async)
   float pre_x[2][DPC][20];
-  float pre_r[2][DPC][4];
+  float pre_q[2][DPC][20];
   float4 pre_a[2][DPC];
   float actb[2][DPC][4];  // actions of the reverse sweep [buffer]
   // reverse-sweep hand-off per step parity: full (4 compute-warp arrivals: the
   // step's tiles are written), empty (4 weight-gradient-warp arrivals: read);
   // ready[v][b]: buffer b holds step k's activations, actions and observation rows
-  // for warp v's rows (32 arrivals of the warp that prepared it, and the bytes of the
-  // bulk copy of its cached h2 and actions where there was one)
+  // for warp v's rows (32 arrivals of the warp that prepared it); per segment
+  // parity: seg_done (4 recompute-warp arrivals: the segment is written), seg_free
+  // (4 weight-gradient-warp arrivals: the segment has been swept)
   unsigned long long full[2], empty[2];
   unsigned long long ready[4][2];
+  unsigned long long seg_done[2], seg_free[2];
 };
+static_assert(sizeof(Smem) <= 227 * 1024, "one CTA per SM within the opt-in shared-memory limit");
 
 struct RolloutArgs {
   const float* x0;        // [n][20]
   const uint16_t* w;      // [NPOL] bf16 bits, packed W1 b1 W2 b2 W3 b3
   const float* p_ref;     // [H + 1][n][3]
   float* ckpt;            // [n_ckpt][n][20]
-  float* seg;             // [C R][n][20]
+  float* seg;             // [2][C R + 1][n][20] recomputed segment states by segment parity
+  float* seg_q;           // [2][C R][n][FQ_FLOATS] their step records (StepRecord)
   float* loss_w;          // [n] per-drone loss
   float* part;            // [n_cta][NPOL_PAD] dW partials
   float* dx0;             // [n][20]
-  uint4* hcache;          // [C][n_warps][CACHE_CHUNKS] activation tiles + actions per step
+  uint4* hcache;          // [2][C][n_warps][CACHE_CHUNKS] h2 and actions per step, by segment parity
   const float* dL;        // device scalar: upstream gradient of the loss
   uint32_t* status;       // device status word or null (SIM_FLAG_TIMEOUT when a bounded wait gave up)
   float4* ckpt_a;         // [n_ckpt][n] previous action at each checkpoint (reward objective)
-  float4* seg_a;          // [C][n] previous action of each segment step (reward objective)
+  float4* seg_a;          // [2][C][n] previous action of each segment step (reward objective)
   int n, H, C, R;
   float dt, w_act, inv_n;
   float w_theta, w_a[4], w_da[4];  // tracking-reward weights
@@ -108,9 +111,6 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 // issuing thread's cp_async_wait_all.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
@@ -258,6 +258,7 @@ __device__ void load_weights(Smem& s, const uint16_t* __restrict__ w) {
         s.dz2[b][1][r * S64 + c] = z;
       }
     }
+    for (int c = 64; c < S64; ++c) s.stage[r >> 4][(r & 15) * S64 + c] = c == 64 ? one : z;
     for (int c = 0; c < S16; ++c) {
       s.obs[0][r * S16 + c] = z;
       s.obs[1][r * S16 + c] = z;
@@ -345,21 +346,24 @@ __device__ __forceinline__ void mlp_layer1(Smem& s, const __nv_bfloat16 (*obs)[D
   ldsm_x4(ol, &obs[1][arow * S16 + acol]);
   // z1[d][i] = sum_c obs[d][c] W1[i][c] + b1[i]
   const int brow = (lane & 7) + (lane >> 4) * 8, bcol = ((lane >> 3) & 1) * 8;
+  // the hi products of all eight n-tiles, then the lo ones: consecutive MMAs
+  // accumulate into different tiles (each tile's order is hi, lo either way)
+  uint32_t b[4][4];
 #pragma unroll
-  for (int n = 0; n < 8; n += 2) {
-    uint32_t b[4];
-    ldsm_x4(b, &s.W1[(8 * n + brow) * S16 + bcol]);
+  for (int n = 0; n < 8; n += 2) ldsm_x4(b[n >> 1], &s.W1[(8 * n + brow) * S16 + bcol]);
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const float b0 = s.b1[8 * (n + u) + 2 * tq], b1v = s.b1[8 * (n + u) + 2 * tq + 1];
-      float* c = h1[n + u];
-      c[0] = b0;
-      c[1] = b1v;
-      c[2] = b0;
-      c[3] = b1v;
-      mma(c, oh, b[2 * u], b[2 * u + 1]);
-      if constexpr (LO) mma(c, ol, b[2 * u], b[2 * u + 1]);
-    }
+  for (int n = 0; n < 8; ++n) {
+    const float b0 = s.b1[8 * n + 2 * tq], b1v = s.b1[8 * n + 2 * tq + 1];
+    float* c = h1[n];
+    c[0] = b0;
+    c[1] = b1v;
+    c[2] = b0;
+    c[3] = b1v;
+    mma(c, oh, b[n >> 1][2 * (n & 1)], b[n >> 1][2 * (n & 1) + 1]);
+  }
+  if constexpr (LO) {
+#pragma unroll
+    for (int n = 0; n < 8; ++n) mma(h1[n], ol, b[n >> 1][2 * (n & 1)], b[n >> 1][2 * (n & 1) + 1]);
   }
 #pragma unroll
   for (int n = 0; n < 8; ++n)
@@ -388,14 +392,14 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
   for (int kk = 0; kk < 4; ++kk) {
     uint32_t ah[4], al[4];
     c_to_a(h1, kk, ah, al);
+    uint32_t b[4][4];
 #pragma unroll
-    for (int n = 0; n < 8; n += 2) {
-      uint32_t b[4];
-      ldsm_x4(b, &s.W2[(8 * n + brow) * S64 + 16 * kk + bcol]);
-      mma(h2[n], ah, b[0], b[1]);
-      if constexpr (LO) mma(h2[n], al, b[0], b[1]);
-      mma(h2[n + 1], ah, b[2], b[3]);
-      if constexpr (LO) mma(h2[n + 1], al, b[2], b[3]);
+    for (int n = 0; n < 8; n += 2) ldsm_x4(b[n >> 1], &s.W2[(8 * n + brow) * S64 + 16 * kk + bcol]);
+#pragma unroll
+    for (int n = 0; n < 8; ++n) mma(h2[n], ah, b[n >> 1][2 * (n & 1)], b[n >> 1][2 * (n & 1) + 1]);
+    if constexpr (LO) {
+#pragma unroll
+      for (int n = 0; n < 8; ++n) mma(h2[n], al, b[n >> 1][2 * (n & 1)], b[n >> 1][2 * (n & 1) + 1]);
     }
   }
 #pragma unroll
@@ -440,16 +444,17 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
     uint32_t ah[4], al[4];
     ldsm_x4(ah, &s.dz3[b][0][arow * S16 + acol]);
     ldsm_x4(al, &s.dz3[b][1][arow * S16 + acol]);
+    uint32_t b[4][4];
 #pragma unroll
-    for (int n = 0; n < 8; n += 2) {
-      uint32_t b[4];
-      ldsm_x4_t(b, &s.W3[trow * S64 + 8 * n + tcol]);
+    for (int n = 0; n < 8; n += 2) ldsm_x4_t(b[n >> 1], &s.W3[trow * S64 + 8 * n + tcol]);
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        d[n + u][0] = d[n + u][1] = d[n + u][2] = d[n + u][3] = 0.f;
-        mma(d[n + u], ah, b[2 * u], b[2 * u + 1]);
-        if constexpr (LO) mma(d[n + u], al, b[2 * u], b[2 * u + 1]);
-      }
+    for (int n = 0; n < 8; ++n) {
+      d[n][0] = d[n][1] = d[n][2] = d[n][3] = 0.f;
+      mma(d[n], ah, b[n >> 1][2 * (n & 1)], b[n >> 1][2 * (n & 1) + 1]);
+    }
+    if constexpr (LO) {
+#pragma unroll
+      for (int n = 0; n < 8; ++n) mma(d[n], al, b[n >> 1][2 * (n & 1)], b[n >> 1][2 * (n & 1) + 1]);
     }
   }
   // dz2 = dh2 (1 - h2^2)
@@ -470,14 +475,14 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
   for (int kk = 0; kk < 4; ++kk) {
     uint32_t ah[4], al[4];
     c_to_a(d, kk, ah, al);
+    uint32_t b[4][4];
 #pragma unroll
-    for (int n = 0; n < 8; n += 2) {
-      uint32_t b[4];
-      ldsm_x4_t(b, &s.W2[(16 * kk + trow) * S64 + 8 * n + tcol]);
-      mma(e1[n], ah, b[0], b[1]);
-      if constexpr (LO) mma(e1[n], al, b[0], b[1]);
-      mma(e1[n + 1], ah, b[2], b[3]);
-      if constexpr (LO) mma(e1[n + 1], al, b[2], b[3]);
+    for (int n = 0; n < 8; n += 2) ldsm_x4_t(b[n >> 1], &s.W2[(16 * kk + trow) * S64 + 8 * n + tcol]);
+#pragma unroll
+    for (int n = 0; n < 8; ++n) mma(e1[n], ah, b[n >> 1][2 * (n & 1)], b[n >> 1][2 * (n & 1) + 1]);
+    if constexpr (LO) {
+#pragma unroll
+      for (int n = 0; n < 8; ++n) mma(e1[n], al, b[n >> 1][2 * (n & 1)], b[n >> 1][2 * (n & 1) + 1]);
     }
   }
   // dz1 = dh1 (1 - h1^2)
@@ -499,8 +504,8 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
     uint32_t b[4];
     ldsm_x4_t(b, &s.W1[(16 * kk + trow) * S16 + tcol]);
     mma(o[0], ah, b[0], b[1]);
-    if constexpr (LO) mma(o[0], al, b[0], b[1]);
     mma(o[1], ah, b[2], b[3]);
+    if constexpr (LO) mma(o[0], al, b[0], b[1]);
     if constexpr (LO) mma(o[1], al, b[2], b[3]);
   }
 #pragma unroll
@@ -515,11 +520,12 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
 // dW accumulation over the CTA's 64 drones for this step (warp v's slice):
 //   dW2 rows j in [16v, 16v+16) x columns 0..64 (64 = bias b2)
 //   dW1 rows i in [16v, 16v+16) x columns 0..15 (13 = bias b1)
-//   dW3 rows o in [0, 16) x columns j in [16v, 16v+16) (+ column 64 = b3 on warp 3)
+//   dW3 transposed: rows j in [16v, 16v+16) x columns o in [0, 8) (o < 4 used), and
+//   on warp 3 db3 as rows o in [0, 16) x the bias column of h2
 struct DwAcc {
   float w2[9][4];
   float w1[2][4];
-  float w3[3][4];
+  float w3[2][4];  // [0]: dW3^T slice, [1]: db3 (warp 3)
 };
 
 template <bool LO>
@@ -535,16 +541,23 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc, int hb) {
     // dW2
     ldsm_x4_t(ah, &s.dz2[hb][0][(d0 + arow) * S64 + 16 * v + acol]);
     ldsm_x4_t(al, &s.dz2[hb][1][(d0 + arow) * S64 + 16 * v + acol]);
+    // four n-tiles at a time, product by product (hi hi, hi lo, lo hi), so that
+    // consecutive MMAs accumulate into different tiles (each tile's order is kept)
 #pragma unroll
-    for (int n = 0; n < 8; n += 2) {
-      uint32_t bh[4], bl[4];
-      ldsm_x4_t(bh, &s.h1[hb][0][(d0 + brow) * S64 + 8 * n + bcol]);
-      ldsm_x4_t(bl, &s.h1[hb][1][(d0 + brow) * S64 + 8 * n + bcol]);
+    for (int n0 = 0; n0 < 8; n0 += 4) {
+      uint32_t bh[2][4], bl[2][4];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        mma(acc.w2[n + u], ah, bh[2 * u], bh[2 * u + 1]);
-        if constexpr (LO) mma(acc.w2[n + u], ah, bl[2 * u], bl[2 * u + 1]);
-        if constexpr (LO) mma(acc.w2[n + u], al, bh[2 * u], bh[2 * u + 1]);
+      for (int p = 0; p < 2; ++p) {
+        ldsm_x4_t(bh[p], &s.h1[hb][0][(d0 + brow) * S64 + 8 * (n0 + 2 * p) + bcol]);
+        if constexpr (LO) ldsm_x4_t(bl[p], &s.h1[hb][1][(d0 + brow) * S64 + 8 * (n0 + 2 * p) + bcol]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) mma(acc.w2[n0 + q], ah, bh[q >> 1][2 * (q & 1)], bh[q >> 1][2 * (q & 1) + 1]);
+      if constexpr (LO) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mma(acc.w2[n0 + q], ah, bl[q >> 1][2 * (q & 1)], bl[q >> 1][2 * (q & 1) + 1]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mma(acc.w2[n0 + q], al, bh[q >> 1][2 * (q & 1)], bh[q >> 1][2 * (q & 1) + 1]);
       }
     }
     {
@@ -561,31 +574,37 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc, int hb) {
       ldsm_x4_t(bh, &s.obsr[hb][0][(d0 + brow) * S16 + bcol]);
       ldsm_x4_t(bl, &s.obsr[hb][1][(d0 + brow) * S16 + bcol]);
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        mma(acc.w1[u], ah, bh[2 * u], bh[2 * u + 1]);
-        if constexpr (LO) mma(acc.w1[u], ah, bl[2 * u], bl[2 * u + 1]);
-        if constexpr (LO) mma(acc.w1[u], al, bh[2 * u], bh[2 * u + 1]);
+      for (int u = 0; u < 2; ++u) mma(acc.w1[u], ah, bh[2 * u], bh[2 * u + 1]);
+      if constexpr (LO) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) mma(acc.w1[u], ah, bl[2 * u], bl[2 * u + 1]);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) mma(acc.w1[u], al, bh[2 * u], bh[2 * u + 1]);
       }
     }
-    // dW3
-    ldsm_x4_t(ah, &s.dz3[hb][0][(d0 + arow) * S16 + acol]);
-    ldsm_x4_t(al, &s.dz3[hb][1][(d0 + arow) * S16 + acol]);
+    // dW3^T = h2^T dz3: A = h2^T (rows j of this warp's slice), B = dz3 (k = d,
+    // n = o; 4 of its 8 columns used) -- one n-tile where dW3 = dz3^T h2 would
+    // spend two m-tiles on the 4 used output rows
+    ldsm_x4_t(ah, &s.h2[hb][0][(d0 + arow) * S64 + 16 * v + acol]);
+    if constexpr (LO) ldsm_x4_t(al, &s.h2[hb][1][(d0 + arow) * S64 + 16 * v + acol]);
     {
-      uint32_t bh[4], bl[4];
-      ldsm_x4_t(bh, &s.h2[hb][0][(d0 + brow) * S64 + 16 * v + bcol]);
-      ldsm_x4_t(bl, &s.h2[hb][1][(d0 + brow) * S64 + 16 * v + bcol]);
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        mma(acc.w3[u], ah, bh[2 * u], bh[2 * u + 1]);
-        if constexpr (LO) mma(acc.w3[u], ah, bl[2 * u], bl[2 * u + 1]);
-        if constexpr (LO) mma(acc.w3[u], al, bh[2 * u], bh[2 * u + 1]);
+      uint32_t bh[2], bl[2];
+      ldsm_x2_t(bh, &s.dz3[hb][0][(d0 + brow) * S16]);
+      if constexpr (LO) ldsm_x2_t(bl, &s.dz3[hb][1][(d0 + brow) * S16]);
+      mma(acc.w3[0], ah, bh[0], bh[1]);
+      if constexpr (LO) {
+        mma(acc.w3[0], ah, bl[0], bl[1]);
+        mma(acc.w3[0], al, bh[0], bh[1]);
       }
-      if (v == 3) {
-        uint32_t b1[2];
-        ldsm_x2_t(b1, &s.h2[hb][0][(d0 + brow) * S64 + 64]);
-        mma(acc.w3[2], ah, b1[0], b1[1]);
-        if constexpr (LO) mma(acc.w3[2], al, b1[0], b1[1]);
-      }
+    }
+    if (v == 3) {
+      // db3 = dz3^T 1: A = dz3^T, B = the bias column of h2 (exact, lo = 0)
+      ldsm_x4_t(ah, &s.dz3[hb][0][(d0 + arow) * S16 + acol]);
+      if constexpr (LO) ldsm_x4_t(al, &s.dz3[hb][1][(d0 + arow) * S16 + acol]);
+      uint32_t b1[2];
+      ldsm_x2_t(b1, &s.h2[hb][0][(d0 + brow) * S64 + 64]);
+      mma(acc.w3[1], ah, b1[0], b1[1]);
+      if constexpr (LO) mma(acc.w3[1], al, b1[0], b1[1]);
     }
   }
 }
@@ -609,15 +628,9 @@ __device__ void store_dw(const DwAcc& acc, int v, int lane, float* __restrict__ 
       if (c < 13) part[OFF_W1 + i * 13 + c] = acc.w1[n][e];
       else if (c == 13) part[OFF_B1 + i] = acc.w1[n][e];
     }
-    // dW3 / db3
-#pragma unroll
-    for (int n = 0; n < 3; ++n) {
-      if (n == 2 && v != 3) continue;
-      const int o = rr, j = (n < 2) ? 16 * v + 8 * n + cc : 64 + cc;
-      if (o >= 4) continue;
-      if (j < 64) part[OFF_W3 + o * 64 + j] = acc.w3[n][e];
-      else if (j == 64) part[OFF_B3 + o] = acc.w3[n][e];
-    }
+    // dW3 (transposed slice: row j, column o) / db3 (row o, bias column)
+    if (cc < 4) part[OFF_W3 + cc * 64 + 16 * v + rr] = acc.w3[0][e];
+    if (v == 3 && rr < 4 && cc == 0) part[OFF_B3 + rr] = acc.w3[1][e];
   }
 }
 
@@ -650,13 +663,20 @@ __device__ __forceinline__ void policy_step(float* x, const float a[4], const De
   x[6] *= in;
 }
 
-// Adjoint of policy_step.  In: x (pre-step state), a, lam = dL/dx_{k+1}.
-// Out: lam = dL/dx_k through the step (the observation path is added by the
-// caller), ga = dL/da through the controller.
-__device__ void policy_step_adjoint(const float* x, const float a[4], float* lam, float ga[4],
-                                    const DevParams& P, float dt) {
-  // ---------------- forward recomputation (as policy_step, with the intermediates
-  // of the quaternion attitude error kept)
+// Forward quantities of one policy_step that its adjoint needs besides the
+// pre- and post-step states: 1 / |q~| of the normalisation, the mixer's factors
+// d W_cmd / d f per rotor (0 where the thrust clip or a zero command stops the
+// gradient), the attitude error's parts (v, w) = qd2* (x) q, twice the desired
+// quaternion qd2 and the half-angle products it is built from.
+constexpr int FQ_FLOATS = 20;  // 19 used; rows of five float4
+struct StepRecord {
+  float in, gWf[4], vx, vy, vz, we, dx, dy, dz, dw, sr, cr, ka, kb, kc, kd;
+};
+
+// policy_step that also records the step's forward quantities (the same
+// arithmetic as policy_step: the state comes out bit for bit the same).
+__device__ __forceinline__ void policy_step_rec(float* x, const float a[4], const DevParams& P, float dt,
+                                                StepRecord& q) {
   const float ac0 = clampf(a[0], -1.f, 1.f), ac1 = clampf(a[1], -1.f, 1.f);
   const float ac2 = clampf(a[2], -1.f, 1.f), ac3 = clampf(a[3], -1.f, 1.f);
   float sr, cr, sp, cp, sy, cy;  // of the half angles
@@ -670,14 +690,13 @@ __device__ void policy_step_adjoint(const float* x, const float a[4], float* lam
   const float dz = fmaf(cr, kd, -sr * kc), dw = fmaf(cr, ka, sr * kb);
   const float Td = fmaf(P.ts_mg, ac3, P.mg);
   const float qx = x[3], qy = x[4], qz = x[5], qw = x[6];
-  const float wx = x[10], wy = x[11], wz = x[12];
   // (v, w) = qd2* (x) q, 2 e_R = w v (attitude_error2_q)
   const float vx = fmaf(dw, qx, fmaf(-qw, dx, fmaf(-dy, qz, dz * qy)));
   const float vy = fmaf(dw, qy, fmaf(-qw, dy, fmaf(-dz, qx, dx * qz)));
   const float vz = fmaf(dw, qz, fmaf(-qw, dz, fmaf(-dx, qy, dy * qx)));
   const float we = fmaf(dw, qw, fmaf(dx, qx, fmaf(dy, qy, dz * qz)));
   float tx, ty, tz;
-  attitude_torque_e(we * vx, we * vy, we * vz, wx, wy, wz, P, tx, ty, tz);
+  attitude_torque_e(we * vx, we * vy, we * vz, x[10], x[11], x[12], P, tx, ty, tz);
   const float A = 0.25f * Td, X = tx * P.mix_a, Y = ty * P.mix_a, Z = tz * P.mix_k;
   float f[4], Wc[4];
   f[0] = (A - X) - (Y + Z);
@@ -685,16 +704,90 @@ __device__ void policy_step_adjoint(const float* x, const float a[4], float* lam
   f[2] = (A + X) + (Y - Z);
   f[3] = (A + X) - (Y - Z);
 #pragma unroll
-  for (int r = 0; r < 4; ++r) Wc[r] = sqrt_approx(clampf(f[r], 0.f, P.fmax) * P.inv_kf);
+  for (int r = 0; r < 4; ++r) {
+    Wc[r] = sqrt_approx(clampf(f[r], 0.f, P.fmax) * P.inv_kf);
+    // W = sqrt(f / kf): dW/df = 1 / (2 kf W) inside the clip
+    const bool pass = f[r] >= 0.f && f[r] <= P.fmax && Wc[r] > 0.f;
+    q.gWf[r] = pass ? P.inv_kf * 0.5f / Wc[r] : 0.f;
+  }
   float d[17];
   deriv_fp<MOTOR_LAG>(x, Wc, P, false, d);
-  float qt[4];
+  // element pairs on the packed FP32 instructions (same rounding as fmaf per lane)
+  const float2 dt2 = make_float2(dt, dt);
 #pragma unroll
-  for (int j = 0; j < 4; ++j) qt[j] = fmaf(dt, d[3 + j], x[3 + j]);
-  const float in = rsqrt_approx(fmaf(qt[0], qt[0], fmaf(qt[1], qt[1], fmaf(qt[2], qt[2], qt[3] * qt[3]))));
+  for (int j = 0; j < 16; j += 2) {
+    const float2 r = __ffma2_rn(dt2, make_float2(d[j], d[j + 1]), make_float2(x[j], x[j + 1]));
+    x[j] = r.x;
+    x[j + 1] = r.y;
+  }
+  x[16] = fmaf(dt, d[16], x[16]);
+  const float in = rsqrt_approx(fmaf(x[3], x[3], fmaf(x[4], x[4], fmaf(x[5], x[5], x[6] * x[6]))));
+  x[3] *= in;
+  x[4] *= in;
+  x[5] *= in;
+  x[6] *= in;
+  q.in = in;
+  q.vx = vx;
+  q.vy = vy;
+  q.vz = vz;
+  q.we = we;
+  q.dx = dx;
+  q.dy = dy;
+  q.dz = dz;
+  q.dw = dw;
+  q.sr = sr;
+  q.cr = cr;
+  q.ka = ka;
+  q.kb = kb;
+  q.kc = kc;
+  q.kd = kd;
+}
+
+__device__ __forceinline__ void store_record(float* __restrict__ base, int i, const StepRecord& q) {
+  float4* p = reinterpret_cast<float4*>(base + (size_t)i * FQ_FLOATS);
+  p[0] = make_float4(q.in, q.gWf[0], q.gWf[1], q.gWf[2]);
+  p[1] = make_float4(q.gWf[3], q.vx, q.vy, q.vz);
+  p[2] = make_float4(q.we, q.dx, q.dy, q.dz);
+  p[3] = make_float4(q.dw, q.sr, q.cr, q.ka);
+  p[4] = make_float4(q.kb, q.kc, q.kd, 0.f);
+}
+__device__ __forceinline__ void record_from(const float* f, StepRecord& q) {
+  q.in = f[0];
+  q.gWf[0] = f[1];
+  q.gWf[1] = f[2];
+  q.gWf[2] = f[3];
+  q.gWf[3] = f[4];
+  q.vx = f[5];
+  q.vy = f[6];
+  q.vz = f[7];
+  q.we = f[8];
+  q.dx = f[9];
+  q.dy = f[10];
+  q.dz = f[11];
+  q.dw = f[12];
+  q.sr = f[13];
+  q.cr = f[14];
+  q.ka = f[15];
+  q.kb = f[16];
+  q.kc = f[17];
+  q.kd = f[18];
+}
+
+// Adjoint of policy_step.  In: x (pre-step state), xn (post-step state), the
+// step's record q, a, lam = dL/dx_{k+1}.  Out: lam = dL/dx_k through the step (the
+// observation path is added by the caller), ga = dL/da through the controller.
+__device__ void policy_step_adjoint(const float* x, const float* xn, const StepRecord& q, const float a[4],
+                                    float* lam, float ga[4], const DevParams& P, float dt) {
+  const float in = q.in;
+  const float vx = q.vx, vy = q.vy, vz = q.vz, we = q.we;
+  const float dx = q.dx, dy = q.dy, dz = q.dz, dw = q.dw;
+  const float sr = q.sr, cr = q.cr, ka = q.ka, kb = q.kb, kc = q.kc, kd = q.kd;
+  const float qx = x[3], qy = x[4], qz = x[5], qw = x[6];
+  const float wx = x[10], wy = x[11], wz = x[12];
   // ---------------- reverse: normalisation q' = qt / |qt|
   {
-    const float q0 = qt[0] * in, q1 = qt[1] * in, q2 = qt[2] * in, q3 = qt[3] * in;
+    // the normalised quaternion is the post-step state's (policy_step's q~ in)
+    const float q0 = xn[3], q1 = xn[4], q2 = xn[5], q3 = xn[6];
     const float dot = fmaf(q0, lam[3], fmaf(q1, lam[4], fmaf(q2, lam[5], q3 * lam[6])));
     lam[3] = (lam[3] - q0 * dot) * in;
     lam[4] = (lam[4] - q1 * dot) * in;
@@ -749,11 +842,7 @@ __device__ void policy_step_adjoint(const float* x, const float a[4], float* lam
   // ---------------- controller: W_cmd -> mixer -> torque -> attitude error
   float gf[4];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const float gWc = P.cv_up * mu[13 + r];
-    const bool pass = f[r] >= 0.f && f[r] <= P.fmax && Wc[r] > 0.f;
-    gf[r] = pass ? gWc * P.inv_kf * 0.5f / Wc[r] : 0.f;
-  }
+  for (int r = 0; r < 4; ++r) gf[r] = P.cv_up * mu[13 + r] * q.gWf[r];
   const float gA = (gf[0] + gf[1]) + (gf[2] + gf[3]);
   const float gX = (gf[2] + gf[3]) - (gf[0] + gf[1]);
   const float gY = (gf[1] + gf[2]) - (gf[0] + gf[3]);
@@ -817,18 +906,12 @@ __device__ __forceinline__ void store_row(float* __restrict__ base, int i, const
   p[4] = make_float4(x[16], 0.f, 0.f, 0.f);
 }
 
-// Prefetch helpers (one lane per drone): a 20-float row, a reference position.
+// Prefetch helper (one lane per drone): a 20-float row (a state row or a step record).
+static_assert(FQ_FLOATS == 20, "step records prefetch like state rows");
 __device__ __forceinline__ void prefetch_row(float* dst, const float* __restrict__ base, int i) {
   const float* q = base + (size_t)i * 20;
 #pragma unroll
   for (int j = 0; j < 5; ++j) cp_async16(dst + 4 * j, q + 4 * j);
-}
-__device__ __forceinline__ void prefetch_ref(float* dst, const float* __restrict__ p_ref, int k, int n,
-                                             int i) {
-  const float* q = p_ref + ((size_t)k * n + i) * 3;
-  cp_async4(dst, q);
-  cp_async4(dst + 1, q + 1);
-  cp_async4(dst + 2, q + 2);
 }
 
 __device__ __forceinline__ void ref_at(const float* __restrict__ p_ref, int k, int n, int i,
@@ -848,21 +931,24 @@ __device__ __forceinline__ void ref_at_pinned(const float* __restrict__ p_ref, i
 
 // ------------------------------------------------------------------ activation cache
 
-// One warp's cached step is three contiguous runs in shared memory and in the cache
-// entry alike: the warp's 16 rows of h2 hi, h2 lo in tile buffer b (TILE_CHUNKS
-// 16-byte chunks each) and its 16 action rows in actb[b].  They move as bulk
-// copies (cp.async.bulk: one thread, the copy engine of the SM).
+// One warp's cached step (rows 16 v..16 v + 15 at one step of a segment) is three
+// contiguous runs, laid out as they sit in shared memory: its 16 rows of h2 hi and
+// of h2 lo (TILE_CHUNKS 16-byte chunks each, padded rows as in the tiles) and its
+// 16 action rows.  The recompute warp writes it from its staging tile, the
+// weight-gradient warp that prepares the step copies it into the tile buffers,
+// both as bulk copies (cp.async.bulk: one thread, the copy engine of the SM).
+constexpr int TILE_CHUNKS = 16 * S64 * 2 / 16, CACHE_CHUNKS = 2 * TILE_CHUNKS + 16;
 constexpr uint32_t TILE_BYTES = TILE_CHUNKS * 16, ACT_BYTES = 16 * 16;
 constexpr uint32_t CACHE_BYTES = 2 * TILE_BYTES + ACT_BYTES;
 static_assert(CACHE_BYTES == CACHE_CHUNKS * 16, "cache entry = two tiles + action rows");
-static_assert(offsetof(Smem, h1) % 16 == 0 && offsetof(Smem, h2) % 16 == 0 &&
-                  offsetof(Smem, actb) % 16 == 0 && (DPC * S64 * 2) % 16 == 0,
+static_assert(offsetof(Smem, h2) % 16 == 0 && offsetof(Smem, actb) % 16 == 0 && offsetof(Smem, act) % 16 == 0 &&
+                  offsetof(Smem, stage) % 16 == 0 && (DPC * S64 * 2) % 16 == 0 && (16 * S64 * 2) % 16 == 0,
               "bulk copies start on 16-byte boundaries");
 
 // L2 priorities of the cache traffic: an entry is written once per segment and
 // read back once in the reverse sweep, so its writes ask L2 to keep it
-// (evict_last) and its read marks it as done (evict_first); a segment's entries
-// then stay in L2 between the two instead of being written back and re-read.
+// (evict_last) and its read marks it as done (evict_first); once consumed it is
+// dropped from L2 without a write-back (cache_discard).
 __device__ __forceinline__ unsigned long long l2_keep() {
   unsigned long long p;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
@@ -888,11 +974,8 @@ __device__ __forceinline__ void bulk_g2s(void* sm, const void* g, uint32_t bytes
       : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-// wait until at most N of this thread's bulk groups still read their source
-template <int N>
-__device__ __forceinline__ void bulk_wait_read() {
-  asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
-}
+// wait until none of this thread's bulk groups still reads its source
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 // wait until all of this thread's bulk groups have completed (writes performed)
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 // order this thread's shared-memory writes before bulk copies that read them
@@ -910,13 +993,33 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* m, uint32_t b
                : "memory");
 }
 
-// Copy out warp rows r0..r0+15 of tile buffer b to cache entry g (one bulk group).
-__device__ __forceinline__ void cache_store(Smem& s, int b, int r0, uint4* g) {
+// The recompute warp's copy-out of one step: h2 (after tanh) through its staging
+// tile, hi then lo (one tile of shared memory: each copy has read the tile before
+// the next part is staged), and its action rows from act.
+__device__ __forceinline__ void cache_put(Smem& s, int v, int r0, int lane, const float h2[8][4], uint4* g) {
+  __nv_bfloat16* t = s.stage[v];
+  const int at = frag_row(lane) * S64 + frag_col(lane);
   const unsigned long long pol = l2_keep();
-  bulk_s2g(g, s.h2[b][0] + r0 * S64, TILE_BYTES, pol);
-  bulk_s2g(g + TILE_CHUNKS, s.h2[b][1] + r0 * S64, TILE_BYTES, pol);
-  bulk_s2g(g + 2 * TILE_CHUNKS, s.actb[b][r0], ACT_BYTES, pol);
-  bulk_commit();
+  if (lane == 0) bulk_wait_read();  // the previous step's lo copy
+  __syncwarp();
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      uint32_t h[4], l[4];
+      c_to_a(h2, kk, h, l);
+      stsm_x4(&t[at + 16 * kk], half ? l : h);
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      bulk_s2g(g + half * TILE_CHUNKS, t, TILE_BYTES, pol);
+      if (!half) bulk_s2g(g + 2 * TILE_CHUNKS, s.act[r0], ACT_BYTES, pol);
+      bulk_commit();
+      if (!half) bulk_wait_read();
+    }
+    __syncwarp();
+  }
 }
 
 // Bring cache entry g back into rows r0..r0+15 of buffer b; the barrier's phase
@@ -931,8 +1034,8 @@ __device__ __forceinline__ void cache_load(Smem& s, int b, int r0, const uint4* 
 }
 
 // Drop a consumed cache entry from L2 without writing it back: the lanes of the
-// warp invalidate its 128-byte lines (entries start on 128-byte boundaries:
-// the workspace is 256-byte aligned and CACHE_BYTES is a multiple of 128).
+// warp invalidate its 128-byte lines (entries start on 128-byte boundaries: the
+// workspace is 256-byte aligned and CACHE_BYTES is a multiple of 128).
 static_assert(CACHE_BYTES % 128 == 0, "cache entries are whole 128-byte lines");
 __device__ __forceinline__ void cache_discard(const uint4* g, int lane) {
   const char* e = reinterpret_cast<const char*>(g);
@@ -1083,21 +1186,30 @@ __global__ void wait_selftest_kernel(uint32_t* status) {
   if (!done && threadIdx.x == 0) atomicOr(status, SIM_FLAG_TIMEOUT);
 }
 
-// The adjoint runs two warp roles per CTA.  Warps 0-3 (compute) own 16 drones each:
-// segment recompute, then per reverse step the loss and step adjoints and the MLP
-// backward, which leave the step's dz, obs and activation tiles in shared memory.
-// Warps 4-7 (weight gradient) accumulate dW over the CTA's 64 drones from those
-// tiles while the compute warps already run the next (earlier) step, and then
+// The adjoint runs three warp roles per CTA, each role one warp per 16-drone block.
+// Warps 8-11 (recompute) run one segment ahead of the reverse sweep: from the
+// segment's checkpoint they step its states forward with the policy in the loop and
+// write the states (segment rows, and the state after the segment) and each step's h2
+// and actions (the activation cache) for the segment buffer of the segment's parity.
+// Warps 0-3 (compute) sweep a recomputed segment in reverse: per step the loss and
+// step adjoints and the MLP backward, which leave the step's dz tiles in shared
+// memory.  Warps 4-7 (weight gradient) accumulate dW over the CTA's 64 drones from
+// those tiles while the compute warps already run the next (earlier) step, and then
 // prepare step k - 2 for compute warp v's drones in the freed buffer: h2 and the
-// actions come back from the segment's cache (bulk copies), h1 is recomputed from
-// the segment state (one layer), so the cache holds half of each step.  The
-// segment's last two steps stay in shared memory from the recompute.  Hand-off per
-// step parity b = k & 1: full[b] (compute threads arrive when the tiles are
-// written), empty[b] (weight-gradient threads arrive when they are read),
-// ready[v][b] (the 32 lanes of the warp that prepared buffer b for warp v's rows
-// arrive, and the copied bytes land).
+// actions come back from the cache, h1 is recomputed from the segment state (one
+// layer).  Hand-offs, all on shared-memory barriers with bounded waits:
+//   full[b] / empty[b]   per step parity b = k & 1: the compute threads arrive when
+//                        the step's tiles are written, the weight-gradient threads when
+//                        they have read them;
+//   ready[v][b]          the 32 lanes of the warp that prepared buffer b for warp v's
+//                        rows arrive;
+//   seg_done[p]          the recompute threads arrive when the segment of parity p
+//                        is written;
+//   seg_free[p]          the weight-gradient threads arrive when the compute warps
+//                        have finished the segment of parity p, so that the recompute
+//                        may write the segment after next into its buffer.
 template <int OBJ, bool LO>
-__global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, DevParams P) {
+__global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, DevParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& s = *reinterpret_cast<Smem*>(smem_raw);
   load_weights(s, a.w);
@@ -1106,6 +1218,8 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       mbar_init(&s.full[b], TPB);
       mbar_init(&s.empty[b], TPB);
       for (int v = 0; v < 4; ++v) mbar_init(&s.ready[v][b], 32);
+      mbar_init(&s.seg_done[b], TPB);
+      mbar_init(&s.seg_free[b], TPB);
     }
   }
   __syncthreads();
@@ -1117,18 +1231,86 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
   auto wait_on = [&](unsigned long long* m, uint32_t par) {
     if (!timed_out && !mbar_wait(m, par)) timed_out = true;
   };
-  // cache entry of warp rows 16 v at segment step j: cache_at(v, j)
-  const size_t cache_step = (size_t)gridDim.x * 4 * CACHE_CHUNKS;
-  auto cache_at = [&](int v, int j) {
-    return a.hcache + (size_t)j * cache_step + ((size_t)blockIdx.x * 4 + v) * CACHE_CHUNKS;
+  // segment buffers of parity p: rows [C R + 1][n][20], previous actions [C][n]
+  const size_t seg_stride = (size_t)(a.C * a.R + 1) * a.n * 20;
+  auto seg_rows = [&](int sg) { return a.seg + (size_t)(sg & 1) * seg_stride; };
+  auto seg_prev = [&](int sg) { return a.seg_a + (size_t)(sg & 1) * a.C * a.n; };
+  auto seg_recs = [&](int sg) { return a.seg_q + (size_t)(sg & 1) * a.C * a.R * a.n * FQ_FLOATS; };
+  // cache entry of warp rows 16 v at step j of a segment of parity p
+  auto cache_at = [&](int p, int v, int j) {
+    return a.hcache + (((size_t)p * a.C + j) * gridDim.x * 4 + (size_t)blockIdx.x * 4 + v) * CACHE_CHUNKS;
   };
-  // drones of warp v (either role): rows 16 v + (lane & 15) of the CTA's 64;
+  // barrier phase of segment sg's use of its parity's barriers: segments are taken
+  // in reverse, so the u-th one (u = nseg - 1 - sg) is its parity's (u >> 1)-th
+  auto seg_phase = [&](int sg) { return (uint32_t)(((nseg - 1 - sg) >> 1) & 1); };
+  // drones of warp v (any role): rows 16 v + (lane & 15) of the CTA's 64;
   // out-of-range rows shadow the last drone (finite data; their seed and dz are zero)
   const int v = warp & 3;
   const int r0 = 16 * v, row = r0 + (lane & 15);
   const int i = blockIdx.x * DPC + row;
   const bool valid = i < a.n;
   const int ii = valid ? i : a.n - 1;
+  if (warp >= 8) {
+    // ---------------- recompute warps
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+      const int k0 = sg * a.C, k1 = min(a.H, k0 + a.C);
+      // the buffer's previous segment (sg + 2) has been swept
+      if (sg + 2 < nseg) wait_on(&s.seg_free[sg & 1], seg_phase(sg + 2));
+      float* rows = seg_rows(sg);
+      float x[17];
+      load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
+      float4 ap4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (OBJ == SIM_OBJ_TRACKING_REWARD) ap4 = a.ckpt_a[(size_t)sg * a.n + ii];
+      // reference positions of steps k, k + 1 and k + 2 in registers, each loaded
+      // two steps before its use
+      float rr[3], rr1[3];
+      ref_at(a.p_ref, k0, a.n, ii, rr);
+      ref_at(a.p_ref, k0 + 1, a.n, ii, rr1);
+      for (int k = k0; k < k1; ++k) {
+        if (valid && lane < 16) {
+          store_row(rows + (size_t)(k - k0) * a.R * a.n * 20, i, x);
+          if (OBJ == SIM_OBJ_TRACKING_REWARD) seg_prev(sg)[(size_t)(k - k0) * a.n + i] = ap4;
+        }
+        float rr2[3] = {0.f, 0.f, 0.f};
+        if (k + 2 <= a.H) ref_at_pinned(a.p_ref, k + 2, a.n, ii, rr2);
+        if (lane < 16) put_obs(s.obs, row, x, rr);
+        __syncwarp();
+        float act[4];
+        {
+          float h1[8][4], h2[8][4];
+          mlp_forward<LO>(s, r0, lane, h1, h2, s.act);
+          cache_put(s, v, r0, lane, h2, cache_at(sg & 1, v, k - k0));  // has warp barriers
+#pragma unroll
+          for (int o = 0; o < 4; ++o) act[o] = s.act[row][o];
+        }
+        __syncwarp();  // the observation and action rows are rewritten next step
+        for (int j = 0; j < a.R; ++j) {
+          if (j > 0 && valid && lane < 16)
+            store_row(rows + ((size_t)(k - k0) * a.R + j) * a.n * 20, i, x);
+          StepRecord q;
+          policy_step_rec(x, act, P, a.dt, q);
+          if (valid && lane < 16) store_record(seg_recs(sg) + ((size_t)(k - k0) * a.R + j) * a.n * FQ_FLOATS, i, q);
+        }
+        ap4 = make_float4(act[0], act[1], act[2], act[3]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          rr[c] = rr1[c];
+          rr1[c] = rr2[c];
+        }
+      }
+      // the state after the segment (the loss term of its last step)
+      if (valid && lane < 16) store_row(rows + (size_t)(k1 - k0) * a.R * a.n * 20, i, x);
+      // the segment's cache entries are complete before its readers copy them back
+      // (they wait for these arrivals first)
+      if (lane == 0) {
+        bulk_wait_all();
+        fence_proxy_async_global();
+      }
+      mbar_arrive(&s.seg_done[sg & 1]);  // release: this thread's rows
+    }
+    if (timed_out && a.status) atomicOr(a.status, SIM_FLAG_TIMEOUT);
+    return;
+  }
   if (warp >= 4) {
     // ---------------- weight-gradient warps: slice v of dW2 / dW1 / dW3
     DwAcc acc;
@@ -1137,62 +1319,69 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
 #pragma unroll
     for (int n = 0; n < 2; ++n) acc.w1[n][0] = acc.w1[n][1] = acc.w1[n][2] = acc.w1[n][3] = 0.f;
 #pragma unroll
-    for (int n = 0; n < 3; ++n) acc.w3[n][0] = acc.w3[n][1] = acc.w3[n][2] = acc.w3[n][3] = 0.f;
-    // Reverse steps k = H - 1 - t in processing order t.  After reading buffer
-    // b = k & 1, and once all four warps of this role have, warp v prepares it with
-    // step k - 2 of compute warp v's rows (the steps k1 - 1 and k1 - 2 of a segment
-    // are left there by the compute warp's recompute).
-    int t = 0;
-    int last0 = -1, last1 = -1;  // processing step of the last load issued into buffer 0, 1
-    for (int sg = nseg - 1; sg >= 0; --sg) {
-      const int k0 = sg * a.C, k1 = min(a.H, k0 + a.C);
-      for (int k = k1 - 1; k >= k0; --k, ++t) {
-        const int b = k & 1;
-        const uint32_t par = (uint32_t)((t >> 1) & 1);
+    for (int n = 0; n < 2; ++n) acc.w3[n][0] = acc.w3[n][1] = acc.w3[n][2] = acc.w3[n][3] = 0.f;
+    // Reverse steps k = H - 1 - t in processing order t.  The step of processing
+    // order t + 2 is prepared in two parts: its state and reference are loaded
+    // before the dW work of step t (their latency overlaps it); once all four warps
+    // of this role have read buffer b = k & 1, its cache entry is copied into the
+    // buffer for compute warp v's rows and h1 is recomputed there from the state.
+    int seen = nseg;  // lowest segment whose recompute this warp has waited for
+    int last[2] = {-1, -1};  // processing order of the last copy issued into buffer 0, 1
+    float px[17], pr[3];
+    auto prep_load = [&](int tp) {
+      const int k = a.H - 1 - tp, sg = k / a.C, k0 = sg * a.C;
+      if (sg < seen) {
+        wait_on(&s.seg_done[sg & 1], seg_phase(sg));
+        seen = sg;
+      }
+      if (valid) load_row(seg_rows(sg) + (size_t)(k - k0) * a.R * a.n * 20, i, px);
+      else load_row(a.ckpt + (size_t)sg * a.n * 20, ii, px);
+      ref_at(a.p_ref, k, a.n, ii, pr);
+    };
+    auto prep_store = [&](int tp) {
+      const int k = a.H - 1 - tp, b = k & 1, sg = k / a.C, k0 = sg * a.C;
+      if (lane == 0) {
+        fence_proxy_async_global();
+        cache_load(s, b, r0, cache_at(sg & 1, v, k - k0), &s.ready[v][b]);
+      }
+      last[b] = tp;
+      if (lane < 16) put_obs(s.obsr[b], row, px, pr);  // the step's observation rows (dW1 operand)
+      __syncwarp();
+      float h1[8][4];
+      mlp_layer1<LO>(s, s.obsr[b], r0, lane, h1);
+      store_c64(s.h1[b], r0, lane, h1);
+      mbar_arrive(&s.ready[v][b]);  // with the copied bytes, completes the phase
+    };
+    // t = -2, -1 only prepare the first two steps (one copy of the code for all)
+    for (int t = -2; t < a.H; ++t) {
+      const int k = a.H - 1 - t, b = k & 1, sg = k / a.C;
+      const uint32_t par = (uint32_t)((t >> 1) & 1);
+      const bool work = t >= 0, ahead = t + 2 < a.H;
+      if (work) {
         wait_on(&s.full[b], par);
-        if (k < k1 - 2) {
-          // step k's cache entry has been copied into shared memory and used: drop
-          // its L2 lines without a write-back; the fence orders the discards before
-          // the bulk stores that reuse the entry in the next segment (issued by the
-          // compute warp after it has waited for this warp's arrivals)
-          cache_discard(cache_at(v, k - k0), lane);
-          fence_proxy_async_global();
-        }
-        // step k - 2's state (its first sub-step state, or the checkpoint for rows
-        // without a drone) and reference, loaded during the dW work.  The segment
-        // rows were stored in the compute warps' recompute, before their arrivals on
-        // full[b] (release), which this warp has just waited for (acquire).
-        float x[17], r[3];
-        const bool ahead = k - 2 >= k0;
-        if (ahead) {
-          if (valid) load_row(a.seg + (size_t)(k - 2 - k0) * a.R * a.n * 20, i, x);
-          else load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
-          ref_at(a.p_ref, k - 2, a.n, ii, r);
-        }
+        // the compute warp has consumed step k's cache entry: drop its L2 lines
+        // without a write-back; the fence orders the discards before the bulk
+        // stores that reuse the entry two segments later (issued after seg_free)
+        cache_discard(cache_at(sg & 1, v, k - sg * a.C), lane);
+        fence_proxy_async_global();
+        // the compute warps are done with the segment once they finish its first
+        // step; so is this warp (its loads of the segment were two steps earlier)
+        if (k == sg * a.C) mbar_arrive(&s.seg_free[sg & 1]);
+      }
+      if (ahead) prep_load(t + 2);
+      if (work) {
         accumulate_dw<LO>(s, v, lane, acc, b);
         mbar_arrive(&s.empty[b]);
-        if (ahead) {
-          wait_on(&s.empty[b], par);
-          if (lane == 0) {
-            fence_proxy_async_global();
-            cache_load(s, b, r0, cache_at(v, k - 2 - k0), &s.ready[v][b]);
-          }
-          // step k - 2's observation rows, the dW1 operand of that step as well
-          if (lane < 16) put_obs(s.obsr[b], row, x, r);
-          __syncwarp();
-          float h1[8][4];
-          mlp_layer1<LO>(s, s.obsr[b], r0, lane, h1);
-          store_c64(s.h1[b], r0, lane, h1);
-          mbar_arrive(&s.ready[v][b]);  // with the copied bytes, completes the phase
-          if (b) last1 = t + 2;
-          else last0 = t + 2;
-        }
+      }
+      if (ahead) {
+        if (work) wait_on(&s.empty[b], par);
+        prep_store(t + 2);
       }
     }
-    // the compute warp consumes every load issued here; wait (bounded) for the
-    // last one into each buffer, so that no copy is in flight when the CTA exits
-    if (last0 >= 0 && !mbar_wait(&s.ready[v][0], (uint32_t)((last0 >> 1) & 1))) timed_out = true;
-    if (last1 >= 0 && !mbar_wait(&s.ready[v][1], (uint32_t)((last1 >> 1) & 1))) timed_out = true;
+    // the compute warp consumes every copy issued here; wait (bounded) for the last
+    // one into each buffer, so that no copy is in flight when the CTA exits
+    for (int b = 0; b < 2; ++b)
+      if (last[b] >= 0 && !mbar_wait(&s.ready[v][b], (uint32_t)((last[b] >> 1) & 1))) timed_out = true;
     store_dw(acc, v, lane, a.part + (size_t)blockIdx.x * NPOL_PAD);
     if (timed_out && a.status) atomicOr(a.status, SIM_FLAG_TIMEOUT);
     return;
@@ -1205,111 +1394,46 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
   // smoothness adjoint carried from step k + 1 to a_k: -2 sd w_dact (a_{k+1} - a_k)
   float carry[4] = {0.f, 0.f, 0.f, 0.f};
   int t = 0;  // reverse steps processed so far (the weight-gradient warps count alike)
-  // wait until the weight-gradient warps have read the tiles of processing step u
-  auto wait_read = [&](int u) {
-    if (u >= 0) wait_on(&s.empty[(a.H - 1 - u) & 1], (uint32_t)((u >> 1) & 1));
-  };
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int k0 = sg * a.C, k1 = min(a.H, k0 + a.C);
-    // the recompute stages its tiles in both buffers: every earlier step's tiles
-    // must have been read
-    wait_read(t - 1);
-    wait_read(t - 2);
-    float x[17];
-    load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
-    float4 ap4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (OBJ == SIM_OBJ_TRACKING_REWARD) ap4 = a.ckpt_a[(size_t)sg * a.n + ii];
-    // recompute the segment's states; the reference positions of steps k, k + 1
-    // and k + 2 are carried in registers, each loaded two steps before its use
-    float rr[3], rr1[3];
-    ref_at(a.p_ref, k0, a.n, ii, rr);
-    ref_at(a.p_ref, k0 + 1, a.n, ii, rr1);
-    for (int k = k0; k < k1; ++k) {
-      if (valid && lane < 16) {
-        store_row(a.seg + (size_t)(k - k0) * a.R * a.n * 20, i, x);
-        if (OBJ == SIM_OBJ_TRACKING_REWARD) a.seg_a[(size_t)(k - k0) * a.n + i] = ap4;
-      }
-      float rr2[3] = {0.f, 0.f, 0.f};
-      if (k + 2 <= a.H) ref_at_pinned(a.p_ref, k + 2, a.n, ii, rr2);
-      if (lane < 16) put_obs(s.obs, row, x, rr);
-      // this step's h2 and actions, kept for the reverse sweep: staged in buffer
-      // b = k & 1, whose copy-out two steps ago must have read it, then copied out.
-      // The segment's last two steps stay in their buffers, with h1, for the first
-      // two reverse steps (the copy-out before them must have read everything).
-      const int b = k & 1;
-      const bool last2 = k >= k1 - 2;
-      if (k - k0 >= 2 && lane == 0) {
-        if (last2) bulk_wait_read<0>();
-        else bulk_wait_read<1>();
-      }
-      __syncwarp();
-      {
-        float h1[8][4], h2[8][4];
-        mlp_forward<LO>(s, r0, lane, h1, h2, s.actb[b]);
-        store_c64(s.h2[b], r0, lane, h2);
-        if (last2) store_c64(s.h1[b], r0, lane, h1);
-      }
-      if (last2 && lane < 16) put_obs(s.obsr[b], row, x, rr);
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0 && !last2) cache_store(s, b, r0, cache_at(v, k - k0));
-      float act[4] = {s.actb[b][row][0], s.actb[b][row][1], s.actb[b][row][2], s.actb[b][row][3]};
-      __syncwarp();
-      for (int j = 0; j < a.R; ++j) {
-        if (j > 0 && valid && lane < 16)
-          store_row(a.seg + ((size_t)(k - k0) * a.R + j) * a.n * 20, i, x);
-        policy_step(x, act, P, a.dt);
-      }
-      ap4 = make_float4(act[0], act[1], act[2], act[3]);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        rr[c] = rr1[c];
-        rr1[c] = rr2[c];
-      }
-    }
-    // the state after policy step k: x_{k1} from the recompute above, then the
-    // state loaded one iteration earlier
-    float xn[17];
-#pragma unroll
-    for (int j = 0; j < 17; ++j) xn[j] = x[j];
-    // reverse sweep.  Step k's state row, reference and previous action are
-    // prefetched during step k + 1.  Padded rows never read rows written by
-    // other warps: they replay the checkpoint row (finite data; their seed and
-    // dz rows are zero).
+    wait_on(&s.seg_done[sg & 1], seg_phase(sg));
+    const float* rows = seg_rows(sg);
+    // the state after the segment and the reference at that step (the loss term of
+    // the segment's last step); padded rows read the checkpoint instead (finite
+    // data; their seed is zero) and never rows written by other warps
+    float xn[17], rn[3];
+    if (valid) load_row(rows + (size_t)(k1 - k0) * a.R * a.n * 20, i, xn);
+    else load_row(a.ckpt + (size_t)sg * a.n * 20, ii, xn);
+    ref_at(a.p_ref, k1, a.n, ii, rn);
+    // step k's state row, step record and previous action, prefetched during step
+    // k + 1 (padded rows take the last drone's record: finite, published with the
+    // segment like every row)
     auto prefetch_step = [&](int k) {
       float* bx = s.pre_x[k & 1][row];
-      if (valid) prefetch_row(bx, a.seg + (size_t)(k - k0) * a.R * a.n * 20, i);
+      if (valid) prefetch_row(bx, rows + (size_t)(k - k0) * a.R * a.n * 20, i);
       else prefetch_row(bx, a.ckpt + (size_t)sg * a.n * 20, ii);
-      prefetch_ref(s.pre_r[k & 1][row], a.p_ref, k, a.n, ii);
+      prefetch_row(s.pre_q[k & 1][row], seg_recs(sg) + (size_t)(k - k0) * a.R * a.n * FQ_FLOATS, ii);
       if (OBJ == SIM_OBJ_TRACKING_REWARD)
-        cp_async16(&s.pre_a[k & 1][row], valid ? &a.seg_a[(size_t)(k - k0) * a.n + i]
+        cp_async16(&s.pre_a[k & 1][row], valid ? &seg_prev(sg)[(size_t)(k - k0) * a.n + i]
                                                : &a.ckpt_a[(size_t)sg * a.n + ii]);
     };
-    // the segment's cache entries are complete before the weight-gradient warps
-    // copy them back (they wait for this warp's arrivals on full[] first); steps
-    // k1 - 1 and k1 - 2 are in their buffers already
-    if (lane == 0) {
-      bulk_wait_all();
-      fence_proxy_async_global();
-    }
-    mbar_arrive(&s.ready[v][(k1 - 1) & 1]);
-    if (k1 - 2 >= k0) mbar_arrive(&s.ready[v][(k1 - 2) & 1]);
-    // the reference at policy step k + 1, carried like xn (the recompute ends with
-    // the one at k1)
-    float rn[3] = {rr[0], rr[1], rr[2]};
-    __threadfence_block();  // this thread's segment rows precede its async copies of them
     if (lane < 16) prefetch_step(k1 - 1);
     cp_async_commit();
+    // the reference at step k, loaded during step k + 1
+    float rnext[3];
+    ref_at(a.p_ref, k1 - 1, a.n, ii, rnext);
     for (int k = k1 - 1; k >= k0; --k, ++t) {
       const int b = k & 1;
-      cp_async_wait_all();  // this step's state row, reference and previous action
-      // this step's tiles and actions; the buffer's previous contents were read
-      // by the weight-gradient warps before the copy was issued
+      cp_async_wait_all();  // this step's state row, step record and previous action
+      // this step's tiles and actions, prepared by the weight-gradient warp after
+      // all four of them had read the buffer's previous contents
       wait_on(&s.ready[v][b], (uint32_t)((t >> 1) & 1));
       __syncwarp();
+      float x[17];
 #pragma unroll
       for (int j = 0; j < 17; ++j) x[j] = s.pre_x[b][row][j];
-      const float r[3] = {s.pre_r[b][row][0], s.pre_r[b][row][1], s.pre_r[b][row][2]};
+      const float r[3] = {rnext[0], rnext[1], rnext[2]};
+      if (k > k0) ref_at(a.p_ref, k - 1, a.n, ii, rnext);
       float ap[4] = {0.f, 0.f, 0.f, 0.f};
       if (OBJ == SIM_OBJ_TRACKING_REWARD) {
         const float4 q = s.pre_a[b][row];
@@ -1320,25 +1444,46 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       }
       if (k > k0 && lane < 16) prefetch_step(k - 1);
       cp_async_commit();
-      // this step's observation rows (the dW1 operand) are in obsr[b] already: written
-      // with its activations by the weight-gradient warp, or by the recompute
+      // this step's observation rows (the dW1 operand) are in obsr[b] already, written
+      // with its activations by the weight-gradient warp that prepared the step
       const float act[4] = {s.actb[b][row][0], s.actb[b][row][1], s.actb[b][row][2], s.actb[b][row][3]};
       // loss term at policy step k + 1 (state after the last sub-step)
       step_loss_state_adjoint<OBJ>(xn, rn, seed, a, lam);
-      // back through the R sub-steps; the held action collects every sub-step's adjoint
+      // back through the R sub-steps (states before and after each, and its record);
+      // the held action collects every sub-step's adjoint
       float ga[4] = {0.f, 0.f, 0.f, 0.f};
+      float xq[17];
+#pragma unroll
+      for (int q = 0; q < 17; ++q) xq[q] = xn[q];
       for (int j = a.R - 1; j >= 0; --j) {
-        float xs[17];
-        if (j > 0 && valid) {
-          load_row(a.seg + ((size_t)(k - k0) * a.R + j) * a.n * 20, i, xs);
+        float xs[17], fq[FQ_FLOATS];
+        if (j > 0) {
+          if (valid) load_row(rows + ((size_t)(k - k0) * a.R + j) * a.n * 20, i, xs);
+          else load_row(a.ckpt + (size_t)sg * a.n * 20, ii, xs);
+          const float4* f4 = reinterpret_cast<const float4*>(
+              seg_recs(sg) + (((size_t)(k - k0) * a.R + j) * a.n + ii) * FQ_FLOATS);
+#pragma unroll
+          for (int c = 0; c < 5; ++c) {
+            const float4 u = f4[c];
+            fq[4 * c] = u.x;
+            fq[4 * c + 1] = u.y;
+            fq[4 * c + 2] = u.z;
+            fq[4 * c + 3] = u.w;
+          }
         } else {
 #pragma unroll
           for (int q = 0; q < 17; ++q) xs[q] = x[q];
+#pragma unroll
+          for (int c = 0; c < FQ_FLOATS; ++c) fq[c] = s.pre_q[b][row][c];
         }
+        StepRecord rec;
+        record_from(fq, rec);
         float gj[4];
-        policy_step_adjoint(xs, act, lam, gj, P, a.dt);
+        policy_step_adjoint(xs, xq, rec, act, lam, gj, P, a.dt);
 #pragma unroll
         for (int o = 0; o < 4; ++o) ga[o] += gj[o];
+#pragma unroll
+        for (int q = 0; q < 17; ++q) xq[q] = xs[q];
       }
       if (OBJ == SIM_OBJ_SQUARED) {
 #pragma unroll
@@ -1379,12 +1524,6 @@ __global__ void __launch_bounds__(2 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       for (int c = 0; c < 3; ++c) rn[c] = r[c];
     }
   }
-  wait_read(t - 1);  // the weight-gradient warps finish before the CTA's memory is released
-  wait_read(t - 2);
-  // no bulk load into this warp's rows may be in flight at exit (bounded, even
-  // after a timeout): the last two deliveries, already consumed unless one was skipped
-  for (int u = t - 2; u < t; ++u)
-    if (u >= 0 && !mbar_wait(&s.ready[v][(a.H - 1 - u) & 1], (uint32_t)((u >> 1) & 1))) timed_out = true;
   if (valid && lane < 16) {
     float4* p = reinterpret_cast<float4*>(a.dx0 + (size_t)i * 20);
 #pragma unroll
@@ -1455,9 +1594,10 @@ size_t rollout_workspace_bytes(int n, int H, int C, int objective, int R) {
   const int n_ck = (H + C - 1) / C;
   const int n_cta = (n + ro::DPC - 1) / ro::DPC;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  size_t b = al((size_t)n_ck * n * 20 * 4) + al((size_t)C * R * n * 20 * 4) + al((size_t)n * 4) +
-             al((size_t)n_cta * ro::NPOL_PAD * 4) + al((size_t)C * n_cta * 4 * ro::CACHE_CHUNKS * 16);
-  if (objective == SIM_OBJ_TRACKING_REWARD) b += al((size_t)n_ck * n * 16) + al((size_t)C * n * 16);
+  size_t b = al((size_t)n_ck * n * 20 * 4) + al((size_t)2 * (C * R + 1) * n * 20 * 4) +
+             al((size_t)2 * C * R * n * ro::FQ_FLOATS * 4) + al((size_t)n * 4) +
+             al((size_t)n_cta * ro::NPOL_PAD * 4) + al((size_t)2 * C * n_cta * 4 * ro::CACHE_BYTES);
+  if (objective == SIM_OBJ_TRACKING_REWARD) b += al((size_t)n_ck * n * 16) + al((size_t)2 * C * n * 16);
   return b;
 }
 
@@ -1470,13 +1610,15 @@ static void carve(void* ws, int n, int H, int C, int R, const RolloutObjective& 
   a.ckpt = (float*)p;
   p += al((size_t)n_ck * n * 20 * 4);
   a.seg = (float*)p;
-  p += al((size_t)C * R * n * 20 * 4);
+  p += al((size_t)2 * (C * R + 1) * n * 20 * 4);
+  a.seg_q = (float*)p;
+  p += al((size_t)2 * C * R * n * ro::FQ_FLOATS * 4);
   a.loss_w = (float*)p;
   p += al((size_t)n * 4);
   a.part = (float*)p;
   p += al((size_t)n_cta * ro::NPOL_PAD * 4);
   a.hcache = (uint4*)p;
-  p += al((size_t)C * n_cta * 4 * ro::CACHE_CHUNKS * 16);
+  p += al((size_t)2 * C * n_cta * 4 * ro::CACHE_BYTES);
   if (obj.kind == SIM_OBJ_TRACKING_REWARD) {
     a.ckpt_a = (float4*)p;
     p += al((size_t)n_ck * n * 16);
@@ -1551,10 +1693,10 @@ cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* 
   a.inv_n = 1.f / (float)n;
   const int grid = (n + ro::DPC - 1) / ro::DPC;
   cudaError_t e = obj.kind == SIM_OBJ_TRACKING_REWARD
-                      ? (obj.hilo ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_TRACKING_REWARD, true>, grid, a, P, st, 2 * ro::TPB)
-                                  : launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_TRACKING_REWARD, false>, grid, a, P, st, 2 * ro::TPB))
-                      : (obj.hilo ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED, true>, grid, a, P, st, 2 * ro::TPB)
-                                  : launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED, false>, grid, a, P, st, 2 * ro::TPB));
+                      ? (obj.hilo ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_TRACKING_REWARD, true>, grid, a, P, st, 3 * ro::TPB)
+                                  : launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_TRACKING_REWARD, false>, grid, a, P, st, 3 * ro::TPB))
+                      : (obj.hilo ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED, true>, grid, a, P, st, 3 * ro::TPB)
+                                  : launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED, false>, grid, a, P, st, 3 * ro::TPB));
   if (e != cudaSuccess) return e;
   ro::reduce_dw_kernel<<<(ro::NPOL + 255) / 256, 256, 0, st>>>(a.part, grid, dW);
   return cudaGetLastError();

@@ -88,7 +88,7 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
     cap = ctypes.c_size_t()
     lib = L.load()
     assert lib.sim_rollout_noalloc_max_bytes(ctypes.byref(cap)) == L.SIM_OK
-    M, H, C = 8192, 250, 25  # needs ~88 MB of scratch
+    M, H, C = 8192, 250, 25  # needs ~170 MB of scratch
     sim = Sim(M, 1, FIRST_PRINCIPLES, EULER, 1 / 500)
     sim.set_params(W.crazyflie_params())
     need = ctypes.c_size_t()
