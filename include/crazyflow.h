@@ -484,7 +484,11 @@ int sim_rollout_fwd(sim_h h, const float* x0, const uint16_t* w, const float* p_
 int sim_rollout_bwd(sim_h h, const float* x0, const uint16_t* w, const float* p_ref, int H, int C,
                     float w_act, void* ws, size_t ws_bytes, const float* dL, float* dW, float* dx0,
                     void* stream);
-/* Forward and backward in one call with dL = 1 (dL_one: device scalar holding 1.0f). */
+/* Forward and backward in one call with dL = 1 (dL_one: device scalar holding 1.0f).
+ * One adjoint launch whose recompute warps run the forward pass first, then the
+ * loss and dW reductions: loss, dW and dx0 equal those of sim_rollout_fwd followed
+ * by sim_rollout_bwd bit for bit, and the workspace holds the same checkpoints
+ * afterwards (sim_rollout_bwd may follow with another dL). */
 int sim_rollout_grad(sim_h h, const float* x0, const uint16_t* w, const float* p_ref, int H, int C,
                      float w_act, void* ws, size_t ws_bytes, float* loss, const float* dL_one,
                      float* dW, float* dx0, void* stream);

@@ -39,6 +39,12 @@ cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* 
                                int C, int R, float dt, float w_act, const RolloutObjective& obj,
                                const DevParams& P, void* ws, const float* dL, float* dW, float* dx0,
                                uint32_t* status, cudaStream_t st);
+// Forward and adjoint in one adjoint launch (its recompute warps run the forward
+// pass first), then the loss and dW reductions.
+cudaError_t launch_rollout_grad(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
+                                int C, int R, float dt, float w_act, const RolloutObjective& obj,
+                                const DevParams& P, void* ws, float* loss, const float* dL, float* dW,
+                                float* dx0, uint32_t* status, cudaStream_t st);
 
 // Batched sampling rollouts (sample.cu).
 cudaError_t launch_sample(const float4* planes, int n, const int* offsets, int M, int N,

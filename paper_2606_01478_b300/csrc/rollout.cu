@@ -96,6 +96,7 @@ struct RolloutArgs {
   float4* ckpt_a;         // [n_ckpt][n] previous action at each checkpoint (reward objective)
   float4* seg_a;          // [2][C][n] previous action of each segment step (reward objective)
   int n, H, C, R;
+  int fused;              // adjoint kernel: run the forward pass first (sim_rollout_grad)
   float dt, w_act, inv_n;
   float w_theta, w_a[4], w_da[4];  // tracking-reward weights
   int store_ckpt;
@@ -708,7 +709,7 @@ __device__ __forceinline__ void policy_step_rec(float* x, const float a[4], cons
     Wc[r] = sqrt_approx(clampf(f[r], 0.f, P.fmax) * P.inv_kf);
     // W = sqrt(f / kf): dW/df = 1 / (2 kf W) inside the clip
     const bool pass = f[r] >= 0.f && f[r] <= P.fmax && Wc[r] > 0.f;
-    q.gWf[r] = pass ? P.inv_kf * 0.5f / Wc[r] : 0.f;
+    q.gWf[r] = pass ? __fdividef(0.5f * P.inv_kf, Wc[r]) : 0.f;
   }
   float d[17];
   deriv_fp<MOTOR_LAG>(x, Wc, P, false, d);
@@ -1252,15 +1253,29 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
   const int ii = valid ? i : a.n - 1;
   if (warp >= 8) {
     // ---------------- recompute warps
-    for (int sg = nseg - 1; sg >= 0; --sg) {
+    // Jobs in order: with a.fused, first the forward pass over all segments
+    // (checkpoints, per-drone loss; its last segment is recorded for the reverse
+    // sweep as a recompute would record it), then the recomputes of the segments
+    // before it from their checkpoints, last first.  One loop body serves both.
+    const int nrec = a.fused ? nseg - 1 : nseg;  // segments recomputed from checkpoints
+    const int njobs = a.fused ? nseg + nrec : nrec;
+    float x[17];
+    float4 ap4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float loss = 0.f;
+    for (int job = 0; job < njobs; ++job) {
+      const bool fwd = a.fused && job < nseg;
+      const int sg = fwd ? job : nrec - 1 - (a.fused ? job - nseg : job);
+      const bool record = !fwd || sg == nseg - 1;
       const int k0 = sg * a.C, k1 = min(a.H, k0 + a.C);
       // the buffer's previous segment (sg + 2) has been swept
-      if (sg + 2 < nseg) wait_on(&s.seg_free[sg & 1], seg_phase(sg + 2));
+      if (record && sg + 2 < nseg) wait_on(&s.seg_free[sg & 1], seg_phase(sg + 2));
       float* rows = seg_rows(sg);
-      float x[17];
-      load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
-      float4 ap4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (OBJ == SIM_OBJ_TRACKING_REWARD) ap4 = a.ckpt_a[(size_t)sg * a.n + ii];
+      if (!fwd) {
+        load_row(a.ckpt + (size_t)sg * a.n * 20, ii, x);
+        if (OBJ == SIM_OBJ_TRACKING_REWARD) ap4 = a.ckpt_a[(size_t)sg * a.n + ii];
+      } else if (sg == 0) {
+        load_row(a.x0, ii, x);
+      }
       // reference positions of steps k, k + 1 and k + 2 in registers, each loaded
       // two steps before its use
       float rr[3], rr1[3];
@@ -1268,8 +1283,14 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       ref_at(a.p_ref, k0 + 1, a.n, ii, rr1);
       for (int k = k0; k < k1; ++k) {
         if (valid && lane < 16) {
-          store_row(rows + (size_t)(k - k0) * a.R * a.n * 20, i, x);
-          if (OBJ == SIM_OBJ_TRACKING_REWARD) seg_prev(sg)[(size_t)(k - k0) * a.n + i] = ap4;
+          if (fwd && k == k0) {
+            store_row(a.ckpt + (size_t)sg * a.n * 20, i, x);
+            if (OBJ == SIM_OBJ_TRACKING_REWARD) a.ckpt_a[(size_t)sg * a.n + i] = ap4;
+          }
+          if (record) {
+            store_row(rows + (size_t)(k - k0) * a.R * a.n * 20, i, x);
+            if (OBJ == SIM_OBJ_TRACKING_REWARD) seg_prev(sg)[(size_t)(k - k0) * a.n + i] = ap4;
+          }
         }
         float rr2[3] = {0.f, 0.f, 0.f};
         if (k + 2 <= a.H) ref_at_pinned(a.p_ref, k + 2, a.n, ii, rr2);
@@ -1279,17 +1300,23 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
         {
           float h1[8][4], h2[8][4];
           mlp_forward<LO>(s, r0, lane, h1, h2, s.act);
-          cache_put(s, v, r0, lane, h2, cache_at(sg & 1, v, k - k0));  // has warp barriers
+          if (record) cache_put(s, v, r0, lane, h2, cache_at(sg & 1, v, k - k0));  // has warp barriers
+          else __syncwarp();
 #pragma unroll
           for (int o = 0; o < 4; ++o) act[o] = s.act[row][o];
         }
         __syncwarp();  // the observation and action rows are rewritten next step
         for (int j = 0; j < a.R; ++j) {
-          if (j > 0 && valid && lane < 16)
+          if (record && j > 0 && valid && lane < 16)
             store_row(rows + ((size_t)(k - k0) * a.R + j) * a.n * 20, i, x);
           StepRecord q;
           policy_step_rec(x, act, P, a.dt, q);
-          if (valid && lane < 16) store_record(seg_recs(sg) + ((size_t)(k - k0) * a.R + j) * a.n * FQ_FLOATS, i, q);
+          if (record && valid && lane < 16)
+            store_record(seg_recs(sg) + ((size_t)(k - k0) * a.R + j) * a.n * FQ_FLOATS, i, q);
+        }
+        if (fwd) {
+          const float ap[4] = {ap4.x, ap4.y, ap4.z, ap4.w};
+          loss += step_loss<OBJ>(x, rr1, act, ap, a);
         }
         ap4 = make_float4(act[0], act[1], act[2], act[3]);
 #pragma unroll
@@ -1298,15 +1325,18 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
           rr1[c] = rr2[c];
         }
       }
-      // the state after the segment (the loss term of its last step)
-      if (valid && lane < 16) store_row(rows + (size_t)(k1 - k0) * a.R * a.n * 20, i, x);
-      // the segment's cache entries are complete before its readers copy them back
-      // (they wait for these arrivals first)
-      if (lane == 0) {
-        bulk_wait_all();
-        fence_proxy_async_global();
+      if (fwd && sg == nseg - 1 && valid && lane < 16) a.loss_w[i] = loss;
+      if (record) {
+        // the state after the segment (the loss term of its last step)
+        if (valid && lane < 16) store_row(rows + (size_t)(k1 - k0) * a.R * a.n * 20, i, x);
+        // the segment's cache entries are complete before its readers copy them
+        // back (they wait for these arrivals first)
+        if (lane == 0) {
+          bulk_wait_all();
+          fence_proxy_async_global();
+        }
+        mbar_arrive(&s.seg_done[sg & 1]);  // release: this thread's rows
       }
-      mbar_arrive(&s.seg_done[sg & 1]);  // release: this thread's rows
     }
     if (timed_out && a.status) atomicOr(a.status, SIM_FLAG_TIMEOUT);
     return;
@@ -1673,10 +1703,12 @@ cudaError_t launch_rollout_fwd(const float* x0, const uint16_t* w, const float* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
-                               int C, int R, float dt, float w_act, const RolloutObjective& obj,
-                               const DevParams& P, void* ws, const float* dL, float* dW, float* dx0,
-                               uint32_t* status, cudaStream_t st) {
+// The adjoint launch; with loss != null it runs the forward pass first (fused) and
+// reduces the loss after it.
+static cudaError_t rollout_adjoint(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
+                                   int C, int R, float dt, float w_act, const RolloutObjective& obj,
+                                   const DevParams& P, void* ws, const float* dL, float* dW, float* dx0,
+                                   uint32_t* status, float* loss, cudaStream_t st) {
   ro::RolloutArgs a{};
   carve(ws, n, H, C, R, obj, a);
   a.status = status;
@@ -1691,6 +1723,7 @@ cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* 
   a.w_act = w_act;
   a.dL = dL;
   a.inv_n = 1.f / (float)n;
+  a.fused = loss != nullptr;
   const int grid = (n + ro::DPC - 1) / ro::DPC;
   cudaError_t e = obj.kind == SIM_OBJ_TRACKING_REWARD
                       ? (obj.hilo ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_TRACKING_REWARD, true>, grid, a, P, st, 3 * ro::TPB)
@@ -1698,8 +1731,23 @@ cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* 
                       : (obj.hilo ? launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED, true>, grid, a, P, st, 3 * ro::TPB)
                                   : launch_rollout_kernel(ro::rollout_bwd_kernel<SIM_OBJ_SQUARED, false>, grid, a, P, st, 3 * ro::TPB));
   if (e != cudaSuccess) return e;
+  if (loss) ro::reduce_loss_kernel<<<1, 256, 0, st>>>(a.loss_w, n, loss);
   ro::reduce_dw_kernel<<<(ro::NPOL + 255) / 256, 256, 0, st>>>(a.part, grid, dW);
   return cudaGetLastError();
+}
+
+cudaError_t launch_rollout_bwd(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
+                               int C, int R, float dt, float w_act, const RolloutObjective& obj,
+                               const DevParams& P, void* ws, const float* dL, float* dW, float* dx0,
+                               uint32_t* status, cudaStream_t st) {
+  return rollout_adjoint(x0, w, p_ref, n, H, C, R, dt, w_act, obj, P, ws, dL, dW, dx0, status, nullptr, st);
+}
+
+cudaError_t launch_rollout_grad(const float* x0, const uint16_t* w, const float* p_ref, int n, int H,
+                                int C, int R, float dt, float w_act, const RolloutObjective& obj,
+                                const DevParams& P, void* ws, float* loss, const float* dL, float* dW,
+                                float* dx0, uint32_t* status, cudaStream_t st) {
+  return rollout_adjoint(x0, w, p_ref, n, H, C, R, dt, w_act, obj, P, ws, dL, dW, dx0, status, loss, st);
 }
 
 }  // namespace cf

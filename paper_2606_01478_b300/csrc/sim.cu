@@ -747,9 +747,17 @@ int sim_rollout_bwd(sim_h h, const float* x0, const uint16_t* w, const float* p_
 int sim_rollout_grad(sim_h h, const float* x0, const uint16_t* w, const float* p_ref, int H, int C,
                      float w_act, void* ws, size_t ws_bytes, float* loss, const float* dL_one,
                      float* dW, float* dx0, void* stream) {
-  int r = sim_rollout_fwd(h, x0, w, p_ref, H, C, w_act, ws, ws_bytes, loss, stream);
+  if (!h) return SIM_EINVAL;
+  int r = rollout_check(h, H, C, ws, ws_bytes, {x0, w, p_ref, loss, dL_one, dW, dx0});
   if (r != SIM_OK) return r;
-  return sim_rollout_bwd(h, x0, w, p_ref, H, C, w_act, ws, ws_bytes, dL_one, dW, dx0, stream);
+  // one adjoint launch whose recompute warps run the forward pass first: the
+  // reverse sweep starts as soon as the last segment is stepped
+  cudaError_t e = cf::launch_rollout_grad(x0, w, p_ref, (int)h->ntot, H, C, h->rollout_repeat, h->dt,
+                                          w_act, h->objective, h->p0, ws, loss, dL_one, dW, dx0,
+                                          h->status, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "rollout gradient launch");
+  h->launches += 3;
+  return SIM_OK;
 }
 
 int sim_adam_step(const float* grad, float* w, float* m, float* v, uint16_t* w_bf16, int64_t n,

@@ -123,6 +123,36 @@ def test_rollout_deterministic():
         assert torch.equal(u, v)
 
 
+@pytest.mark.parametrize("M,H,C,repeat,reward,prec", [
+    (300, 40, 10, 1, None, "hilo"),            # ragged last CTA, four segments
+    (100, 23, 5, 1, TRACKING_REWARD, "hilo"),  # ragged last segment, tracking reward
+    (64, 7, 7, 1, None, "bf16"),               # one segment: the forward pass records it
+    (70, 12, 6, 10, TRACKING_REWARD, "bf16"),  # two segments, actions held for 10 steps
+])
+def test_fused_gradient_equals_forward_then_backward(M, H, C, repeat, reward, prec):
+    """sim_rollout_grad runs the forward pass inside the adjoint launch; its loss,
+    dW and dx0 equal sim_rollout_fwd followed by sim_rollout_bwd bit for bit, and a
+    backward after it (from the checkpoints it left) gives the same again."""
+    rw = W.policy_bptt(seed=35, M=M, H=H, C=C, repeat=repeat)
+    sim = Sim(rw.M, 1, FIRST_PRINCIPLES, EULER, rw.dt)
+    sim.set_params(rw.params)
+    runner = PolicyRollout(sim, rw.H, rw.C, rw.w_act, reward=reward, action_repeat=rw.repeat, precision=prec)
+    x0 = torch.tensor(rw.x0, dtype=torch.float32, device="cuda")
+    wb = torch.tensor(po.pack(rw.weights), dtype=torch.float32, device="cuda").to(torch.bfloat16)
+    p_ref = torch.tensor(rw.p_ref, dtype=torch.float32, device="cuda").contiguous()
+    one = torch.ones(1, device="cuda")
+    loss_f = runner.forward(x0, wb, p_ref)
+    dW_s, dx_s = runner.backward(x0, wb, p_ref, one)
+    loss_g, dW_g, dx_g = runner.grad(x0, wb, p_ref)
+    dW_b, dx_b = runner.backward(x0, wb, p_ref, one)
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+    assert torch.isfinite(dW_g).all() and torch.isfinite(dx_g).all()
+    assert torch.equal(loss_f, loss_g)
+    for a, b in ((dW_s, dW_g), (dx_s, dx_g), (dW_s, dW_b), (dx_s, dx_b)):
+        assert torch.equal(a, b)
+
+
 def test_autograd_function_matches_direct_call():
     rw = W.policy_bptt(seed=34, M=128, H=20, C=5)
     sim, runner, x0, w, p_ref = _gpu_inputs(rw)
