@@ -772,7 +772,7 @@ def _time_ms(fn, reps: int, dev) -> float:
 MLP_FLOP = 2.0 * (13 * 64 + 64 * 64 + 64 * 4)
 
 
-def measure_policy_bptt(dev, reps: int = 3) -> dict:
+def measure_policy_bptt(dev, reps: int = 9) -> dict:
     """The BPTT workload (8192 drones, policy MLP in the loop, Euler at 500 Hz, H = 250,
     checkpoints every C = 25): forward rollout, forward + adjoint (BPTT), and
     plain forward stepping of the same drones without the policy."""
