@@ -1190,11 +1190,12 @@ __global__ void wait_selftest_kernel(uint32_t* status) {
 // The adjoint runs three warp roles per CTA, each role one warp per 16-drone block.
 // Warps 8-11 (recompute) run one segment ahead of the reverse sweep: from the
 // segment's checkpoint they step its states forward with the policy in the loop and
-// write the states (segment rows, and the state after the segment) and each step's h2
-// and actions (the activation cache) for the segment buffer of the segment's parity.
-// Warps 0-3 (compute) sweep a recomputed segment in reverse: per step the loss and
-// step adjoints and the MLP backward, which leave the step's dz tiles in shared
-// memory.  Warps 4-7 (weight gradient) accumulate dW over the CTA's 64 drones from
+// write the states (segment rows, and the state after the segment), each step's
+// record of forward quantities (StepRecord) and each step's h2 and actions (the
+// activation cache) into the segment buffer of the segment's parity; launched for
+// sim_rollout_grad (a.fused) they first run the forward pass itself.  Warps 0-3
+// (compute) sweep a recomputed segment in reverse: per step the loss and step
+// adjoints and the MLP backward, which leave the step's dz tiles in shared memory.  Warps 4-7 (weight gradient) accumulate dW over the CTA's 64 drones from
 // those tiles while the compute warps already run the next (earlier) step, and then
 // prepare step k - 2 for compute warp v's drones in the freed buffer: h2 and the
 // actions come back from the cache, h1 is recomputed from the segment state (one
@@ -1232,7 +1233,8 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
   auto wait_on = [&](unsigned long long* m, uint32_t par) {
     if (!timed_out && !mbar_wait(m, par)) timed_out = true;
   };
-  // segment buffers of parity p: rows [C R + 1][n][20], previous actions [C][n]
+  // segment buffers of parity p: rows [C R + 1][n][20], step records [C R][n][20],
+  // previous actions [C][n] (tracking reward), activation cache [C][n / 16][CACHE_CHUNKS]
   const size_t seg_stride = (size_t)(a.C * a.R + 1) * a.n * 20;
   auto seg_rows = [&](int sg) { return a.seg + (size_t)(sg & 1) * seg_stride; };
   auto seg_prev = [&](int sg) { return a.seg_a + (size_t)(sg & 1) * a.C * a.n; };
@@ -1430,7 +1432,8 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
     const float* rows = seg_rows(sg);
     // the state after the segment and the reference at that step (the loss term of
     // the segment's last step); padded rows read the checkpoint instead (finite
-    // data; their seed is zero) and never rows written by other warps
+    // data; their seed is zero).  Everything read here was published with the
+    // segment (seg_done), checkpoints included
     float xn[17], rn[3];
     if (valid) load_row(rows + (size_t)(k1 - k0) * a.R * a.n * 20, i, xn);
     else load_row(a.ckpt + (size_t)sg * a.n * 20, ii, xn);
