@@ -1360,8 +1360,8 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
     int seen = nseg;  // lowest segment whose recompute this warp has waited for
     int last[2] = {-1, -1};  // processing order of the last copy issued into buffer 0, 1
     float px[17], pr[3];
-    auto prep_load = [&](int tp) {
-      const int k = a.H - 1 - tp, sg = k / a.C, k0 = sg * a.C;
+    // step k of segment sg (first step k0) is prepared as processing step tp
+    auto prep_load = [&](int k, int sg, int k0) {
       if (sg < seen) {
         wait_on(&s.seg_done[sg & 1], seg_phase(sg));
         seen = sg;
@@ -1370,8 +1370,8 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       else load_row(a.ckpt + (size_t)sg * a.n * 20, ii, px);
       ref_at(a.p_ref, k, a.n, ii, pr);
     };
-    auto prep_store = [&](int tp) {
-      const int k = a.H - 1 - tp, b = k & 1, sg = k / a.C, k0 = sg * a.C;
+    auto prep_store = [&](int k, int sg, int k0, int tp) {
+      const int b = k & 1;
       if (lane == 0) {
         fence_proxy_async_global();
         cache_load(s, b, r0, cache_at(sg & 1, v, k - k0), &s.ready[v][b]);
@@ -1384,30 +1384,42 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       store_c64(s.h1[b], r0, lane, h1);
       mbar_arrive(&s.ready[v][b]);  // with the copied bytes, completes the phase
     };
+    // segments (and their first steps) of the step accumulated (k) and of the one
+    // prepared (k - 2), followed as k decreases by one per iteration
+    int sg = (a.H - 1) / a.C, k0 = sg * a.C;
+    int sgp = sg, k0p = k0;
     // t = -2, -1 only prepare the first two steps (one copy of the code for all)
     for (int t = -2; t < a.H; ++t) {
-      const int k = a.H - 1 - t, b = k & 1, sg = k / a.C;
+      const int k = a.H - 1 - t, b = k & 1, kp = k - 2;
       const uint32_t par = (uint32_t)((t >> 1) & 1);
       const bool work = t >= 0, ahead = t + 2 < a.H;
+      if (ahead && kp < k0p) {
+        --sgp;
+        k0p -= a.C;
+      }
       if (work) {
         wait_on(&s.full[b], par);
         // the compute warp has consumed step k's cache entry: drop its L2 lines
         // without a write-back; the fence orders the discards before the bulk
         // stores that reuse the entry two segments later (issued after seg_free)
-        cache_discard(cache_at(sg & 1, v, k - sg * a.C), lane);
+        cache_discard(cache_at(sg & 1, v, k - k0), lane);
         fence_proxy_async_global();
         // the compute warps are done with the segment once they finish its first
         // step; so is this warp (its loads of the segment were two steps earlier)
-        if (k == sg * a.C) mbar_arrive(&s.seg_free[sg & 1]);
+        if (k == k0) mbar_arrive(&s.seg_free[sg & 1]);
       }
-      if (ahead) prep_load(t + 2);
+      if (ahead) prep_load(kp, sgp, k0p);
       if (work) {
         accumulate_dw<LO>(s, v, lane, acc, b);
         mbar_arrive(&s.empty[b]);
       }
       if (ahead) {
         if (work) wait_on(&s.empty[b], par);
-        prep_store(t + 2);
+        prep_store(kp, sgp, k0p, t + 2);
+      }
+      if (work && k == k0) {
+        --sg;
+        k0 -= a.C;
       }
     }
     // the compute warp consumes every copy issued here; wait (bounded) for the last
