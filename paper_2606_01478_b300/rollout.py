@@ -112,7 +112,8 @@ class PolicyRollout:
 
     @on_device
     def grad(self, x0, w_bf16, p_ref, stream=None, loss=None, dW=None, dx0=None):
-        """Loss, dL/dw and dL/dx0 in one call (forward + backward kernels)."""
+        """Loss, dL/dw and dL/dx0 in one call (sim_rollout_grad: one adjoint launch that
+        runs the forward pass first, then the loss and dW reductions)."""
         self._check_inputs(x0, w_bf16, p_ref)
         dev = self.sim.device
         loss = torch.empty(1, dtype=torch.float32, device=dev) if loss is None else loss
