@@ -128,6 +128,9 @@ def test_rollout_deterministic():
     (100, 23, 5, 1, TRACKING_REWARD, "hilo"),  # ragged last segment, tracking reward
     (64, 7, 7, 1, None, "bf16"),               # one segment: the forward pass records it
     (70, 12, 6, 10, TRACKING_REWARD, "bf16"),  # two segments, actions held for 10 steps
+    (1, 1, 1, 1, None, "hilo"),                # one drone (63 padded rows), one step
+    (33, 2, 1, 1, TRACKING_REWARD, "hilo"),    # two one-step segments
+    (96, 5, 2, 3, None, "hilo"),               # three segments, the last of one step
 ])
 def test_fused_gradient_equals_forward_then_backward(M, H, C, repeat, reward, prec):
     """sim_rollout_grad runs the forward pass inside the adjoint launch; its loss,
