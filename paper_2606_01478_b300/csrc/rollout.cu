@@ -434,7 +434,7 @@ __device__ void mlp_forward(Smem& s, int r0, int lane, float h1[8][4], float h2[
 // forward activations in buffer b of s.h1 / s.h2 (hi + lo).  Writes dz1, dz2 tiles and the
 // observation adjoint into s.dobs.
 template <bool LO>
-__device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
+__device__ void mlp_backward(Smem& s, int r0, int lane, int b, float sb2[8][2]) {
   const int g = lane >> 2, tq = lane & 3;
   const int arow = r0 + (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
   // transposed B fragments: storage [k][n]
@@ -466,6 +466,12 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
     for (int n = 0; n < 8; ++n)
 #pragma unroll
       for (int e = 0; e < 4; ++e) d[n][e] *= fmaf(-h[n][e], h[n][e], 1.f);
+  }
+  // db2: this lane's two drones (rows g, g + 8) of columns 8 n + 2 tq, + 1
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    sb2[n][0] += d[n][0] + d[n][2];
+    sb2[n][1] += d[n][1] + d[n][3];
   }
   store_c64(s.dz2[b], r0, lane, d);
   // dh1[d][i] = sum_j dz2[d][j] W2[j][i]
@@ -519,14 +525,15 @@ __device__ void mlp_backward(Smem& s, int r0, int lane, int b) {
 }
 
 // dW accumulation over the CTA's 64 drones for this step (warp v's slice):
-//   dW2 rows j in [16v, 16v+16) x columns 0..64 (64 = bias b2)
+//   dW2 rows j in [16v, 16v+16) x columns 0..63
 //   dW1 rows i in [16v, 16v+16) x columns 0..15 (13 = bias b1)
-//   dW3 transposed: rows j in [16v, 16v+16) x columns o in [0, 8) (o < 4 used), and
-//   on warp 3 db3 as rows o in [0, 16) x the bias column of h2
+//   dW3 transposed: rows j in [16v, 16v+16) x columns o in [0, 8) (o < 4 used)
+// (db2 and db3, the sums of dz2 and dz3 over drones and steps, are summed by the
+// compute warps, which hold dz2 and dz3 in registers.)
 struct DwAcc {
-  float w2[9][4];
+  float w2[8][4];
   float w1[2][4];
-  float w3[2][4];  // [0]: dW3^T slice, [1]: db3 (warp 3)
+  float w3[4];
 };
 
 template <bool LO>
@@ -561,12 +568,6 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc, int hb) {
         for (int q = 0; q < 4; ++q) mma(acc.w2[n0 + q], al, bh[q >> 1][2 * (q & 1)], bh[q >> 1][2 * (q & 1) + 1]);
       }
     }
-    {
-      uint32_t bh[2];
-      ldsm_x2_t(bh, &s.h1[hb][0][(d0 + brow) * S64 + 64]);
-      mma(acc.w2[8], ah, bh[0], bh[1]);
-      if constexpr (LO) mma(acc.w2[8], al, bh[0], bh[1]);  // the bias column is exact (lo = 0)
-    }
     // dW1
     ldsm_x4_t(ah, &s.dz1[hb][0][(d0 + arow) * S64 + 16 * v + acol]);
     ldsm_x4_t(al, &s.dz1[hb][1][(d0 + arow) * S64 + 16 * v + acol]);
@@ -592,20 +593,11 @@ __device__ void accumulate_dw(Smem& s, int v, int lane, DwAcc& acc, int hb) {
       uint32_t bh[2], bl[2];
       ldsm_x2_t(bh, &s.dz3[hb][0][(d0 + brow) * S16]);
       if constexpr (LO) ldsm_x2_t(bl, &s.dz3[hb][1][(d0 + brow) * S16]);
-      mma(acc.w3[0], ah, bh[0], bh[1]);
+      mma(acc.w3, ah, bh[0], bh[1]);
       if constexpr (LO) {
-        mma(acc.w3[0], ah, bl[0], bl[1]);
-        mma(acc.w3[0], al, bh[0], bh[1]);
+        mma(acc.w3, ah, bl[0], bl[1]);
+        mma(acc.w3, al, bh[0], bh[1]);
       }
-    }
-    if (v == 3) {
-      // db3 = dz3^T 1: A = dz3^T, B = the bias column of h2 (exact, lo = 0)
-      ldsm_x4_t(ah, &s.dz3[hb][0][(d0 + arow) * S16 + acol]);
-      if constexpr (LO) ldsm_x4_t(al, &s.dz3[hb][1][(d0 + arow) * S16 + acol]);
-      uint32_t b1[2];
-      ldsm_x2_t(b1, &s.h2[hb][0][(d0 + brow) * S64 + 64]);
-      mma(acc.w3[1], ah, b1[0], b1[1]);
-      if constexpr (LO) mma(acc.w3[1], al, b1[0], b1[1]);
     }
   }
 }
@@ -615,13 +607,9 @@ __device__ void store_dw(const DwAcc& acc, int v, int lane, float* __restrict__ 
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int rr = g + (e >= 2 ? 8 : 0), cc = 2 * tq + (e & 1);
-    // dW2 / db2
+    // dW2
 #pragma unroll
-    for (int n = 0; n < 9; ++n) {
-      const int j = 16 * v + rr, i = 8 * n + cc;
-      if (i < 64) part[OFF_W2 + j * 64 + i] = acc.w2[n][e];
-      else if (i == 64) part[OFF_B2 + j] = acc.w2[n][e];
-    }
+    for (int n = 0; n < 8; ++n) part[OFF_W2 + (16 * v + rr) * 64 + 8 * n + cc] = acc.w2[n][e];
     // dW1 / db1
 #pragma unroll
     for (int n = 0; n < 2; ++n) {
@@ -629,9 +617,8 @@ __device__ void store_dw(const DwAcc& acc, int v, int lane, float* __restrict__ 
       if (c < 13) part[OFF_W1 + i * 13 + c] = acc.w1[n][e];
       else if (c == 13) part[OFF_B1 + i] = acc.w1[n][e];
     }
-    // dW3 (transposed slice: row j, column o) / db3 (row o, bias column)
-    if (cc < 4) part[OFF_W3 + cc * 64 + 16 * v + rr] = acc.w3[0][e];
-    if (v == 3 && rr < 4 && cc == 0) part[OFF_B3 + rr] = acc.w3[1][e];
+    // dW3 (transposed slice: row j, column o)
+    if (cc < 4) part[OFF_W3 + cc * 64 + 16 * v + rr] = acc.w3[e];
   }
 }
 
@@ -1347,11 +1334,11 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
     // ---------------- weight-gradient warps: slice v of dW2 / dW1 / dW3
     DwAcc acc;
 #pragma unroll
-    for (int n = 0; n < 9; ++n) acc.w2[n][0] = acc.w2[n][1] = acc.w2[n][2] = acc.w2[n][3] = 0.f;
+    for (int n = 0; n < 8; ++n) acc.w2[n][0] = acc.w2[n][1] = acc.w2[n][2] = acc.w2[n][3] = 0.f;
 #pragma unroll
     for (int n = 0; n < 2; ++n) acc.w1[n][0] = acc.w1[n][1] = acc.w1[n][2] = acc.w1[n][3] = 0.f;
 #pragma unroll
-    for (int n = 0; n < 2; ++n) acc.w3[n][0] = acc.w3[n][1] = acc.w3[n][2] = acc.w3[n][3] = 0.f;
+    acc.w3[0] = acc.w3[1] = acc.w3[2] = acc.w3[3] = 0.f;
     // Reverse steps k = H - 1 - t in processing order t.  The step of processing
     // order t + 2 is prepared in two parts: its state and reference are loaded
     // before the dW work of step t (their latency overlaps it); once all four warps
@@ -1437,6 +1424,11 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
   for (int j = 0; j < 17; ++j) lam[j] = 0.f;
   // smoothness adjoint carried from step k + 1 to a_k: -2 sd w_dact (a_{k+1} - a_k)
   float carry[4] = {0.f, 0.f, 0.f, 0.f};
+  // running sums of dz2 (this lane's two drones, its 16 columns of the fragment) and
+  // of dz3 (lanes 0-15: their drone), over all steps: db2 and db3 of the warp's drones
+  float sb2[8][2], sb3[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int n = 0; n < 8; ++n) sb2[n][0] = sb2[n][1] = 0.f;
   int t = 0;  // reverse steps processed so far (the weight-gradient warps count alike)
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int k0 = sg * a.C, k1 = min(a.H, k0 + a.C);
@@ -1547,7 +1539,10 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
 #pragma unroll
         for (int o = 0; o < 16; ++o) dz[o] = 0.f;
 #pragma unroll
-        for (int o = 0; o < 4; ++o) dz[o] = valid ? ga[o] * fmaf(-act[o], act[o], 1.f) : 0.f;
+        for (int o = 0; o < 4; ++o) {
+          dz[o] = valid ? ga[o] * fmaf(-act[o], act[o], 1.f) : 0.f;
+          sb3[o] += dz[o];
+        }
 #pragma unroll
         for (int o = 0; o < 16; o += 2) {
           uint32_t h, l;
@@ -1557,7 +1552,7 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
         }
       }
       __syncwarp();
-      mlp_backward<LO>(s, r0, lane, b);
+      mlp_backward<LO>(s, r0, lane, b, sb2);
       __syncwarp();
       mbar_arrive(&s.full[b]);  // this warp's tiles of step k are written
       // observation adjoint: obs = [p - r, q, v, w]
@@ -1567,6 +1562,44 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
       for (int j = 0; j < 17; ++j) xn[j] = x[j];
 #pragma unroll
       for (int c = 0; c < 3; ++c) rn[c] = r[c];
+    }
+  }
+  // db2, db3 of the CTA: the warp's sums over its lanes (shuffles, fixed order), then
+  // over the four compute warps in a fixed order through this warp's rows of dobs
+  // (no longer used by the sweep), written by warp 0 into the CTA's partials
+  {
+    const unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int m = 4; m < 32; m <<= 1) sb2[n][c] += __shfl_xor_sync(FULL, sb2[n][c], m);
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int m = 1; m < 32; m <<= 1) sb3[o] += __shfl_xor_sync(FULL, sb3[o], m);
+    float* red = &s.dobs[r0][0];  // 256 floats of this warp
+    __syncwarp();
+    if (lane < 4) {
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        red[8 * n + 2 * lane] = sb2[n][0];
+        red[8 * n + 2 * lane + 1] = sb2[n][1];
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int o = 0; o < 4; ++o) red[64 + o] = sb3[o];
+    }
+    asm volatile("bar.sync 1, 128;\n" ::: "memory");  // the four compute warps
+    if (v == 0) {
+      float* part = a.part + (size_t)blockIdx.x * NPOL_PAD;
+      for (int u = lane; u < 68; u += 32) {
+        const float tot = ((s.dobs[0][u] + s.dobs[16][u]) + s.dobs[32][u]) + s.dobs[48][u];
+        if (u < 64) part[OFF_B2 + u] = tot;
+        else part[OFF_B3 + u - 64] = tot;
+      }
     }
   }
   if (valid && lane < 16) {
