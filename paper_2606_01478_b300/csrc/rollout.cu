@@ -1562,18 +1562,17 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
           carry[o] = -sm;
         }
       }
-      // dz3 = ga (1 - a^2); rows of padded drones are zero
+      // dz3 = ga (1 - a^2); rows of padded drones are zero.  Columns 4-15 of the
+      // tiles stay zero from the launch's set-up
       if (lane < 16) {
-        float dz[16];
-#pragma unroll
-        for (int o = 0; o < 16; ++o) dz[o] = 0.f;
+        float dz[4];
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
           dz[o] = valid ? ga[o] * fmaf(-act[o], act[o], 1.f) : 0.f;
           sb3[o] += dz[o];
         }
 #pragma unroll
-        for (int o = 0; o < 16; o += 2) {
+        for (int o = 0; o < 4; o += 2) {
           uint32_t h, l;
           split2(dz[o], dz[o + 1], h, l);
           *reinterpret_cast<uint32_t*>(&s.dz3[b][0][row * S16 + o]) = h;
