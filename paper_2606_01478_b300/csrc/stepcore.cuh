@@ -49,10 +49,64 @@ constexpr bool lag_step_form() {
   return MODEL == SIM_FIRST_PRINCIPLES && MOTOR == MOTOR_LAG;
 }
 
+// Explicit Euler step of the abstracted model without drag (Eqs. 7-10), s + dt
+// f(s), with the step size folded into the linear terms (equal in exact
+// arithmetic; cu as for deriv_abs):
+//   p' = p + dt v,   Psi' = Psi + dt Psidot,
+//   v' = v + (dt c_f f / m) R(Psi) e3 - dt g e3,
+//   Psidot' = (dt c1) Psi + (1 + dt c2) Psidot + dt cu_Psi,
+//   f' = (1 - dt c_tau) f + dt cu_f.
+// Every right-hand side reads the state at the start of the step.  Element pairs
+// go through the packed FP32 instructions (each lane rounded as its scalar form).
+__device__ __forceinline__ void euler_abs(float* s, const float cu[4], const DevParams& P, float dt) {
+  float sr, cr, sp, cp, sy, cy;
+  __sincosf(s[3], &sr, &cr);
+  __sincosf(s[4], &sp, &cp);
+  __sincosf(s[5], &sy, &cy);
+  // third column of Rz Ry Rx
+  const float r02 = fmaf(cy * sp, cr, sy * sr);
+  const float r12 = fmaf(sy * sp, cr, -cy * sr);
+  const float r22 = cp * cr;
+  const float fmd = (dt * P.cf_inv_m) * s[12];
+  const float2 dt2 = make_float2(dt, dt);
+  const float x3 = s[3];
+  const float2 x45 = make_float2(s[4], s[5]);
+  const float2 p01 = __ffma2_rn(dt2, make_float2(s[6], s[7]), make_float2(s[0], s[1]));
+  const float2 p23 = __ffma2_rn(dt2, make_float2(s[8], s[9]), make_float2(s[2], s[3]));
+  const float2 p45 = __ffma2_rn(dt2, make_float2(s[10], s[11]), x45);
+  const float2 v01 = __ffma2_rn(make_float2(fmd, fmd), make_float2(r02, r12), make_float2(s[6], s[7]));
+  const float v2 = fmaf(fmd, r22, fmaf(-dt, P.g, s[8]));
+  const float w0 = fmaf(dt * P.c1_r, x3, fmaf(fmaf(dt, P.c2_r, 1.f), s[9], dt * cu[0]));
+  const float2 w12 = __ffma2_rn(make_float2(dt * P.c1_p, dt * P.c1_y), x45,
+                                __ffma2_rn(make_float2(fmaf(dt, P.c2_p, 1.f), fmaf(dt, P.c2_y, 1.f)),
+                                           make_float2(s[10], s[11]),
+                                           make_float2(dt * cu[1], dt * cu[2])));
+  const float f = fmaf(fmaf(-dt, P.c_tau, 1.f), s[12], dt * cu[3]);
+  s[0] = p01.x;
+  s[1] = p01.y;
+  s[2] = p23.x;
+  s[3] = p23.y;
+  s[4] = p45.x;
+  s[5] = p45.y;
+  s[6] = v01.x;
+  s[7] = v01.y;
+  s[8] = v2;
+  s[9] = w0;
+  s[10] = w12.x;
+  s[11] = w12.y;
+  s[12] = f;
+}
+
 // SYM_XY (lag step form only): Jx = Jy, the yaw rate's gyroscopic term left out.
 template <int MODEL, int INTEG, int CTRL, int MOTOR, bool SYM_XY = false>
 __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevParams& P, bool drag,
                                          float dt) {
+  if constexpr (INTEG == SIM_EULER && MODEL == SIM_ABSTRACTED) {
+    if (MOTOR == MOTOR_LAG || !drag) {  // drag exists only with general motors
+      euler_abs(s, h.cu, P, dt);
+      return;
+    }
+  }
   constexpr int D = (MODEL == SIM_FIRST_PRINCIPLES) ? 17 : 13;
   constexpr bool LSF = lag_step_form<MODEL, MOTOR>();
   float Wc[4];  // rotor-speed commands (rates cv W_cmd in the lag step form)
