@@ -97,6 +97,94 @@ __device__ __forceinline__ void euler_abs(float* s, const float cu[4], const Dev
   s[12] = f;
 }
 
+// Explicit Euler step of the first-principles model (Eqs. 1-6) under the attitude
+// interface with lag rotors, s + dt f(s), with the step size folded into the
+// constant of each term (equal in exact arithmetic; constants as in
+// deriv_fp_rate and attitude_mixer_rate_e):
+//   dt u_i = sqrt(clip(dt^2 f_i))    the step-form mixer on dt^2-scaled gains
+//   W' = (1 - dt cv) W + dt u,       v' = v + (dt kf / m) S R e3 - dt g e3,
+//   q' = q + q (x) [dt w / 2, 0],    w' = w + dt J^-1 (tau - w x J w),
+// then the quaternion renormalisation.  Every right-hand side reads the state at
+// the start of the step.  SYM_XY as for deriv_fp_rate.
+template <bool SYM_XY>
+__device__ __forceinline__ void euler_fp_lag_attitude(float* s, const CtrlHold& h, const DevParams& P,
+                                                      float dt) {
+  const float qx = s[3], qy = s[4], qz = s[5], qw = s[6];
+  const float wx = s[10], wy = s[11], wz = s[12];
+  // controller and mixer: 2 e_R from quaternions, dt u from dt^2-scaled gains
+  float ex, ey, ez;
+  attitude_error2_q(s, h.qd, ex, ey, ez);
+  const float d2 = dt * dt;
+  // products that feed an addition are rounded on their own (__fmul_rn), so that
+  // no launch shape contracts them differently (fused and single-step launches
+  // give the same state bit for bit)
+  const float A = __fmul_rn(d2 * P.cA, h.Td);
+  const float X = -fmaf(d2 * P.cRx, ex, (d2 * P.cwx) * wx);
+  const float Y = -fmaf(d2 * P.cRy, ey, (d2 * P.cwy) * wy);
+  const float Z = -fmaf(d2 * P.cRz, ez, (d2 * P.cwz) * wz);
+  const float um = d2 * P.u2max;
+  const float du0 = sqrt_approx(clampf((A - X) - (Y + Z), 0.f, um));
+  const float du1 = sqrt_approx(clampf((A - X) + (Y + Z), 0.f, um));
+  const float du2 = sqrt_approx(clampf((A + X) + (Y - Z), 0.f, um));
+  const float du3 = sqrt_approx(clampf((A + X) - (Y - Z), 0.f, um));
+  // rotor-square sums of the wrench (deriv_fp_rate)
+  const float W0 = s[13], W1 = s[14], W2 = s[15], W3 = s[16];
+  const float s0 = W0 * W0, s2 = W2 * W2;
+  const float a01 = fmaf(W1, W1, s0), a23 = fmaf(W3, W3, s2), S = a01 + a23;
+  const float e10 = fmaf(W1, W1, -s0), e32 = fmaf(W3, W3, -s2);
+  // translation
+  const float Tmd = (dt * P.kfm) * S, Tm2d = (dt * P.kfm2) * S;
+  const float2 dt2 = make_float2(dt, dt);
+  const float2 p01 = __ffma2_rn(dt2, make_float2(s[7], s[8]), make_float2(s[0], s[1]));
+  const float p2 = fmaf(dt, s[9], s[2]);
+  const float2 v01 = __ffma2_rn(make_float2(Tm2d, Tm2d),
+                                make_float2(fmaf(qx, qz, qw * qy), fmaf(qy, qz, -qw * qx)),
+                                make_float2(s[7], s[8]));
+  const float v2 = fmaf(Tmd, fmaf(qw, qw, __fmul_rn(qz, qz)) - fmaf(qx, qx, __fmul_rn(qy, qy)),
+                        fmaf(-dt, P.g, s[9]));
+  // attitude: q (x) [h, 0] with h = dt w / 2
+  const float hd = 0.5f * dt;
+  const float hx = hd * wx, hy = hd * wy, hz = hd * wz;
+  const float nqx = fmaf(qw, hx, fmaf(qy, hz, fmaf(-qz, hy, qx)));
+  const float nqy = fmaf(qw, hy, fmaf(qz, hx, fmaf(-qx, hz, qy)));
+  const float nqz = fmaf(qw, hz, fmaf(qx, hy, fmaf(-qy, hx, qz)));
+  const float nqw = fmaf(-qx, hx, fmaf(-qy, hy, fmaf(-qz, hz, qw)));
+  // body rates: roll (s2 + s3) - (s0 + s1), pitch e10 - e32, yaw e10 + e32
+  float nwx, nwy, nwz;
+  if constexpr (SYM_XY) {
+    const float t = (dt * P.cJx) * wz;
+    nwx = fmaf(dt * P.kfaJx, a23 - a01, fmaf(t, wy, wx));
+    nwy = fmaf(dt * P.kfaJy, e10 - e32, fmaf(-t, wx, wy));
+    nwz = fmaf(dt * P.kmJz, e10 + e32, wz);
+  } else {
+    nwx = fmaf(dt * P.kfaJx, a23 - a01, fmaf((dt * P.cJx) * wy, wz, wx));
+    nwy = fmaf(dt * P.kfaJy, e10 - e32, fmaf((dt * P.cJy) * wz, wx, wy));
+    nwz = fmaf(dt * P.kmJz, e10 + e32, fmaf((dt * P.cJz) * wx, wy, wz));
+  }
+  // rotors (ncv = -cv)
+  const float ar = fmaf(dt, P.ncv, 1.f);
+  const float2 W01 = __ffma2_rn(make_float2(ar, ar), make_float2(W0, W1), make_float2(du0, du1));
+  const float2 W23 = __ffma2_rn(make_float2(ar, ar), make_float2(W2, W3), make_float2(du2, du3));
+  const float in = rsqrt_approx(fmaf(nqx, nqx, fmaf(nqy, nqy, fmaf(nqz, nqz, nqw * nqw))));
+  s[0] = p01.x;
+  s[1] = p01.y;
+  s[2] = p2;
+  s[3] = nqx * in;
+  s[4] = nqy * in;
+  s[5] = nqz * in;
+  s[6] = nqw * in;
+  s[7] = v01.x;
+  s[8] = v01.y;
+  s[9] = v2;
+  s[10] = nwx;
+  s[11] = nwy;
+  s[12] = nwz;
+  s[13] = W01.x;
+  s[14] = W01.y;
+  s[15] = W23.x;
+  s[16] = W23.y;
+}
+
 // SYM_XY (lag step form only): Jx = Jy, the yaw rate's gyroscopic term left out.
 template <int MODEL, int INTEG, int CTRL, int MOTOR, bool SYM_XY = false>
 __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevParams& P, bool drag,
@@ -107,8 +195,12 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
       return;
     }
   }
-  constexpr int D = (MODEL == SIM_FIRST_PRINCIPLES) ? 17 : 13;
   constexpr bool LSF = lag_step_form<MODEL, MOTOR>();
+  if constexpr (INTEG == SIM_EULER && LSF && CTRL == SIM_CTRL_ATTITUDE) {
+    euler_fp_lag_attitude<SYM_XY>(s, h, P, dt);
+    return;
+  }
+  constexpr int D = (MODEL == SIM_FIRST_PRINCIPLES) ? 17 : 13;
   float Wc[4];  // rotor-speed commands (rates cv W_cmd in the lag step form)
   float ep[3] = {0.f, 0.f, 0.f};
   // R(q) of the state at the start of the step: the position controller's
