@@ -75,7 +75,9 @@ __device__ __forceinline__ void euler_abs(float* s, const float cu[4], const Dev
   const float2 p23 = __ffma2_rn(dt2, make_float2(s[8], s[9]), make_float2(s[2], s[3]));
   const float2 p45 = __ffma2_rn(dt2, make_float2(s[10], s[11]), x45);
   const float2 v01 = __ffma2_rn(make_float2(fmd, fmd), make_float2(r02, r12), make_float2(s[6], s[7]));
-  const float v2 = fmaf(fmd, r22, fmaf(-dt, P.g, s[8]));
+  // vertical: thrust and gravity nearly cancel near hover, so their sum is formed
+  // (one rounding) before it is added to v
+  const float v2 = s[8] + fmaf(fmd, r22, -dt * P.g);
   const float w0 = fmaf(dt * P.c1_r, x3, fmaf(fmaf(dt, P.c2_r, 1.f), s[9], dt * cu[0]));
   const float2 w12 = __ffma2_rn(make_float2(dt * P.c1_p, dt * P.c1_y), x45,
                                 __ffma2_rn(make_float2(fmaf(dt, P.c2_p, 1.f), fmaf(dt, P.c2_y, 1.f)),
@@ -140,8 +142,9 @@ __device__ __forceinline__ void euler_fp_lag_attitude(float* s, const CtrlHold& 
   const float2 v01 = __ffma2_rn(make_float2(Tm2d, Tm2d),
                                 make_float2(fmaf(qx, qz, qw * qy), fmaf(qy, qz, -qw * qx)),
                                 make_float2(s[7], s[8]));
-  const float v2 = fmaf(Tmd, fmaf(qw, qw, __fmul_rn(qz, qz)) - fmaf(qx, qx, __fmul_rn(qy, qy)),
-                        fmaf(-dt, P.g, s[9]));
+  // vertical: thrust and gravity summed first, as for the abstracted model
+  const float v2 = s[9] + fmaf(Tmd, fmaf(qw, qw, __fmul_rn(qz, qz)) - fmaf(qx, qx, __fmul_rn(qy, qy)),
+                               -dt * P.g);
   // attitude: q (x) [h, 0] with h = dt w / 2
   const float hd = 0.5f * dt;
   const float hx = hd * wx, hy = hd * wy, hz = hd * wz;
