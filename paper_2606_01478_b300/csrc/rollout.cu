@@ -1366,7 +1366,6 @@ __global__ void __launch_bounds__(3 * TPB, 1) rollout_bwd_kernel(RolloutArgs a, 
     for (int n = 0; n < 8; ++n) acc.w2[n][0] = acc.w2[n][1] = acc.w2[n][2] = acc.w2[n][3] = 0.f;
 #pragma unroll
     for (int n = 0; n < 2; ++n) acc.w1[n][0] = acc.w1[n][1] = acc.w1[n][2] = acc.w1[n][3] = 0.f;
-#pragma unroll
     acc.w3[0] = acc.w3[1] = acc.w3[2] = acc.w3[3] = 0.f;
     // Reverse steps k = H - 1 - t in processing order t.  The step of processing
     // order t + 2 is prepared in two parts: its state and reference are loaded
