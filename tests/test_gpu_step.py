@@ -2,6 +2,7 @@
 C-ABI), plus properties that hold at any size (fused K == repeated K = 1,
 determinism, layout round trip, non-finite detection)."""
 import ctypes
+import dataclasses
 
 import numpy as np
 import pytest
@@ -134,6 +135,40 @@ def test_abstracted_model_per_world_coefficients(integrator):
     gpu, _ = _run_gpu(wl)
     ref = ph.rollout_workload(wl).numpy()
     assert_parity(gpu, ref, _models_of(wl))
+
+
+@pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
+def test_abstracted_model_drag_and_general_variant(integrator):
+    """Abstracted worlds in the general rotor-model kernel variant: every other
+    world with body drag (the Euler step through the derivative), the rest
+    without drag (the Euler step with the step size folded into its terms),
+    against the FP64 oracle."""
+    wl = W.mixed_swarm_euler(M=8, N=64, steps=120, K=40)
+    worlds = np.nonzero(wl.model_of_world == 1)[0]
+    drones = (worlds[:, None] * wl.N + np.arange(wl.N)[None, :]).ravel()
+    wl.x0 = wl.x0[drones]
+    wl.cmd = wl.cmd[:, drones]
+    params = []
+    for i, w in enumerate(worlds):
+        p = dict(wl.params[w])
+        if i % 2 == 0:
+            p.update(Ca_x=-0.01, Ca_y=-0.012, Ca_z=-0.02)
+        else:
+            p.update(cv_up=40.0, cv_down=20.0)  # no drag, general rotor-model variant
+        params.append(p)
+    wl.params = params
+    wl.M = len(worlds)
+    wl.param_set_of_world = np.arange(wl.M, dtype=np.int32)
+    wl.model_of_world = np.ones(wl.M, np.int32)
+    wl.integrator = integrator
+    gpu, _ = _run_gpu(wl)
+    ref = ph.rollout_workload(wl).numpy()
+    assert_parity(gpu, ref, _models_of(wl))
+    # the drag worlds do move differently from drag-free ones with the same inputs
+    free = [dict(p, Ca_x=0.0, Ca_y=0.0, Ca_z=0.0) for p in params]
+    ref_free = ph.rollout_workload(dataclasses.replace(wl, params=free)).numpy()
+    drag_rows = np.repeat(np.arange(wl.M) % 2 == 0, wl.N)
+    assert np.abs(ref_free[drag_rows, 6:9] - ref[drag_rows, 6:9]).max() > 1e-4
 
 
 def test_attitude_swarm_full_size_sampled():
