@@ -136,12 +136,11 @@ __device__ __forceinline__ void euler_fp_lag_attitude(float* s, const CtrlHold& 
   const float e10 = fmaf(W1, W1, -s0), e32 = fmaf(W3, W3, -s2);
   // translation
   const float Tmd = (dt * P.kfm) * S, Tm2d = (dt * P.kfm2) * S;
-  const float2 dt2 = make_float2(dt, dt);
-  const float2 p01 = __ffma2_rn(dt2, make_float2(s[7], s[8]), make_float2(s[0], s[1]));
-  const float p2 = fmaf(dt, s[9], s[2]);
-  const float2 v01 = __ffma2_rn(make_float2(Tm2d, Tm2d),
-                                make_float2(fmaf(qx, qz, qw * qy), fmaf(qy, qz, -qw * qx)),
-                                make_float2(s[7], s[8]));
+  // scalar multiply-adds: as packed pairs these operands would first be moved into
+  // register pairs (measured slower than the scalar form)
+  const float p0 = fmaf(dt, s[7], s[0]), p1 = fmaf(dt, s[8], s[1]), p2 = fmaf(dt, s[9], s[2]);
+  const float v0 = fmaf(Tm2d, fmaf(qx, qz, qw * qy), s[7]);
+  const float v1 = fmaf(Tm2d, fmaf(qy, qz, -qw * qx), s[8]);
   // vertical: thrust and gravity summed first, as for the abstracted model
   const float v2 = s[9] + fmaf(Tmd, fmaf(qw, qw, __fmul_rn(qz, qz)) - fmaf(qx, qx, __fmul_rn(qy, qy)),
                                -dt * P.g);
@@ -166,26 +165,26 @@ __device__ __forceinline__ void euler_fp_lag_attitude(float* s, const CtrlHold& 
   }
   // rotors (ncv = -cv)
   const float ar = fmaf(dt, P.ncv, 1.f);
-  const float2 W01 = __ffma2_rn(make_float2(ar, ar), make_float2(W0, W1), make_float2(du0, du1));
-  const float2 W23 = __ffma2_rn(make_float2(ar, ar), make_float2(W2, W3), make_float2(du2, du3));
+  const float nW0 = fmaf(ar, W0, du0), nW1 = fmaf(ar, W1, du1);
+  const float nW2 = fmaf(ar, W2, du2), nW3 = fmaf(ar, W3, du3);
   const float in = rsqrt_approx(fmaf(nqx, nqx, fmaf(nqy, nqy, fmaf(nqz, nqz, nqw * nqw))));
-  s[0] = p01.x;
-  s[1] = p01.y;
+  s[0] = p0;
+  s[1] = p1;
   s[2] = p2;
   s[3] = nqx * in;
   s[4] = nqy * in;
   s[5] = nqz * in;
   s[6] = nqw * in;
-  s[7] = v01.x;
-  s[8] = v01.y;
+  s[7] = v0;
+  s[8] = v1;
   s[9] = v2;
   s[10] = nwx;
   s[11] = nwy;
   s[12] = nwz;
-  s[13] = W01.x;
-  s[14] = W01.y;
-  s[15] = W23.x;
-  s[16] = W23.y;
+  s[13] = nW0;
+  s[14] = nW1;
+  s[15] = nW2;
+  s[16] = nW3;
 }
 
 // SYM_XY (lag step form only): Jx = Jy, the yaw rate's gyroscopic term left out.
@@ -257,39 +256,27 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
     }
   };
   const float* R0 = NEED_R ? R : nullptr;
-  // integrator coefficient c for element j (halved for q in the lag step form)
+  // integrator coefficient c for element j (halved for q in the lag step form).
+  // The element-wise arithmetic is scalar: as packed FP32 pairs (__ffma2_rn) it
+  // measured slower under RK4 (operands moved into register pairs first).
   auto co = [&](int j, float c) { return (LSF && j >= 3 && j <= 6) ? 0.5f * c : c; };
-  // Element-wise integrator arithmetic runs on element pairs (2i, 2i + 1) with the
-  // packed FP32 instructions (two lanes per instruction, each lane rounded as its
-  // scalar counterpart); D is odd, so element D - 1 is scalar.
-  constexpr int DP = D - 1;
-  auto c2 = [&](int j, float c) { return make_float2(co(j, c), co(j + 1, c)); };
-  auto pr = [](const float* a, int j) { return make_float2(a[j], a[j + 1]); };
-  auto put = [](float* a, int j, float2 v) {
-    a[j] = v.x;
-    a[j + 1] = v.y;
-  };
   if constexpr (INTEG == SIM_EULER) {
     float d[D];
     deriv(s, d, R0);
 #pragma unroll
-    for (int j = 0; j < DP; j += 2) put(s, j, __ffma2_rn(c2(j, dt), pr(d, j), pr(s, j)));
-    s[DP] = fmaf(dt, d[DP], s[DP]);
+    for (int j = 0; j < D; ++j) s[j] = fmaf(co(j, dt), d[j], s[j]);
   } else {
     // classic RK4; in the lag step form the rotor speeds (13..16) take the
     // closed-form update and need no stage accumulator
     constexpr int NA = LSF ? 13 : D;  // elements with an RK4 accumulator
     float k[D], acc[D], xs[D], k1W[4];
     const float h2 = 0.5f * dt, h6 = dt * (1.f / 6.f);
-    const float2 two = make_float2(2.f, 2.f);
     deriv(s, k, R0);
 #pragma unroll
-    for (int j = 0; j < DP; j += 2) {
-      put(acc, j, pr(k, j));
-      put(xs, j, __ffma2_rn(c2(j, h2), pr(k, j), pr(s, j)));
+    for (int j = 0; j < D; ++j) {
+      if (j < NA) acc[j] = k[j];
+      xs[j] = fmaf(co(j, h2), k[j], s[j]);
     }
-    acc[DP] = k[DP];
-    xs[DP] = fmaf(h2, k[DP], s[DP]);
     if constexpr (LSF) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) k1W[r] = k[13 + r];
@@ -299,30 +286,20 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
       deriv(xs, k, nullptr);
       const float c = st == 0 ? h2 : dt;
 #pragma unroll
-      for (int j = 0; j < DP; j += 2) {
-        if (j < NA) put(acc, j, __ffma2_rn(two, pr(k, j), pr(acc, j)));
-        put(xs, j, __ffma2_rn(c2(j, c), pr(k, j), pr(s, j)));
+      for (int j = 0; j < D; ++j) {
+        if (j < NA) acc[j] = fmaf(2.f, k[j], acc[j]);
+        xs[j] = fmaf(co(j, c), k[j], s[j]);
       }
-      if (DP < NA) acc[DP] = fmaf(2.f, k[DP], acc[DP]);
-      xs[DP] = fmaf(c, k[DP], s[DP]);
     }
     deriv(xs, k, nullptr);
-    if constexpr (LSF) {
 #pragma unroll
-      for (int j = 0; j < 12; j += 2)
-        put(s, j, __ffma2_rn(c2(j, h6), __fadd2_rn(pr(acc, j), pr(k, j)), pr(s, j)));
-      s[12] = fmaf(h6, acc[12] + k[12], s[12]);
+    for (int j = 0; j < NA; ++j) s[j] = fmaf(co(j, h6), acc[j] + k[j], s[j]);
+    if constexpr (LSF) {
       // (1 - P4(-h)) / cv = dt (1 - h/2 + h^2/6 - h^3/24), h = cv dt
       const float hc = -P.ncv * dt;
       const float c4 = dt * fmaf(hc, fmaf(hc, fmaf(hc, -1.f / 24.f, 1.f / 6.f), -0.5f), 1.f);
-      s[13] = fmaf(c4, k1W[0], s[13]);
-      put(s, 14, __ffma2_rn(make_float2(c4, c4), make_float2(k1W[1], k1W[2]), pr(s, 14)));
-      s[16] = fmaf(c4, k1W[3], s[16]);
-    } else {
 #pragma unroll
-      for (int j = 0; j < DP; j += 2)
-        put(s, j, __ffma2_rn(c2(j, h6), __fadd2_rn(pr(acc, j), pr(k, j)), pr(s, j)));
-      s[DP] = fmaf(h6, acc[DP] + k[DP], s[DP]);
+      for (int r = 0; r < 4; ++r) s[13 + r] = fmaf(c4, k1W[r], s[13 + r]);
     }
   }
   if constexpr (MODEL == SIM_ABSTRACTED_NOTHRUST) s[12] = h.u[3];  // f_sum follows f_cmd at once
