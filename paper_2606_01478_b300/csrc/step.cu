@@ -96,7 +96,14 @@ __device__ __forceinline__ void run_drone(const StepArgs& a, int i, const DevPar
         if (a.K - k > left) next = a.cmd[(size_t)min(blk + 1, last) * n + i];
       }
       const int seg = min(left, a.K - k);
-      for (int j = 0; j < seg; ++j) one_step<MODEL, INTEG, CTRL, MOTOR, SYM>(s, h, P, drag, a.dt);
+      if constexpr (INTEG == SIM_EULER) {
+        // the short Euler step unrolled by two (measured faster than the compiler's
+        // own choice); RK4 keeps the compiler's (two measured slower there)
+#pragma unroll 2
+        for (int j = 0; j < seg; ++j) one_step<MODEL, INTEG, CTRL, MOTOR, SYM>(s, h, P, drag, a.dt);
+      } else {
+        for (int j = 0; j < seg; ++j) one_step<MODEL, INTEG, CTRL, MOTOR, SYM>(s, h, P, drag, a.dt);
+      }
       k += seg;
       left -= seg;
     }
