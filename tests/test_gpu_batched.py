@@ -108,12 +108,15 @@ def test_mixed_swarm_full_size_sampled():
 
 @pytest.mark.parametrize("integrator", [ph.EULER, ph.RK4])
 def test_single_step_launches_match_fused(integrator):
-    """K = 1 launches (the HBM-bound single-step mode, a kernel of its own) and one
-    fused launch give identical states on a mixed batch, both at parity with the
-    oracle."""
+    """K = 1 launches (the HBM-bound single-step mode, a kernel of its own) and
+    fused launches give identical states on a mixed batch, both at parity with the
+    oracle.  K = 7 splits every 10-step command block into odd runs of steps (the
+    fused Euler loop is unrolled by two)."""
     bw = W.batched_workload(13, [100, 250, 3, 77], [0, 1, 1, 0], integrator=integrator, steps=40,
                             K=40, hold=10)
     a = _gpu_batched(bw, K=40)
     b = _gpu_batched(bw, K=1)
+    c = _gpu_batched(bw, K=7)
     assert_parity(b, _oracle_batched(bw), bw.model_of_world[bw.world_of_drone()])
     assert np.array_equal(a, b)
+    assert np.array_equal(a, c)

@@ -196,10 +196,13 @@ def test_hover_fixed_point_on_gpu():
     assert np.abs(gpu[:, 7:13]).max() < 1e-5
 
 
-def test_fused_K_equals_single_steps():
+@pytest.mark.parametrize("integrator", [ph.RK4, ph.EULER])
+def test_fused_K_equals_single_steps(integrator):
     """One launch of K steps and K launches of one step run the same float
-    operations: the states agree bit for bit."""
+    operations: the states agree bit for bit (Euler: the fused hold loop is
+    unrolled by two, and K = 7 leaves odd remainders in every command block)."""
     wl = W.attitude_swarm_rk4(M=500, steps=60, K=60)
+    wl.integrator = integrator
     a, _ = _run_gpu(wl, K=60)
     b, _ = _run_gpu(wl, K=1)
     c, _ = _run_gpu(wl, K=7)
