@@ -136,8 +136,8 @@ __device__ __forceinline__ void euler_fp_lag_attitude(float* s, const CtrlHold& 
   const float e10 = fmaf(W1, W1, -s0), e32 = fmaf(W3, W3, -s2);
   // translation
   const float Tmd = (dt * P.kfm) * S, Tm2d = (dt * P.kfm2) * S;
-  // scalar multiply-adds: as packed pairs these operands would first be moved into
-  // register pairs (measured slower than the scalar form)
+  // scalar multiply-adds: as packed pairs (operands in aligned register pairs) they
+  // measured slower
   const float p0 = fmaf(dt, s[7], s[0]), p1 = fmaf(dt, s[8], s[1]), p2 = fmaf(dt, s[9], s[2]);
   const float v0 = fmaf(Tm2d, fmaf(qx, qz, qw * qy), s[7]);
   const float v1 = fmaf(Tm2d, fmaf(qy, qz, -qw * qx), s[8]);
@@ -258,7 +258,7 @@ __device__ __forceinline__ void one_step(float* s, const CtrlHold& h, const DevP
   const float* R0 = NEED_R ? R : nullptr;
   // integrator coefficient c for element j (halved for q in the lag step form).
   // The element-wise arithmetic is scalar: as packed FP32 pairs (__ffma2_rn) it
-  // measured slower under RK4 (operands moved into register pairs first).
+  // measured slower under RK4.
   auto co = [&](int j, float c) { return (LSF && j >= 3 && j <= 6) ? 0.5f * c : c; };
   if constexpr (INTEG == SIM_EULER) {
     float d[D];
